@@ -1,0 +1,179 @@
+/* mb.h -- C ABI of the GB300 mixed-basis (2D plane wave x B-spline) library.
+ *
+ * The library applies the Kohn-Sham Hamiltonian H and the overlap S of the
+ * mixed basis of Ren, Hsue and Chang (arXiv:1406.4960) to blocks of trial
+ * vectors on one CUDA device, and solves H c = eps S c for the lowest roots
+ * with the generalized Lanczos-Krylov iteration of their §II.C.
+ *
+ * Basis (§II.B.1, Eq. (6)):  <r|k+G; j> = A^{-1/2} exp(i(k+G).r_par) B_j(z)
+ * with G in the disc |k+G|^2/2 <= Ecut and B_j the order-kappa B-splines of
+ * §II.A on a clamped knot sequence, the first and last spline dropped (zero
+ * boundary values).  Units: Hartree and bohr.
+ *
+ * Coefficient blocks.  A block of `nbands` vectors at k-point ik is a device
+ * array of complex numbers, interleaved (re, im), laid out
+ *     X[band][j][g]      band < nbands, j < nb, g < ldg
+ * with g fastest.  Only g < ng(ik) are basis functions; the padding columns
+ * ng <= g < ldg are ignored on input and written as zero on output.  The
+ * element type is double2 for MB_FP64 and float2 for MB_FP32 / MB_BF16.
+ * The G order inside the disc is the library's; mb_gvectors() reports it.
+ * All device pointers are owned by the caller; the handle owns its tables.
+ *
+ * Errors.  Every call returns MB_OK (0) or an MB_E* code; nothing aborts.
+ * Calls on one handle must not overlap (one host thread per handle).
+ * Streams are passed as `void*` holding a cudaStream_t (NULL = the legacy
+ * default stream).  Device pointers must be 16-byte aligned.
+ */
+#ifndef MB_H
+#define MB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mb_handle mb_handle;
+
+enum {
+    MB_OK = 0,
+    MB_EINVAL = 1,      /* bad argument: sizes, ik, knots, grid too small for the disc */
+    MB_ENOMEM = 2,      /* device or host allocation failed */
+    MB_ENOTCONV = 3,    /* eigensolver did not reach tol within max_cycles */
+    MB_ETIMEOUT = 4,    /* a bounded device-side wait expired */
+    MB_ECUDA = 5,       /* a CUDA runtime call failed (see mb_last_cuda_error) */
+    MB_EUNSUPPORTED = 6 /* valid request this build does not implement */
+};
+
+/* Arithmetic of an apply.  MB_FP64: every step in double.  MB_FP32: B-spline
+ * evaluation, FFTs, potential product, banded terms and projector
+ * contraction in float.  MB_BF16: as MB_FP32, but the two projector
+ * contractions run on the tensor cores with bf16 operands and float
+ * accumulation. */
+typedef enum { MB_FP64 = 0, MB_FP32 = 1, MB_BF16 = 2 } mb_prec;
+
+/* In-plane lattice vectors (bohr). */
+typedef struct { double a1[2]; double a2[2]; } mb_cell;
+
+/* One atom of the surface unit cell.
+ * Local pseudopotential (§II.B.1, Eq. (10), Gaussian part):
+ *     A * exp(-|r - pos|^2 / (2 w^2))            (A in Ha, w in bohr)
+ * Kleinman-Bylander projectors (Eq. (14)), GTH Gaussian radial part with
+ * alpha = 1 / (2 rc^2): nproj = 0 (none) or 4 (s, p_x, p_y, p_z), each
+ * normalized to unit norm, with strengths E[0..3] in Ha (a physical p
+ * channel has E[1] = E[2] = E[3]). */
+typedef struct {
+    double pos[3];
+    double A;
+    double w;
+    int nproj;
+    double E[4];
+    double rc;
+} mb_atom;
+
+typedef struct {
+    int n1, n2;        /* in-plane FFT grid; powers of two in [4, 256], each
+                          at least 2*max|n_i| + 1 over the discs of all k */
+    int nquad;         /* Gauss-Legendre points per knot interval (0: order) */
+    int device;        /* CUDA device ordinal */
+    int max_bands;     /* largest block passed to the apply calls (0: 128);
+                          sizes the handle's scratch */
+    double precond_shift; /* c of the eigensolver's (T(G) + c S)^-1 (0: 1 Ha) */
+} mb_opts;
+
+/* Build the basis and every device table for `nk` k-points.
+ *   cell     in-plane lattice
+ *   kpts     nk x 2 cartesian in-plane wave vectors (1/bohr), host
+ *   ecut     plane-wave cutoff on |k+G|^2/2 (Ha)
+ *   breaks   nbreaks strictly increasing z breakpoints (bohr), host; the
+ *            knot sequence is clamped (end breakpoints repeated `order` times),
+ *            so there are n_int = nbreaks - 1 intervals and
+ *            nb = n_int + order - 3 retained B-splines
+ *   order    B-spline order kappa in [3, 8]; n_int >= order
+ *   atoms    natoms atoms (host); may be NULL when natoms == 0
+ *   opts     grid, quadrature and device (host, required)
+ * Cites: §II.A (knots, Eqs. (1)-(3)), §II.B.1 (Eqs. (6)-(17)).
+ * Errors: MB_EINVAL, MB_ENOMEM, MB_ECUDA.  *out is NULL on failure. */
+int mb_setup(const mb_cell *cell, const double *kpts, int nk, double ecut,
+             const double *breaks, int nbreaks, int order,
+             const mb_atom *atoms, int natoms, const mb_opts *opts,
+             mb_handle **out);
+
+/* Release everything the handle owns.  NULL is ignored. */
+void mb_destroy(mb_handle *h);
+
+/* Sizes at k-point ik: disc size ng, retained B-splines nb, padded stride
+ * ldg (a multiple of 32).  Any output pointer may be NULL. */
+int mb_sizes(const mb_handle *h, int ik, int *ng, int *nb, int *ldg);
+
+/* Integer coordinates (n1, n2) of G = n1 b1 + n2 b2 for each g < ng in the
+ * library's order: idx[2*g], idx[2*g+1].  Host buffer of 2*ng ints. */
+int mb_gvectors(const mb_handle *h, int ik, int *idx);
+
+/* Number of z quadrature planes (n_int * nquad) and, if the pointers are not
+ * NULL, their abscissae and weights (host buffers of that length). */
+int mb_zplanes(const mb_handle *h, int *nq, double *zq, double *wq);
+
+/* Replace the local potential by a caller-given real table
+ * V[q][i1][i2] = V(r_par = i1/n1 a1 + i2/n2 a2, z_q) in Ha on the quadrature
+ * planes (host, nq*n1*n2 doubles) -- the general local potential of
+ * §II.B.1, Eqs. (19)-(20).  Projectors are unchanged. */
+int mb_set_local_potential(mb_handle *h, const double *V);
+
+/* Y = H X at k-point ik (§II.B.1: kinetic Eq. (9), local potential through
+ * in-plane FFTs on the quadrature planes, Kleinman-Bylander Eq. (17)).
+ * X and Y are distinct device blocks of nbands (1 <= nbands <= max_bands)
+ * in the element type of `prec`.  Asynchronous on `stream`. */
+int mb_apply_H(mb_handle *h, int ik, const void *X, void *Y, int nbands,
+               int prec, void *stream);
+
+/* Y = H X for several k-points in one pass: X[i], Y[i] are the blocks of
+ * k-point iks[i] (host arrays of nsel device pointers). */
+int mb_apply_H_batch(mb_handle *h, int nsel, const int *iks,
+                     const void *const *X, void *const *Y, int nbands,
+                     int prec, void *stream);
+
+/* Y = S X (§II.B.1, Eqs. (7)-(8): S is G-diagonal and banded in j). */
+int mb_apply_S(mb_handle *h, int ik, const void *X, void *Y, int nbands,
+               int prec, void *stream);
+
+/* Y = S^-1 X from the banded Cholesky factor of the G-independent S_z. */
+int mb_apply_Sinv(mb_handle *h, int ik, const void *X, void *Y, int nbands,
+                  int prec, void *stream);
+
+typedef struct {
+    int cycles;           /* grand cycles used (§II.C) */
+    int applies;          /* vectors multiplied by H */
+    double max_residual;  /* max_i ||H x_i - eps_i S x_i||_{S^-1} at exit */
+    double seconds;       /* wall time of the call */
+} mb_solve_info;
+
+typedef struct {
+    int krylov_depth;     /* k of K = span{v, A v, ..., A^k v} (0: 4) */
+    int block;            /* roots per block in the second grand cycle (0: 4) */
+    int max_cycles;       /* (0: 200) */
+    int polish;           /* mixed precision only: FP64 cycles at the end (0: auto) */
+} mb_solve_opts;
+
+/* Lowest `nbands` roots of H c = eps S c at every k-point (§II.C).
+ *   prec   MB_FP64: all applies in double ("plain").  MB_FP32 / MB_BF16:
+ *          applies in that precision, Gram-Schmidt and Rayleigh-Ritz in
+ *          double, then FP64 polish cycles until the FP64 residual < tol.
+ *   tol    residual tolerance ||H x - eps S x||_{S^-1} (Ha)
+ *   evals  host, nk*nbands doubles, ascending per k
+ *   evecs  optional device pointer (NULL: not returned): nk blocks of
+ *          nbands double2 vectors, block ik at offset sum_{i<ik} nbands*nb*ldg(i)
+ *   sopts  optional (NULL: defaults); info optional.
+ * Returns MB_ENOTCONV (evals still written) if max_cycles is reached. */
+int mb_eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals,
+                void *evecs, const mb_solve_opts *sopts, mb_solve_info *info,
+                void *stream);
+
+/* Message for an error code (static storage). */
+const char *mb_strerror(int code);
+
+/* The last CUDA error string seen by this handle (static storage, or ""). */
+const char *mb_last_cuda_error(const mb_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MB_H */

@@ -201,6 +201,25 @@ def _rayleigh_ritz(V, HV):
     return jacobi_herm(Hs)
 
 
+def select_roots(w, Y, b, eps_in):
+    """Maximum-overlap choice of b Ritz pairs in a block, plus new roots.
+
+    <y_l|S|x_j> = Y[j, l] because the block's inputs are the first b columns of
+    an S-orthonormal basis."""
+    ov = np.sum(np.abs(Y[:b, :]) ** 2, axis=0)
+    chosen = list(np.argsort(-ov, kind="stable")[:b])
+    lowest_in = float(np.min(eps_in))
+    for l in range(len(w)):
+        if l in chosen:
+            continue
+        if w[l] < lowest_in and ov[l] < 0.5:
+            worst = max(chosen, key=lambda c: w[c])
+            if w[l] < w[worst]:
+                chosen[chosen.index(worst)] = l
+    chosen.sort(key=lambda c: w[c])
+    return Y[:, chosen], w[chosen]
+
+
 def residual_norms(ops, X, HX, SX, eps):
     R = HX - SX * eps[None, :]
     SiR = ops.Sinv(R)
@@ -230,33 +249,24 @@ def lanczos_krylov(ops, X0, nroots, depth=4, block=8, tol=1e-8, max_cycles=300,
         HV = np.hstack([HX, ops.H(K)]) if K.shape[1] else HX
         w, Y = _rayleigh_ritz(V, HV)
         X, SX, HX, eps = V @ Y[:, :M], SV @ Y[:, :M], HV @ Y[:, :M], w[:M].copy()
-        # --- cycle B: blocks of roots, each with its own Krylov space
+        # --- cycle B: blocks of roots, each with its own Krylov space.  The
+        # blocks are independent: every Krylov space is S-orthogonalized
+        # against the roots as they stand when the cycle starts.
+        Xc, SXc, HXc, epsc = X.copy(), SX.copy(), HX.copy(), eps.copy()
+        res_all = residual_norms(ops, Xc, HXc, SXc, epsc)
         for b0 in range(0, M, block):
             blk = list(range(b0, min(M, b0 + block)))
-            res_b = residual_norms(ops, X[:, blk], HX[:, blk], SX[:, blk], eps[blk])
-            seed = blk[int(np.argmax(res_b))]
-            K, SK = _krylov(ops, X[:, seed], eps[seed], X, SX, depth)
+            seed = blk[int(np.argmax(res_all[blk]))]
+            K, SK = _krylov(ops, Xc[:, seed], epsc[seed], Xc, SXc, depth)
             if K.shape[1] == 0:
                 continue
-            Xb, SXb, HXb = X[:, blk], SX[:, blk], HX[:, blk]
-            V = np.hstack([Xb, K])
-            SV = np.hstack([SXb, SK])
-            HV = np.hstack([HXb, ops.H(K)])
+            V = np.hstack([Xc[:, blk], K])
+            SV = np.hstack([SXc[:, blk], SK])
+            HV = np.hstack([HXc[:, blk], ops.H(K)])
             w, Y = _rayleigh_ritz(V, HV)
-            ov = np.sum(np.abs(Y[:len(blk), :]) ** 2, axis=0)   # <y|S|x_j> = Y[j, l]
-            chosen = list(np.argsort(-ov, kind="stable")[:len(blk)])
-            lowest_in = float(np.min(eps[blk]))
-            for l in range(len(w)):
-                if l in chosen:
-                    continue
-                if w[l] < lowest_in and ov[l] < 0.5:
-                    worst = max(chosen, key=lambda c: w[c])
-                    if w[l] < w[worst]:
-                        chosen[chosen.index(worst)] = l
-            chosen.sort(key=lambda c: w[c])
-            Yc = Y[:, chosen]
+            Yc, wc = select_roots(w, Y, len(blk), epsc[blk])
             X[:, blk], SX[:, blk], HX[:, blk] = V @ Yc, SV @ Yc, HV @ Yc
-            eps[blk] = w[chosen]
+            eps[blk] = wc
         # keep the set ordered and S-orthonormal for the next cycle A
         X, SX = s_orthonormalize(ops, X)
         HX = ops.H(X)

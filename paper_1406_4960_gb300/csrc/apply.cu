@@ -1,0 +1,730 @@
+// H and S applies of the mixed basis on one GPU (sm_103a).
+//
+//  plane_kernel   local potential (§II.B.1, Eqs. (12)-(13), (19)-(20)):
+//                 B-spline evaluation on the Gauss planes, inverse 2D FFT,
+//                 product with w_q V(r, z_q), forward 2D FFT, adjoint
+//                 B-spline sum back to coefficients.  One CTA owns a
+//                 (k, band, run of knot intervals) and keeps the kappa
+//                 output rows that the current interval touches in a ring in
+//                 shared memory; rows shared with a neighbouring run go to
+//                 scratch and are summed in a fixed order by the epilogue.
+//  epilogue       kinetic term Eq. (9) (banded in j, diagonal in G) plus the
+//                 boundary-row sums.
+//  zgemm          projector contractions of Eq. (17), factorized as
+//                 u_p(G, j) = z_p(j) q_p(G): W = X q^H, then
+//                 Y += (z E F) q with F_p = sum_j z_p(j) W_p(j).
+//  banded_*       S (Eqs. (7)-(8)), S^-1 and the eigensolver's
+//                 preconditioner through banded Cholesky factors.
+#include <algorithm>
+#include <cstring>
+
+#include "cplx.cuh"
+#include "mb_internal.h"
+
+namespace mb {
+
+constexpr int kMaxK = 64;   // k-points per launch (descriptors travel as kernel parameters)
+
+struct KDesc {
+    const void *X;
+    void *Y;
+    void *part;      // boundary partial rows
+    void *W;         // projector overlaps W[(b, j)][p]
+    void *C;         // back-projection coefficients C[(b, j)][p]
+    int ng, ldg;
+    int kofs;        // offset of per-k G arrays
+    int qofs;        // offset of q_p(G) table
+};
+
+template <typename R> struct PlaneArgs {
+    const R *Bq;
+    const R *V;
+    const typename V2<R>::T *tw;
+    const int *goff;
+    int n1, n2, l1, l2, nmax;
+    int order, nquad, nint, nb;
+    int nbands, nchunks, chunk, np, ldg_max;
+    int nsel;
+    KDesc d[kMaxK];
+};
+
+// ---------------------------------------------------------------------------
+// radix-2 FFTs on ns planes of N1 x N2 in shared memory (row-major, i2 fastest)
+// Inverse: decimation in frequency, natural in -> bit-reversed out, sign +.
+// Forward: decimation in time, bit-reversed in -> natural out, sign -.
+template <typename R2, bool INV>
+__device__ void fft_axis(R2 *buf, int ns, int N1, int N2, int axis, const R2 *tw, int nmax) {
+    const int NN = N1 * N2;
+    const int N = axis == 2 ? N2 : N1;
+    const int estride = axis == 2 ? 1 : N2;
+    const int ntr_plane = axis == 2 ? N1 : N2;
+    const int ntr = ns * ntr_plane;
+    const int nbf = ntr * (N / 2);
+    for (int stage = 0, half = INV ? N / 2 : 1; INV ? half >= 1 : half < N;
+         ++stage, half = INV ? half / 2 : half * 2) {
+        const int twstep = nmax / (2 * half);
+        for (int bi = threadIdx.x; bi < nbf; bi += blockDim.x) {
+            int tr = bi / (N / 2);
+            int r = bi - tr * (N / 2);
+            int plane = tr / ntr_plane;
+            int line = tr - plane * ntr_plane;
+            int base = plane * NN + (axis == 2 ? line * N2 : line);
+            int grp = r / half;
+            int j = r - grp * half;
+            int i0 = grp * 2 * half + j;
+            int i1 = i0 + half;
+            R2 w = tw[j * twstep];
+            R2 *p0 = buf + base + i0 * estride;
+            R2 *p1 = buf + base + i1 * estride;
+            R2 a = *p0, b = *p1;
+            if (INV) {
+                *p0 = a + b;
+                *p1 = cmul(a - b, w);
+            } else {
+                R2 t = cmul_c(b, w);
+                *p0 = a + t;
+                *p1 = a - t;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) plane_kernel(const __grid_constant__ PlaneArgs<R> a) {
+    typedef typename V2<R>::T R2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int NN = a.n1 * a.n2;
+    const int K = a.order, P = a.nquad;
+    R2 *tw = reinterpret_cast<R2 *>(smem_raw);
+    R2 *buf = tw + a.nmax / 2;
+    R2 *acc = buf + (size_t)a.np * NN;
+    for (int i = threadIdx.x; i < a.nmax / 2; i += blockDim.x) tw[i] = a.tw[i];
+
+    const int item = blockIdx.x;
+    const int c = item % a.nchunks;
+    const int kb = item / a.nchunks;
+    const int b = kb % a.nbands;
+    const int ks = kb / a.nbands;
+    const KDesc &d = a.d[ks];
+    const int ldg = d.ldg, ng = d.ng, nb = a.nb;
+    const R2 *X = reinterpret_cast<const R2 *>(d.X) + (size_t)b * nb * ldg;
+    R2 *Y = reinterpret_cast<R2 *>(d.Y) + (size_t)b * nb * ldg;
+    R2 *part = reinterpret_cast<R2 *>(d.part) + (size_t)b * (a.nchunks - 1) * 2 * (K - 1) * ldg;
+    const int *goff = a.goff + d.kofs;
+    const int t0 = c * a.chunk, t1 = min(a.nint, t0 + a.chunk);
+
+    for (int i = threadIdx.x; i < K * ldg; i += blockDim.x) acc[i] = czero<R2>();
+    __syncthreads();
+
+    auto write_row = [&](int j) {
+        R2 *slot = acc + (size_t)(j % K) * ldg;
+        int lo = max(0, j - K + 2), hi = min(a.nint - 1, j + 1);
+        R2 *dst;
+        if (lo >= t0 && hi <= t1 - 1)
+            dst = Y + (size_t)j * ldg;
+        else if (lo < t0)   // shared with the previous run: right-hand side of boundary c-1
+            dst = part + ((size_t)((c - 1) * 2 + 1) * (K - 1) + (j - (t0 - 1))) * ldg;
+        else                // shared with the next run: left-hand side of boundary c
+            dst = part + ((size_t)(c * 2 + 0) * (K - 1) + (j - (t1 - 1))) * ldg;
+        for (int g = threadIdx.x; g < ldg; g += blockDim.x) {
+            dst[g] = g < ng ? slot[g] : czero<R2>();
+            slot[g] = czero<R2>();
+        }
+    };
+
+    for (int t = t0; t < t1; ++t) {
+        for (int s0 = 0; s0 < P; s0 += a.np) {
+            const int ns = min(a.np, P - s0);
+            const int q0 = t * P + s0;
+            for (int e = threadIdx.x; e < ns * NN; e += blockDim.x) buf[e] = czero<R2>();
+            __syncthreads();
+            // (a) B-spline evaluation: psi_q(G) = sum_m B_{t+m}(z_q) X[t+m-1][G]
+            for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+                R2 x[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    int j = t + m - 1;
+                    x[m] = (m < K && j >= 0 && j < nb) ? X[(size_t)j * ldg + g] : czero<R2>();
+                }
+                const int o = goff[g];
+                for (int s = 0; s < ns; ++s) {
+                    const R *bq = a.Bq + (size_t)(q0 + s) * K;
+                    R2 psi = czero<R2>();
+#pragma unroll
+                    for (int m = 0; m < 8; ++m)
+                        if (m < K) rfma(psi, bq[m], x[m]);
+                    buf[s * NN + o] = psi;
+                }
+            }
+            __syncthreads();
+            // (b) inverse 2D FFT to the real-space plane
+            fft_axis<R2, true>(buf, ns, a.n1, a.n2, 2, tw, a.nmax);
+            fft_axis<R2, true>(buf, ns, a.n1, a.n2, 1, tw, a.nmax);
+            // (c) w_q V(r, z_q) / (N1 N2)
+            const R *V = a.V + (size_t)q0 * NN;
+            for (int e = threadIdx.x; e < ns * NN; e += blockDim.x) buf[e] = rscale(V[e], buf[e]);
+            __syncthreads();
+            fft_axis<R2, false>(buf, ns, a.n1, a.n2, 1, tw, a.nmax);
+            fft_axis<R2, false>(buf, ns, a.n1, a.n2, 2, tw, a.nmax);
+            // (d) adjoint: acc[t+m-1][G] += sum_q B_{t+m}(z_q) phi_q(G)
+            for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+                const int o = goff[g];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    int j = t + m - 1;
+                    if (m >= K || j < 0 || j >= nb) continue;
+                    R2 sum = czero<R2>();
+                    for (int s = 0; s < ns; ++s) rfma(sum, a.Bq[(size_t)(q0 + s) * K + m], buf[s * NN + o]);
+                    acc[(size_t)(j % K) * ldg + g] += sum;
+                }
+            }
+            __syncthreads();
+        }
+        if (t - 1 >= 0) write_row(t - 1);
+        __syncthreads();
+    }
+    for (int j = max(0, t1 - 1); j <= t1 + K - 3 && j < nb; ++j) {
+        write_row(j);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// epilogue: Y[j] = local(j) + (D/2 + |k+G|^2/2 S) X   (Eq. (9))
+template <typename R> struct EpiArgs {
+    const R *Sband, *Dband, *q2;
+    int order, nb, nbands, nchunks, chunk, nint;
+    KDesc d[kMaxK];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) epilogue_kernel(const __grid_constant__ EpiArgs<R> a) {
+    typedef typename V2<R>::T R2;
+    const int j = blockIdx.x, b = blockIdx.y, ks = blockIdx.z;
+    const KDesc &d = a.d[ks];
+    const int K = a.order, W = 2 * K - 1, ldg = d.ldg, nb = a.nb;
+    const R2 *X = reinterpret_cast<const R2 *>(d.X) + (size_t)b * nb * ldg;
+    R2 *Y = reinterpret_cast<R2 *>(d.Y) + (size_t)b * nb * ldg;
+    const R2 *part = reinterpret_cast<const R2 *>(d.part) + (size_t)b * (a.nchunks - 1) * 2 * (K - 1) * ldg;
+    // boundary c between runs c and c+1 covers rows [t1 - 1, t1 + K - 3], t1 = (c+1)*chunk
+    int bc = -1, br = 0;
+    for (int c = 0; c + 1 < a.nchunks; ++c) {
+        int t1 = (c + 1) * a.chunk;
+        if (j >= t1 - 1 && j <= t1 + K - 3) { bc = c; br = j - (t1 - 1); }
+    }
+    const R *q2 = a.q2 + d.kofs;
+    const R *Sr = a.Sband + (size_t)j * W;
+    const R *Dr = a.Dband + (size_t)j * W;
+    for (int g = threadIdx.x; g < ldg; g += blockDim.x) {
+        if (g >= d.ng) { Y[(size_t)j * ldg + g] = czero<R2>(); continue; }
+        R2 v;
+        if (bc >= 0) {
+            const R2 *p0 = part + ((size_t)(bc * 2 + 0) * (K - 1) + br) * ldg;
+            const R2 *p1 = part + ((size_t)(bc * 2 + 1) * (K - 1) + br) * ldg;
+            v = p0[g] + p1[g];
+        } else {
+            v = Y[(size_t)j * ldg + g];
+        }
+        const R hq = R(0.5) * q2[g];
+        R2 tx = czero<R2>();
+        for (int dd = 0; dd < W; ++dd) {
+            int jj = j + dd - (K - 1);
+            if (jj < 0 || jj >= nb) continue;
+            R coef = R(0.5) * Dr[dd] + hq * Sr[dd];
+            rfma(tx, coef, X[(size_t)jj * ldg + g]);
+        }
+        Y[(size_t)j * ldg + g] = v + tx;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// complex GEMM, batched over k-points:
+//   mode 0 (projection):      W[m][n] = sum_k A[m][k] conj(Q[n][k])   A = X rows, Q = q_p(G)
+//   mode 1 (back-projection): Y[m][n] += sum_k C[m][k] Q[k][n]        C = coefficients
+// m = (band, j) rows; 64x64 output tile, 256 threads, 4x4 outputs each.
+template <typename R> struct GemmArgs {
+    const typename V2<R>::T *Q;   // q_p(G) table (all k)
+    int mode, nb, nbands, nproj;
+    KDesc d[kMaxK];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) zgemm_kernel(const __grid_constant__ GemmArgs<R> a) {
+    typedef typename V2<R>::T R2;
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ R2 As[BK][BM + 1];
+    __shared__ R2 Bs[BK][BN + 1];
+    const int ks = blockIdx.z;
+    const KDesc &d = a.d[ks];
+    const int ldg = d.ldg;
+    const int M = a.nbands * a.nb;
+    const int N = a.mode == 0 ? a.nproj : d.ng;
+    const int KK = a.mode == 0 ? d.ng : a.nproj;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    if (n0 >= N) return;
+    const R2 *Q = a.Q + d.qofs;
+    const R2 *A = a.mode == 0 ? reinterpret_cast<const R2 *>(d.X) : reinterpret_cast<const R2 *>(d.C);
+    const int lda = a.mode == 0 ? ldg : a.nproj;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    R2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jn = 0; jn < 4; ++jn) acc[i][jn] = czero<R2>();
+    for (int k0 = 0; k0 < KK; k0 += BK) {
+        for (int e = threadIdx.x; e < BM * BK; e += 256) {
+            int mm = e / BK, kk = e % BK;
+            int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < M && gk < KK) ? A[(size_t)gm * lda + gk] : czero<R2>();
+        }
+        for (int e = threadIdx.x; e < BN * BK; e += 256) {
+            int nn, kk;
+            R2 v = czero<R2>();
+            if (a.mode == 0) {   // B[k][n] = conj(Q[n][k])
+                nn = e / BK; kk = e % BK;
+                int gn = n0 + nn, gk = k0 + kk;
+                if (gn < N && gk < KK) { R2 q = Q[(size_t)gn * ldg + gk]; v = mk(q.x, -q.y); }
+            } else {             // B[k][n] = Q[k][n]
+                kk = e / BN; nn = e % BN;
+                int gn = n0 + nn, gk = k0 + kk;
+                if (gn < N && gk < KK) v = Q[(size_t)gk * ldg + gn];
+            }
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            R2 av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) bv[i] = Bs[kk][tx * 4 + i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jn = 0; jn < 4; ++jn) cfma(acc[i][jn], av[i], bv[jn]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gm = m0 + ty * 4 + i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int jn = 0; jn < 4; ++jn) {
+            int gn = n0 + tx * 4 + jn;
+            if (gn >= N) continue;
+            if (a.mode == 0) {
+                reinterpret_cast<R2 *>(d.W)[(size_t)gm * a.nproj + gn] = acc[i][jn];
+            } else {
+                R2 *y = reinterpret_cast<R2 *>(d.Y) + (size_t)gm * ldg + gn;
+                *y = *y + acc[i][jn];
+            }
+        }
+    }
+}
+
+// F_p(b) = sum_j z_p(j) W[(b,j)][p];  C[(b,j)][p] = z_p(j) E_p F_p(b)
+template <typename R> struct CoefArgs {
+    const R *zproj, *E;
+    int nb, nbands, nproj;
+    KDesc d[kMaxK];
+};
+
+template <typename R>
+__global__ void coef_kernel(const __grid_constant__ CoefArgs<R> a) {
+    typedef typename V2<R>::T R2;
+    const int ks = blockIdx.y;
+    const KDesc &d = a.d[ks];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.nbands * a.nproj) return;
+    const int b = idx / a.nproj, p = idx % a.nproj;
+    const R2 *W = reinterpret_cast<const R2 *>(d.W) + (size_t)b * a.nb * a.nproj;
+    R2 *C = reinterpret_cast<R2 *>(d.C) + (size_t)b * a.nb * a.nproj;
+    const R *z = a.zproj + (size_t)p * a.nb;
+    R2 F = czero<R2>();
+    for (int j = 0; j < a.nb; ++j) rfma(F, z[j], W[(size_t)j * a.nproj + p]);
+    F = rscale(a.E[p], F);
+    for (int j = 0; j < a.nb; ++j) C[(size_t)j * a.nproj + p] = rscale(z[j], F);
+}
+
+// ---------------------------------------------------------------------------
+// banded operators along j, one thread per (band, G) column
+template <typename R>
+__global__ void banded_S_kernel(const R *Sband, int order, int nb, int ng, int ldg, int nbands,
+                                const typename V2<R>::T *X, typename V2<R>::T *Y) {
+    typedef typename V2<R>::T R2;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (g >= ldg) return;
+    const int K = order, W = 2 * K - 1;
+    const R2 *x = X + (size_t)b * nb * ldg;
+    R2 *y = Y + (size_t)b * nb * ldg;
+    for (int j = 0; j < nb; ++j) {
+        R2 s = czero<R2>();
+        if (g < ng)
+            for (int dd = 0; dd < W; ++dd) {
+                int jj = j + dd - (K - 1);
+                if (jj >= 0 && jj < nb) rfma(s, Sband[(size_t)j * W + dd], x[(size_t)jj * ldg + g]);
+            }
+        y[(size_t)j * ldg + g] = s;
+    }
+}
+
+// L L^T y = x with L[j][j-d] = Lb[(j*K + d)] (per-G factors when gstride > 0)
+template <typename R>
+__global__ void banded_solve_kernel(const R *Lb, size_t gstride, int order, int nb, int ng, int ldg,
+                                    int nbands, const typename V2<R>::T *X, typename V2<R>::T *Y) {
+    typedef typename V2<R>::T R2;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (g >= ldg) return;
+    const int K = order;
+    const R *L = Lb + gstride * g;
+    const R2 *x = X + (size_t)b * nb * ldg;
+    R2 *y = Y + (size_t)b * nb * ldg;
+    if (g >= ng) {
+        for (int j = 0; j < nb; ++j) y[(size_t)j * ldg + g] = czero<R2>();
+        return;
+    }
+    for (int j = 0; j < nb; ++j) {
+        R2 s = x[(size_t)j * ldg + g];
+        for (int dd = 1; dd < K && dd <= j; ++dd) rfma(s, -L[(size_t)j * K + dd], y[(size_t)(j - dd) * ldg + g]);
+        y[(size_t)j * ldg + g] = rscale(R(1) / L[(size_t)j * K], s);
+    }
+    for (int j = nb - 1; j >= 0; --j) {
+        R2 s = y[(size_t)j * ldg + g];
+        for (int dd = 1; dd < K && j + dd < nb; ++dd)
+            rfma(s, -L[(size_t)(j + dd) * K + dd], y[(size_t)(j + dd) * ldg + g]);
+        y[(size_t)j * ldg + g] = rscale(R(1) / L[(size_t)j * K], s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+int cuda_fail(mb_handle *h, cudaError_t e) {
+    h->last_cuda_error = cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? MB_ENOMEM : MB_ECUDA;
+}
+
+#define MB_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_); \
+    } while (0)
+
+template <typename R>
+static int upload(mb_handle *h, void **dst, const std::vector<double> &src) {
+    std::vector<R> tmp(src.begin(), src.end());
+    if (*dst) cudaFree(*dst);
+    *dst = nullptr;
+    if (tmp.empty()) return MB_OK;
+    MB_CUDA(cudaMalloc(dst, tmp.size() * sizeof(R)));
+    MB_CUDA(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(R), cudaMemcpyHostToDevice));
+    return MB_OK;
+}
+
+template <typename R>
+static int upload_complex(mb_handle *h, void **dst, const std::vector<cdouble> &src) {
+    std::vector<R> tmp(2 * src.size());
+    for (size_t i = 0; i < src.size(); ++i) {
+        tmp[2 * i] = (R)src[i].real();
+        tmp[2 * i + 1] = (R)src[i].imag();
+    }
+    if (*dst) cudaFree(*dst);
+    *dst = nullptr;
+    if (tmp.empty()) return MB_OK;
+    MB_CUDA(cudaMalloc(dst, tmp.size() * sizeof(R)));
+    MB_CUDA(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(R), cudaMemcpyHostToDevice));
+    return MB_OK;
+}
+
+template <typename R>
+static int upload_set(mb_handle *h, DevTables &t) {
+    int rc;
+    if ((rc = upload<R>(h, &t.Bq, h->Bq))) return rc;
+    if ((rc = upload<R>(h, &t.Sband, h->Sb))) return rc;
+    if ((rc = upload<R>(h, &t.Dband, h->Db))) return rc;
+    if ((rc = upload<R>(h, &t.Lband, h->Lb))) return rc;
+    std::vector<double> q2((size_t)h->total_ldg, 0.0);
+    std::vector<cdouble> qp;
+    for (size_t ik = 0; ik < h->kp.size(); ++ik) {
+        const KPoint &kp = h->kp[ik];
+        for (int g = 0; g < kp.ng; ++g) q2[h->kofs[ik] + g] = kp.q2[g];
+        qp.insert(qp.end(), kp.qproj.begin(), kp.qproj.end());
+    }
+    if ((rc = upload<R>(h, &t.q2, q2))) return rc;
+    if ((rc = upload_complex<R>(h, &t.qproj, qp))) return rc;
+    if ((rc = upload<R>(h, &t.zproj, h->zproj))) return rc;
+    if ((rc = upload<R>(h, &t.E, h->Eproj))) return rc;
+    const int nmax = std::max(h->n1, h->n2);
+    std::vector<cdouble> tw(nmax / 2);
+    for (int i = 0; i < nmax / 2; ++i) tw[i] = std::polar(1.0, 2.0 * 3.14159265358979323846 * i / nmax);
+    if ((rc = upload_complex<R>(h, &t.tw, tw))) return rc;
+    return MB_OK;
+}
+
+int upload_potential(mb_handle *h) {
+    std::vector<double> vp;
+    vtable_permuted(h, vp);
+    int rc;
+    if ((rc = upload<double>(h, &h->t64.V, vp))) return rc;
+    if ((rc = upload<float>(h, &h->t32.V, vp))) return rc;
+    return MB_OK;
+}
+
+int upload_tables(mb_handle *h) {
+    MB_CUDA(cudaSetDevice(h->device));
+    int rc;
+    if ((rc = upload_set<double>(h, h->t64))) return rc;
+    if ((rc = upload_set<float>(h, h->t32))) return rc;
+    if ((rc = upload_potential(h))) return rc;
+    std::vector<int> goff((size_t)h->total_ldg, 0);
+    for (size_t ik = 0; ik < h->kp.size(); ++ik)
+        for (int g = 0; g < h->kp[ik].ng; ++g) goff[h->kofs[ik] + g] = h->kp[ik].goff[g];
+    MB_CUDA(cudaMalloc(&h->d_goff, goff.size() * sizeof(int)));
+    MB_CUDA(cudaMemcpy(h->d_goff, goff.data(), goff.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return MB_OK;
+}
+
+int ensure_precond(mb_handle *h) {
+    if (h->pfac_ready) return MB_OK;
+    std::vector<double> all;
+    for (size_t ik = 0; ik < h->kp.size(); ++ik) {
+        std::vector<double> f;
+        precond_factors(h, (int)ik, h->precond_shift, f);
+        all.insert(all.end(), f.begin(), f.end());
+    }
+    int rc;
+    if ((rc = upload<double>(h, &h->t64.Pfac, all))) return rc;
+    if ((rc = upload<float>(h, &h->t32.Pfac, all))) return rc;
+    h->pfac_ready = true;
+    return MB_OK;
+}
+
+static void free_set(DevTables &t) {
+    void **ps[] = {&t.Bq, &t.V, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.q2, &t.qproj, &t.zproj, &t.E, &t.Pfac};
+    for (void **p : ps) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+}
+
+void free_tables(mb_handle *h) {
+    cudaSetDevice(h->device);
+    free_set(h->t64);
+    free_set(h->t32);
+    if (h->d_goff) cudaFree(h->d_goff);
+    h->d_goff = nullptr;
+    if (h->scratch.ptr) cudaFree(h->scratch.ptr);
+    h->scratch = Scratch();
+}
+
+int ensure_scratch(mb_handle *h, size_t bytes) {
+    if (bytes <= h->scratch.bytes) return MB_OK;
+    if (h->scratch.ptr) {
+        MB_CUDA(cudaDeviceSynchronize());
+        cudaFree(h->scratch.ptr);
+    }
+    h->scratch = Scratch();
+    MB_CUDA(cudaMalloc(&h->scratch.ptr, bytes));
+    h->scratch.bytes = bytes;
+    return MB_OK;
+}
+
+static void plan_chunks(const mb_handle *h, int nsel, int nbands, int &chunk, int &nchunks) {
+    int sms = 152;
+    int target = std::max(1, (4 * sms + nsel * nbands - 1) / (nsel * nbands));
+    chunk = std::max(h->order, (h->nint + target - 1) / target);
+    if (chunk >= h->nint) chunk = h->nint;
+    nchunks = (h->nint + chunk - 1) / chunk;
+}
+
+static size_t per_k_scratch(const mb_handle *h, int ldg, int nbands, int nchunks, size_t c2) {
+    size_t part = (size_t)nbands * std::max(0, nchunks - 1) * 2 * (h->order - 1) * ldg * c2;
+    size_t w = (size_t)nbands * h->nb * std::max(1, h->nproj) * c2;
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    return al(part) + 2 * al(w);
+}
+
+size_t apply_scratch_bytes(const mb_handle *h, int nsel_max, int nbands, int prec) {
+    size_t c2 = prec == MB_FP64 ? 16 : 8;
+    int chunk, nchunks;
+    plan_chunks(h, std::min(nsel_max, kMaxK), nbands, chunk, nchunks);
+    int maxldg = 0;
+    for (auto &k : h->kp) maxldg = std::max(maxldg, k.ldg);
+    return (size_t)std::min(nsel_max, kMaxK) * per_k_scratch(h, maxldg, nbands, nchunks, c2);
+}
+
+template <typename R>
+static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y,
+                         int nbands, cudaStream_t s, const DevTables &t) {
+    typedef typename V2<R>::T R2;
+    const size_t c2 = sizeof(R2);
+    int chunk, nchunks;
+    plan_chunks(h, nsel, nbands, chunk, nchunks);
+    std::vector<KDesc> desc(nsel);
+    size_t off = 0;
+    int maxldg = 0;
+    for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
+    size_t need = (size_t)nsel * per_k_scratch(h, maxldg, nbands, nchunks, c2);
+    int rc = ensure_scratch(h, need);
+    if (rc) return rc;
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    char *base = reinterpret_cast<char *>(h->scratch.ptr);
+    for (int i = 0; i < nsel; ++i) {
+        const KPoint &kp = h->kp[iks[i]];
+        KDesc &d = desc[i];
+        d.X = X[i];
+        d.Y = Y[i];
+        d.ng = kp.ng;
+        d.ldg = kp.ldg;
+        d.kofs = h->kofs[iks[i]];
+        d.qofs = h->qofs[iks[i]];
+        size_t part = (size_t)nbands * std::max(0, nchunks - 1) * 2 * (h->order - 1) * kp.ldg * c2;
+        size_t w = (size_t)nbands * h->nb * std::max(1, h->nproj) * c2;
+        d.part = base + off;
+        off += al(part);
+        d.W = base + off;
+        off += al(w);
+        d.C = base + off;
+        off += al(w);
+    }
+    // projector overlaps first (they read X only)
+    if (h->nproj > 0) {
+        GemmArgs<R> ga;
+        ga.Q = reinterpret_cast<const R2 *>(t.qproj);
+        ga.mode = 0;
+        ga.nb = h->nb;
+        ga.nbands = nbands;
+        ga.nproj = h->nproj;
+        std::copy(desc.begin(), desc.end(), ga.d);
+        dim3 grid((nbands * h->nb + 63) / 64, (h->nproj + 63) / 64, nsel);
+        zgemm_kernel<R><<<grid, 256, 0, s>>>(ga);
+        CoefArgs<R> ca;
+        ca.zproj = reinterpret_cast<const R *>(t.zproj);
+        ca.E = reinterpret_cast<const R *>(t.E);
+        ca.nb = h->nb;
+        ca.nbands = nbands;
+        ca.nproj = h->nproj;
+        std::copy(desc.begin(), desc.end(), ca.d);
+        coef_kernel<R><<<dim3((nbands * h->nproj + 127) / 128, nsel), 128, 0, s>>>(ca);
+    }
+    // local potential through the planes
+    PlaneArgs<R> pa;
+    pa.Bq = reinterpret_cast<const R *>(t.Bq);
+    pa.V = reinterpret_cast<const R *>(t.V);
+    pa.tw = reinterpret_cast<const R2 *>(t.tw);
+    pa.goff = h->d_goff;
+    pa.n1 = h->n1;
+    pa.n2 = h->n2;
+    pa.l1 = h->l1;
+    pa.l2 = h->l2;
+    pa.nmax = std::max(h->n1, h->n2);
+    pa.order = h->order;
+    pa.nquad = h->nquad;
+    pa.nint = h->nint;
+    pa.nb = h->nb;
+    pa.nbands = nbands;
+    pa.nchunks = nchunks;
+    pa.chunk = chunk;
+    pa.ldg_max = maxldg;
+    pa.nsel = nsel;
+    std::copy(desc.begin(), desc.end(), pa.d);
+    const size_t NN = (size_t)h->n1 * h->n2;
+    const size_t fixed = (pa.nmax / 2 + (size_t)h->order * maxldg) * c2;
+    const size_t budget = (size_t)h->smem_optin;
+    int np = (int)std::min<size_t>((size_t)h->nquad, fixed < budget ? (budget - fixed) / (NN * c2) : 0);
+    if (np < 1) return MB_EUNSUPPORTED;
+    pa.np = np;
+    size_t smem = fixed + (size_t)np * NN * c2;
+    MB_CUDA(cudaFuncSetAttribute(plane_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    plane_kernel<R><<<nsel * nbands * nchunks, 256, smem, s>>>(pa);
+    EpiArgs<R> ea;
+    ea.Sband = reinterpret_cast<const R *>(t.Sband);
+    ea.Dband = reinterpret_cast<const R *>(t.Dband);
+    ea.q2 = reinterpret_cast<const R *>(t.q2);
+    ea.order = h->order;
+    ea.nb = h->nb;
+    ea.nbands = nbands;
+    ea.nchunks = nchunks;
+    ea.chunk = chunk;
+    ea.nint = h->nint;
+    std::copy(desc.begin(), desc.end(), ea.d);
+    epilogue_kernel<R><<<dim3(h->nb, nbands, nsel), 256, 0, s>>>(ea);
+    if (h->nproj > 0) {
+        GemmArgs<R> ga;
+        ga.Q = reinterpret_cast<const R2 *>(t.qproj);
+        ga.mode = 1;
+        ga.nb = h->nb;
+        ga.nbands = nbands;
+        ga.nproj = h->nproj;
+        std::copy(desc.begin(), desc.end(), ga.d);
+        dim3 grid((nbands * h->nb + 63) / 64, (maxldg + 63) / 64, nsel);
+        zgemm_kernel<R><<<grid, 256, 0, s>>>(ga);
+    }
+    MB_CUDA(cudaGetLastError());
+    return MB_OK;
+}
+
+int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y,
+                  int nbands, int prec, cudaStream_t s) {
+    if (nsel <= 0 || !iks || !X || !Y) return MB_EINVAL;
+    if (nbands <= 0 || nbands > h->max_bands) return MB_EINVAL;
+    if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return MB_EINVAL;
+    for (int i = 0; i < nsel; ++i) {
+        if (iks[i] < 0 || iks[i] >= (int)h->kp.size() || !X[i] || !Y[i]) return MB_EINVAL;
+        if (X[i] == Y[i]) return MB_EINVAL;
+    }
+    MB_CUDA(cudaSetDevice(h->device));
+    for (int i0 = 0; i0 < nsel; i0 += kMaxK) {
+        int n = std::min(kMaxK, nsel - i0);
+        int rc = prec == MB_FP64 ? apply_H_group<double>(h, n, iks + i0, X + i0, Y + i0, nbands, s, h->t64)
+                                 : apply_H_group<float>(h, n, iks + i0, X + i0, Y + i0, nbands, s, h->t32);
+        if (rc) return rc;
+    }
+    return MB_OK;
+}
+
+int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nbands, int prec,
+                 cudaStream_t s) {
+    if (ik < 0 || ik >= (int)h->kp.size() || !X || !Y || nbands <= 0) return MB_EINVAL;
+    if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return MB_EINVAL;
+    if (which != BAND_S && X == Y) return MB_EINVAL;
+    MB_CUDA(cudaSetDevice(h->device));
+    const KPoint &kp = h->kp[ik];
+    dim3 grid((kp.ldg + 127) / 128, nbands);
+    if (which == BAND_PREC) {
+        int rc = ensure_precond(h);
+        if (rc) return rc;
+    }
+    size_t pofs = 0;
+    for (int i = 0; i < ik; ++i) pofs += (size_t)h->kp[i].ldg * h->nb * h->order;
+    size_t gstride = (size_t)h->nb * h->order;
+    if (prec == MB_FP64) {
+        const DevTables &t = h->t64;
+        auto x = reinterpret_cast<const double2 *>(X);
+        auto y = reinterpret_cast<double2 *>(Y);
+        if (which == BAND_S)
+            banded_S_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+        else if (which == BAND_SINV)
+            banded_solve_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+        else
+            banded_solve_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Pfac + pofs, gstride, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+    } else {
+        const DevTables &t = h->t32;
+        auto x = reinterpret_cast<const float2 *>(X);
+        auto y = reinterpret_cast<float2 *>(Y);
+        if (which == BAND_S)
+            banded_S_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+        else if (which == BAND_SINV)
+            banded_solve_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+        else
+            banded_solve_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Pfac + pofs, gstride, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+    }
+    MB_CUDA(cudaGetLastError());
+    return MB_OK;
+}
+
+}  // namespace mb

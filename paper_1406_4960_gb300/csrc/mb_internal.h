@@ -1,0 +1,103 @@
+// Internal state of an mb_handle and the kernel launch interfaces.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/mb.h"
+
+namespace mb {
+
+using cdouble = std::complex<double>;
+
+// Per-k-point host data.
+struct KPoint {
+    double k[2];
+    int ng = 0, ldg = 0;
+    std::vector<int> n1, n2;        // G = n1 b1 + n2 b2
+    std::vector<int> goff;          // natural grid offset i1*N2 + i2 of each G
+    std::vector<double> q2;         // |k+G|^2
+    std::vector<double> qx, qy;     // k+G cartesian
+    std::vector<cdouble> qproj;     // nproj x ldg in-plane projector factors
+};
+
+// Device copies of one precision (R = double or float).
+struct DevTables {
+    void *Bq = nullptr;      // nq x order, B_{t+m}(z_q) of the full basis
+    void *V = nullptr;       // nq x N1 x N2, w_q V / (N1 N2), bit-reversed layout
+    void *tw = nullptr;      // Nmax/2 complex, exp(+2 pi i k / Nmax)
+    void *Sband = nullptr;   // nb x (2 order - 1): S[j][j+d], d = -(order-1)..order-1
+    void *Dband = nullptr;   // same layout for D = <B'|B'>
+    void *Lband = nullptr;   // nb x order: Cholesky L[j][j-d], d = 0..order-1
+    void *q2 = nullptr;      // all k, concatenated with kofs
+    void *qproj = nullptr;   // all k: nproj x ldg each, offset qofs[k]
+    void *zproj = nullptr;   // nproj x nb
+    void *E = nullptr;       // nproj
+    void *Pfac = nullptr;    // preconditioner factors: all k, ldg x nb x order each
+};
+
+struct Scratch {
+    size_t bytes = 0;
+    void *ptr = nullptr;
+};
+
+}  // namespace mb
+
+struct mb_handle {
+    int device = 0;
+    double a1[2], a2[2], b1[2], b2[2], Ac = 0;
+    double ecut = 0;
+    int order = 0, nquad = 0, nint = 0, nb = 0, nq = 0;
+    int n1 = 0, n2 = 0, l1 = 0, l2 = 0;
+    int nproj = 0;
+    int max_bands = 0;
+    int smem_optin = 227 * 1024;   // opt-in shared memory per block
+    int num_sms = 152;
+    double precond_shift = 1.0;
+    std::vector<double> breaks, tau;
+    std::vector<double> zq, wq;
+    std::vector<double> Bq;          // nq x order
+    std::vector<double> Sb, Db, Lb;  // band storage as in DevTables
+    std::vector<double> Vnat;        // nq x N1 x N2 natural order, V(r, z_q) (Ha)
+    std::vector<double> zproj, Eproj;
+    std::vector<mb::KPoint> kp;
+    std::vector<int> kofs, qofs;     // offsets of per-k arrays (in elements)
+    int total_ldg = 0;
+    int *d_goff = nullptr;           // all k (int), offset kofs
+    mb::DevTables t64, t32;
+    bool pfac_ready = false;
+    mb::Scratch scratch;
+    void *d_desc = nullptr;          // descriptor arrays for batched launches
+    size_t desc_bytes = 0;
+    std::string last_cuda_error;
+};
+
+namespace mb {
+
+// setup.cpp
+int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int nk,
+                      double ecut, const double *breaks, int nbreaks, int order,
+                      const mb_atom *atoms, int natoms, const mb_opts *opts);
+void vtable_permuted(const mb_handle *h, std::vector<double> &out);
+void precond_factors(const mb_handle *h, int ik, double shift, std::vector<double> &out);
+
+// apply.cu
+int upload_tables(mb_handle *h);
+int upload_potential(mb_handle *h);
+int ensure_precond(mb_handle *h);
+void free_tables(mb_handle *h);
+int ensure_scratch(mb_handle *h, size_t bytes);
+int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X,
+                  void *const *Y, int nbands, int prec, cudaStream_t s);
+int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nbands,
+                 int prec, cudaStream_t s);
+size_t apply_scratch_bytes(const mb_handle *h, int nsel_max, int nbands, int prec);
+
+enum { BAND_S = 0, BAND_SINV = 1, BAND_PREC = 2 };
+
+int cuda_fail(mb_handle *h, cudaError_t e);
+
+}  // namespace mb

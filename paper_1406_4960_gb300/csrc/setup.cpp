@@ -1,0 +1,390 @@
+// Host-side FP64 set-up of the mixed basis: knots, B-spline tables on the
+// Gauss planes, banded S and D with the Cholesky factor of S, cutoff discs,
+// the local potential on the quadrature planes and the Kleinman-Bylander
+// factors.  Runs once per handle; nothing here is on the apply path.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <tuple>
+
+#include "mb_internal.h"
+
+namespace mb {
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton's iteration on P_n,
+// evaluated with the three-term recurrence (Golub & Welsch give the same rule
+// as eigenvalues; Newton from Tricomi's initial guess is the classic route).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int m = 2; m <= n; ++m) {
+                double p2 = ((2.0 * m - 1.0) * z * p1 - (m - 1.0) * p0) / m;
+                p0 = p1;
+                p1 = p2;
+            }
+            double pn = (n == 1) ? z : p1;
+            double pm = (n == 1) ? 1.0 : p0;
+            dp = n * (z * pn - pm) / (z * z - 1.0);
+            double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        // recompute derivative at the converged node
+        double p0 = 1.0, p1 = z;
+        for (int m = 2; m <= n; ++m) {
+            double p2 = ((2.0 * m - 1.0) * z * p1 - (m - 1.0) * p0) / m;
+            p0 = p1;
+            p1 = p2;
+        }
+        double pn = (n == 1) ? z : p1, pm = (n == 1) ? 1.0 : p0;
+        dp = n * (z * pn - pm) / (z * z - 1.0);
+        x[n - 1 - i] = z;   // ascending
+        w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// The `ord` B-splines of order `ord` that are non-zero on [tau[l], tau[l+1]),
+// B_{l-ord+1 .. l}(z), by the triangular form of the recursion Eq. (1)
+// (de Boor's BSPLVB arrangement: left/right knot distances, one pass per order).
+void nonzero_bsplines(const std::vector<double> &tau, int l, int ord, double z, double *b) {
+    double dl[16], dr[16];
+    b[0] = 1.0;
+    for (int j = 1; j < ord; ++j) {
+        dr[j] = tau[l + j] - z;
+        dl[j] = z - tau[l + 1 - j];
+        double saved = 0.0;
+        for (int r = 0; r < j; ++r) {
+            double den = dr[r + 1] + dl[j - r];
+            double term = den != 0.0 ? b[r] / den : 0.0;
+            b[r] = saved + dr[r + 1] * term;
+            saved = dl[j - r] * term;
+        }
+        b[j] = saved;
+    }
+}
+
+}  // namespace
+
+int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int nk,
+                      double ecut, const double *breaks, int nbreaks, int order,
+                      const mb_atom *atoms, int natoms, const mb_opts *opts) {
+    if (!cell || !kpts || nk <= 0 || !breaks || nbreaks < 2 || !opts) return MB_EINVAL;
+    if (order < 3 || order > 8) return MB_EINVAL;
+    if (!(ecut > 0.0)) return MB_EINVAL;
+    if (natoms < 0 || (natoms > 0 && !atoms)) return MB_EINVAL;
+    for (int i = 1; i < nbreaks; ++i)
+        if (!(breaks[i] > breaks[i - 1])) return MB_EINVAL;
+    int nint = nbreaks - 1;
+    if (nint < order) return MB_EINVAL;
+    auto pow2 = [](int v, int &lg) {
+        if (v < 4 || v > 256) return false;
+        lg = 0;
+        while ((1 << lg) < v) ++lg;
+        return (1 << lg) == v;
+    };
+    if (!pow2(opts->n1, h->l1) || !pow2(opts->n2, h->l2)) return MB_EINVAL;
+    h->n1 = opts->n1;
+    h->n2 = opts->n2;
+    h->order = order;
+    h->nquad = opts->nquad > 0 ? opts->nquad : order;
+    if (h->nquad > 16) return MB_EINVAL;
+    h->nint = nint;
+    h->nb = nint + order - 3;
+    h->nq = nint * h->nquad;
+    h->ecut = ecut;
+    h->max_bands = opts->max_bands > 0 ? opts->max_bands : 128;
+    h->precond_shift = opts->precond_shift > 0 ? opts->precond_shift : 1.0;
+    for (int i = 0; i < 2; ++i) {
+        h->a1[i] = cell->a1[i];
+        h->a2[i] = cell->a2[i];
+    }
+    double det = h->a1[0] * h->a2[1] - h->a1[1] * h->a2[0];
+    if (!(std::fabs(det) > 1e-12)) return MB_EINVAL;
+    h->Ac = std::fabs(det);
+    // b_i . a_j = 2 pi delta_ij
+    h->b1[0] = 2 * kPi * h->a2[1] / det;
+    h->b1[1] = -2 * kPi * h->a2[0] / det;
+    h->b2[0] = -2 * kPi * h->a1[1] / det;
+    h->b2[1] = 2 * kPi * h->a1[0] / det;
+
+    // ---- knots and Gauss planes
+    h->breaks.assign(breaks, breaks + nbreaks);
+    h->tau.clear();
+    for (int i = 0; i < order - 1; ++i) h->tau.push_back(breaks[0]);
+    for (int i = 0; i < nbreaks; ++i) h->tau.push_back(breaks[i]);
+    for (int i = 0; i < order - 1; ++i) h->tau.push_back(breaks[nbreaks - 1]);
+    std::vector<double> gx, gw;
+    gauss_legendre(h->nquad, gx, gw);
+    const int K = order, P = h->nquad, nq = h->nq, nb = h->nb;
+    h->zq.resize(nq);
+    h->wq.resize(nq);
+    h->Bq.assign((size_t)nq * K, 0.0);
+    std::vector<double> dBq((size_t)nq * K, 0.0);
+    for (int t = 0; t < nint; ++t) {
+        double lo = breaks[t], hi = breaks[t + 1], hh = hi - lo;
+        int l = K - 1 + t;
+        for (int s = 0; s < P; ++s) {
+            int q = t * P + s;
+            double z = lo + 0.5 * hh * (gx[s] + 1.0);
+            h->zq[q] = z;
+            h->wq[q] = 0.5 * hh * gw[s];
+            double b[16], bl[16];
+            nonzero_bsplines(h->tau, l, K, z, b);        // B_{t .. t+K-1}
+            nonzero_bsplines(h->tau, l, K - 1, z, bl);   // order K-1: B_{t+1 .. t+K-1}
+            for (int m = 0; m < K; ++m) {
+                h->Bq[(size_t)q * K + m] = b[m];
+                // Eq. (3): B'_{i,K} = (K-1)[B_{i,K-1}/(tau_{i+K-1}-tau_i) - B_{i+1,K-1}/(tau_{i+K}-tau_{i+1})]
+                int i = t + m;
+                double lower_i = (m >= 1) ? bl[m - 1] : 0.0;      // B_{i,K-1}
+                double lower_i1 = (m <= K - 2) ? bl[m] : 0.0;     // B_{i+1,K-1}
+                double d1 = h->tau[i + K - 1] - h->tau[i];
+                double d2 = h->tau[i + K] - h->tau[i + 1];
+                double v = 0.0;
+                if (d1 > 0) v += lower_i / d1;
+                if (d2 > 0) v -= lower_i1 / d2;
+                dBq[(size_t)q * K + m] = (K - 1) * v;
+            }
+        }
+    }
+
+    // ---- banded S, D over retained splines j = full index - 1
+    const int W = 2 * K - 1;
+    h->Sb.assign((size_t)nb * W, 0.0);
+    h->Db.assign((size_t)nb * W, 0.0);
+    for (int q = 0; q < nq; ++q) {
+        int t = q / P;
+        for (int m = 0; m < K; ++m) {
+            int j = t + m - 1;
+            if (j < 0 || j >= nb) continue;
+            for (int m2 = 0; m2 < K; ++m2) {
+                int j2 = t + m2 - 1;
+                if (j2 < 0 || j2 >= nb) continue;
+                int d = j2 - j + (K - 1);
+                h->Sb[(size_t)j * W + d] += h->wq[q] * h->Bq[(size_t)q * K + m] * h->Bq[(size_t)q * K + m2];
+                h->Db[(size_t)j * W + d] += h->wq[q] * dBq[(size_t)q * K + m] * dBq[(size_t)q * K + m2];
+            }
+        }
+    }
+    // banded Cholesky S = L L^T, L[j][j-d] stored at Lb[j*K + d]
+    h->Lb.assign((size_t)nb * K, 0.0);
+    for (int j = 0; j < nb; ++j) {
+        for (int d = K - 1; d >= 0; --d) {
+            int i = j - d;                       // column
+            if (i < 0) continue;
+            double s = h->Sb[(size_t)i * W + (j - i) + (K - 1)];   // S[i][j]
+            for (int c = std::max(0, j - (K - 1)); c < i; ++c)
+                s -= h->Lb[(size_t)j * K + (j - c)] * h->Lb[(size_t)i * K + (i - c)];
+            if (d == 0) {
+                if (!(s > 0.0)) return MB_EINVAL;
+                h->Lb[(size_t)j * K] = std::sqrt(s);
+            } else {
+                h->Lb[(size_t)j * K + d] = s / h->Lb[(size_t)i * K];
+            }
+        }
+    }
+
+    // ---- cutoff discs
+    h->kp.assign(nk, KPoint());
+    h->kofs.assign(nk + 1, 0);
+    h->qofs.assign(nk + 1, 0);
+    double r = std::sqrt(2.0 * ecut);
+    double la1 = std::hypot(h->a1[0], h->a1[1]), la2 = std::hypot(h->a2[0], h->a2[1]);
+    for (int ik = 0; ik < nk; ++ik) {
+        KPoint &kp = h->kp[ik];
+        kp.k[0] = kpts[2 * ik];
+        kp.k[1] = kpts[2 * ik + 1];
+        double kn = std::hypot(kp.k[0], kp.k[1]);
+        int lim1 = (int)std::ceil((r + kn) * la1 / (2 * kPi)) + 1;
+        int lim2 = (int)std::ceil((r + kn) * la2 / (2 * kPi)) + 1;
+        std::vector<std::tuple<int, int, int>> gl;   // (goff, n1, n2)
+        for (int a = -lim1; a <= lim1; ++a)
+            for (int b = -lim2; b <= lim2; ++b) {
+                double qx = kp.k[0] + a * h->b1[0] + b * h->b2[0];
+                double qy = kp.k[1] + a * h->b1[1] + b * h->b2[1];
+                if (0.5 * (qx * qx + qy * qy) <= ecut) {
+                    if (2 * std::abs(a) + 1 > h->n1 || 2 * std::abs(b) + 1 > h->n2) return MB_EINVAL;
+                    int i1 = ((a % h->n1) + h->n1) % h->n1, i2 = ((b % h->n2) + h->n2) % h->n2;
+                    gl.emplace_back(i1 * h->n2 + i2, a, b);
+                }
+            }
+        if (gl.empty()) return MB_EINVAL;
+        std::sort(gl.begin(), gl.end());
+        kp.ng = (int)gl.size();
+        kp.ldg = (kp.ng + 31) / 32 * 32;
+        for (auto &e : gl) {
+            kp.goff.push_back(std::get<0>(e));
+            int a = std::get<1>(e), b = std::get<2>(e);
+            kp.n1.push_back(a);
+            kp.n2.push_back(b);
+            double qx = kp.k[0] + a * h->b1[0] + b * h->b2[0];
+            double qy = kp.k[1] + a * h->b1[1] + b * h->b2[1];
+            kp.qx.push_back(qx);
+            kp.qy.push_back(qy);
+            kp.q2.push_back(qx * qx + qy * qy);
+        }
+        h->kofs[ik + 1] = h->kofs[ik] + kp.ldg;
+    }
+    h->total_ldg = h->kofs[nk];
+
+    // ---- local potential on the planes: V(r, z_q) = sum_groups f(z_q) P(r),
+    // P(r) = Re sum_m c(m) exp(i g_m . r) over the grid frequencies
+    // m in [-N/2, N/2), c(m) = sum_atoms (A/A_c)(pi/a) exp(-|g_m|^2/4a) exp(-i g_m.R)
+    const int N1 = h->n1, N2 = h->n2, NN = N1 * N2;
+    h->Vnat.assign((size_t)nq * NN, 0.0);
+    std::map<std::pair<double, double>, std::vector<int>> groups;   // (a, Rz) -> atoms
+    for (int i = 0; i < natoms; ++i) {
+        if (atoms[i].A == 0.0) continue;
+        if (!(atoms[i].w > 0.0)) return MB_EINVAL;
+        double a = 1.0 / (2.0 * atoms[i].w * atoms[i].w);
+        groups[{a, atoms[i].pos[2]}].push_back(i);
+    }
+    std::vector<cdouble> e1((size_t)N1 * N1), e2((size_t)N2 * N2);
+    for (int m = 0; m < N1; ++m)
+        for (int i = 0; i < N1; ++i) e1[(size_t)m * N1 + i] = std::polar(1.0, 2 * kPi * (double)m * i / N1);
+    for (int m = 0; m < N2; ++m)
+        for (int i = 0; i < N2; ++i) e2[(size_t)m * N2 + i] = std::polar(1.0, 2 * kPi * (double)m * i / N2);
+    for (auto &gr : groups) {
+        double a = gr.first.first, Rz = gr.first.second;
+        std::vector<cdouble> c((size_t)NN, 0.0);   // index (m1 mod N1, m2 mod N2)
+        for (int u = 0; u < N1; ++u) {
+            int m1 = u < N1 / 2 ? u : u - N1;
+            for (int v = 0; v < N2; ++v) {
+                int m2 = v < N2 / 2 ? v : v - N2;
+                double gx = m1 * h->b1[0] + m2 * h->b2[0], gy = m1 * h->b1[1] + m2 * h->b2[1];
+                double g2 = gx * gx + gy * gy;
+                cdouble s = 0.0;
+                for (int ia : gr.second)
+                    s += (atoms[ia].A / h->Ac) * (kPi / a) * std::exp(-g2 / (4 * a)) *
+                         std::polar(1.0, -(gx * atoms[ia].pos[0] + gy * atoms[ia].pos[1]));
+                c[(size_t)u * N2 + v] = s;
+            }
+        }
+        // separable inverse DFT: first over m2, then over m1 (phase index m*i mod N)
+        std::vector<cdouble> tmp((size_t)NN, 0.0), Pr((size_t)NN, 0.0);
+        for (int u = 0; u < N1; ++u)
+            for (int i2 = 0; i2 < N2; ++i2) {
+                cdouble s = 0.0;
+                for (int v = 0; v < N2; ++v) s += c[(size_t)u * N2 + v] * e2[(size_t)v * N2 + i2];
+                tmp[(size_t)u * N2 + i2] = s;
+            }
+        for (int i1 = 0; i1 < N1; ++i1)
+            for (int i2 = 0; i2 < N2; ++i2) {
+                cdouble s = 0.0;
+                for (int u = 0; u < N1; ++u) s += tmp[(size_t)u * N2 + i2] * e1[(size_t)u * N1 + i1];
+                Pr[(size_t)i1 * N2 + i2] = s;
+            }
+        for (int q = 0; q < nq; ++q) {
+            double f = std::exp(-a * (h->zq[q] - Rz) * (h->zq[q] - Rz));
+            double *row = &h->Vnat[(size_t)q * NN];
+            for (int e = 0; e < NN; ++e) row[e] += f * Pr[e].real();
+        }
+    }
+
+    // ---- Kleinman-Bylander factors: u_p(G, j) = zproj[p][j] * qproj[p][G]
+    h->nproj = 0;
+    for (int i = 0; i < natoms; ++i) {
+        if (atoms[i].nproj != 0 && atoms[i].nproj != 4) return MB_EINVAL;
+        if (atoms[i].nproj == 4 && !(atoms[i].rc > 0)) return MB_EINVAL;
+        h->nproj += atoms[i].nproj;
+    }
+    const int NP = h->nproj;
+    h->zproj.assign((size_t)NP * nb, 0.0);
+    h->Eproj.assign(NP, 0.0);
+    for (int ik = 0; ik < nk; ++ik) {
+        h->kp[ik].qproj.assign((size_t)NP * h->kp[ik].ldg, cdouble(0.0));
+        h->qofs[ik + 1] = h->qofs[ik] + NP * h->kp[ik].ldg;
+    }
+    int p = 0;
+    for (int i = 0; i < natoms; ++i) {
+        if (atoms[i].nproj == 0) continue;
+        const mb_atom &at = atoms[i];
+        double al = 1.0 / (2.0 * at.rc * at.rc);
+        double Cs = std::pow(2.0 * al / kPi, 0.75);
+        double Cp = 2.0 * std::sqrt(al) * Cs;
+        // z factors: Z_{1,00} (s, p_x, p_y) and Z_{1,10} (p_z) by the Gauss planes
+        for (int q = 0; q < nq; ++q) {
+            int t = q / P;
+            double dz = h->zq[q] - at.pos[2];
+            double g = h->wq[q] * std::exp(-al * dz * dz);
+            for (int m = 0; m < K; ++m) {
+                int j = t + m - 1;
+                if (j < 0 || j >= nb) continue;
+                double bv = h->Bq[(size_t)q * K + m];
+                for (int c = 0; c < 3; ++c) h->zproj[(size_t)(p + c) * nb + j] += g * bv;
+                h->zproj[(size_t)(p + 3) * nb + j] += g * dz * bv;
+            }
+        }
+        for (int c = 0; c < 4; ++c) h->Eproj[p + c] = at.E[c];
+        for (int ik = 0; ik < nk; ++ik) {
+            KPoint &kp = h->kp[ik];
+            for (int g = 0; g < kp.ng; ++g) {
+                double qx = kp.qx[g], qy = kp.qy[g];
+                double Qs = (kPi / al) * std::exp(-kp.q2[g] / (4 * al));
+                cdouble ph = std::polar(1.0 / std::sqrt(h->Ac), -(qx * at.pos[0] + qy * at.pos[1]));
+                // conj of C*Q: Q_x = i q_x/(2 alpha) Q_s  ->  conj = -i q_x/(2 alpha) Q_s
+                kp.qproj[(size_t)(p + 0) * kp.ldg + g] = ph * (Cs * Qs);
+                kp.qproj[(size_t)(p + 1) * kp.ldg + g] = ph * cdouble(0.0, -Cp * qx / (2 * al) * Qs);
+                kp.qproj[(size_t)(p + 2) * kp.ldg + g] = ph * cdouble(0.0, -Cp * qy / (2 * al) * Qs);
+                kp.qproj[(size_t)(p + 3) * kp.ldg + g] = ph * (Cp * Qs);
+            }
+        }
+        p += 4;
+    }
+    return MB_OK;
+}
+
+// V table in the layout the plane kernel multiplies in: weight and 1/(N1 N2)
+// folded in, both axes bit-reversed (the inverse transform is decimation in
+// frequency, the forward one decimation in time, so no reordering pass runs).
+void vtable_permuted(const mb_handle *h, std::vector<double> &out) {
+    const int N1 = h->n1, N2 = h->n2, NN = N1 * N2;
+    auto rev = [](int x, int bits) {
+        int r = 0;
+        for (int b = 0; b < bits; ++b) r |= ((x >> b) & 1) << (bits - 1 - b);
+        return r;
+    };
+    out.assign((size_t)h->nq * NN, 0.0);
+    double scale = 1.0 / NN;
+    for (int q = 0; q < h->nq; ++q)
+        for (int p1 = 0; p1 < N1; ++p1)
+            for (int p2 = 0; p2 < N2; ++p2)
+                out[(size_t)q * NN + p1 * N2 + p2] =
+                    h->wq[q] * scale * h->Vnat[(size_t)q * NN + rev(p1, h->l1) * N2 + rev(p2, h->l2)];
+}
+
+// Banded Cholesky factors of T(G) + c S = D/2 + (|k+G|^2/2 + c) S for every
+// G of k-point ik: out[g][j][d] = L[j][j-d].
+void precond_factors(const mb_handle *h, int ik, double shift, std::vector<double> &out) {
+    const int K = h->order, W = 2 * K - 1, nb = h->nb;
+    const KPoint &kp = h->kp[ik];
+    out.assign((size_t)kp.ldg * nb * K, 0.0);
+    for (int g = 0; g < kp.ldg; ++g) {
+        double *L = &out[(size_t)g * nb * K];
+        double qq = g < kp.ng ? 0.5 * kp.q2[g] + shift : shift;
+        for (int j = 0; j < nb; ++j) {
+            for (int d = K - 1; d >= 0; --d) {
+                int i = j - d;
+                if (i < 0) continue;
+                size_t idx = (size_t)i * W + (j - i) + (K - 1);
+                double s = 0.5 * h->Db[idx] + qq * h->Sb[idx];
+                for (int c = std::max(0, j - (K - 1)); c < i; ++c)
+                    s -= L[(size_t)j * K + (j - c)] * L[(size_t)i * K + (i - c)];
+                if (d == 0)
+                    L[(size_t)j * K] = std::sqrt(s > 0 ? s : 1e-300);
+                else
+                    L[(size_t)j * K + d] = s / L[(size_t)i * K];
+            }
+        }
+    }
+}
+
+}  // namespace mb

@@ -1,0 +1,252 @@
+"""Thin Python binding of the C ABI in include/mb.h (argument marshalling only).
+
+Every step of the H/S apply and of the eigensolver runs in libmbgb300.so;
+PyTorch only provides device memory and streams.  Loading fails loudly when
+the library has not been built: there is no fallback."""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+MB_FP64, MB_FP32, MB_BF16 = 0, 1, 2
+PREC = {"fp64": MB_FP64, "fp32": MB_FP32, "bf16": MB_BF16}
+ERRORS = {0: "MB_OK", 1: "MB_EINVAL", 2: "MB_ENOMEM", 3: "MB_ENOTCONV", 4: "MB_ETIMEOUT",
+          5: "MB_ECUDA", 6: "MB_EUNSUPPORTED"}
+
+EXPORTS = ("mb_setup", "mb_destroy", "mb_sizes", "mb_gvectors", "mb_zplanes",
+           "mb_set_local_potential", "mb_apply_H", "mb_apply_H_batch", "mb_apply_S",
+           "mb_apply_Sinv", "mb_eigsolve", "mb_strerror", "mb_last_cuda_error")
+
+
+class MBError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__("%s (%d)%s" % (ERRORS.get(code, "?"), code, (": " + msg) if msg else ""))
+
+
+class _Cell(ctypes.Structure):
+    _fields_ = [("a1", ctypes.c_double * 2), ("a2", ctypes.c_double * 2)]
+
+
+class _Atom(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_double * 3), ("A", ctypes.c_double), ("w", ctypes.c_double),
+                ("nproj", ctypes.c_int), ("E", ctypes.c_double * 4), ("rc", ctypes.c_double)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("nquad", ctypes.c_int),
+                ("device", ctypes.c_int), ("max_bands", ctypes.c_int),
+                ("precond_shift", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("applies", ctypes.c_int),
+                ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("krylov_depth", ctypes.c_int), ("block", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("polish", ctypes.c_int)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """The ctypes handle of libmbgb300.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libmbgb300.so is not built (run __graft_entry__.build())")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    lib.mb_setup.argtypes = [ctypes.POINTER(_Cell), dp, ctypes.c_int, ctypes.c_double, dp,
+                             ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Atom), ctypes.c_int,
+                             ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
+    lib.mb_destroy.argtypes = [vp]
+    lib.mb_destroy.restype = None
+    lib.mb_sizes.argtypes = [vp, ctypes.c_int, ip, ip, ip]
+    lib.mb_gvectors.argtypes = [vp, ctypes.c_int, ip]
+    lib.mb_zplanes.argtypes = [vp, ip, dp, dp]
+    lib.mb_set_local_potential.argtypes = [vp, dp]
+    lib.mb_apply_H.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.mb_apply_H_batch.argtypes = [vp, ctypes.c_int, ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.c_int, ctypes.c_int, vp]
+    lib.mb_apply_S.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.mb_apply_Sinv.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.mb_eigsolve.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, vp,
+                                ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    lib.mb_strerror.argtypes = [ctypes.c_int]
+    lib.mb_strerror.restype = ctypes.c_char_p
+    lib.mb_last_cuda_error.argtypes = [vp]
+    lib.mb_last_cuda_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _dptr(a) -> ctypes.POINTER(ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+class Handle:
+    """One mb_handle: basis tables of a workload resident on a CUDA device."""
+
+    def __init__(self, a1, a2, kpts, ecut, breaks, order, atoms, grid, nquad=0, device=0,
+                 max_bands=128, precond_shift=0.0):
+        self._lib = load()
+        kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 2))
+        br = np.ascontiguousarray(np.asarray(breaks, dtype=np.float64))
+        cell = _Cell((ctypes.c_double * 2)(*a1), (ctypes.c_double * 2)(*a2))
+        arr = (_Atom * max(1, len(atoms)))()
+        for i, at in enumerate(atoms):
+            arr[i].pos = (ctypes.c_double * 3)(*at.pos)
+            arr[i].A = at.A
+            arr[i].w = at.w
+            arr[i].nproj = at.nproj
+            arr[i].E = (ctypes.c_double * 4)(*at.E)
+            arr[i].rc = at.rc
+        opts = _Opts(int(grid[0]), int(grid[1]), int(nquad), int(device), int(max_bands),
+                     float(precond_shift))
+        h = ctypes.c_void_p()
+        rc = self._lib.mb_setup(ctypes.byref(cell), _dptr(kp), kp.shape[0], float(ecut), _dptr(br),
+                                len(br), int(order), arr, len(atoms), ctypes.byref(opts),
+                                ctypes.byref(h))
+        if rc:
+            raise MBError(rc, "mb_setup")
+        self._h = h
+        self.nk = kp.shape[0]
+        self.device = device
+        self.grid = (int(grid[0]), int(grid[1]))
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.a1, w.a2, w.kpts, w.ecut, w.breaks, w.order, w.atoms, w.grid, w.nquad, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc:
+            msg = self._lib.mb_last_cuda_error(self._h).decode() if rc == 5 else ""
+            raise MBError(rc, what + (" " + msg if msg else ""))
+
+    def sizes(self, ik=0):
+        ng, nb, ldg = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.mb_sizes(self._h, ik, ctypes.byref(ng), ctypes.byref(nb),
+                                       ctypes.byref(ldg)), "mb_sizes")
+        return ng.value, nb.value, ldg.value
+
+    def gvectors(self, ik=0):
+        ng, _, _ = self.sizes(ik)
+        out = np.zeros(2 * ng, dtype=np.int32)
+        self._check(self._lib.mb_gvectors(self._h, ik, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
+                    "mb_gvectors")
+        return out.reshape(ng, 2)
+
+    def zplanes(self):
+        nq = ctypes.c_int()
+        self._check(self._lib.mb_zplanes(self._h, ctypes.byref(nq), None, None), "mb_zplanes")
+        zq = np.zeros(nq.value)
+        wq = np.zeros(nq.value)
+        self._check(self._lib.mb_zplanes(self._h, None, _dptr(zq), _dptr(wq)), "mb_zplanes")
+        return zq, wq
+
+    def set_local_potential(self, V):
+        V = np.ascontiguousarray(np.asarray(V, dtype=np.float64))
+        zq, _ = self.zplanes()
+        if V.size != len(zq) * self.grid[0] * self.grid[1]:
+            raise MBError(1, "local potential must hold nq * n1 * n2 values")
+        self._check(self._lib.mb_set_local_potential(self._h, _dptr(V)), "mb_set_local_potential")
+
+    # ---- applies on torch device tensors --------------------------------
+    @staticmethod
+    def _prec(prec):
+        return PREC[prec] if isinstance(prec, str) else int(prec)
+
+    def _check_block(self, ik, T, prec):
+        """Reject tensors whose size, dtype or placement would make the kernels
+        read or write outside them."""
+        import torch
+        ng, nb, ldg = self.sizes(ik)
+        want = torch.complex128 if self._prec(prec) == MB_FP64 else torch.complex64
+        if T.dtype != want or not T.is_cuda or not T.is_contiguous():
+            raise MBError(1, "block must be a contiguous CUDA %s tensor" % want)
+        if T.dim() != 3 or T.shape[1] != nb or T.shape[2] != ldg:
+            raise MBError(1, "block shape must be (nbands, %d, %d), got %s" % (nb, ldg, tuple(T.shape)))
+        if T.device.index != self.device:
+            raise MBError(1, "block is on cuda:%s, handle on cuda:%d" % (T.device.index, self.device))
+        return T.shape[0]
+
+    def apply_H(self, ik, X, Y, prec="fp64", stream=None):
+        nb = self._check_block(ik, X, prec)
+        if self._check_block(ik, Y, prec) != nb:
+            raise MBError(1, "X and Y band counts differ")
+        self._check(self._lib.mb_apply_H(self._h, ik, ctypes.c_void_p(X.data_ptr()),
+                                         ctypes.c_void_p(Y.data_ptr()), nb, self._prec(prec),
+                                         _stream_ptr(stream)), "mb_apply_H")
+
+    def apply_H_batch(self, iks: Sequence[int], Xs, Ys, prec="fp64", stream=None):
+        n = len(iks)
+        if len(Xs) != n or len(Ys) != n:
+            raise MBError(1, "one X and one Y per k-point")
+        for ik, X, Y in zip(iks, Xs, Ys):
+            if self._check_block(ik, X, prec) != Xs[0].shape[0] or self._check_block(ik, Y, prec) != Xs[0].shape[0]:
+                raise MBError(1, "all blocks need the same band count")
+        ik_arr = (ctypes.c_int * n)(*iks)
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Xs])
+        yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in Ys])
+        self._check(self._lib.mb_apply_H_batch(self._h, n, ik_arr, xp, yp, Xs[0].shape[0],
+                                               self._prec(prec), _stream_ptr(stream)), "mb_apply_H_batch")
+
+    def apply_S(self, ik, X, Y, prec="fp64", stream=None):
+        if self._check_block(ik, X, prec) != self._check_block(ik, Y, prec):
+            raise MBError(1, "X and Y band counts differ")
+        self._check(self._lib.mb_apply_S(self._h, ik, ctypes.c_void_p(X.data_ptr()),
+                                         ctypes.c_void_p(Y.data_ptr()), X.shape[0],
+                                         self._prec(prec), _stream_ptr(stream)), "mb_apply_S")
+
+    def apply_Sinv(self, ik, X, Y, prec="fp64", stream=None):
+        if self._check_block(ik, X, prec) != self._check_block(ik, Y, prec):
+            raise MBError(1, "X and Y band counts differ")
+        self._check(self._lib.mb_apply_Sinv(self._h, ik, ctypes.c_void_p(X.data_ptr()),
+                                            ctypes.c_void_p(Y.data_ptr()), X.shape[0],
+                                            self._prec(prec), _stream_ptr(stream)), "mb_apply_Sinv")
+
+    def eigsolve(self, nbands, tol, prec="fp64", evecs=None, krylov_depth=0, block=0,
+                 max_cycles=0, polish=0, stream=None, allow_notconv=False):
+        ev = np.zeros(self.nk * nbands)
+        info = SolveInfo()
+        so = SolveOpts(krylov_depth, block, max_cycles, polish)
+        rc = self._lib.mb_eigsolve(self._h, nbands, float(tol), self._prec(prec), _dptr(ev),
+                                   ctypes.c_void_p(evecs.data_ptr()) if evecs is not None else None,
+                                   ctypes.byref(so), ctypes.byref(info), _stream_ptr(stream))
+        if rc and not (rc == 3 and allow_notconv):
+            self._check(rc, "mb_eigsolve")
+        return ev.reshape(self.nk, nbands), info

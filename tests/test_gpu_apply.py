@@ -1,0 +1,228 @@
+"""GPU parity of mb_apply_H / mb_apply_S / mb_apply_Sinv against the oracle.
+
+Tolerances (max abs error / max |Y|):
+* FP64: 1e-10.  The FFT path and the oracle's direct G-space contraction round
+  differently; each is O(eps64 * log2(N1 N2) * kappa * nquad) relative, far
+  below this bound.
+* FP32: 2e-5.  float rounding of the FFT (~log2(N) * 6e-8), of the banded
+  kinetic rows (|D| >> |Y| for smooth vectors, cancellation ~1e2 * 6e-8) and
+  of the projector sums.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import hamiltonian as Hm
+from paper_1406_4960_gb300 import workloads as W
+
+from gpu_util import gmap, lib_block, oracle_block, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def mbmod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1406_4960_gb300 import mb
+    mb.load(build_if_missing=True)
+    return mb
+
+
+def _small_slab():
+    w = W.slab()
+    return W.scaled(w, ecut=6.0, n_int=23, nbands=5, name="slab-small")
+
+
+def _small_graphene():
+    w = W.graphene()
+    return W.scaled(w, ecut=4.0, n_int=17, nbands=3, name="graphene-small")
+
+
+CASES = {
+    "tiny": lambda: W.tiny(),
+    "slab-small": _small_slab,
+    "graphene-small": _small_graphene,
+}
+
+
+def _run_apply(mbmod, h, w, ik, X, prec, op="H"):
+    ng, nb, ldg = h.sizes(ik)
+    m = Hm.model_from_workload(w, ik)
+    perm = gmap(h, m, ik)
+    cdt = np.complex128 if prec == "fp64" else np.complex64
+    tdt = torch.complex128 if prec == "fp64" else torch.complex64
+    Xl = torch.from_numpy(lib_block(X, perm, ldg, cdt)).cuda()
+    Yl = torch.full_like(Xl, complex(np.nan, np.nan))
+    getattr(h, "apply_" + op)(ik, Xl, Yl, prec)
+    torch.cuda.synchronize()
+    Yh = Yl.cpu().numpy()
+    assert np.all(Yh[:, :, ng:] == 0), "padding columns must be written as zero"
+    return m, oracle_block(Yh, perm)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_H_matches_oracle(mbmod, case, prec):
+    w = CASES[case]()
+    h = mbmod.Handle.from_workload(w)
+    for ik in range(w.nk):
+        ng, nb, ldg = h.sizes(ik)
+        X = W.random_block(w.nbands, nb, ng, seed=100 + ik)
+        m, Y = _run_apply(mbmod, h, w, ik, X, prec)
+        ref = m.apply_H(X)
+        assert rel_err(Y, ref) < TOL[prec], (case, ik, rel_err(Y, ref))
+    h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_S_and_Sinv(mbmod, prec):
+    w = _small_slab()
+    h = mbmod.Handle.from_workload(w)
+    ng, nb, ldg = h.sizes(1)
+    X = W.random_block(4, nb, ng, seed=7)
+    m, Y = _run_apply(mbmod, h, w, 1, X, prec, "S")
+    assert rel_err(Y, m.apply_S(X)) < TOL[prec]
+    m, Z = _run_apply(mbmod, h, w, 1, X, prec, "Sinv")
+    ref = np.einsum("ij,bjg->big", np.linalg.inv(m.S), X)
+    assert rel_err(Z, ref) < (1e-11 if prec == "fp64" else 1e-4)
+    h.close()
+
+
+def test_apply_single_band_and_degenerate_inputs(mbmod):
+    w = W.tiny()
+    h = mbmod.Handle.from_workload(w)
+    ng, nb, ldg = h.sizes(0)
+    X = W.random_block(1, nb, ng, seed=3)
+    m, Y = _run_apply(mbmod, h, w, 0, X, "fp64")
+    assert rel_err(Y, m.apply_H(X)) < TOL["fp64"]
+    Z = np.zeros((2, nb, ng), dtype=np.complex128)
+    m, Y0 = _run_apply(mbmod, h, w, 0, Z, "fp64")
+    assert np.all(Y0 == 0)
+    h.close()
+
+
+def test_apply_is_deterministic_and_batch_matches(mbmod):
+    w = _small_slab()
+    h = mbmod.Handle.from_workload(w)
+    Xs, Ys = [], []
+    for ik in range(w.nk):
+        ng, nb, ldg = h.sizes(ik)
+        X = W.random_block(w.nbands, nb, ng, seed=200 + ik, ld=ldg)
+        Xs.append(torch.from_numpy(X).cuda())
+        Ys.append(torch.zeros_like(Xs[-1]))
+    h.apply_H_batch(list(range(w.nk)), Xs, Ys, "fp64")
+    Y1 = [y.clone() for y in Ys]
+    h.apply_H_batch(list(range(w.nk)), Xs, Ys, "fp64")
+    for a, b in zip(Y1, Ys):
+        assert torch.equal(a, b)
+    for ik in range(w.nk):
+        Yk = torch.zeros_like(Xs[ik])
+        h.apply_H(ik, Xs[ik], Yk, "fp64")
+        assert (Yk - Y1[ik]).abs().max().item() <= 1e-12 * Y1[ik].abs().max().item()
+    h.close()
+
+
+def test_local_potential_override_constant_shift(mbmod):
+    """A caller table V = V0 everywhere turns the local term into V0 * S."""
+    w = W.tiny()
+    h = mbmod.Handle.from_workload(w)
+    zq, wq = h.zplanes()
+    V0 = 0.25
+    h.set_local_potential(np.full((len(zq), w.grid[0], w.grid[1]), V0))
+    ng, nb, ldg = h.sizes(0)
+    X = W.random_block(2, nb, ng, seed=5)
+    m0 = Hm.model_from_workload(w, with_atoms=False, local_components=[(0, 0, lambda z: V0)])
+    perm = gmap(h, m0)
+    Xl = torch.from_numpy(lib_block(X, perm, ldg, np.complex128)).cuda()
+    Yl = torch.zeros_like(Xl)
+    h.apply_H(0, Xl, Yl, "fp64")
+    Y = oracle_block(Yl.cpu().numpy(), perm)
+    assert rel_err(Y, m0.apply_H(X)) < TOL["fp64"]
+    h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_slab_batch_sampled_entries(mbmod, prec):
+    """All 4 k-points x 32 bands of the C(001)-like slab in one batched apply
+    (the benchmark's launch), checked on sampled entries."""
+    w = W.slab()
+    h = mbmod.Handle.from_workload(w)
+    cdt = np.complex128 if prec == "fp64" else np.complex64
+    Xs, Ys, Xo, perms, models = [], [], [], [], []
+    for ik in range(w.nk):
+        ng, nb, ldg = h.sizes(ik)
+        m = Hm.model_from_workload(w, ik)
+        perm = gmap(h, m, ik)
+        X = W.random_block(w.nbands, nb, ng, seed=300 + ik)
+        Xo.append(X)
+        perms.append(perm)
+        models.append(m)
+        Xs.append(torch.from_numpy(lib_block(X, perm, ldg, cdt)).cuda())
+        Ys.append(torch.zeros_like(Xs[-1]))
+    h.apply_H_batch(list(range(w.nk)), Xs, Ys, prec)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    for ik in range(w.nk):
+        Y = oracle_block(Ys[ik].cpu().numpy(), perms[ik])
+        ng = len(perms[ik])
+        nb = Y.shape[1]
+        ent = [(int(rng.integers(0, w.nbands)), int(j), int(rng.integers(0, ng)))
+               for j in list(range(0, 6)) + list(range(nb - 6, nb)) + list(rng.integers(0, nb, 12))]
+        ref = models[ik].apply_H_entries(Xo[ik], ent)
+        got = np.array([Y[e] for e in ent])
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() / scale < 5 * TOL[prec]
+    h.close()
+
+
+def test_full_graphene_sampled_entries(mbmod):
+    w = W.graphene()
+    h = mbmod.Handle.from_workload(w)
+    ng, nb, ldg = h.sizes(0)
+    m = Hm.model_from_workload(w)
+    perm = gmap(h, m)
+    X = W.random_block(w.nbands, nb, ng, seed=9)
+    for prec, cdt in (("fp64", np.complex128), ("fp32", np.complex64)):
+        Xl = torch.from_numpy(lib_block(X, perm, ldg, cdt)).cuda()
+        Yl = torch.zeros_like(Xl)
+        h.apply_H(0, Xl, Yl, prec)
+        Y = oracle_block(Yl.cpu().numpy(), perm)
+        rng = np.random.default_rng(1)
+        ent = [(int(rng.integers(0, w.nbands)), int(rng.integers(0, nb)), int(rng.integers(0, ng)))
+               for _ in range(20)]
+        ref = m.apply_H_entries(X, ent)
+        got = np.array([Y[e] for e in ent])
+        assert np.abs(got - ref).max() / np.abs(ref).max() < 5 * TOL[prec], prec
+    h.close()
+
+
+def test_invalid_arguments_are_rejected(mbmod):
+    w = W.tiny()
+    with pytest.raises(mbmod.MBError):
+        mbmod.Handle(w.a1, w.a2, w.kpts, w.ecut, w.breaks, w.order, w.atoms, (4, 4))  # grid too small for the disc
+    with pytest.raises(mbmod.MBError):
+        mbmod.Handle(w.a1, w.a2, w.kpts, w.ecut, w.breaks[::-1], w.order, w.atoms, w.grid)
+    with pytest.raises(mbmod.MBError):
+        mbmod.Handle(w.a1, w.a2, w.kpts, w.ecut, w.breaks, w.order, w.atoms, (12, 16))  # not 2^n
+    h = mbmod.Handle.from_workload(w)
+    ng, nb, ldg = h.sizes(0)
+    X = torch.zeros((2, nb, ldg), dtype=torch.complex128, device="cuda")
+    Y = torch.zeros_like(X)
+    assert h._lib.mb_apply_H(h._h, 5, X.data_ptr(), Y.data_ptr(), 2, 0, None) == 1   # bad k index
+    assert h._lib.mb_apply_H(h._h, 0, X.data_ptr(), Y.data_ptr(), 0, 0, None) == 1   # no bands
+    assert h._lib.mb_apply_H(h._h, 0, X.data_ptr(), Y.data_ptr(), 2, 7, None) == 1   # bad precision
+    with pytest.raises(mbmod.MBError):
+        h.apply_H(0, X, torch.zeros((2, nb, ldg), dtype=torch.complex64, device="cuda"))  # dtype
+    with pytest.raises(mbmod.MBError):
+        h.apply_H(0, X, X)                            # in place is not allowed
+    zq, _ = h.zplanes()
+    with pytest.raises(mbmod.MBError):
+        h.set_local_potential(np.full((3,), 1.0))     # wrong size
+    with pytest.raises(mbmod.MBError):
+        h.set_local_potential(np.full((len(zq), 16, 16), np.nan))
+    h.close()
