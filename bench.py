@@ -1,0 +1,362 @@
+"""Benchmark of the mixed-basis hot path on GB300.
+
+Workload (N=1): the C(001)-(2x1)-like slab -- rectangular 9.5 x 4.75 bohr
+cell, 12 pseudo-atoms, Ecut 25 Ha (179-ish G per k), 32x16 grid, 120 order-6
+B-splines on slab-dense/geometric knots, KB s+p projectors, 2x2 k-points,
+32 bands.  Synthetic, seeded inputs.
+
+A step is one H application to the 32-band block at all 4 k-points in one
+batched call (B-spline evaluation, inverse FFTs, potential product, forward
+FFTs, adjoint, banded kinetic term, projector contractions).  `value` is
+Hpsi GB/s = algorithmic bytes / device time; the same apply in FP64 and the
+mixed-precision and plain-FP64 eigensolves are reported beside it.
+
+--impl reference times the CPU oracle (plain FP64 numpy/C) on a bounded
+sample of the same workload.
+
+Multi-GPU (torchrun): every rank runs an independent replica of the workload
+(k-point sets are independent problems; no collective on the data path), the
+step time is the max over ranks and `value` sums all ranks' bytes.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hψ GB/s & eigensolves/s at 1e-6 Ha vs plain FP64 GPU; p50/p99 solve latency"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3   # SMs x FP32 lanes x 2 flop x max SM clock (GHz)
+# dram bytes per plane-kernel launch from the ncu capture summarised in
+# profiles/plane_kernel_slab.md (None until a capture of the current kernel exists)
+PLANE_TRAFFIC_BYTES = None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def workload_sizes(h, w, prec):
+    """Algorithmic bytes and plane-kernel flops of one batched apply."""
+    cb = 16 if prec == "fp64" else 8
+    rb = cb // 2
+    zq, _ = h.zplanes()
+    nq = len(zq)
+    n1, n2 = w.grid
+    N = n1 * n2
+    nproj = sum(a.nproj for a in w.atoms)
+    byts = nq * N * rb
+    flops = 0.0
+    for ik in range(w.nk):
+        ng, nb, ldg = h.sizes(ik)
+        byts += 2 * ng * nb * w.nbands * cb + nproj * (ng + nb) * cb
+        flops += w.nbands * nq * (8 * w.order * ng + 10 * N * math.log2(N) + 2 * N)
+    return byts, flops
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, budget_s=12.0, impl_steps=None):
+    """The FP64 oracle applying H to the 32-band block, one k-point at a time,
+    until the budget is spent; returns (GB/s, cores, sample, seconds)."""
+    from oracle import hamiltonian as Hm
+    from paper_1406_4960_gb300 import workloads as W
+    t_setup = time.perf_counter()
+    models = [Hm.model_from_workload(w, ik) for ik in range(w.nk)]
+    del t_setup
+    nproj = sum(a.nproj for a in w.atoms)
+    n1, n2 = w.grid
+    nq = models[0].zb.zq.size
+    done_bytes, t_used, n_apply = 0.0, 0.0, 0
+    ik = 0
+    while (n_apply < impl_steps) if impl_steps is not None else (t_used < budget_s):
+        m = models[ik % w.nk]
+        X = W.random_block(w.nbands, m.nb, m.ng, seed=500 + ik)
+        t0 = time.perf_counter()
+        m.apply_H(X)
+        t_used += time.perf_counter() - t0
+        done_bytes += 2 * m.ng * m.nb * w.nbands * 8 + nproj * (m.ng + m.nb) * 8 + nq * n1 * n2 * 4 / w.nk
+        n_apply += 1
+        ik += 1
+    cores = _blas_threads()
+    sample = "%d single-k-point H applies of the %d-band block (FP64 oracle, bytes counted at FP32 widths)" % (
+        n_apply, w.nbands)
+    return done_bytes / t_used / 1e9, cores, sample, t_used, n_apply
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    from paper_1406_4960_gb300 import workloads as W
+    w = W.slab()
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline(w, budget_s=0.0, impl_steps=1)
+    t0 = time.perf_counter()
+    per_step = []
+    gbs_all = []
+    for _ in range(args.steps):
+        gbs, cores, sample, secs, n = cpu_baseline(w, budget_s=0.0, impl_steps=1)
+        per_step.append(secs)
+        gbs_all.append(gbs)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(gbs_all))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(per_step)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "slab: C(001)-like, 12 atoms, Ecut 25 Ha, 32x16 grid, 120 B-splines, 4 k, 32 bands",
+                   "step": "one single-k-point H apply of the 32-band block (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d single-k-point applies" % args.steps},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1406_4960_gb300 import mb, workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def allmax(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = W.slab()
+    mb.load(build_if_missing=True)
+    lib = mb.load()
+    h = mb.Handle.from_workload(w, device=local)
+    iks = list(range(w.nk))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def blocks(prec, seed):
+        dt = torch.complex128 if prec == "fp64" else torch.complex64
+        Xs, Ys = [], []
+        for ik in iks:
+            ng, nb, ldg = h.sizes(ik)
+            x = W.random_block(w.nbands, nb, ng, seed=seed + ik, ld=ldg)
+            Xs.append(torch.from_numpy(x).to(dt).cuda())
+            Ys.append(torch.zeros_like(Xs[-1]))
+        return Xs, Ys
+
+    def timed(prec, steps, warmup, profile=False):
+        Xs, Ys = blocks(prec, 1000 + rank)
+        for _ in range(warmup):
+            h.apply_H_batch(iks, Xs, Ys, prec, stream)
+        torch.cuda.synchronize()
+        if profile:
+            lib.mb_profile_reset(h._h)
+            lib.mb_set_profiling(h._h, 1)
+        n0 = lib.mb_launch_count(h._h)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.zero_()                      # L2 flush outside the timed events
+            ev[i][0].record(stream)
+            h.apply_H_batch(iks, Xs, Ys, prec, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        launches = lib.mb_launch_count(h._h) - n0
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        prof = {}
+        if profile:
+            import ctypes
+            lib.mb_set_profiling(h._h, 0)
+            for kid in range(11):
+                t, c = ctypes.c_double(), ctypes.c_longlong()
+                lib.mb_profile_read(h._h, kid, ctypes.byref(t), ctypes.byref(c))
+                if c.value:
+                    prof[lib.mb_kernel_name(kid).decode()] = (t.value, c.value)
+        return allmax(ms), launches, prof
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms32, launches, prof = timed("fp32", args.steps, args.warmup, profile=True)
+    clk = clocks.stop()
+    ms64, _, prof64 = timed("fp64", max(3, args.steps // 5), 3, profile=True)
+
+    bytes32, flops32 = workload_sizes(h, w, "fp32")
+    bytes64, _ = workload_sizes(h, w, "fp64")
+    value = world * bytes32 / (ms32 * 1e-3) / 1e9
+
+    # e2e: host (pinned) X -> device, apply, device -> host Y, every step
+    Xs, Ys = blocks("fp32", 2000 + rank)
+    hX = [x.cpu().pin_memory() for x in Xs]
+    hY = [torch.empty_like(y, device="cpu").pin_memory() for y in Ys]
+    for _ in range(2):
+        for a, b in zip(hX, Xs):
+            b.copy_(a, non_blocking=True)
+        h.apply_H_batch(iks, Xs, Ys, "fp32", stream)
+        for a, b in zip(Ys, hY):
+            b.copy_(a, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for a, b in zip(hX, Xs):
+            b.copy_(a, non_blocking=True)
+        h.apply_H_batch(iks, Xs, Ys, "fp32", stream)
+        for a, b in zip(Ys, hY):
+            b.copy_(a, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = allmax(e0.elapsed_time(e1) / args.steps)
+    h2d = sum(x.numel() * x.element_size() for x in hX)
+    d2h = sum(y.numel() * y.element_size() for y in hY)
+
+    roof = None
+    if "plane" in prof:
+        t, c = prof["plane"]
+        per_launch_ms = t / c
+        plane_flops = flops32 / max(1, c // max(1, args.steps))
+        ach = plane_flops / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": PLANE_TRAFFIC_BYTES,
+                "kernel": "plane_kernel<float>", "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                "kernel_ms": per_launch_ms,
+                "share_of_step": t / args.steps / ms32}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "slab: C(001)-like, 12 atoms, Ecut 25 Ha, 32x16 grid, 120 B-splines, 4 k, 32 bands",
+                   "step": "one batched H apply, 4 k x 32 bands, FP32",
+                   "l2": "256 MB buffer written between timed steps (outside the events)",
+                   "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
+        "fp64_apply": {"value": world * bytes64 / (ms64 * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms64},
+        "kernels_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in prof.items()},
+        "kernels_ms_per_step_fp64": {k: v[0] / max(1, args.steps // 5) for k, v in prof64.items()},
+        "gpu_launches": int(launches),
+        "e2e": {"value": world * bytes32 / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        gbs, cores, sample, secs, n = cpu_baseline(w, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                                "sample": sample, "seconds": secs}
+    if rank == 0:
+        print(json.dumps(line))
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -150,7 +150,9 @@ typedef struct {
     int krylov_depth;     /* k of K = span{v, A v, ..., A^k v} (0: 4) */
     int block;            /* roots per block in the second grand cycle (0: 4) */
     int max_cycles;       /* (0: 200) */
-    int polish;           /* mixed precision only: FP64 cycles at the end (0: auto) */
+    int polish;           /* reserved (0) */
+    int guard;            /* extra roots carried above the requested ones
+                             (0: max(2, ceil(nbands/8)); negative: none) */
 } mb_solve_opts;
 
 /* Lowest `nbands` roots of H c = eps S c at every k-point (§II.C).
@@ -166,6 +168,18 @@ typedef struct {
 int mb_eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals,
                 void *evecs, const mb_solve_opts *sopts, mb_solve_info *info,
                 void *stream);
+
+/* ---- instrumentation ------------------------------------------------
+ * Every kernel the library launches is counted per handle.  With profiling
+ * on, each launch is also bracketed by CUDA events on its own stream; the
+ * per-kernel totals accumulate until mb_profile_reset.  Kernel ids:
+ * 0 plane, 1 epilogue, 2 proj, 3 coef, 4 backproj, 5 banded, 6 gram,
+ * 7 combine, 8 jacobi, 9 small, 10 vec (mb_kernel_name gives the names). */
+int mb_set_profiling(mb_handle *h, int on);
+int mb_profile_read(mb_handle *h, int kernel, double *ms_total, long long *count);
+int mb_profile_reset(mb_handle *h);
+long long mb_launch_count(const mb_handle *h);
+const char *mb_kernel_name(int kernel);
 
 /* Message for an error code (static storage). */
 const char *mb_strerror(int code);

@@ -26,7 +26,11 @@ Readings of §II.C (the paper leaves them open):
   sum_j |<y|S|x_j>|^2 over the block's inputs; a Ritz vector whose value lies
   below the block's lowest input value and whose overlap is below 1/2 is a
   new root: it replaces the selected vector with the highest value.
-* Converged when every residual ||H x - eps S x||_{S^-1} < tol.
+* Converged when every residual ||H x - eps S x||_{S^-1} < tol over the
+  requested roots.  g = max(2, ceil(M/8)) guard roots above them are
+  carried along (and seeded from the free-electron start) so that a root the
+  trial set misses is captured instead of the iteration settling on a
+  higher one.
 """
 from __future__ import annotations
 
@@ -226,11 +230,19 @@ def residual_norms(ops, X, HX, SX, eps):
     return np.sqrt(np.maximum(np.real(np.sum(np.conj(R) * SiR, axis=0)), 0.0))
 
 
+def default_guard(nroots):
+    return max(2, -(-nroots // 8))
+
+
 def lanczos_krylov(ops, X0, nroots, depth=4, block=8, tol=1e-8, max_cycles=300,
-                   history=None):
+                   history=None, guard=None):
     """Lowest `nroots` eigenpairs of H c = eps S c from trial vectors X0 (n, m0).
 
+    `guard` extra roots are carried along (X0 needs nroots + guard columns)
+    and only the lowest `nroots` are tested for convergence and returned.
     Returns (eps, X, info) with X S-orthonormal."""
+    nconv = nroots
+    nroots = nroots + (default_guard(nroots) if guard is None else guard)
     X, SX = s_orthonormalize(ops, X0)
     HX = ops.H(X)
     w, Y = _rayleigh_ritz(X, HX)
@@ -241,8 +253,9 @@ def lanczos_krylov(ops, X0, nroots, depth=4, block=8, tol=1e-8, max_cycles=300,
     res = residual_norms(ops, X, HX, SX, eps)
     cycles = 0
     for cycles in range(1, max_cycles + 1):
-        # --- cycle A: all roots + one Krylov space, seeded at the worst root
-        i = int(np.argmax(res))
+        # --- cycle A: all roots + one Krylov space, seeded at the worst
+        # root among those that are tested for convergence
+        i = int(np.argmax(res[:nconv]))
         K, SK = _krylov(ops, X[:, i], eps[i], X, SX, depth)
         V = np.hstack([X, K])
         SV = np.hstack([SX, SK])
@@ -274,7 +287,7 @@ def lanczos_krylov(ops, X0, nroots, depth=4, block=8, tol=1e-8, max_cycles=300,
         X, SX, HX, eps = X @ Y, SX @ Y, HX @ Y, w.copy()
         res = residual_norms(ops, X, HX, SX, eps)
         if history is not None:
-            history.append((cycles, eps.copy(), res.copy()))
-        if np.max(res) < tol:
+            history.append((cycles, eps[:nconv].copy(), res[:nconv].copy()))
+        if np.max(res[:nconv]) < tol:
             break
-    return eps, X, {"cycles": cycles, "residuals": res}
+    return eps[:nconv], X[:, :nconv], {"cycles": cycles, "residuals": res[:nconv]}

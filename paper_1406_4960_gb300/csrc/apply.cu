@@ -18,35 +18,11 @@
 #include <algorithm>
 #include <cstring>
 
+#include "apply_common.cuh"
 #include "cplx.cuh"
 #include "mb_internal.h"
 
 namespace mb {
-
-constexpr int kMaxK = 64;   // k-points per launch (descriptors travel as kernel parameters)
-
-struct KDesc {
-    const void *X;
-    void *Y;
-    void *part;      // boundary partial rows
-    void *W;         // projector overlaps W[(b, j)][p]
-    void *C;         // back-projection coefficients C[(b, j)][p]
-    int ng, ldg;
-    int kofs;        // offset of per-k G arrays
-    int qofs;        // offset of q_p(G) table
-};
-
-template <typename R> struct PlaneArgs {
-    const R *Bq;
-    const R *V;
-    const typename V2<R>::T *tw;
-    const int *goff;
-    int n1, n2, l1, l2, nmax;
-    int order, nquad, nint, nb;
-    int nbands, nchunks, chunk, np, ldg_max;
-    int nsel;
-    KDesc d[kMaxK];
-};
 
 // ---------------------------------------------------------------------------
 // radix-2 FFTs on ns planes of N1 x N2 in shared memory (row-major, i2 fastest)
@@ -408,6 +384,16 @@ int cuda_fail(mb_handle *h, cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? MB_ENOMEM : MB_ECUDA;
 }
 
+// Launch with accounting: counts the launch and, when profiling, brackets it
+// with events on the launch stream.
+#define MB_LAUNCH(h, s, kid, ...)                       \
+    do {                                                \
+        cudaEvent_t ev_;                                \
+        prof_begin(h, s, kid, &ev_);                    \
+        __VA_ARGS__;                                    \
+        prof_end(h, s, kid, ev_);                       \
+    } while (0)
+
 #define MB_CUDA(call)                                  \
     do {                                               \
         cudaError_t e_ = (call);                       \
@@ -466,11 +452,14 @@ static int upload_set(mb_handle *h, DevTables &t) {
 }
 
 int upload_potential(mb_handle *h) {
-    std::vector<double> vp;
+    std::vector<double> vp, vn;
     vtable_permuted(h, vp);
+    vtable_natural(h, vn);
     int rc;
     if ((rc = upload<double>(h, &h->t64.V, vp))) return rc;
     if ((rc = upload<float>(h, &h->t32.V, vp))) return rc;
+    if ((rc = upload<double>(h, &h->t64.Vn, vn))) return rc;
+    if ((rc = upload<float>(h, &h->t32.Vn, vn))) return rc;
     return MB_OK;
 }
 
@@ -485,6 +474,26 @@ int upload_tables(mb_handle *h) {
         for (int g = 0; g < h->kp[ik].ng; ++g) goff[h->kofs[ik] + g] = h->kp[ik].goff[g];
     MB_CUDA(cudaMalloc(&h->d_goff, goff.size() * sizeof(int)));
     MB_CUDA(cudaMemcpy(h->d_goff, goff.data(), goff.size() * sizeof(int), cudaMemcpyHostToDevice));
+    // grid rows that hold disc points, per k-point
+    std::vector<int> rows;
+    h->rows_ofs.assign(h->kp.size(), 0);
+    h->nrows.assign(h->kp.size(), 0);
+    h->rowmask.assign(h->kp.size(), 0ull);
+    for (size_t ik = 0; ik < h->kp.size(); ++ik) {
+        std::vector<char> used(h->n1, 0);
+        for (int g = 0; g < h->kp[ik].ng; ++g) used[h->kp[ik].goff[g] / h->n2] = 1;
+        h->rows_ofs[ik] = (int)rows.size();
+        for (int r = 0; r < h->n1; ++r)
+            if (used[r]) {
+                rows.push_back(r);
+                if (r < 64) h->rowmask[ik] |= 1ull << r;
+            }
+        h->nrows[ik] = (int)rows.size() - h->rows_ofs[ik];
+    }
+    MB_CUDA(cudaMalloc(&h->d_rows, rows.size() * sizeof(int)));
+    MB_CUDA(cudaMemcpy(h->d_rows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+    upload_fft_twiddles();
+    MB_CUDA(cudaGetLastError());
     return MB_OK;
 }
 
@@ -504,7 +513,7 @@ int ensure_precond(mb_handle *h) {
 }
 
 static void free_set(DevTables &t) {
-    void **ps[] = {&t.Bq, &t.V, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.q2, &t.qproj, &t.zproj, &t.E, &t.Pfac};
+    void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.q2, &t.qproj, &t.zproj, &t.E, &t.Pfac};
     for (void **p : ps) {
         if (*p) cudaFree(*p);
         *p = nullptr;
@@ -517,6 +526,8 @@ void free_tables(mb_handle *h) {
     free_set(h->t32);
     if (h->d_goff) cudaFree(h->d_goff);
     h->d_goff = nullptr;
+    if (h->d_rows) cudaFree(h->d_rows);
+    h->d_rows = nullptr;
     if (h->scratch.ptr) cudaFree(h->scratch.ptr);
     h->scratch = Scratch();
 }
@@ -533,12 +544,51 @@ int ensure_scratch(mb_handle *h, size_t bytes) {
     return MB_OK;
 }
 
-static void plan_chunks(const mb_handle *h, int nsel, int nbands, int &chunk, int &nchunks) {
-    int sms = 152;
-    int target = std::max(1, (4 * sms + nsel * nbands - 1) / (nsel * nbands));
-    chunk = std::max(h->order, (h->nint + target - 1) / target);
-    if (chunk >= h->nint) chunk = h->nint;
-    nchunks = (h->nint + chunk - 1) / chunk;
+// Launch plan of the plane kernel for one batched apply.
+struct PlanePlan {
+    bool reg = false;      // register-FFT kernel (else radix-2 shared-memory kernel)
+    int bt = 1;            // bands per CTA
+    int np = 1;            // planes in flight
+    int chunk = 1, nchunks = 1;
+    size_t smem = 0;
+};
+
+static PlanePlan plan_plane(const mb_handle *h, int nsel, int nbands, size_t c2, int maxldg, bool reg_ok) {
+    PlanePlan p;
+    const int K = h->order, P = h->nquad;
+    const size_t NN = (size_t)h->n1 * h->n2;
+    int ctas_per_sm = 1;
+    if (reg_ok) {
+        const size_t plane_bytes = (size_t)h->n1 * (h->n2 + 1) * c2;
+        ctas_per_sm = NN <= 1024 ? 2 : 1;
+        for (int bt = NN <= 1024 ? 2 : 1; bt >= 1 && !p.reg; --bt) {
+            size_t budget = (size_t)h->smem_optin / ctas_per_sm - 1024;
+            size_t acc = (size_t)bt * K * maxldg * c2;
+            if (acc + plane_bytes > budget) continue;
+            int np = (int)std::min<size_t>((size_t)bt * P, (budget - acc) / plane_bytes);
+            if (np < 1) continue;
+            p.reg = true;
+            p.bt = bt;
+            p.np = np;
+            p.smem = acc + (size_t)np * plane_bytes;
+        }
+    }
+    if (!p.reg) {
+        ctas_per_sm = 1;
+        const int nmax = std::max(h->n1, h->n2);
+        const size_t fixed = (nmax / 2 + (size_t)K * maxldg) * c2;
+        const size_t budget = (size_t)h->smem_optin;
+        p.bt = 1;
+        p.np = (int)std::min<size_t>((size_t)P, fixed < budget ? (budget - fixed) / (NN * c2) : 0);
+        p.smem = fixed + (size_t)p.np * NN * c2;
+    }
+    const int pairs = nsel * ((nbands + p.bt - 1) / p.bt);
+    const int want = 2 * h->num_sms * ctas_per_sm;
+    const int target = std::max(1, (want + pairs - 1) / pairs);
+    p.chunk = std::max(K, (h->nint + target - 1) / target);
+    if (p.chunk >= h->nint) p.chunk = h->nint;
+    p.nchunks = (h->nint + p.chunk - 1) / p.chunk;
+    return p;
 }
 
 static size_t per_k_scratch(const mb_handle *h, int ldg, int nbands, int nchunks, size_t c2) {
@@ -550,11 +600,12 @@ static size_t per_k_scratch(const mb_handle *h, int ldg, int nbands, int nchunks
 
 size_t apply_scratch_bytes(const mb_handle *h, int nsel_max, int nbands, int prec) {
     size_t c2 = prec == MB_FP64 ? 16 : 8;
-    int chunk, nchunks;
-    plan_chunks(h, std::min(nsel_max, kMaxK), nbands, chunk, nchunks);
     int maxldg = 0;
     for (auto &k : h->kp) maxldg = std::max(maxldg, k.ldg);
-    return (size_t)std::min(nsel_max, kMaxK) * per_k_scratch(h, maxldg, nbands, nchunks, c2);
+    int nsel = std::min(nsel_max, kMaxK);
+    bool reg = prec == MB_FP64 ? plane_reg_supported<double>(h->n1, h->n2) : plane_reg_supported<float>(h->n1, h->n2);
+    PlanePlan p = plan_plane(h, nsel, nbands, c2, maxldg, reg);
+    return (size_t)nsel * per_k_scratch(h, maxldg, nbands, p.nchunks, c2);
 }
 
 template <typename R>
@@ -562,12 +613,13 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
                          int nbands, cudaStream_t s, const DevTables &t) {
     typedef typename V2<R>::T R2;
     const size_t c2 = sizeof(R2);
-    int chunk, nchunks;
-    plan_chunks(h, nsel, nbands, chunk, nchunks);
     std::vector<KDesc> desc(nsel);
     size_t off = 0;
     int maxldg = 0;
     for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
+    const PlanePlan plan = plan_plane(h, nsel, nbands, c2, maxldg, plane_reg_supported<R>(h->n1, h->n2));
+    const int chunk = plan.chunk, nchunks = plan.nchunks;
+    if (plan.np < 1) return MB_EUNSUPPORTED;
     size_t need = (size_t)nsel * per_k_scratch(h, maxldg, nbands, nchunks, c2);
     int rc = ensure_scratch(h, need);
     if (rc) return rc;
@@ -582,6 +634,9 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
         d.ldg = kp.ldg;
         d.kofs = h->kofs[iks[i]];
         d.qofs = h->qofs[iks[i]];
+        d.rows_ofs = h->rows_ofs[iks[i]];
+        d.nrows = h->nrows[iks[i]];
+        d.rowmask = h->rowmask[iks[i]];
         size_t part = (size_t)nbands * std::max(0, nchunks - 1) * 2 * (h->order - 1) * kp.ldg * c2;
         size_t w = (size_t)nbands * h->nb * std::max(1, h->nproj) * c2;
         d.part = base + off;
@@ -601,7 +656,7 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
         ga.nproj = h->nproj;
         std::copy(desc.begin(), desc.end(), ga.d);
         dim3 grid((nbands * h->nb + 63) / 64, (h->nproj + 63) / 64, nsel);
-        zgemm_kernel<R><<<grid, 256, 0, s>>>(ga);
+        MB_LAUNCH(h, s, KN_PROJ, zgemm_kernel<R><<<grid, 256, 0, s>>>(ga));
         CoefArgs<R> ca;
         ca.zproj = reinterpret_cast<const R *>(t.zproj);
         ca.E = reinterpret_cast<const R *>(t.E);
@@ -609,12 +664,14 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
         ca.nbands = nbands;
         ca.nproj = h->nproj;
         std::copy(desc.begin(), desc.end(), ca.d);
-        coef_kernel<R><<<dim3((nbands * h->nproj + 127) / 128, nsel), 128, 0, s>>>(ca);
+        MB_LAUNCH(h, s, KN_COEF, coef_kernel<R><<<dim3((nbands * h->nproj + 127) / 128, nsel), 128, 0, s>>>(ca));
     }
     // local potential through the planes
     PlaneArgs<R> pa;
     pa.Bq = reinterpret_cast<const R *>(t.Bq);
     pa.V = reinterpret_cast<const R *>(t.V);
+    pa.Vn = reinterpret_cast<const R *>(t.Vn);
+    pa.rows = h->d_rows;
     pa.tw = reinterpret_cast<const R2 *>(t.tw);
     pa.goff = h->d_goff;
     pa.n1 = h->n1;
@@ -631,16 +688,18 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
     pa.chunk = chunk;
     pa.ldg_max = maxldg;
     pa.nsel = nsel;
+    pa.bt = plan.bt;
+    pa.np = plan.np;
     std::copy(desc.begin(), desc.end(), pa.d);
-    const size_t NN = (size_t)h->n1 * h->n2;
-    const size_t fixed = (pa.nmax / 2 + (size_t)h->order * maxldg) * c2;
-    const size_t budget = (size_t)h->smem_optin;
-    int np = (int)std::min<size_t>((size_t)h->nquad, fixed < budget ? (budget - fixed) / (NN * c2) : 0);
-    if (np < 1) return MB_EUNSUPPORTED;
-    pa.np = np;
-    size_t smem = fixed + (size_t)np * NN * c2;
-    MB_CUDA(cudaFuncSetAttribute(plane_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    plane_kernel<R><<<nsel * nbands * nchunks, 256, smem, s>>>(pa);
+    if (plan.reg) {
+        const unsigned grid = (unsigned)(nsel * ((nbands + plan.bt - 1) / plan.bt) * nchunks);
+        cudaError_t e = cudaSuccess;
+        MB_LAUNCH(h, s, KN_PLANE, e = plane_reg_launch<R>(pa, grid, plan.smem, s));
+        MB_CUDA(e);
+    } else {
+        MB_CUDA(cudaFuncSetAttribute(plane_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem));
+        MB_LAUNCH(h, s, KN_PLANE, plane_kernel<R><<<nsel * nbands * nchunks, 256, plan.smem, s>>>(pa));
+    }
     EpiArgs<R> ea;
     ea.Sband = reinterpret_cast<const R *>(t.Sband);
     ea.Dband = reinterpret_cast<const R *>(t.Dband);
@@ -652,7 +711,7 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
     ea.chunk = chunk;
     ea.nint = h->nint;
     std::copy(desc.begin(), desc.end(), ea.d);
-    epilogue_kernel<R><<<dim3(h->nb, nbands, nsel), 256, 0, s>>>(ea);
+    MB_LAUNCH(h, s, KN_EPILOGUE, epilogue_kernel<R><<<dim3(h->nb, nbands, nsel), 256, 0, s>>>(ea));
     if (h->nproj > 0) {
         GemmArgs<R> ga;
         ga.Q = reinterpret_cast<const R2 *>(t.qproj);
@@ -662,7 +721,7 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
         ga.nproj = h->nproj;
         std::copy(desc.begin(), desc.end(), ga.d);
         dim3 grid((nbands * h->nb + 63) / 64, (maxldg + 63) / 64, nsel);
-        zgemm_kernel<R><<<grid, 256, 0, s>>>(ga);
+        MB_LAUNCH(h, s, KN_BACKPROJ, zgemm_kernel<R><<<grid, 256, 0, s>>>(ga));
     }
     MB_CUDA(cudaGetLastError());
     return MB_OK;
@@ -707,21 +766,21 @@ int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nb
         auto x = reinterpret_cast<const double2 *>(X);
         auto y = reinterpret_cast<double2 *>(Y);
         if (which == BAND_S)
-            banded_S_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+            MB_LAUNCH(h, s, KN_BANDED, banded_S_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
         else if (which == BAND_SINV)
-            banded_solve_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
         else
-            banded_solve_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Pfac + pofs, gstride, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Pfac + pofs, gstride, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
     } else {
         const DevTables &t = h->t32;
         auto x = reinterpret_cast<const float2 *>(X);
         auto y = reinterpret_cast<float2 *>(Y);
         if (which == BAND_S)
-            banded_S_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+            MB_LAUNCH(h, s, KN_BANDED, banded_S_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
         else if (which == BAND_SINV)
-            banded_solve_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
         else
-            banded_solve_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Pfac + pofs, gstride, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y);
+            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Pfac + pofs, gstride, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
     }
     MB_CUDA(cudaGetLastError());
     return MB_OK;

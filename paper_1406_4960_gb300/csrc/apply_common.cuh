@@ -1,0 +1,46 @@
+// Launch descriptors shared by the apply kernels.
+#pragma once
+
+#include "cplx.cuh"
+
+namespace mb {
+
+constexpr int kMaxK = 64;   // k-points per launch (descriptors travel as kernel parameters)
+
+struct KDesc {
+    const void *X;
+    void *Y;
+    void *part;      // boundary partial rows
+    void *W;         // projector overlaps W[(b, j)][p]
+    void *C;         // back-projection coefficients C[(b, j)][p]
+    int ng, ldg;
+    int kofs;        // offset of per-k G arrays
+    int qofs;        // offset of q_p(G) table
+    int rows_ofs;    // offset of this k-point's list of grid rows that hold disc points
+    int nrows;
+    unsigned long long rowmask;   // bit i1 set when grid row i1 holds disc points
+};
+
+template <typename R> struct PlaneArgs {
+    const R *Bq;
+    const R *V;       // bit-reversed layout (radix-2 kernel)
+    const R *Vn;      // natural layout (register-FFT kernel)
+    const int *rows;  // active grid rows of every k-point
+    const typename V2<R>::T *tw;
+    const int *goff;
+    int n1, n2, l1, l2, nmax;
+    int order, nquad, nint, nb;
+    int nbands, nchunks, chunk, np, ldg_max;
+    int nsel;
+    int bt;           // bands per CTA (register-FFT kernel)
+    KDesc d[kMaxK];
+};
+
+
+// register-FFT plane kernel (plane_reg.cu): available grids and launch
+template <typename R> bool plane_reg_supported(int n1, int n2);
+template <typename R>
+cudaError_t plane_reg_launch(const PlaneArgs<R> &a, unsigned grid, size_t smem, cudaStream_t s);
+void upload_fft_twiddles();
+
+}  // namespace mb

@@ -1,11 +1,1072 @@
-// Generalized Lanczos-Krylov eigensolver (§II.C) -- placeholder until the
-// device solver lands.
+// Generalized Lanczos-Krylov eigensolver (§II.C) on the device.
+//
+// Per k-point the solver keeps M roots X with HX and SX, and runs two
+// alternating grand cycles:
+//   A  Rayleigh-Ritz on [X | K_A], K_A the Krylov space of the root with the
+//      largest residual;
+//   B  roots split into blocks of b; each block does Rayleigh-Ritz on
+//      [X_b | K_b] and keeps the b Ritz pairs of maximum overlap with its
+//      inputs (plus any new lower root).
+// after which X is S-orthonormalized (Cholesky-QR, twice) and rotated to
+// Ritz vectors.  Krylov vectors come from A = P (H - theta S), P the banded
+// per-G solve (T(G) + c S)^-1, S-orthogonalized by classical Gram-Schmidt
+// applied twice.  Every step runs for all k-points in one launch.
+//
+// Precision: the H applies run in the requested precision; Gram products,
+// Jacobi, Cholesky-QR, residuals and the banded S / P solves are FP64.  In
+// the mixed mode the last cycles switch the applies to FP64 (the FP64
+// residual is the convergence test).
+#include <algorithm>
+#include <chrono>
+#include <tuple>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cplx.cuh"
 #include "mb_internal.h"
 
 namespace mb {
-int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void *evecs,
-             const mb_solve_opts *sopts, mb_solve_info *info, cudaStream_t s) {
-    (void)h; (void)nbands; (void)tol; (void)prec; (void)evals; (void)evecs; (void)sopts; (void)info; (void)s;
-    return MB_EUNSUPPORTED;
+
+constexpr int LD = 128;       // leading dimension of subspace matrices
+constexpr int JMAX = 112;     // largest subspace the Jacobi kernel holds (matrix in shared memory)
+constexpr int GT = 16;        // n-tile of the Gram kernel
+constexpr int JPAIRS = 58;    // rotation slots per Jacobi round (>= JMAX/2 + 1, even so that
+                              // 5*JPAIRS doubles keep the next double2 array 16-byte aligned)
+
+struct EigK {
+    double2 *base;            // FP64 vectors of this k-point, stride nvec
+    float2 *stage;            // FP32 staging for mixed-precision applies
+    const double *pfac;       // preconditioner factors of this k-point
+    long long nvec;           // nb * ldg
+    int ldg, ng;
+};
+
+// vector index sets: i < c1 -> s1 + ch*cs1 + i;  else s2 + ch*cs2 + (i - c1)
+struct VSet {
+    int s1, c1, cs1, s2, c2, cs2;
+    __host__ __device__ int count() const { return c1 + c2; }
+    __host__ __device__ int at(int i, int ch) const {
+        return i < c1 ? s1 + ch * cs1 + i : s2 + ch * cs2 + (i - c1);
+    }
+};
+static VSet vs(int s1, int c1, int cs1 = 0, int s2 = 0, int c2 = 0, int cs2 = 0) {
+    VSet v;
+    v.s1 = s1; v.c1 = c1; v.cs1 = cs1; v.s2 = s2; v.c2 = c2; v.cs2 = cs2;
+    return v;
 }
+
+// ---------------------------------------------------------------------------
+// Gram products G = A^H B over the full vector length, split into n-chunks
+// whose partial sums are reduced in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) gram_partial_kernel(const EigK *ks, int nch, VSet A, VSet B,
+                                                           int nsplit, double2 *part) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int prob = blockIdx.y, split = blockIdx.x;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const int ma = A.count(), mb = B.count();
+    double2 *As = reinterpret_cast<double2 *>(sm);          // [GT][ma]
+    double2 *Bs = As + GT * ma;                             // [GT][mb]
+    const long long n = d.nvec;
+    const long long chunk = ((n + nsplit - 1) / nsplit + GT - 1) / GT * GT;
+    const long long t0 = split * chunk, t1 = min(n, t0 + chunk);
+    constexpr int RMAX = 36;
+    double2 acc[RMAX];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) acc[r] = make_double2(0.0, 0.0);
+    const int nout = ma * mb;
+    const int obase = blockIdx.z * RMAX * 256;     // this CTA's slice of the outputs
+    for (long long tb = t0; tb < t1; tb += GT) {
+        for (int e = threadIdx.x; e < GT * ma; e += blockDim.x) {
+            int i = e / GT, tt = e % GT;
+            long long t = tb + tt;
+            As[tt * ma + i] = t < t1 ? d.base[(long long)A.at(i, ch) * n + t] : make_double2(0.0, 0.0);
+        }
+        for (int e = threadIdx.x; e < GT * mb; e += blockDim.x) {
+            int j = e / GT, tt = e % GT;
+            long long t = tb + tt;
+            Bs[tt * mb + j] = t < t1 ? d.base[(long long)B.at(j, ch) * n + t] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        for (int tt = 0; tt < GT; ++tt) {
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r) {
+                int o = obase + threadIdx.x + r * 256;
+                if (o < nout) {
+                    int i = o / mb, j = o - (o / mb) * mb;
+                    double2 a = As[tt * ma + i], b = Bs[tt * mb + j];
+                    acc[r].x = fma(a.x, b.x, fma(a.y, b.y, acc[r].x));
+                    acc[r].y = fma(a.x, b.y, fma(-a.y, b.x, acc[r].y));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    double2 *out = part + ((size_t)prob * nsplit + split) * nout;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+        int o = obase + threadIdx.x + r * 256;
+        if (o < nout) out[o] = acc[r];
+    }
+}
+
+__global__ void gram_reduce_kernel(const double2 *part, int nsplit, int ma, int mb, double2 *G) {
+    const int prob = blockIdx.x;
+    const int nout = ma * mb;
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int sp = 0; sp < nsplit; ++sp) s = s + part[((size_t)prob * nsplit + sp) * nout + o];
+        int i = o / mb, j = o % mb;
+        G[(size_t)prob * LD * LD + i * LD + j] = s;
+    }
+}
+
+// C_j = beta C_j + alpha sum_i A_i Y[i][j]   (Y per problem, leading dim LD)
+__global__ void __launch_bounds__(256) combine_kernel(const EigK *ks, int nch, VSet A, VSet C,
+                                                      const double2 *Y, double alpha, double beta) {
+    const int prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= d.nvec) return;
+    const int ma = A.count(), mc = C.count();
+    const double2 *y = Y + (size_t)prob * LD * LD;
+    for (int j0 = 0; j0 < mc; j0 += 8) {
+        double2 acc[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[jj] = make_double2(0.0, 0.0);
+        for (int i = 0; i < ma; ++i) {
+            double2 a = d.base[(long long)A.at(i, ch) * d.nvec + t];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+                if (j0 + jj < mc) cfma(acc[jj], a, __ldg(&y[i * LD + j0 + jj]));
+        }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            if (j0 + jj >= mc) break;
+            double2 *c = d.base + (long long)C.at(j0 + jj, ch) * d.nvec + t;
+            double2 v = rscale(alpha, acc[jj]);
+            *c = beta == 0.0 ? v : rscale(beta, *c) + v;
+        }
+    }
+}
+
+// dst_i = src_i for index sets (FP64 -> FP64), or into / out of the FP32 stage
+__global__ void copy_kernel(const EigK *ks, int nch, VSet S, VSet D, int mode) {
+    // mode 0: base -> base; 1: base -> stage (to float); 2: stage -> base (to double)
+    const int prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const int m = S.count();
+    const long long total = (long long)m * d.nvec;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(e / d.nvec);
+        long long t = e - (long long)i * d.nvec;
+        long long si = (long long)S.at(i, ch) * d.nvec + t, di = (long long)D.at(i, ch) * d.nvec + t;
+        if (mode == 0) d.base[di] = d.base[si];
+        else if (mode == 1) d.stage[di] = make_float2((float)d.base[si].x, (float)d.base[si].y);
+        else d.base[di] = make_double2((double)d.stage[si].x, (double)d.stage[si].y);
+    }
+}
+
+// W_ch = H_src - theta_ch S_src   (per-(k, ch) source indices)
+__global__ void krylov_residual_kernel(const EigK *ks, int nch, const int *srcH, const int *srcS,
+                                       const double *theta, int dst) {
+    const int prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const double th = theta[prob];
+    const double2 *h = d.base + (long long)srcH[prob] * d.nvec;
+    const double2 *s = d.base + (long long)srcS[prob] * d.nvec;
+    double2 *w = d.base + (long long)(dst + ch) * d.nvec;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.nvec;
+         t += (long long)gridDim.x * blockDim.x)
+        w[t] = h[t] - rscale(th, s[t]);
+}
+
+// R_i = HX_i - eps_i SX_i into dst
+__global__ void residual_kernel(const EigK *ks, int M, int oX, int oHX, int oSX, int dst, const double *eps) {
+    const int k = blockIdx.y;
+    const EigK d = ks[k];
+    const long long total = (long long)M * d.nvec;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(e / d.nvec);
+        long long t = e - (long long)i * d.nvec;
+        double ev = eps[k * M + i];
+        d.base[(long long)(dst + i) * d.nvec + t] =
+            d.base[(long long)(oHX + i) * d.nvec + t] - rscale(ev, d.base[(long long)(oSX + i) * d.nvec + t]);
+    }
+    (void)oX;
+}
+
+// out[prob*m + i] = Re <A_i, B_i>   (block reduction with warp shuffles)
+__global__ void coldot_kernel(const EigK *ks, int nch, VSet A, VSet B, double *out) {
+    const int i = blockIdx.x, prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const double2 *a = d.base + (long long)A.at(i, ch) * d.nvec;
+    const double2 *b = d.base + (long long)B.at(i, ch) * d.nvec;
+    double s = 0.0;
+    for (long long t = threadIdx.x; t < d.nvec; t += blockDim.x) s = fma(a[t].x, b[t].x, fma(a[t].y, b[t].y, s));
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (threadIdx.x == 0) out[(size_t)prob * A.count() + i] = s;
+    }
+}
+
+// new Krylov vector: K = W / ||W||_S, SK = SW / ||W||_S, HK slot cleared;
+// a norm below the breakdown threshold marks the slot dead (zero vector).
+__global__ void normalize_kernel(const EigK *ks, int nch, int oW, int oSW, int kV, int kS, int cs,
+                                 int slot, const double *nrm2, int *alive, int kd) {
+    const int prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const double n2 = nrm2[prob];
+    const bool ok = n2 > 1e-24;
+    const double inv = ok ? 1.0 / sqrt(n2) : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) alive[prob * kd + slot] = ok ? 1 : 0;
+    const double2 *w = d.base + (long long)(oW + ch) * d.nvec;
+    const double2 *sw = d.base + (long long)(oSW + ch) * d.nvec;
+    double2 *kv = d.base + (long long)(kV + ch * cs + slot) * d.nvec;
+    double2 *ksv = d.base + (long long)(kS + ch * cs + slot) * d.nvec;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.nvec;
+         t += (long long)gridDim.x * blockDim.x) {
+        kv[t] = rscale(inv, w[t]);
+        ksv[t] = rscale(inv, sw[t]);
+    }
+}
+
+// residual norms and seeds: res[k*M + i] = sqrt(max(0, dot)); seed = argmax over a range
+__global__ void seed_kernel(const double *dots, int M, int mconv, int nk, int nch, int bsize, double *res,
+                            const double *eps, int *seed, double *theta, int *srcH, int *srcS,
+                            int oHX, int oSX) {
+    const int prob = blockIdx.x * blockDim.x + threadIdx.x;
+    if (prob >= nk * nch) return;
+    const int k = prob / nch, ch = prob % nch;
+    if (ch == 0)
+        for (int i = 0; i < M; ++i) res[k * M + i] = sqrt(fmax(0.0, dots[k * M + i]));
+    int lo = nch == 1 ? 0 : ch * bsize, hi = nch == 1 ? mconv : min(M, lo + bsize);
+    int best = lo;
+    double bv = -1.0;
+    for (int i = lo; i < hi; ++i) {
+        double v = sqrt(fmax(0.0, dots[k * M + i]));
+        if (v > bv) { bv = v; best = i; }
+    }
+    seed[prob] = best;
+    theta[prob] = eps[k * M + best];
+    srcH[prob] = oHX + best;
+    srcS[prob] = oSX + best;
+}
+
+// ---------------------------------------------------------------------------
+// Jacobi diagonalization of one Hermitian m x m matrix per CTA (m <= JMAX),
+// parallel (round-robin) ordering: m'/2 disjoint rotations per round.
+// VS: the eigenvector matrix lives in shared memory beside A (m <= 84);
+// otherwise it overwrites the input matrix G in global memory (m <= JMAX).
+template <bool VS>
+__global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const int *dead, int dead_stride,
+                                                     int dead_ofs, double *evals, double2 *evecs,
+                                                     int max_sweeps, double rel_tol) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int prob = blockIdx.x;
+    double2 *A = reinterpret_cast<double2 *>(sm);
+    double2 *V = VS ? A + m * m : G + (size_t)prob * LD * LD;
+    const int ldv = VS ? m : LD;
+    double *rc = reinterpret_cast<double *>(A + (VS ? 2 : 1) * m * m);   // per pair: c, s, t*|apq|, app, aqq
+    double2 *re = reinterpret_cast<double2 *>(rc + 5 * JPAIRS);         // per pair: phase e
+    int *pp = reinterpret_cast<int *>(re + JPAIRS);                      // per pair: p, q
+    __shared__ double red[32];
+    __shared__ int stop;
+    const double2 *g = G + (size_t)prob * LD * LD;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int i = e / m, j = e % m;
+        double2 a = g[i * LD + j], b = g[j * LD + i];
+        double2 v = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));   // (A + A^H)/2
+        if (i == j) v.y = 0.0;
+        bool di = dead && dead[prob * dead_stride + i] == 0 && i >= dead_ofs;
+        bool dj = dead && dead[prob * dead_stride + j] == 0 && j >= dead_ofs;
+        if (di || dj) v = make_double2((i == j) ? 1e30 : 0.0, 0.0);
+        A[e] = v;
+    }
+    __syncthreads();   // G is read completely before V (possibly G itself) is initialised
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int i = e / m, j = e % m;
+        V[i * ldv + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    // Frobenius norm of the live part for the stopping rule
+    double f = 0.0;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        double2 a = A[e];
+        if (fabs(a.x) < 1e29) f += a.x * a.x + a.y * a.y;
+    }
+    for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        red[0] = s;
+    }
+    __syncthreads();
+    const double fro2 = red[0];
+    __syncthreads();
+    const int mp = (m + 1) & ~1;      // players, padded to even
+    const int npair = mp / 2;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        for (int r = 0; r < mp - 1; ++r) {
+            for (int pi = threadIdx.x; pi < npair; pi += blockDim.x) {
+                int a = pi == 0 ? 0 : ((r + pi - 1) % (mp - 1)) + 1;
+                int b = ((r + mp - 1 - pi - 1) % (mp - 1)) + 1;
+                if (pi == 0) b = ((r + mp - 2) % (mp - 1)) + 1;
+                int p = min(a, b), q = max(a, b);
+                double c = 1.0, s = 0.0, tm = 0.0;
+                double2 ep = make_double2(1.0, 0.0);
+                if (q < m) {
+                    double2 apq = A[p * m + q];
+                    double mag = hypot(apq.x, apq.y);
+                    double app = A[p * m + p].x, aqq = A[q * m + q].x;
+                    rc[5 * pi + 3] = app;
+                    rc[5 * pi + 4] = aqq;
+                    if (mag > 0.0) {
+                        ep = make_double2(apq.x / mag, apq.y / mag);
+                        double th = (aqq - app) / (2.0 * mag);
+                        double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        s = t * c;
+                        tm = t * mag;
+                    }
+                } else {
+                    p = q = -1;
+                }
+                pp[2 * pi] = p;
+                pp[2 * pi + 1] = q;
+                rc[5 * pi] = c;
+                rc[5 * pi + 1] = s;
+                rc[5 * pi + 2] = tm;
+                re[pi] = ep;
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J;  J = diag(1, e^-i phi) [[c, s], [-s, c]]
+            for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
+                int pi = e / m, row = e % m;
+                int p = pp[2 * pi], q = pp[2 * pi + 1];
+                if (p < 0 || rc[5 * pi + 1] == 0.0) continue;
+                double c = rc[5 * pi], s = rc[5 * pi + 1];
+                double2 ec = make_double2(re[pi].x, -re[pi].y);
+                double2 xp = A[row * m + p], xq = cmul(ec, A[row * m + q]);
+                A[row * m + p] = rscale(c, xp) - rscale(s, xq);
+                A[row * m + q] = rscale(s, xp) + rscale(c, xq);
+                double2 vp = V[row * ldv + p], vq = cmul(ec, V[row * ldv + q]);
+                V[row * ldv + p] = rscale(c, vp) - rscale(s, vq);
+                V[row * ldv + q] = rscale(s, vp) + rscale(c, vq);
+            }
+            __syncthreads();
+            // rows: A <- J^H A
+            for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
+                int pi = e / m, col = e % m;
+                int p = pp[2 * pi], q = pp[2 * pi + 1];
+                if (p < 0 || rc[5 * pi + 1] == 0.0) continue;
+                double c = rc[5 * pi], s = rc[5 * pi + 1];
+                double2 yp = A[p * m + col], yq = cmul(re[pi], A[q * m + col]);
+                A[p * m + col] = rscale(c, yp) - rscale(s, yq);
+                A[q * m + col] = rscale(s, yp) + rscale(c, yq);
+            }
+            __syncthreads();
+            for (int pi = threadIdx.x; pi < npair; pi += blockDim.x) {
+                int p = pp[2 * pi], q = pp[2 * pi + 1];
+                if (p < 0 || rc[5 * pi + 1] == 0.0) continue;
+                A[p * m + q] = make_double2(0.0, 0.0);
+                A[q * m + p] = make_double2(0.0, 0.0);
+                A[p * m + p] = make_double2(rc[5 * pi + 3] - rc[5 * pi + 2], 0.0);
+                A[q * m + q] = make_double2(rc[5 * pi + 4] + rc[5 * pi + 2], 0.0);
+            }
+            __syncthreads();
+        }
+        // off-diagonal norm
+        double o = 0.0;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            int i = e / m, j = e % m;
+            if (i != j) o += A[e].x * A[e].x + A[e].y * A[e].y;
+        }
+        for (int off = 16; off > 0; off >>= 1) o += __shfl_down_sync(0xffffffffu, o, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = o;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+            stop = s <= rel_tol * rel_tol * fro2;
+        }
+        __syncthreads();
+        if (stop) break;
+    }
+    // sort ascending (selection sort by one thread on the diagonal)
+    __shared__ int perm[LD];
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < m; ++i) perm[i] = i;
+        for (int i = 0; i < m; ++i) {
+            int b = i;
+            for (int j = i + 1; j < m; ++j)
+                if (A[perm[j] * m + perm[j]].x < A[perm[b] * m + perm[b]].x) b = j;
+            int t = perm[i]; perm[i] = perm[b]; perm[b] = t;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < m; c += blockDim.x) evals[(size_t)prob * LD + c] = A[perm[c] * m + perm[c]].x;
+    double2 *out = evecs + (size_t)prob * LD * LD;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int r = e / m, c = e % m;
+        out[r * LD + c] = V[r * ldv + perm[c]];
+    }
+}
+
+// U = L^{-H} with G = L L^H (G Hermitian positive definite, m <= JMAX).
+// L lives in shared memory; U is written row by row to global memory.
+__global__ void __launch_bounds__(128) cholinv_kernel(const double2 *G, int m, double2 *U, int *status) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    double2 *L = reinterpret_cast<double2 *>(sm);     // m x m, lower
+    const int prob = blockIdx.x;
+    const double2 *g = G + (size_t)prob * LD * LD;
+    double2 *u = U + (size_t)prob * LD * LD;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int i = e / m, j = e % m;
+        L[e] = i >= j ? g[i * LD + j] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    __shared__ double piv;
+    for (int j = 0; j < m; ++j) {
+        if (threadIdx.x == 0) {
+            double d = L[j * m + j].x;
+            if (!(d > 0.0)) {
+                status[prob] = 1;
+                d = 1e-300;
+            }
+            piv = sqrt(d);
+            L[j * m + j] = make_double2(piv, 0.0);
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) L[i * m + j] = rscale(1.0 / piv, L[i * m + j]);
+        __syncthreads();
+        // trailing update: L[i][c] -= L[i][j] conj(L[c][j]) for j < c <= i
+        for (int e = threadIdx.x; e < (m - j - 1) * (m - j - 1); e += blockDim.x) {
+            int i = j + 1 + e / (m - j - 1), c = j + 1 + e % (m - j - 1);
+            if (c > i) continue;
+            double2 lij = L[i * m + j], lcj = L[c * m + j];
+            L[i * m + c] = L[i * m + c] - cmul_c(lij, lcj);
+        }
+        __syncthreads();
+    }
+    // column c of Z = L^{-1} by forward substitution (one thread per column);
+    // U[c][i] = conj(Z[i][c]), and Z[q][c] is read back as conj(U[c][q])
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        for (int i = 0; i < c; ++i) u[c * LD + i] = make_double2(0.0, 0.0);
+        for (int i = c; i < m; ++i) {
+            double2 acc = make_double2(i == c ? 1.0 : 0.0, 0.0);
+            for (int q = c; q < i; ++q) {
+                double2 uq = u[c * LD + q];
+                acc = acc - cmul(L[i * m + q], make_double2(uq.x, -uq.y));
+            }
+            double2 z = rscale(1.0 / L[i * m + i].x, acc);
+            u[c * LD + i] = make_double2(z.x, -z.y);
+        }
+    }
+}
+
+// Maximum-overlap selection of bsz Ritz pairs in a block (+ new roots).
+__global__ void select_kernel(const double *evals, const double2 *evecs, int mB, int b, int M, int nblk,
+                              int nprob, double *eps, double2 *Ysel) {
+    const int prob = blockIdx.x * blockDim.x + threadIdx.x;
+    if (prob >= nprob) return;
+    const int k = prob / nblk, blk = prob % nblk;
+    const int lo = blk * b, bsz = min(b, M - lo);
+    const double *w = evals + (size_t)prob * LD;
+    const double2 *Y = evecs + (size_t)prob * LD * LD;
+    double ov[LD];
+    int chosen[LD];
+    bool used[LD];
+    for (int l = 0; l < mB; ++l) {
+        double s = 0.0;
+        for (int i = 0; i < bsz; ++i) s += Y[i * LD + l].x * Y[i * LD + l].x + Y[i * LD + l].y * Y[i * LD + l].y;
+        ov[l] = s;
+        used[l] = false;
+    }
+    for (int c = 0; c < bsz; ++c) {     // stable top-bsz by overlap
+        int best = -1;
+        for (int l = 0; l < mB; ++l)
+            if (!used[l] && (best < 0 || ov[l] > ov[best])) best = l;
+        chosen[c] = best;
+        used[best] = true;
+    }
+    double lowest_in = 1e300;
+    for (int i = 0; i < bsz; ++i) lowest_in = fmin(lowest_in, eps[k * M + lo + i]);
+    for (int l = 0; l < mB; ++l) {
+        if (used[l]) continue;
+        if (w[l] < lowest_in && ov[l] < 0.5) {
+            int worst = 0;
+            for (int c = 1; c < bsz; ++c)
+                if (w[chosen[c]] > w[chosen[worst]]) worst = c;
+            if (w[l] < w[chosen[worst]]) {
+                used[chosen[worst]] = false;
+                chosen[worst] = l;
+                used[l] = true;
+            }
+        }
+    }
+    for (int i = 1; i < bsz; ++i) {     // sort chosen by Ritz value
+        int x = chosen[i], j = i - 1;
+        while (j >= 0 && w[chosen[j]] > w[x]) { chosen[j + 1] = chosen[j]; --j; }
+        chosen[j + 1] = x;
+    }
+    double2 *ys = Ysel + (size_t)prob * LD * LD;
+    for (int c = 0; c < bsz; ++c) {
+        for (int r = 0; r < mB; ++r) ys[r * LD + c] = Y[r * LD + chosen[c]];
+        eps[k * M + lo + c] = w[chosen[c]];
+    }
+}
+
+__global__ void take_evals_kernel(const double *evals, int M, int nk, double *eps) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < M * nk) eps[e] = evals[(size_t)(e / M) * LD + (e % M)];
+}
+
+// banded S and banded solves on vector ranges of every k-point (FP64)
+__global__ void eig_banded_S_kernel(const EigK *ks, const double *Sband, int order, int nb, int src, int dst, int nv) {
+    const int k = blockIdx.z, v = blockIdx.y;
+    const EigK d = ks[k];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= d.ldg || v >= nv) return;
+    const int K = order, W = 2 * K - 1;
+    const double2 *x = d.base + (long long)(src + v) * d.nvec;
+    double2 *y = d.base + (long long)(dst + v) * d.nvec;
+    for (int j = 0; j < nb; ++j) {
+        double2 s = make_double2(0.0, 0.0);
+        if (g < d.ng)
+            for (int dd = 0; dd < W; ++dd) {
+                int jj = j + dd - (K - 1);
+                if (jj >= 0 && jj < nb) rfma(s, Sband[(size_t)j * W + dd], x[(size_t)jj * d.ldg + g]);
+            }
+        y[(size_t)j * d.ldg + g] = s;
+    }
+}
+
+__global__ void eig_banded_solve_kernel(const EigK *ks, const double *Lb, int per_g, int order, int nb,
+                                        int src, int dst, int nv) {
+    const int k = blockIdx.z, v = blockIdx.y;
+    const EigK d = ks[k];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= d.ldg || v >= nv) return;
+    const int K = order;
+    const double *L = per_g ? d.pfac + (size_t)g * nb * K : Lb;
+    const double2 *x = d.base + (long long)(src + v) * d.nvec;
+    double2 *y = d.base + (long long)(dst + v) * d.nvec;
+    if (g >= d.ng) {
+        for (int j = 0; j < nb; ++j) y[(size_t)j * d.ldg + g] = make_double2(0.0, 0.0);
+        return;
+    }
+    for (int j = 0; j < nb; ++j) {
+        double2 s = x[(size_t)j * d.ldg + g];
+        for (int dd = 1; dd < K && dd <= j; ++dd) rfma(s, -L[(size_t)j * K + dd], y[(size_t)(j - dd) * d.ldg + g]);
+        y[(size_t)j * d.ldg + g] = rscale(1.0 / L[(size_t)j * K], s);
+    }
+    for (int j = nb - 1; j >= 0; --j) {
+        double2 s = y[(size_t)j * d.ldg + g];
+        for (int dd = 1; dd < K && j + dd < nb; ++dd)
+            rfma(s, -L[(size_t)(j + dd) * K + dd], y[(size_t)(j + dd) * d.ldg + g]);
+        y[(size_t)j * d.ldg + g] = rscale(1.0 / L[(size_t)j * K], s);
+    }
+}
+
+// dead-slot mask of a subspace: columns < ofs are the block's inputs (the
+// first bsz live), columns >= ofs are Krylov slots with their alive flags
+__global__ void alive_mask_kernel(const int *alive, int kd, int ofs, int M, int b, int nch, int m,
+                                  int nprob, int *mask) {
+    const int prob = blockIdx.x * blockDim.x + threadIdx.x;
+    if (prob >= nprob) return;
+    const int ch = prob % nch;
+    const int bsz = nch == 1 ? M : min(b, M - ch * b);
+    for (int c = 0; c < m; ++c)
+        mask[prob * LD + c] = c < ofs ? (c < bsz ? 1 : 0) : alive[prob * kd + (c - ofs)];
+}
+
+__global__ void fill_int_kernel(int *p, int n, int v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+__global__ void set_src_kernel(int *srcH, int *srcS, int nprob, int nch, int kH, int kS, int cs, int slot) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nprob) return;
+    srcH[p] = kH + (p % nch) * cs + slot;
+    srcS[p] = kS + (p % nch) * cs + slot;
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+#define MB_LAUNCH_E(kid, ...)            \
+    do {                                 \
+        if (rc) break;                   \
+        cudaEvent_t ev_;                 \
+        prof_begin(h, s, kid, &ev_);     \
+        __VA_ARGS__;                     \
+        prof_end(h, s, kid, ev_);        \
+        launched();                      \
+    } while (0)
+
+namespace {
+
+// real symmetric Jacobi (host, small): z-modes of the initial guess
+void host_jacobi_sym(int n, std::vector<double> &A, std::vector<double> &w, std::vector<double> &V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                tot += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+                if (i != j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                double th = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2 * apq);
+                double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1));
+                double c = 1 / std::sqrt(t * t + 1), s = t * c;
+                for (int r = 0; r < n; ++r) {
+                    double xp = A[(size_t)r * n + p], xq = A[(size_t)r * n + q];
+                    A[(size_t)r * n + p] = c * xp - s * xq;
+                    A[(size_t)r * n + q] = s * xp + c * xq;
+                }
+                for (int r = 0; r < n; ++r) {
+                    double xp = A[(size_t)p * n + r], xq = A[(size_t)q * n + r];
+                    A[(size_t)p * n + r] = c * xp - s * xq;
+                    A[(size_t)q * n + r] = s * xp + c * xq;
+                }
+                for (int r = 0; r < n; ++r) {
+                    double vp = V[(size_t)r * n + p], vq = V[(size_t)r * n + q];
+                    V[(size_t)r * n + p] = c * vp - s * vq;
+                    V[(size_t)r * n + q] = s * vp + c * vq;
+                }
+            }
+    }
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
+}
+
+// Lowest M free-electron states (|k+G|^2/2 + z-mode n): pure plane wave times
+// an S-normalized eigenvector of (D/2) c = e S c.  S-orthonormal by construction.
+void free_electron_start(const mb_handle *h, int ik, int M, std::vector<double2> &X) {
+    const int nb = h->nb, K = h->order, W = 2 * K - 1;
+    const KPoint &kp = h->kp[ik];
+    // dense L^{-1} (D/2) L^{-T} with S = L L^T
+    std::vector<double> L((size_t)nb * nb, 0.0), D((size_t)nb * nb, 0.0);
+    for (int j = 0; j < nb; ++j)
+        for (int d = 0; d < K && j - d >= 0; ++d) L[(size_t)j * nb + (j - d)] = h->Lb[(size_t)j * K + d];
+    for (int j = 0; j < nb; ++j)
+        for (int dd = 0; dd < W; ++dd) {
+            int jj = j + dd - (K - 1);
+            if (jj >= 0 && jj < nb) D[(size_t)j * nb + jj] = 0.5 * h->Db[(size_t)j * W + dd];
+        }
+    // Linv by forward substitution
+    std::vector<double> Li((size_t)nb * nb, 0.0);
+    for (int c = 0; c < nb; ++c)
+        for (int i = c; i < nb; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int q = c; q < i; ++q) s -= L[(size_t)i * nb + q] * Li[(size_t)q * nb + c];
+            Li[(size_t)i * nb + c] = s / L[(size_t)i * nb + i];
+        }
+    std::vector<double> T1((size_t)nb * nb, 0.0), A((size_t)nb * nb, 0.0);
+    for (int i = 0; i < nb; ++i)
+        for (int j = 0; j < nb; ++j) {
+            double s = 0;
+            for (int q = 0; q < nb; ++q) s += Li[(size_t)i * nb + q] * D[(size_t)q * nb + j];
+            T1[(size_t)i * nb + j] = s;
+        }
+    for (int i = 0; i < nb; ++i)
+        for (int j = 0; j < nb; ++j) {
+            double s = 0;
+            for (int q = 0; q < nb; ++q) s += T1[(size_t)i * nb + q] * Li[(size_t)j * nb + q];
+            A[(size_t)i * nb + j] = s;
+        }
+    std::vector<double> w, V;
+    host_jacobi_sym(nb, A, w, V);
+    std::vector<int> ord(nb);
+    for (int i = 0; i < nb; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return w[a] < w[b]; });
+    // candidate (energy, g, mode)
+    std::vector<std::tuple<double, int, int>> cand;
+    int nmode = std::min(nb, M);
+    for (int g = 0; g < kp.ng; ++g)
+        for (int n = 0; n < nmode; ++n) cand.emplace_back(0.5 * kp.q2[g] + w[ord[n]], g, n);
+    std::sort(cand.begin(), cand.end());
+    X.assign((size_t)M * nb * kp.ldg, make_double2(0.0, 0.0));
+    for (int c = 0; c < M; ++c) {
+        int g = std::get<1>(cand[c]), n = ord[std::get<2>(cand[c])];
+        for (int j = 0; j < nb; ++j) {   // c_z = L^{-T} y
+            double s = 0;
+            for (int q = j; q < nb; ++q) s += Li[(size_t)q * nb + j] * V[(size_t)q * nb + n];
+            X[((size_t)c * nb + j) * kp.ldg + g] = make_double2(s, 0.0);
+        }
+    }
+}
+
+struct Solver {
+    mb_handle *h;
+    cudaStream_t s;
+    int nk, M, kd, b, nblk, mA, mB, nc;
+    int Mconv;          // roots tested for convergence and returned (M includes guards)
+    int prec;
+    int oV, oHV, oSV, oVB, oHVB, oSVB, oQ, oHQ, oW, oSW, oT;
+    int nvecs;
+    std::vector<EigK> kd_host;
+    EigK *d_k = nullptr;
+    std::vector<void *> allocs;
+    double2 *d_G = nullptr, *d_part = nullptr, *d_Y = nullptr, *d_Ysel = nullptr;
+    double *d_evals = nullptr, *d_eps = nullptr, *d_res = nullptr, *d_dots = nullptr, *d_theta = nullptr;
+    int *d_seed = nullptr, *d_srcH = nullptr, *d_srcS = nullptr, *d_alive = nullptr, *d_status = nullptr;
+    int *d_mask = nullptr;
+    size_t part_cap = 0;
+    long long nmax = 0;
+    int maxldg = 0;
+    int applies = 0;
+    int rc = MB_OK;
+
+    ~Solver() {
+        for (void *p : allocs) cudaFree(p);
+    }
+    int cuda(cudaError_t e) {
+        if (e != cudaSuccess && rc == MB_OK) rc = cuda_fail(h, e);
+        return rc;
+    }
+    int launched() { return cuda(cudaGetLastError()); }
+    template <typename T> T *alloc(size_t n) {
+        void *p = nullptr;
+        if (rc) return nullptr;
+        if (cuda(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)))) return nullptr;
+        allocs.push_back(p);
+        return reinterpret_cast<T *>(p);
+    }
+
+    void gram(int nch, VSet A, VSet B, double2 *G) {
+        int nprob = nk * nch;
+        int ma = A.count(), mbc = B.count();
+        int nsplit = std::max(1, std::min(64, (2 * h->num_sms + nprob - 1) / nprob));
+        while ((size_t)nprob * nsplit * ma * mbc > part_cap && nsplit > 1) --nsplit;
+        size_t smem = (size_t)GT * (ma + mbc) * sizeof(double2);
+        const int otiles = (ma * mbc + 36 * 256 - 1) / (36 * 256);
+        if (smem > 48 * 1024)
+            cuda(cudaFuncSetAttribute(gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MB_LAUNCH_E(KN_GRAM, gram_partial_kernel<<<dim3(nsplit, nprob, otiles), 256, smem, s>>>(d_k, nch, A, B, nsplit, d_part));
+        MB_LAUNCH_E(KN_GRAM, gram_reduce_kernel<<<nprob, 256, 0, s>>>(d_part, nsplit, ma, mbc, G));
+    }
+    void combine(int nch, VSet A, VSet C, const double2 *Y, double alpha, double beta) {
+        MB_LAUNCH_E(KN_COMBINE, combine_kernel<<<dim3((unsigned)((nmax + 255) / 256), nk * nch), 256, 0, s>>>(
+                                    d_k, nch, A, C, Y, alpha, beta));
+    }
+    void copy(int nch, VSet S, VSet D, int mode) {
+        MB_LAUNCH_E(KN_VEC, copy_kernel<<<dim3(256, nk * nch), 256, 0, s>>>(d_k, nch, S, D, mode));
+    }
+    void bandS(int src, int dst, int nv) {
+        MB_LAUNCH_E(KN_BANDED, eig_banded_S_kernel<<<dim3((maxldg + 127) / 128, nv, nk), 128, 0, s>>>(
+                                   d_k, (const double *)h->t64.Sband, h->order, h->nb, src, dst, nv));
+    }
+    void bandSolve(int per_g, int src, int dst, int nv) {
+        MB_LAUNCH_E(KN_BANDED, eig_banded_solve_kernel<<<dim3((maxldg + 127) / 128, nv, nk), 128, 0, s>>>(
+                                   d_k, (const double *)h->t64.Lband, per_g, h->order, h->nb, src, dst, nv));
+    }
+    int nc_stage() const { return std::max(M, nc); }
+    void applyH(int src, int dst, int nv, int p) {
+        if (rc) return;
+        std::vector<int> iks(nk);
+        std::vector<const void *> xs(nk);
+        std::vector<void *> ys(nk);
+        for (int k = 0; k < nk; ++k) {
+            iks[k] = k;
+            if (p == MB_FP64) {
+                xs[k] = kd_host[k].base + (long long)src * kd_host[k].nvec;
+                ys[k] = kd_host[k].base + (long long)dst * kd_host[k].nvec;
+            } else {
+                xs[k] = kd_host[k].stage;
+                ys[k] = kd_host[k].stage + (long long)nc_stage() * kd_host[k].nvec;
+            }
+        }
+        if (p != MB_FP64) copy(1, vs(src, nv), vs(0, nv), 1);
+        if (rc) return;
+        int r = apply_H_batch(h, nk, iks.data(), xs.data(), ys.data(), nv, p, s);
+        if (r && rc == MB_OK) rc = r;
+        if (p != MB_FP64) copy(1, vs(nc_stage(), nv), vs(dst, nv), 2);
+        applies += nv * nk;
+    }
+    void residuals_and_seeds(int nch) {
+        MB_LAUNCH_E(KN_VEC, residual_kernel<<<dim3(256, nk), 256, 0, s>>>(d_k, M, oV, oHV, oSV, oT, d_eps));
+        bandSolve(0, oT, oT + M, M);
+        MB_LAUNCH_E(KN_SMALL, coldot_kernel<<<dim3(M, nk), 256, 0, s>>>(d_k, 1, vs(oT, M), vs(oT + M, M), d_dots));
+        int np = nk * nch;
+        MB_LAUNCH_E(KN_SMALL, seed_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_dots, M, Mconv, nk, nch, b, d_res, d_eps, d_seed,
+                                                                        d_theta, d_srcH, d_srcS, oHV, oSV));
+    }
+    void applyH_chain(int nch, int slot, int kH, int cs) {
+        applyH(oQ, oHQ, nch, prec);
+        copy(nch, vs(oHQ, 1, 1), vs(kH + slot, 1, cs), 0);
+    }
+    void krylov(int nch, int kV, int kS, int kH, int cs) {
+        int np = nk * nch;
+        MB_LAUNCH_E(KN_SMALL, fill_int_kernel<<<(np * kd + 127) / 128, 128, 0, s>>>(d_alive, np * kd, 1));
+        for (int i = 0; i < kd && !rc; ++i) {
+            if (i > 0) {
+                copy(nch, vs(kV + i - 1, 1, cs), vs(oQ, 1, 1), 0);
+                applyH_chain(nch, i - 1, kH, cs);
+                MB_LAUNCH_E(KN_SMALL, set_src_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_srcH, d_srcS, np, nch, kH, kS, cs, i - 1));
+            }
+            MB_LAUNCH_E(KN_VEC, krylov_residual_kernel<<<dim3((unsigned)std::min<long long>(1024, (nmax + 255) / 256), np), 256, 0, s>>>(
+                                    d_k, nch, d_srcH, d_srcS, d_theta, oW));
+            bandSolve(1, oW, oW, nch);
+            for (int pass = 0; pass < 2; ++pass) {
+                VSet Sset = vs(oSV, M, 0, kS, i, cs), Vset = vs(oV, M, 0, kV, i, cs);
+                gram(nch, Sset, vs(oW, 1, 1), d_G);
+                combine(nch, Vset, vs(oW, 1, 1), d_G, -1.0, 1.0);
+            }
+            bandS(oW, oSW, nch);
+            MB_LAUNCH_E(KN_SMALL, coldot_kernel<<<dim3(1, np), 256, 0, s>>>(d_k, nch, vs(oW, 1, 1), vs(oSW, 1, 1), d_dots));
+            MB_LAUNCH_E(KN_VEC, normalize_kernel<<<dim3(128, np), 256, 0, s>>>(d_k, nch, oW, oSW, kV, kS, cs, i,
+                                                                               d_dots, d_alive, kd));
+        }
+        copy(nch, vs(kV + kd - 1, 1, cs), vs(oQ, 1, 1), 0);
+        applyH_chain(nch, kd - 1, kH, cs);
+    }
+    void jacobi(int nch, int m, bool masked, int ofs) {
+        const size_t extra = 5 * JPAIRS * sizeof(double) + JPAIRS * sizeof(double2) + 2 * JPAIRS * sizeof(int);
+        const size_t stat = 32 * sizeof(double) + sizeof(int) + LD * sizeof(int) + 256;
+        size_t smem2 = (size_t)2 * m * m * sizeof(double2) + extra;
+        size_t smem1 = (size_t)m * m * sizeof(double2) + extra;
+        const bool vs = smem2 + stat <= (size_t)h->smem_optin;
+        int np = nk * nch;
+        if (masked)
+            MB_LAUNCH_E(KN_SMALL, alive_mask_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_alive, kd, ofs, M, b, nch, m, np, d_mask));
+        if (vs) {
+            cuda(cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+            MB_LAUNCH_E(KN_JACOBI, jacobi_kernel<true><<<np, 256, smem2, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
+                                                                              d_evals, d_Y, 40, 1e-15));
+        } else {
+            cuda(cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+            MB_LAUNCH_E(KN_JACOBI, jacobi_kernel<false><<<np, 256, smem1, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
+                                                                               d_evals, d_Y, 40, 1e-15));
+        }
+    }
+    void rotate_set(const double2 *Y, int m) {   // X, HX, SX <- [V|..](m) Y[:, :M]
+        combine(1, vs(oV, m), vs(oT, M), Y, 1.0, 0.0);
+        combine(1, vs(oHV, m), vs(oT + M, M), Y, 1.0, 0.0);
+        combine(1, vs(oSV, m), vs(oT + 2 * M, M), Y, 1.0, 0.0);
+        copy(1, vs(oT, M), vs(oV, M), 0);
+        copy(1, vs(oT + M, M), vs(oHV, M), 0);
+        copy(1, vs(oT + 2 * M, M), vs(oSV, M), 0);
+    }
+    void rr_full(bool withK) {
+        int m = withK ? mA : M;
+        gram(1, vs(oV, m), vs(oHV, m), d_G);
+        jacobi(1, m, withK, M);
+        rotate_set(d_Y, m);
+        MB_LAUNCH_E(KN_SMALL, take_evals_kernel<<<(M * nk + 127) / 128, 128, 0, s>>>(d_evals, M, nk, d_eps));
+    }
+    void cholqr() {
+        for (int pass = 0; pass < 2; ++pass) {
+            gram(1, vs(oV, M), vs(oSV, M), d_G);
+            size_t smem = (size_t)M * M * sizeof(double2);
+            cuda(cudaFuncSetAttribute(cholinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            MB_LAUNCH_E(KN_SMALL, cholinv_kernel<<<nk, 128, smem, s>>>(d_G, M, d_Y, d_status));
+            rotate_set(d_Y, M);
+        }
+    }
+    void cycle_B() {
+        residuals_and_seeds(nblk);
+        copy(nblk, vs(oV, b, b), vs(oVB, b, mB), 0);
+        copy(nblk, vs(oHV, b, b), vs(oHVB, b, mB), 0);
+        copy(nblk, vs(oSV, b, b), vs(oSVB, b, mB), 0);
+        krylov(nblk, oVB + b, oSVB + b, oHVB + b, mB);
+        gram(nblk, vs(oVB, mB, mB), vs(oHVB, mB, mB), d_G);
+        jacobi(nblk, mB, true, b);
+        int np = nk * nblk;
+        MB_LAUNCH_E(KN_SMALL, select_kernel<<<(np + 31) / 32, 32, 0, s>>>(d_evals, d_Y, mB, b, M, nblk, np, d_eps, d_Ysel));
+        combine(nblk, vs(oVB, mB, mB), vs(oV, b, b), d_Ysel, 1.0, 0.0);
+        combine(nblk, vs(oHVB, mB, mB), vs(oHV, b, b), d_Ysel, 1.0, 0.0);
+        combine(nblk, vs(oSVB, mB, mB), vs(oSV, b, b), d_Ysel, 1.0, 0.0);
+    }
+};
+
+}  // namespace
+
+int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void *evecs,
+             const mb_solve_opts *so, mb_solve_info *info, cudaStream_t s) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!evals || nbands < 1 || !(tol > 0.0)) return MB_EINVAL;
+    if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return MB_EINVAL;
+    Solver S;
+    S.h = h;
+    S.s = s;
+    S.nk = (int)h->kp.size();
+    int guard = so && so->guard != 0 ? std::max(0, so->guard) : std::max(2, (nbands + 7) / 8);
+    S.Mconv = nbands;
+    S.M = nbands + guard;
+    S.kd = so && so->krylov_depth > 0 ? so->krylov_depth : 4;
+    S.b = so && so->block > 0 ? so->block : 4;
+    int max_cycles = so && so->max_cycles > 0 ? so->max_cycles : 200;
+    if (S.b > S.M) S.b = S.M;
+    S.nblk = (S.M + S.b - 1) / S.b;
+    S.mA = S.M + S.kd;
+    S.mB = S.b + S.kd;
+    S.nc = std::max(1, S.nblk);
+    if (S.mA > JMAX || S.mB > JMAX || S.M > LD) return MB_EUNSUPPORTED;
+    if (S.nc_stage() > h->max_bands) return MB_EUNSUPPORTED;
+    for (auto &k : h->kp)
+        if ((long long)k.ng * h->nb < S.mA) return MB_EINVAL;
+    if (cudaSetDevice(h->device) != cudaSuccess) return MB_ECUDA;
+    int rc = ensure_precond(h);
+    if (rc) return rc;
+    // vector regions
+    // [X | K_A] regions are sized so that the last block of cycle B, when M is
+    // not a multiple of b, writes its unused columns into K_A (scratch then)
+    const int mAr = std::max(S.mA, S.nblk * S.b);
+    S.oV = 0;
+    S.oHV = mAr;
+    S.oSV = 2 * mAr;
+    S.oVB = 3 * mAr;
+    S.oHVB = S.oVB + S.nblk * S.mB;
+    S.oSVB = S.oHVB + S.nblk * S.mB;
+    S.oQ = S.oSVB + S.nblk * S.mB;
+    S.oHQ = S.oQ + S.nc;
+    S.oW = S.oHQ + S.nc;
+    S.oSW = S.oW + S.nc;
+    S.oT = S.oSW + S.nc;
+    S.nvecs = S.oT + 3 * S.mA;
+    // per-k memory
+    S.kd_host.resize(S.nk);
+    size_t pofs = 0;
+    for (int k = 0; k < S.nk; ++k) {
+        EigK &e = S.kd_host[k];
+        e.ldg = h->kp[k].ldg;
+        e.ng = h->kp[k].ng;
+        e.nvec = (long long)h->nb * e.ldg;
+        e.base = S.alloc<double2>((size_t)S.nvecs * e.nvec);
+        e.stage = S.alloc<float2>((size_t)2 * S.nc_stage() * e.nvec);
+        e.pfac = (const double *)h->t64.Pfac + pofs;
+        pofs += (size_t)e.ldg * h->nb * h->order;
+        if (S.rc) return S.rc;
+        S.cuda(cudaMemsetAsync(e.base, 0, sizeof(double2) * (size_t)S.nvecs * e.nvec, s));
+        S.nmax = std::max(S.nmax, e.nvec);
+        S.maxldg = std::max(S.maxldg, e.ldg);
+    }
+    int nprob = S.nk * S.nc;
+    S.d_k = S.alloc<EigK>(S.nk);
+    S.d_G = S.alloc<double2>((size_t)nprob * LD * LD);
+    S.d_Y = S.alloc<double2>((size_t)nprob * LD * LD);
+    S.d_Ysel = S.alloc<double2>((size_t)nprob * LD * LD);
+    S.part_cap = (size_t)std::max(2 * h->num_sms, nprob) * JMAX * JMAX;
+    S.d_part = S.alloc<double2>(S.part_cap);
+    S.d_evals = S.alloc<double>((size_t)nprob * LD);
+    S.d_eps = S.alloc<double>((size_t)S.nk * S.M);
+    S.d_res = S.alloc<double>((size_t)S.nk * S.M);
+    S.d_dots = S.alloc<double>((size_t)S.nk * std::max(S.M, S.nc));
+    S.d_theta = S.alloc<double>(nprob);
+    S.d_seed = S.alloc<int>(nprob);
+    S.d_srcH = S.alloc<int>(nprob);
+    S.d_srcS = S.alloc<int>(nprob);
+    S.d_alive = S.alloc<int>((size_t)nprob * S.kd);
+    S.d_mask = S.alloc<int>((size_t)nprob * LD);
+    S.d_status = S.alloc<int>(S.nk);
+    if (S.rc) return S.rc;
+    S.cuda(cudaMemcpyAsync(S.d_k, S.kd_host.data(), sizeof(EigK) * S.nk, cudaMemcpyHostToDevice, s));
+    S.cuda(cudaMemsetAsync(S.d_Ysel, 0, sizeof(double2) * (size_t)nprob * LD * LD, s));
+    S.cuda(cudaMemsetAsync(S.d_status, 0, sizeof(int) * S.nk, s));
+    // initial trial vectors
+    for (int k = 0; k < S.nk && !S.rc; ++k) {
+        std::vector<double2> X0;
+        free_electron_start(h, k, S.M, X0);
+        S.cuda(cudaMemcpyAsync(S.kd_host[k].base, X0.data(), sizeof(double2) * X0.size(), cudaMemcpyHostToDevice, s));
+        S.cuda(cudaStreamSynchronize(s));
+    }
+    const bool mixed = prec != MB_FP64;
+    S.prec = prec;
+    S.applyH(S.oV, S.oHV, S.M, S.prec);
+    S.bandS(S.oV, S.oSV, S.M);
+    S.rr_full(false);
+    S.residuals_and_seeds(1);
+    std::vector<double> res((size_t)S.nk * S.M);
+    double last = 1e300, prev = 1e300, maxres = 1e300;
+    int cycles = 0;
+    bool converged = false;
+    for (cycles = 1; cycles <= max_cycles && !S.rc; ++cycles) {
+        S.krylov(1, S.oV + S.M, S.oSV + S.M, S.oHV + S.M, 0);      // cycle A
+        S.rr_full(true);
+        S.cycle_B();                                                // cycle B
+        S.cholqr();
+        S.rr_full(false);
+        S.residuals_and_seeds(1);
+        S.cuda(cudaMemcpyAsync(res.data(), S.d_res, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, s));
+        S.cuda(cudaStreamSynchronize(s));
+        if (S.rc) break;
+        auto conv_max = [&]() {
+            double mx = 0.0;
+            for (int k = 0; k < S.nk; ++k)
+                for (int i = 0; i < S.Mconv; ++i) {
+                    double r = res[(size_t)k * S.M + i];
+                    mx = std::max(mx, r == r ? r : 1e300);
+                }
+            return mx;
+        };
+        maxres = conv_max();
+        if (S.prec != MB_FP64) {
+            bool stalled = cycles > 3 && maxres > 0.7 * prev;
+            if (maxres < 30.0 * tol || stalled) {
+                // switch the applies to FP64: fresh HX, SX, Ritz rotation
+                S.prec = MB_FP64;
+                S.applyH(S.oV, S.oHV, S.M, MB_FP64);
+                S.bandS(S.oV, S.oSV, S.M);
+                S.rr_full(false);
+                S.residuals_and_seeds(1);
+                S.cuda(cudaMemcpyAsync(res.data(), S.d_res, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, s));
+                S.cuda(cudaStreamSynchronize(s));
+                maxres = conv_max();
+            }
+        }
+        prev = last;
+        last = maxres;
+        if (S.prec == MB_FP64 && maxres < tol) {
+            converged = true;
+            break;
+        }
+    }
+    (void)mixed;
+    if (S.rc) return S.rc;
+    std::vector<double> eps((size_t)S.nk * S.M);
+    S.cuda(cudaMemcpyAsync(eps.data(), S.d_eps, sizeof(double) * eps.size(), cudaMemcpyDeviceToHost, s));
+    if (evecs) {
+        char *dst = reinterpret_cast<char *>(evecs);
+        for (int k = 0; k < S.nk; ++k) {
+            size_t bytes = sizeof(double2) * (size_t)S.Mconv * S.kd_host[k].nvec;
+            S.cuda(cudaMemcpyAsync(dst, S.kd_host[k].base, bytes, cudaMemcpyDeviceToDevice, s));
+            dst += bytes;
+        }
+    }
+    S.cuda(cudaStreamSynchronize(s));
+    if (S.rc) return S.rc;
+    for (int k = 0; k < S.nk; ++k)
+        std::memcpy(evals + (size_t)k * S.Mconv, eps.data() + (size_t)k * S.M, sizeof(double) * S.Mconv);
+    if (info) {
+        info->cycles = std::min(cycles, max_cycles);
+        info->applies = S.applies;
+        info->max_residual = maxres;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return converged ? MB_OK : MB_ENOTCONV;
+}
+
 }  // namespace mb

@@ -28,6 +28,7 @@ struct KPoint {
 struct DevTables {
     void *Bq = nullptr;      // nq x order, B_{t+m}(z_q) of the full basis
     void *V = nullptr;       // nq x N1 x N2, w_q V / (N1 N2), bit-reversed layout
+    void *Vn = nullptr;      // the same in natural layout
     void *tw = nullptr;      // Nmax/2 complex, exp(+2 pi i k / Nmax)
     void *Sband = nullptr;   // nb x (2 order - 1): S[j][j+d], d = -(order-1)..order-1
     void *Dband = nullptr;   // same layout for D = <B'|B'>
@@ -67,12 +68,23 @@ struct mb_handle {
     std::vector<int> kofs, qofs;     // offsets of per-k arrays (in elements)
     int total_ldg = 0;
     int *d_goff = nullptr;           // all k (int), offset kofs
+    int *d_rows = nullptr;           // occupied grid rows of every k, offset rows_ofs[k]
+    std::vector<int> rows_ofs, nrows;
+    std::vector<unsigned long long> rowmask;
     mb::DevTables t64, t32;
     bool pfac_ready = false;
     mb::Scratch scratch;
     void *d_desc = nullptr;          // descriptor arrays for batched launches
     size_t desc_bytes = 0;
     std::string last_cuda_error;
+    // launch accounting (always on) and optional per-kernel event timing
+    long long launches = 0;
+    bool profiling = false;
+    struct ProfEvent { int kernel; cudaEvent_t a, b; };
+    std::vector<ProfEvent> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[16] = {0};
+    long long prof_count[16] = {0};
 };
 
 namespace mb {
@@ -82,6 +94,7 @@ int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int
                       double ecut, const double *breaks, int nbreaks, int order,
                       const mb_atom *atoms, int natoms, const mb_opts *opts);
 void vtable_permuted(const mb_handle *h, std::vector<double> &out);
+void vtable_natural(const mb_handle *h, std::vector<double> &out);
 void precond_factors(const mb_handle *h, int ik, double shift, std::vector<double> &out);
 
 // apply.cu
@@ -97,6 +110,14 @@ int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nb
 size_t apply_scratch_bytes(const mb_handle *h, int nsel_max, int nbands, int prec);
 
 enum { BAND_S = 0, BAND_SINV = 1, BAND_PREC = 2 };
+
+// kernel ids for launch accounting / profiling
+enum { KN_PLANE = 0, KN_EPILOGUE, KN_PROJ, KN_COEF, KN_BACKPROJ, KN_BANDED, KN_GRAM, KN_COMBINE,
+       KN_JACOBI, KN_SMALL, KN_VEC, KN_COUNT };
+extern const char *const kKernelNames[KN_COUNT];
+void prof_begin(mb_handle *h, cudaStream_t s, int kernel, cudaEvent_t *a);
+void prof_end(mb_handle *h, cudaStream_t s, int kernel, cudaEvent_t a);
+int prof_collect(mb_handle *h);
 
 int cuda_fail(mb_handle *h, cudaError_t e);
 

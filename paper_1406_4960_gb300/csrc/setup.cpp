@@ -361,6 +361,15 @@ void vtable_permuted(const mb_handle *h, std::vector<double> &out) {
                     h->wq[q] * scale * h->Vnat[(size_t)q * NN + rev(p1, h->l1) * N2 + rev(p2, h->l2)];
 }
 
+// The same table in natural layout (register-FFT kernel).
+void vtable_natural(const mb_handle *h, std::vector<double> &out) {
+    const int NN = h->n1 * h->n2;
+    out.assign((size_t)h->nq * NN, 0.0);
+    double scale = 1.0 / NN;
+    for (int q = 0; q < h->nq; ++q)
+        for (int e = 0; e < NN; ++e) out[(size_t)q * NN + e] = h->wq[q] * scale * h->Vnat[(size_t)q * NN + e];
+}
+
 // Banded Cholesky factors of T(G) + c S = D/2 + (|k+G|^2/2 + c) S for every
 // G of k-point ik: out[g][j][d] = L[j][j-d].
 void precond_factors(const mb_handle *h, int ik, double shift, std::vector<double> &out) {

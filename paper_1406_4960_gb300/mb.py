@@ -20,7 +20,9 @@ ERRORS = {0: "MB_OK", 1: "MB_EINVAL", 2: "MB_ENOMEM", 3: "MB_ENOTCONV", 4: "MB_E
 
 EXPORTS = ("mb_setup", "mb_destroy", "mb_sizes", "mb_gvectors", "mb_zplanes",
            "mb_set_local_potential", "mb_apply_H", "mb_apply_H_batch", "mb_apply_S",
-           "mb_apply_Sinv", "mb_eigsolve", "mb_strerror", "mb_last_cuda_error")
+           "mb_apply_Sinv", "mb_eigsolve", "mb_strerror", "mb_last_cuda_error",
+           "mb_set_profiling", "mb_profile_read", "mb_profile_reset", "mb_launch_count",
+           "mb_kernel_name")
 
 
 class MBError(RuntimeError):
@@ -51,7 +53,7 @@ class SolveInfo(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("krylov_depth", ctypes.c_int), ("block", ctypes.c_int),
-                ("max_cycles", ctypes.c_int), ("polish", ctypes.c_int)]
+                ("max_cycles", ctypes.c_int), ("polish", ctypes.c_int), ("guard", ctypes.c_int)]
 
 
 _lib = None
@@ -93,6 +95,13 @@ def load(build_if_missing: bool = False):
     lib.mb_strerror.restype = ctypes.c_char_p
     lib.mb_last_cuda_error.argtypes = [vp]
     lib.mb_last_cuda_error.restype = ctypes.c_char_p
+    lib.mb_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.mb_profile_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.mb_profile_reset.argtypes = [vp]
+    lib.mb_launch_count.argtypes = [vp]
+    lib.mb_launch_count.restype = ctypes.c_longlong
+    lib.mb_kernel_name.argtypes = [ctypes.c_int]
+    lib.mb_kernel_name.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -240,10 +249,14 @@ class Handle:
                                             self._prec(prec), _stream_ptr(stream)), "mb_apply_Sinv")
 
     def eigsolve(self, nbands, tol, prec="fp64", evecs=None, krylov_depth=0, block=0,
-                 max_cycles=0, polish=0, stream=None, allow_notconv=False):
+                 max_cycles=0, polish=0, stream=None, allow_notconv=False, guard=0):
         ev = np.zeros(self.nk * nbands)
         info = SolveInfo()
-        so = SolveOpts(krylov_depth, block, max_cycles, polish)
+        so = SolveOpts(krylov_depth, block, max_cycles, polish, guard)
+        if evecs is not None:
+            need = sum(nbands * self.sizes(ik)[1] * self.sizes(ik)[2] for ik in range(self.nk))
+            if evecs.dtype.itemsize != 16 or evecs.numel() < need or not evecs.is_cuda or not evecs.is_contiguous():
+                raise MBError(1, "evecs must be a contiguous CUDA complex128 buffer of %d elements" % need)
         rc = self._lib.mb_eigsolve(self._h, nbands, float(tol), self._prec(prec), _dptr(ev),
                                    ctypes.c_void_p(evecs.data_ptr()) if evecs is not None else None,
                                    ctypes.byref(so), ctypes.byref(info), _stream_ptr(stream))

@@ -65,7 +65,7 @@ def test_lanczos_krylov_matches_dense_tiny():
     m = Hm.model_from_workload(w)
     ref = E.generalized_lowest(m.dense_H(), m.dense_S(), w.nbands)
     ops = E.BlockOps(m)
-    eps, X, info = E.lanczos_krylov(ops, _free_electron_start(m, w.nbands), w.nbands, tol=1e-8)
+    eps, X, info = E.lanczos_krylov(ops, _free_electron_start(m, w.nbands + E.default_guard(w.nbands)), w.nbands, tol=1e-8)
     assert info["residuals"].max() < 1e-8
     assert np.abs(eps - ref).max() < 1e-10
     SX = ops.S(X)
@@ -78,7 +78,7 @@ def test_lanczos_krylov_with_projectors_and_k():
     m = Hm.model_from_workload(w)
     ref = E.generalized_lowest(m.dense_H(), m.dense_S(), 6)
     ops = E.BlockOps(m)
-    eps, X, info = E.lanczos_krylov(ops, _free_electron_start(m, 6), 6, block=3, tol=1e-8)
+    eps, X, info = E.lanczos_krylov(ops, _free_electron_start(m, 6 + E.default_guard(6)), 6, block=3, tol=1e-8)
     assert np.abs(eps - ref).max() < 1e-10
 
 
@@ -89,6 +89,6 @@ def test_lanczos_krylov_overlap_operator_is_the_literal_krylov_space():
     m = Hm.model_from_workload(w)
     ref = E.generalized_lowest(m.dense_H(), m.dense_S(), 4)
     ops = E.BlockOps(m, precond="overlap")
-    eps, X, info = E.lanczos_krylov(ops, _free_electron_start(m, 4), 4, depth=6, block=2,
+    eps, X, info = E.lanczos_krylov(ops, _free_electron_start(m, 4 + E.default_guard(4)), 4, depth=6, block=2,
                                     tol=1e-7, max_cycles=400)
     assert np.abs(eps - ref).max() < 1e-9
