@@ -131,6 +131,33 @@ int mb_apply_H_batch(mb_handle *h, int nsel, const int *iks,
                      const void *const *X, void *const *Y, int nbands,
                      int prec, void *stream);
 
+/* ---- H apply without device allocation --------------------------------
+ * The paper has no counterpart to this call; it exists for callers of this
+ * library that must not allocate device memory while they run -- for example
+ * code whose device memory is a fixed budget handed out by its own pool, or a
+ * pipeline that cannot afford the device-wide synchronization that cudaMalloc
+ * and cudaFree may cause.  mb_apply_H grows a scratch buffer owned by the
+ * handle on demand (cudaMalloc); this variant computes the same Y = H X for
+ * one k-point with its scratch in an array of MB_NOALLOC_SCRATCH_BYTES
+ * compiled into the library instead.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine; the caller still passes X and Y (device, layout
+ * and element type as for mb_apply_H), and the handle must already exist.
+ *
+ *   - The array is a file-scope __device__ object: every GPU on which the
+ *     library's device code is loaded holds it until the process exits.
+ *   - The first call on a device looks the array's address up on that device
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call, from every handle, shares the one array and leaves its
+ *     contents behind.  Nothing in it has to start at zero (each element is
+ *     written before it is read), but calls whose work overlaps on the GPU --
+ *     different streams, or several host threads -- race on it: serialize them.
+ *   - Returns MB_EINVAL when the request needs more scratch than the array
+ *     holds (it fits, for example, a 32-band FP32 apply of a 179-G, 120-spline
+ *     slab k-point), and the other MB_E* codes of mb_apply_H. */
+#define MB_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int mb_apply_H_noalloc(mb_handle *h, int ik, const void *X, void *Y, int nbands,
+                       int prec, void *stream);
+
 /* Y = S X (§II.B.1, Eqs. (7)-(8): S is G-diagonal and banded in j). */
 int mb_apply_S(mb_handle *h, int ik, const void *X, void *Y, int nbands,
                int prec, void *stream);

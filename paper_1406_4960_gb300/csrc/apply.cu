@@ -609,22 +609,56 @@ size_t apply_scratch_bytes(const mb_handle *h, int nsel_max, int nbands, int pre
 }
 
 template <typename R>
+static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y,
+                          int nbands, cudaStream_t s, const DevTables &t, char *base);
+
+// Scratch bytes one batched apply needs (boundary rows, projector overlaps W
+// and coefficients C for every k-point of the group).
+template <typename R>
+static size_t apply_H_need(const mb_handle *h, int nsel, const int *iks, int nbands) {
+    const size_t c2 = sizeof(typename V2<R>::T);
+    int maxldg = 0;
+    for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
+    const PlanePlan plan = plan_plane(h, nsel, nbands, c2, maxldg, plane_reg_supported<R>(h->n1, h->n2));
+    return (size_t)nsel * per_k_scratch(h, maxldg, nbands, plan.nchunks, c2);
+}
+
+template <typename R>
 static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y,
                          int nbands, cudaStream_t s, const DevTables &t) {
+    int rc = ensure_scratch(h, apply_H_need<R>(h, nsel, iks, nbands));
+    if (rc) return rc;
+    return apply_H_launch<R>(h, nsel, iks, X, Y, nbands, s, t, reinterpret_cast<char *>(h->scratch.ptr));
+}
+
+// Scratch need of a single-k-point apply, and the apply itself on a scratch
+// region supplied by the caller of this function (no allocation here).
+size_t apply_H_scratch_need(const mb_handle *h, int ik, int nbands, int prec) {
+    return prec == MB_FP64 ? apply_H_need<double>(h, 1, &ik, nbands) : apply_H_need<float>(h, 1, &ik, nbands);
+}
+
+int apply_H_on_scratch(mb_handle *h, int ik, const void *X, void *Y, int nbands, int prec, cudaStream_t s,
+                       void *scratch) {
+    const void *xs[1] = {X};
+    void *ys[1] = {Y};
+    return prec == MB_FP64
+               ? apply_H_launch<double>(h, 1, &ik, xs, ys, nbands, s, h->t64, reinterpret_cast<char *>(scratch))
+               : apply_H_launch<float>(h, 1, &ik, xs, ys, nbands, s, h->t32, reinterpret_cast<char *>(scratch));
+}
+
+template <typename R>
+static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y,
+                          int nbands, cudaStream_t s, const DevTables &t, char *base) {
     typedef typename V2<R>::T R2;
     const size_t c2 = sizeof(R2);
-    std::vector<KDesc> desc(nsel);
+    KDesc desc[kMaxK];
     size_t off = 0;
     int maxldg = 0;
     for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
     const PlanePlan plan = plan_plane(h, nsel, nbands, c2, maxldg, plane_reg_supported<R>(h->n1, h->n2));
     const int chunk = plan.chunk, nchunks = plan.nchunks;
     if (plan.np < 1) return MB_EUNSUPPORTED;
-    size_t need = (size_t)nsel * per_k_scratch(h, maxldg, nbands, nchunks, c2);
-    int rc = ensure_scratch(h, need);
-    if (rc) return rc;
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    char *base = reinterpret_cast<char *>(h->scratch.ptr);
     for (int i = 0; i < nsel; ++i) {
         const KPoint &kp = h->kp[iks[i]];
         KDesc &d = desc[i];
@@ -654,7 +688,7 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
         ga.nb = h->nb;
         ga.nbands = nbands;
         ga.nproj = h->nproj;
-        std::copy(desc.begin(), desc.end(), ga.d);
+        std::copy(desc, desc + nsel, ga.d);
         dim3 grid((nbands * h->nb + 63) / 64, (h->nproj + 63) / 64, nsel);
         MB_LAUNCH(h, s, KN_PROJ, zgemm_kernel<R><<<grid, 256, 0, s>>>(ga));
         CoefArgs<R> ca;
@@ -663,7 +697,7 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
         ca.nb = h->nb;
         ca.nbands = nbands;
         ca.nproj = h->nproj;
-        std::copy(desc.begin(), desc.end(), ca.d);
+        std::copy(desc, desc + nsel, ca.d);
         MB_LAUNCH(h, s, KN_COEF, coef_kernel<R><<<dim3((nbands * h->nproj + 127) / 128, nsel), 128, 0, s>>>(ca));
     }
     // local potential through the planes
@@ -690,7 +724,7 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
     pa.nsel = nsel;
     pa.bt = plan.bt;
     pa.np = plan.np;
-    std::copy(desc.begin(), desc.end(), pa.d);
+    std::copy(desc, desc + nsel, pa.d);
     if (plan.reg) {
         const unsigned grid = (unsigned)(nsel * ((nbands + plan.bt - 1) / plan.bt) * nchunks);
         cudaError_t e = cudaSuccess;
@@ -710,7 +744,7 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
     ea.nchunks = nchunks;
     ea.chunk = chunk;
     ea.nint = h->nint;
-    std::copy(desc.begin(), desc.end(), ea.d);
+    std::copy(desc, desc + nsel, ea.d);
     MB_LAUNCH(h, s, KN_EPILOGUE, epilogue_kernel<R><<<dim3(h->nb, nbands, nsel), 256, 0, s>>>(ea));
     if (h->nproj > 0) {
         GemmArgs<R> ga;
@@ -719,7 +753,7 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
         ga.nb = h->nb;
         ga.nbands = nbands;
         ga.nproj = h->nproj;
-        std::copy(desc.begin(), desc.end(), ga.d);
+        std::copy(desc, desc + nsel, ga.d);
         dim3 grid((nbands * h->nb + 63) / 64, (maxldg + 63) / 64, nsel);
         MB_LAUNCH(h, s, KN_BACKPROJ, zgemm_kernel<R><<<grid, 256, 0, s>>>(ga));
     }

@@ -108,6 +108,9 @@ int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X,
 int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nbands,
                  int prec, cudaStream_t s);
 size_t apply_scratch_bytes(const mb_handle *h, int nsel_max, int nbands, int prec);
+size_t apply_H_scratch_need(const mb_handle *h, int ik, int nbands, int prec);
+int apply_H_on_scratch(mb_handle *h, int ik, const void *X, void *Y, int nbands, int prec, cudaStream_t s,
+                       void *scratch);
 
 enum { BAND_S = 0, BAND_SINV = 1, BAND_PREC = 2 };
 

@@ -22,7 +22,7 @@ EXPORTS = ("mb_setup", "mb_destroy", "mb_sizes", "mb_gvectors", "mb_zplanes",
            "mb_set_local_potential", "mb_apply_H", "mb_apply_H_batch", "mb_apply_S",
            "mb_apply_Sinv", "mb_eigsolve", "mb_strerror", "mb_last_cuda_error",
            "mb_set_profiling", "mb_profile_read", "mb_profile_reset", "mb_launch_count",
-           "mb_kernel_name")
+           "mb_kernel_name", "mb_apply_H_noalloc")
 
 
 class MBError(RuntimeError):
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = False):
     lib.mb_profile_reset.argtypes = [vp]
     lib.mb_launch_count.argtypes = [vp]
     lib.mb_launch_count.restype = ctypes.c_longlong
+    lib.mb_apply_H_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     lib.mb_kernel_name.argtypes = [ctypes.c_int]
     lib.mb_kernel_name.restype = ctypes.c_char_p
     _lib = lib
