@@ -148,6 +148,55 @@ def cpu_baseline(w, budget_s=12.0, impl_steps=None):
     return done_bytes / t_used / 1e9, cores, sample, t_used, n_apply
 
 
+def golden_slab():
+    """Oracle eigenvalues of the slab workload (tests/golden/slab_eigs.txt,
+    written by tests/golden/make_slab_eigs.py from the oracle alone)."""
+    path = os.path.join(ROOT, "tests", "golden", "slab_eigs.txt")
+    if not os.path.exists(path):
+        return None
+    rows = [l for l in open(path) if l.strip() and not l.startswith("#")]
+    return np.array([[float(x) for x in r.split()] for r in rows])
+
+
+def eig_bench(h, w, args):
+    """Mixed-precision and plain-FP64 eigensolves of the whole workload
+    (4 k-points x 32 roots, residual tolerance 1e-6 Ha, which bounds every
+    eigenvalue error by 1e-6 Ha); wall time per solve = solve latency."""
+    ref = golden_slab()
+    out = {"tol_ha": 1e-6, "roots": w.nbands, "kpoints": w.nk}
+    for prec, reps in (("fp32", args.eig_reps), ("fp64", max(1, args.eig_reps // 2))):
+        h.eigsolve(w.nbands, 1e-6, prec)          # warm-up (module load, set-up of factors)
+        times, infos, ev = [], [], None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            ev, info = h.eigsolve(w.nbands, 1e-6, prec)
+            times.append(time.perf_counter() - t0)
+            infos.append(info)
+        ts = np.array(times) * 1e3
+        # one more solve with per-kernel event timing (not part of the timed reps)
+        import ctypes
+        lib = h._lib
+        lib.mb_profile_reset(h._h)
+        lib.mb_set_profiling(h._h, 1)
+        n0 = lib.mb_launch_count(h._h)
+        h.eigsolve(w.nbands, 1e-6, prec)
+        nl = lib.mb_launch_count(h._h) - n0
+        lib.mb_set_profiling(h._h, 0)
+        kms = {}
+        for kid in range(11):
+            t_, c_ = ctypes.c_double(), ctypes.c_longlong()
+            lib.mb_profile_read(h._h, kid, ctypes.byref(t_), ctypes.byref(c_))
+            if c_.value:
+                kms[lib.mb_kernel_name(kid).decode()] = [round(t_.value, 3), int(c_.value)]
+        rec = {"kernels_ms_launches": kms, "launches": int(nl),"solves_per_s": 1e3 / float(np.mean(ts)), "ms_p50": float(np.percentile(ts, 50)),
+               "ms_p99": float(np.percentile(ts, 99)), "reps": reps, "cycles": infos[-1].cycles,
+               "applies": infos[-1].applies, "max_residual": infos[-1].max_residual,
+               "max_abs_err_vs_oracle_ha": None if ref is None else float(np.abs(ev - ref).max())}
+        out["mixed" if prec == "fp32" else "fp64"] = rec
+    out["mixed_speedup_vs_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
+
+
 def _blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -264,6 +313,15 @@ def run_ours(args):
                     prof[lib.mb_kernel_name(kid).decode()] = (t.value, c.value)
         return allmax(ms), launches, prof
 
+    if args.eig_only:
+        # one mixed and one plain-FP64 solve (for launch lists under ncu)
+        for prec in ("fp32", "fp64"):
+            t0 = time.perf_counter()
+            ev, info = h.eigsolve(w.nbands, 1e-6, prec)
+            print(json.dumps({"eig_only": prec, "seconds": time.perf_counter() - t0, "cycles": info.cycles}))
+        h.close()
+        return
+
     clocks = Clocks(local)
     clocks.start()
     ms32, launches, prof = timed("fp32", args.steps, args.warmup, profile=True)
@@ -330,6 +388,8 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clk,
     }
+    if not args.no_eig:
+        line["eigsolve"] = eig_bench(h, w, args)
     if rank == 0 and world == 1 and not args.no_cpu:
         gbs, cores, sample, secs, n = cpu_baseline(w, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
@@ -349,6 +409,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-eig", action="store_true")
+    ap.add_argument("--eig-only", action="store_true")
+    ap.add_argument("--eig-reps", type=int, default=6)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

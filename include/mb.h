@@ -196,6 +196,57 @@ int mb_eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals,
                 void *evecs, const mb_solve_opts *sopts, mb_solve_info *info,
                 void *stream);
 
+/* ---- launch-shape autotuner -------------------------------------------
+ * Times the plane kernel's candidate launch shapes (bands per CTA, resident
+ * waves of CTAs, and with them the length of the knot-interval runs) for an
+ * apply of `nbands` bands at all k-points of the handle, on scratch blocks
+ * it allocates, and keeps the fastest for later applies and eigensolves of
+ * that shape.  Set-up time call (allocates; not during stream capture).
+ * Outputs may be NULL. */
+int mb_autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves,
+                double *best_ms);
+
+/* ---- continuous-batching solve server ---------------------------------
+ * Serves mb_eigsolve requests of mixed sizes on one device.  Submitted
+ * requests queue; `slots` worker threads admit them whenever a slot is idle
+ * and the request's device footprint (basis tables, apply scratch, Krylov
+ * workspace -- computed exactly from a host-side set-up of its basis) fits in
+ * what is left of `hbm_budget_bytes`, first fit over the queue.  Each
+ * admitted request keeps its own handle and stream, so requests that arrive
+ * while others run are admitted as memory frees up and their work overlaps
+ * on the device.  Results do not depend on the mix (private state, fixed
+ * reduction orders).  The request's arrays are copied at submission. */
+typedef struct mb_server mb_server;
+typedef struct {
+    mb_cell cell;
+    const double *kpts;   /* nk x 2 */
+    int nk;
+    double ecut;
+    const double *breaks;
+    int nbreaks;
+    int order;
+    const mb_atom *atoms;
+    int natoms;
+    mb_opts opts;         /* device is overridden by the server's */
+    int nbands;
+    double tol;
+    int prec;
+} mb_request;
+
+int mb_server_create(int device, int slots, double hbm_budget_bytes, mb_server **out);
+/* MB_ENOMEM if the request could never fit the budget. */
+int mb_server_submit(mb_server *srv, const mb_request *req, long long *ticket);
+/* Blocks until the request completes (timeout_s <= 0: no limit; otherwise
+ * MB_ETIMEOUT after that many seconds, the request still pending).  evals:
+ * host nk*nbands doubles; latency_s: submission to completion.  Returns the
+ * request's own status (that of mb_setup / mb_eigsolve). */
+int mb_server_wait(mb_server *srv, long long ticket, double *evals, mb_solve_info *info,
+                   double *latency_s, double timeout_s);
+int mb_server_stats(mb_server *srv, int *queued, int *running, int *peak_running,
+                    double *bytes_in_use, double *peak_bytes);
+/* Finishes every queued and running request, then frees the server. */
+void mb_server_destroy(mb_server *srv);
+
 /* ---- instrumentation ------------------------------------------------
  * Every kernel the library launches is counted per handle.  With profiling
  * on, each launch is also bracketed by CUDA events on its own stream; the

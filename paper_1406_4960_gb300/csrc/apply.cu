@@ -558,19 +558,28 @@ static PlanePlan plan_plane(const mb_handle *h, int nsel, int nbands, size_t c2,
     const int K = h->order, P = h->nquad;
     const size_t NN = (size_t)h->n1 * h->n2;
     int ctas_per_sm = 1;
+    // defaults, or the shape mb_autotune measured fastest for this batch
+    const bool small = h->n1 <= 32 && h->n2 <= 32;
+    int bt_max = small ? 2 : 1, waves = 2;
+    auto it = h->tuned.find(std::make_tuple(nsel, nbands, c2 == 16 ? 1 : 0));
+    if (it != h->tuned.end()) {
+        bt_max = it->second.first;
+        waves = it->second.second;
+    }
     if (reg_ok) {
         const size_t plane_bytes = (size_t)h->n1 * (h->n2 + 1) * c2;
-        ctas_per_sm = NN <= 1024 ? 2 : 1;
-        for (int bt = NN <= 1024 ? 2 : 1; bt >= 1 && !p.reg; --bt) {
+        ctas_per_sm = (small && c2 == 8) ? 2 : 1;     // matches the kernel's launch bounds
+        for (int bt = bt_max; bt >= 1 && !p.reg; --bt) {
             size_t budget = (size_t)h->smem_optin / ctas_per_sm - 1024;
             size_t acc = (size_t)bt * K * maxldg * c2;
             if (acc + plane_bytes > budget) continue;
-            int np = (int)std::min<size_t>((size_t)bt * P, (budget - acc) / plane_bytes);
+            const size_t meta = 8 + 8 * (2 * sizeof(int) + 8 * c2 / 2);   // per plane, rounded up below
+            int np = (int)std::min<size_t>((size_t)bt * P, (budget - acc) / (plane_bytes + meta));
             if (np < 1) continue;
             p.reg = true;
             p.bt = bt;
             p.np = np;
-            p.smem = acc + (size_t)np * plane_bytes;
+            p.smem = acc + (size_t)np * plane_bytes + ((size_t)(np + 1) * 2 * sizeof(int) + (size_t)np * 8 * (c2 / 2) + 15) / 16 * 16;
         }
     }
     if (!p.reg) {
@@ -583,7 +592,7 @@ static PlanePlan plan_plane(const mb_handle *h, int nsel, int nbands, size_t c2,
         p.smem = fixed + (size_t)p.np * NN * c2;
     }
     const int pairs = nsel * ((nbands + p.bt - 1) / p.bt);
-    const int want = 2 * h->num_sms * ctas_per_sm;
+    const int want = waves * h->num_sms * ctas_per_sm;
     const int target = std::max(1, (want + pairs - 1) / pairs);
     p.chunk = std::max(K, (h->nint + target - 1) / target);
     if (p.chunk >= h->nint) p.chunk = h->nint;
@@ -671,6 +680,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         d.rows_ofs = h->rows_ofs[iks[i]];
         d.nrows = h->nrows[iks[i]];
         d.rowmask = h->rowmask[iks[i]];
+        d.rows_magic = (unsigned)((1ull << 32) / (unsigned)std::max(1, d.nrows) + 1);
         size_t part = (size_t)nbands * std::max(0, nchunks - 1) * 2 * (h->order - 1) * kp.ldg * c2;
         size_t w = (size_t)nbands * h->nb * std::max(1, h->nproj) * c2;
         d.part = base + off;
@@ -731,7 +741,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         MB_LAUNCH(h, s, KN_PLANE, e = plane_reg_launch<R>(pa, grid, plan.smem, s));
         MB_CUDA(e);
     } else {
-        MB_CUDA(cudaFuncSetAttribute(plane_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem));
+        MB_CUDA(smem_limit_once((const void *)plane_kernel<R>, h->device, h->smem_optin));
         MB_LAUNCH(h, s, KN_PLANE, plane_kernel<R><<<nsel * nbands * nchunks, 256, plan.smem, s>>>(pa));
     }
     EpiArgs<R> ea;
@@ -788,36 +798,92 @@ int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nb
     MB_CUDA(cudaSetDevice(h->device));
     const KPoint &kp = h->kp[ik];
     dim3 grid((kp.ldg + 127) / 128, nbands);
-    if (which == BAND_PREC) {
-        int rc = ensure_precond(h);
-        if (rc) return rc;
-    }
-    size_t pofs = 0;
-    for (int i = 0; i < ik; ++i) pofs += (size_t)h->kp[i].ldg * h->nb * h->order;
-    size_t gstride = (size_t)h->nb * h->order;
+    if (which != BAND_S && which != BAND_SINV) return MB_EINVAL;
     if (prec == MB_FP64) {
         const DevTables &t = h->t64;
         auto x = reinterpret_cast<const double2 *>(X);
         auto y = reinterpret_cast<double2 *>(Y);
         if (which == BAND_S)
             MB_LAUNCH(h, s, KN_BANDED, banded_S_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
-        else if (which == BAND_SINV)
-            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
         else
-            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Pfac + pofs, gstride, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
+            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
     } else {
         const DevTables &t = h->t32;
         auto x = reinterpret_cast<const float2 *>(X);
         auto y = reinterpret_cast<float2 *>(Y);
         if (which == BAND_S)
             MB_LAUNCH(h, s, KN_BANDED, banded_S_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
-        else if (which == BAND_SINV)
-            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
         else
-            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Pfac + pofs, gstride, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
+            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
     }
     MB_CUDA(cudaGetLastError());
     return MB_OK;
 }
 
 }  // namespace mb
+
+// ---------------------------------------------------------------------------
+// mb_autotune: time the candidate plane-kernel launch shapes for a batch of
+// `nbands` bands at every k-point of the handle and keep the fastest.
+namespace mb {
+int autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves, double *best_ms) {
+    if (nbands < 1 || nbands > h->max_bands) return MB_EINVAL;
+    if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return MB_EINVAL;
+    MB_CUDA(cudaSetDevice(h->device));
+    const int nk = (int)h->kp.size();
+    const size_t c2 = prec == MB_FP64 ? 16 : 8;
+    std::vector<void *> X(nk, nullptr), Y(nk, nullptr);
+    std::vector<int> iks(nk);
+    int rc = MB_OK;
+    for (int i = 0; i < nk && rc == MB_OK; ++i) {
+        iks[i] = i;
+        size_t bytes = (size_t)nbands * h->nb * h->kp[i].ldg * c2;
+        if (cudaMalloc(&X[i], bytes) != cudaSuccess || cudaMalloc(&Y[i], bytes) != cudaSuccess) rc = MB_ENOMEM;
+        else cudaMemset(X[i], 0, bytes);
+    }
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == MB_OK && (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = MB_ECUDA;
+    const bool small = h->n1 <= 32 && h->n2 <= 32;
+    const auto key = std::make_tuple(std::min(nk, kMaxK), nbands, c2 == 16 ? 1 : 0);
+    double best = 1e300;
+    std::pair<int, int> bestp(small ? 2 : 1, 2);
+    for (int bt = small ? 2 : 1; bt >= 1 && rc == MB_OK; --bt)
+        for (int waves : {1, 2, 4, 8}) {
+            h->tuned[key] = std::make_pair(bt, waves);
+            for (int w = 0; w < 2 && rc == MB_OK; ++w)
+                rc = apply_H_batch(h, nk, iks.data(), (const void *const *)X.data(), Y.data(), nbands, prec, s);
+            if (rc) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 5 && rc == MB_OK; ++r)
+                rc = apply_H_batch(h, nk, iks.data(), (const void *const *)X.data(), Y.data(), nbands, prec, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = MB_ECUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rc == MB_OK && ms / 5 < best) {
+                best = ms / 5;
+                bestp = std::make_pair(bt, waves);
+            }
+        }
+    h->tuned[key] = bestp;
+    if (best_bt) *best_bt = bestp.first;
+    if (best_waves) *best_waves = bestp.second;
+    if (best_ms) *best_ms = best;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    for (int i = 0; i < nk; ++i) {
+        if (X[i]) cudaFree(X[i]);
+        if (Y[i]) cudaFree(Y[i]);
+    }
+    return rc;
+}
+}  // namespace mb
+
+extern "C" int mb_autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves, double *best_ms) {
+    if (!h) return MB_EINVAL;
+    return mb::autotune(h, nbands, prec, best_bt, best_waves, best_ms);
+}

@@ -19,6 +19,7 @@ struct KDesc {
     int rows_ofs;    // offset of this k-point's list of grid rows that hold disc points
     int nrows;
     unsigned long long rowmask;   // bit i1 set when grid row i1 holds disc points
+    unsigned rows_magic;          // floor(2^32 / nrows) + 1: e / nrows = umulhi(e, rows_magic)
 };
 
 template <typename R> struct PlaneArgs {

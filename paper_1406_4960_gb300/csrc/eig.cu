@@ -30,7 +30,6 @@ namespace mb {
 
 constexpr int LD = 128;       // leading dimension of subspace matrices
 constexpr int JMAX = 112;     // largest subspace the Jacobi kernel holds (matrix in shared memory)
-constexpr int GT = 16;        // n-tile of the Gram kernel
 constexpr int JPAIRS = 58;    // rotation slots per Jacobi round (>= JMAX/2 + 1, even so that
                               // 5*JPAIRS doubles keep the next double2 array 16-byte aligned)
 
@@ -57,60 +56,7 @@ static VSet vs(int s1, int c1, int cs1 = 0, int s2 = 0, int c2 = 0, int cs2 = 0)
 }
 
 // ---------------------------------------------------------------------------
-// Gram products G = A^H B over the full vector length, split into n-chunks
-// whose partial sums are reduced in a fixed order (deterministic).
-__global__ void __launch_bounds__(256) gram_partial_kernel(const EigK *ks, int nch, VSet A, VSet B,
-                                                           int nsplit, double2 *part) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int prob = blockIdx.y, split = blockIdx.x;
-    const int k = prob / nch, ch = prob % nch;
-    const EigK d = ks[k];
-    const int ma = A.count(), mb = B.count();
-    double2 *As = reinterpret_cast<double2 *>(sm);          // [GT][ma]
-    double2 *Bs = As + GT * ma;                             // [GT][mb]
-    const long long n = d.nvec;
-    const long long chunk = ((n + nsplit - 1) / nsplit + GT - 1) / GT * GT;
-    const long long t0 = split * chunk, t1 = min(n, t0 + chunk);
-    constexpr int RMAX = 36;
-    double2 acc[RMAX];
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) acc[r] = make_double2(0.0, 0.0);
-    const int nout = ma * mb;
-    const int obase = blockIdx.z * RMAX * 256;     // this CTA's slice of the outputs
-    for (long long tb = t0; tb < t1; tb += GT) {
-        for (int e = threadIdx.x; e < GT * ma; e += blockDim.x) {
-            int i = e / GT, tt = e % GT;
-            long long t = tb + tt;
-            As[tt * ma + i] = t < t1 ? d.base[(long long)A.at(i, ch) * n + t] : make_double2(0.0, 0.0);
-        }
-        for (int e = threadIdx.x; e < GT * mb; e += blockDim.x) {
-            int j = e / GT, tt = e % GT;
-            long long t = tb + tt;
-            Bs[tt * mb + j] = t < t1 ? d.base[(long long)B.at(j, ch) * n + t] : make_double2(0.0, 0.0);
-        }
-        __syncthreads();
-        for (int tt = 0; tt < GT; ++tt) {
-#pragma unroll
-            for (int r = 0; r < RMAX; ++r) {
-                int o = obase + threadIdx.x + r * 256;
-                if (o < nout) {
-                    int i = o / mb, j = o - (o / mb) * mb;
-                    double2 a = As[tt * ma + i], b = Bs[tt * mb + j];
-                    acc[r].x = fma(a.x, b.x, fma(a.y, b.y, acc[r].x));
-                    acc[r].y = fma(a.x, b.y, fma(-a.y, b.x, acc[r].y));
-                }
-            }
-        }
-        __syncthreads();
-    }
-    double2 *out = part + ((size_t)prob * nsplit + split) * nout;
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-        int o = obase + threadIdx.x + r * 256;
-        if (o < nout) out[o] = acc[r];
-    }
-}
-
+// Fixed-order reduction of per-chunk partial Gram products (deterministic).
 __global__ void gram_reduce_kernel(const double2 *part, int nsplit, int ma, int mb, double2 *G) {
     const int prob = blockIdx.x;
     const int nout = ma * mb;
@@ -119,36 +65,6 @@ __global__ void gram_reduce_kernel(const double2 *part, int nsplit, int ma, int 
         for (int sp = 0; sp < nsplit; ++sp) s = s + part[((size_t)prob * nsplit + sp) * nout + o];
         int i = o / mb, j = o % mb;
         G[(size_t)prob * LD * LD + i * LD + j] = s;
-    }
-}
-
-// C_j = beta C_j + alpha sum_i A_i Y[i][j]   (Y per problem, leading dim LD)
-__global__ void __launch_bounds__(256) combine_kernel(const EigK *ks, int nch, VSet A, VSet C,
-                                                      const double2 *Y, double alpha, double beta) {
-    const int prob = blockIdx.y;
-    const int k = prob / nch, ch = prob % nch;
-    const EigK d = ks[k];
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= d.nvec) return;
-    const int ma = A.count(), mc = C.count();
-    const double2 *y = Y + (size_t)prob * LD * LD;
-    for (int j0 = 0; j0 < mc; j0 += 8) {
-        double2 acc[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) acc[jj] = make_double2(0.0, 0.0);
-        for (int i = 0; i < ma; ++i) {
-            double2 a = d.base[(long long)A.at(i, ch) * d.nvec + t];
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj)
-                if (j0 + jj < mc) cfma(acc[jj], a, __ldg(&y[i * LD + j0 + jj]));
-        }
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-            if (j0 + jj >= mc) break;
-            double2 *c = d.base + (long long)C.at(j0 + jj, ch) * d.nvec + t;
-            double2 v = rscale(alpha, acc[jj]);
-            *c = beta == 0.0 ? v : rscale(beta, *c) + v;
-        }
     }
 }
 
@@ -288,8 +204,12 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
     const double2 *g = G + (size_t)prob * LD * LD;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         int i = e / m, j = e % m;
-        double2 a = g[i * LD + j], b = g[j * LD + i];
-        double2 v = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));   // (A + A^H)/2
+        // Hermitian completion from the lower triangle: with the subspace
+        // ordered [roots | Krylov vectors], the coupling block comes from
+        // K^H (H X), which uses the roots' HX rather than the Krylov vectors'
+        // HK (HK may come from a reduced-precision apply)
+        double2 v = i >= j ? g[i * LD + j] : g[j * LD + i];
+        if (i < j) v.y = -v.y;
         if (i == j) v.y = 0.0;
         bool di = dead && dead[prob * dead_stride + i] == 0 && i >= dead_ofs;
         bool dj = dead && dead[prob * dead_stride + j] == 0 && j >= dead_ofs;
@@ -336,7 +256,8 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
                     double app = A[p * m + p].x, aqq = A[q * m + q].x;
                     rc[5 * pi + 3] = app;
                     rc[5 * pi + 4] = aqq;
-                    if (mag > 0.0) {
+                    // rotations below rounding level of the diagonal are skipped
+                    if (mag > 1e-15 * sqrt(fabs(app * aqq)) && mag > 1e-300) {
                         ep = make_double2(apq.x / mag, apq.y / mag);
                         double th = (aqq - app) / (2.0 * mag);
                         double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
@@ -538,50 +459,217 @@ __global__ void take_evals_kernel(const double *evals, int M, int nk, double *ep
 }
 
 // banded S and banded solves on vector ranges of every k-point (FP64)
-__global__ void eig_banded_S_kernel(const EigK *ks, const double *Sband, int order, int nb, int src, int dst, int nv) {
-    const int k = blockIdx.z, v = blockIdx.y;
+// S apply: one thread per (vector, j, G).
+template <int K>
+__global__ void eig_banded_S_kernel(const EigK *ks, const double *Sband, int nb, int src, int dst, int nv) {
+    const int k = blockIdx.z / nv, v = blockIdx.z % nv, j = blockIdx.y;
     const EigK d = ks[k];
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= d.ldg || v >= nv) return;
-    const int K = order, W = 2 * K - 1;
+    if (g >= d.ldg) return;
+    constexpr int W = 2 * K - 1;
     const double2 *x = d.base + (long long)(src + v) * d.nvec;
     double2 *y = d.base + (long long)(dst + v) * d.nvec;
+    double2 s = make_double2(0.0, 0.0);
+    if (g < d.ng) {
+#pragma unroll
+        for (int dd = 0; dd < W; ++dd) {
+            const int jj = j + dd - (K - 1);
+            if (jj >= 0 && jj < nb) rfma(s, __ldg(&Sband[(size_t)j * W + dd]), x[(size_t)jj * d.ldg + g]);
+        }
+    }
+    y[(size_t)j * d.ldg + g] = s;
+}
+
+// L L^T y = x, one thread per (vector, G) column; the last K-1 solution values
+// ride in registers.  per_g: the k-point's factors L_G[j][d] stored as
+// pfac[(j*K + d)*ldg + G] (coalesced over G); else the G-independent L_z.
+template <int K>
+__global__ void eig_banded_solve_kernel(const EigK *ks, const double *Lb, int per_g, int nb, int src, int dst,
+                                        int nv) {
+    const int k = blockIdx.z / nv, v = blockIdx.z % nv;
+    const EigK d = ks[k];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= d.ldg) return;
+    const double2 *x = d.base + (long long)(src + v) * d.nvec;
+    double2 *y = d.base + (long long)(dst + v) * d.nvec;
+    const size_t ldg = d.ldg;
+    if (g >= d.ng) {
+        for (int j = 0; j < nb; ++j) y[(size_t)j * ldg + g] = make_double2(0.0, 0.0);
+        return;
+    }
+    auto L = [&](int j, int dd) -> double {
+        return per_g ? d.pfac[((size_t)j * K + dd) * ldg + g] : __ldg(&Lb[(size_t)j * K + dd]);
+    };
+    double2 win[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) win[i] = make_double2(0.0, 0.0);
+#pragma unroll 2
     for (int j = 0; j < nb; ++j) {
-        double2 s = make_double2(0.0, 0.0);
-        if (g < d.ng)
-            for (int dd = 0; dd < W; ++dd) {
-                int jj = j + dd - (K - 1);
-                if (jj >= 0 && jj < nb) rfma(s, Sband[(size_t)j * W + dd], x[(size_t)jj * d.ldg + g]);
-            }
-        y[(size_t)j * d.ldg + g] = s;
+        double2 s = x[(size_t)j * ldg + g];
+#pragma unroll
+        for (int dd = 1; dd < K; ++dd)
+            if (j - dd >= 0) rfma(s, -L(j, dd), win[dd - 1]);
+        const double2 yj = rscale(1.0 / L(j, 0), s);
+        y[(size_t)j * ldg + g] = yj;
+#pragma unroll
+        for (int i = K - 1; i > 0; --i) win[i] = win[i - 1];
+        win[0] = yj;
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) win[i] = make_double2(0.0, 0.0);
+#pragma unroll 2
+    for (int j = nb - 1; j >= 0; --j) {
+        double2 s = y[(size_t)j * ldg + g];
+#pragma unroll
+        for (int dd = 1; dd < K; ++dd)
+            if (j + dd < nb) rfma(s, -L(j + dd, dd), win[dd - 1]);
+        const double2 zj = rscale(1.0 / L(j, 0), s);
+        y[(size_t)j * ldg + g] = zj;
+#pragma unroll
+        for (int i = K - 1; i > 0; --i) win[i] = win[i - 1];
+        win[0] = zj;
     }
 }
 
-__global__ void eig_banded_solve_kernel(const EigK *ks, const double *Lb, int per_g, int order, int nb,
-                                        int src, int dst, int nv) {
-    const int k = blockIdx.z, v = blockIdx.y;
+// A^H w for one vector w per problem (the Gram-Schmidt coefficients): one
+// warp per row i over an n-chunk, warp-shuffle reduction, partials per chunk.
+__global__ void __launch_bounds__(256) gram_mv_kernel(const EigK *ks, int nch, VSet A, VSet B, int nsplit,
+                                                      double2 *part) {
+    const int prob = blockIdx.y, split = blockIdx.x;
+    const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= d.ldg || v >= nv) return;
-    const int K = order;
-    const double *L = per_g ? d.pfac + (size_t)g * nb * K : Lb;
-    const double2 *x = d.base + (long long)(src + v) * d.nvec;
-    double2 *y = d.base + (long long)(dst + v) * d.nvec;
-    if (g >= d.ng) {
-        for (int j = 0; j < nb; ++j) y[(size_t)j * d.ldg + g] = make_double2(0.0, 0.0);
-        return;
+    const int ma = A.count();
+    const long long n = d.nvec;
+    const long long chunk = (n + nsplit - 1) / nsplit;
+    const long long t0 = split * chunk, t1 = min(n, t0 + chunk);
+    const double2 *w = d.base + (long long)B.at(0, ch) * n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < ma; i += (blockDim.x >> 5)) {
+        const double2 *a = d.base + (long long)A.at(i, ch) * n;
+        double sx = 0.0, sy = 0.0;
+        for (long long t = t0 + lane; t < t1; t += 32) {
+            double2 av = a[t], wv = w[t];
+            sx = fma(av.x, wv.x, fma(av.y, wv.y, sx));
+            sy = fma(av.x, wv.y, fma(-av.y, wv.x, sy));
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            sx += __shfl_down_sync(0xffffffffu, sx, off);
+            sy += __shfl_down_sync(0xffffffffu, sy, off);
+        }
+        if (lane == 0) part[((size_t)prob * nsplit + split) * ma + i] = make_double2(sx, sy);
     }
-    for (int j = 0; j < nb; ++j) {
-        double2 s = x[(size_t)j * d.ldg + g];
-        for (int dd = 1; dd < K && dd <= j; ++dd) rfma(s, -L[(size_t)j * K + dd], y[(size_t)(j - dd) * d.ldg + g]);
-        y[(size_t)j * d.ldg + g] = rscale(1.0 / L[(size_t)j * K], s);
+}
+
+// A^H B with every output owned by one thread (up to GF_R per thread, output
+// slices over blockIdx.z), n-tiles of GF_T staged in shared memory as
+// [t][column]; no padded outputs, so every FP64 FMA is useful.
+constexpr int GF_T = 32, GF_R = 8;
+__global__ void __launch_bounds__(256) gram_flat_kernel(const EigK *ks, int nch, VSet A, VSet B, int nsplit,
+                                                        double2 *part) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int prob = blockIdx.y, split = blockIdx.x;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const int ma = A.count(), mb = B.count();
+    double2 *As = reinterpret_cast<double2 *>(sm);      // [GF_T][ma]
+    double2 *Bs = As + GF_T * ma;                       // [GF_T][mb]
+    const long long n = d.nvec;
+    const long long chunk = ((n + nsplit - 1) / nsplit + GF_T - 1) / GF_T * GF_T;
+    const long long t0 = split * chunk, t1 = min(n, t0 + chunk);
+    const int nout = ma * mb;
+    const int obase = blockIdx.z * GF_R * 256;
+    int oi[GF_R], oj[GF_R];
+    double2 acc[GF_R];
+#pragma unroll
+    for (int r = 0; r < GF_R; ++r) {
+        const int o = obase + threadIdx.x + r * 256;
+        oi[r] = o < nout ? o / mb : -1;
+        oj[r] = o < nout ? o - (o / mb) * mb : 0;
+        acc[r] = make_double2(0.0, 0.0);
     }
-    for (int j = nb - 1; j >= 0; --j) {
-        double2 s = y[(size_t)j * d.ldg + g];
-        for (int dd = 1; dd < K && j + dd < nb; ++dd)
-            rfma(s, -L[(size_t)(j + dd) * K + dd], y[(size_t)(j + dd) * d.ldg + g]);
-        y[(size_t)j * d.ldg + g] = rscale(1.0 / L[(size_t)j * K], s);
+    for (long long tb = t0; tb < t1; tb += GF_T) {
+        for (int e = threadIdx.x; e < GF_T * ma; e += blockDim.x) {
+            const int i = e / GF_T, tt = e % GF_T;
+            const long long t = tb + tt;
+            As[tt * ma + i] = t < t1 ? d.base[(long long)A.at(i, ch) * n + t] : make_double2(0.0, 0.0);
+        }
+        for (int e = threadIdx.x; e < GF_T * mb; e += blockDim.x) {
+            const int j = e / GF_T, tt = e % GF_T;
+            const long long t = tb + tt;
+            Bs[tt * mb + j] = t < t1 ? d.base[(long long)B.at(j, ch) * n + t] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        for (int tt = 0; tt < GF_T; ++tt) {
+#pragma unroll
+            for (int r = 0; r < GF_R; ++r) {
+                if (oi[r] < 0) continue;
+                const double2 a = As[tt * ma + oi[r]], b = Bs[tt * mb + oj[r]];
+                acc[r].x = fma(a.x, b.x, fma(a.y, b.y, acc[r].x));
+                acc[r].y = fma(a.x, b.y, fma(-a.y, b.x, acc[r].y));
+            }
+        }
+        __syncthreads();
     }
+    double2 *out = part + ((size_t)prob * nsplit + split) * nout;
+#pragma unroll
+    for (int r = 0; r < GF_R; ++r)
+        if (oi[r] >= 0) out[oi[r] * mb + oj[r]] = acc[r];
+}
+
+// C_j = beta C_j + alpha sum_i A_i Y[i][j]: one element t per thread, JC
+// output columns at a time with their coefficients staged in shared memory.
+template <int JC>
+__global__ void __launch_bounds__(256) combine2_kernel(const EigK *ks, int nch, VSet A, VSet C,
+                                                       const double2 *Y, double alpha, double beta) {
+    __shared__ double2 Ys[JMAX][JC];
+    const int prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = t < d.nvec;
+    const int ma = A.count(), mc = C.count();
+    const double2 *y = Y + (size_t)prob * LD * LD;
+    for (int j0 = 0; j0 < mc; j0 += JC) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < ma * JC; e += blockDim.x) {
+            const int i = e / JC, jj = e % JC;
+            Ys[i][jj] = j0 + jj < mc ? y[i * LD + j0 + jj] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        if (!live) continue;
+        double2 acc[JC];
+#pragma unroll
+        for (int jj = 0; jj < JC; ++jj) acc[jj] = make_double2(0.0, 0.0);
+        for (int i = 0; i < ma; ++i) {
+            const double2 a = d.base[(long long)A.at(i, ch) * d.nvec + t];
+#pragma unroll
+            for (int jj = 0; jj < JC; ++jj) cfma(acc[jj], a, Ys[i][jj]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < JC; ++jj) {
+            if (j0 + jj >= mc) break;
+            double2 *c = d.base + (long long)C.at(j0 + jj, ch) * d.nvec + t;
+            const double2 v = rscale(alpha, acc[jj]);
+            *c = beta == 0.0 ? v : rscale(beta, *c) + v;
+        }
+    }
+}
+
+// C = op(A) B for small m x m matrices (leading dimension LD), one thread per
+// output element; op = conjugate transpose when conjA.
+__global__ void small_zgemm_kernel(const double2 *A, const double2 *B, double2 *C, int m, int conjA) {
+    const int prob = blockIdx.y;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    const int i = e / m, j = e % m;
+    const double2 *a = A + (size_t)prob * LD * LD, *b = B + (size_t)prob * LD * LD;
+    double2 s = make_double2(0.0, 0.0);
+    for (int q = 0; q < m; ++q) {
+        double2 av = conjA ? a[q * LD + i] : a[i * LD + q];
+        if (conjA) av.y = -av.y;
+        cfma(s, av, b[q * LD + j]);
+    }
+    C[(size_t)prob * LD * LD + i * LD + j] = s;
 }
 
 // dead-slot mask of a subspace: columns < ofs are the block's inputs (the
@@ -724,13 +812,15 @@ struct Solver {
     cudaStream_t s;
     int nk, M, kd, b, nblk, mA, mB, nc;
     int Mconv;          // roots tested for convergence and returned (M includes guards)
-    int prec;
+    int prec;           // precision of the H applies that build Krylov vectors
+    bool fp64_roots = false;   // finish phase: HX of the roots recomputed in FP64 every cycle
     int oV, oHV, oSV, oVB, oHVB, oSVB, oQ, oHQ, oW, oSW, oT;
     int nvecs;
     std::vector<EigK> kd_host;
     EigK *d_k = nullptr;
     std::vector<void *> allocs;
     double2 *d_G = nullptr, *d_part = nullptr, *d_Y = nullptr, *d_Ysel = nullptr;
+    double2 *d_U = nullptr, *d_G2 = nullptr, *d_T = nullptr;
     double *d_evals = nullptr, *d_eps = nullptr, *d_res = nullptr, *d_dots = nullptr, *d_theta = nullptr;
     int *d_seed = nullptr, *d_srcH = nullptr, *d_srcS = nullptr, *d_alive = nullptr, *d_status = nullptr;
     int *d_mask = nullptr;
@@ -741,7 +831,7 @@ struct Solver {
     int rc = MB_OK;
 
     ~Solver() {
-        for (void *p : allocs) cudaFree(p);
+        for (void *p : allocs) cudaFreeAsync(p, s);   // stream-ordered: no device-wide synchronization
     }
     int cuda(cudaError_t e) {
         if (e != cudaSuccess && rc == MB_OK) rc = cuda_fail(h, e);
@@ -751,37 +841,69 @@ struct Solver {
     template <typename T> T *alloc(size_t n) {
         void *p = nullptr;
         if (rc) return nullptr;
-        if (cuda(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)))) return nullptr;
+        if (cuda(cudaMallocAsync(&p, std::max<size_t>(n, 1) * sizeof(T), s))) return nullptr;
         allocs.push_back(p);
         return reinterpret_cast<T *>(p);
     }
 
     void gram(int nch, VSet A, VSet B, double2 *G) {
-        int nprob = nk * nch;
-        int ma = A.count(), mbc = B.count();
-        int nsplit = std::max(1, std::min(64, (2 * h->num_sms + nprob - 1) / nprob));
+        const int nprob = nk * nch;
+        const int ma = A.count(), mbc = B.count();
+        if (mbc == 1) {
+            int nsplit = std::max(1, std::min(64, (4 * h->num_sms + nprob - 1) / nprob));
+            while ((size_t)nprob * nsplit * ma > part_cap && nsplit > 1) --nsplit;
+            MB_LAUNCH_E(KN_GRAM, gram_mv_kernel<<<dim3(nsplit, nprob), 256, 0, s>>>(d_k, nch, A, B, nsplit, d_part));
+            MB_LAUNCH_E(KN_GRAM, gram_reduce_kernel<<<nprob, 128, 0, s>>>(d_part, nsplit, ma, 1, G));
+            return;
+        }
+        const int slices = (ma * mbc + GF_R * 256 - 1) / (GF_R * 256);
+        int nsplit = std::max(1, std::min(256, (4 * h->num_sms + nprob * slices - 1) / (nprob * slices)));
         while ((size_t)nprob * nsplit * ma * mbc > part_cap && nsplit > 1) --nsplit;
-        size_t smem = (size_t)GT * (ma + mbc) * sizeof(double2);
-        const int otiles = (ma * mbc + 36 * 256 - 1) / (36 * 256);
-        if (smem > 48 * 1024)
-            cuda(cudaFuncSetAttribute(gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MB_LAUNCH_E(KN_GRAM, gram_partial_kernel<<<dim3(nsplit, nprob, otiles), 256, smem, s>>>(d_k, nch, A, B, nsplit, d_part));
+        const size_t smem = (size_t)GF_T * (ma + mbc) * sizeof(double2);
+        if (smem > 48 * 1024) cuda(smem_limit_once((const void *)gram_flat_kernel, h->device, h->smem_optin));
+        MB_LAUNCH_E(KN_GRAM, gram_flat_kernel<<<dim3(nsplit, nprob, slices), 256, smem, s>>>(d_k, nch, A, B, nsplit,
+                                                                                           d_part));
         MB_LAUNCH_E(KN_GRAM, gram_reduce_kernel<<<nprob, 256, 0, s>>>(d_part, nsplit, ma, mbc, G));
     }
     void combine(int nch, VSet A, VSet C, const double2 *Y, double alpha, double beta) {
-        MB_LAUNCH_E(KN_COMBINE, combine_kernel<<<dim3((unsigned)((nmax + 255) / 256), nk * nch), 256, 0, s>>>(
-                                    d_k, nch, A, C, Y, alpha, beta));
+        const dim3 grid((unsigned)((nmax + 255) / 256), nk * nch);
+        const int mc = C.count();
+        // column width with the least padding (12 divides the common 36)
+        auto waste = [&](int jc) { return (mc + jc - 1) / jc * jc - mc; };
+        if (mc == 1)
+            MB_LAUNCH_E(KN_COMBINE, combine2_kernel<1><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta));
+        else if (mc <= 4)
+            MB_LAUNCH_E(KN_COMBINE, combine2_kernel<4><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta));
+        else if (mc <= 8)
+            MB_LAUNCH_E(KN_COMBINE, combine2_kernel<8><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta));
+        else if (waste(12) < waste(16))
+            MB_LAUNCH_E(KN_COMBINE, combine2_kernel<12><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta));
+        else
+            MB_LAUNCH_E(KN_COMBINE, combine2_kernel<16><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta));
+    }
+    void small_gemm(const double2 *A, const double2 *B, double2 *C, int m, int conjA) {
+        MB_LAUNCH_E(KN_SMALL, small_zgemm_kernel<<<dim3((m * m + 127) / 128, nk), 128, 0, s>>>(A, B, C, m, conjA));
     }
     void copy(int nch, VSet S, VSet D, int mode) {
         MB_LAUNCH_E(KN_VEC, copy_kernel<<<dim3(256, nk * nch), 256, 0, s>>>(d_k, nch, S, D, mode));
     }
     void bandS(int src, int dst, int nv) {
-        MB_LAUNCH_E(KN_BANDED, eig_banded_S_kernel<<<dim3((maxldg + 127) / 128, nv, nk), 128, 0, s>>>(
-                                   d_k, (const double *)h->t64.Sband, h->order, h->nb, src, dst, nv));
+        const dim3 grid((maxldg + 127) / 128, h->nb, nk * nv);
+        const double *Sb = (const double *)h->t64.Sband;
+        switch (h->order) {
+#define MB_BS(KK) case KK: MB_LAUNCH_E(KN_BANDED, eig_banded_S_kernel<KK><<<grid, 128, 0, s>>>(d_k, Sb, h->nb, src, dst, nv)); break;
+            MB_BS(3) MB_BS(4) MB_BS(5) MB_BS(6) MB_BS(7) MB_BS(8)
+#undef MB_BS
+        }
     }
     void bandSolve(int per_g, int src, int dst, int nv) {
-        MB_LAUNCH_E(KN_BANDED, eig_banded_solve_kernel<<<dim3((maxldg + 127) / 128, nv, nk), 128, 0, s>>>(
-                                   d_k, (const double *)h->t64.Lband, per_g, h->order, h->nb, src, dst, nv));
+        const dim3 grid((maxldg + 63) / 64, 1, nk * nv);
+        const double *Lb = (const double *)h->t64.Lband;
+        switch (h->order) {
+#define MB_BL(KK) case KK: MB_LAUNCH_E(KN_BANDED, eig_banded_solve_kernel<KK><<<grid, 64, 0, s>>>(d_k, Lb, per_g, h->nb, src, dst, nv)); break;
+            MB_BL(3) MB_BL(4) MB_BL(5) MB_BL(6) MB_BL(7) MB_BL(8)
+#undef MB_BL
+        }
     }
     int nc_stage() const { return std::max(M, nc); }
     void applyH(int src, int dst, int nv, int p) {
@@ -830,10 +952,15 @@ struct Solver {
             MB_LAUNCH_E(KN_VEC, krylov_residual_kernel<<<dim3((unsigned)std::min<long long>(1024, (nmax + 255) / 256), np), 256, 0, s>>>(
                                     d_k, nch, d_srcH, d_srcS, d_theta, oW));
             bandSolve(1, oW, oW, nch);
+            // classical Gram-Schmidt, twice, in the S inner product: all
+            // coefficients of a pass come from the same (pre-update) vector.
+            // The roots X are common to every chain of a k-point, so their
+            // part is one product with a column per chain.
             for (int pass = 0; pass < 2; ++pass) {
-                VSet Sset = vs(oSV, M, 0, kS, i, cs), Vset = vs(oV, M, 0, kV, i, cs);
-                gram(nch, Sset, vs(oW, 1, 1), d_G);
-                combine(nch, Vset, vs(oW, 1, 1), d_G, -1.0, 1.0);
+                gram(1, vs(oSV, M), vs(oW, nch), d_G2);                    // SX^H [W_0 .. W_nch-1]
+                if (i > 0) gram(nch, vs(kS, i, cs), vs(oW, 1, 1), d_G);     // SK_ch^H W_ch
+                combine(1, vs(oV, M), vs(oW, nch), d_G2, -1.0, 1.0);
+                if (i > 0) combine(nch, vs(kV, i, cs), vs(oW, 1, 1), d_G, -1.0, 1.0);
             }
             bandS(oW, oSW, nch);
             MB_LAUNCH_E(KN_SMALL, coldot_kernel<<<dim3(1, np), 256, 0, s>>>(d_k, nch, vs(oW, 1, 1), vs(oSW, 1, 1), d_dots));
@@ -853,22 +980,23 @@ struct Solver {
         if (masked)
             MB_LAUNCH_E(KN_SMALL, alive_mask_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_alive, kd, ofs, M, b, nch, m, np, d_mask));
         if (vs) {
-            cuda(cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+            cuda(smem_limit_once((const void *)jacobi_kernel<true>, h->device, h->smem_optin));
             MB_LAUNCH_E(KN_JACOBI, jacobi_kernel<true><<<np, 256, smem2, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
-                                                                              d_evals, d_Y, 40, 1e-15));
+                                                                              d_evals, d_Y, 30, 1e-13));
         } else {
-            cuda(cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+            cuda(smem_limit_once((const void *)jacobi_kernel<false>, h->device, h->smem_optin));
             MB_LAUNCH_E(KN_JACOBI, jacobi_kernel<false><<<np, 256, smem1, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
-                                                                               d_evals, d_Y, 40, 1e-15));
+                                                                               d_evals, d_Y, 30, 1e-13));
         }
     }
-    void rotate_set(const double2 *Y, int m) {   // X, HX, SX <- [V|..](m) Y[:, :M]
+    // X, HX <- [V|..](m) Y[:, :M] and SX = S X (S is banded: recomputing it is
+    // cheaper than rotating it)
+    void rotate_set(const double2 *Y, int m) {
         combine(1, vs(oV, m), vs(oT, M), Y, 1.0, 0.0);
         combine(1, vs(oHV, m), vs(oT + M, M), Y, 1.0, 0.0);
-        combine(1, vs(oSV, m), vs(oT + 2 * M, M), Y, 1.0, 0.0);
         copy(1, vs(oT, M), vs(oV, M), 0);
         copy(1, vs(oT + M, M), vs(oHV, M), 0);
-        copy(1, vs(oT + 2 * M, M), vs(oSV, M), 0);
+        bandS(oV, oSV, M);
     }
     void rr_full(bool withK) {
         int m = withK ? mA : M;
@@ -877,20 +1005,25 @@ struct Solver {
         rotate_set(d_Y, m);
         MB_LAUNCH_E(KN_SMALL, take_evals_kernel<<<(M * nk + 127) / 128, 128, 0, s>>>(d_evals, M, nk, d_eps));
     }
-    void cholqr() {
-        for (int pass = 0; pass < 2; ++pass) {
-            gram(1, vs(oV, M), vs(oSV, M), d_G);
-            size_t smem = (size_t)M * M * sizeof(double2);
-            cuda(cudaFuncSetAttribute(cholinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            MB_LAUNCH_E(KN_SMALL, cholinv_kernel<<<nk, 128, smem, s>>>(d_G, M, d_Y, d_status));
-            rotate_set(d_Y, M);
-        }
+    // S-orthonormalization and Rayleigh-Ritz in one rotation: U = L^{-H} from
+    // X^H S X = L L^H, Ritz pairs of U^H (X^H H X) U, then X <- X U Y.
+    void orth_rr() {
+        gram(1, vs(oV, M), vs(oSV, M), d_G);
+        size_t smem = (size_t)M * M * sizeof(double2);
+        cuda(smem_limit_once((const void *)cholinv_kernel, h->device, h->smem_optin));
+        MB_LAUNCH_E(KN_SMALL, cholinv_kernel<<<nk, 128, smem, s>>>(d_G, M, d_U, d_status));
+        gram(1, vs(oV, M), vs(oHV, M), d_G2);
+        small_gemm(d_G2, d_U, d_T, M, 0);     // (X^H H X) U
+        small_gemm(d_U, d_T, d_G, M, 1);      // U^H (X^H H X) U
+        jacobi(1, M, false, M);
+        small_gemm(d_U, d_Y, d_T, M, 0);      // U Y
+        rotate_set(d_T, M);
+        MB_LAUNCH_E(KN_SMALL, take_evals_kernel<<<(M * nk + 127) / 128, 128, 0, s>>>(d_evals, M, nk, d_eps));
     }
     void cycle_B() {
         residuals_and_seeds(nblk);
         copy(nblk, vs(oV, b, b), vs(oVB, b, mB), 0);
         copy(nblk, vs(oHV, b, b), vs(oHVB, b, mB), 0);
-        copy(nblk, vs(oSV, b, b), vs(oSVB, b, mB), 0);
         krylov(nblk, oVB + b, oSVB + b, oHVB + b, mB);
         gram(nblk, vs(oVB, mB, mB), vs(oHVB, mB, mB), d_G);
         jacobi(nblk, mB, true, b);
@@ -898,17 +1031,46 @@ struct Solver {
         MB_LAUNCH_E(KN_SMALL, select_kernel<<<(np + 31) / 32, 32, 0, s>>>(d_evals, d_Y, mB, b, M, nblk, np, d_eps, d_Ysel));
         combine(nblk, vs(oVB, mB, mB), vs(oV, b, b), d_Ysel, 1.0, 0.0);
         combine(nblk, vs(oHVB, mB, mB), vs(oHV, b, b), d_Ysel, 1.0, 0.0);
-        combine(nblk, vs(oSVB, mB, mB), vs(oSV, b, b), d_Ysel, 1.0, 0.0);
+        bandS(oV, oSV, M);
     }
 };
 
 }  // namespace
 
+namespace {
+// The solve runs on a private non-blocking stream (capturable, unlike the
+// legacy default stream) that first waits for the caller's stream.
+struct SolveStream {
+    cudaStream_t s = nullptr;
+    cudaError_t err = cudaSuccess;
+    SolveStream(cudaStream_t caller) {
+        err = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (err != cudaSuccess) return;
+        cudaEvent_t ev;
+        err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (err != cudaSuccess) return;
+        err = cudaEventRecord(ev, caller);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    ~SolveStream() {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    }
+};
+}  // namespace
+
 int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void *evecs,
-             const mb_solve_opts *so, mb_solve_info *info, cudaStream_t s) {
+             const mb_solve_opts *so, mb_solve_info *info, cudaStream_t caller) {
     auto t0 = std::chrono::steady_clock::now();
     if (!evals || nbands < 1 || !(tol > 0.0)) return MB_EINVAL;
     if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return MB_EINVAL;
+    if (cudaSetDevice(h->device) != cudaSuccess) return MB_ECUDA;
+    SolveStream stream(caller);       // declared before the solver: its workspace is freed on it first
+    if (stream.err != cudaSuccess) return cuda_fail(h, stream.err);
+    cudaStream_t s = stream.s;
     Solver S;
     S.h = h;
     S.s = s;
@@ -969,6 +1131,9 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     S.d_G = S.alloc<double2>((size_t)nprob * LD * LD);
     S.d_Y = S.alloc<double2>((size_t)nprob * LD * LD);
     S.d_Ysel = S.alloc<double2>((size_t)nprob * LD * LD);
+    S.d_U = S.alloc<double2>((size_t)S.nk * LD * LD);
+    S.d_G2 = S.alloc<double2>((size_t)S.nk * LD * LD);
+    S.d_T = S.alloc<double2>((size_t)S.nk * LD * LD);
     S.part_cap = (size_t)std::max(2 * h->num_sms, nprob) * JMAX * JMAX;
     S.d_part = S.alloc<double2>(S.part_cap);
     S.d_evals = S.alloc<double>((size_t)nprob * LD);
@@ -993,8 +1158,21 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
         S.cuda(cudaMemcpyAsync(S.kd_host[k].base, X0.data(), sizeof(double2) * X0.size(), cudaMemcpyHostToDevice, s));
         S.cuda(cudaStreamSynchronize(s));
     }
-    const bool mixed = prec != MB_FP64;
     S.prec = prec;
+    // the apply scratch is sized up front for every batch this solve issues,
+    // so that nothing allocates while a grand cycle is being captured
+    {
+        size_t need = 0;
+        const int sizes[3] = {1, S.nc, S.nc_stage()};
+        for (int pi = 0; pi < 2; ++pi)
+            for (int bi = 0; bi < 3; ++bi)
+                need = std::max(need, apply_scratch_bytes(h, S.nk, sizes[bi], pi == 0 ? MB_FP64 : MB_FP32));
+        S.cuda(cudaStreamSynchronize(s));
+        if (S.rc == MB_OK) {
+            int r2 = ensure_scratch(h, need);
+            if (r2) return r2;
+        }
+    }
     S.applyH(S.oV, S.oHV, S.M, S.prec);
     S.bandS(S.oV, S.oSV, S.M);
     S.rr_full(false);
@@ -1003,31 +1181,69 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     double last = 1e300, prev = 1e300, maxres = 1e300;
     int cycles = 0;
     bool converged = false;
-    for (cycles = 1; cycles <= max_cycles && !S.rc; ++cycles) {
-        S.krylov(1, S.oV + S.M, S.oSV + S.M, S.oHV + S.M, 0);      // cycle A
+    // One grand cycle: A (Krylov space of the worst root + Rayleigh-Ritz on
+    // all roots), B (per-block Krylov spaces, Rayleigh-Ritz, maximum-overlap
+    // selection), S-orthonormalization + Rayleigh-Ritz, residuals and seeds.
+    auto cycle_body = [&]() {
+        S.krylov(1, S.oV + S.M, S.oSV + S.M, S.oHV + S.M, 0);
         S.rr_full(true);
-        S.cycle_B();                                                // cycle B
-        S.cholqr();
-        S.rr_full(false);
+        S.cycle_B();
+        // Krylov vectors may come from reduced-precision applies: in the
+        // finish phase the roots' HX is recomputed in FP64 first, so the
+        // Rayleigh-Ritz values and the residual test below are FP64
+        if (S.fp64_roots) S.applyH(S.oV, S.oHV, S.M, MB_FP64);
+        S.orth_rr();
         S.residuals_and_seeds(1);
+    };
+    // From the second cycle of each apply precision on, a cycle is one CUDA
+    // graph launch (captured once); the host only reads the residuals.
+    const bool use_graphs = !h->profiling;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int applies_per_cycle[2] = {0, 0};
+    int cur_gi = -1, plain_left = 0;
+    auto conv_max = [&]() {
+        double mx = 0.0;
+        for (int k = 0; k < S.nk; ++k)
+            for (int i = 0; i < S.Mconv; ++i) {
+                double r = res[(size_t)k * S.M + i];
+                mx = std::max(mx, r == r ? r : 1e300);
+            }
+        return mx;
+    };
+    for (cycles = 1; cycles <= max_cycles && !S.rc; ++cycles) {
+        const int gi = (S.prec == MB_FP64 || S.fp64_roots) ? 1 : 0;
+        if (gi != cur_gi) {
+            cur_gi = gi;
+            plain_left = 1;
+        }
+        if (!use_graphs || plain_left > 0) {
+            cycle_body();
+            --plain_left;
+        } else {
+            if (!gexec[gi]) {
+                cudaGraph_t graph = nullptr;
+                const int before = S.applies;
+                S.cuda(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                cycle_body();
+                applies_per_cycle[gi] = S.applies - before;
+                S.applies = before;
+                cudaError_t e = cudaStreamEndCapture(s, &graph);
+                S.cuda(e);
+                if (S.rc == MB_OK) S.cuda(cudaGraphInstantiate(&gexec[gi], graph, 0));
+                if (graph) cudaGraphDestroy(graph);
+            }
+            if (S.rc == MB_OK) S.cuda(cudaGraphLaunch(gexec[gi], s));
+            S.applies += applies_per_cycle[gi];
+        }
         S.cuda(cudaMemcpyAsync(res.data(), S.d_res, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, s));
         S.cuda(cudaStreamSynchronize(s));
         if (S.rc) break;
-        auto conv_max = [&]() {
-            double mx = 0.0;
-            for (int k = 0; k < S.nk; ++k)
-                for (int i = 0; i < S.Mconv; ++i) {
-                    double r = res[(size_t)k * S.M + i];
-                    mx = std::max(mx, r == r ? r : 1e300);
-                }
-            return mx;
-        };
         maxres = conv_max();
-        if (S.prec != MB_FP64) {
+        if (S.prec != MB_FP64 && !S.fp64_roots) {
             bool stalled = cycles > 3 && maxres > 0.7 * prev;
             if (maxres < 30.0 * tol || stalled) {
-                // switch the applies to FP64: fresh HX, SX, Ritz rotation
-                S.prec = MB_FP64;
+                // finish phase: the roots get FP64 HX from here on
+                S.fp64_roots = true;
                 S.applyH(S.oV, S.oHV, S.M, MB_FP64);
                 S.bandS(S.oV, S.oSV, S.M);
                 S.rr_full(false);
@@ -1039,12 +1255,13 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
         }
         prev = last;
         last = maxres;
-        if (S.prec == MB_FP64 && maxres < tol) {
+        if ((S.prec == MB_FP64 || S.fp64_roots) && maxres < tol) {
             converged = true;
             break;
         }
     }
-    (void)mixed;
+    for (auto &g : gexec)
+        if (g) cudaGraphExecDestroy(g);
     if (S.rc) return S.rc;
     std::vector<double> eps((size_t)S.nk * S.M);
     S.cuda(cudaMemcpyAsync(eps.data(), S.d_eps, sizeof(double) * eps.size(), cudaMemcpyDeviceToHost, s));

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <complex>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/mb.h"
@@ -77,6 +79,9 @@ struct mb_handle {
     void *d_desc = nullptr;          // descriptor arrays for batched launches
     size_t desc_bytes = 0;
     std::string last_cuda_error;
+    // plane-kernel launch shapes picked by mb_autotune: (k-points per batch,
+    // bands, FP64?) -> (largest bands per CTA, resident-CTA waves)
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
     // launch accounting (always on) and optional per-kernel event timing
     long long launches = 0;
     bool profiling = false;
@@ -123,5 +128,6 @@ void prof_end(mb_handle *h, cudaStream_t s, int kernel, cudaEvent_t a);
 int prof_collect(mb_handle *h);
 
 int cuda_fail(mb_handle *h, cudaError_t e);
+cudaError_t smem_limit_once(const void *func, int device, int bytes);
 
 }  // namespace mb

@@ -87,8 +87,11 @@ __device__ __forceinline__ void fft_reg(C (&x)[N]) {
     }
 }
 
+// FP32 grids with both sides <= 32 run two CTAs per SM (the host plan sizes
+// shared memory for that); the register budget follows.
 template <typename R, int N1, int N2>
-__global__ void __launch_bounds__(256) plane_reg_kernel(const __grid_constant__ PlaneArgs<R> a) {
+__global__ void __launch_bounds__(256, (N1 <= 32 && N2 <= 32 && sizeof(R) == 4) ? 2 : 1)
+    plane_reg_kernel(const __grid_constant__ PlaneArgs<R> a) {
     typedef typename V2<R>::T C;
     constexpr int LDP = N2 + 1;
     constexpr int PS = N1 * LDP;
@@ -139,13 +142,28 @@ __global__ void __launch_bounds__(256) plane_reg_kernel(const __grid_constant__ 
         }
     };
 
+    // per-group plane metadata: band and Gauss point of each plane, and its B values
+    int *pl_b = reinterpret_cast<int *>(acc + (size_t)a.bt * K * a.ldg_max);
+    int *pl_s = pl_b + a.np;
+    R *bqs = reinterpret_cast<R *>(pl_s + a.np + (a.np & 1));   // np x 8 (keeps 8-byte alignment)
+    const unsigned rmagic = d.rows_magic;
+
     for (int t = t0; t < t1; ++t) {
+        const int slot0 = (t - 1 + K) % K;      // ring slot of row t-1
         for (int p0 = 0; p0 < nplanes; p0 += a.np) {
             const int npl = min(a.np, nplanes - p0);
-            // zero the occupied rows (empty rows are masked in the column pass)
-            for (int e = threadIdx.x; e < npl * nrows * N2; e += blockDim.x) {
-                int pl = e / (nrows * N2), r = (e / N2) % nrows, col = e % N2;
-                planes[(size_t)pl * PS + rows[r] * LDP + col] = czero<C>();
+            if (threadIdx.x < npl) {
+                const int p = p0 + threadIdx.x, bb = p / P, s = p - bb * P;
+                pl_b[threadIdx.x] = bb;
+                pl_s[threadIdx.x] = s;
+#pragma unroll
+                for (int m = 0; m < 8; ++m) bqs[threadIdx.x * 8 + m] = m < K ? a.Bq[(size_t)(t * P + s) * K + m] : R(0);
+            }
+            // zero the planes of the group (16-byte stores)
+            {
+                float4 *z = reinterpret_cast<float4 *>(planes);
+                const int n16 = (int)((size_t)npl * PS * sizeof(C) / 16);
+                for (int e = threadIdx.x; e < n16; e += blockDim.x) z[e] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             __syncthreads();
             // (a) B-spline evaluation of every plane of the group
@@ -155,7 +173,7 @@ __global__ void __launch_bounds__(256) plane_reg_kernel(const __grid_constant__ 
                 int cur_b = -1;
                 C x[8];
                 for (int pl = 0; pl < npl; ++pl) {
-                    const int p = p0 + pl, bb = p / P, s = p - bb * P;
+                    const int bb = pl_b[pl];
                     if (bb != cur_b) {
                         cur_b = bb;
                         const C *X = reinterpret_cast<const C *>(d.X) + (size_t)(b0 + bb) * band_stride;
@@ -165,18 +183,18 @@ __global__ void __launch_bounds__(256) plane_reg_kernel(const __grid_constant__ 
                             x[m] = (m < K && j >= 0 && j < nb) ? X[(size_t)j * ldg + g] : czero<C>();
                         }
                     }
-                    const R *bq = a.Bq + (size_t)(t * P + s) * K;
                     C psi = czero<C>();
 #pragma unroll
                     for (int m = 0; m < 8; ++m)
-                        if (m < K) rfma(psi, bq[m], x[m]);
+                        if (m < K) rfma(psi, bqs[pl * 8 + m], x[m]);
                     planes[(size_t)pl * PS + op] = psi;
                 }
             }
             __syncthreads();
             // (b1) inverse transform of the occupied rows
             for (int e = threadIdx.x; e < npl * nrows; e += blockDim.x) {
-                int pl = e / nrows, r = rows[e % nrows];
+                const int pl = __umulhi((unsigned)e, rmagic);
+                const int r = rows[e - pl * nrows];
                 C *line = planes + (size_t)pl * PS + r * LDP;
                 C v[N2];
 #pragma unroll
@@ -188,14 +206,12 @@ __global__ void __launch_bounds__(256) plane_reg_kernel(const __grid_constant__ 
             __syncthreads();
             // (b2, c, d1) column: inverse transform, w_q V / (N1 N2), forward transform
             for (int e = threadIdx.x; e < npl * N2; e += blockDim.x) {
-                int pl = e / N2, col = e % N2;
-                const int p = p0 + pl, s = p % P;
+                const int pl = e / N2, col = e % N2;
                 C *line = planes + (size_t)pl * PS + col;
-                const R *V = a.Vn + (size_t)(t * P + s) * NN + col;
+                const R *V = a.Vn + (size_t)(t * P + pl_s[pl]) * NN + col;
                 C v[N1];
-                const unsigned long long rm = d.rowmask;
 #pragma unroll
-                for (int i = 0; i < N1; ++i) v[i] = ((rm >> i) & 1ull) ? line[i * LDP] : czero<C>();
+                for (int i = 0; i < N1; ++i) v[i] = line[i * LDP];
                 fft_reg<N1, true>(v);
 #pragma unroll
                 for (int i = 0; i < N1; ++i) v[i] = rscale(__ldg(V + i * N2), v[i]);
@@ -206,7 +222,8 @@ __global__ void __launch_bounds__(256) plane_reg_kernel(const __grid_constant__ 
             __syncthreads();
             // (d2) forward transform of the rows that hold disc points
             for (int e = threadIdx.x; e < npl * nrows; e += blockDim.x) {
-                int pl = e / nrows, r = rows[e % nrows];
+                const int pl = __umulhi((unsigned)e, rmagic);
+                const int r = rows[e - pl * nrows];
                 C *line = planes + (size_t)pl * PS + r * LDP;
                 C v[N2];
 #pragma unroll
@@ -220,22 +237,34 @@ __global__ void __launch_bounds__(256) plane_reg_kernel(const __grid_constant__ 
             for (int g = threadIdx.x; g < ng; g += blockDim.x) {
                 const int o = goff[g];
                 const int op = o + o / N2;
-                int pl = 0;
-                while (pl < npl) {
-                    const int p = p0 + pl, bb = p / P;
-                    const int s_end = min(P, (p0 + npl) - bb * P);   // planes of this band in the group
-                    const int s_beg = p - bb * P;
+                C sum[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) sum[m] = czero<C>();
+                int cur = pl_b[0];
+                auto flush = [&](int bb) {
 #pragma unroll
                     for (int m = 0; m < 8; ++m) {
-                        int j = t + m - 1;
-                        if (m >= K || j < 0 || j >= nb) continue;
-                        C sum = czero<C>();
-                        for (int s = s_beg; s < s_end; ++s)
-                            rfma(sum, a.Bq[(size_t)(t * P + s) * K + m], planes[(size_t)(pl + s - s_beg) * PS + op]);
-                        acc[((size_t)bb * K + (j % K)) * ldg + g] += sum;
+                        const int j = t + m - 1;
+                        if (m < K && j >= 0 && j < nb) {
+                            int sl = slot0 + m;
+                            if (sl >= K) sl -= K;
+                            acc[((size_t)bb * K + sl) * ldg + g] += sum[m];
+                        }
+                        sum[m] = czero<C>();
                     }
-                    pl += s_end - s_beg;
+                };
+                for (int pl = 0; pl < npl; ++pl) {
+                    const int bb = pl_b[pl];
+                    if (bb != cur) {
+                        flush(cur);
+                        cur = bb;
+                    }
+                    const C v = planes[(size_t)pl * PS + op];
+#pragma unroll
+                    for (int m = 0; m < 8; ++m)
+                        if (m < K) rfma(sum[m], bqs[pl * 8 + m], v);
                 }
+                flush(cur);
             }
             __syncthreads();
         }
@@ -256,8 +285,12 @@ template <typename R> bool plane_reg_supported(int n1, int n2) {
 
 template <typename R, int N1, int N2>
 static cudaError_t launch_one(const PlaneArgs<R> &a, unsigned grid, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(plane_reg_kernel<R, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaError_t e = smem_limit_once((const void *)plane_reg_kernel<R, N1, N2>, dev, optin);
     if (e != cudaSuccess) return e;
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
     plane_reg_kernel<R, N1, N2><<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -1,7 +1,28 @@
 // Launch accounting and optional per-kernel CUDA-event timing.
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "mb_internal.h"
 
 namespace mb {
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` (the device's
+// opt-in maximum) minus its static shared memory, once per (kernel, device)
+// instead of on every launch.
+cudaError_t smem_limit_once(const void *func, int device, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(func, device);
+    if (done.count(key)) return cudaSuccess;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
 
 const char *const kKernelNames[KN_COUNT] = {
     "plane", "epilogue", "proj", "coef", "backproj", "banded", "gram", "combine",

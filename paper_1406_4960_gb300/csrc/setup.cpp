@@ -371,13 +371,15 @@ void vtable_natural(const mb_handle *h, std::vector<double> &out) {
 }
 
 // Banded Cholesky factors of T(G) + c S = D/2 + (|k+G|^2/2 + c) S for every
-// G of k-point ik: out[g][j][d] = L[j][j-d].
+// G of k-point ik, stored G-fastest: out[(j*K + d)*ldg + g] = L_G[j][j-d].
 void precond_factors(const mb_handle *h, int ik, double shift, std::vector<double> &out) {
     const int K = h->order, W = 2 * K - 1, nb = h->nb;
     const KPoint &kp = h->kp[ik];
-    out.assign((size_t)kp.ldg * nb * K, 0.0);
+    const size_t ldg = kp.ldg;
+    out.assign(ldg * nb * K, 0.0);
+    std::vector<double> L((size_t)nb * K);
     for (int g = 0; g < kp.ldg; ++g) {
-        double *L = &out[(size_t)g * nb * K];
+        std::fill(L.begin(), L.end(), 0.0);
         double qq = g < kp.ng ? 0.5 * kp.q2[g] + shift : shift;
         for (int j = 0; j < nb; ++j) {
             for (int d = K - 1; d >= 0; --d) {
@@ -393,6 +395,8 @@ void precond_factors(const mb_handle *h, int ik, double shift, std::vector<doubl
                     L[(size_t)j * K + d] = s / L[(size_t)i * K];
             }
         }
+        for (int j = 0; j < nb; ++j)
+            for (int d = 0; d < K; ++d) out[((size_t)j * K + d) * ldg + g] = L[(size_t)j * K + d];
     }
 }
 

@@ -22,7 +22,8 @@ EXPORTS = ("mb_setup", "mb_destroy", "mb_sizes", "mb_gvectors", "mb_zplanes",
            "mb_set_local_potential", "mb_apply_H", "mb_apply_H_batch", "mb_apply_S",
            "mb_apply_Sinv", "mb_eigsolve", "mb_strerror", "mb_last_cuda_error",
            "mb_set_profiling", "mb_profile_read", "mb_profile_reset", "mb_launch_count",
-           "mb_kernel_name", "mb_apply_H_noalloc")
+           "mb_kernel_name", "mb_apply_H_noalloc", "mb_server_create", "mb_server_submit",
+           "mb_server_wait", "mb_server_stats", "mb_server_destroy", "mb_autotune")
 
 
 class MBError(RuntimeError):
@@ -49,6 +50,14 @@ class _Opts(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("applies", ctypes.c_int),
                 ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("cell", _Cell), ("kpts", ctypes.POINTER(ctypes.c_double)), ("nk", ctypes.c_int),
+                ("ecut", ctypes.c_double), ("breaks", ctypes.POINTER(ctypes.c_double)),
+                ("nbreaks", ctypes.c_int), ("order", ctypes.c_int), ("atoms", ctypes.POINTER(_Atom)),
+                ("natoms", ctypes.c_int), ("opts", _Opts), ("nbands", ctypes.c_int),
+                ("tol", ctypes.c_double), ("prec", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -101,6 +110,13 @@ def load(build_if_missing: bool = False):
     lib.mb_launch_count.argtypes = [vp]
     lib.mb_launch_count.restype = ctypes.c_longlong
     lib.mb_apply_H_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.mb_server_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(vp)]
+    lib.mb_server_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_longlong)]
+    lib.mb_server_wait.argtypes = [vp, ctypes.c_longlong, dp, ctypes.POINTER(SolveInfo), dp, ctypes.c_double]
+    lib.mb_server_stats.argtypes = [vp, ip, ip, ip, dp, dp]
+    lib.mb_server_destroy.argtypes = [vp]
+    lib.mb_server_destroy.restype = None
+    lib.mb_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, ip, ip, dp]
     lib.mb_kernel_name.argtypes = [ctypes.c_int]
     lib.mb_kernel_name.restype = ctypes.c_char_p
     _lib = lib
@@ -115,6 +131,75 @@ def _stream_ptr(stream):
     if stream is None:
         return None
     return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _atoms_array(atoms):
+    arr = (_Atom * max(1, len(atoms)))()
+    for i, at in enumerate(atoms):
+        arr[i].pos = (ctypes.c_double * 3)(*at.pos)
+        arr[i].A = at.A
+        arr[i].w = at.w
+        arr[i].nproj = at.nproj
+        arr[i].E = (ctypes.c_double * 4)(*at.E)
+        arr[i].rc = at.rc
+    return arr
+
+
+class Server:
+    """The continuous-batching solve server (mb_server_*)."""
+
+    def __init__(self, device=0, slots=4, hbm_budget_bytes=64e9):
+        self._lib = load()
+        s = ctypes.c_void_p()
+        rc = self._lib.mb_server_create(int(device), int(slots), float(hbm_budget_bytes), ctypes.byref(s))
+        if rc:
+            raise MBError(rc, "mb_server_create")
+        self._s = s
+        self._meta = {}
+
+    def submit(self, w, nbands, tol=1e-6, prec="fp32", max_bands=128):
+        kp = np.ascontiguousarray(np.asarray(w.kpts, dtype=np.float64).reshape(-1, 2))
+        br = np.ascontiguousarray(np.asarray(w.breaks, dtype=np.float64))
+        atoms = _atoms_array(w.atoms)
+        req = _Request(_Cell((ctypes.c_double * 2)(*w.a1), (ctypes.c_double * 2)(*w.a2)),
+                       _dptr(kp), kp.shape[0], float(w.ecut), _dptr(br), len(br), int(w.order),
+                       atoms, len(w.atoms),
+                       _Opts(int(w.grid[0]), int(w.grid[1]), int(w.nquad), 0, int(max_bands), 0.0),
+                       int(nbands), float(tol), PREC[prec] if isinstance(prec, str) else int(prec))
+        t = ctypes.c_longlong()
+        rc = self._lib.mb_server_submit(self._s, ctypes.byref(req), ctypes.byref(t))
+        if rc:
+            raise MBError(rc, "mb_server_submit")
+        self._meta[t.value] = (kp.shape[0], int(nbands))
+        return t.value
+
+    def wait(self, ticket, timeout_s=0.0):
+        nk, nb = self._meta.pop(ticket)
+        ev = np.zeros(nk * nb)
+        info = SolveInfo()
+        lat = ctypes.c_double()
+        rc = self._lib.mb_server_wait(self._s, ticket, _dptr(ev), ctypes.byref(info), ctypes.byref(lat),
+                                      float(timeout_s))
+        return rc, ev.reshape(nk, nb), info, lat.value
+
+    def stats(self):
+        q, r, pr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        b, pb = ctypes.c_double(), ctypes.c_double()
+        self._lib.mb_server_stats(self._s, ctypes.byref(q), ctypes.byref(r), ctypes.byref(pr),
+                                  ctypes.byref(b), ctypes.byref(pb))
+        return {"queued": q.value, "running": r.value, "peak_running": pr.value,
+                "bytes_in_use": b.value, "peak_bytes": pb.value}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            self._lib.mb_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Handle:
@@ -248,6 +333,12 @@ class Handle:
         self._check(self._lib.mb_apply_Sinv(self._h, ik, ctypes.c_void_p(X.data_ptr()),
                                             ctypes.c_void_p(Y.data_ptr()), X.shape[0],
                                             self._prec(prec), _stream_ptr(stream)), "mb_apply_Sinv")
+
+    def autotune(self, nbands, prec="fp32"):
+        bt, waves, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self._lib.mb_autotune(self._h, int(nbands), self._prec(prec), ctypes.byref(bt),
+                                          ctypes.byref(waves), ctypes.byref(ms)), "mb_autotune")
+        return {"bands_per_cta": bt.value, "waves": waves.value, "ms": ms.value}
 
     def eigsolve(self, nbands, tol, prec="fp64", evecs=None, krylov_depth=0, block=0,
                  max_cycles=0, polish=0, stream=None, allow_notconv=False, guard=0):

@@ -255,11 +255,36 @@ def serve_stream(n: int = 256, rate_hz: float = 50.0, seed: int = 4) -> List[Req
     for i in range(n):
         t += rng.exponential(1.0 / rate_hz)
         base = bases[int(rng.integers(0, 3))]
-        nz = int(rng.integers(40, 161))
+        nz = int(rng.integers(40, 161))    # retained B-splines
         m = int(rng.integers(8, 81))
         nk = int(rng.integers(1, 9))
         out.append(Request(t, base, nz, m, nk, 1000 + i))
     return out
+
+
+def random_kpoints(a1, a2, nk: int, seed: int) -> np.ndarray:
+    """Seeded k-points uniform in the first cell of the reciprocal lattice."""
+    b1, b2 = reciprocal(a1, a2)
+    rng = np.random.default_rng(seed)
+    u = rng.random((nk, 2)) - 0.5
+    return u[:, :1] * b1[None, :] + u[:, 1:] * b2[None, :]
+
+
+def request_workload(r: Request) -> Workload:
+    """The slab problem of a served request: its base workload with the
+    request's z resolution (Nz retained B-splines), band count and k-points."""
+    base = BY_NAME[r.base]()
+    nb = max(r.n_int, base.order + 1)
+    n_int = nb - base.order + 3
+    if r.base == "slab":
+        try:
+            breaks = slab_geometric_breaks(n_int)
+        except ValueError:
+            breaks = uniform_breaks(-15.0, 15.0, n_int)
+    else:
+        breaks = uniform_breaks(float(base.breaks[0]), float(base.breaks[-1]), n_int)
+    return dataclasses.replace(base, name="req-%s" % r.base, breaks=breaks, nbands=r.nbands,
+                               kpts=random_kpoints(base.a1, base.a2, r.nk, r.seed))
 
 
 BY_NAME = {"tiny": tiny, "slab": slab, "graphene": graphene, "kbatch": kbatch}
