@@ -197,6 +197,80 @@ def eig_bench(h, w, args):
     return out
 
 
+def kbatch_bench(mb, W, local, args):
+    """Batched k-points: the 2x2 graphene cell with 64 wedge k-points x 24 bands.
+    The plane-kernel launch shape is autotuned for the batch, then one FP32 H
+    apply of all 64 k-points (one launch sequence) is timed; with
+    --kbatch-solve, one mixed-precision eigensolve of all 64 k-points (grand
+    cycles replayed as CUDA graphs) is timed too."""
+    import torch
+    w = W.kbatch()
+    h = mb.Handle.from_workload(w, device=local)
+    tune = h.autotune(w.nbands, "fp32")
+    iks = list(range(w.nk))
+    Xs, Ys = [], []
+    for ik in iks:
+        ng, nb, ldg = h.sizes(ik)
+        Xs.append(torch.from_numpy(W.random_block(w.nbands, nb, ng, seed=700 + ik, ld=ldg)).to(torch.complex64).cuda())
+        Ys.append(torch.zeros_like(Xs[-1]))
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        h.apply_H_batch(iks, Xs, Ys, "fp32", stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = 10
+    for _ in range(reps):
+        h.apply_H_batch(iks, Xs, Ys, "fp32", stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    byts, flops = workload_sizes(h, w, "fp32")
+    out = {"workload": "kbatch: 2x2 graphene, Ecut 30 Ha, 32x32 grid, 100 B-splines, 64 k x 24 bands",
+           "autotune": tune, "apply_ms": ms, "apply_gbs": byts / (ms * 1e-3) / 1e9,
+           "plane_tflops_algorithmic": None}
+    if args.kbatch_solve:
+        t0 = time.perf_counter()
+        ev, info = h.eigsolve(w.nbands, 1e-6, "fp32")
+        out["eigsolve"] = {"seconds": time.perf_counter() - t0, "cycles": info.cycles,
+                           "max_residual": info.max_residual}
+    h.close()
+    return out
+
+
+def serve_bench(mb, W, local, args):
+    """The serving stream: Poisson arrivals (50/s) of slab solves drawn from
+    the tiny/slab/graphene workloads (Nz 40-160, 8-80 bands, 1-8 k-points),
+    mixed precision, replayed in real time into the continuous-batching
+    server; a bounded sample of the first --serve-n requests."""
+    import torch
+    reqs = W.serve_stream()[:args.serve_n]
+    free, total = torch.cuda.mem_get_info(local)
+    budget = 0.7 * free
+    srv = mb.Server(device=local, slots=args.serve_slots, hbm_budget_bytes=budget)
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        dt = r.arrival_s - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(W.request_workload(r), r.nbands, 1e-6, "fp32"))
+    lats, bad = [], 0
+    for t in tickets:
+        rc, ev, info, lat = srv.wait(t)
+        bad += rc != 0
+        lats.append(lat)
+    elapsed = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    la = np.array(lats) * 1e3
+    return {"sample": "first %d requests of the 256-request stream" % len(reqs),
+            "slots": args.serve_slots, "hbm_budget_gb": budget / 1e9,
+            "solves_per_s": len(reqs) / elapsed, "p50_ms": float(np.percentile(la, 50)),
+            "p99_ms": float(np.percentile(la, 99)), "failed": int(bad),
+            "peak_running": st["peak_running"], "peak_gb": st["peak_bytes"] / 1e9}
+
+
 def _blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -390,6 +464,10 @@ def run_ours(args):
     }
     if not args.no_eig:
         line["eigsolve"] = eig_bench(h, w, args)
+    if not args.no_kbatch:
+        line["kbatch"] = kbatch_bench(mb, W, local, args)
+    if not args.no_serve:
+        line["serve"] = serve_bench(mb, W, local, args)
     if rank == 0 and world == 1 and not args.no_cpu:
         gbs, cores, sample, secs, n = cpu_baseline(w, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
@@ -411,6 +489,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-eig", action="store_true")
     ap.add_argument("--eig-only", action="store_true")
+    ap.add_argument("--no-kbatch", action="store_true")
+    ap.add_argument("--kbatch-solve", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-n", type=int, default=12)
+    ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--eig-reps", type=int, default=6)
     args = ap.parse_args()
     if args.warmup < 3:

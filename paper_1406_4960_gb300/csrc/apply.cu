@@ -433,6 +433,11 @@ static int upload_set(mb_handle *h, DevTables &t) {
     if ((rc = upload<R>(h, &t.Sband, h->Sb))) return rc;
     if ((rc = upload<R>(h, &t.Dband, h->Db))) return rc;
     if ((rc = upload<R>(h, &t.Lband, h->Lb))) return rc;
+    {
+        std::vector<double> lr(h->Lb);
+        for (int j = 0; j < h->nb; ++j) lr[(size_t)j * h->order] = 1.0 / lr[(size_t)j * h->order];
+        if ((rc = upload<R>(h, &t.Lrecip, lr))) return rc;
+    }
     std::vector<double> q2((size_t)h->total_ldg, 0.0);
     std::vector<cdouble> qp;
     for (size_t ik = 0; ik < h->kp.size(); ++ik) {
@@ -494,7 +499,7 @@ int upload_tables(mb_handle *h) {
     MB_CUDA(cudaMemcpy(h->d_rows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
     upload_fft_twiddles();
     MB_CUDA(cudaGetLastError());
-    return MB_OK;
+    return upload_proj_tables(h);
 }
 
 int ensure_precond(mb_handle *h) {
@@ -513,7 +518,7 @@ int ensure_precond(mb_handle *h) {
 }
 
 static void free_set(DevTables &t) {
-    void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.q2, &t.qproj, &t.zproj, &t.E, &t.Pfac};
+    void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.Lrecip, &t.q2, &t.qproj, &t.zproj, &t.E, &t.Pfac};
     for (void **p : ps) {
         if (*p) cudaFree(*p);
         *p = nullptr;
@@ -528,6 +533,10 @@ void free_tables(mb_handle *h) {
     h->d_goff = nullptr;
     if (h->d_rows) cudaFree(h->d_rows);
     h->d_rows = nullptr;
+    if (h->d_projB) cudaFree(h->d_projB);
+    h->d_projB = nullptr;
+    if (h->d_tcerr) cudaFree(h->d_tcerr);
+    h->d_tcerr = nullptr;
     if (h->scratch.ptr) cudaFree(h->scratch.ptr);
     h->scratch = Scratch();
 }
@@ -617,9 +626,12 @@ size_t apply_scratch_bytes(const mb_handle *h, int nsel_max, int nbands, int pre
     return (size_t)nsel * per_k_scratch(h, maxldg, nbands, p.nchunks, c2);
 }
 
+cudaError_t proj_tc_launch(mb_handle *h, int mode, int nsel, const int *iks, const KDesc *desc, int nbands,
+                           cudaStream_t s);
+
 template <typename R>
 static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y,
-                          int nbands, cudaStream_t s, const DevTables &t, char *base);
+                          int nbands, cudaStream_t s, const DevTables &t, char *base, bool tensor = false);
 
 // Scratch bytes one batched apply needs (boundary rows, projector overlaps W
 // and coefficients C for every k-point of the group).
@@ -634,10 +646,10 @@ static size_t apply_H_need(const mb_handle *h, int nsel, const int *iks, int nba
 
 template <typename R>
 static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y,
-                         int nbands, cudaStream_t s, const DevTables &t) {
+                         int nbands, cudaStream_t s, const DevTables &t, bool tensor = false) {
     int rc = ensure_scratch(h, apply_H_need<R>(h, nsel, iks, nbands));
     if (rc) return rc;
-    return apply_H_launch<R>(h, nsel, iks, X, Y, nbands, s, t, reinterpret_cast<char *>(h->scratch.ptr));
+    return apply_H_launch<R>(h, nsel, iks, X, Y, nbands, s, t, reinterpret_cast<char *>(h->scratch.ptr), tensor);
 }
 
 // Scratch need of a single-k-point apply, and the apply itself on a scratch
@@ -652,12 +664,13 @@ int apply_H_on_scratch(mb_handle *h, int ik, const void *X, void *Y, int nbands,
     void *ys[1] = {Y};
     return prec == MB_FP64
                ? apply_H_launch<double>(h, 1, &ik, xs, ys, nbands, s, h->t64, reinterpret_cast<char *>(scratch))
-               : apply_H_launch<float>(h, 1, &ik, xs, ys, nbands, s, h->t32, reinterpret_cast<char *>(scratch));
+               : apply_H_launch<float>(h, 1, &ik, xs, ys, nbands, s, h->t32, reinterpret_cast<char *>(scratch),
+                                       prec == MB_BF16);
 }
 
 template <typename R>
 static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y,
-                          int nbands, cudaStream_t s, const DevTables &t, char *base) {
+                          int nbands, cudaStream_t s, const DevTables &t, char *base, bool tensor) {
     typedef typename V2<R>::T R2;
     const size_t c2 = sizeof(R2);
     KDesc desc[kMaxK];
@@ -700,7 +713,13 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         ga.nproj = h->nproj;
         std::copy(desc, desc + nsel, ga.d);
         dim3 grid((nbands * h->nb + 63) / 64, (h->nproj + 63) / 64, nsel);
-        MB_LAUNCH(h, s, KN_PROJ, zgemm_kernel<R><<<grid, 256, 0, s>>>(ga));
+        if (tensor) {
+            cudaError_t e = cudaSuccess;
+            MB_LAUNCH(h, s, KN_PROJ, e = proj_tc_launch(h, 0, nsel, iks, desc, nbands, s));
+            MB_CUDA(e);
+        } else {
+            MB_LAUNCH(h, s, KN_PROJ, zgemm_kernel<R><<<grid, 256, 0, s>>>(ga));
+        }
         CoefArgs<R> ca;
         ca.zproj = reinterpret_cast<const R *>(t.zproj);
         ca.E = reinterpret_cast<const R *>(t.E);
@@ -765,7 +784,13 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         ga.nproj = h->nproj;
         std::copy(desc, desc + nsel, ga.d);
         dim3 grid((nbands * h->nb + 63) / 64, (maxldg + 63) / 64, nsel);
-        MB_LAUNCH(h, s, KN_BACKPROJ, zgemm_kernel<R><<<grid, 256, 0, s>>>(ga));
+        if (tensor) {
+            cudaError_t e = cudaSuccess;
+            MB_LAUNCH(h, s, KN_BACKPROJ, e = proj_tc_launch(h, 1, nsel, iks, desc, nbands, s));
+            MB_CUDA(e);
+        } else {
+            MB_LAUNCH(h, s, KN_BACKPROJ, zgemm_kernel<R><<<grid, 256, 0, s>>>(ga));
+        }
     }
     MB_CUDA(cudaGetLastError());
     return MB_OK;
@@ -784,7 +809,8 @@ int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X, 
     for (int i0 = 0; i0 < nsel; i0 += kMaxK) {
         int n = std::min(kMaxK, nsel - i0);
         int rc = prec == MB_FP64 ? apply_H_group<double>(h, n, iks + i0, X + i0, Y + i0, nbands, s, h->t64)
-                                 : apply_H_group<float>(h, n, iks + i0, X + i0, Y + i0, nbands, s, h->t32);
+                                 : apply_H_group<float>(h, n, iks + i0, X + i0, Y + i0, nbands, s, h->t32,
+                                                        prec == MB_BF16);
         if (rc) return rc;
     }
     return MB_OK;

@@ -497,6 +497,7 @@ __global__ void eig_banded_solve_kernel(const EigK *ks, const double *Lb, int pe
         for (int j = 0; j < nb; ++j) y[(size_t)j * ldg + g] = make_double2(0.0, 0.0);
         return;
     }
+    // factors hold L[j][j-d] for d >= 1 and 1 / L[j][j] at d = 0
     auto L = [&](int j, int dd) -> double {
         return per_g ? d.pfac[((size_t)j * K + dd) * ldg + g] : __ldg(&Lb[(size_t)j * K + dd]);
     };
@@ -509,7 +510,7 @@ __global__ void eig_banded_solve_kernel(const EigK *ks, const double *Lb, int pe
 #pragma unroll
         for (int dd = 1; dd < K; ++dd)
             if (j - dd >= 0) rfma(s, -L(j, dd), win[dd - 1]);
-        const double2 yj = rscale(1.0 / L(j, 0), s);
+        const double2 yj = rscale(L(j, 0), s);
         y[(size_t)j * ldg + g] = yj;
 #pragma unroll
         for (int i = K - 1; i > 0; --i) win[i] = win[i - 1];
@@ -523,7 +524,7 @@ __global__ void eig_banded_solve_kernel(const EigK *ks, const double *Lb, int pe
 #pragma unroll
         for (int dd = 1; dd < K; ++dd)
             if (j + dd < nb) rfma(s, -L(j + dd, dd), win[dd - 1]);
-        const double2 zj = rscale(1.0 / L(j, 0), s);
+        const double2 zj = rscale(L(j, 0), s);
         y[(size_t)j * ldg + g] = zj;
 #pragma unroll
         for (int i = K - 1; i > 0; --i) win[i] = win[i - 1];
@@ -531,89 +532,53 @@ __global__ void eig_banded_solve_kernel(const EigK *ks, const double *Lb, int pe
     }
 }
 
-// A^H w for one vector w per problem (the Gram-Schmidt coefficients): one
-// warp per row i over an n-chunk, warp-shuffle reduction, partials per chunk.
-__global__ void __launch_bounds__(256) gram_mv_kernel(const EigK *ks, int nch, VSet A, VSet B, int nsplit,
-                                                      double2 *part) {
-    const int prob = blockIdx.y, split = blockIdx.x;
-    const int k = prob / nch, ch = prob % nch;
-    const EigK d = ks[k];
-    const int ma = A.count();
-    const long long n = d.nvec;
-    const long long chunk = (n + nsplit - 1) / nsplit;
-    const long long t0 = split * chunk, t1 = min(n, t0 + chunk);
-    const double2 *w = d.base + (long long)B.at(0, ch) * n;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < ma; i += (blockDim.x >> 5)) {
-        const double2 *a = d.base + (long long)A.at(i, ch) * n;
-        double sx = 0.0, sy = 0.0;
-        for (long long t = t0 + lane; t < t1; t += 32) {
-            double2 av = a[t], wv = w[t];
-            sx = fma(av.x, wv.x, fma(av.y, wv.y, sx));
-            sy = fma(av.x, wv.y, fma(-av.y, wv.x, sy));
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-            sx += __shfl_down_sync(0xffffffffu, sx, off);
-            sy += __shfl_down_sync(0xffffffffu, sy, off);
-        }
-        if (lane == 0) part[((size_t)prob * nsplit + split) * ma + i] = make_double2(sx, sy);
-    }
-}
-
-// A^H B with every output owned by one thread (up to GF_R per thread, output
-// slices over blockIdx.z), n-tiles of GF_T staged in shared memory as
-// [t][column]; no padded outputs, so every FP64 FMA is useful.
-constexpr int GF_T = 32, GF_R = 8;
-__global__ void __launch_bounds__(256) gram_flat_kernel(const EigK *ks, int nch, VSet A, VSet B, int nsplit,
-                                                        double2 *part) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int prob = blockIdx.y, split = blockIdx.x;
+// A^H B, one warp per row i and up to GJ columns: the lanes stride over an
+// n-chunk with coalesced loads, each holding GJ complex partial sums in
+// registers, then reduce them by warp shuffles.  Grid: (n-chunks, problems,
+// row groups of 8 x column groups of GJ).
+constexpr int GJ = 16;
+__global__ void __launch_bounds__(256) gram_rows_kernel(const EigK *ks, int nch, VSet A, VSet B, int nsplit,
+                                                        int colgroups, double2 *part) {
+    const int split = blockIdx.x, prob = blockIdx.y;
+    const int rg = blockIdx.z / colgroups, cg = blockIdx.z % colgroups;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
     const int ma = A.count(), mb = B.count();
-    double2 *As = reinterpret_cast<double2 *>(sm);      // [GF_T][ma]
-    double2 *Bs = As + GF_T * ma;                       // [GF_T][mb]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = rg * 8 + warp;
+    const int j0 = cg * GJ, nj = min(GJ, mb - j0);
+    if (i >= ma || nj <= 0) return;                     // whole warp leaves together
     const long long n = d.nvec;
-    const long long chunk = ((n + nsplit - 1) / nsplit + GF_T - 1) / GF_T * GF_T;
+    const long long chunk = (n + nsplit - 1) / nsplit;
     const long long t0 = split * chunk, t1 = min(n, t0 + chunk);
-    const int nout = ma * mb;
-    const int obase = blockIdx.z * GF_R * 256;
-    int oi[GF_R], oj[GF_R];
-    double2 acc[GF_R];
+    const double2 *a = d.base + (long long)A.at(i, ch) * n;
+    const double2 *bp[GJ];
 #pragma unroll
-    for (int r = 0; r < GF_R; ++r) {
-        const int o = obase + threadIdx.x + r * 256;
-        oi[r] = o < nout ? o / mb : -1;
-        oj[r] = o < nout ? o - (o / mb) * mb : 0;
-        acc[r] = make_double2(0.0, 0.0);
-    }
-    for (long long tb = t0; tb < t1; tb += GF_T) {
-        for (int e = threadIdx.x; e < GF_T * ma; e += blockDim.x) {
-            const int i = e / GF_T, tt = e % GF_T;
-            const long long t = tb + tt;
-            As[tt * ma + i] = t < t1 ? d.base[(long long)A.at(i, ch) * n + t] : make_double2(0.0, 0.0);
-        }
-        for (int e = threadIdx.x; e < GF_T * mb; e += blockDim.x) {
-            const int j = e / GF_T, tt = e % GF_T;
-            const long long t = tb + tt;
-            Bs[tt * mb + j] = t < t1 ? d.base[(long long)B.at(j, ch) * n + t] : make_double2(0.0, 0.0);
-        }
-        __syncthreads();
-        for (int tt = 0; tt < GF_T; ++tt) {
+    for (int jj = 0; jj < GJ; ++jj) bp[jj] = d.base + (long long)B.at(j0 + (jj < nj ? jj : 0), ch) * n;
+    double sx[GJ], sy[GJ];
 #pragma unroll
-            for (int r = 0; r < GF_R; ++r) {
-                if (oi[r] < 0) continue;
-                const double2 a = As[tt * ma + oi[r]], b = Bs[tt * mb + oj[r]];
-                acc[r].x = fma(a.x, b.x, fma(a.y, b.y, acc[r].x));
-                acc[r].y = fma(a.x, b.y, fma(-a.y, b.x, acc[r].y));
+    for (int jj = 0; jj < GJ; ++jj) sx[jj] = sy[jj] = 0.0;
+    for (long long t = t0 + lane; t < t1; t += 32) {
+        const double2 av = a[t];
+#pragma unroll
+        for (int jj = 0; jj < GJ; ++jj) {
+            if (jj < nj) {
+                const double2 bv = bp[jj][t];
+                sx[jj] = fma(av.x, bv.x, fma(av.y, bv.y, sx[jj]));
+                sy[jj] = fma(av.x, bv.y, fma(-av.y, bv.x, sy[jj]));
             }
         }
-        __syncthreads();
     }
-    double2 *out = part + ((size_t)prob * nsplit + split) * nout;
 #pragma unroll
-    for (int r = 0; r < GF_R; ++r)
-        if (oi[r] >= 0) out[oi[r] * mb + oj[r]] = acc[r];
+    for (int jj = 0; jj < GJ; ++jj) {
+        if (jj >= nj) break;
+        double x = sx[jj], y = sy[jj];
+        for (int off = 16; off > 0; off >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, off);
+            y += __shfl_down_sync(0xffffffffu, y, off);
+        }
+        if (lane == 0) part[((size_t)prob * nsplit + split) * ma * mb + (size_t)i * mb + j0 + jj] = make_double2(x, y);
+    }
 }
 
 // C_j = beta C_j + alpha sum_i A_i Y[i][j]: one element t per thread, JC
@@ -849,20 +814,13 @@ struct Solver {
     void gram(int nch, VSet A, VSet B, double2 *G) {
         const int nprob = nk * nch;
         const int ma = A.count(), mbc = B.count();
-        if (mbc == 1) {
-            int nsplit = std::max(1, std::min(64, (4 * h->num_sms + nprob - 1) / nprob));
-            while ((size_t)nprob * nsplit * ma > part_cap && nsplit > 1) --nsplit;
-            MB_LAUNCH_E(KN_GRAM, gram_mv_kernel<<<dim3(nsplit, nprob), 256, 0, s>>>(d_k, nch, A, B, nsplit, d_part));
-            MB_LAUNCH_E(KN_GRAM, gram_reduce_kernel<<<nprob, 128, 0, s>>>(d_part, nsplit, ma, 1, G));
-            return;
-        }
-        const int slices = (ma * mbc + GF_R * 256 - 1) / (GF_R * 256);
-        int nsplit = std::max(1, std::min(256, (4 * h->num_sms + nprob * slices - 1) / (nprob * slices)));
+        const int rowgroups = (ma + 7) / 8, colgroups = (mbc + GJ - 1) / GJ;
+        const int per_split = nprob * rowgroups * colgroups;
+        int nsplit = std::max(1, std::min(512, (8 * h->num_sms + per_split - 1) / per_split));
+        nsplit = std::min<long long>(nsplit, std::max<long long>(1, nmax / 256));   // >= 256 elements per chunk
         while ((size_t)nprob * nsplit * ma * mbc > part_cap && nsplit > 1) --nsplit;
-        const size_t smem = (size_t)GF_T * (ma + mbc) * sizeof(double2);
-        if (smem > 48 * 1024) cuda(smem_limit_once((const void *)gram_flat_kernel, h->device, h->smem_optin));
-        MB_LAUNCH_E(KN_GRAM, gram_flat_kernel<<<dim3(nsplit, nprob, slices), 256, smem, s>>>(d_k, nch, A, B, nsplit,
-                                                                                           d_part));
+        MB_LAUNCH_E(KN_GRAM, gram_rows_kernel<<<dim3(nsplit, nprob, rowgroups * colgroups), 256, 0, s>>>(
+                                 d_k, nch, A, B, nsplit, colgroups, d_part));
         MB_LAUNCH_E(KN_GRAM, gram_reduce_kernel<<<nprob, 256, 0, s>>>(d_part, nsplit, ma, mbc, G));
     }
     void combine(int nch, VSet A, VSet C, const double2 *Y, double alpha, double beta) {
@@ -898,7 +856,7 @@ struct Solver {
     }
     void bandSolve(int per_g, int src, int dst, int nv) {
         const dim3 grid((maxldg + 63) / 64, 1, nk * nv);
-        const double *Lb = (const double *)h->t64.Lband;
+        const double *Lb = (const double *)h->t64.Lrecip;
         switch (h->order) {
 #define MB_BL(KK) case KK: MB_LAUNCH_E(KN_BANDED, eig_banded_solve_kernel<KK><<<grid, 64, 0, s>>>(d_k, Lb, per_g, h->nb, src, dst, nv)); break;
             MB_BL(3) MB_BL(4) MB_BL(5) MB_BL(6) MB_BL(7) MB_BL(8)

@@ -35,6 +35,7 @@ struct DevTables {
     void *Sband = nullptr;   // nb x (2 order - 1): S[j][j+d], d = -(order-1)..order-1
     void *Dband = nullptr;   // same layout for D = <B'|B'>
     void *Lband = nullptr;   // nb x order: Cholesky L[j][j-d], d = 0..order-1
+    void *Lrecip = nullptr;  // the same with 1 / L[j][j] at d = 0 (eigensolver's solves)
     void *q2 = nullptr;      // all k, concatenated with kofs
     void *qproj = nullptr;   // all k: nproj x ldg each, offset qofs[k]
     void *zproj = nullptr;   // nproj x nb
@@ -71,6 +72,9 @@ struct mb_handle {
     int total_ldg = 0;
     int *d_goff = nullptr;           // all k (int), offset kofs
     int *d_rows = nullptr;           // occupied grid rows of every k, offset rows_ofs[k]
+    void *d_projB = nullptr;         // BF16 projector tables for the tensor-core contractions
+    void *d_tcerr = nullptr;         // status word of the tensor-core kernels' bounded waits
+    std::vector<int> pb0_ofs, pb1_ofs, pb0_ld, pb1_ld;
     std::vector<int> rows_ofs, nrows;
     std::vector<unsigned long long> rowmask;
     mb::DevTables t64, t32;
@@ -128,6 +132,7 @@ void prof_end(mb_handle *h, cudaStream_t s, int kernel, cudaEvent_t a);
 int prof_collect(mb_handle *h);
 
 int cuda_fail(mb_handle *h, cudaError_t e);
+int upload_proj_tables(mb_handle *h);
 cudaError_t smem_limit_once(const void *func, int device, int bytes);
 
 }  // namespace mb

@@ -371,7 +371,8 @@ void vtable_natural(const mb_handle *h, std::vector<double> &out) {
 }
 
 // Banded Cholesky factors of T(G) + c S = D/2 + (|k+G|^2/2 + c) S for every
-// G of k-point ik, stored G-fastest: out[(j*K + d)*ldg + g] = L_G[j][j-d].
+// G of k-point ik, stored G-fastest: out[(j*K + d)*ldg + g] = L_G[j][j-d]
+// for d >= 1 and 1 / L_G[j][j] for d = 0.
 void precond_factors(const mb_handle *h, int ik, double shift, std::vector<double> &out) {
     const int K = h->order, W = 2 * K - 1, nb = h->nb;
     const KPoint &kp = h->kp[ik];
@@ -395,8 +396,10 @@ void precond_factors(const mb_handle *h, int ik, double shift, std::vector<doubl
                     L[(size_t)j * K + d] = s / L[(size_t)i * K];
             }
         }
+        // stored with the reciprocal of the diagonal (the solves multiply by it)
         for (int j = 0; j < nb; ++j)
-            for (int d = 0; d < K; ++d) out[((size_t)j * K + d) * ldg + g] = L[(size_t)j * K + d];
+            for (int d = 0; d < K; ++d)
+                out[((size_t)j * K + d) * ldg + g] = d == 0 ? 1.0 / L[(size_t)j * K] : L[(size_t)j * K + d];
     }
 }
 

@@ -226,3 +226,30 @@ def test_invalid_arguments_are_rejected(mbmod):
     with pytest.raises(mbmod.MBError):
         h.set_local_potential(np.full((len(zq), 16, 16), np.nan))
     h.close()
+
+
+@pytest.mark.parametrize("case", ["slab-small", "graphene-small"])
+def test_apply_bf16_projector_contraction_on_tensor_cores(mbmod, case):
+    """MB_BF16 runs both projector contractions on the tensor cores (tcgen05,
+    BF16 operands, FP32 accumulation).  Its projector part, isolated as
+    H X - H_{E=0} X, matches the FP32 path to the BF16 bound: operands
+    rounded to 8 significant bits (relative 2^-9 each), two contractions ->
+    about 4 * 2^-9 = 8e-3 of the largest projector term; 2e-2 is asserted."""
+    w = CASES[case]()
+    w0 = dataclasses.replace(w, atoms=[dataclasses.replace(a, E=(0.0, 0.0, 0.0, 0.0)) for a in w.atoms])
+    h = mbmod.Handle.from_workload(w)
+    h0 = mbmod.Handle.from_workload(w0)
+    for ik in range(w.nk):
+        ng, nb, ldg = h.sizes(ik)
+        X = torch.from_numpy(W.random_block(w.nbands, nb, ng, seed=60 + ik, ld=ldg)).to(torch.complex64).cuda()
+        Y32, Y16, Yloc = (torch.zeros_like(X) for _ in range(3))
+        h.apply_H(ik, X, Y32, "fp32")
+        h.apply_H(ik, X, Y16, "bf16")
+        h0.apply_H(ik, X, Yloc, "fp32")
+        torch.cuda.synchronize()
+        nl32, nl16 = Y32 - Yloc, Y16 - Yloc
+        scale = nl32.abs().max().item()
+        assert scale > 0
+        assert (nl16 - nl32).abs().max().item() <= 2e-2 * scale, (ik, (nl16 - nl32).abs().max().item() / scale)
+    h.close()
+    h0.close()

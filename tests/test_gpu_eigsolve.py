@@ -126,3 +126,26 @@ def test_eigsolve_rejects_bad_arguments(mbmod):
     with pytest.raises(mbmod.MBError):
         h.eigsolve(120, 1e-6)         # with guards beyond the largest subspace
     h.close()
+
+
+def _golden_slab():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "slab_eigs.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return np.array(rows, dtype=float)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_eigsolve_full_slab_matches_oracle_golden(mbmod, prec):
+    """The full slab workload (4 k-points, 32 roots, ~4k plane waves x 114
+    splines) in the launch configuration the benchmark times, against the
+    oracle's own Lanczos-Krylov eigenvalues (written by
+    golden/make_slab_eigs.py, residual < 1e-9)."""
+    w = W.slab()
+    ref = _golden_slab()
+    assert ref.shape == (w.nk, w.nbands)
+    h = mbmod.Handle.from_workload(w)
+    ev, info = h.eigsolve(w.nbands, 1e-6, prec)
+    assert info.max_residual < 1e-6
+    assert np.abs(ev - ref).max() < EV_TOL, np.abs(ev - ref).max()
+    h.close()
