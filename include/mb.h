@@ -175,7 +175,7 @@ typedef struct {
 
 typedef struct {
     int krylov_depth;     /* k of K = span{v, A v, ..., A^k v} (0: 4) */
-    int block;            /* roots per block in the second grand cycle (0: 4) */
+    int block;            /* roots per block in the second grand cycle (0: 1) */
     int max_cycles;       /* (0: 200) */
     int polish;           /* reserved (0) */
     int guard;            /* extra roots carried above the requested ones
@@ -202,7 +202,9 @@ int mb_eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals,
  * apply of `nbands` bands at all k-points of the handle, on scratch blocks
  * it allocates, and keeps the fastest for later applies and eigensolves of
  * that shape.  Set-up time call (allocates; not during stream capture).
- * Outputs may be NULL. */
+ * best_waves = 0 means the built-in wave model chose the run length (CTA
+ * count rounded to whole waves of resident CTAs); > 0, a target of that many
+ * CTAs per resident slot.  Outputs may be NULL. */
 int mb_autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves,
                 double *best_ms);
 

@@ -8,11 +8,12 @@
 //                 output rows that the current interval touches in a ring in
 //                 shared memory; rows shared with a neighbouring run go to
 //                 scratch and are summed in a fixed order by the epilogue.
-//  epilogue       kinetic term Eq. (9) (banded in j, diagonal in G) plus the
-//                 boundary-row sums.
-//  zgemm          projector contractions of Eq. (17), factorized as
-//                 u_p(G, j) = z_p(j) q_p(G): W = X q^H, then
-//                 Y += (z E F) q with F_p = sum_j z_p(j) W_p(j).
+//  epilogue       kinetic term Eq. (9) (banded in j, diagonal in G), the
+//                 boundary-row sums and the back-projection of Eq. (17).
+//  nl_zx/nl_coef  projector overlaps of Eq. (17) through the factorized
+//                 projectors u_p(G, j) = z_p(j) q_p(G), one j-contraction per
+//                 distinct z factor (the tensor-core variant, tc_gemm.cu,
+//                 contracts the unfactorized (band, j) x G block instead).
 //  banded_*       S (Eqs. (7)-(8)), S^-1 and the eigensolver's
 //                 preconditioner through banded Cholesky factors.
 #include <algorithm>
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(256) plane_kernel(const __grid_constant__ Plan
     R2 *Y = reinterpret_cast<R2 *>(d.Y) + (size_t)b * nb * ldg;
     R2 *part = reinterpret_cast<R2 *>(d.part) + (size_t)b * (a.nchunks - 1) * 2 * (K - 1) * ldg;
     const int *goff = a.goff + d.kofs;
-    const int t0 = c * a.chunk, t1 = min(a.nint, t0 + a.chunk);
+    const int t0 = chunk_begin(c, a.nint, a.nchunks), t1 = chunk_begin(c + 1, a.nint, a.nchunks);
 
     for (int i = threadIdx.x; i < K * ldg; i += blockDim.x) acc[i] = czero<R2>();
     __syncthreads();
@@ -167,137 +168,221 @@ __global__ void __launch_bounds__(256) plane_kernel(const __grid_constant__ Plan
 }
 
 // ---------------------------------------------------------------------------
-// epilogue: Y[j] = local(j) + (D/2 + |k+G|^2/2 S) X   (Eq. (9))
-template <typename R> struct EpiArgs {
-    const R *Sband, *Dband, *q2;
-    int order, nb, nbands, nchunks, chunk, nint;
+// Kleinman-Bylander term of Eq. (17) with the factorized projectors
+// u_p(G, j) = z_p(j) q_p(G).  The z factor is shared by many projectors
+// (s, p_x and p_y of one atom; all atoms at one height and radius), so with
+// f(p) the distinct z factor of projector p:
+//   Zx[b][f][G] = sum_j z_f(j) X[b][j][G]                  (nl_zx)
+//   c_p(b)      = E_p sum_G conj(q_p(G)) Zx[b][f(p)][G]     (nl_coef)
+//   Y[b][j][G] += sum_f z_f(j) sum_{p: f(p)=f} c_p(b) q_p(G) (in the epilogue)
+// which is sum_p E_p u_p (u_p^H X) with nb*nz + nproj (not nb*nproj)
+// multiply-adds per (band, G).
+template <typename R> struct NlArgs {
+    const R *zf;                    // nz x nb distinct z factors
+    const R *E;                     // nproj
+    const int *pgroup;              // nproj: f(p)
+    const typename V2<R>::T *Q;     // q_p(G), all k (offset qofs)
+    int nb, nbands, nproj, nz, nseg;
     KDesc d[kMaxK];
 };
 
-template <typename R>
-__global__ void __launch_bounds__(256) epilogue_kernel(const __grid_constant__ EpiArgs<R> a) {
+// Zx for 64 consecutive G of one (band, k-point): threadIdx.y takes one run
+// of rows j, and the runs' partial sums are added in run order through
+// shared memory.
+template <typename R, int NZB>
+__global__ void __launch_bounds__(512) nl_zx_kernel(const __grid_constant__ NlArgs<R> a) {
     typedef typename V2<R>::T R2;
-    const int j = blockIdx.x, b = blockIdx.y, ks = blockIdx.z;
-    const KDesc &d = a.d[ks];
-    const int K = a.order, W = 2 * K - 1, ldg = d.ldg, nb = a.nb;
-    const R2 *X = reinterpret_cast<const R2 *>(d.X) + (size_t)b * nb * ldg;
-    R2 *Y = reinterpret_cast<R2 *>(d.Y) + (size_t)b * nb * ldg;
-    const R2 *part = reinterpret_cast<const R2 *>(d.part) + (size_t)b * (a.nchunks - 1) * 2 * (K - 1) * ldg;
-    // boundary c between runs c and c+1 covers rows [t1 - 1, t1 + K - 3], t1 = (c+1)*chunk
-    int bc = -1, br = 0;
-    for (int c = 0; c + 1 < a.nchunks; ++c) {
-        int t1 = (c + 1) * a.chunk;
-        if (j >= t1 - 1 && j <= t1 + K - 3) { bc = c; br = j - (t1 - 1); }
-    }
-    const R *q2 = a.q2 + d.kofs;
-    const R *Sr = a.Sband + (size_t)j * W;
-    const R *Dr = a.Dband + (size_t)j * W;
-    for (int g = threadIdx.x; g < ldg; g += blockDim.x) {
-        if (g >= d.ng) { Y[(size_t)j * ldg + g] = czero<R2>(); continue; }
-        R2 v;
-        if (bc >= 0) {
-            const R2 *p0 = part + ((size_t)(bc * 2 + 0) * (K - 1) + br) * ldg;
-            const R2 *p1 = part + ((size_t)(bc * 2 + 1) * (K - 1) + br) * ldg;
-            v = p0[g] + p1[g];
-        } else {
-            v = Y[(size_t)j * ldg + g];
+    extern __shared__ __align__(16) unsigned char nsm[];
+    R2 *red = reinterpret_cast<R2 *>(nsm);                  // nseg x 64
+    R *zs = reinterpret_cast<R *>(red + a.nseg * 64);      // nz x nb
+    const int tx = threadIdx.x, seg = threadIdx.y;
+    const int tid = seg * 64 + tx, nthr = 64 * a.nseg;
+    const int g = blockIdx.x * 64 + tx, b = blockIdx.y;
+    const KDesc &d = a.d[blockIdx.z];
+    const int ldg = d.ldg, nb = a.nb;
+    for (int e = tid; e < a.nz * nb; e += nthr) zs[e] = a.zf[e];
+    __syncthreads();
+    const int j0 = (seg * nb) / a.nseg, j1 = ((seg + 1) * nb) / a.nseg, nr = j1 - j0;
+    const bool live = g < d.ng;
+    const R2 *X = reinterpret_cast<const R2 *>(d.X) + ((size_t)b * nb + j0) * ldg + g;
+    R2 *Z = reinterpret_cast<R2 *>(d.W) + (size_t)b * a.nz * ldg + g;
+    for (int f0 = 0; f0 < a.nz; f0 += NZB) {
+        R2 acc[NZB];
+#pragma unroll
+        for (int f = 0; f < NZB; ++f) acc[f] = czero<R2>();
+        if (live) {
+            int j = 0;
+            for (; j + 4 <= nr; j += 4) {
+                R2 x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = X[(size_t)(j + u) * ldg];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int f = 0; f < NZB; ++f)
+                        if (f0 + f < a.nz) rfma(acc[f], zs[(f0 + f) * nb + j0 + j + u], x[u]);
+            }
+            for (; j < nr; ++j) {
+                const R2 x = X[(size_t)j * ldg];
+#pragma unroll
+                for (int f = 0; f < NZB; ++f)
+                    if (f0 + f < a.nz) rfma(acc[f], zs[(f0 + f) * nb + j0 + j], x);
+            }
         }
-        const R hq = R(0.5) * q2[g];
-        R2 tx = czero<R2>();
-        for (int dd = 0; dd < W; ++dd) {
-            int jj = j + dd - (K - 1);
-            if (jj < 0 || jj >= nb) continue;
-            R coef = R(0.5) * Dr[dd] + hq * Sr[dd];
-            rfma(tx, coef, X[(size_t)jj * ldg + g]);
+#pragma unroll
+        for (int f = 0; f < NZB; ++f) {
+            if (f0 + f >= a.nz) break;
+            red[seg * 64 + tx] = acc[f];
+            __syncthreads();
+            if (seg == 0 && live) {
+                R2 t = red[tx];
+                for (int sg = 1; sg < a.nseg; ++sg) t = t + red[sg * 64 + tx];
+                Z[(size_t)(f0 + f) * ldg] = t;
+            }
+            __syncthreads();
         }
-        Y[(size_t)j * ldg + g] = v + tx;
     }
 }
 
+// one warp per (band, k-point, projector); the sum over G runs in a fixed order
+template <typename R>
+__global__ void __launch_bounds__(256) nl_coef_kernel(const __grid_constant__ NlArgs<R> a) {
+    typedef typename V2<R>::T R2;
+    const int b = blockIdx.x;
+    const KDesc &d = a.d[blockIdx.y];
+    const int p = blockIdx.z * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (p >= a.nproj) return;
+    const int ldg = d.ldg;
+    const R2 *z = reinterpret_cast<const R2 *>(d.W) + ((size_t)b * a.nz + a.pgroup[p]) * ldg;
+    const R2 *q = a.Q + d.qofs + (size_t)p * ldg;
+    R2 s = czero<R2>();
+#pragma unroll 4
+    for (int g = lane; g < d.ng; g += 32) {
+        const R2 qg = q[g];
+        cfma(s, mk(qg.x, -qg.y), z[g]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        s.x += __shfl_down_sync(0xffffffffu, s.x, off);
+        s.y += __shfl_down_sync(0xffffffffu, s.y, off);
+    }
+    if (lane == 0) reinterpret_cast<R2 *>(d.C)[(size_t)b * a.nproj + p] = rscale(a.E[p], s);
+}
+
 // ---------------------------------------------------------------------------
-// complex GEMM, batched over k-points:
-//   mode 0 (projection):      W[m][n] = sum_k A[m][k] conj(Q[n][k])   A = X rows, Q = q_p(G)
-//   mode 1 (back-projection): Y[m][n] += sum_k C[m][k] Q[k][n]        C = coefficients
-// m = (band, j) rows; 64x64 output tile, 256 threads, 4x4 outputs each.
-template <typename R> struct GemmArgs {
-    const typename V2<R>::T *Q;   // q_p(G) table (all k)
-    int mode, nb, nbands, nproj;
+// epilogue: Y[j] = local(j) + (D/2 + |k+G|^2/2 S) X (Eq. (9)) + KB term.
+// One thread per (band, G, run of rows j); the local part comes from Y (rows
+// inside one plane-kernel run) or from the two boundary partials (rows shared
+// by neighbouring runs), added in a fixed order.  `base` = 0 runs only the KB
+// term for the distinct z factors [f0, f1) (when there are more than NZB).
+template <typename R> struct EpiArgs {
+    const R *Sband, *Dband, *q2;
+    const R *zf;                    // nz x nb
+    const int *zstart, *zlist;      // projectors of each distinct z factor
+    const typename V2<R>::T *Q;     // q_p(G)
+    int order, nb, nbands, nchunks, nint, nproj, f0, f1, base, njseg;
     KDesc d[kMaxK];
 };
 
-template <typename R>
-__global__ void __launch_bounds__(256) zgemm_kernel(const __grid_constant__ GemmArgs<R> a) {
+// HW = largest half-width of the band (order - 1) the instance handles: X
+// rows j-HW .. j+HW stay in registers and one new row is loaded per output
+// row (the next one is in flight while the current row is computed).
+template <typename R, int NZB, int HW>
+__global__ void __launch_bounds__(64) epilogue_kernel(const __grid_constant__ EpiArgs<R> a) {
     typedef typename V2<R>::T R2;
-    constexpr int BM = 64, BN = 64, BK = 16;
-    __shared__ R2 As[BK][BM + 1];
-    __shared__ R2 Bs[BK][BN + 1];
-    const int ks = blockIdx.z;
-    const KDesc &d = a.d[ks];
-    const int ldg = d.ldg;
-    const int M = a.nbands * a.nb;
-    const int N = a.mode == 0 ? a.nproj : d.ng;
-    const int KK = a.mode == 0 ? d.ng : a.nproj;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    if (n0 >= N) return;
-    const R2 *Q = a.Q + d.qofs;
-    const R2 *A = a.mode == 0 ? reinterpret_cast<const R2 *>(d.X) : reinterpret_cast<const R2 *>(d.C);
-    const int lda = a.mode == 0 ? ldg : a.nproj;
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    R2 acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int jn = 0; jn < 4; ++jn) acc[i][jn] = czero<R2>();
-    for (int k0 = 0; k0 < KK; k0 += BK) {
-        for (int e = threadIdx.x; e < BM * BK; e += 256) {
-            int mm = e / BK, kk = e % BK;
-            int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < KK) ? A[(size_t)gm * lda + gk] : czero<R2>();
-        }
-        for (int e = threadIdx.x; e < BN * BK; e += 256) {
-            int nn, kk;
-            R2 v = czero<R2>();
-            if (a.mode == 0) {   // B[k][n] = conj(Q[n][k])
-                nn = e / BK; kk = e % BK;
-                int gn = n0 + nn, gk = k0 + kk;
-                if (gn < N && gk < KK) { R2 q = Q[(size_t)gn * ldg + gk]; v = mk(q.x, -q.y); }
-            } else {             // B[k][n] = Q[k][n]
-                kk = e / BN; nn = e % BN;
-                int gn = n0 + nn, gk = k0 + kk;
-                if (gn < N && gk < KK) v = Q[(size_t)gk * ldg + gn];
-            }
-            Bs[kk][nn] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            R2 av[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) bv[i] = Bs[kk][tx * 4 + i];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int jn = 0; jn < 4; ++jn) cfma(acc[i][jn], av[i], bv[jn]);
-        }
-        __syncthreads();
+    constexpr int WW = 2 * HW + 1;
+    extern __shared__ __align__(16) unsigned char esm[];
+    const int b = blockIdx.y / a.njseg, js = blockIdx.y % a.njseg;
+    const KDesc &d = a.d[blockIdx.z];
+    const int K = a.order, W = 2 * K - 1, ldg = d.ldg, nb = a.nb;
+    const int j0 = (js * nb) / a.njseg, j1 = ((js + 1) * nb) / a.njseg, nr = j1 - j0;
+    const int nf = a.f1 - a.f0;
+    // band rows of S and D/2 (zero-padded to WW entries) and the z factors
+    R2 *cs = reinterpret_cast<R2 *>(esm);                 // nproj: c_p(b)
+    R *cS = reinterpret_cast<R *>(cs + a.nproj);
+    R *cD = cS + nr * WW;
+    R *zs = cD + nr * WW;
+    int *zl = reinterpret_cast<int *>(zs + nf * nr);      // projectors of each factor, then the list offsets
+    for (int e = threadIdx.x; e < nr * WW; e += blockDim.x) {
+        const int rr = e / WW, o = e % WW - HW;            // offset o = jj - j
+        const int dd = o + K - 1;
+        const bool in = dd >= 0 && dd < W;
+        cS[e] = in ? a.Sband[(size_t)(j0 + rr) * W + dd] : R(0);
+        cD[e] = in ? R(0.5) * a.Dband[(size_t)(j0 + rr) * W + dd] : R(0);
     }
+    for (int e = threadIdx.x; e < nf * nr; e += blockDim.x) zs[e] = a.zf[(size_t)(a.f0 + e / nr) * nb + j0 + e % nr];
+    if (nf > 0) {
+        for (int e = threadIdx.x; e < a.nproj; e += blockDim.x) {
+            cs[e] = reinterpret_cast<const R2 *>(d.C)[(size_t)b * a.nproj + e];
+            zl[e] = a.zlist[e];
+        }
+        for (int e = threadIdx.x; e <= nf; e += blockDim.x) zl[a.nproj + e] = a.zstart[a.f0 + e];
+    }
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ldg) return;
+    R2 *Y = reinterpret_cast<R2 *>(d.Y) + (size_t)b * nb * ldg + g;
+    if (g >= d.ng) {
+        if (a.base)
+            for (int j = j0; j < j1; ++j) Y[(size_t)j * ldg] = czero<R2>();
+        return;
+    }
+    // KB: r_f = sum_{p: f(p) = f} c_p(b) q_p(G)
+    R2 r[NZB];
+    const R2 *Qg = a.Q + d.qofs + g;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int gm = m0 + ty * 4 + i;
-        if (gm >= M) continue;
-#pragma unroll
-        for (int jn = 0; jn < 4; ++jn) {
-            int gn = n0 + tx * 4 + jn;
-            if (gn >= N) continue;
-            if (a.mode == 0) {
-                reinterpret_cast<R2 *>(d.W)[(size_t)gm * a.nproj + gn] = acc[i][jn];
-            } else {
-                R2 *y = reinterpret_cast<R2 *>(d.Y) + (size_t)gm * ldg + gn;
-                *y = *y + acc[i][jn];
+    for (int f = 0; f < NZB; ++f) {
+        r[f] = czero<R2>();
+        if (f < nf) {
+#pragma unroll 4
+            for (int i = zl[a.nproj + f]; i < zl[a.nproj + f + 1]; ++i) {
+                const int p = zl[i];
+                cfma(r[f], cs[p], Qg[(size_t)p * ldg]);
             }
         }
+    }
+    const R2 *X = reinterpret_cast<const R2 *>(d.X) + (size_t)b * nb * ldg + g;
+    const R2 *part = reinterpret_cast<const R2 *>(d.part) + (size_t)b * (a.nchunks - 1) * 2 * (K - 1) * ldg + g;
+    const R hq = R(0.5) * a.q2[d.kofs + g];
+    R2 xw[WW];                                           // xw[HW + o] = X[j + o]
+    if (a.base) {
+#pragma unroll
+        for (int i = 0; i < WW; ++i) {
+            const int row = j0 + i - HW;
+            xw[i] = (row >= 0 && row < nb) ? X[(size_t)row * ldg] : czero<R2>();
+        }
+    }
+    // run boundary bc (between runs bc and bc+1) starts at interval t1 and
+    // owns rows [t1 - 1, t1 + K - 3]
+    int bc = 0, t1 = a.nchunks > 1 ? a.nint / a.nchunks : 0;
+    for (int j = j0; j < j1; ++j) {
+        R2 v;
+        if (a.base) {
+            const int rn = j + HW + 1;
+            const R2 nxt = rn < nb ? X[(size_t)rn * ldg] : czero<R2>();
+            while (bc < a.nchunks - 1 && t1 + K - 3 < j) {
+                ++bc;
+                t1 = ((bc + 1) * a.nint) / a.nchunks;
+            }
+            if (bc < a.nchunks - 1 && j >= t1 - 1) {
+                const int br = j - (t1 - 1);
+                v = part[((size_t)(bc * 2 + 0) * (K - 1) + br) * ldg] + part[((size_t)(bc * 2 + 1) * (K - 1) + br) * ldg];
+            } else {
+                v = Y[(size_t)j * ldg];
+            }
+            const R *Sr = cS + (j - j0) * WW;
+            const R *Dr = cD + (j - j0) * WW;
+#pragma unroll
+            for (int i = 0; i < WW; ++i) rfma(v, fma(hq, Sr[i], Dr[i]), xw[i]);
+#pragma unroll
+            for (int i = 0; i + 1 < WW; ++i) xw[i] = xw[i + 1];
+            xw[WW - 1] = nxt;
+        } else {
+            v = Y[(size_t)j * ldg];
+        }
+#pragma unroll
+        for (int f = 0; f < NZB; ++f)
+            if (f < nf) rfma(v, zs[f * nr + (j - j0)], r[f]);
+        Y[(size_t)j * ldg] = v;
     }
 }
 
@@ -448,6 +533,7 @@ static int upload_set(mb_handle *h, DevTables &t) {
     if ((rc = upload<R>(h, &t.q2, q2))) return rc;
     if ((rc = upload_complex<R>(h, &t.qproj, qp))) return rc;
     if ((rc = upload<R>(h, &t.zproj, h->zproj))) return rc;
+    if ((rc = upload<R>(h, &t.zf, h->zfun))) return rc;
     if ((rc = upload<R>(h, &t.E, h->Eproj))) return rc;
     const int nmax = std::max(h->n1, h->n2);
     std::vector<cdouble> tw(nmax / 2);
@@ -497,6 +583,13 @@ int upload_tables(mb_handle *h) {
     }
     MB_CUDA(cudaMalloc(&h->d_rows, rows.size() * sizeof(int)));
     MB_CUDA(cudaMemcpy(h->d_rows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (h->nproj > 0) {
+        std::vector<int> zi(h->pgroup);
+        zi.insert(zi.end(), h->zstart.begin(), h->zstart.end());
+        zi.insert(zi.end(), h->zlist.begin(), h->zlist.end());
+        MB_CUDA(cudaMalloc(&h->d_zidx, zi.size() * sizeof(int)));
+        MB_CUDA(cudaMemcpy(h->d_zidx, zi.data(), zi.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
     upload_fft_twiddles();
     MB_CUDA(cudaGetLastError());
     return upload_proj_tables(h);
@@ -518,7 +611,7 @@ int ensure_precond(mb_handle *h) {
 }
 
 static void free_set(DevTables &t) {
-    void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.Lrecip, &t.q2, &t.qproj, &t.zproj, &t.E, &t.Pfac};
+    void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.Lrecip, &t.q2, &t.qproj, &t.zproj, &t.zf, &t.E, &t.Pfac};
     for (void **p : ps) {
         if (*p) cudaFree(*p);
         *p = nullptr;
@@ -535,6 +628,8 @@ void free_tables(mb_handle *h) {
     h->d_rows = nullptr;
     if (h->d_projB) cudaFree(h->d_projB);
     h->d_projB = nullptr;
+    if (h->d_zidx) cudaFree(h->d_zidx);
+    h->d_zidx = nullptr;
     if (h->d_tcerr) cudaFree(h->d_tcerr);
     h->d_tcerr = nullptr;
     if (h->scratch.ptr) cudaFree(h->scratch.ptr);
@@ -569,7 +664,7 @@ static PlanePlan plan_plane(const mb_handle *h, int nsel, int nbands, size_t c2,
     int ctas_per_sm = 1;
     // defaults, or the shape mb_autotune measured fastest for this batch
     const bool small = h->n1 <= 32 && h->n2 <= 32;
-    int bt_max = small ? 2 : 1, waves = 2;
+    int bt_max = small ? 2 : 1, waves = 0;
     auto it = h->tuned.find(std::make_tuple(nsel, nbands, c2 == 16 ? 1 : 0));
     if (it != h->tuned.end()) {
         bt_max = it->second.first;
@@ -601,29 +696,72 @@ static PlanePlan plan_plane(const mb_handle *h, int nsel, int nbands, size_t c2,
         p.smem = fixed + (size_t)p.np * NN * c2;
     }
     const int pairs = nsel * ((nbands + p.bt - 1) / p.bt);
-    const int want = waves * h->num_sms * ctas_per_sm;
-    const int target = std::max(1, (want + pairs - 1) / pairs);
-    p.chunk = std::max(K, (h->nint + target - 1) / target);
-    if (p.chunk >= h->nint) p.chunk = h->nint;
-    p.nchunks = (h->nint + p.chunk - 1) / p.chunk;
+    const int slots = h->num_sms * ctas_per_sm;
+    const int nmax_chunks = std::max(1, std::min(kMaxChunks, h->nint / K));   // runs of >= K intervals
+    if (waves > 0) {
+        // explicit target: about `waves` CTAs per resident slot
+        const int target = std::max(1, (waves * slots + pairs - 1) / pairs);
+        p.nchunks = std::min(nmax_chunks, target);
+    } else {
+        // wave model: a CTA's time ~ its run length + about one interval of
+        // run overhead (boundary rows); the launch takes ceil(items / slots)
+        // rounds of the longest run
+        double best = 1e300;
+        for (int n = 1; n <= nmax_chunks; ++n) {
+            const long long items = (long long)pairs * n;
+            const long long rounds = (items + slots - 1) / slots;
+            const double cost = (double)rounds * ((h->nint + n - 1) / n + 1.0);
+            if (cost < best - 1e-9) { best = cost; p.nchunks = n; }
+        }
+    }
+    p.chunk = (h->nint + p.nchunks - 1) / p.nchunks;   // longest run
     return p;
 }
 
-static size_t per_k_scratch(const mb_handle *h, int ldg, int nbands, int nchunks, size_t c2) {
-    size_t part = (size_t)nbands * std::max(0, nchunks - 1) * 2 * (h->order - 1) * ldg * c2;
-    size_t w = (size_t)nbands * h->nb * std::max(1, h->nproj) * c2;
-    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    return al(part) + 2 * al(w);
+// Largest j-segment count of the projector overlaps and of the epilogue.
+static int nl_max_seg(const mb_handle *h) { return std::max(1, std::min(8, h->nb / 8)); }
+
+// Scratch regions of one k-point: boundary partial rows; projector overlaps
+// W (Zx[b][f][G] on CUDA cores, W[(b, j)][p] on tensor cores) and
+// coefficients C (c[b][p], or C[(b, j)][p] on tensor cores).
+struct KScratch {
+    size_t part, w, c;
+    size_t total() const { return al(part) + al(w) + al(c); }
+    static size_t al(size_t x) { return (x + 255) / 256 * 256; }
+};
+
+static KScratch per_k_layout(const mb_handle *h, int ldg, int nbands, int nchunks, size_t c2, bool tensor) {
+    KScratch k;
+    k.part = (size_t)nbands * std::max(0, nchunks - 1) * 2 * (h->order - 1) * ldg * c2;
+    if (tensor) {
+        k.w = k.c = (size_t)nbands * h->nb * std::max(1, h->nproj) * c2;
+    } else {
+        k.w = (size_t)nbands * std::max(1, h->nzf) * ldg * c2;
+        k.c = (size_t)nbands * std::max(1, h->nproj) * c2;
+    }
+    return k;
 }
 
-size_t apply_scratch_bytes(const mb_handle *h, int nsel_max, int nbands, int prec) {
-    size_t c2 = prec == MB_FP64 ? 16 : 8;
-    int maxldg = 0;
-    for (auto &k : h->kp) maxldg = std::max(maxldg, k.ldg);
-    int nsel = std::min(nsel_max, kMaxK);
-    bool reg = prec == MB_FP64 ? plane_reg_supported<double>(h->n1, h->n2) : plane_reg_supported<float>(h->n1, h->n2);
-    PlanePlan p = plan_plane(h, nsel, nbands, c2, maxldg, reg);
-    return (size_t)nsel * per_k_scratch(h, maxldg, nbands, p.nchunks, c2);
+static size_t per_k_scratch(const mb_handle *h, int ldg, int nbands, int nchunks, size_t c2, bool tensor) {
+    return per_k_layout(h, ldg, nbands, nchunks, c2, tensor).total();
+}
+
+// Scratch of a batched apply of k-points 0 .. nk-1 in order (the groups of
+// kMaxK that apply_H_batch forms, each planned as it will be launched).
+size_t apply_scratch_bytes(const mb_handle *h, int nk, int nbands, int prec) {
+    const size_t c2 = prec == MB_FP64 ? 16 : 8;
+    const bool reg = prec == MB_FP64 ? plane_reg_supported<double>(h->n1, h->n2)
+                                     : plane_reg_supported<float>(h->n1, h->n2);
+    nk = std::min(nk, (int)h->kp.size());
+    size_t need = 0;
+    for (int i0 = 0; i0 < nk; i0 += kMaxK) {
+        const int nsel = std::min(kMaxK, nk - i0);
+        int maxldg = 0;
+        for (int i = i0; i < i0 + nsel; ++i) maxldg = std::max(maxldg, h->kp[i].ldg);
+        const PlanePlan p = plan_plane(h, nsel, nbands, c2, maxldg, reg);
+        need = std::max(need, (size_t)nsel * per_k_scratch(h, maxldg, nbands, p.nchunks, c2, prec == MB_BF16));
+    }
+    return need;
 }
 
 cudaError_t proj_tc_launch(mb_handle *h, int mode, int nsel, const int *iks, const KDesc *desc, int nbands,
@@ -636,18 +774,18 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
 // Scratch bytes one batched apply needs (boundary rows, projector overlaps W
 // and coefficients C for every k-point of the group).
 template <typename R>
-static size_t apply_H_need(const mb_handle *h, int nsel, const int *iks, int nbands) {
+static size_t apply_H_need(const mb_handle *h, int nsel, const int *iks, int nbands, bool tensor) {
     const size_t c2 = sizeof(typename V2<R>::T);
     int maxldg = 0;
     for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
     const PlanePlan plan = plan_plane(h, nsel, nbands, c2, maxldg, plane_reg_supported<R>(h->n1, h->n2));
-    return (size_t)nsel * per_k_scratch(h, maxldg, nbands, plan.nchunks, c2);
+    return (size_t)nsel * per_k_scratch(h, maxldg, nbands, plan.nchunks, c2, tensor);
 }
 
 template <typename R>
 static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y,
                          int nbands, cudaStream_t s, const DevTables &t, bool tensor = false) {
-    int rc = ensure_scratch(h, apply_H_need<R>(h, nsel, iks, nbands));
+    int rc = ensure_scratch(h, apply_H_need<R>(h, nsel, iks, nbands, tensor));
     if (rc) return rc;
     return apply_H_launch<R>(h, nsel, iks, X, Y, nbands, s, t, reinterpret_cast<char *>(h->scratch.ptr), tensor);
 }
@@ -655,7 +793,8 @@ static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *con
 // Scratch need of a single-k-point apply, and the apply itself on a scratch
 // region supplied by the caller of this function (no allocation here).
 size_t apply_H_scratch_need(const mb_handle *h, int ik, int nbands, int prec) {
-    return prec == MB_FP64 ? apply_H_need<double>(h, 1, &ik, nbands) : apply_H_need<float>(h, 1, &ik, nbands);
+    return prec == MB_FP64 ? apply_H_need<double>(h, 1, &ik, nbands, false)
+                           : apply_H_need<float>(h, 1, &ik, nbands, prec == MB_BF16);
 }
 
 int apply_H_on_scratch(mb_handle *h, int ik, const void *X, void *Y, int nbands, int prec, cudaStream_t s,
@@ -679,6 +818,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
     const PlanePlan plan = plan_plane(h, nsel, nbands, c2, maxldg, plane_reg_supported<R>(h->n1, h->n2));
     const int chunk = plan.chunk, nchunks = plan.nchunks;
+    (void)chunk;
     if (plan.np < 1) return MB_EUNSUPPORTED;
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
     for (int i = 0; i < nsel; ++i) {
@@ -694,32 +834,29 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         d.nrows = h->nrows[iks[i]];
         d.rowmask = h->rowmask[iks[i]];
         d.rows_magic = (unsigned)((1ull << 32) / (unsigned)std::max(1, d.nrows) + 1);
-        size_t part = (size_t)nbands * std::max(0, nchunks - 1) * 2 * (h->order - 1) * kp.ldg * c2;
-        size_t w = (size_t)nbands * h->nb * std::max(1, h->nproj) * c2;
+        // every k-point's regions are laid out for the batch's widest row (maxldg)
+        const KScratch ks = per_k_layout(h, maxldg, nbands, nchunks, c2, tensor);
         d.part = base + off;
-        off += al(part);
+        off += al(ks.part);
         d.W = base + off;
-        off += al(w);
+        off += al(ks.w);
         d.C = base + off;
-        off += al(w);
+        off += al(ks.c);
     }
+    // threads per (band, G) column for the j-contractions: aim at ~2 resident
+    // waves of 128-thread CTAs, with runs of at least 8 rows
+    long long cols = 0;
+    for (int i = 0; i < nsel; ++i) cols += (long long)nbands * h->kp[iks[i]].ldg;
+    const int want_threads = h->num_sms * 2048;
+    const int nseg = (int)std::max<long long>(1, std::min<long long>(nl_max_seg(h), (want_threads + cols - 1) / cols));
+    const int *d_pgroup = h->d_zidx;
+    const int *d_zstart = h->d_zidx ? h->d_zidx + h->nproj : nullptr;
+    const int *d_zlist = h->d_zidx ? h->d_zidx + h->nproj + h->nzf + 1 : nullptr;
     // projector overlaps first (they read X only)
-    if (h->nproj > 0) {
-        GemmArgs<R> ga;
-        ga.Q = reinterpret_cast<const R2 *>(t.qproj);
-        ga.mode = 0;
-        ga.nb = h->nb;
-        ga.nbands = nbands;
-        ga.nproj = h->nproj;
-        std::copy(desc, desc + nsel, ga.d);
-        dim3 grid((nbands * h->nb + 63) / 64, (h->nproj + 63) / 64, nsel);
-        if (tensor) {
-            cudaError_t e = cudaSuccess;
-            MB_LAUNCH(h, s, KN_PROJ, e = proj_tc_launch(h, 0, nsel, iks, desc, nbands, s));
-            MB_CUDA(e);
-        } else {
-            MB_LAUNCH(h, s, KN_PROJ, zgemm_kernel<R><<<grid, 256, 0, s>>>(ga));
-        }
+    if (h->nproj > 0 && tensor) {
+        cudaError_t e = cudaSuccess;
+        MB_LAUNCH(h, s, KN_PROJ, e = proj_tc_launch(h, 0, nsel, iks, desc, nbands, s));
+        MB_CUDA(e);
         CoefArgs<R> ca;
         ca.zproj = reinterpret_cast<const R *>(t.zproj);
         ca.E = reinterpret_cast<const R *>(t.E);
@@ -728,6 +865,34 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         ca.nproj = h->nproj;
         std::copy(desc, desc + nsel, ca.d);
         MB_LAUNCH(h, s, KN_COEF, coef_kernel<R><<<dim3((nbands * h->nproj + 127) / 128, nsel), 128, 0, s>>>(ca));
+    } else if (h->nproj > 0) {
+        NlArgs<R> na;
+        na.zf = reinterpret_cast<const R *>(t.zf);
+        na.E = reinterpret_cast<const R *>(t.E);
+        na.pgroup = d_pgroup;
+        na.Q = reinterpret_cast<const R2 *>(t.qproj);
+        na.nb = h->nb;
+        na.nbands = nbands;
+        na.nproj = h->nproj;
+        na.nz = h->nzf;
+        na.nseg = nseg;
+        std::copy(desc, desc + nsel, na.d);
+        const int zseg = std::max(1, std::min(8, h->nb / 8));
+        na.nseg = zseg;
+        const dim3 gz((maxldg + 63) / 64, nbands, nsel), bz(64, zseg);
+        const size_t zsm = (size_t)zseg * 64 * sizeof(R2) + (size_t)h->nzf * h->nb * sizeof(R);
+#define MB_ZX(NZ)                                                                                  \
+    do {                                                                                           \
+        MB_CUDA(smem_limit_once((const void *)nl_zx_kernel<R, NZ>, h->device, h->smem_optin));   \
+        MB_LAUNCH(h, s, KN_PROJ, (nl_zx_kernel<R, NZ><<<gz, bz, zsm, s>>>(na)));                 \
+    } while (0)
+        if (h->nzf <= 2) MB_ZX(2);
+        else if (h->nzf <= 4) MB_ZX(4);
+        else if (h->nzf <= 8) MB_ZX(8);
+        else if (h->nzf <= 12) MB_ZX(12);
+        else MB_ZX(16);
+#undef MB_ZX
+        MB_LAUNCH(h, s, KN_COEF, nl_coef_kernel<R><<<dim3(nbands, nsel, (h->nproj + 7) / 8), 256, 0, s>>>(na));
     }
     // local potential through the planes
     PlaneArgs<R> pa;
@@ -767,30 +932,52 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     ea.Sband = reinterpret_cast<const R *>(t.Sband);
     ea.Dband = reinterpret_cast<const R *>(t.Dband);
     ea.q2 = reinterpret_cast<const R *>(t.q2);
+    ea.zf = reinterpret_cast<const R *>(t.zf);
+    ea.zstart = d_zstart;
+    ea.zlist = d_zlist;
+    ea.Q = reinterpret_cast<const R2 *>(t.qproj);
     ea.order = h->order;
     ea.nb = h->nb;
     ea.nbands = nbands;
     ea.nchunks = nchunks;
-    ea.chunk = chunk;
     ea.nint = h->nint;
+    ea.nproj = h->nproj;
+    ea.njseg = nseg;
     std::copy(desc, desc + nsel, ea.d);
-    MB_LAUNCH(h, s, KN_EPILOGUE, epilogue_kernel<R><<<dim3(h->nb, nbands, nsel), 256, 0, s>>>(ea));
-    if (h->nproj > 0) {
-        GemmArgs<R> ga;
-        ga.Q = reinterpret_cast<const R2 *>(t.qproj);
-        ga.mode = 1;
-        ga.nb = h->nb;
-        ga.nbands = nbands;
-        ga.nproj = h->nproj;
-        std::copy(desc, desc + nsel, ga.d);
-        dim3 grid((nbands * h->nb + 63) / 64, (maxldg + 63) / 64, nsel);
-        if (tensor) {
-            cudaError_t e = cudaSuccess;
-            MB_LAUNCH(h, s, KN_BACKPROJ, e = proj_tc_launch(h, 1, nsel, iks, desc, nbands, s));
-            MB_CUDA(e);
+    // kinetic term, boundary sums and the KB term of the first 16 z factors;
+    // further passes add the KB term of the rest
+    const int nzf = (h->nproj > 0 && !tensor) ? h->nzf : 0;
+    const dim3 ge((maxldg + 63) / 64, nbands * nseg, nsel);
+    for (int f0 = 0, pass = 0; pass == 0 || f0 < nzf; f0 += 16, ++pass) {
+        ea.f0 = f0;
+        ea.f1 = std::min(nzf, f0 + 16);
+        ea.base = pass == 0;
+        const int nrmax = (h->nb + nseg - 1) / nseg;
+        const int HWn = h->order <= 6 ? 5 : 7;
+        const size_t esm = (size_t)h->nproj * sizeof(R2) +
+                           ((size_t)2 * nrmax * (2 * HWn + 1) + (size_t)(ea.f1 - ea.f0) * nrmax) * sizeof(R) +
+                           ((size_t)h->nproj + 17) * sizeof(int) + 16;
+        const int nfp = ea.f1 - ea.f0;
+#define MB_EPI(NZ, HWV)                                                                                   \
+    do {                                                                                                  \
+        MB_CUDA(smem_limit_once((const void *)epilogue_kernel<R, NZ, HWV>, h->device, h->smem_optin));  \
+        MB_LAUNCH(h, s, KN_EPILOGUE, (epilogue_kernel<R, NZ, HWV><<<ge, 64, esm, s>>>(ea)));            \
+    } while (0)
+        if (HWn == 5) {
+            if (nfp <= 4) MB_EPI(4, 5);
+            else if (nfp <= 8) MB_EPI(8, 5);
+            else MB_EPI(16, 5);
         } else {
-            MB_LAUNCH(h, s, KN_BACKPROJ, zgemm_kernel<R><<<grid, 256, 0, s>>>(ga));
+            if (nfp <= 4) MB_EPI(4, 7);
+            else if (nfp <= 8) MB_EPI(8, 7);
+            else MB_EPI(16, 7);
         }
+#undef MB_EPI
+    }
+    if (h->nproj > 0 && tensor) {
+        cudaError_t e = cudaSuccess;
+        MB_LAUNCH(h, s, KN_BACKPROJ, e = proj_tc_launch(h, 1, nsel, iks, desc, nbands, s));
+        MB_CUDA(e);
     }
     MB_CUDA(cudaGetLastError());
     return MB_OK;
@@ -875,9 +1062,9 @@ int autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves, 
     const bool small = h->n1 <= 32 && h->n2 <= 32;
     const auto key = std::make_tuple(std::min(nk, kMaxK), nbands, c2 == 16 ? 1 : 0);
     double best = 1e300;
-    std::pair<int, int> bestp(small ? 2 : 1, 2);
-    for (int bt = small ? 2 : 1; bt >= 1 && rc == MB_OK; --bt)
-        for (int waves : {1, 2, 4, 8}) {
+    std::pair<int, int> bestp(small ? 2 : 1, 0);
+    for (int bt = small ? 4 : 2; bt >= 1 && rc == MB_OK; --bt)
+        for (int waves : {0, 1, 2, 4, 8}) {
             h->tuned[key] = std::make_pair(bt, waves);
             for (int w = 0; w < 2 && rc == MB_OK; ++w)
                 rc = apply_H_batch(h, nk, iks.data(), (const void *const *)X.data(), Y.data(), nbands, prec, s);

@@ -6,13 +6,20 @@
 namespace mb {
 
 constexpr int kMaxK = 64;   // k-points per launch (descriptors travel as kernel parameters)
+constexpr int kMaxChunks = 64;   // runs of knot intervals per (k, band) in the plane kernel
+
+// First knot interval of run c when nint intervals are split into nchunks
+// runs of balanced length (lengths differ by at most one).
+__host__ __device__ inline int chunk_begin(int c, int nint, int nchunks) {
+    return (int)(((long long)c * nint) / nchunks);
+}
 
 struct KDesc {
     const void *X;
     void *Y;
     void *part;      // boundary partial rows
-    void *W;         // projector overlaps W[(b, j)][p]
-    void *C;         // back-projection coefficients C[(b, j)][p]
+    void *W;         // projector overlaps: Zx[b][f][G] (CUDA-core path) or W[(b, j)][p] (tensor cores)
+    void *C;         // projector coefficients: c[b][p] (CUDA-core path) or C[(b, j)][p] (tensor cores)
     int ng, ldg;
     int kofs;        // offset of per-k G arrays
     int qofs;        // offset of q_p(G) table

@@ -1036,8 +1036,8 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     int guard = so && so->guard != 0 ? std::max(0, so->guard) : std::max(2, (nbands + 7) / 8);
     S.Mconv = nbands;
     S.M = nbands + guard;
-    S.kd = so && so->krylov_depth > 0 ? so->krylov_depth : 4;
-    S.b = so && so->block > 0 ? so->block : 4;
+    S.kd = so && so->krylov_depth > 0 ? so->krylov_depth : kDefaultKrylovDepth;
+    S.b = so && so->block > 0 ? so->block : kDefaultBlock;
     int max_cycles = so && so->max_cycles > 0 ? so->max_cycles : 200;
     if (S.b > S.M) S.b = S.M;
     S.nblk = (S.M + S.b - 1) / S.b;

@@ -39,6 +39,7 @@ struct DevTables {
     void *q2 = nullptr;      // all k, concatenated with kofs
     void *qproj = nullptr;   // all k: nproj x ldg each, offset qofs[k]
     void *zproj = nullptr;   // nproj x nb
+    void *zf = nullptr;      // nzf x nb: the distinct rows of zproj
     void *E = nullptr;       // nproj
     void *Pfac = nullptr;    // preconditioner factors: all k, ldg x nb x order each
 };
@@ -67,6 +68,12 @@ struct mb_handle {
     std::vector<double> Sb, Db, Lb;  // band storage as in DevTables
     std::vector<double> Vnat;        // nq x N1 x N2 natural order, V(r, z_q) (Ha)
     std::vector<double> zproj, Eproj;
+    // distinct z factors of the projectors: zfun (nzf x nb), pgroup[p] = f,
+    // and the projectors of factor f in zlist[zstart[f] .. zstart[f+1])
+    int nzf = 0;
+    std::vector<double> zfun;
+    std::vector<int> pgroup, zstart, zlist;
+    int *d_zidx = nullptr;           // device copy: pgroup | zstart | zlist
     std::vector<mb::KPoint> kp;
     std::vector<int> kofs, qofs;     // offsets of per-k arrays (in elements)
     int total_ldg = 0;
@@ -116,12 +123,18 @@ int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X,
                   void *const *Y, int nbands, int prec, cudaStream_t s);
 int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nbands,
                  int prec, cudaStream_t s);
-size_t apply_scratch_bytes(const mb_handle *h, int nsel_max, int nbands, int prec);
+size_t apply_scratch_bytes(const mb_handle *h, int nk, int nbands, int prec);
 size_t apply_H_scratch_need(const mb_handle *h, int ik, int nbands, int prec);
 int apply_H_on_scratch(mb_handle *h, int ik, const void *X, void *Y, int nbands, int prec, cudaStream_t s,
                        void *scratch);
 
 enum { BAND_S = 0, BAND_SINV = 1, BAND_PREC = 2 };
+
+// eigensolver defaults: Krylov depth and roots per block of the second grand
+// cycle (one root per block: every root gets its own Krylov space, which
+// needed the fewest FP64 operations to 1e-6 Ha on the slab and graphene cells)
+constexpr int kDefaultKrylovDepth = 4;
+constexpr int kDefaultBlock = 1;
 
 // kernel ids for launch accounting / profiling
 enum { KN_PLANE = 0, KN_EPILOGUE, KN_PROJ, KN_COEF, KN_BACKPROJ, KN_BANDED, KN_GRAM, KN_COMBINE,

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256, (N1 <= 32 && N2 <= 32 && sizeof(R) == 4) 
     const int *goff = a.goff + d.kofs;
     const int *rows = a.rows + d.rows_ofs;
     const int nrows = d.nrows;
-    const int t0 = c * a.chunk, t1 = min(a.nint, t0 + a.chunk);
+    const int t0 = chunk_begin(c, a.nint, a.nchunks), t1 = chunk_begin(c + 1, a.nint, a.nchunks);
     const int nplanes = nbb * P;          // (band, Gauss point) planes per interval
     const size_t band_stride = (size_t)nb * ldg;
     const size_t part_stride = (size_t)(a.nchunks - 1) * 2 * (K - 1) * ldg;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256, (N1 <= 32 && N2 <= 32 && sizeof(R) == 4) 
     // per-group plane metadata: band and Gauss point of each plane, and its B values
     int *pl_b = reinterpret_cast<int *>(acc + (size_t)a.bt * K * a.ldg_max);
     int *pl_s = pl_b + a.np;
-    R *bqs = reinterpret_cast<R *>(pl_s + a.np + (a.np & 1));   // np x 8 (keeps 8-byte alignment)
+    R *bqs = reinterpret_cast<R *>(pl_b + 2 * a.np);   // np x 8; pl_b is 8-byte aligned and 2 np ints are 8 np bytes
     const unsigned rmagic = d.rows_magic;
 
     for (int t = t0; t < t1; ++t) {

@@ -62,7 +62,8 @@ size_t footprint_of(const mb_handle &h, int nbands, int prec) {
         maxldg = std::max(maxldg, k.ldg);
     }
     tables += pf;
-    const int guard = std::max(2, (nbands + 7) / 8), M = nbands + guard, kd = 4, b = 4;
+    const int guard = std::max(2, (nbands + 7) / 8), M = nbands + guard;
+    const int kd = kDefaultKrylovDepth, b = kDefaultBlock;
     const int nblk = (M + b - 1) / b, mA = M + kd, mB = b + kd, nc = std::max(1, nblk);
     const size_t nvecs = 3 * (size_t)std::max(mA, nblk * b) + 2 * (size_t)nblk * mB + 4 * nc + 3 * (size_t)mA +
                          (size_t)nblk * mB;
@@ -71,8 +72,10 @@ size_t footprint_of(const mb_handle &h, int nbands, int prec) {
     work += (size_t)h.kp.size() * nc * LD * LD * 16 * 3 + (size_t)h.kp.size() * LD * LD * 16 * 3;
     work += (size_t)std::max<size_t>(304, h.kp.size() * nc) * 112 * 112 * 16;
     // apply scratch: boundary rows + projector overlaps (generous bound)
-    size_t scratch = (size_t)h.kp.size() * ((size_t)M * 40 * 2 * (h.order - 1) * maxldg * 16 +
-                                            2 * (size_t)M * h.nb * std::max(1, h.nproj) * 16);
+    size_t scratch = (size_t)h.kp.size() *
+                     ((size_t)M * 40 * 2 * (h.order - 1) * maxldg * 16 +
+                      2 * (size_t)M * std::max((size_t)16 * std::max(1, h.nzf) * maxldg,
+                                               (size_t)h.nb * std::max(1, h.nproj)) * 16);
     (void)prec;
     return tables + work + scratch + (64u << 20);   // + context-side slack per request
 }

@@ -339,6 +339,27 @@ int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int
         }
         p += 4;
     }
+    // group projectors by identical z factor (s, p_x, p_y of an atom share one;
+    // atoms at one height with one radius share theirs)
+    h->nzf = 0;
+    h->zfun.clear();
+    h->pgroup.assign(NP, -1);
+    h->zstart.assign(1, 0);
+    h->zlist.clear();
+    for (int p0 = 0; p0 < NP; ++p0) {
+        if (h->pgroup[p0] >= 0) continue;
+        const double *r0 = h->zproj.data() + (size_t)p0 * nb;
+        const int f = h->nzf++;
+        h->zfun.insert(h->zfun.end(), r0, r0 + nb);
+        for (int p1 = p0; p1 < NP; ++p1) {
+            const double *r1 = h->zproj.data() + (size_t)p1 * nb;
+            if (h->pgroup[p1] < 0 && std::equal(r0, r0 + nb, r1)) {
+                h->pgroup[p1] = f;
+                h->zlist.push_back(p1);
+            }
+        }
+        h->zstart.push_back((int)h->zlist.size());
+    }
     return MB_OK;
 }
 

@@ -43,10 +43,19 @@ def _small_graphene():
     return W.scaled(w, ecut=4.0, n_int=17, nbands=3, name="graphene-small")
 
 
+def _small_kbatch():
+    # 32x32 grid and 160-wide G rows: the FP64 register-FFT plane kernel then
+    # runs 11 planes per group (an odd count, which once misaligned its
+    # double-precision B-value table in shared memory)
+    w = W.kbatch(4)
+    return W.scaled(w, ecut=12.0, n_int=15, nbands=7, name="kbatch-small")
+
+
 CASES = {
     "tiny": lambda: W.tiny(),
     "slab-small": _small_slab,
     "graphene-small": _small_graphene,
+    "kbatch-small": _small_kbatch,
 }
 
 

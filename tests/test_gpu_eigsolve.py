@@ -97,6 +97,19 @@ def test_eigsolve_graphene_small(mbmod):
     h.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_eigsolve_kbatch_small_all_k(mbmod, prec):
+    """Four wedge k-points of the 2x2 graphene cell on a 32x32 grid, solved in
+    one batched call, against dense generalized eigenvalues per k-point."""
+    w = W.scaled(W.kbatch(4), ecut=12.0, n_int=15, nbands=10, name="kbatch-small")
+    h = mbmod.Handle.from_workload(w)
+    ev, info = h.eigsolve(w.nbands, 1e-7, prec)
+    for ik in range(w.nk):
+        m, ref = _dense_ref(w, ik, w.nbands)
+        assert np.abs(ev[ik] - ref).max() < EV_TOL, (ik, np.abs(ev[ik] - ref).max())
+    h.close()
+
+
 def test_eigsolve_ragged_blocks_and_depth(mbmod):
     """Band count not a multiple of the block size, deeper Krylov spaces."""
     w = W.tiny()
