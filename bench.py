@@ -38,9 +38,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Hψ GB/s & eigensolves/s at 1e-6 Ha vs plain FP64 GPU; p50/p99 solve latency"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3   # SMs x FP32 lanes x 2 flop x max SM clock (GHz)
-# dram bytes per plane-kernel launch from the ncu capture summarised in
-# profiles/plane_kernel_slab.md (None until a capture of the current kernel exists)
-PLANE_TRAFFIC_BYTES = None
+# dram bytes (read + write) per FP32 plane-kernel launch of this workload,
+# from the ncu capture summarised in profiles/plane_reg_kernel_slab_fp32.md
+# (set to None whenever the kernel changes until it is captured again)
+PLANE_TRAFFIC_BYTES = 25.41e6
 
 
 def _peaks():
@@ -463,7 +464,7 @@ def run_ours(args):
         ach = plane_flops / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP32_PEAK_TFLOPS, "traffic": PLANE_TRAFFIC_BYTES,
-                "kernel": "plane_kernel<float>", "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                "kernel": "plane_reg_kernel<float, 32, 16>", "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
                 "kernel_ms": per_launch_ms,
                 "share_of_step": t / args.steps / ms32}
 
