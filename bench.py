@@ -38,9 +38,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Hψ GB/s & eigensolves/s at 1e-6 Ha vs plain FP64 GPU; p50/p99 solve latency"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3   # SMs x FP32 lanes x 2 flop x max SM clock (GHz)
-# dram bytes (read + write) per FP32 plane-kernel launch of this workload,
-# from the ncu capture summarised in profiles/plane_reg_kernel_slab_fp32.md
-# (set to None whenever the kernel changes until it is captured again)
+# dram bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one FP32
+# plane-kernel launch of this workload, from an ncu capture of the current
+# kernel (None whenever the kernel changes until it is captured again)
 PLANE_TRAFFIC_BYTES = 25.41e6
 
 
