@@ -21,6 +21,7 @@
 #include <tuple>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "cplx.cuh"
@@ -36,6 +37,7 @@ constexpr int JPAIRS = 58;    // rotation slots per Jacobi round (>= JMAX/2 + 1,
 struct EigK {
     double2 *base;            // FP64 vectors of this k-point, stride nvec
     float2 *stage;            // FP32 staging for mixed-precision applies
+    float2 *v32;              // FP32 copies for the Krylov Gram-Schmidt (mixed precision)
     const double *pfac;       // preconditioner factors of this k-point
     long long nvec;           // nb * ldg
     int ldg, ng;
@@ -70,7 +72,8 @@ __global__ void gram_reduce_kernel(const double2 *part, int nsplit, int ma, int 
 
 // dst_i = src_i for index sets (FP64 -> FP64), or into / out of the FP32 stage
 __global__ void copy_kernel(const EigK *ks, int nch, VSet S, VSet D, int mode) {
-    // mode 0: base -> base; 1: base -> stage (to float); 2: stage -> base (to double)
+    // mode 0: base -> base; 1: base -> stage (to float); 2: stage -> base (to double);
+    // 3: base -> v32 (to float); 4: v32 -> base (to double)
     const int prob = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
@@ -83,7 +86,9 @@ __global__ void copy_kernel(const EigK *ks, int nch, VSet S, VSet D, int mode) {
         long long si = (long long)S.at(i, ch) * d.nvec + t, di = (long long)D.at(i, ch) * d.nvec + t;
         if (mode == 0) d.base[di] = d.base[si];
         else if (mode == 1) d.stage[di] = make_float2((float)d.base[si].x, (float)d.base[si].y);
-        else d.base[di] = make_double2((double)d.stage[si].x, (double)d.stage[si].y);
+        else if (mode == 2) d.base[di] = make_double2((double)d.stage[si].x, (double)d.stage[si].y);
+        else if (mode == 3) d.v32[di] = make_float2((float)d.base[si].x, (float)d.base[si].y);
+        else d.base[di] = make_double2((double)d.v32[si].x, (double)d.v32[si].y);
     }
 }
 
@@ -537,8 +542,13 @@ __global__ void eig_banded_solve_kernel(const EigK *ks, const double *Lb, int pe
 // registers, then reduce them by warp shuffles.  Grid: (n-chunks, problems,
 // row groups of 8 x column groups of GJ).
 constexpr int GJ = 16;
+// F32: the vectors are the FP32 Gram-Schmidt copies (v32) and the partial
+// sums are FP32 (the reduction over chunks stays FP64).
+template <bool F32>
 __global__ void __launch_bounds__(256) gram_rows_kernel(const EigK *ks, int nch, VSet A, VSet B, int nsplit,
                                                         int colgroups, double2 *part) {
+    typedef typename std::conditional<F32, float2, double2>::type T2;
+    typedef typename std::conditional<F32, float, double>::type T;
     const int split = blockIdx.x, prob = blockIdx.y;
     const int rg = blockIdx.z / colgroups, cg = blockIdx.z % colgroups;
     const int k = prob / nch, ch = prob % nch;
@@ -551,19 +561,20 @@ __global__ void __launch_bounds__(256) gram_rows_kernel(const EigK *ks, int nch,
     const long long n = d.nvec;
     const long long chunk = (n + nsplit - 1) / nsplit;
     const long long t0 = split * chunk, t1 = min(n, t0 + chunk);
-    const double2 *a = d.base + (long long)A.at(i, ch) * n;
-    const double2 *bp[GJ];
+    const T2 *vb = F32 ? reinterpret_cast<const T2 *>(d.v32) : reinterpret_cast<const T2 *>(d.base);
+    const T2 *a = vb + (long long)A.at(i, ch) * n;
+    const T2 *bp[GJ];
 #pragma unroll
-    for (int jj = 0; jj < GJ; ++jj) bp[jj] = d.base + (long long)B.at(j0 + (jj < nj ? jj : 0), ch) * n;
-    double sx[GJ], sy[GJ];
+    for (int jj = 0; jj < GJ; ++jj) bp[jj] = vb + (long long)B.at(j0 + (jj < nj ? jj : 0), ch) * n;
+    T sx[GJ], sy[GJ];
 #pragma unroll
-    for (int jj = 0; jj < GJ; ++jj) sx[jj] = sy[jj] = 0.0;
+    for (int jj = 0; jj < GJ; ++jj) sx[jj] = sy[jj] = T(0);
     for (long long t = t0 + lane; t < t1; t += 32) {
-        const double2 av = a[t];
+        const T2 av = a[t];
 #pragma unroll
         for (int jj = 0; jj < GJ; ++jj) {
             if (jj < nj) {
-                const double2 bv = bp[jj][t];
+                const T2 bv = bp[jj][t];
                 sx[jj] = fma(av.x, bv.x, fma(av.y, bv.y, sx[jj]));
                 sy[jj] = fma(av.x, bv.y, fma(-av.y, bv.x, sy[jj]));
             }
@@ -572,7 +583,7 @@ __global__ void __launch_bounds__(256) gram_rows_kernel(const EigK *ks, int nch,
 #pragma unroll
     for (int jj = 0; jj < GJ; ++jj) {
         if (jj >= nj) break;
-        double x = sx[jj], y = sy[jj];
+        T x = sx[jj], y = sy[jj];
         for (int off = 16; off > 0; off >>= 1) {
             x += __shfl_down_sync(0xffffffffu, x, off);
             y += __shfl_down_sync(0xffffffffu, y, off);
@@ -583,10 +594,12 @@ __global__ void __launch_bounds__(256) gram_rows_kernel(const EigK *ks, int nch,
 
 // C_j = beta C_j + alpha sum_i A_i Y[i][j]: one element t per thread, JC
 // output columns at a time with their coefficients staged in shared memory.
-template <int JC>
+template <int JC, bool F32>
 __global__ void __launch_bounds__(256) combine2_kernel(const EigK *ks, int nch, VSet A, VSet C,
                                                        const double2 *Y, double alpha, double beta) {
-    __shared__ double2 Ys[JMAX][JC];
+    typedef typename std::conditional<F32, float2, double2>::type T2;
+    typedef typename std::conditional<F32, float, double>::type T;
+    __shared__ T2 Ys[JMAX][JC];
     const int prob = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
@@ -598,26 +611,55 @@ __global__ void __launch_bounds__(256) combine2_kernel(const EigK *ks, int nch, 
         __syncthreads();
         for (int e = threadIdx.x; e < ma * JC; e += blockDim.x) {
             const int i = e / JC, jj = e % JC;
-            Ys[i][jj] = j0 + jj < mc ? y[i * LD + j0 + jj] : make_double2(0.0, 0.0);
+            const double2 yv = j0 + jj < mc ? y[i * LD + j0 + jj] : make_double2(0.0, 0.0);
+            Ys[i][jj] = mk((T)yv.x, (T)yv.y);
         }
         __syncthreads();
         if (!live) continue;
-        double2 acc[JC];
+        T2 *vb = F32 ? reinterpret_cast<T2 *>(d.v32) : reinterpret_cast<T2 *>(d.base);
+        T2 acc[JC];
 #pragma unroll
-        for (int jj = 0; jj < JC; ++jj) acc[jj] = make_double2(0.0, 0.0);
+        for (int jj = 0; jj < JC; ++jj) acc[jj] = czero<T2>();
         for (int i = 0; i < ma; ++i) {
-            const double2 a = d.base[(long long)A.at(i, ch) * d.nvec + t];
+            const T2 a = vb[(long long)A.at(i, ch) * d.nvec + t];
 #pragma unroll
             for (int jj = 0; jj < JC; ++jj) cfma(acc[jj], a, Ys[i][jj]);
         }
 #pragma unroll
         for (int jj = 0; jj < JC; ++jj) {
             if (j0 + jj >= mc) break;
-            double2 *c = d.base + (long long)C.at(j0 + jj, ch) * d.nvec + t;
-            const double2 v = rscale(alpha, acc[jj]);
-            *c = beta == 0.0 ? v : rscale(beta, *c) + v;
+            T2 *c = vb + (long long)C.at(j0 + jj, ch) * d.nvec + t;
+            const T2 v = rscale((T)alpha, acc[jj]);
+            *c = beta == 0.0 ? v : rscale((T)beta, *c) + v;
         }
     }
+}
+
+// G <- the Hermitian matrix of its lower triangle (keeps the couplings
+// K^H (H X), which use the roots' HX, over X^H (H K))
+__global__ void herm_lower_kernel(double2 *G, int m) {
+    double2 *g = G + (size_t)blockIdx.y * LD * LD;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    const int i = e / m, j = e % m;
+    if (i < j) {
+        const double2 v = g[j * LD + i];
+        g[i * LD + j] = make_double2(v.x, -v.y);
+    } else if (i == j) {
+        g[i * LD + i].y = 0.0;
+    }
+}
+
+// dead slots (mask 0) of an S-Gram matrix become identity rows and columns,
+// so that its Cholesky factor exists and leaves them decoupled
+__global__ void mask_sgram_kernel(double2 *G, const int *mask, int m) {
+    const int prob = blockIdx.y;
+    double2 *g = G + (size_t)prob * LD * LD;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    const int i = e / m, j = e % m;
+    const bool di = mask[prob * LD + i] == 0, dj = mask[prob * LD + j] == 0;
+    if (di || dj) g[i * LD + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
 }
 
 // C = op(A) B for small m x m matrices (leading dimension LD), one thread per
@@ -779,6 +821,14 @@ struct Solver {
     int Mconv;          // roots tested for convergence and returned (M includes guards)
     int prec;           // precision of the H applies that build Krylov vectors
     bool fp64_roots = false;   // finish phase: HX of the roots recomputed in FP64 every cycle
+    // mixed precision: the Krylov Gram-Schmidt runs on FP32 copies (v32), and
+    // the small Rayleigh-Ritz problems of cycles A and B use the FP64 S-Gram
+    // of their basis (a pencil), so that their result does not depend on how
+    // orthogonal the Krylov vectors came out
+    bool gs32 = false;
+    int o32X = 0, o32SX = 0, o32W = 0, o32K = 0, o32SK = 0, n32 = 0;
+    double2 *d_Sg = nullptr, *d_Ub = nullptr, *d_Tb = nullptr;
+    int *d_statb = nullptr;
     int oV, oHV, oSV, oVB, oHVB, oSVB, oQ, oHQ, oW, oSW, oT;
     int nvecs;
     std::vector<EigK> kd_host;
@@ -811,7 +861,7 @@ struct Solver {
         return reinterpret_cast<T *>(p);
     }
 
-    void gram(int nch, VSet A, VSet B, double2 *G) {
+    void gram(int nch, VSet A, VSet B, double2 *G, bool f32 = false) {
         const int nprob = nk * nch;
         const int ma = A.count(), mbc = B.count();
         const int rowgroups = (ma + 7) / 8, colgroups = (mbc + GJ - 1) / GJ;
@@ -819,28 +869,37 @@ struct Solver {
         int nsplit = std::max(1, std::min(512, (8 * h->num_sms + per_split - 1) / per_split));
         nsplit = std::min<long long>(nsplit, std::max<long long>(1, nmax / 256));   // >= 256 elements per chunk
         while ((size_t)nprob * nsplit * ma * mbc > part_cap && nsplit > 1) --nsplit;
-        MB_LAUNCH_E(KN_GRAM, gram_rows_kernel<<<dim3(nsplit, nprob, rowgroups * colgroups), 256, 0, s>>>(
-                                 d_k, nch, A, B, nsplit, colgroups, d_part));
+        if (f32)
+            MB_LAUNCH_E(KN_GRAM, gram_rows_kernel<true><<<dim3(nsplit, nprob, rowgroups * colgroups), 256, 0, s>>>(
+                                     d_k, nch, A, B, nsplit, colgroups, d_part));
+        else
+            MB_LAUNCH_E(KN_GRAM, gram_rows_kernel<false><<<dim3(nsplit, nprob, rowgroups * colgroups), 256, 0, s>>>(
+                                     d_k, nch, A, B, nsplit, colgroups, d_part));
         MB_LAUNCH_E(KN_GRAM, gram_reduce_kernel<<<nprob, 256, 0, s>>>(d_part, nsplit, ma, mbc, G));
     }
-    void combine(int nch, VSet A, VSet C, const double2 *Y, double alpha, double beta) {
+    void combine(int nch, VSet A, VSet C, const double2 *Y, double alpha, double beta, bool f32 = false) {
+        if (f32) combine_t<true>(nch, A, C, Y, alpha, beta);
+        else combine_t<false>(nch, A, C, Y, alpha, beta);
+    }
+    template <bool F32> void combine_t(int nch, VSet A, VSet C, const double2 *Y, double alpha, double beta) {
         const dim3 grid((unsigned)((nmax + 255) / 256), nk * nch);
         const int mc = C.count();
         // column width with the least padding (12 divides the common 36)
         auto waste = [&](int jc) { return (mc + jc - 1) / jc * jc - mc; };
         if (mc == 1)
-            MB_LAUNCH_E(KN_COMBINE, combine2_kernel<1><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta));
+            MB_LAUNCH_E(KN_COMBINE, (combine2_kernel<1, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
         else if (mc <= 4)
-            MB_LAUNCH_E(KN_COMBINE, combine2_kernel<4><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta));
+            MB_LAUNCH_E(KN_COMBINE, (combine2_kernel<4, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
         else if (mc <= 8)
-            MB_LAUNCH_E(KN_COMBINE, combine2_kernel<8><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta));
+            MB_LAUNCH_E(KN_COMBINE, (combine2_kernel<8, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
         else if (waste(12) < waste(16))
-            MB_LAUNCH_E(KN_COMBINE, combine2_kernel<12><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta));
+            MB_LAUNCH_E(KN_COMBINE, (combine2_kernel<12, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
         else
-            MB_LAUNCH_E(KN_COMBINE, combine2_kernel<16><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta));
+            MB_LAUNCH_E(KN_COMBINE, (combine2_kernel<16, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
     }
-    void small_gemm(const double2 *A, const double2 *B, double2 *C, int m, int conjA) {
-        MB_LAUNCH_E(KN_SMALL, small_zgemm_kernel<<<dim3((m * m + 127) / 128, nk), 128, 0, s>>>(A, B, C, m, conjA));
+    void small_gemm(const double2 *A, const double2 *B, double2 *C, int m, int conjA, int np = 0) {
+        MB_LAUNCH_E(KN_SMALL, small_zgemm_kernel<<<dim3((m * m + 127) / 128, np > 0 ? np : nk), 128, 0, s>>>(
+                                  A, B, C, m, conjA));
     }
     void copy(int nch, VSet S, VSet D, int mode) {
         MB_LAUNCH_E(KN_VEC, copy_kernel<<<dim3(256, nk * nch), 256, 0, s>>>(d_k, nch, S, D, mode));
@@ -901,6 +960,10 @@ struct Solver {
     void krylov(int nch, int kV, int kS, int kH, int cs) {
         int np = nk * nch;
         MB_LAUNCH_E(KN_SMALL, fill_int_kernel<<<(np * kd + 127) / 128, 128, 0, s>>>(d_alive, np * kd, 1));
+        if (gs32) {
+            copy(1, vs(oV, M), vs(o32X, M), 3);
+            copy(1, vs(oSV, M), vs(o32SX, M), 3);
+        }
         for (int i = 0; i < kd && !rc; ++i) {
             if (i > 0) {
                 copy(nch, vs(kV + i - 1, 1, cs), vs(oQ, 1, 1), 0);
@@ -914,16 +977,31 @@ struct Solver {
             // coefficients of a pass come from the same (pre-update) vector.
             // The roots X are common to every chain of a k-point, so their
             // part is one product with a column per chain.
-            for (int pass = 0; pass < 2; ++pass) {
-                gram(1, vs(oSV, M), vs(oW, nch), d_G2);                    // SX^H [W_0 .. W_nch-1]
-                if (i > 0) gram(nch, vs(kS, i, cs), vs(oW, 1, 1), d_G);     // SK_ch^H W_ch
-                combine(1, vs(oV, M), vs(oW, nch), d_G2, -1.0, 1.0);
-                if (i > 0) combine(nch, vs(kV, i, cs), vs(oW, 1, 1), d_G, -1.0, 1.0);
+            if (gs32) {
+                copy(nch, vs(oW, 1, 1), vs(o32W, 1, 1), 3);
+                for (int pass = 0; pass < 2; ++pass) {
+                    gram(1, vs(o32SX, M), vs(o32W, nch), d_G2, true);
+                    if (i > 0) gram(nch, vs(o32SK, i, kd), vs(o32W, 1, 1), d_G, true);
+                    combine(1, vs(o32X, M), vs(o32W, nch), d_G2, -1.0, 1.0, true);
+                    if (i > 0) combine(nch, vs(o32K, i, kd), vs(o32W, 1, 1), d_G, -1.0, 1.0, true);
+                }
+                copy(nch, vs(o32W, 1, 1), vs(oW, 1, 1), 4);
+            } else {
+                for (int pass = 0; pass < 2; ++pass) {
+                    gram(1, vs(oSV, M), vs(oW, nch), d_G2);                    // SX^H [W_0 .. W_nch-1]
+                    if (i > 0) gram(nch, vs(kS, i, cs), vs(oW, 1, 1), d_G);     // SK_ch^H W_ch
+                    combine(1, vs(oV, M), vs(oW, nch), d_G2, -1.0, 1.0);
+                    if (i > 0) combine(nch, vs(kV, i, cs), vs(oW, 1, 1), d_G, -1.0, 1.0);
+                }
             }
             bandS(oW, oSW, nch);
             MB_LAUNCH_E(KN_SMALL, coldot_kernel<<<dim3(1, np), 256, 0, s>>>(d_k, nch, vs(oW, 1, 1), vs(oSW, 1, 1), d_dots));
             MB_LAUNCH_E(KN_VEC, normalize_kernel<<<dim3(128, np), 256, 0, s>>>(d_k, nch, oW, oSW, kV, kS, cs, i,
                                                                                d_dots, d_alive, kd));
+            if (gs32 && i + 1 < kd) {
+                copy(nch, vs(kV + i, 1, cs), vs(o32K + i, 1, kd), 3);
+                copy(nch, vs(kS + i, 1, cs), vs(o32SK + i, 1, kd), 3);
+            }
         }
         copy(nch, vs(kV + kd - 1, 1, cs), vs(oQ, 1, 1), 0);
         applyH_chain(nch, kd - 1, kH, cs);
@@ -947,6 +1025,26 @@ struct Solver {
                                                                                d_evals, d_Y, 30, 1e-13));
         }
     }
+    // Rayleigh-Ritz of the pencil (V^H H V, V^H S V) of nch problems of size m
+    // per k-point: U = L^{-H} from V^H S V = L L^H (dead Krylov slots made
+    // identity), Ritz pairs of U^H (V^H H V) U; returns the Ritz vectors'
+    // coordinates in the V basis (U Y) and leaves the values in d_evals.
+    const double2 *rr_pencil(int nch, VSet V, VSet HV, VSet SV, int m, int ofs) {
+        const int np = nk * nch;
+        gram(nch, V, HV, d_G);
+        gram(nch, V, SV, d_Sg);
+        const dim3 gs((m * m + 127) / 128, np);
+        MB_LAUNCH_E(KN_SMALL, herm_lower_kernel<<<gs, 128, 0, s>>>(d_G, m));
+        MB_LAUNCH_E(KN_SMALL, alive_mask_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_alive, kd, ofs, M, b, nch, m, np, d_mask));
+        MB_LAUNCH_E(KN_SMALL, mask_sgram_kernel<<<gs, 128, 0, s>>>(d_Sg, d_mask, m));
+        cuda(smem_limit_once((const void *)cholinv_kernel, h->device, h->smem_optin));
+        MB_LAUNCH_E(KN_SMALL, cholinv_kernel<<<np, 128, (size_t)m * m * sizeof(double2), s>>>(d_Sg, m, d_Ub, d_statb));
+        small_gemm(d_G, d_Ub, d_Tb, m, 0, np);    // (V^H H V) U
+        small_gemm(d_Ub, d_Tb, d_G, m, 1, np);    // U^H (V^H H V) U
+        jacobi(nch, m, true, ofs);
+        small_gemm(d_Ub, d_Y, d_Tb, m, 0, np);    // U Y
+        return d_Tb;
+    }
     // X, HX <- [V|..](m) Y[:, :M] and SX = S X (S is banded: recomputing it is
     // cheaper than rotating it)
     void rotate_set(const double2 *Y, int m) {
@@ -958,9 +1056,13 @@ struct Solver {
     }
     void rr_full(bool withK) {
         int m = withK ? mA : M;
-        gram(1, vs(oV, m), vs(oHV, m), d_G);
-        jacobi(1, m, withK, M);
-        rotate_set(d_Y, m);
+        if (gs32 && withK) {
+            rotate_set(rr_pencil(1, vs(oV, m), vs(oHV, m), vs(oSV, m), m, M), m);
+        } else {
+            gram(1, vs(oV, m), vs(oHV, m), d_G);
+            jacobi(1, m, withK, M);
+            rotate_set(d_Y, m);
+        }
         MB_LAUNCH_E(KN_SMALL, take_evals_kernel<<<(M * nk + 127) / 128, 128, 0, s>>>(d_evals, M, nk, d_eps));
     }
     // S-orthonormalization and Rayleigh-Ritz in one rotation: U = L^{-H} from
@@ -982,11 +1084,17 @@ struct Solver {
         residuals_and_seeds(nblk);
         copy(nblk, vs(oV, b, b), vs(oVB, b, mB), 0);
         copy(nblk, vs(oHV, b, b), vs(oHVB, b, mB), 0);
+        if (gs32) copy(nblk, vs(oSV, b, b), vs(oSVB, b, mB), 0);
         krylov(nblk, oVB + b, oSVB + b, oHVB + b, mB);
-        gram(nblk, vs(oVB, mB, mB), vs(oHVB, mB, mB), d_G);
-        jacobi(nblk, mB, true, b);
+        const double2 *Yc = d_Y;
+        if (gs32) {
+            Yc = rr_pencil(nblk, vs(oVB, mB, mB), vs(oHVB, mB, mB), vs(oSVB, mB, mB), mB, b);
+        } else {
+            gram(nblk, vs(oVB, mB, mB), vs(oHVB, mB, mB), d_G);
+            jacobi(nblk, mB, true, b);
+        }
         int np = nk * nblk;
-        MB_LAUNCH_E(KN_SMALL, select_kernel<<<(np + 31) / 32, 32, 0, s>>>(d_evals, d_Y, mB, b, M, nblk, np, d_eps, d_Ysel));
+        MB_LAUNCH_E(KN_SMALL, select_kernel<<<(np + 31) / 32, 32, 0, s>>>(d_evals, Yc, mB, b, M, nblk, np, d_eps, d_Ysel));
         combine(nblk, vs(oVB, mB, mB), vs(oV, b, b), d_Ysel, 1.0, 0.0);
         combine(nblk, vs(oHVB, mB, mB), vs(oHV, b, b), d_Ysel, 1.0, 0.0);
         bandS(oV, oSV, M);
@@ -1067,6 +1175,15 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     S.oSW = S.oW + S.nc;
     S.oT = S.oSW + S.nc;
     S.nvecs = S.oT + 3 * S.mA;
+    // FP32 Gram-Schmidt workspace (mixed precision): X, SX, the chain inputs W,
+    // then K and SK of every chain (chain ch, depth i at + ch*kd + i)
+    S.gs32 = prec != MB_FP64;
+    S.o32X = 0;
+    S.o32SX = S.M;
+    S.o32W = 2 * S.M;
+    S.o32K = S.o32W + S.nc;
+    S.o32SK = S.o32K + S.nc * S.kd;
+    S.n32 = S.o32SK + S.nc * S.kd;
     // per-k memory
     S.kd_host.resize(S.nk);
     size_t pofs = 0;
@@ -1077,6 +1194,7 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
         e.nvec = (long long)h->nb * e.ldg;
         e.base = S.alloc<double2>((size_t)S.nvecs * e.nvec);
         e.stage = S.alloc<float2>((size_t)2 * S.nc_stage() * e.nvec);
+        e.v32 = S.gs32 ? S.alloc<float2>((size_t)S.n32 * e.nvec) : nullptr;
         e.pfac = (const double *)h->t64.Pfac + pofs;
         pofs += (size_t)e.ldg * h->nb * h->order;
         if (S.rc) return S.rc;
@@ -1105,6 +1223,12 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     S.d_alive = S.alloc<int>((size_t)nprob * S.kd);
     S.d_mask = S.alloc<int>((size_t)nprob * LD);
     S.d_status = S.alloc<int>(S.nk);
+    if (S.gs32) {
+        S.d_Sg = S.alloc<double2>((size_t)nprob * LD * LD);
+        S.d_Ub = S.alloc<double2>((size_t)nprob * LD * LD);
+        S.d_Tb = S.alloc<double2>((size_t)nprob * LD * LD);
+        S.d_statb = S.alloc<int>(nprob);
+    }
     if (S.rc) return S.rc;
     S.cuda(cudaMemcpyAsync(S.d_k, S.kd_host.data(), sizeof(EigK) * S.nk, cudaMemcpyHostToDevice, s));
     S.cuda(cudaMemsetAsync(S.d_Ysel, 0, sizeof(double2) * (size_t)nprob * LD * LD, s));

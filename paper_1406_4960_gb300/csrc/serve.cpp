@@ -68,15 +68,15 @@ size_t footprint_of(const mb_handle &h, int nbands, int prec) {
     const size_t nvecs = 3 * (size_t)std::max(mA, nblk * b) + 2 * (size_t)nblk * mB + 4 * nc + 3 * (size_t)mA +
                          (size_t)nblk * mB;
     size_t work = nvecs * vec_bytes + 2 * (size_t)std::max(M, nc) * vec_bytes / 2;
+    if (prec != MB_FP64) work += (size_t)(2 * M + nc * (1 + 2 * kd)) * vec_bytes / 2;   // FP32 Gram-Schmidt copies
     const size_t LD = 128;
-    work += (size_t)h.kp.size() * nc * LD * LD * 16 * 3 + (size_t)h.kp.size() * LD * LD * 16 * 3;
+    work += (size_t)h.kp.size() * nc * LD * LD * 16 * (prec != MB_FP64 ? 6 : 3) + (size_t)h.kp.size() * LD * LD * 16 * 3;
     work += (size_t)std::max<size_t>(304, h.kp.size() * nc) * 112 * 112 * 16;
     // apply scratch: boundary rows + projector overlaps (generous bound)
     size_t scratch = (size_t)h.kp.size() *
                      ((size_t)M * 40 * 2 * (h.order - 1) * maxldg * 16 +
                       2 * (size_t)M * std::max((size_t)16 * std::max(1, h.nzf) * maxldg,
                                                (size_t)h.nb * std::max(1, h.nproj)) * 16);
-    (void)prec;
     return tables + work + scratch + (64u << 20);   // + context-side slack per request
 }
 
