@@ -184,7 +184,7 @@ def eig_bench(h, w, args):
         nl = lib.mb_launch_count(h._h) - n0
         lib.mb_set_profiling(h._h, 0)
         kms = {}
-        for kid in range(11):
+        for kid in range(13):
             t_, c_ = ctypes.c_double(), ctypes.c_longlong()
             lib.mb_profile_read(h._h, kid, ctypes.byref(t_), ctypes.byref(c_))
             if c_.value:
@@ -403,7 +403,7 @@ def run_ours(args):
         if profile:
             import ctypes
             lib.mb_set_profiling(h._h, 0)
-            for kid in range(11):
+            for kid in range(13):
                 t, c = ctypes.c_double(), ctypes.c_longlong()
                 lib.mb_profile_read(h._h, kid, ctypes.byref(t), ctypes.byref(c))
                 if c.value:

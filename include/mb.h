@@ -174,7 +174,7 @@ typedef struct {
 } mb_solve_info;
 
 typedef struct {
-    int krylov_depth;     /* k of K = span{v, A v, ..., A^k v} (0: 4) */
+    int krylov_depth;     /* k of K = span{v, A v, ..., A^k v} (0: 5) */
     int block;            /* roots per block in the second grand cycle (0: 1) */
     int max_cycles;       /* (0: 200) */
     int polish;           /* reserved (0) */
@@ -254,7 +254,9 @@ void mb_server_destroy(mb_server *srv);
  * on, each launch is also bracketed by CUDA events on its own stream; the
  * per-kernel totals accumulate until mb_profile_reset.  Kernel ids:
  * 0 plane, 1 epilogue, 2 proj, 3 coef, 4 backproj, 5 banded, 6 gram,
- * 7 combine, 8 jacobi, 9 small, 10 vec (mb_kernel_name gives the names). */
+ * 7 combine, 8 jacobi, 9 small, 10 vec, 11 gram32, 12 combine32 (the FP32
+ * Gram-Schmidt products of the mixed-precision eigensolver); mb_kernel_name
+ * gives the names. */
 int mb_set_profiling(mb_handle *h, int on);
 int mb_profile_read(mb_handle *h, int kernel, double *ms_total, long long *count);
 int mb_profile_reset(mb_handle *h);

@@ -39,6 +39,7 @@ struct EigK {
     float2 *stage;            // FP32 staging for mixed-precision applies
     float2 *v32;              // FP32 copies for the Krylov Gram-Schmidt (mixed precision)
     const double *pfac;       // preconditioner factors of this k-point
+    const float *pfac32;      // the same in FP32 (the mixed-precision Krylov chains)
     long long nvec;           // nb * ldg
     int ldg, ng;
 };
@@ -59,13 +60,18 @@ static VSet vs(int s1, int c1, int cs1 = 0, int s2 = 0, int c2 = 0, int cs2 = 0)
 
 // ---------------------------------------------------------------------------
 // Fixed-order reduction of per-chunk partial Gram products (deterministic).
-__global__ void gram_reduce_kernel(const double2 *part, int nsplit, int ma, int mb, double2 *G) {
+// lower: only entries j <= i were computed (a Hermitian product); the upper
+// triangle is written as the conjugate of the lower one.
+__global__ void gram_reduce_kernel(const double2 *part, int nsplit, int ma, int mb, double2 *G, int lower) {
     const int prob = blockIdx.x;
     const int nout = ma * mb;
     for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int sp = 0; sp < nsplit; ++sp) s = s + part[((size_t)prob * nsplit + sp) * nout + o];
         int i = o / mb, j = o % mb;
+        const bool up = lower && j > i;
+        const int src = up ? j * mb + i : o;
+        double2 s = make_double2(0.0, 0.0);
+        for (int sp = 0; sp < nsplit; ++sp) s = s + part[((size_t)prob * nsplit + sp) * nout + src];
+        if (up) s.y = -s.y;
         G[(size_t)prob * LD * LD + i * LD + j] = s;
     }
 }
@@ -488,48 +494,55 @@ __global__ void eig_banded_S_kernel(const EigK *ks, const double *Sband, int nb,
 // L L^T y = x, one thread per (vector, G) column; the last K-1 solution values
 // ride in registers.  per_g: the k-point's factors L_G[j][d] stored as
 // pfac[(j*K + d)*ldg + G] (coalesced over G); else the G-independent L_z.
-template <int K>
-__global__ void eig_banded_solve_kernel(const EigK *ks, const double *Lb, int per_g, int nb, int src, int dst,
+// F32: on the FP32 Gram-Schmidt copies with FP32 factors (a preconditioner
+// solve, whose rounding only changes which Krylov space is built).
+template <int K, bool F32>
+__global__ void eig_banded_solve_kernel(const EigK *ks, const void *Lbv, int per_g, int nb, int src, int dst,
                                         int nv) {
+    typedef typename std::conditional<F32, float2, double2>::type T2;
+    typedef typename std::conditional<F32, float, double>::type T;
     const int k = blockIdx.z / nv, v = blockIdx.z % nv;
     const EigK d = ks[k];
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= d.ldg) return;
-    const double2 *x = d.base + (long long)(src + v) * d.nvec;
-    double2 *y = d.base + (long long)(dst + v) * d.nvec;
+    T2 *vb = F32 ? reinterpret_cast<T2 *>(d.v32) : reinterpret_cast<T2 *>(d.base);
+    const T *Lb = reinterpret_cast<const T *>(Lbv);
+    const T *pf = F32 ? reinterpret_cast<const T *>(d.pfac32) : reinterpret_cast<const T *>(d.pfac);
+    const T2 *x = vb + (long long)(src + v) * d.nvec;
+    T2 *y = vb + (long long)(dst + v) * d.nvec;
     const size_t ldg = d.ldg;
     if (g >= d.ng) {
-        for (int j = 0; j < nb; ++j) y[(size_t)j * ldg + g] = make_double2(0.0, 0.0);
+        for (int j = 0; j < nb; ++j) y[(size_t)j * ldg + g] = czero<T2>();
         return;
     }
     // factors hold L[j][j-d] for d >= 1 and 1 / L[j][j] at d = 0
-    auto L = [&](int j, int dd) -> double {
-        return per_g ? d.pfac[((size_t)j * K + dd) * ldg + g] : __ldg(&Lb[(size_t)j * K + dd]);
+    auto L = [&](int j, int dd) -> T {
+        return per_g ? pf[((size_t)j * K + dd) * ldg + g] : __ldg(&Lb[(size_t)j * K + dd]);
     };
-    double2 win[K];
+    T2 win[K];
 #pragma unroll
-    for (int i = 0; i < K; ++i) win[i] = make_double2(0.0, 0.0);
+    for (int i = 0; i < K; ++i) win[i] = czero<T2>();
 #pragma unroll 2
     for (int j = 0; j < nb; ++j) {
-        double2 s = x[(size_t)j * ldg + g];
+        T2 s = x[(size_t)j * ldg + g];
 #pragma unroll
         for (int dd = 1; dd < K; ++dd)
             if (j - dd >= 0) rfma(s, -L(j, dd), win[dd - 1]);
-        const double2 yj = rscale(L(j, 0), s);
+        const T2 yj = rscale(L(j, 0), s);
         y[(size_t)j * ldg + g] = yj;
 #pragma unroll
         for (int i = K - 1; i > 0; --i) win[i] = win[i - 1];
         win[0] = yj;
     }
 #pragma unroll
-    for (int i = 0; i < K; ++i) win[i] = make_double2(0.0, 0.0);
+    for (int i = 0; i < K; ++i) win[i] = czero<T2>();
 #pragma unroll 2
     for (int j = nb - 1; j >= 0; --j) {
-        double2 s = y[(size_t)j * ldg + g];
+        T2 s = y[(size_t)j * ldg + g];
 #pragma unroll
         for (int dd = 1; dd < K; ++dd)
             if (j + dd < nb) rfma(s, -L(j + dd, dd), win[dd - 1]);
-        const double2 zj = rscale(L(j, 0), s);
+        const T2 zj = rscale(L(j, 0), s);
         y[(size_t)j * ldg + g] = zj;
 #pragma unroll
         for (int i = K - 1; i > 0; --i) win[i] = win[i - 1];
@@ -541,12 +554,13 @@ __global__ void eig_banded_solve_kernel(const EigK *ks, const double *Lb, int pe
 // n-chunk with coalesced loads, each holding GJ complex partial sums in
 // registers, then reduce them by warp shuffles.  Grid: (n-chunks, problems,
 // row groups of 8 x column groups of GJ).
-constexpr int GJ = 16;
+// GJ, the column-group width, is picked per call so that predicated-off
+// column slots (which still occupy the FP64 pipe) are few.
 // F32: the vectors are the FP32 Gram-Schmidt copies (v32) and the partial
 // sums are FP32 (the reduction over chunks stays FP64).
-template <bool F32>
+template <bool F32, int GJ>
 __global__ void __launch_bounds__(256) gram_rows_kernel(const EigK *ks, int nch, VSet A, VSet B, int nsplit,
-                                                        int colgroups, double2 *part) {
+                                                        int colgroups, double2 *part, int lower) {
     typedef typename std::conditional<F32, float2, double2>::type T2;
     typedef typename std::conditional<F32, float, double>::type T;
     const int split = blockIdx.x, prob = blockIdx.y;
@@ -558,6 +572,7 @@ __global__ void __launch_bounds__(256) gram_rows_kernel(const EigK *ks, int nch,
     const int i = rg * 8 + warp;
     const int j0 = cg * GJ, nj = min(GJ, mb - j0);
     if (i >= ma || nj <= 0) return;                     // whole warp leaves together
+    if (lower && j0 > i) return;                        // tile above the diagonal
     const long long n = d.nvec;
     const long long chunk = (n + nsplit - 1) / nsplit;
     const long long t0 = split * chunk, t1 = min(n, t0 + chunk);
@@ -648,6 +663,35 @@ __global__ void herm_lower_kernel(double2 *G, int m) {
     } else if (i == j) {
         g[i * LD + i].y = 0.0;
     }
+}
+
+// [X|K]^H H [X|K] (and the S counterpart) when X holds Ritz vectors of the
+// last Rayleigh-Ritz (X^H H X = diag(eps), X^H S X = I): rows i >= M come
+// from the products KH = K^H H [X|K], KS = K^H S [X|K] (row i - M), the
+// upper triangle is their conjugate.  GS may be null (no S matrix).
+__global__ void assemble_rr_kernel(const double2 *KH, const double2 *KS, const double *eps, int M, int m,
+                                   double2 *GH, double2 *GS) {
+    const int k = blockIdx.y;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    const int i = e / m, j = e % m;
+    const size_t o = (size_t)k * LD * LD;
+    double2 h, sv;
+    if (i < M && j < M) {
+        h = make_double2(i == j ? eps[k * M + i] : 0.0, 0.0);
+        sv = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    } else if (i >= j) {
+        h = KH[o + (i - M) * LD + j];
+        sv = KS ? KS[o + (i - M) * LD + j] : make_double2(0.0, 0.0);
+    } else {
+        h = KH[o + (j - M) * LD + i];
+        h.y = -h.y;
+        sv = KS ? KS[o + (j - M) * LD + i] : make_double2(0.0, 0.0);
+        sv.y = -sv.y;
+    }
+    if (i == j) { h.y = 0.0; sv.y = 0.0; }
+    GH[o + i * LD + j] = h;
+    if (GS) GS[o + i * LD + j] = sv;
 }
 
 // dead slots (mask 0) of an S-Gram matrix become identity rows and columns,
@@ -861,7 +905,26 @@ struct Solver {
         return reinterpret_cast<T *>(p);
     }
 
-    void gram(int nch, VSet A, VSet B, double2 *G, bool f32 = false) {
+    // G = A^H B per problem; lower: A^H B is Hermitian (A and B span the same
+    // vectors in the same order), only j <= i is computed
+    void gram(int nch, VSet A, VSet B, double2 *G, bool f32 = false, bool lower = false) {
+        const int mbc = B.count();
+        // narrowest column group that covers mbc in the fewest slots
+        static const int widths[] = {1, 2, 3, 4, 5, 6, 7, 8, 12, 16};
+        int gj = 16;
+        long long best = 1ll << 40;
+        for (int w : widths) {
+            const long long slots = (long long)((mbc + w - 1) / w) * w;
+            const long long cost = slots * 64 + (mbc + w - 1) / w;   // column slots, then fewer groups
+            if (cost < best) { best = cost; gj = w; }
+        }
+        switch (gj) {
+#define MB_GJ(W) case W: gram_t<W>(nch, A, B, G, f32, lower); break;
+            MB_GJ(1) MB_GJ(2) MB_GJ(3) MB_GJ(4) MB_GJ(5) MB_GJ(6) MB_GJ(7) MB_GJ(8) MB_GJ(12) MB_GJ(16)
+#undef MB_GJ
+        }
+    }
+    template <int GJ> void gram_t(int nch, VSet A, VSet B, double2 *G, bool f32, bool lower) {
         const int nprob = nk * nch;
         const int ma = A.count(), mbc = B.count();
         const int rowgroups = (ma + 7) / 8, colgroups = (mbc + GJ - 1) / GJ;
@@ -870,12 +933,13 @@ struct Solver {
         nsplit = std::min<long long>(nsplit, std::max<long long>(1, nmax / 256));   // >= 256 elements per chunk
         while ((size_t)nprob * nsplit * ma * mbc > part_cap && nsplit > 1) --nsplit;
         if (f32)
-            MB_LAUNCH_E(KN_GRAM, gram_rows_kernel<true><<<dim3(nsplit, nprob, rowgroups * colgroups), 256, 0, s>>>(
-                                     d_k, nch, A, B, nsplit, colgroups, d_part));
+            MB_LAUNCH_E(KN_GRAM32, (gram_rows_kernel<true, GJ><<<dim3(nsplit, nprob, rowgroups * colgroups), 256, 0, s>>>(
+                                       d_k, nch, A, B, nsplit, colgroups, d_part, lower ? 1 : 0)));
         else
-            MB_LAUNCH_E(KN_GRAM, gram_rows_kernel<false><<<dim3(nsplit, nprob, rowgroups * colgroups), 256, 0, s>>>(
-                                     d_k, nch, A, B, nsplit, colgroups, d_part));
-        MB_LAUNCH_E(KN_GRAM, gram_reduce_kernel<<<nprob, 256, 0, s>>>(d_part, nsplit, ma, mbc, G));
+            MB_LAUNCH_E(KN_GRAM, (gram_rows_kernel<false, GJ><<<dim3(nsplit, nprob, rowgroups * colgroups), 256, 0, s>>>(
+                                     d_k, nch, A, B, nsplit, colgroups, d_part, lower ? 1 : 0)));
+        MB_LAUNCH_E(f32 ? KN_GRAM32 : KN_GRAM,
+                    gram_reduce_kernel<<<nprob, 256, 0, s>>>(d_part, nsplit, ma, mbc, G, lower ? 1 : 0));
     }
     void combine(int nch, VSet A, VSet C, const double2 *Y, double alpha, double beta, bool f32 = false) {
         if (f32) combine_t<true>(nch, A, C, Y, alpha, beta);
@@ -887,15 +951,15 @@ struct Solver {
         // column width with the least padding (12 divides the common 36)
         auto waste = [&](int jc) { return (mc + jc - 1) / jc * jc - mc; };
         if (mc == 1)
-            MB_LAUNCH_E(KN_COMBINE, (combine2_kernel<1, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
+            MB_LAUNCH_E(F32 ? KN_COMBINE32 : KN_COMBINE, (combine2_kernel<1, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
         else if (mc <= 4)
-            MB_LAUNCH_E(KN_COMBINE, (combine2_kernel<4, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
+            MB_LAUNCH_E(F32 ? KN_COMBINE32 : KN_COMBINE, (combine2_kernel<4, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
         else if (mc <= 8)
-            MB_LAUNCH_E(KN_COMBINE, (combine2_kernel<8, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
+            MB_LAUNCH_E(F32 ? KN_COMBINE32 : KN_COMBINE, (combine2_kernel<8, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
         else if (waste(12) < waste(16))
-            MB_LAUNCH_E(KN_COMBINE, (combine2_kernel<12, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
+            MB_LAUNCH_E(F32 ? KN_COMBINE32 : KN_COMBINE, (combine2_kernel<12, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
         else
-            MB_LAUNCH_E(KN_COMBINE, (combine2_kernel<16, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
+            MB_LAUNCH_E(F32 ? KN_COMBINE32 : KN_COMBINE, (combine2_kernel<16, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
     }
     void small_gemm(const double2 *A, const double2 *B, double2 *C, int m, int conjA, int np = 0) {
         MB_LAUNCH_E(KN_SMALL, small_zgemm_kernel<<<dim3((m * m + 127) / 128, np > 0 ? np : nk), 128, 0, s>>>(
@@ -913,11 +977,17 @@ struct Solver {
 #undef MB_BS
         }
     }
-    void bandSolve(int per_g, int src, int dst, int nv) {
+    void bandSolve(int per_g, int src, int dst, int nv, bool f32 = false) {
         const dim3 grid((maxldg + 63) / 64, 1, nk * nv);
-        const double *Lb = (const double *)h->t64.Lrecip;
+        const void *Lb = f32 ? h->t32.Lrecip : h->t64.Lrecip;
         switch (h->order) {
-#define MB_BL(KK) case KK: MB_LAUNCH_E(KN_BANDED, eig_banded_solve_kernel<KK><<<grid, 64, 0, s>>>(d_k, Lb, per_g, h->nb, src, dst, nv)); break;
+#define MB_BL(KK)                                                                                                 \
+    case KK:                                                                                                      \
+        if (f32)                                                                                                  \
+            MB_LAUNCH_E(KN_BANDED, (eig_banded_solve_kernel<KK, true><<<grid, 64, 0, s>>>(d_k, Lb, per_g, h->nb, src, dst, nv))); \
+        else                                                                                                      \
+            MB_LAUNCH_E(KN_BANDED, (eig_banded_solve_kernel<KK, false><<<grid, 64, 0, s>>>(d_k, Lb, per_g, h->nb, src, dst, nv))); \
+        break;
             MB_BL(3) MB_BL(4) MB_BL(5) MB_BL(6) MB_BL(7) MB_BL(8)
 #undef MB_BL
         }
@@ -972,13 +1042,14 @@ struct Solver {
             }
             MB_LAUNCH_E(KN_VEC, krylov_residual_kernel<<<dim3((unsigned)std::min<long long>(1024, (nmax + 255) / 256), np), 256, 0, s>>>(
                                     d_k, nch, d_srcH, d_srcS, d_theta, oW));
-            bandSolve(1, oW, oW, nch);
+            if (!gs32) bandSolve(1, oW, oW, nch);
             // classical Gram-Schmidt, twice, in the S inner product: all
             // coefficients of a pass come from the same (pre-update) vector.
             // The roots X are common to every chain of a k-point, so their
             // part is one product with a column per chain.
             if (gs32) {
                 copy(nch, vs(oW, 1, 1), vs(o32W, 1, 1), 3);
+                bandSolve(1, o32W, o32W, nch, true);
                 for (int pass = 0; pass < 2; ++pass) {
                     gram(1, vs(o32SX, M), vs(o32W, nch), d_G2, true);
                     if (i > 0) gram(nch, vs(o32SK, i, kd), vs(o32W, 1, 1), d_G, true);
@@ -1030,11 +1101,14 @@ struct Solver {
     // identity), Ritz pairs of U^H (V^H H V) U; returns the Ritz vectors'
     // coordinates in the V basis (U Y) and leaves the values in d_evals.
     const double2 *rr_pencil(int nch, VSet V, VSet HV, VSet SV, int m, int ofs) {
+        gram(nch, V, HV, d_G, false, true);
+        gram(nch, V, SV, d_Sg, false, true);
+        return pencil_solve(nch, m, ofs);
+    }
+    // the pencil (d_G, d_Sg) of nch problems per k-point
+    const double2 *pencil_solve(int nch, int m, int ofs) {
         const int np = nk * nch;
-        gram(nch, V, HV, d_G);
-        gram(nch, V, SV, d_Sg);
         const dim3 gs((m * m + 127) / 128, np);
-        MB_LAUNCH_E(KN_SMALL, herm_lower_kernel<<<gs, 128, 0, s>>>(d_G, m));
         MB_LAUNCH_E(KN_SMALL, alive_mask_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_alive, kd, ofs, M, b, nch, m, np, d_mask));
         MB_LAUNCH_E(KN_SMALL, mask_sgram_kernel<<<gs, 128, 0, s>>>(d_Sg, d_mask, m));
         cuda(smem_limit_once((const void *)cholinv_kernel, h->device, h->smem_optin));
@@ -1054,13 +1128,25 @@ struct Solver {
         copy(1, vs(oT + M, M), vs(oHV, M), 0);
         bandS(oV, oSV, M);
     }
+    // Rayleigh-Ritz on [X | K_A] (withK) or on X.  With K_A, X holds the Ritz
+    // vectors of the last Rayleigh-Ritz, so only the Krylov rows of the
+    // projected matrices are computed.
     void rr_full(bool withK) {
         int m = withK ? mA : M;
-        if (gs32 && withK) {
-            rotate_set(rr_pencil(1, vs(oV, m), vs(oHV, m), vs(oSV, m), m, M), m);
+        if (withK) {
+            gram(1, vs(oV + M, kd), vs(oHV, m), d_G2);
+            if (gs32) gram(1, vs(oV + M, kd), vs(oSV, m), d_T);
+            MB_LAUNCH_E(KN_SMALL, assemble_rr_kernel<<<dim3((m * m + 127) / 128, nk), 128, 0, s>>>(
+                                      d_G2, gs32 ? d_T : nullptr, d_eps, M, m, d_G, gs32 ? d_Sg : nullptr));
+            if (gs32) {
+                rotate_set(pencil_solve(1, m, M), m);
+            } else {
+                jacobi(1, m, true, M);
+                rotate_set(d_Y, m);
+            }
         } else {
-            gram(1, vs(oV, m), vs(oHV, m), d_G);
-            jacobi(1, m, withK, M);
+            gram(1, vs(oV, m), vs(oHV, m), d_G, false, true);
+            jacobi(1, m, false, M);
             rotate_set(d_Y, m);
         }
         MB_LAUNCH_E(KN_SMALL, take_evals_kernel<<<(M * nk + 127) / 128, 128, 0, s>>>(d_evals, M, nk, d_eps));
@@ -1068,11 +1154,11 @@ struct Solver {
     // S-orthonormalization and Rayleigh-Ritz in one rotation: U = L^{-H} from
     // X^H S X = L L^H, Ritz pairs of U^H (X^H H X) U, then X <- X U Y.
     void orth_rr() {
-        gram(1, vs(oV, M), vs(oSV, M), d_G);
+        gram(1, vs(oV, M), vs(oSV, M), d_G, false, true);
         size_t smem = (size_t)M * M * sizeof(double2);
         cuda(smem_limit_once((const void *)cholinv_kernel, h->device, h->smem_optin));
         MB_LAUNCH_E(KN_SMALL, cholinv_kernel<<<nk, 128, smem, s>>>(d_G, M, d_U, d_status));
-        gram(1, vs(oV, M), vs(oHV, M), d_G2);
+        gram(1, vs(oV, M), vs(oHV, M), d_G2, false, true);
         small_gemm(d_G2, d_U, d_T, M, 0);     // (X^H H X) U
         small_gemm(d_U, d_T, d_G, M, 1);      // U^H (X^H H X) U
         jacobi(1, M, false, M);
@@ -1090,7 +1176,7 @@ struct Solver {
         if (gs32) {
             Yc = rr_pencil(nblk, vs(oVB, mB, mB), vs(oHVB, mB, mB), vs(oSVB, mB, mB), mB, b);
         } else {
-            gram(nblk, vs(oVB, mB, mB), vs(oHVB, mB, mB), d_G);
+            gram(nblk, vs(oVB, mB, mB), vs(oHVB, mB, mB), d_G, false, true);
             jacobi(nblk, mB, true, b);
         }
         int np = nk * nblk;
@@ -1196,6 +1282,7 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
         e.stage = S.alloc<float2>((size_t)2 * S.nc_stage() * e.nvec);
         e.v32 = S.gs32 ? S.alloc<float2>((size_t)S.n32 * e.nvec) : nullptr;
         e.pfac = (const double *)h->t64.Pfac + pofs;
+        e.pfac32 = (const float *)h->t32.Pfac + pofs;
         pofs += (size_t)e.ldg * h->nb * h->order;
         if (S.rc) return S.rc;
         S.cuda(cudaMemsetAsync(e.base, 0, sizeof(double2) * (size_t)S.nvecs * e.nvec, s));

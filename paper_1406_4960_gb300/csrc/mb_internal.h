@@ -133,12 +133,12 @@ enum { BAND_S = 0, BAND_SINV = 1, BAND_PREC = 2 };
 // eigensolver defaults: Krylov depth and roots per block of the second grand
 // cycle (one root per block: every root gets its own Krylov space, which
 // needed the fewest FP64 operations to 1e-6 Ha on the slab and graphene cells)
-constexpr int kDefaultKrylovDepth = 4;
+constexpr int kDefaultKrylovDepth = 5;
 constexpr int kDefaultBlock = 1;
 
 // kernel ids for launch accounting / profiling
 enum { KN_PLANE = 0, KN_EPILOGUE, KN_PROJ, KN_COEF, KN_BACKPROJ, KN_BANDED, KN_GRAM, KN_COMBINE,
-       KN_JACOBI, KN_SMALL, KN_VEC, KN_COUNT };
+       KN_JACOBI, KN_SMALL, KN_VEC, KN_GRAM32, KN_COMBINE32, KN_COUNT };
 extern const char *const kKernelNames[KN_COUNT];
 void prof_begin(mb_handle *h, cudaStream_t s, int kernel, cudaEvent_t *a);
 void prof_end(mb_handle *h, cudaStream_t s, int kernel, cudaEvent_t a);

@@ -26,7 +26,7 @@ cudaError_t smem_limit_once(const void *func, int device, int bytes) {
 
 const char *const kKernelNames[KN_COUNT] = {
     "plane", "epilogue", "proj", "coef", "backproj", "banded", "gram", "combine",
-    "jacobi", "small", "vec"};
+    "jacobi", "small", "vec", "gram32", "combine32"};
 
 void prof_begin(mb_handle *h, cudaStream_t s, int kernel, cudaEvent_t *a) {
     h->launches++;
