@@ -87,10 +87,11 @@ __device__ __forceinline__ void fft_reg(C (&x)[N]) {
     }
 }
 
-// FP32 grids with both sides <= 32 run two CTAs per SM (the host plan sizes
-// shared memory for that); the register budget follows.
+// FP32 grids of at most 512 points run three CTAs per SM, other FP32 grids
+// with both sides <= 32 two (the host plan sizes shared memory for that);
+// the register budget follows.
 template <typename R, int N1, int N2>
-__global__ void __launch_bounds__(256, (N1 <= 32 && N2 <= 32 && sizeof(R) == 4) ? 2 : 1)
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && N1 * N2 <= 512) ? 3 : (N1 <= 32 && N2 <= 32 && sizeof(R) == 4) ? 2 : 1)
     plane_reg_kernel(const __grid_constant__ PlaneArgs<R> a) {
     typedef typename V2<R>::T C;
     constexpr int LDP = N2 + 1;
