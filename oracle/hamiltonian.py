@@ -15,7 +15,11 @@ Elements, in Hartree (the paper's Rydberg -nabla^2 becomes -nabla^2/2):
 * a general local potential given by its in-plane Fourier components per z,
   Eqs. (19)-(20): <i|V|i'>(dG) = int B_i B_i' V(z, dG) dz;
 * Kleinman-Bylander projectors, Eqs. (14)-(17) and the Z.Q factorization that
-  follows them: s (n=1) and a real p_x, p_y, p_z set per atom.
+  follows them: s (n=1), a real p_x, p_y, p_z set, and optionally the second
+  s channel (n=2, beta ~ r^2 exp(-alpha r^2)) whose projection is the sum
+  Z_{1,00} Q_{2,00} + Z_{2,00} Q_{1,00} (r^2 split into its in-plane and z
+  parts).  The strengths form a Hermitian matrix per atom: E_{nl} on the
+  diagonal and an optional 1s-2s coupling (the general E_{nl,n'l'} of GTH).
 
 Readings:
 * Gaussian local term A exp(-|r-R|^2/(2 w^2)), i.e. a = 1/(2 w^2);
@@ -25,6 +29,7 @@ Readings:
   x exp(-alpha r^2) carries a factor i that the printed Q_{1,1+-1} omits; it is
   a constant phase per projector and cancels in |beta><beta|;
 * C normalizes each projector to int |beta|^2 d^3r = 1;
+* one Gaussian radius per atom: alpha_0 = alpha_1 = 1 / (2 r_c^2);
 * dG is wrapped to the grid frequency range [-N/2, N/2) per axis, which is what
   a product on an N1 x N2 grid computes; the unwrapped element differs by terms
   of size exp(-g_Nyquist^2 / 4a).
@@ -133,8 +138,11 @@ class Model:
 
     # ---- Kleinman-Bylander projectors (Eqs. (14)-(17), Z.Q factors) ----
     def kb_projectors(self):
-        """(E (nproj,), U (nproj, nb, ng)) with V_NL = sum_p E_p u_p u_p^H."""
-        Es, Us = [], []
+        """(E (nproj, nproj), U (nproj, nb, ng)) with V_NL = sum_pq E_pq u_p u_q^H.
+
+        Per atom the projectors are 1s, p_x, p_y, p_z and (nproj == 5) 2s; E
+        is block diagonal over atoms, diagonal but for the 1s-2s coupling."""
+        Es, Us, blocks = [], [], []
         for at in self.atoms:
             if at.nproj == 0:
                 continue
@@ -144,20 +152,36 @@ class Model:
             gz = np.exp(-alpha * dz * dz)
             Z0 = self.zb.B.T @ (self.zb.wq * gz)            # Z_{1,00}, Z_{1,1+-1}
             Z1 = self.zb.B.T @ (self.zb.wq * dz * gz)       # Z_{1,10}
+            Z2 = self.zb.B.T @ (self.zb.wq * dz * dz * gz)  # Z_{2,00}
             Qs = (math.pi / alpha) * np.exp(-self.q2 / (4.0 * alpha))
             Qx = 1j * (self.q[:, 0] / (2.0 * alpha)) * Qs
             Qy = 1j * (self.q[:, 1] / (2.0 * alpha)) * Qs
+            Q2 = (1.0 / alpha - self.q2 / (4.0 * alpha * alpha)) * Qs   # Q_{2,00}
             Cs = (2.0 * alpha / math.pi) ** 0.75
             Cp = 2.0 * math.sqrt(alpha) * Cs
+            # int (r^2)^2 exp(-2 alpha r^2) d^3r = 4 pi (15/16) sqrt(pi) (2 alpha)^{-7/2}
+            C2 = (4.0 * math.pi * 15.0 / 16.0 * math.sqrt(math.pi) * (2.0 * alpha) ** -3.5) ** -0.5
             phase = np.exp(-1j * (self.q[:, 0] * at.pos[0] + self.q[:, 1] * at.pos[1]))
             fs = [Cs * np.outer(Z0, Qs), Cp * np.outer(Z0, Qx),
-                  Cp * np.outer(Z0, Qy), Cp * np.outer(Z1, Qs)]
+                  Cp * np.outer(Z0, Qy), Cp * np.outer(Z1, Qs),
+                  C2 * (np.outer(Z0, Q2) + np.outer(Z2, Qs))]
+            if at.nproj not in (4, 5):
+                raise ValueError("nproj must be 0, 4 or 5")
             for p in range(at.nproj):
                 Us.append(phase[None, :] * np.conj(fs[p]) / math.sqrt(self.Ac))
-                Es.append(at.E[p])
+            Eb = np.diag(np.array(list(at.E) + ([at.e2s] if at.nproj == 5 else []), dtype=float))
+            if at.nproj == 5:
+                Eb[0, 4] = Eb[4, 0] = at.e12
+            blocks.append(Eb)
         if not Us:
-            return np.zeros(0), np.zeros((0, self.nb, self.ng), dtype=np.complex128)
-        return np.array(Es), np.array(Us)
+            return np.zeros((0, 0)), np.zeros((0, self.nb, self.ng), dtype=np.complex128)
+        n = sum(b.shape[0] for b in blocks)
+        E = np.zeros((n, n))
+        o = 0
+        for b in blocks:
+            E[o:o + b.shape[0], o:o + b.shape[0]] = b
+            o += b.shape[0]
+        return E, np.array(Us)
 
     # ---- dense matrices -------------------------------------------------
     def dense_S(self):
@@ -174,9 +198,9 @@ class Model:
         for I, F in self.local_terms():
             H += np.kron(I, F)
         E, U = self.kb_projectors()
-        for p in range(len(E)):
-            u = U[p].reshape(-1)
-            H += E[p] * np.outer(u, np.conj(u))
+        if len(E):
+            Uf = U.reshape(len(E), -1).T
+            H += Uf @ E @ Uf.conj().T
         return H
 
     # ---- matrix-free apply (the same elements, contracted directly) ----
@@ -193,7 +217,7 @@ class Model:
         E, U = self.kb_projectors()
         if len(E):
             Fp = np.einsum("pjg,bjg->pb", np.conj(U), X)
-            Y += np.einsum("p,pjg,pb->bjg", E, U, Fp)
+            Y += np.einsum("pq,pjg,qb->bjg", E, U, Fp)
         return Y
 
     def apply_H_entries(self, X, entries):
@@ -209,7 +233,7 @@ class Model:
             for I, F in terms:
                 v += I[i] @ X[b] @ F[g]
             if Fp is not None:
-                v += np.sum(E * U[:, i, g] * Fp[:, b])
+                v += U[:, i, g] @ (E @ Fp[:, b])
             out[n] = v
         return out
 

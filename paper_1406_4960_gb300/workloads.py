@@ -46,9 +46,11 @@ class Atom:
     pos: Tuple[float, float, float]      # cartesian, bohr
     A: float                             # local Gaussian amplitude, Ha
     w: float                             # local Gaussian width, bohr
-    nproj: int = 0                       # 0 or 4 (s, px, py, pz)
+    nproj: int = 0                       # 0, 4 (1s, px, py, pz) or 5 (+ 2s)
     E: Tuple[float, float, float, float] = (0.0, 0.0, 0.0, 0.0)
     rc: float = 1.0                      # KB Gaussian radius, bohr
+    e2s: float = 0.0                     # E of the second s channel (nproj == 5), Ha
+    e12: float = 0.0                     # 1s-2s coupling E_{12} = E_{21} (nproj == 5), Ha
 
 
 @dataclasses.dataclass

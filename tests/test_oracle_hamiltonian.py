@@ -213,7 +213,7 @@ def test_hamiltonian_structure():
     assert np.abs(H - H.conj().T).max() < 1e-14
     Es, U = m.kb_projectors()
     Unl = U.reshape(len(Es), -1).T
-    Hnl = Unl @ np.diag(Es) @ Unl.conj().T
+    Hnl = Unl @ Es @ Unl.conj().T
     assert np.linalg.matrix_rank(Hnl, tol=1e-10 * np.abs(Hnl).max()) <= len(Es)
     w0 = dataclasses.replace(w, atoms=[dataclasses.replace(a, E=(0, 0, 0, 0)) for a in w.atoms])
     wl = dataclasses.replace(w, atoms=[dataclasses.replace(a, nproj=0) for a in w.atoms])
@@ -279,3 +279,111 @@ def test_p_channel_differs_from_s_only():
     e1 = _eigs(Hm.model_from_workload(w), 14)
     e2 = _eigs(Hm.model_from_workload(w2), 14)
     assert np.abs(e1 - e2).max() > 1e-4
+
+
+# --------------------------------------------------------------------------
+# second s channel (n = 2) and the 1s-2s coupling
+def _small2s(e12=0.23, e2s=-0.35, **kw):
+    w = _small(with_kb=True, **kw)
+    atoms = [dataclasses.replace(a, nproj=5, e2s=e2s, e12=e12) for a in w.atoms]
+    return dataclasses.replace(w, atoms=atoms)
+
+
+def test_second_s_channel_transform_and_normalization():
+    """Q_{2,00} closed form vs a Riemann sum of (x^2 + y^2) exp(-alpha r^2)
+    e^{iq.r}, and int |beta_2s|^2 = 1 for beta_2s = C r^2 exp(-alpha r^2)
+    from separable 1D integrals ((x^2+y^2+z^2)^2 expanded)."""
+    alpha = 1.0 / (2 * 1.1 ** 2)
+    L, n = 16.0, 400
+    x = (np.arange(n) + 0.5) / n * 2 * L - L
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    dA = (2 * L / n) ** 2
+    r2 = X * X + Y * Y
+    gauss = np.exp(-alpha * r2)
+    for q in ([0.0, 0.0], [0.7, -0.3], [1.9, 1.2]):
+        ph = np.exp(1j * (q[0] * X + q[1] * Y))
+        num = np.sum(r2 * ph * gauss) * dA
+        q2 = q[0] ** 2 + q[1] ** 2
+        closed = (1 / alpha - q2 / (4 * alpha ** 2)) * math.pi / alpha * math.exp(-q2 / (4 * alpha))
+        assert abs(num - closed) < 1e-9
+    t = np.linspace(-20, 20, 400001)
+    h = t[1] - t[0]
+    gk = [np.sum(t ** k * np.exp(-2 * alpha * t * t)) * h for k in (0, 2, 4)]
+    norm_int = 3 * gk[2] * gk[0] ** 2 + 6 * gk[1] ** 2 * gk[0]
+    C2 = (4.0 * math.pi * 15.0 / 16.0 * math.sqrt(math.pi) * (2.0 * alpha) ** -3.5) ** -0.5
+    assert abs(C2 ** 2 * norm_int - 1) < 1e-10
+
+
+def test_second_s_projector_by_direct_integration():
+    """u_2s(G, i) = A_c^{-1/2} int exp(-i(k+G).r) B_i(z) C r^2 exp(-alpha r^2) d^3r
+    (r relative to the atom) by a Riemann sum in plane and a fine z rule."""
+    w = _small2s(k=(0.23, -0.11))
+    m = Hm.model_from_workload(w)
+    Emat, U = m.kb_projectors()
+    assert U.shape[0] == 10 and Emat.shape == (10, 10)
+    at = w.atoms[1]
+    alpha = 1.0 / (2 * at.rc ** 2)
+    C2 = (4.0 * math.pi * 15.0 / 16.0 * math.sqrt(math.pi) * (2.0 * alpha) ** -3.5) ** -0.5
+    L, n = 14.0, 280
+    x = (np.arange(n) + 0.5) / n * 2 * L - L
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    dA = (2 * L / n) ** 2
+    zz = np.linspace(w.breaks[0], w.breaks[-1], 12001)
+    hz = zz[1] - zz[0]
+    Bz = np.array([m.zb.values(z) for z in zz])
+    wz = np.full_like(zz, hz)
+    wz[0] = wz[-1] = hz / 2
+    rng = np.random.default_rng(2)
+    for _ in range(6):
+        g = int(rng.integers(0, m.ng))
+        i = int(rng.integers(0, m.nb))
+        q = m.q[g]
+        ph = np.exp(-1j * (q[0] * (X + at.pos[0]) + q[1] * (Y + at.pos[1])))
+        rho2 = X * X + Y * Y
+        rad = np.exp(-alpha * rho2)
+        dz = zz - at.pos[2]
+        gz = np.exp(-alpha * dz * dz) * Bz[:, i]
+        val = C2 * (np.sum(ph * rho2 * rad) * dA * (wz @ gz) + np.sum(ph * rad) * dA * (wz @ (dz * dz * gz)))
+        ref = val / math.sqrt(m.Ac)
+        assert abs(U[5 + 4, i, g] - ref) < 2e-6 * max(1e-3, abs(ref)), (U[9, i, g], ref)
+    # the strengths: E_1s, E_p, E_2s on the diagonal, E_12 coupling 1s <-> 2s
+    assert Emat[0, 4] == Emat[4, 0] == 0.23 and Emat[4, 4] == -0.35 and Emat[0, 0] == 0.7
+    assert np.count_nonzero(Emat - np.diag(np.diag(Emat))) == 4
+
+
+def test_second_s_channel_structure():
+    w = _small2s(k=(0.1, 0.2))
+    m = Hm.model_from_workload(w)
+    H = m.dense_H()
+    assert np.abs(H - H.conj().T).max() < 1e-14
+    Emat, U = m.kb_projectors()
+    Unl = U.reshape(len(Emat), -1).T
+    Hnl = Unl @ Emat @ Unl.conj().T
+    assert np.linalg.matrix_rank(Hnl, tol=1e-10 * np.abs(Hnl).max()) <= len(Emat)
+    # all strengths zero == no projectors at all
+    w0 = dataclasses.replace(w, atoms=[dataclasses.replace(a, E=(0, 0, 0, 0), e2s=0.0, e12=0.0) for a in w.atoms])
+    wl = dataclasses.replace(w, atoms=[dataclasses.replace(a, nproj=0) for a in w.atoms])
+    assert np.abs(Hm.model_from_workload(w0).dense_H() - Hm.model_from_workload(wl).dense_H()).max() < 1e-15
+    # with E_2s = E_12 = 0 the fifth projector drops out
+    w4 = dataclasses.replace(w, atoms=[dataclasses.replace(a, nproj=4) for a in w.atoms])
+    wz = dataclasses.replace(w, atoms=[dataclasses.replace(a, e2s=0.0, e12=0.0) for a in w.atoms])
+    assert np.abs(Hm.model_from_workload(w4).dense_H() - Hm.model_from_workload(wz).dense_H()).max() < 1e-14
+    # matrix-free apply and single entries against the dense matrix
+    X = W.random_block(3, m.nb, m.ng, 9)
+    Y = m.apply_H(X)
+    Yd = (H @ X.reshape(3, -1).T).T.reshape(X.shape)
+    assert np.abs(Y - Yd).max() < 1e-12 * np.abs(Yd).max()
+    ent = [(0, 1, 2), (2, m.nb - 1, m.ng - 1)]
+    assert np.abs(m.apply_H_entries(X, ent) - np.array([Y[e] for e in ent])).max() < 1e-12 * np.abs(Y).max()
+    # the coupling moves the spectrum; translation, time reversal and z reflection do not
+    e1 = _eigs(m, 14)
+    wc = dataclasses.replace(w, atoms=[dataclasses.replace(a, e12=0.0) for a in w.atoms])
+    assert np.abs(_eigs(Hm.model_from_workload(wc), 14) - e1).max() > 1e-5
+    t = np.array([1.37, -0.58])
+    wt = dataclasses.replace(w, atoms=[dataclasses.replace(a, pos=(a.pos[0] + t[0], a.pos[1] + t[1], a.pos[2]))
+                                       for a in w.atoms])
+    assert np.abs(_eigs(Hm.model_from_workload(wt), 14) - e1).max() < 1e-11
+    wm = dataclasses.replace(w, kpts=-w.kpts)
+    assert np.abs(_eigs(Hm.model_from_workload(wm), 14) - e1).max() < 1e-11
+    wr = dataclasses.replace(w, atoms=[dataclasses.replace(a, pos=(a.pos[0], a.pos[1], -a.pos[2])) for a in w.atoms])
+    assert np.abs(_eigs(Hm.model_from_workload(wr), 14) - e1).max() < 1e-11
