@@ -56,10 +56,13 @@ typedef struct { double a1[2]; double a2[2]; } mb_cell;
 /* One atom of the surface unit cell.
  * Local pseudopotential (§II.B.1, Eq. (10), Gaussian part):
  *     A * exp(-|r - pos|^2 / (2 w^2))            (A in Ha, w in bohr)
- * Kleinman-Bylander projectors (Eq. (14)), GTH Gaussian radial part with
- * alpha = 1 / (2 rc^2): nproj = 0 (none) or 4 (s, p_x, p_y, p_z), each
- * normalized to unit norm, with strengths E[0..3] in Ha (a physical p
- * channel has E[1] = E[2] = E[3]). */
+ * Kleinman-Bylander projectors (Eq. (14)), GTH Gaussian radial parts with
+ * alpha = 1 / (2 rc^2) for every channel: nproj = 0 (none), 4 (1s, p_x, p_y,
+ * p_z) or 5 (the same and the second s channel, beta ~ r^2 exp(-alpha r^2),
+ * whose projection is Z_{1,00} Q_{2,00} + Z_{2,00} Q_{1,00}), each normalized
+ * to unit norm.  Strengths in Ha: E[0..3] for 1s, p_x, p_y, p_z (a physical p
+ * channel has E[1] = E[2] = E[3]), E2s for 2s and E12 for the 1s-2s coupling
+ * (the off-diagonal element of GTH's h matrix; used when nproj = 5). */
 typedef struct {
     double pos[3];
     double A;
@@ -67,6 +70,8 @@ typedef struct {
     int nproj;
     double E[4];
     double rc;
+    double E2s;
+    double E12;
 } mb_atom;
 
 typedef struct {

@@ -168,21 +168,25 @@ __global__ void __launch_bounds__(256) plane_kernel(const __grid_constant__ Plan
 }
 
 // ---------------------------------------------------------------------------
-// Kleinman-Bylander term of Eq. (17) with the factorized projectors
-// u_p(G, j) = z_p(j) q_p(G).  The z factor is shared by many projectors
-// (s, p_x and p_y of one atom; all atoms at one height and radius), so with
-// f(p) the distinct z factor of projector p:
-//   Zx[b][f][G] = sum_j z_f(j) X[b][j][G]                  (nl_zx)
-//   c_p(b)      = E_p sum_G conj(q_p(G)) Zx[b][f(p)][G]     (nl_coef)
-//   Y[b][j][G] += sum_f z_f(j) sum_{p: f(p)=f} c_p(b) q_p(G) (in the epilogue)
-// which is sum_p E_p u_p (u_p^H X) with nb*nz + nproj (not nb*nproj)
+// Kleinman-Bylander term of Eq. (17).  Every projector is a sum of
+// separable terms u_p(G, j) = sum_{t in p} z_t(j) q_t(G) (one term for 1s
+// and p, two for 2s), and the z factors repeat (s, p_x, p_y of one atom; all
+// atoms at one height and radius), so with f(t) the distinct z factor of
+// term t:
+//   Zx[b][f][G] = sum_j z_f(j) X[b][j][G]                            (nl_zx)
+//   F_p(b)      = sum_{t in p} sum_G conj(q_t(G)) Zx[b][f(t)][G]
+//   c_p(b)      = E_p F_p(b) + E'_p F_{partner(p)}(b)                (nl_coef)
+//   Y[b][j][G] += sum_f z_f(j) sum_{t: f(t)=f} c_{p(t)}(b) q_t(G)     (epilogue)
+// which is sum_pq E_pq u_p (u_q^H X) with nb*nz + nterm (not nb*nterm)
 // multiply-adds per (band, G).
 template <typename R> struct NlArgs {
     const R *zf;                    // nz x nb distinct z factors
-    const R *E;                     // nproj
-    const int *pgroup;              // nproj: f(p)
-    const typename V2<R>::T *Q;     // q_p(G), all k (offset qofs)
-    int nb, nbands, nproj, nz, nseg;
+    const R *E;                     // nkb strengths E_p, then nkb couplings E'_p
+    const int *pgroup;              // nterm: f(t)
+    const int *partner;             // nkb: coupled projector or -1
+    const int *pstart, *plist;      // terms of projector p: plist[pstart[p] .. pstart[p+1])
+    const typename V2<R>::T *Q;     // q_t(G), all k (offset qofs)
+    int nb, nbands, nterm, nkb, nz, nseg;
     KDesc d[kMaxK];
 };
 
@@ -244,28 +248,45 @@ __global__ void __launch_bounds__(512) nl_zx_kernel(const __grid_constant__ NlAr
     }
 }
 
-// one warp per (band, k-point, projector); the sum over G runs in a fixed order
+// F_p(b) of one projector (all its terms) summed by one warp in a fixed order
+template <typename R>
+__device__ __forceinline__ typename V2<R>::T nl_overlap(const NlArgs<R> &a, const KDesc &d, int b, int p,
+                                                        int lane) {
+    typedef typename V2<R>::T R2;
+    const int ldg = d.ldg;
+    R2 s = czero<R2>();
+    for (int i = a.pstart[p]; i < a.pstart[p + 1]; ++i) {
+        const int t = a.plist[i];
+        const R2 *z = reinterpret_cast<const R2 *>(d.W) + ((size_t)b * a.nz + a.pgroup[t]) * ldg;
+        const R2 *q = a.Q + d.qofs + (size_t)t * ldg;
+#pragma unroll 4
+        for (int g = lane; g < d.ng; g += 32) {
+            const R2 qg = q[g];
+            cfma(s, mk(qg.x, -qg.y), z[g]);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        s.x += __shfl_down_sync(0xffffffffu, s.x, off);
+        s.y += __shfl_down_sync(0xffffffffu, s.y, off);
+    }
+    return s;   // complete in lane 0
+}
+
+// one warp per (band, k-point, projector): c_p = E_p F_p + E'_p F_partner
 template <typename R>
 __global__ void __launch_bounds__(256) nl_coef_kernel(const __grid_constant__ NlArgs<R> a) {
     typedef typename V2<R>::T R2;
     const int b = blockIdx.x;
     const KDesc &d = a.d[blockIdx.y];
     const int p = blockIdx.z * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (p >= a.nproj) return;
-    const int ldg = d.ldg;
-    const R2 *z = reinterpret_cast<const R2 *>(d.W) + ((size_t)b * a.nz + a.pgroup[p]) * ldg;
-    const R2 *q = a.Q + d.qofs + (size_t)p * ldg;
-    R2 s = czero<R2>();
-#pragma unroll 4
-    for (int g = lane; g < d.ng; g += 32) {
-        const R2 qg = q[g];
-        cfma(s, mk(qg.x, -qg.y), z[g]);
+    if (p >= a.nkb) return;
+    R2 c = rscale(a.E[p], nl_overlap(a, d, b, p, lane));
+    const int q = a.partner[p];
+    if (q >= 0) {
+        const R2 fq = nl_overlap(a, d, b, q, lane);
+        rfma(c, a.E[a.nkb + p], fq);
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        s.x += __shfl_down_sync(0xffffffffu, s.x, off);
-        s.y += __shfl_down_sync(0xffffffffu, s.y, off);
-    }
-    if (lane == 0) reinterpret_cast<R2 *>(d.C)[(size_t)b * a.nproj + p] = rscale(a.E[p], s);
+    if (lane == 0) reinterpret_cast<R2 *>(d.C)[(size_t)b * a.nkb + p] = c;
 }
 
 // ---------------------------------------------------------------------------
@@ -277,9 +298,10 @@ __global__ void __launch_bounds__(256) nl_coef_kernel(const __grid_constant__ Nl
 template <typename R> struct EpiArgs {
     const R *Sband, *Dband, *q2;
     const R *zf;                    // nz x nb
-    const int *zstart, *zlist;      // projectors of each distinct z factor
-    const typename V2<R>::T *Q;     // q_p(G)
-    int order, nb, nbands, nchunks, nint, nproj, f0, f1, base, njseg;
+    const int *zstart, *zlist;      // terms of each distinct z factor
+    const int *tproj;               // nterm: projector of each term
+    const typename V2<R>::T *Q;     // q_t(G)
+    int order, nb, nbands, nchunks, nint, nterm, nkb, f0, f1, base, njseg;
     KDesc d[kMaxK];
 };
 
@@ -297,8 +319,8 @@ __global__ void __launch_bounds__(64) epilogue_kernel(const __grid_constant__ Ep
     const int j0 = (js * nb) / a.njseg, j1 = ((js + 1) * nb) / a.njseg, nr = j1 - j0;
     const int nf = a.f1 - a.f0;
     // band rows of S and D/2 (zero-padded to WW entries) and the z factors
-    R2 *cs = reinterpret_cast<R2 *>(esm);                 // nproj: c_p(b)
-    R *cS = reinterpret_cast<R *>(cs + a.nproj);
+    R2 *cs = reinterpret_cast<R2 *>(esm);                 // c_t(b) = c_{p(t)}(b) per term
+    R *cS = reinterpret_cast<R *>(cs + a.nterm);
     R *cD = cS + nr * WW;
     R *zs = cD + nr * WW;
     int *zl = reinterpret_cast<int *>(zs + nf * nr);      // projectors of each factor, then the list offsets
@@ -311,11 +333,11 @@ __global__ void __launch_bounds__(64) epilogue_kernel(const __grid_constant__ Ep
     }
     for (int e = threadIdx.x; e < nf * nr; e += blockDim.x) zs[e] = a.zf[(size_t)(a.f0 + e / nr) * nb + j0 + e % nr];
     if (nf > 0) {
-        for (int e = threadIdx.x; e < a.nproj; e += blockDim.x) {
-            cs[e] = reinterpret_cast<const R2 *>(d.C)[(size_t)b * a.nproj + e];
+        for (int e = threadIdx.x; e < a.nterm; e += blockDim.x) {
+            cs[e] = reinterpret_cast<const R2 *>(d.C)[(size_t)b * a.nkb + a.tproj[e]];
             zl[e] = a.zlist[e];
         }
-        for (int e = threadIdx.x; e <= nf; e += blockDim.x) zl[a.nproj + e] = a.zstart[a.f0 + e];
+        for (int e = threadIdx.x; e <= nf; e += blockDim.x) zl[a.nterm + e] = a.zstart[a.f0 + e];
     }
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -326,7 +348,7 @@ __global__ void __launch_bounds__(64) epilogue_kernel(const __grid_constant__ Ep
             for (int j = j0; j < j1; ++j) Y[(size_t)j * ldg] = czero<R2>();
         return;
     }
-    // KB: r_f = sum_{p: f(p) = f} c_p(b) q_p(G)
+    // KB: r_f = sum_{t: f(t) = f} c_{p(t)}(b) q_t(G)
     R2 r[NZB];
     const R2 *Qg = a.Q + d.qofs + g;
 #pragma unroll
@@ -334,9 +356,9 @@ __global__ void __launch_bounds__(64) epilogue_kernel(const __grid_constant__ Ep
         r[f] = czero<R2>();
         if (f < nf) {
 #pragma unroll 4
-            for (int i = zl[a.nproj + f]; i < zl[a.nproj + f + 1]; ++i) {
-                const int p = zl[i];
-                cfma(r[f], cs[p], Qg[(size_t)p * ldg]);
+            for (int i = zl[a.nterm + f]; i < zl[a.nterm + f + 1]; ++i) {
+                const int t = zl[i];
+                cfma(r[f], cs[t], Qg[(size_t)t * ldg]);
             }
         }
     }
@@ -386,12 +408,28 @@ __global__ void __launch_bounds__(64) epilogue_kernel(const __grid_constant__ Ep
     }
 }
 
-// F_p(b) = sum_j z_p(j) W[(b,j)][p];  C[(b,j)][p] = z_p(j) E_p F_p(b)
+// Tensor-core path, per term t of projector p: W[(b,j)][t] = sum_G X conj(q_t);
+// F_p(b) = sum_{t in p} sum_j z_t(j) W[(b,j)][t];
+// c_p = E_p F_p + E'_p F_partner;  C[(b,j)][t] = z_t(j) c_{p(t)}(b)
 template <typename R> struct CoefArgs {
     const R *zproj, *E;
-    int nb, nbands, nproj;
+    const int *partner, *pstart, *plist;
+    int nb, nbands, nterm, nkb;
     KDesc d[kMaxK];
 };
+
+template <typename R>
+__device__ __forceinline__ typename V2<R>::T coef_overlap(const CoefArgs<R> &a, const KDesc &d, int b, int p) {
+    typedef typename V2<R>::T R2;
+    const R2 *W = reinterpret_cast<const R2 *>(d.W) + (size_t)b * a.nb * a.nterm;
+    R2 F = czero<R2>();
+    for (int i = a.pstart[p]; i < a.pstart[p + 1]; ++i) {
+        const int t = a.plist[i];
+        const R *z = a.zproj + (size_t)t * a.nb;
+        for (int j = 0; j < a.nb; ++j) rfma(F, z[j], W[(size_t)j * a.nterm + t]);
+    }
+    return F;
+}
 
 template <typename R>
 __global__ void coef_kernel(const __grid_constant__ CoefArgs<R> a) {
@@ -399,15 +437,16 @@ __global__ void coef_kernel(const __grid_constant__ CoefArgs<R> a) {
     const int ks = blockIdx.y;
     const KDesc &d = a.d[ks];
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= a.nbands * a.nproj) return;
-    const int b = idx / a.nproj, p = idx % a.nproj;
-    const R2 *W = reinterpret_cast<const R2 *>(d.W) + (size_t)b * a.nb * a.nproj;
-    R2 *C = reinterpret_cast<R2 *>(d.C) + (size_t)b * a.nb * a.nproj;
-    const R *z = a.zproj + (size_t)p * a.nb;
-    R2 F = czero<R2>();
-    for (int j = 0; j < a.nb; ++j) rfma(F, z[j], W[(size_t)j * a.nproj + p]);
-    F = rscale(a.E[p], F);
-    for (int j = 0; j < a.nb; ++j) C[(size_t)j * a.nproj + p] = rscale(z[j], F);
+    if (idx >= a.nbands * a.nkb) return;
+    const int b = idx / a.nkb, p = idx % a.nkb;
+    R2 c = rscale(a.E[p], coef_overlap(a, d, b, p));
+    if (a.partner[p] >= 0) rfma(c, a.E[a.nkb + p], coef_overlap(a, d, b, a.partner[p]));
+    R2 *C = reinterpret_cast<R2 *>(d.C) + (size_t)b * a.nb * a.nterm;
+    for (int i = a.pstart[p]; i < a.pstart[p + 1]; ++i) {
+        const int t = a.plist[i];
+        const R *z = a.zproj + (size_t)t * a.nb;
+        for (int j = 0; j < a.nb; ++j) C[(size_t)j * a.nterm + t] = rscale(z[j], c);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -534,7 +573,11 @@ static int upload_set(mb_handle *h, DevTables &t) {
     if ((rc = upload_complex<R>(h, &t.qproj, qp))) return rc;
     if ((rc = upload<R>(h, &t.zproj, h->zproj))) return rc;
     if ((rc = upload<R>(h, &t.zf, h->zfun))) return rc;
-    if ((rc = upload<R>(h, &t.E, h->Eproj))) return rc;
+    {
+        std::vector<double> e(h->Ekb);
+        e.insert(e.end(), h->Ecoup.begin(), h->Ecoup.end());
+        if ((rc = upload<R>(h, &t.E, e))) return rc;
+    }
     const int nmax = std::max(h->n1, h->n2);
     std::vector<cdouble> tw(nmax / 2);
     for (int i = 0; i < nmax / 2; ++i) tw[i] = std::polar(1.0, 2.0 * 3.14159265358979323846 * i / nmax);
@@ -583,10 +626,14 @@ int upload_tables(mb_handle *h) {
     }
     MB_CUDA(cudaMalloc(&h->d_rows, rows.size() * sizeof(int)));
     MB_CUDA(cudaMemcpy(h->d_rows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
-    if (h->nproj > 0) {
+    if (h->nterm > 0) {
         std::vector<int> zi(h->pgroup);
         zi.insert(zi.end(), h->zstart.begin(), h->zstart.end());
         zi.insert(zi.end(), h->zlist.begin(), h->zlist.end());
+        zi.insert(zi.end(), h->tproj.begin(), h->tproj.end());
+        zi.insert(zi.end(), h->partner.begin(), h->partner.end());
+        zi.insert(zi.end(), h->pstart.begin(), h->pstart.end());
+        zi.insert(zi.end(), h->plist.begin(), h->plist.end());
         MB_CUDA(cudaMalloc(&h->d_zidx, zi.size() * sizeof(int)));
         MB_CUDA(cudaMemcpy(h->d_zidx, zi.data(), zi.size() * sizeof(int), cudaMemcpyHostToDevice));
     }
@@ -735,10 +782,10 @@ static KScratch per_k_layout(const mb_handle *h, int ldg, int nbands, int nchunk
     KScratch k;
     k.part = (size_t)nbands * std::max(0, nchunks - 1) * 2 * (h->order - 1) * ldg * c2;
     if (tensor) {
-        k.w = k.c = (size_t)nbands * h->nb * std::max(1, h->nproj) * c2;
+        k.w = k.c = (size_t)nbands * h->nb * std::max(1, h->nterm) * c2;
     } else {
         k.w = (size_t)nbands * std::max(1, h->nzf) * ldg * c2;
-        k.c = (size_t)nbands * std::max(1, h->nproj) * c2;
+        k.c = (size_t)nbands * std::max(1, h->nterm) * c2;
     }
     return k;
 }
@@ -850,31 +897,44 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     for (int i = 0; i < nsel; ++i) cols += (long long)nbands * h->kp[iks[i]].ldg;
     const int want_threads = h->num_sms * 2048;
     const int nseg = (int)std::max<long long>(1, std::min<long long>(nl_max_seg(h), (want_threads + cols - 1) / cols));
+    // index tables (layout of d_zidx: pgroup | zstart | zlist | tproj | partner | pstart | plist)
     const int *d_pgroup = h->d_zidx;
-    const int *d_zstart = h->d_zidx ? h->d_zidx + h->nproj : nullptr;
-    const int *d_zlist = h->d_zidx ? h->d_zidx + h->nproj + h->nzf + 1 : nullptr;
+    const int *d_zstart = h->d_zidx ? d_pgroup + h->nterm : nullptr;
+    const int *d_zlist = h->d_zidx ? d_zstart + h->nzf + 1 : nullptr;
+    const int *d_tproj = h->d_zidx ? d_zlist + h->nterm : nullptr;
+    const int *d_partner = h->d_zidx ? d_tproj + h->nterm : nullptr;
+    const int *d_pstart = h->d_zidx ? d_partner + h->nkb : nullptr;
+    const int *d_plist = h->d_zidx ? d_pstart + h->nkb + 1 : nullptr;
     // projector overlaps first (they read X only)
-    if (h->nproj > 0 && tensor) {
+    if (h->nterm > 0 && tensor) {
         cudaError_t e = cudaSuccess;
         MB_LAUNCH(h, s, KN_PROJ, e = proj_tc_launch(h, 0, nsel, iks, desc, nbands, s));
         MB_CUDA(e);
         CoefArgs<R> ca;
         ca.zproj = reinterpret_cast<const R *>(t.zproj);
         ca.E = reinterpret_cast<const R *>(t.E);
+        ca.partner = d_partner;
+        ca.pstart = d_pstart;
+        ca.plist = d_plist;
         ca.nb = h->nb;
         ca.nbands = nbands;
-        ca.nproj = h->nproj;
+        ca.nterm = h->nterm;
+        ca.nkb = h->nkb;
         std::copy(desc, desc + nsel, ca.d);
-        MB_LAUNCH(h, s, KN_COEF, coef_kernel<R><<<dim3((nbands * h->nproj + 127) / 128, nsel), 128, 0, s>>>(ca));
-    } else if (h->nproj > 0) {
+        MB_LAUNCH(h, s, KN_COEF, coef_kernel<R><<<dim3((nbands * h->nkb + 127) / 128, nsel), 128, 0, s>>>(ca));
+    } else if (h->nterm > 0) {
         NlArgs<R> na;
         na.zf = reinterpret_cast<const R *>(t.zf);
         na.E = reinterpret_cast<const R *>(t.E);
         na.pgroup = d_pgroup;
+        na.partner = d_partner;
+        na.pstart = d_pstart;
+        na.plist = d_plist;
         na.Q = reinterpret_cast<const R2 *>(t.qproj);
         na.nb = h->nb;
         na.nbands = nbands;
-        na.nproj = h->nproj;
+        na.nterm = h->nterm;
+        na.nkb = h->nkb;
         na.nz = h->nzf;
         na.nseg = nseg;
         std::copy(desc, desc + nsel, na.d);
@@ -893,7 +953,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         else if (h->nzf <= 12) MB_ZX(12);
         else MB_ZX(16);
 #undef MB_ZX
-        MB_LAUNCH(h, s, KN_COEF, nl_coef_kernel<R><<<dim3(nbands, nsel, (h->nproj + 7) / 8), 256, 0, s>>>(na));
+        MB_LAUNCH(h, s, KN_COEF, nl_coef_kernel<R><<<dim3(nbands, nsel, (h->nkb + 7) / 8), 256, 0, s>>>(na));
     }
     // local potential through the planes
     PlaneArgs<R> pa;
@@ -936,18 +996,20 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     ea.zf = reinterpret_cast<const R *>(t.zf);
     ea.zstart = d_zstart;
     ea.zlist = d_zlist;
+    ea.tproj = d_tproj;
     ea.Q = reinterpret_cast<const R2 *>(t.qproj);
     ea.order = h->order;
     ea.nb = h->nb;
     ea.nbands = nbands;
     ea.nchunks = nchunks;
     ea.nint = h->nint;
-    ea.nproj = h->nproj;
+    ea.nterm = h->nterm;
+    ea.nkb = h->nkb;
     ea.njseg = nseg;
     std::copy(desc, desc + nsel, ea.d);
     // kinetic term, boundary sums and the KB term of the first 16 z factors;
     // further passes add the KB term of the rest
-    const int nzf = (h->nproj > 0 && !tensor) ? h->nzf : 0;
+    const int nzf = (h->nterm > 0 && !tensor) ? h->nzf : 0;
     const dim3 ge((maxldg + 63) / 64, nbands * nseg, nsel);
     for (int f0 = 0, pass = 0; pass == 0 || f0 < nzf; f0 += 16, ++pass) {
         ea.f0 = f0;
@@ -955,9 +1017,9 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         ea.base = pass == 0;
         const int nrmax = (h->nb + nseg - 1) / nseg;
         const int HWn = h->order <= 6 ? 5 : 7;
-        const size_t esm = (size_t)h->nproj * sizeof(R2) +
+        const size_t esm = (size_t)h->nterm * sizeof(R2) +
                            ((size_t)2 * nrmax * (2 * HWn + 1) + (size_t)(ea.f1 - ea.f0) * nrmax) * sizeof(R) +
-                           ((size_t)h->nproj + 17) * sizeof(int) + 16;
+                           ((size_t)h->nterm + 17) * sizeof(int) + 16;
         const int nfp = ea.f1 - ea.f0;
 #define MB_EPI(NZ, HWV)                                                                                   \
     do {                                                                                                  \
@@ -975,7 +1037,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         }
 #undef MB_EPI
     }
-    if (h->nproj > 0 && tensor) {
+    if (h->nterm > 0 && tensor) {
         cudaError_t e = cudaSuccess;
         MB_LAUNCH(h, s, KN_BACKPROJ, e = proj_tc_launch(h, 1, nsel, iks, desc, nbands, s));
         MB_CUDA(e);

@@ -23,7 +23,7 @@ struct KPoint {
     std::vector<int> goff;          // natural grid offset i1*N2 + i2 of each G
     std::vector<double> q2;         // |k+G|^2
     std::vector<double> qx, qy;     // k+G cartesian
-    std::vector<cdouble> qproj;     // nproj x ldg in-plane projector factors
+    std::vector<cdouble> qproj;     // nterm x ldg in-plane projector factors
 };
 
 // Device copies of one precision (R = double or float).
@@ -37,10 +37,10 @@ struct DevTables {
     void *Lband = nullptr;   // nb x order: Cholesky L[j][j-d], d = 0..order-1
     void *Lrecip = nullptr;  // the same with 1 / L[j][j] at d = 0 (eigensolver's solves)
     void *q2 = nullptr;      // all k, concatenated with kofs
-    void *qproj = nullptr;   // all k: nproj x ldg each, offset qofs[k]
-    void *zproj = nullptr;   // nproj x nb
+    void *qproj = nullptr;   // all k: nterm x ldg each (in-plane factor of every term), offset qofs[k]
+    void *zproj = nullptr;   // nterm x nb: z factor of every projector term
     void *zf = nullptr;      // nzf x nb: the distinct rows of zproj
-    void *E = nullptr;       // nproj
+    void *E = nullptr;       // nkb diagonal strengths, then nkb partner couplings
     void *Pfac = nullptr;    // preconditioner factors: all k, ldg x nb x order each
 };
 
@@ -57,7 +57,7 @@ struct mb_handle {
     double ecut = 0;
     int order = 0, nquad = 0, nint = 0, nb = 0, nq = 0;
     int n1 = 0, n2 = 0, l1 = 0, l2 = 0;
-    int nproj = 0;
+    int nterm = 0;
     int max_bands = 0;
     int smem_optin = 227 * 1024;   // opt-in shared memory per block
     int num_sms = 152;
@@ -67,13 +67,22 @@ struct mb_handle {
     std::vector<double> Bq;          // nq x order
     std::vector<double> Sb, Db, Lb;  // band storage as in DevTables
     std::vector<double> Vnat;        // nq x N1 x N2 natural order, V(r, z_q) (Ha)
-    std::vector<double> zproj, Eproj;
-    // distinct z factors of the projectors: zfun (nzf x nb), pgroup[p] = f,
-    // and the projectors of factor f in zlist[zstart[f] .. zstart[f+1])
+    // Kleinman-Bylander projectors as sums of separable terms: projector p
+    // (nkb of them) is u_p = sum_{t in terms(p)} zproj[t](j) qproj[t](G); a
+    // 1s or p projector has one term, a 2s projector two.  Strengths: the
+    // diagonal Ekb[p] and one coupling Ecoup[p] to projector partner[p]
+    // (the 1s-2s pair of an atom; -1 for none).
+    int nkb = 0;
+    std::vector<double> zproj, Ekb, Ecoup;
+    std::vector<int> tproj, partner, pstart, plist;   // term -> projector; terms of projector p
+    // distinct z factors of the terms: zfun (nzf x nb), pgroup[t] = f, and
+    // the terms of factor f in zlist[zstart[f] .. zstart[f+1])
     int nzf = 0;
     std::vector<double> zfun;
     std::vector<int> pgroup, zstart, zlist;
-    int *d_zidx = nullptr;           // device copy: pgroup | zstart | zlist
+    // device copy: pgroup (nterm) | zstart (nzf+1) | zlist (nterm) | tproj (nterm)
+    //              | partner (nkb) | pstart (nkb+1) | plist (nterm)
+    int *d_zidx = nullptr;
     std::vector<mb::KPoint> kp;
     std::vector<int> kofs, qofs;     // offsets of per-k arrays (in elements)
     int total_ldg = 0;

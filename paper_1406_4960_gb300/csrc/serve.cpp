@@ -56,7 +56,7 @@ size_t footprint_of(const mb_handle &h, int nbands, int prec) {
     size_t vec_bytes = 0, pf = 0;
     int maxldg = 0;
     for (auto &k : h.kp) {
-        tables += (size_t)k.ldg * (12 + 4) + (size_t)h.nproj * k.ldg * 24;
+        tables += (size_t)k.ldg * (12 + 4) + (size_t)h.nterm * k.ldg * 24;
         pf += (size_t)k.ldg * h.nb * h.order * 12;
         vec_bytes += (size_t)h.nb * k.ldg * 16;
         maxldg = std::max(maxldg, k.ldg);
@@ -76,7 +76,7 @@ size_t footprint_of(const mb_handle &h, int nbands, int prec) {
     size_t scratch = (size_t)h.kp.size() *
                      ((size_t)M * 40 * 2 * (h.order - 1) * maxldg * 16 +
                       2 * (size_t)M * std::max((size_t)16 * std::max(1, h.nzf) * maxldg,
-                                               (size_t)h.nb * std::max(1, h.nproj)) * 16);
+                                               (size_t)h.nb * std::max(1, h.nterm)) * 16);
     return tables + work + scratch + (64u << 20);   // + context-side slack per request
 }
 

@@ -289,58 +289,90 @@ int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int
         }
     }
 
-    // ---- Kleinman-Bylander factors: u_p(G, j) = zproj[p][j] * qproj[p][G]
-    h->nproj = 0;
+    // ---- Kleinman-Bylander projectors (Eqs. (14)-(17)) as separable terms
+    // zproj[t][j] * qproj[t][G].  Per atom: 1s, p_x, p_y, p_z (one term each)
+    // and, with nproj = 5, 2s = C2 (Z_{1,00} Q_{2,00} + Z_{2,00} Q_{1,00}).
+    h->nterm = 0;
+    h->nkb = 0;
     for (int i = 0; i < natoms; ++i) {
-        if (atoms[i].nproj != 0 && atoms[i].nproj != 4) return MB_EINVAL;
-        if (atoms[i].nproj == 4 && !(atoms[i].rc > 0)) return MB_EINVAL;
-        h->nproj += atoms[i].nproj;
+        if (atoms[i].nproj != 0 && atoms[i].nproj != 4 && atoms[i].nproj != 5) return MB_EINVAL;
+        if (atoms[i].nproj > 0 && !(atoms[i].rc > 0)) return MB_EINVAL;
+        h->nkb += atoms[i].nproj;
+        h->nterm += atoms[i].nproj == 5 ? 6 : atoms[i].nproj;
     }
-    const int NP = h->nproj;
+    const int NP = h->nterm;
     h->zproj.assign((size_t)NP * nb, 0.0);
-    h->Eproj.assign(NP, 0.0);
+    h->Ekb.assign(h->nkb, 0.0);
+    h->Ecoup.assign(h->nkb, 0.0);
+    h->partner.assign(h->nkb, -1);
+    h->tproj.assign(NP, 0);
+    h->pstart.assign(h->nkb + 1, 0);
+    h->plist.clear();
     for (int ik = 0; ik < nk; ++ik) {
         h->kp[ik].qproj.assign((size_t)NP * h->kp[ik].ldg, cdouble(0.0));
         h->qofs[ik + 1] = h->qofs[ik] + NP * h->kp[ik].ldg;
     }
-    int p = 0;
+    int tt = 0, pp = 0;
     for (int i = 0; i < natoms; ++i) {
         if (atoms[i].nproj == 0) continue;
         const mb_atom &at = atoms[i];
+        const bool two_s = at.nproj == 5;
         double al = 1.0 / (2.0 * at.rc * at.rc);
         double Cs = std::pow(2.0 * al / kPi, 0.75);
         double Cp = 2.0 * std::sqrt(al) * Cs;
-        // z factors: Z_{1,00} (s, p_x, p_y) and Z_{1,10} (p_z) by the Gauss planes
+        // int (r^2)^2 exp(-2 alpha r^2) d^3r = 4 pi (15/16) sqrt(pi) (2 alpha)^(-7/2)
+        double C2 = 1.0 / std::sqrt(4.0 * kPi * 15.0 / 16.0 * std::sqrt(kPi) * std::pow(2.0 * al, -3.5));
+        // terms of this atom: 0 1s, 1 p_x, 2 p_y, 3 p_z, [4 2s: Z_{1,00} Q_{2,00}, 5 2s: Z_{2,00} Q_{1,00}]
+        const int nt = two_s ? 6 : 4;
+        const int zkind[6] = {0, 0, 0, 1, 0, 2};   // Z_{1,00}, Z_{1,10}, Z_{2,00}
         for (int q = 0; q < nq; ++q) {
             int t = q / P;
             double dz = h->zq[q] - at.pos[2];
             double g = h->wq[q] * std::exp(-al * dz * dz);
+            const double zf[3] = {g, g * dz, g * dz * dz};
             for (int m = 0; m < K; ++m) {
                 int j = t + m - 1;
                 if (j < 0 || j >= nb) continue;
                 double bv = h->Bq[(size_t)q * K + m];
-                for (int c = 0; c < 3; ++c) h->zproj[(size_t)(p + c) * nb + j] += g * bv;
-                h->zproj[(size_t)(p + 3) * nb + j] += g * dz * bv;
+                for (int c = 0; c < nt; ++c) h->zproj[(size_t)(tt + c) * nb + j] += zf[zkind[c]] * bv;
             }
         }
-        for (int c = 0; c < 4; ++c) h->Eproj[p + c] = at.E[c];
+        for (int c = 0; c < 4; ++c) h->Ekb[pp + c] = at.E[c];
+        for (int c = 0; c < nt; ++c) h->tproj[tt + c] = pp + (c < 4 ? c : 4);
+        if (two_s) {
+            h->Ekb[pp + 4] = at.E2s;
+            h->partner[pp] = pp + 4;
+            h->partner[pp + 4] = pp;
+            h->Ecoup[pp] = h->Ecoup[pp + 4] = at.E12;
+        }
         for (int ik = 0; ik < nk; ++ik) {
             KPoint &kp = h->kp[ik];
             for (int g = 0; g < kp.ng; ++g) {
                 double qx = kp.qx[g], qy = kp.qy[g];
                 double Qs = (kPi / al) * std::exp(-kp.q2[g] / (4 * al));
+                double Q2 = (1.0 / al - kp.q2[g] / (4 * al * al)) * Qs;   // Q_{2,00}
                 cdouble ph = std::polar(1.0 / std::sqrt(h->Ac), -(qx * at.pos[0] + qy * at.pos[1]));
                 // conj of C*Q: Q_x = i q_x/(2 alpha) Q_s  ->  conj = -i q_x/(2 alpha) Q_s
-                kp.qproj[(size_t)(p + 0) * kp.ldg + g] = ph * (Cs * Qs);
-                kp.qproj[(size_t)(p + 1) * kp.ldg + g] = ph * cdouble(0.0, -Cp * qx / (2 * al) * Qs);
-                kp.qproj[(size_t)(p + 2) * kp.ldg + g] = ph * cdouble(0.0, -Cp * qy / (2 * al) * Qs);
-                kp.qproj[(size_t)(p + 3) * kp.ldg + g] = ph * (Cp * Qs);
+                kp.qproj[(size_t)(tt + 0) * kp.ldg + g] = ph * (Cs * Qs);
+                kp.qproj[(size_t)(tt + 1) * kp.ldg + g] = ph * cdouble(0.0, -Cp * qx / (2 * al) * Qs);
+                kp.qproj[(size_t)(tt + 2) * kp.ldg + g] = ph * cdouble(0.0, -Cp * qy / (2 * al) * Qs);
+                kp.qproj[(size_t)(tt + 3) * kp.ldg + g] = ph * (Cp * Qs);
+                if (two_s) {
+                    kp.qproj[(size_t)(tt + 4) * kp.ldg + g] = ph * (C2 * Q2);
+                    kp.qproj[(size_t)(tt + 5) * kp.ldg + g] = ph * (C2 * Qs);
+                }
             }
         }
-        p += 4;
+        tt += nt;
+        pp += at.nproj;
     }
-    // group projectors by identical z factor (s, p_x, p_y of an atom share one;
-    // atoms at one height with one radius share theirs)
+    for (int p = 0; p < h->nkb; ++p) {
+        for (int t = 0; t < NP; ++t)
+            if (h->tproj[t] == p) h->plist.push_back(t);
+        h->pstart[p + 1] = (int)h->plist.size();
+    }
+    // group terms by identical z factor (s, p_x, p_y and the first 2s term of
+    // an atom share one; atoms at one height with one radius share theirs)
     h->nzf = 0;
     h->zfun.clear();
     h->pgroup.assign(NP, -1);

@@ -52,12 +52,12 @@ size_t smem_bytes(int ntile) { return (size_t)(128 + ntile) * 64 * 2 + 1024; }
 // Complex products become real ones on interleaved (re, im) rows.
 //  projection       W[m][p] = sum_G X[m][G] conj(q_p(G)):  A = X rows (K = 2 ng),
 //                   Bt0[2p + c][2G + c'] = real 2x2 block of conj(q_p(G))
-//  back-projection  Y[m][G] += sum_p C[m][p] q_p(G):       A = C rows (K = 2 nproj),
+//  back-projection  Y[m][G] += sum_p C[m][p] q_p(G):       A = C rows (K = 2 nterm),
 //                   Bt1[2G + c][2p + c'] = real 2x2 block of q_p(G)
 // with m = (band, j).  Both B matrices are BF16 tables built once per k-point.
 struct ProjArgs {
     const __nv_bfloat16 *B;   // all k: per k at bofs[k]
-    int mode, nb, nbands, nproj;
+    int mode, nb, nbands, nterm;
     int *err;
     KDesc d[kMaxK];
     int bofs[kMaxK];          // element offset of this k-point's B table
@@ -69,10 +69,10 @@ __global__ void __launch_bounds__(128) proj_tc_kernel(const __grid_constant__ Pr
     const KDesc &d = a.d[ks];
     const int M = a.nbands * a.nb;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * ntile;
-    const int N = a.mode == 0 ? 2 * a.nproj : 2 * d.ng;
+    const int N = a.mode == 0 ? 2 * a.nterm : 2 * d.ng;
     if (n0 >= N) return;
-    const int K = a.mode == 0 ? 2 * d.ng : 2 * a.nproj;
-    const int lda = a.mode == 0 ? d.ldg : a.nproj;          // complex elements per A row
+    const int K = a.mode == 0 ? 2 * d.ng : 2 * a.nterm;
+    const int lda = a.mode == 0 ? d.ldg : a.nterm;          // complex elements per A row
     const float2 *Ar = reinterpret_cast<const float2 *>(a.mode == 0 ? d.X : d.C);
     const __nv_bfloat16 *B = a.B + a.bofs[ks];
     const int ldb = a.bld[ks];
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(128) proj_tc_kernel(const __grid_constant__ Pr
         return *reinterpret_cast<const __nv_bfloat162 *>(B + (size_t)r * ldb + k);
     };
     float *out = reinterpret_cast<float *>(a.mode == 0 ? d.W : d.Y);
-    const int ldo = a.mode == 0 ? 2 * a.nproj : 2 * d.ldg;
+    const int ldo = a.mode == 0 ? 2 * a.nterm : 2 * d.ldg;
     auto st = [&](int r, int c, float x) {
         if (a.mode == 0) out[(size_t)r * ldo + c] = x;
         else out[(size_t)r * ldo + c] += x;
@@ -100,8 +100,8 @@ namespace mb {
 
 // host: the BF16 B tables of every k-point (uploaded once per handle)
 int upload_proj_tables(mb_handle *h) {
-    if (h->nproj == 0) return MB_OK;
-    const int NP = h->nproj;
+    if (h->nterm == 0) return MB_OK;
+    const int NP = h->nterm;
     std::vector<__nv_bfloat16> all;
     h->pb0_ofs.assign(h->kp.size(), 0);
     h->pb1_ofs.assign(h->kp.size(), 0);
@@ -163,14 +163,14 @@ cudaError_t proj_tc_launch(mb_handle *h, int mode, int nsel, const int *iks, con
     a.mode = mode;
     a.nb = h->nb;
     a.nbands = nbands;
-    a.nproj = h->nproj;
+    a.nterm = h->nterm;
     a.err = reinterpret_cast<int *>(h->d_tcerr);
     int maxN = 0;
     for (int i = 0; i < nsel; ++i) {
         a.d[i] = desc[i];
         a.bofs[i] = mode == 0 ? h->pb0_ofs[iks[i]] : h->pb1_ofs[iks[i]];
         a.bld[i] = mode == 0 ? h->pb0_ld[iks[i]] : h->pb1_ld[iks[i]];
-        maxN = std::max(maxN, mode == 0 ? 2 * h->nproj : 2 * h->kp[iks[i]].ng);
+        maxN = std::max(maxN, mode == 0 ? 2 * h->nterm : 2 * h->kp[iks[i]].ng);
     }
     const int ntile = maxN <= 256 ? (maxN + 15) / 16 * 16 : 256;
     const dim3 grid((nbands * h->nb + 127) / 128, (maxN + ntile - 1) / ntile, nsel);

@@ -38,7 +38,8 @@ class _Cell(ctypes.Structure):
 
 class _Atom(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_double * 3), ("A", ctypes.c_double), ("w", ctypes.c_double),
-                ("nproj", ctypes.c_int), ("E", ctypes.c_double * 4), ("rc", ctypes.c_double)]
+                ("nproj", ctypes.c_int), ("E", ctypes.c_double * 4), ("rc", ctypes.c_double),
+                ("E2s", ctypes.c_double), ("E12", ctypes.c_double)]
 
 
 class _Opts(ctypes.Structure):
@@ -142,6 +143,8 @@ def _atoms_array(atoms):
         arr[i].nproj = at.nproj
         arr[i].E = (ctypes.c_double * 4)(*at.E)
         arr[i].rc = at.rc
+        arr[i].E2s = getattr(at, "e2s", 0.0)
+        arr[i].E12 = getattr(at, "e12", 0.0)
     return arr
 
 
@@ -211,14 +214,7 @@ class Handle:
         kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 2))
         br = np.ascontiguousarray(np.asarray(breaks, dtype=np.float64))
         cell = _Cell((ctypes.c_double * 2)(*a1), (ctypes.c_double * 2)(*a2))
-        arr = (_Atom * max(1, len(atoms)))()
-        for i, at in enumerate(atoms):
-            arr[i].pos = (ctypes.c_double * 3)(*at.pos)
-            arr[i].A = at.A
-            arr[i].w = at.w
-            arr[i].nproj = at.nproj
-            arr[i].E = (ctypes.c_double * 4)(*at.E)
-            arr[i].rc = at.rc
+        arr = _atoms_array(atoms)
         opts = _Opts(int(grid[0]), int(grid[1]), int(nquad), int(device), int(max_bands),
                      float(precond_shift))
         h = ctypes.c_void_p()

@@ -51,11 +51,19 @@ def _small_kbatch():
     return W.scaled(w, ecut=12.0, n_int=15, nbands=7, name="kbatch-small")
 
 
+def _small_slab_2s():
+    # second s channel (nproj = 5) with a 1s-2s coupling on every atom
+    w = _small_slab()
+    atoms = [dataclasses.replace(a, nproj=5, e2s=-0.35, e12=0.23) for a in w.atoms]
+    return dataclasses.replace(w, atoms=atoms, name="slab2s-small")
+
+
 CASES = {
     "tiny": lambda: W.tiny(),
     "slab-small": _small_slab,
     "graphene-small": _small_graphene,
     "kbatch-small": _small_kbatch,
+    "slab2s-small": _small_slab_2s,
 }
 
 
@@ -237,7 +245,7 @@ def test_invalid_arguments_are_rejected(mbmod):
     h.close()
 
 
-@pytest.mark.parametrize("case", ["slab-small", "graphene-small"])
+@pytest.mark.parametrize("case", ["slab-small", "graphene-small", "slab2s-small"])
 def test_apply_bf16_projector_contraction_on_tensor_cores(mbmod, case):
     """MB_BF16 runs both projector contractions on the tensor cores (tcgen05,
     BF16 operands, FP32 accumulation).  Its projector part, isolated as
@@ -245,7 +253,8 @@ def test_apply_bf16_projector_contraction_on_tensor_cores(mbmod, case):
     rounded to 8 significant bits (relative 2^-9 each), two contractions ->
     about 4 * 2^-9 = 8e-3 of the largest projector term; 2e-2 is asserted."""
     w = CASES[case]()
-    w0 = dataclasses.replace(w, atoms=[dataclasses.replace(a, E=(0.0, 0.0, 0.0, 0.0)) for a in w.atoms])
+    w0 = dataclasses.replace(w, atoms=[dataclasses.replace(a, E=(0.0, 0.0, 0.0, 0.0), e2s=0.0, e12=0.0)
+                                       for a in w.atoms])
     h = mbmod.Handle.from_workload(w)
     h0 = mbmod.Handle.from_workload(w0)
     for ik in range(w.nk):

@@ -110,6 +110,19 @@ def test_eigsolve_kbatch_small_all_k(mbmod, prec):
     h.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_eigsolve_second_s_channel(mbmod, prec):
+    """Atoms with the second s projector and a 1s-2s coupling (nproj = 5)."""
+    w = _small_slab()
+    w = dataclasses.replace(w, atoms=[dataclasses.replace(a, nproj=5, e2s=-0.35, e12=0.23) for a in w.atoms])
+    h = mbmod.Handle.from_workload(w)
+    ev, info = h.eigsolve(w.nbands, 1e-7, prec)
+    for ik in range(w.nk):
+        m, ref = _dense_ref(w, ik, w.nbands)
+        assert np.abs(ev[ik] - ref).max() < EV_TOL, (ik, np.abs(ev[ik] - ref).max())
+    h.close()
+
+
 def test_eigsolve_ragged_blocks_and_depth(mbmod):
     """Band count not a multiple of the block size, deeper Krylov spaces."""
     w = W.tiny()
