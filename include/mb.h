@@ -176,6 +176,8 @@ typedef struct {
     int applies;          /* vectors multiplied by H */
     double max_residual;  /* max_i ||H x_i - eps_i S x_i||_{S^-1} at exit */
     double seconds;       /* wall time of the call */
+    int finish_cycles;    /* of `cycles`, those run with FP64 root applies (all
+                             of them for MB_FP64; the finish phase otherwise) */
 } mb_solve_info;
 
 typedef struct {

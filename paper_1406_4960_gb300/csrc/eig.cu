@@ -198,18 +198,32 @@ __global__ void seed_kernel(const double *dots, int M, int mconv, int nk, int nc
 // parallel (round-robin) ordering: m'/2 disjoint rotations per round.
 // VS: the eigenvector matrix lives in shared memory beside A (m <= 84);
 // otherwise it overwrites the input matrix G in global memory (m <= JMAX).
-template <bool VS>
+// T = float runs the rotations in FP32 (the mixed solver's bulk cycles;
+// eigenvectors good to ~1e-6, refined by the FP64 finish cycles).
+template <bool VS, typename T>
 __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const int *dead, int dead_stride,
                                                      int dead_ofs, double *evals, double2 *evecs,
                                                      int max_sweeps, double rel_tol) {
+    typedef typename std::conditional<std::is_same<T, float>::value, float2, double2>::type T2;
+    const T skip_rel = std::is_same<T, float>::value ? T(1e-7) : T(1e-15);
     extern __shared__ __align__(16) unsigned char sm[];
     const int prob = blockIdx.x;
-    double2 *A = reinterpret_cast<double2 *>(sm);
-    double2 *V = VS ? A + m * m : G + (size_t)prob * LD * LD;
+    T2 *A = reinterpret_cast<T2 *>(sm);
+    T2 *Vs = A + m * m;                                                  // eigenvectors in shared memory (VS)
+    double2 *Vg = G + (size_t)prob * LD * LD;                            // or in place of G
     const int ldv = VS ? m : LD;
-    double *rc = reinterpret_cast<double *>(A + (VS ? 2 : 1) * m * m);   // per pair: c, s, t*|apq|, app, aqq
-    double2 *re = reinterpret_cast<double2 *>(rc + 5 * JPAIRS);         // per pair: phase e
+    T *rc = reinterpret_cast<T *>(A + (VS ? 2 : 1) * m * m);             // per pair: c, s, t*|apq|, app, aqq
+    T2 *re = reinterpret_cast<T2 *>(rc + 5 * JPAIRS);                   // per pair: phase e
     int *pp = reinterpret_cast<int *>(re + JPAIRS);                      // per pair: p, q
+    auto vget = [&](int r, int c) -> T2 {
+        if (VS) return Vs[r * ldv + c];
+        const double2 v = Vg[r * ldv + c];
+        return mk((T)v.x, (T)v.y);
+    };
+    auto vset = [&](int r, int c, T2 v) {
+        if (VS) Vs[r * ldv + c] = v;
+        else Vg[r * ldv + c] = make_double2((double)v.x, (double)v.y);
+    };
     __shared__ double red[32];
     __shared__ int stop;
     const double2 *g = G + (size_t)prob * LD * LD;
@@ -225,19 +239,19 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
         bool di = dead && dead[prob * dead_stride + i] == 0 && i >= dead_ofs;
         bool dj = dead && dead[prob * dead_stride + j] == 0 && j >= dead_ofs;
         if (di || dj) v = make_double2((i == j) ? 1e30 : 0.0, 0.0);
-        A[e] = v;
+        A[e] = mk((T)v.x, (T)v.y);
     }
     __syncthreads();   // G is read completely before V (possibly G itself) is initialised
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         int i = e / m, j = e % m;
-        V[i * ldv + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+        vset(i, j, mk(T(i == j ? 1 : 0), T(0)));
     }
     __syncthreads();
     // Frobenius norm of the live part for the stopping rule
     double f = 0.0;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        double2 a = A[e];
-        if (fabs(a.x) < 1e29) f += a.x * a.x + a.y * a.y;
+        T2 a = A[e];
+        if (fabs((double)a.x) < 1e29) f += (double)a.x * a.x + (double)a.y * a.y;
     }
     for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
@@ -259,20 +273,20 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
                 int b = ((r + mp - 1 - pi - 1) % (mp - 1)) + 1;
                 if (pi == 0) b = ((r + mp - 2) % (mp - 1)) + 1;
                 int p = min(a, b), q = max(a, b);
-                double c = 1.0, s = 0.0, tm = 0.0;
-                double2 ep = make_double2(1.0, 0.0);
+                T c = 1, s = 0, tm = 0;
+                T2 ep = mk(T(1), T(0));
                 if (q < m) {
-                    double2 apq = A[p * m + q];
-                    double mag = hypot(apq.x, apq.y);
-                    double app = A[p * m + p].x, aqq = A[q * m + q].x;
+                    T2 apq = A[p * m + q];
+                    T mag = hypot(apq.x, apq.y);
+                    T app = A[p * m + p].x, aqq = A[q * m + q].x;
                     rc[5 * pi + 3] = app;
                     rc[5 * pi + 4] = aqq;
                     // rotations below rounding level of the diagonal are skipped
-                    if (mag > 1e-15 * sqrt(fabs(app * aqq)) && mag > 1e-300) {
-                        ep = make_double2(apq.x / mag, apq.y / mag);
-                        double th = (aqq - app) / (2.0 * mag);
-                        double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
+                    if (mag > skip_rel * sqrt(fabs(app * aqq)) && mag > T(1e-30)) {
+                        ep = mk(apq.x / mag, apq.y / mag);
+                        T th = (aqq - app) / (T(2) * mag);
+                        T t = (th >= 0 ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+                        c = T(1) / sqrt(t * t + T(1));
                         s = t * c;
                         tm = t * mag;
                     }
@@ -291,35 +305,35 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
             for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
                 int pi = e / m, row = e % m;
                 int p = pp[2 * pi], q = pp[2 * pi + 1];
-                if (p < 0 || rc[5 * pi + 1] == 0.0) continue;
-                double c = rc[5 * pi], s = rc[5 * pi + 1];
-                double2 ec = make_double2(re[pi].x, -re[pi].y);
-                double2 xp = A[row * m + p], xq = cmul(ec, A[row * m + q]);
+                if (p < 0 || rc[5 * pi + 1] == T(0)) continue;
+                T c = rc[5 * pi], s = rc[5 * pi + 1];
+                T2 ec = mk(re[pi].x, -re[pi].y);
+                T2 xp = A[row * m + p], xq = cmul(ec, A[row * m + q]);
                 A[row * m + p] = rscale(c, xp) - rscale(s, xq);
                 A[row * m + q] = rscale(s, xp) + rscale(c, xq);
-                double2 vp = V[row * ldv + p], vq = cmul(ec, V[row * ldv + q]);
-                V[row * ldv + p] = rscale(c, vp) - rscale(s, vq);
-                V[row * ldv + q] = rscale(s, vp) + rscale(c, vq);
+                T2 vp = vget(row, p), vq = cmul(ec, vget(row, q));
+                vset(row, p, rscale(c, vp) - rscale(s, vq));
+                vset(row, q, rscale(s, vp) + rscale(c, vq));
             }
             __syncthreads();
             // rows: A <- J^H A
             for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
                 int pi = e / m, col = e % m;
                 int p = pp[2 * pi], q = pp[2 * pi + 1];
-                if (p < 0 || rc[5 * pi + 1] == 0.0) continue;
-                double c = rc[5 * pi], s = rc[5 * pi + 1];
-                double2 yp = A[p * m + col], yq = cmul(re[pi], A[q * m + col]);
+                if (p < 0 || rc[5 * pi + 1] == T(0)) continue;
+                T c = rc[5 * pi], s = rc[5 * pi + 1];
+                T2 yp = A[p * m + col], yq = cmul(re[pi], A[q * m + col]);
                 A[p * m + col] = rscale(c, yp) - rscale(s, yq);
                 A[q * m + col] = rscale(s, yp) + rscale(c, yq);
             }
             __syncthreads();
             for (int pi = threadIdx.x; pi < npair; pi += blockDim.x) {
                 int p = pp[2 * pi], q = pp[2 * pi + 1];
-                if (p < 0 || rc[5 * pi + 1] == 0.0) continue;
-                A[p * m + q] = make_double2(0.0, 0.0);
-                A[q * m + p] = make_double2(0.0, 0.0);
-                A[p * m + p] = make_double2(rc[5 * pi + 3] - rc[5 * pi + 2], 0.0);
-                A[q * m + q] = make_double2(rc[5 * pi + 4] + rc[5 * pi + 2], 0.0);
+                if (p < 0 || rc[5 * pi + 1] == T(0)) continue;
+                A[p * m + q] = czero<T2>();
+                A[q * m + p] = czero<T2>();
+                A[p * m + p] = mk(rc[5 * pi + 3] - rc[5 * pi + 2], T(0));
+                A[q * m + q] = mk(rc[5 * pi + 4] + rc[5 * pi + 2], T(0));
             }
             __syncthreads();
         }
@@ -327,7 +341,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
         double o = 0.0;
         for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
             int i = e / m, j = e % m;
-            if (i != j) o += A[e].x * A[e].x + A[e].y * A[e].y;
+            if (i != j) o += (double)A[e].x * A[e].x + (double)A[e].y * A[e].y;
         }
         for (int off = 16; off > 0; off >>= 1) o += __shfl_down_sync(0xffffffffu, o, off);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = o;
@@ -354,9 +368,21 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
     __syncthreads();
     for (int c = threadIdx.x; c < m; c += blockDim.x) evals[(size_t)prob * LD + c] = A[perm[c] * m + perm[c]].x;
     double2 *out = evecs + (size_t)prob * LD * LD;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int r = e / m, c = e % m;
-        out[r * LD + c] = V[r * ldv + perm[c]];
+    if (!VS && out == Vg) {
+        // eigenvectors already in place of G: permute their columns through
+        // the (now free) shared matrix A, one row at a time
+        for (int r = 0; r < m; ++r) {
+            for (int c = threadIdx.x; c < m; c += blockDim.x) A[c] = vget(r, perm[c]);
+            __syncthreads();
+            for (int c = threadIdx.x; c < m; c += blockDim.x) out[r * LD + c] = make_double2(A[c].x, A[c].y);
+            __syncthreads();
+        }
+    } else {
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            int r = e / m, c = e % m;
+            const T2 v = vget(r, perm[c]);
+            out[r * LD + c] = make_double2(v.x, v.y);
+        }
     }
 }
 
@@ -1077,25 +1103,32 @@ struct Solver {
         copy(nch, vs(kV + kd - 1, 1, cs), vs(oQ, 1, 1), 0);
         applyH_chain(nch, kd - 1, kH, cs);
     }
-    void jacobi(int nch, int m, bool masked, int ofs) {
-        const size_t extra = 5 * JPAIRS * sizeof(double) + JPAIRS * sizeof(double2) + 2 * JPAIRS * sizeof(int);
+    void jacobi(int nch, int m, bool masked, int ofs, bool f32 = false) {
+        if (f32) jacobi_t<float>(nch, m, masked, ofs, 1e-6);
+        else jacobi_t<double>(nch, m, masked, ofs, 1e-13);
+    }
+    template <typename T> void jacobi_t(int nch, int m, bool masked, int ofs, double tol) {
+        const size_t c2 = 2 * sizeof(T);
+        const size_t extra = 5 * JPAIRS * sizeof(T) + JPAIRS * c2 + 2 * JPAIRS * sizeof(int);
         const size_t stat = 32 * sizeof(double) + sizeof(int) + LD * sizeof(int) + 256;
-        size_t smem2 = (size_t)2 * m * m * sizeof(double2) + extra;
-        size_t smem1 = (size_t)m * m * sizeof(double2) + extra;
+        size_t smem2 = (size_t)2 * m * m * c2 + extra;
+        size_t smem1 = (size_t)m * m * c2 + extra;
         const bool vs = smem2 + stat <= (size_t)h->smem_optin;
         int np = nk * nch;
         if (masked)
             MB_LAUNCH_E(KN_SMALL, alive_mask_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_alive, kd, ofs, M, b, nch, m, np, d_mask));
         if (vs) {
-            cuda(smem_limit_once((const void *)jacobi_kernel<true>, h->device, h->smem_optin));
-            MB_LAUNCH_E(KN_JACOBI, jacobi_kernel<true><<<np, 256, smem2, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
-                                                                              d_evals, d_Y, 30, 1e-13));
+            cuda(smem_limit_once((const void *)jacobi_kernel<true, T>, h->device, h->smem_optin));
+            MB_LAUNCH_E(KN_JACOBI, (jacobi_kernel<true, T><<<np, 256, smem2, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
+                                                                                  d_evals, d_Y, 30, tol)));
         } else {
-            cuda(smem_limit_once((const void *)jacobi_kernel<false>, h->device, h->smem_optin));
-            MB_LAUNCH_E(KN_JACOBI, jacobi_kernel<false><<<np, 256, smem1, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
-                                                                               d_evals, d_Y, 30, 1e-13));
+            cuda(smem_limit_once((const void *)jacobi_kernel<false, T>, h->device, h->smem_optin));
+            MB_LAUNCH_E(KN_JACOBI, (jacobi_kernel<false, T><<<np, 256, smem1, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
+                                                                                   d_evals, d_Y, 30, tol)));
         }
     }
+    // bulk cycles of the mixed solver (before the FP64 finish phase)
+    bool lowp() const { return gs32 && !fp64_roots; }
     // Rayleigh-Ritz of the pencil (V^H H V, V^H S V) of nch problems of size m
     // per k-point: U = L^{-H} from V^H S V = L L^H (dead Krylov slots made
     // identity), Ritz pairs of U^H (V^H H V) U; returns the Ritz vectors'
@@ -1115,17 +1148,21 @@ struct Solver {
         MB_LAUNCH_E(KN_SMALL, cholinv_kernel<<<np, 128, (size_t)m * m * sizeof(double2), s>>>(d_Sg, m, d_Ub, d_statb));
         small_gemm(d_G, d_Ub, d_Tb, m, 0, np);    // (V^H H V) U
         small_gemm(d_Ub, d_Tb, d_G, m, 1, np);    // U^H (V^H H V) U
-        jacobi(nch, m, true, ofs);
+        jacobi(nch, m, true, ofs, lowp());
         small_gemm(d_Ub, d_Y, d_Tb, m, 0, np);    // U Y
         return d_Tb;
     }
     // X, HX <- [V|..](m) Y[:, :M] and SX = S X (S is banded: recomputing it is
     // cheaper than rotating it)
-    void rotate_set(const double2 *Y, int m) {
+    // fresh_hx: HX from a new apply in the solve's precision instead of the
+    // rotation of [HX|HK] (cheaper than the FP64 rotation when the applies are
+    // FP32, and no less accurate than HK from FP32 applies)
+    void rotate_set(const double2 *Y, int m, bool fresh_hx = false) {
         combine(1, vs(oV, m), vs(oT, M), Y, 1.0, 0.0);
-        combine(1, vs(oHV, m), vs(oT + M, M), Y, 1.0, 0.0);
+        if (!fresh_hx) combine(1, vs(oHV, m), vs(oT + M, M), Y, 1.0, 0.0);
         copy(1, vs(oT, M), vs(oV, M), 0);
-        copy(1, vs(oT + M, M), vs(oHV, M), 0);
+        if (fresh_hx) applyH(oV, oHV, M, prec);
+        else copy(1, vs(oT + M, M), vs(oHV, M), 0);
         bandS(oV, oSV, M);
     }
     // Rayleigh-Ritz on [X | K_A] (withK) or on X.  With K_A, X holds the Ritz
@@ -1139,7 +1176,7 @@ struct Solver {
             MB_LAUNCH_E(KN_SMALL, assemble_rr_kernel<<<dim3((m * m + 127) / 128, nk), 128, 0, s>>>(
                                       d_G2, gs32 ? d_T : nullptr, d_eps, M, m, d_G, gs32 ? d_Sg : nullptr));
             if (gs32) {
-                rotate_set(pencil_solve(1, m, M), m);
+                rotate_set(pencil_solve(1, m, M), m, lowp());
             } else {
                 jacobi(1, m, true, M);
                 rotate_set(d_Y, m);
@@ -1161,9 +1198,9 @@ struct Solver {
         gram(1, vs(oV, M), vs(oHV, M), d_G2, false, true);
         small_gemm(d_G2, d_U, d_T, M, 0);     // (X^H H X) U
         small_gemm(d_U, d_T, d_G, M, 1);      // U^H (X^H H X) U
-        jacobi(1, M, false, M);
+        jacobi(1, M, false, M, lowp());
         small_gemm(d_U, d_Y, d_T, M, 0);      // U Y
-        rotate_set(d_T, M);
+        rotate_set(d_T, M, lowp());
         MB_LAUNCH_E(KN_SMALL, take_evals_kernel<<<(M * nk + 127) / 128, 128, 0, s>>>(d_evals, M, nk, d_eps));
     }
     void cycle_B() {
@@ -1347,7 +1384,8 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     S.rr_full(false);
     S.residuals_and_seeds(1);
     std::vector<double> res((size_t)S.nk * S.M);
-    double last = 1e300, prev = 1e300, maxres = 1e300;
+    double last = 1e300, prev = 1e300, maxres = 1e300, bulk_best = 1e300;
+    int bulk_idle = 0;
     int cycles = 0;
     bool converged = false;
     // One grand cycle: A (Krylov space of the worst root + Rayleigh-Ritz on
@@ -1379,8 +1417,10 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
             }
         return mx;
     };
+    int finish_cycles = 0;
     for (cycles = 1; cycles <= max_cycles && !S.rc; ++cycles) {
         const int gi = (S.prec == MB_FP64 || S.fp64_roots) ? 1 : 0;
+        finish_cycles += gi;
         if (gi != cur_gi) {
             cur_gi = gi;
             plain_left = 1;
@@ -1409,13 +1449,22 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
         if (S.rc) break;
         maxres = conv_max();
         if (S.prec != MB_FP64 && !S.fp64_roots) {
-            bool stalled = cycles > 3 && maxres > 0.7 * prev;
+            // stalled: two bulk cycles in a row without a 30 % gain on the best
+            // residual so far (the FP32 arithmetic of the bulk cycles has a
+            // floor, and its residuals need not decrease monotonically there)
+            if (maxres < 0.7 * bulk_best) {
+                bulk_best = maxres;
+                bulk_idle = 0;
+            } else {
+                ++bulk_idle;
+            }
+            bool stalled = cycles > 3 && (maxres > 0.7 * prev || bulk_idle >= 2);
             if (maxres < 30.0 * tol || stalled) {
                 // finish phase: the roots get FP64 HX from here on
                 S.fp64_roots = true;
                 S.applyH(S.oV, S.oHV, S.M, MB_FP64);
                 S.bandS(S.oV, S.oSV, S.M);
-                S.rr_full(false);
+                S.orth_rr();
                 S.residuals_and_seeds(1);
                 S.cuda(cudaMemcpyAsync(res.data(), S.d_res, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, s));
                 S.cuda(cudaStreamSynchronize(s));
@@ -1450,6 +1499,7 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
         info->cycles = std::min(cycles, max_cycles);
         info->applies = S.applies;
         info->max_residual = maxres;
+        info->finish_cycles = std::min(finish_cycles, max_cycles);
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return converged ? MB_OK : MB_ENOTCONV;

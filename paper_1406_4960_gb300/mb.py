@@ -50,7 +50,8 @@ class _Opts(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("applies", ctypes.c_int),
-                ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("finish_cycles", ctypes.c_int)]
 
 
 class _Request(ctypes.Structure):
