@@ -289,6 +289,36 @@ __global__ void __launch_bounds__(256) nl_coef_kernel(const __grid_constant__ Nl
     if (lane == 0) reinterpret_cast<R2 *>(d.C)[(size_t)b * a.nkb + p] = c;
 }
 
+// R[b][f][G] = sum_{t: f(t)=f} c_{p(t)}(b) q_t(G), written over Zx (which
+// nl_coef has consumed); one thread per (band, z factor, G).
+template <typename R>
+__global__ void __launch_bounds__(128) nl_back_kernel(const __grid_constant__ NlArgs<R> a, const int *zstart,
+                                                      const int *zlist, const int *tproj) {
+    typedef typename V2<R>::T R2;
+    extern __shared__ __align__(16) unsigned char bsm[];
+    R2 *cl = reinterpret_cast<R2 *>(bsm);                     // c_{p(t)} of the factor's terms
+    int *tl = reinterpret_cast<int *>(cl + a.nterm);          // the terms
+    const int g = blockIdx.x * blockDim.x + threadIdx.x, f = blockIdx.y;
+    const int b = blockIdx.z % a.nbands;
+    const KDesc &d = a.d[blockIdx.z / a.nbands];
+    const int i0 = zstart[f], n = zstart[f + 1] - i0;
+    const R2 *c = reinterpret_cast<const R2 *>(d.C) + (size_t)b * a.nkb;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int t = zlist[i0 + e];
+        tl[e] = t;
+        cl[e] = c[tproj[t]];
+    }
+    __syncthreads();
+    if (g >= d.ldg) return;
+    R2 r = czero<R2>();
+    if (g < d.ng) {
+        const R2 *Qg = a.Q + d.qofs + g;
+#pragma unroll 4
+        for (int e = 0; e < n; ++e) cfma(r, cl[e], Qg[(size_t)tl[e] * d.ldg]);
+    }
+    reinterpret_cast<R2 *>(d.W)[((size_t)b * a.nz + f) * d.ldg + g] = r;
+}
+
 // ---------------------------------------------------------------------------
 // epilogue: Y[j] = local(j) + (D/2 + |k+G|^2/2 S) X (Eq. (9)) + KB term.
 // One thread per (band, G, run of rows j); the local part comes from Y (rows
@@ -298,10 +328,7 @@ __global__ void __launch_bounds__(256) nl_coef_kernel(const __grid_constant__ Nl
 template <typename R> struct EpiArgs {
     const R *Sband, *Dband, *q2;
     const R *zf;                    // nz x nb
-    const int *zstart, *zlist;      // terms of each distinct z factor
-    const int *tproj;               // nterm: projector of each term
-    const typename V2<R>::T *Q;     // q_t(G)
-    int order, nb, nbands, nchunks, nint, nterm, nkb, f0, f1, base, njseg;
+    int order, nb, nbands, nchunks, nint, nz, f0, f1, base, njseg;
     KDesc d[kMaxK];
 };
 
@@ -319,11 +346,9 @@ __global__ void __launch_bounds__(64) epilogue_kernel(const __grid_constant__ Ep
     const int j0 = (js * nb) / a.njseg, j1 = ((js + 1) * nb) / a.njseg, nr = j1 - j0;
     const int nf = a.f1 - a.f0;
     // band rows of S and D/2 (zero-padded to WW entries) and the z factors
-    R2 *cs = reinterpret_cast<R2 *>(esm);                 // c_t(b) = c_{p(t)}(b) per term
-    R *cS = reinterpret_cast<R *>(cs + a.nterm);
+    R *cS = reinterpret_cast<R *>(esm);
     R *cD = cS + nr * WW;
     R *zs = cD + nr * WW;
-    int *zl = reinterpret_cast<int *>(zs + nf * nr);      // projectors of each factor, then the list offsets
     for (int e = threadIdx.x; e < nr * WW; e += blockDim.x) {
         const int rr = e / WW, o = e % WW - HW;            // offset o = jj - j
         const int dd = o + K - 1;
@@ -332,13 +357,6 @@ __global__ void __launch_bounds__(64) epilogue_kernel(const __grid_constant__ Ep
         cD[e] = in ? R(0.5) * a.Dband[(size_t)(j0 + rr) * W + dd] : R(0);
     }
     for (int e = threadIdx.x; e < nf * nr; e += blockDim.x) zs[e] = a.zf[(size_t)(a.f0 + e / nr) * nb + j0 + e % nr];
-    if (nf > 0) {
-        for (int e = threadIdx.x; e < a.nterm; e += blockDim.x) {
-            cs[e] = reinterpret_cast<const R2 *>(d.C)[(size_t)b * a.nkb + a.tproj[e]];
-            zl[e] = a.zlist[e];
-        }
-        for (int e = threadIdx.x; e <= nf; e += blockDim.x) zl[a.nterm + e] = a.zstart[a.f0 + e];
-    }
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ldg) return;
@@ -348,20 +366,11 @@ __global__ void __launch_bounds__(64) epilogue_kernel(const __grid_constant__ Ep
             for (int j = j0; j < j1; ++j) Y[(size_t)j * ldg] = czero<R2>();
         return;
     }
-    // KB: r_f = sum_{t: f(t) = f} c_{p(t)}(b) q_t(G)
+    // KB: r_f = R[b][f][G] = sum_{t: f(t) = f} c_{p(t)}(b) q_t(G) (nl_back)
     R2 r[NZB];
-    const R2 *Qg = a.Q + d.qofs + g;
+    const R2 *Rg = reinterpret_cast<const R2 *>(d.W) + ((size_t)b * a.nz + a.f0) * ldg + g;
 #pragma unroll
-    for (int f = 0; f < NZB; ++f) {
-        r[f] = czero<R2>();
-        if (f < nf) {
-#pragma unroll 4
-            for (int i = zl[a.nterm + f]; i < zl[a.nterm + f + 1]; ++i) {
-                const int t = zl[i];
-                cfma(r[f], cs[t], Qg[(size_t)t * ldg]);
-            }
-        }
-    }
+    for (int f = 0; f < NZB; ++f) r[f] = f < nf ? Rg[(size_t)f * ldg] : czero<R2>();
     const R2 *X = reinterpret_cast<const R2 *>(d.X) + (size_t)b * nb * ldg + g;
     const R2 *part = reinterpret_cast<const R2 *>(d.part) + (size_t)b * (a.nchunks - 1) * 2 * (K - 1) * ldg + g;
     const R hq = R(0.5) * a.q2[d.kofs + g];
@@ -376,21 +385,27 @@ __global__ void __launch_bounds__(64) epilogue_kernel(const __grid_constant__ Ep
     // run boundary bc (between runs bc and bc+1) starts at interval t1 and
     // owns rows [t1 - 1, t1 + K - 3]
     int bc = 0, t1 = a.nchunks > 1 ? a.nint / a.nchunks : 0;
+    // local part of row j: Y (rows inside one plane-kernel run) or the two
+    // boundary partials; loaded one row ahead of its use
+    auto local_row = [&](int j) -> R2 {
+        while (bc < a.nchunks - 1 && t1 + K - 3 < j) {
+            ++bc;
+            t1 = ((bc + 1) * a.nint) / a.nchunks;
+        }
+        if (bc < a.nchunks - 1 && j >= t1 - 1) {
+            const int br = j - (t1 - 1);
+            return part[((size_t)(bc * 2 + 0) * (K - 1) + br) * ldg] + part[((size_t)(bc * 2 + 1) * (K - 1) + br) * ldg];
+        }
+        return Y[(size_t)j * ldg];
+    };
+    R2 vnext = (a.base && j0 < j1) ? local_row(j0) : czero<R2>();
     for (int j = j0; j < j1; ++j) {
         R2 v;
         if (a.base) {
             const int rn = j + HW + 1;
             const R2 nxt = rn < nb ? X[(size_t)rn * ldg] : czero<R2>();
-            while (bc < a.nchunks - 1 && t1 + K - 3 < j) {
-                ++bc;
-                t1 = ((bc + 1) * a.nint) / a.nchunks;
-            }
-            if (bc < a.nchunks - 1 && j >= t1 - 1) {
-                const int br = j - (t1 - 1);
-                v = part[((size_t)(bc * 2 + 0) * (K - 1) + br) * ldg] + part[((size_t)(bc * 2 + 1) * (K - 1) + br) * ldg];
-            } else {
-                v = Y[(size_t)j * ldg];
-            }
+            v = vnext;
+            if (j + 1 < j1) vnext = local_row(j + 1);
             const R *Sr = cS + (j - j0) * WW;
             const R *Dr = cD + (j - j0) * WW;
 #pragma unroll
@@ -954,6 +969,10 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         else MB_ZX(16);
 #undef MB_ZX
         MB_LAUNCH(h, s, KN_COEF, nl_coef_kernel<R><<<dim3(nbands, nsel, (h->nkb + 7) / 8), 256, 0, s>>>(na));
+        const size_t bsm = (size_t)h->nterm * (sizeof(R2) + sizeof(int));
+        MB_CUDA(smem_limit_once((const void *)nl_back_kernel<R>, h->device, h->smem_optin));
+        MB_LAUNCH(h, s, KN_COEF, nl_back_kernel<R><<<dim3((maxldg + 127) / 128, h->nzf, nbands * nsel), 128, bsm, s>>>(
+                                     na, d_zstart, d_zlist, d_tproj));
     }
     // local potential through the planes
     PlaneArgs<R> pa;
@@ -994,17 +1013,13 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     ea.Dband = reinterpret_cast<const R *>(t.Dband);
     ea.q2 = reinterpret_cast<const R *>(t.q2);
     ea.zf = reinterpret_cast<const R *>(t.zf);
-    ea.zstart = d_zstart;
-    ea.zlist = d_zlist;
-    ea.tproj = d_tproj;
-    ea.Q = reinterpret_cast<const R2 *>(t.qproj);
+
     ea.order = h->order;
     ea.nb = h->nb;
     ea.nbands = nbands;
     ea.nchunks = nchunks;
     ea.nint = h->nint;
-    ea.nterm = h->nterm;
-    ea.nkb = h->nkb;
+    ea.nz = h->nzf;
     ea.njseg = nseg;
     std::copy(desc, desc + nsel, ea.d);
     // kinetic term, boundary sums and the KB term of the first 16 z factors;
@@ -1017,9 +1032,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         ea.base = pass == 0;
         const int nrmax = (h->nb + nseg - 1) / nseg;
         const int HWn = h->order <= 6 ? 5 : 7;
-        const size_t esm = (size_t)h->nterm * sizeof(R2) +
-                           ((size_t)2 * nrmax * (2 * HWn + 1) + (size_t)(ea.f1 - ea.f0) * nrmax) * sizeof(R) +
-                           ((size_t)h->nterm + 17) * sizeof(int) + 16;
+        const size_t esm = ((size_t)2 * nrmax * (2 * HWn + 1) + (size_t)(ea.f1 - ea.f0) * nrmax) * sizeof(R);
         const int nfp = ea.f1 - ea.f0;
 #define MB_EPI(NZ, HWV)                                                                                   \
     do {                                                                                                  \

@@ -292,7 +292,10 @@ static cudaError_t launch_one(const PlaneArgs<R> &a, unsigned grid, size_t smem,
     cudaError_t e = smem_limit_once((const void *)plane_reg_kernel<R, N1, N2>, dev, optin);
     if (e != cudaSuccess) return e;
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    plane_reg_kernel<R, N1, N2><<<grid, 256, smem, s>>>(a);
+    // 192 threads when a plane has 16 columns: the fused column pass then
+    // has exactly one line per thread for a 12-plane group
+    const int threads = (sizeof(R) == 4 && N2 == 16 && a.np % 4 == 0) ? 192 : 256;
+    plane_reg_kernel<R, N1, N2><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
