@@ -87,11 +87,18 @@ __device__ __forceinline__ void fft_reg(C (&x)[N]) {
     }
 }
 
-// FP32 grids of at most 512 points run three CTAs per SM, other FP32 grids
-// with both sides <= 32 two (the host plan sizes shared memory for that);
-// the register budget follows.
+// CTA shape: FP32 planes of 16 columns use 192 threads (a 12-plane group is
+// then one fused column line per thread), everything else 256.  FP32 grids of
+// at most 512 points run three CTAs per SM, other FP32 grids with both sides
+// <= 32 two (the host plan sizes shared memory for that); the register budget
+// follows.
+template <typename R, int N1, int N2> struct PlaneShape {
+    static constexpr int threads = (sizeof(R) == 4 && N2 == 16) ? 192 : 256;
+    static constexpr int ctas = (sizeof(R) == 4 && N1 * N2 <= 512) ? 3 : (N1 <= 32 && N2 <= 32 && sizeof(R) == 4) ? 2 : 1;
+};
+
 template <typename R, int N1, int N2>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4 && N1 * N2 <= 512) ? 3 : (N1 <= 32 && N2 <= 32 && sizeof(R) == 4) ? 2 : 1)
+__global__ void __launch_bounds__(PlaneShape<R, N1, N2>::threads, PlaneShape<R, N1, N2>::ctas)
     plane_reg_kernel(const __grid_constant__ PlaneArgs<R> a) {
     typedef typename V2<R>::T C;
     constexpr int LDP = N2 + 1;
@@ -292,10 +299,7 @@ static cudaError_t launch_one(const PlaneArgs<R> &a, unsigned grid, size_t smem,
     cudaError_t e = smem_limit_once((const void *)plane_reg_kernel<R, N1, N2>, dev, optin);
     if (e != cudaSuccess) return e;
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    // 192 threads when a plane has 16 columns: the fused column pass then
-    // has exactly one line per thread for a 12-plane group
-    const int threads = (sizeof(R) == 4 && N2 == 16 && a.np % 4 == 0) ? 192 : 256;
-    plane_reg_kernel<R, N1, N2><<<grid, threads, smem, s>>>(a);
+    plane_reg_kernel<R, N1, N2><<<grid, PlaneShape<R, N1, N2>::threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
