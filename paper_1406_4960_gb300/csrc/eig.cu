@@ -545,34 +545,63 @@ __global__ void eig_banded_solve_kernel(const EigK *ks, const void *Lbv, int per
     auto L = [&](int j, int dd) -> T {
         return per_g ? pf[((size_t)j * K + dd) * ldg + g] : __ldg(&Lb[(size_t)j * K + dd]);
     };
+    // rows are handled in tiles of PD: every load of a tile (right-hand
+    // sides and factors, none of which depends on the recurrence) is issued
+    // before the tile's recurrence runs
+    constexpr int PD = F32 ? 8 : 4;
     T2 win[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) win[i] = czero<T2>();
-#pragma unroll 2
-    for (int j = 0; j < nb; ++j) {
-        T2 s = x[(size_t)j * ldg + g];
+    for (int j0 = 0; j0 < nb; j0 += PD) {
+        T2 xs[PD];
+        T fs[PD][K];
 #pragma unroll
-        for (int dd = 1; dd < K; ++dd)
-            if (j - dd >= 0) rfma(s, -L(j, dd), win[dd - 1]);
-        const T2 yj = rscale(L(j, 0), s);
-        y[(size_t)j * ldg + g] = yj;
+        for (int u = 0; u < PD; ++u) {
+            const int j = j0 + u;
+            xs[u] = j < nb ? x[(size_t)j * ldg + g] : czero<T2>();
 #pragma unroll
-        for (int i = K - 1; i > 0; --i) win[i] = win[i - 1];
-        win[0] = yj;
+            for (int dd = 0; dd < K; ++dd) fs[u][dd] = (j < nb && j - dd >= 0) ? L(j, dd) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < PD; ++u) {
+            const int j = j0 + u;
+            if (j >= nb) break;
+            T2 s = xs[u];
+#pragma unroll
+            for (int dd = 1; dd < K; ++dd) rfma(s, -fs[u][dd], win[dd - 1]);
+            const T2 yj = rscale(fs[u][0], s);
+            y[(size_t)j * ldg + g] = yj;
+#pragma unroll
+            for (int i = K - 1; i > 0; --i) win[i] = win[i - 1];
+            win[0] = yj;
+        }
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) win[i] = czero<T2>();
-#pragma unroll 2
-    for (int j = nb - 1; j >= 0; --j) {
-        T2 s = y[(size_t)j * ldg + g];
+    for (int j1 = nb - 1; j1 >= 0; j1 -= PD) {
+        T2 xs[PD];
+        T fs[PD][K];
 #pragma unroll
-        for (int dd = 1; dd < K; ++dd)
-            if (j + dd < nb) rfma(s, -L(j + dd, dd), win[dd - 1]);
-        const T2 zj = rscale(L(j, 0), s);
-        y[(size_t)j * ldg + g] = zj;
+        for (int u = 0; u < PD; ++u) {
+            const int j = j1 - u;
+            xs[u] = j >= 0 ? y[(size_t)j * ldg + g] : czero<T2>();
+            fs[u][0] = j >= 0 ? L(j, 0) : T(0);
 #pragma unroll
-        for (int i = K - 1; i > 0; --i) win[i] = win[i - 1];
-        win[0] = zj;
+            for (int dd = 1; dd < K; ++dd) fs[u][dd] = (j >= 0 && j + dd < nb) ? L(j + dd, dd) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < PD; ++u) {
+            const int j = j1 - u;
+            if (j < 0) break;
+            T2 s = xs[u];
+#pragma unroll
+            for (int dd = 1; dd < K; ++dd) rfma(s, -fs[u][dd], win[dd - 1]);
+            const T2 zj = rscale(fs[u][0], s);
+            y[(size_t)j * ldg + g] = zj;
+#pragma unroll
+            for (int i = K - 1; i > 0; --i) win[i] = win[i - 1];
+            win[0] = zj;
+        }
     }
 }
 
@@ -631,6 +660,71 @@ __global__ void __launch_bounds__(256) gram_rows_kernel(const EigK *ks, int nch,
         }
         if (lane == 0) part[((size_t)prob * nsplit + split) * ma * mb + (size_t)i * mb + j0 + jj] = make_double2(x, y);
     }
+}
+
+// A^H B for small ma, mb (<= 48) on the FP32 Gram-Schmidt copies: a CTA
+// takes one chunk of the vector length for the whole ma x mb product,
+// staging KC elements of every A and B vector in shared memory; each thread
+// keeps a 3 x 3 block of outputs in registers.  Partial sums per chunk go to
+// `part` (FP64) and are reduced in a fixed order by gram_reduce_kernel.
+constexpr int GT_KC = 32, GT_MAX = 48;
+__global__ void __launch_bounds__(256) gram_tile32_kernel(const EigK *ks, int nch, VSet A, VSet B, int nsplit,
+                                                          double2 *part) {
+    __shared__ float2 As[GT_KC][GT_MAX + 1];
+    __shared__ float2 Bs[GT_KC][GT_MAX + 1];
+    const int split = blockIdx.x, prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const int ma = A.count(), mb = B.count();
+    const long long n = d.nvec;
+    const long long chunk = (n + nsplit - 1) / nsplit;
+    const long long t0 = split * chunk, t1 = min(n, t0 + chunk);
+    const int ti = threadIdx.x / 16, tj = threadIdx.x % 16;   // rows 3*ti.., columns 3*tj..
+    float2 acc[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (long long tb = t0; tb < t1; tb += GT_KC) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < (ma + mb) * GT_KC; e += blockDim.x) {
+            const int v = e / GT_KC, kk = e % GT_KC;
+            const long long t = tb + kk;
+            float2 val = make_float2(0.f, 0.f);
+            if (v < ma) {
+                if (t < t1) val = d.v32[(long long)A.at(v, ch) * n + t];
+                As[kk][v] = val;
+            } else {
+                if (t < t1) val = d.v32[(long long)B.at(v - ma, ch) * n + t];
+                Bs[kk][v - ma] = val;
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < GT_KC; ++kk) {
+            float2 a[3], b[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) a[i] = As[kk][min(3 * ti + i, GT_MAX)];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) b[j] = Bs[kk][min(3 * tj + j, GT_MAX)];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(a[i].y, b[j].y, acc[i][j].x));
+                    acc[i][j].y = fmaf(a[i].x, b[j].y, fmaf(-a[i].y, b[j].x, acc[i][j].y));
+                }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int r = 3 * ti + i, c = 3 * tj + j;
+            if (r < ma && c < mb)
+                part[((size_t)prob * nsplit + split) * ma * mb + (size_t)r * mb + c] =
+                    make_double2(acc[i][j].x, acc[i][j].y);
+        }
 }
 
 // C_j = beta C_j + alpha sum_i A_i Y[i][j]: one element t per thread, JC
@@ -953,6 +1047,16 @@ struct Solver {
     template <int GJ> void gram_t(int nch, VSet A, VSet B, double2 *G, bool f32, bool lower) {
         const int nprob = nk * nch;
         const int ma = A.count(), mbc = B.count();
+        if (f32 && ma <= GT_MAX && mbc <= GT_MAX && ma * mbc >= 64) {
+            // tile kernel: about two resident CTAs per SM over the whole grid
+            int nsplit = std::max(1, std::min(1024, (2 * h->num_sms + nprob - 1) / nprob));
+            nsplit = std::min<long long>(nsplit, std::max<long long>(1, nmax / (4 * GT_KC)));
+            while ((size_t)nprob * nsplit * ma * mbc > part_cap && nsplit > 1) --nsplit;
+            MB_LAUNCH_E(KN_GRAM32, gram_tile32_kernel<<<dim3(nsplit, nprob), 256, 0, s>>>(d_k, nch, A, B, nsplit, d_part));
+            MB_LAUNCH_E(KN_GRAM32,
+                        gram_reduce_kernel<<<nprob, 256, 0, s>>>(d_part, nsplit, ma, mbc, G, lower ? 1 : 0));
+            return;
+        }
         const int rowgroups = (ma + 7) / 8, colgroups = (mbc + GJ - 1) / GJ;
         const int per_split = nprob * rowgroups * colgroups;
         int nsplit = std::max(1, std::min(512, (8 * h->num_sms + per_split - 1) / per_split));
