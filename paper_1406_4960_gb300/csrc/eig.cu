@@ -98,9 +98,10 @@ __global__ void copy_kernel(const EigK *ks, int nch, VSet S, VSet D, int mode) {
     }
 }
 
-// W_ch = H_src - theta_ch S_src   (per-(k, ch) source indices)
+// W_ch = H_src - theta_ch S_src   (per-(k, ch) source indices); to32: W goes
+// to the FP32 Gram-Schmidt copies (slot dst + ch of v32) instead
 __global__ void krylov_residual_kernel(const EigK *ks, int nch, const int *srcH, const int *srcS,
-                                       const double *theta, int dst) {
+                                       const double *theta, int dst, int to32) {
     const int prob = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
@@ -108,9 +109,13 @@ __global__ void krylov_residual_kernel(const EigK *ks, int nch, const int *srcH,
     const double2 *h = d.base + (long long)srcH[prob] * d.nvec;
     const double2 *s = d.base + (long long)srcS[prob] * d.nvec;
     double2 *w = d.base + (long long)(dst + ch) * d.nvec;
+    float2 *w32 = to32 ? d.v32 + (long long)(dst + ch) * d.nvec : nullptr;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.nvec;
-         t += (long long)gridDim.x * blockDim.x)
-        w[t] = h[t] - rscale(th, s[t]);
+         t += (long long)gridDim.x * blockDim.x) {
+        const double2 r = h[t] - rscale(th, s[t]);
+        if (to32) w32[t] = make_float2((float)r.x, (float)r.y);
+        else w[t] = r;
+    }
 }
 
 // R_i = HX_i - eps_i SX_i into dst
@@ -152,7 +157,7 @@ __global__ void coldot_kernel(const EigK *ks, int nch, VSet A, VSet B, double *o
 // new Krylov vector: K = W / ||W||_S, SK = SW / ||W||_S, HK slot cleared;
 // a norm below the breakdown threshold marks the slot dead (zero vector).
 __global__ void normalize_kernel(const EigK *ks, int nch, int oW, int oSW, int kV, int kS, int cs,
-                                 int slot, const double *nrm2, int *alive, int kd) {
+                                 int slot, const double *nrm2, int *alive, int kd, int k32, int sk32) {
     const int prob = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
@@ -164,10 +169,18 @@ __global__ void normalize_kernel(const EigK *ks, int nch, int oW, int oSW, int k
     const double2 *sw = d.base + (long long)(oSW + ch) * d.nvec;
     double2 *kv = d.base + (long long)(kV + ch * cs + slot) * d.nvec;
     double2 *ksv = d.base + (long long)(kS + ch * cs + slot) * d.nvec;
+    // FP32 copies for later Gram-Schmidt steps (k32 < 0: none)
+    float2 *kv32 = k32 >= 0 ? d.v32 + (long long)(k32 + ch * kd + slot) * d.nvec : nullptr;
+    float2 *ks32 = k32 >= 0 ? d.v32 + (long long)(sk32 + ch * kd + slot) * d.nvec : nullptr;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.nvec;
          t += (long long)gridDim.x * blockDim.x) {
-        kv[t] = rscale(inv, w[t]);
-        ksv[t] = rscale(inv, sw[t]);
+        const double2 a = rscale(inv, w[t]), b = rscale(inv, sw[t]);
+        kv[t] = a;
+        ksv[t] = b;
+        if (kv32) {
+            kv32[t] = make_float2((float)a.x, (float)a.y);
+            ks32[t] = make_float2((float)b.x, (float)b.y);
+        }
     }
 }
 
@@ -1153,9 +1166,30 @@ struct Solver {
         MB_LAUNCH_E(KN_SMALL, seed_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_dots, M, Mconv, nk, nch, b, d_res, d_eps, d_seed,
                                                                         d_theta, d_srcH, d_srcS, oHV, oSV));
     }
-    void applyH_chain(int nch, int slot, int kH, int cs) {
-        applyH(oQ, oHQ, nch, prec);
-        copy(nch, vs(oHQ, 1, 1), vs(kH + slot, 1, cs), 0);
+    // H K[slot] of every chain into HK[slot]; reduced-precision applies go
+    // straight from the chain slots through the FP32 stage
+    void applyH_chain(int nch, int slot, int kV, int kH, int cs) {
+        if (prec == MB_FP64) {
+            copy(nch, vs(kV + slot, 1, cs), vs(oQ, 1, 1), 0);
+            applyH(oQ, oHQ, nch, prec);
+            copy(nch, vs(oHQ, 1, 1), vs(kH + slot, 1, cs), 0);
+            return;
+        }
+        if (rc) return;
+        std::vector<int> iks(nk);
+        std::vector<const void *> xs(nk);
+        std::vector<void *> ys(nk);
+        for (int k = 0; k < nk; ++k) {
+            iks[k] = k;
+            xs[k] = kd_host[k].stage;
+            ys[k] = kd_host[k].stage + (long long)nc_stage() * kd_host[k].nvec;
+        }
+        copy(nch, vs(kV + slot, 1, cs), vs(0, 1, 1), 1);
+        if (rc) return;
+        int r = apply_H_batch(h, nk, iks.data(), xs.data(), ys.data(), nch, prec, s);
+        if (r && rc == MB_OK) rc = r;
+        copy(nch, vs(nc_stage(), 1, 1), vs(kH + slot, 1, cs), 2);
+        applies += nch * nk;
     }
     void krylov(int nch, int kV, int kS, int kH, int cs) {
         int np = nk * nch;
@@ -1166,19 +1200,17 @@ struct Solver {
         }
         for (int i = 0; i < kd && !rc; ++i) {
             if (i > 0) {
-                copy(nch, vs(kV + i - 1, 1, cs), vs(oQ, 1, 1), 0);
-                applyH_chain(nch, i - 1, kH, cs);
+                applyH_chain(nch, i - 1, kV, kH, cs);
                 MB_LAUNCH_E(KN_SMALL, set_src_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_srcH, d_srcS, np, nch, kH, kS, cs, i - 1));
             }
             MB_LAUNCH_E(KN_VEC, krylov_residual_kernel<<<dim3((unsigned)std::min<long long>(1024, (nmax + 255) / 256), np), 256, 0, s>>>(
-                                    d_k, nch, d_srcH, d_srcS, d_theta, oW));
+                                    d_k, nch, d_srcH, d_srcS, d_theta, gs32 ? o32W : oW, gs32 ? 1 : 0));
             if (!gs32) bandSolve(1, oW, oW, nch);
             // classical Gram-Schmidt, twice, in the S inner product: all
             // coefficients of a pass come from the same (pre-update) vector.
             // The roots X are common to every chain of a k-point, so their
             // part is one product with a column per chain.
             if (gs32) {
-                copy(nch, vs(oW, 1, 1), vs(o32W, 1, 1), 3);
                 bandSolve(1, o32W, o32W, nch, true);
                 for (int pass = 0; pass < 2; ++pass) {
                     gram(1, vs(o32SX, M), vs(o32W, nch), d_G2, true);
@@ -1197,15 +1229,12 @@ struct Solver {
             }
             bandS(oW, oSW, nch);
             MB_LAUNCH_E(KN_SMALL, coldot_kernel<<<dim3(1, np), 256, 0, s>>>(d_k, nch, vs(oW, 1, 1), vs(oSW, 1, 1), d_dots));
+            const bool need32 = gs32 && i + 1 < kd;
             MB_LAUNCH_E(KN_VEC, normalize_kernel<<<dim3(128, np), 256, 0, s>>>(d_k, nch, oW, oSW, kV, kS, cs, i,
-                                                                               d_dots, d_alive, kd));
-            if (gs32 && i + 1 < kd) {
-                copy(nch, vs(kV + i, 1, cs), vs(o32K + i, 1, kd), 3);
-                copy(nch, vs(kS + i, 1, cs), vs(o32SK + i, 1, kd), 3);
-            }
+                                                                               d_dots, d_alive, kd,
+                                                                               need32 ? o32K : -1, o32SK));
         }
-        copy(nch, vs(kV + kd - 1, 1, cs), vs(oQ, 1, 1), 0);
-        applyH_chain(nch, kd - 1, kH, cs);
+        applyH_chain(nch, kd - 1, kV, kH, cs);
     }
     void jacobi(int nch, int m, bool masked, int ofs, bool f32 = false) {
         if (f32) jacobi_t<float>(nch, m, masked, ofs, 1e-6);
