@@ -216,8 +216,8 @@ class Model:
             Y += np.einsum("ij,bjh,gh->big", I, X, F, optimize=True)
         E, U = self.kb_projectors()
         if len(E):
-            Fp = np.einsum("pjg,bjg->pb", np.conj(U), X)
-            Y += np.einsum("pq,pjg,qb->bjg", E, U, Fp)
+            Fp = np.einsum("pjg,bjg->pb", np.conj(U), X)      # u_q^H X
+            Y += np.einsum("pjg,pb->bjg", U, E @ Fp)           # sum_pq u_p E_pq (u_q^H X)
         return Y
 
     def apply_H_entries(self, X, entries):
