@@ -1591,7 +1591,12 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
             } else {
                 ++bulk_idle;
             }
-            bool stalled = cycles > 3 && (maxres > 0.7 * prev || bulk_idle >= 2);
+            // a stall counts only near the FP32 floor (~1e-5 of the spectrum's
+            // width): far above it the largest residual belongs to roots still
+            // converging, which the cheaper bulk cycles handle as well; past
+            // half the cycle budget the finish phase starts regardless
+            bool stalled = (cycles > 3 && maxres < 1e-3 && (maxres > 0.7 * prev || bulk_idle >= 2)) ||
+                           cycles >= max_cycles / 2;
             if (maxres < 30.0 * tol || stalled) {
                 // finish phase: the roots get FP64 HX from here on
                 S.fp64_roots = true;
