@@ -681,6 +681,7 @@ __global__ void __launch_bounds__(256) gram_rows_kernel(const EigK *ks, int nch,
 // keeps a 3 x 3 block of outputs in registers.  Partial sums per chunk go to
 // `part` (FP64) and are reduced in a fixed order by gram_reduce_kernel.
 constexpr int GT_KC = 32, GT_MAX = 48;
+// Larger products are covered by GT_MAX x GT_MAX tiles (blockIdx.z).
 __global__ void __launch_bounds__(256) gram_tile32_kernel(const EigK *ks, int nch, VSet A, VSet B, int nsplit,
                                                           double2 *part) {
     __shared__ float2 As[GT_KC][GT_MAX + 1];
@@ -688,7 +689,10 @@ __global__ void __launch_bounds__(256) gram_tile32_kernel(const EigK *ks, int nc
     const int split = blockIdx.x, prob = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
-    const int ma = A.count(), mb = B.count();
+    const int MA = A.count(), MB = B.count();
+    const int ncb = (MB + GT_MAX - 1) / GT_MAX;
+    const int r0 = (blockIdx.z / ncb) * GT_MAX, c0 = (blockIdx.z % ncb) * GT_MAX;
+    const int ma = min(GT_MAX, MA - r0), mb = min(GT_MAX, MB - c0);
     const long long n = d.nvec;
     const long long chunk = (n + nsplit - 1) / nsplit;
     const long long t0 = split * chunk, t1 = min(n, t0 + chunk);
@@ -705,10 +709,10 @@ __global__ void __launch_bounds__(256) gram_tile32_kernel(const EigK *ks, int nc
             const long long t = tb + kk;
             float2 val = make_float2(0.f, 0.f);
             if (v < ma) {
-                if (t < t1) val = d.v32[(long long)A.at(v, ch) * n + t];
+                if (t < t1) val = d.v32[(long long)A.at(r0 + v, ch) * n + t];
                 As[kk][v] = val;
             } else {
-                if (t < t1) val = d.v32[(long long)B.at(v - ma, ch) * n + t];
+                if (t < t1) val = d.v32[(long long)B.at(c0 + v - ma, ch) * n + t];
                 Bs[kk][v - ma] = val;
             }
         }
@@ -735,7 +739,7 @@ __global__ void __launch_bounds__(256) gram_tile32_kernel(const EigK *ks, int nc
         for (int j = 0; j < 3; ++j) {
             const int r = 3 * ti + i, c = 3 * tj + j;
             if (r < ma && c < mb)
-                part[((size_t)prob * nsplit + split) * ma * mb + (size_t)r * mb + c] =
+                part[((size_t)prob * nsplit + split) * MA * MB + (size_t)(r0 + r) * MB + c0 + c] =
                     make_double2(acc[i][j].x, acc[i][j].y);
         }
 }
@@ -1060,12 +1064,14 @@ struct Solver {
     template <int GJ> void gram_t(int nch, VSet A, VSet B, double2 *G, bool f32, bool lower) {
         const int nprob = nk * nch;
         const int ma = A.count(), mbc = B.count();
-        if (f32 && ma <= GT_MAX && mbc <= GT_MAX && ma * mbc >= 64) {
+        if (f32 && ma * mbc >= 64 && mbc >= 4) {
             // tile kernel: about two resident CTAs per SM over the whole grid
-            int nsplit = std::max(1, std::min(1024, (2 * h->num_sms + nprob - 1) / nprob));
+            const int tiles = ((ma + GT_MAX - 1) / GT_MAX) * ((mbc + GT_MAX - 1) / GT_MAX);
+            int nsplit = std::max(1, std::min(1024, (2 * h->num_sms + nprob * tiles - 1) / (nprob * tiles)));
             nsplit = std::min<long long>(nsplit, std::max<long long>(1, nmax / (4 * GT_KC)));
             while ((size_t)nprob * nsplit * ma * mbc > part_cap && nsplit > 1) --nsplit;
-            MB_LAUNCH_E(KN_GRAM32, gram_tile32_kernel<<<dim3(nsplit, nprob), 256, 0, s>>>(d_k, nch, A, B, nsplit, d_part));
+            MB_LAUNCH_E(KN_GRAM32, gram_tile32_kernel<<<dim3(nsplit, nprob, tiles), 256, 0, s>>>(d_k, nch, A, B, nsplit,
+                                                                                               d_part));
             MB_LAUNCH_E(KN_GRAM32,
                         gram_reduce_kernel<<<nprob, 256, 0, s>>>(d_part, nsplit, ma, mbc, G, lower ? 1 : 0));
             return;
