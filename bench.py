@@ -41,7 +41,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3   # SMs x FP32 lanes x 2 flop x max 
 # dram bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one FP32
 # plane-kernel launch of this workload, from an ncu capture of the current
 # kernel (None whenever the kernel changes until it is captured again)
-PLANE_TRAFFIC_BYTES = None
+PLANE_TRAFFIC_BYTES = 25.39e6
 
 
 def _peaks():
