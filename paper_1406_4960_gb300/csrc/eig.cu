@@ -79,7 +79,7 @@ __global__ void gram_reduce_kernel(const double2 *part, int nsplit, int ma, int 
 // dst_i = src_i for index sets (FP64 -> FP64), or into / out of the FP32 stage
 __global__ void copy_kernel(const EigK *ks, int nch, VSet S, VSet D, int mode) {
     // mode 0: base -> base; 1: base -> stage (to float); 2: stage -> base (to double);
-    // 3: base -> v32 (to float); 4: v32 -> base (to double)
+    // 3: base -> v32 (to float); 4: v32 -> base (to double); 5: stage -> v32
     const int prob = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
@@ -94,7 +94,8 @@ __global__ void copy_kernel(const EigK *ks, int nch, VSet S, VSet D, int mode) {
         else if (mode == 1) d.stage[di] = make_float2((float)d.base[si].x, (float)d.base[si].y);
         else if (mode == 2) d.base[di] = make_double2((double)d.stage[si].x, (double)d.stage[si].y);
         else if (mode == 3) d.v32[di] = make_float2((float)d.base[si].x, (float)d.base[si].y);
-        else d.base[di] = make_double2((double)d.v32[si].x, (double)d.v32[si].y);
+        else if (mode == 4) d.base[di] = make_double2((double)d.v32[si].x, (double)d.v32[si].y);
+        else d.v32[di] = d.stage[si];
     }
 }
 
@@ -1007,7 +1008,7 @@ struct Solver {
     // of their basis (a pencil), so that their result does not depend on how
     // orthogonal the Krylov vectors came out
     bool gs32 = false;
-    int o32X = 0, o32SX = 0, o32W = 0, o32K = 0, o32SK = 0, n32 = 0;
+    int o32X = 0, o32SX = 0, o32HX = 0, o32W = 0, o32K = 0, o32SK = 0, o32HK = 0, o32T = 0, n32 = 0;
     double2 *d_Sg = nullptr, *d_Ub = nullptr, *d_Tb = nullptr;
     int *d_statb = nullptr;
     int oV, oHV, oSV, oVB, oHVB, oSVB, oQ, oHQ, oW, oSW, oT;
@@ -1195,6 +1196,7 @@ struct Solver {
         int r = apply_H_batch(h, nk, iks.data(), xs.data(), ys.data(), nch, prec, s);
         if (r && rc == MB_OK) rc = r;
         copy(nch, vs(nc_stage(), 1, 1), vs(kH + slot, 1, cs), 2);
+        if (lowp()) copy(nch, vs(nc_stage(), 1, 1), vs(o32HK + slot, 1, kd), 5);
         applies += nch * nk;
     }
     void krylov(int nch, int kV, int kS, int kH, int cs) {
@@ -1203,6 +1205,7 @@ struct Solver {
         if (gs32) {
             copy(1, vs(oV, M), vs(o32X, M), 3);
             copy(1, vs(oSV, M), vs(o32SX, M), 3);
+            if (lowp()) copy(1, vs(oHV, M), vs(o32HX, M), 3);
         }
         for (int i = 0; i < kd && !rc; ++i) {
             if (i > 0) {
@@ -1235,7 +1238,7 @@ struct Solver {
             }
             bandS(oW, oSW, nch);
             MB_LAUNCH_E(KN_SMALL, coldot_kernel<<<dim3(1, np), 256, 0, s>>>(d_k, nch, vs(oW, 1, 1), vs(oSW, 1, 1), d_dots));
-            const bool need32 = gs32 && i + 1 < kd;
+            const bool need32 = gs32 && (i + 1 < kd || lowp());
             MB_LAUNCH_E(KN_VEC, normalize_kernel<<<dim3(128, np), 256, 0, s>>>(d_k, nch, oW, oSW, kV, kS, cs, i,
                                                                                d_dots, d_alive, kd,
                                                                                need32 ? o32K : -1, o32SK));
@@ -1272,9 +1275,9 @@ struct Solver {
     // per k-point: U = L^{-H} from V^H S V = L L^H (dead Krylov slots made
     // identity), Ritz pairs of U^H (V^H H V) U; returns the Ritz vectors'
     // coordinates in the V basis (U Y) and leaves the values in d_evals.
-    const double2 *rr_pencil(int nch, VSet V, VSet HV, VSet SV, int m, int ofs) {
-        gram(nch, V, HV, d_G, false, true);
-        gram(nch, V, SV, d_Sg, false, true);
+    const double2 *rr_pencil(int nch, VSet V, VSet HV, VSet SV, int m, int ofs, bool f32 = false) {
+        gram(nch, V, HV, d_G, f32, true);
+        gram(nch, V, SV, d_Sg, f32, true);
         return pencil_solve(nch, m, ofs);
     }
     // the pencil (d_G, d_Sg) of nch problems per k-point
@@ -1296,10 +1299,17 @@ struct Solver {
     // fresh_hx: HX from a new apply in the solve's precision instead of the
     // rotation of [HX|HK] (cheaper than the FP64 rotation when the applies are
     // FP32, and no less accurate than HK from FP32 applies)
-    void rotate_set(const double2 *Y, int m, bool fresh_hx = false) {
-        combine(1, vs(oV, m), vs(oT, M), Y, 1.0, 0.0);
+    // V32: in the bulk cycles, the FP32 copies of the rotated vectors (the
+    // rotation then runs in FP32 and X keeps FP32 accuracy until the finish)
+    void rotate_set(const double2 *Y, int m, bool fresh_hx = false, const VSet *V32 = nullptr) {
+        if (V32) {
+            combine(1, *V32, vs(o32T, M), Y, 1.0, 0.0, true);
+            copy(1, vs(o32T, M), vs(oV, M), 4);
+        } else {
+            combine(1, vs(oV, m), vs(oT, M), Y, 1.0, 0.0);
+        }
         if (!fresh_hx) combine(1, vs(oHV, m), vs(oT + M, M), Y, 1.0, 0.0);
-        copy(1, vs(oT, M), vs(oV, M), 0);
+        if (!V32) copy(1, vs(oT, M), vs(oV, M), 0);
         if (fresh_hx) applyH(oV, oHV, M, prec);
         else copy(1, vs(oT + M, M), vs(oHV, M), 0);
         bandS(oV, oSV, M);
@@ -1309,13 +1319,20 @@ struct Solver {
     // projected matrices are computed.
     void rr_full(bool withK) {
         int m = withK ? mA : M;
-        if (withK) {
+        if (withK && lowp()) {
+            // bulk cycles: the Krylov rows from the FP32 copies
+            gram(1, vs(o32K, kd), vs(o32HX, M, 0, o32HK, kd, 0), d_G2, true);
+            gram(1, vs(o32K, kd), vs(o32SX, M, 0, o32SK, kd, 0), d_T, true);
+        } else if (withK) {
             gram(1, vs(oV + M, kd), vs(oHV, m), d_G2);
             if (gs32) gram(1, vs(oV + M, kd), vs(oSV, m), d_T);
+        }
+        if (withK) {
             MB_LAUNCH_E(KN_SMALL, assemble_rr_kernel<<<dim3((m * m + 127) / 128, nk), 128, 0, s>>>(
                                       d_G2, gs32 ? d_T : nullptr, d_eps, M, m, d_G, gs32 ? d_Sg : nullptr));
             if (gs32) {
-                rotate_set(pencil_solve(1, m, M), m, lowp());
+                const VSet v32 = vs(o32X, M, 0, o32K, kd, 0);
+                rotate_set(pencil_solve(1, m, M), m, lowp(), lowp() ? &v32 : nullptr);
             } else {
                 jacobi(1, m, true, M);
                 rotate_set(d_Y, m);
@@ -1330,16 +1347,26 @@ struct Solver {
     // S-orthonormalization and Rayleigh-Ritz in one rotation: U = L^{-H} from
     // X^H S X = L L^H, Ritz pairs of U^H (X^H H X) U, then X <- X U Y.
     void orth_rr() {
-        gram(1, vs(oV, M), vs(oSV, M), d_G, false, true);
+        const bool f32 = lowp();
+        if (f32) {
+            copy(1, vs(oV, M), vs(o32X, M), 3);
+            copy(1, vs(oSV, M), vs(o32SX, M), 3);
+            copy(1, vs(oHV, M), vs(o32HX, M), 3);
+            gram(1, vs(o32X, M), vs(o32SX, M), d_G, true, true);
+        } else {
+            gram(1, vs(oV, M), vs(oSV, M), d_G, false, true);
+        }
         size_t smem = (size_t)M * M * sizeof(double2);
         cuda(smem_limit_once((const void *)cholinv_kernel, h->device, h->smem_optin));
         MB_LAUNCH_E(KN_SMALL, cholinv_kernel<<<nk, 128, smem, s>>>(d_G, M, d_U, d_status));
-        gram(1, vs(oV, M), vs(oHV, M), d_G2, false, true);
+        if (f32) gram(1, vs(o32X, M), vs(o32HX, M), d_G2, true, true);
+        else gram(1, vs(oV, M), vs(oHV, M), d_G2, false, true);
         small_gemm(d_G2, d_U, d_T, M, 0);     // (X^H H X) U
         small_gemm(d_U, d_T, d_G, M, 1);      // U^H (X^H H X) U
         jacobi(1, M, false, M, lowp());
         small_gemm(d_U, d_Y, d_T, M, 0);      // U Y
-        rotate_set(d_T, M, lowp());
+        const VSet x32 = vs(o32X, M);
+        rotate_set(d_T, M, lowp(), f32 ? &x32 : nullptr);
         MB_LAUNCH_E(KN_SMALL, take_evals_kernel<<<(M * nk + 127) / 128, 128, 0, s>>>(d_evals, M, nk, d_eps));
     }
     void cycle_B() {
@@ -1349,7 +1376,10 @@ struct Solver {
         if (gs32) copy(nblk, vs(oSV, b, b), vs(oSVB, b, mB), 0);
         krylov(nblk, oVB + b, oSVB + b, oHVB + b, mB);
         const double2 *Yc = d_Y;
-        if (gs32) {
+        if (lowp()) {
+            Yc = rr_pencil(nblk, vs(o32X, b, b, o32K, kd, kd), vs(o32HX, b, b, o32HK, kd, kd),
+                           vs(o32SX, b, b, o32SK, kd, kd), mB, b, true);
+        } else if (gs32) {
             Yc = rr_pencil(nblk, vs(oVB, mB, mB), vs(oHVB, mB, mB), vs(oSVB, mB, mB), mB, b);
         } else {
             gram(nblk, vs(oVB, mB, mB), vs(oHVB, mB, mB), d_G, false, true);
@@ -1442,10 +1472,13 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     S.gs32 = prec != MB_FP64;
     S.o32X = 0;
     S.o32SX = S.M;
-    S.o32W = 2 * S.M;
+    S.o32HX = 2 * S.M;
+    S.o32W = 3 * S.M;
     S.o32K = S.o32W + S.nc;
     S.o32SK = S.o32K + S.nc * S.kd;
-    S.n32 = S.o32SK + S.nc * S.kd;
+    S.o32HK = S.o32SK + S.nc * S.kd;
+    S.o32T = S.o32HK + S.nc * S.kd;
+    S.n32 = S.o32T + S.M;
     // per-k memory
     S.kd_host.resize(S.nk);
     size_t pofs = 0;
