@@ -653,6 +653,9 @@ int upload_tables(mb_handle *h) {
         MB_CUDA(cudaMemcpy(h->d_zidx, zi.data(), zi.size() * sizeof(int), cudaMemcpyHostToDevice));
     }
     upload_fft_twiddles();
+    MB_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    MB_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    MB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     MB_CUDA(cudaGetLastError());
     return upload_proj_tables(h);
 }
@@ -692,6 +695,11 @@ void free_tables(mb_handle *h) {
     h->d_projB = nullptr;
     if (h->d_zidx) cudaFree(h->d_zidx);
     h->d_zidx = nullptr;
+    if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    h->aux = nullptr;
+    h->ev_fork = h->ev_join = nullptr;
     if (h->d_tcerr) cudaFree(h->d_tcerr);
     h->d_tcerr = nullptr;
     if (h->scratch.ptr) cudaFree(h->scratch.ptr);
@@ -920,6 +928,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     const int *d_partner = h->d_zidx ? d_tproj + h->nterm : nullptr;
     const int *d_pstart = h->d_zidx ? d_partner + h->nkb : nullptr;
     const int *d_plist = h->d_zidx ? d_pstart + h->nkb + 1 : nullptr;
+    bool forked = false;
     // projector overlaps first (they read X only)
     if (h->nterm > 0 && tensor) {
         cudaError_t e = cudaSuccess;
@@ -938,6 +947,11 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         std::copy(desc, desc + nsel, ca.d);
         MB_LAUNCH(h, s, KN_COEF, coef_kernel<R><<<dim3((nbands * h->nkb + 127) / 128, nsel), 128, 0, s>>>(ca));
     } else if (h->nterm > 0) {
+        // the overlaps read X only: they run on the aux stream beside the
+        // plane kernel and are joined before the epilogue
+        MB_CUDA(cudaEventRecord(h->ev_fork, s));
+        MB_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+        cudaStream_t s = h->aux;
         NlArgs<R> na;
         na.zf = reinterpret_cast<const R *>(t.zf);
         na.E = reinterpret_cast<const R *>(t.E);
@@ -973,6 +987,8 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         MB_CUDA(smem_limit_once((const void *)nl_back_kernel<R>, h->device, h->smem_optin));
         MB_LAUNCH(h, s, KN_COEF, nl_back_kernel<R><<<dim3((maxldg + 127) / 128, h->nzf, nbands * nsel), 128, bsm, s>>>(
                                      na, d_zstart, d_zlist, d_tproj));
+        MB_CUDA(cudaEventRecord(h->ev_join, s));
+        forked = true;
     }
     // local potential through the planes
     PlaneArgs<R> pa;
@@ -1008,6 +1024,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         MB_CUDA(smem_limit_once((const void *)plane_kernel<R>, h->device, h->smem_optin));
         MB_LAUNCH(h, s, KN_PLANE, plane_kernel<R><<<nsel * nbands * nchunks, 256, plan.smem, s>>>(pa));
     }
+    if (forked) MB_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
     EpiArgs<R> ea;
     ea.Sband = reinterpret_cast<const R *>(t.Sband);
     ea.Dband = reinterpret_cast<const R *>(t.Dband);

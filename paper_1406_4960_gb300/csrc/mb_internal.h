@@ -97,6 +97,10 @@ struct mb_handle {
     bool pfac_ready = false;
     mb::Scratch scratch;
     void *d_desc = nullptr;          // descriptor arrays for batched launches
+    // second stream of the apply: the projector overlaps run there beside the
+    // plane kernel (fork and join by events, capturable into graphs)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t desc_bytes = 0;
     std::string last_cuda_error;
     // plane-kernel launch shapes picked by mb_autotune: (k-points per batch,
