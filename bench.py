@@ -411,8 +411,8 @@ def run_ours(args):
         return allmax(ms), launches, prof
 
     if args.eig_only:
-        # one mixed and one plain-FP64 solve (for launch lists under ncu)
-        for prec in ("fp32", "fp64"):
+        # one mixed and/or one plain-FP64 solve (for launch lists under ncu)
+        for prec in args.eig_prec.split(","):
             t0 = time.perf_counter()
             ev, info = h.eigsolve(w.nbands, 1e-6, prec)
             print(json.dumps({"eig_only": prec, "seconds": time.perf_counter() - t0, "cycles": info.cycles}))
@@ -550,6 +550,7 @@ def main():
     ap.add_argument("--serve-n", type=int, default=12)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--eig-reps", type=int, default=6)
+    ap.add_argument("--eig-prec", default="fp32,fp64", help="precisions of --eig-only (comma-separated)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
