@@ -63,33 +63,34 @@ static VSet vs(int s1, int c1, int cs1 = 0, int s2 = 0, int c2 = 0, int cs2 = 0)
 // lower: only entries j <= i were computed (a Hermitian product); the upper
 // triangle is written as the conjugate of the lower one.
 __global__ void gram_reduce_kernel(const double2 *part, int nsplit, int ma, int mb, double2 *G, int lower) {
-    const int prob = blockIdx.x;
+    const int prob = blockIdx.y;
     const int nout = ma * mb;
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-        int i = o / mb, j = o % mb;
-        const bool up = lower && j > i;
-        const int src = up ? j * mb + i : o;
-        double2 s = make_double2(0.0, 0.0);
-        for (int sp = 0; sp < nsplit; ++sp) s = s + part[((size_t)prob * nsplit + sp) * nout + src];
-        if (up) s.y = -s.y;
-        G[(size_t)prob * LD * LD + i * LD + j] = s;
-    }
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= nout) return;
+    int i = o / mb, j = o % mb;
+    const bool up = lower && j > i;
+    const int src = up ? j * mb + i : o;
+    const double2 *p = part + (size_t)prob * nsplit * nout + src;
+    double2 s = make_double2(0.0, 0.0);
+#pragma unroll 8
+    for (int sp = 0; sp < nsplit; ++sp) s = s + p[(size_t)sp * nout];
+    if (up) s.y = -s.y;
+    G[(size_t)prob * LD * LD + i * LD + j] = s;
 }
 
 // dst_i = src_i for index sets (FP64 -> FP64), or into / out of the FP32 stage
 __global__ void copy_kernel(const EigK *ks, int nch, VSet S, VSet D, int mode) {
+    // grid: (blocks along the vector, vector of the set, problem)
     // mode 0: base -> base; 1: base -> stage (to float); 2: stage -> base (to double);
     // 3: base -> v32 (to float); 4: v32 -> base (to double); 5: stage -> v32
-    const int prob = blockIdx.y;
+    const int prob = blockIdx.z, i = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
-    const int m = S.count();
-    const long long total = (long long)m * d.nvec;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(e / d.nvec);
-        long long t = e - (long long)i * d.nvec;
-        long long si = (long long)S.at(i, ch) * d.nvec + t, di = (long long)D.at(i, ch) * d.nvec + t;
+    if (i >= S.count()) return;
+    const long long sb = (long long)S.at(i, ch) * d.nvec, db = (long long)D.at(i, ch) * d.nvec;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.nvec;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long si = sb + t, di = db + t;
         if (mode == 0) d.base[di] = d.base[si];
         else if (mode == 1) d.stage[di] = make_float2((float)d.base[si].x, (float)d.base[si].y);
         else if (mode == 2) d.base[di] = make_double2((double)d.stage[si].x, (double)d.stage[si].y);
@@ -1074,7 +1075,8 @@ struct Solver {
             MB_LAUNCH_E(KN_GRAM32, gram_tile32_kernel<<<dim3(nsplit, nprob, tiles), 256, 0, s>>>(d_k, nch, A, B, nsplit,
                                                                                                d_part));
             MB_LAUNCH_E(KN_GRAM32,
-                        gram_reduce_kernel<<<nprob, 256, 0, s>>>(d_part, nsplit, ma, mbc, G, lower ? 1 : 0));
+                        gram_reduce_kernel<<<dim3((ma * mbc + 127) / 128, nprob), 128, 0, s>>>(d_part, nsplit, ma, mbc, G,
+                                                                                           lower ? 1 : 0));
             return;
         }
         const int rowgroups = (ma + 7) / 8, colgroups = (mbc + GJ - 1) / GJ;
@@ -1089,7 +1091,8 @@ struct Solver {
             MB_LAUNCH_E(KN_GRAM, (gram_rows_kernel<false, GJ><<<dim3(nsplit, nprob, rowgroups * colgroups), 256, 0, s>>>(
                                      d_k, nch, A, B, nsplit, colgroups, d_part, lower ? 1 : 0)));
         MB_LAUNCH_E(f32 ? KN_GRAM32 : KN_GRAM,
-                    gram_reduce_kernel<<<nprob, 256, 0, s>>>(d_part, nsplit, ma, mbc, G, lower ? 1 : 0));
+                    gram_reduce_kernel<<<dim3((ma * mbc + 127) / 128, nprob), 128, 0, s>>>(d_part, nsplit, ma, mbc, G,
+                                                                                           lower ? 1 : 0));
     }
     void combine(int nch, VSet A, VSet C, const double2 *Y, double alpha, double beta, bool f32 = false) {
         if (f32) combine_t<true>(nch, A, C, Y, alpha, beta);
@@ -1116,7 +1119,8 @@ struct Solver {
                                   A, B, C, m, conjA));
     }
     void copy(int nch, VSet S, VSet D, int mode) {
-        MB_LAUNCH_E(KN_VEC, copy_kernel<<<dim3(256, nk * nch), 256, 0, s>>>(d_k, nch, S, D, mode));
+        const unsigned bx = (unsigned)std::min<long long>(64, (nmax + 255) / 256);
+        MB_LAUNCH_E(KN_VEC, copy_kernel<<<dim3(bx, S.count(), nk * nch), 256, 0, s>>>(d_k, nch, S, D, mode));
     }
     void bandS(int src, int dst, int nv) {
         const dim3 grid((maxldg + 127) / 128, h->nb, nk * nv);
