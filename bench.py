@@ -420,6 +420,10 @@ def run_ours(args):
 
     if args.eig_only:
         # one mixed and/or one plain-FP64 solve (for launch lists under ncu)
+        if args.eig_workload != "slab":
+            h.close()
+            w = W.BY_NAME[args.eig_workload]()
+            h = mb.Handle.from_workload(w, device=local)
         for prec in args.eig_prec.split(","):
             t0 = time.perf_counter()
             ev, info = h.eigsolve(w.nbands, 1e-6, prec)
@@ -556,6 +560,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--eig-reps", type=int, default=6)
     ap.add_argument("--eig-prec", default="fp32,fp64", help="precisions of --eig-only (comma-separated)")
+    ap.add_argument("--eig-workload", default="slab", help="workload of --eig-only (slab, graphene, kbatch, tiny)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
