@@ -229,7 +229,7 @@ def kbatch_bench(mb, W, local, args):
     byts, flops = workload_sizes(h, w, "fp32")
     out = {"workload": "kbatch: 2x2 graphene, Ecut 30 Ha, 32x32 grid, 100 B-splines, 64 k x 24 bands",
            "autotune": tune, "apply_ms": ms, "apply_gbs": byts / (ms * 1e-3) / 1e9,
-           "plane_tflops_algorithmic": None}
+           "plane_flops_per_apply_ms_tflops": flops / (ms * 1e-3) / 1e12}
     if args.kbatch_solve:
         t0 = time.perf_counter()
         ev, info = h.eigsolve(w.nbands, 1e-6, "fp32")

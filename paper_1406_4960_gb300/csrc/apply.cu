@@ -743,7 +743,7 @@ static PlanePlan plan_plane(const mb_handle *h, int nsel, int nbands, size_t c2,
     if (reg_ok) {
         const size_t plane_bytes = (size_t)h->n1 * (h->n2 + 1) * c2;
         // matches the kernel's launch bounds
-        ctas_per_sm = c2 == 8 ? (NN <= 512 ? 3 : small ? 2 : 1) : 1;
+        ctas_per_sm = c2 == 8 ? ((NN <= 512 || (h->n1 == 32 && h->n2 == 32)) ? 3 : small ? 2 : 1) : 1;
         for (int bt = bt_max; bt >= 1 && !p.reg; --bt) {
             size_t budget = (size_t)h->smem_optin / ctas_per_sm - 1024;
             size_t acc = (size_t)bt * K * maxldg * c2;

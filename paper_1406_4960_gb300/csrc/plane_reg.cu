@@ -87,14 +87,16 @@ __device__ __forceinline__ void fft_reg(C (&x)[N]) {
     }
 }
 
-// CTA shape: FP32 planes of 16 columns use 192 threads (a 12-plane group is
-// then one fused column line per thread), everything else 256.  FP32 grids of
-// at most 512 points run three CTAs per SM, other FP32 grids with both sides
-// <= 32 two (the host plan sizes shared memory for that); the register budget
-// follows.
+// CTA shape: FP32 planes of 16 columns, and 32 x 32 FP32 planes, use 192
+// threads (a 12-plane group of 16 columns, or a 6-plane group of 32 columns,
+// is then one fused column line per thread), everything else 256.  Those FP32
+// grids and all others of at most 512 points run three CTAs per SM, the
+// remaining FP32 grids with both sides <= 32 two (the host plan sizes shared
+// memory for that); the register budget follows.
 template <typename R, int N1, int N2> struct PlaneShape {
-    static constexpr int threads = (sizeof(R) == 4 && N2 == 16) ? 192 : 256;
-    static constexpr int ctas = (sizeof(R) == 4 && N1 * N2 <= 512) ? 3 : (N1 <= 32 && N2 <= 32 && sizeof(R) == 4) ? 2 : 1;
+    static constexpr int threads = (sizeof(R) == 4 && (N2 == 16 || (N1 == 32 && N2 == 32))) ? 192 : 256;
+    static constexpr int ctas = (sizeof(R) == 4 && (N1 * N2 <= 512 || (N1 == 32 && N2 == 32))) ? 3
+                              : (N1 <= 32 && N2 <= 32 && sizeof(R) == 4) ? 2 : 1;
 };
 
 template <typename R, int N1, int N2>
