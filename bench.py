@@ -557,7 +557,7 @@ def main():
     ap.add_argument("--kbatch-solve", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-n", type=int, default=12)
-    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--eig-reps", type=int, default=6)
     ap.add_argument("--eig-prec", default="fp32,fp64", help="precisions of --eig-only (comma-separated)")
     ap.add_argument("--eig-workload", default="slab", help="workload of --eig-only (slab, graphene, kbatch, tiny)")
