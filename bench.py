@@ -438,6 +438,27 @@ def run_ours(args):
     ms64, _, prof64 = timed("fp64", max(3, args.steps // 5), 3, profile=True)
     msbf, _, profbf = timed("bf16", max(3, args.steps // 5), 3, profile=True)
 
+    # S and S^-1 (row a7) on the same blocks, all k-points, FP32 and FP64
+    def timed_banded(which, prec, reps=10):
+        Xs, Ys = blocks(prec, replica_seed(3000, rank))
+        fn = h.apply_S if which == "S" else h.apply_Sinv
+        for _ in range(3):
+            for ik in iks:
+                fn(ik, Xs[ik], Ys[ik], prec, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            for ik in iks:
+                fn(ik, Xs[ik], Ys[ik], prec, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        byts = sum(2 * x.numel() * x.element_size() for x in Xs)     # read X, write Y
+        return {"ms": ms, "GB/s": byts / (ms * 1e-3) / 1e9, "of_hbm_peak": byts / (ms * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6797.2)}
+
+    banded = {"%s_%s" % (w_, p_): timed_banded(w_, p_) for w_ in ("S", "Sinv") for p_ in ("fp32", "fp64")}
+
     bytes32, flops32 = workload_sizes(h, w, "fp32")
     bytes64, _ = workload_sizes(h, w, "fp64")
     value = job_gbs(bytes32, ms32, world)
@@ -516,6 +537,7 @@ def run_ours(args):
         "fp64_apply": {"value": job_gbs(bytes64, ms64, world), "unit": "GB/s", "ms_per_step": ms64},
         "kernels_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in prof.items()},
         "kernels_ms_per_step_fp64": {k: v[0] / max(3, args.steps // 5) for k, v in prof64.items()},
+        "banded_S_Sinv": banded,
         "bf16_apply": {"value": job_gbs(bytes32, msbf, world), "unit": "GB/s", "ms_per_step": msbf,
                        "note": "FP32 planes, projector contractions in BF16 on tcgen05 tensor cores",
                        "kernels_ms_per_step": {k: v[0] / max(3, args.steps // 5) for k, v in profbf.items()}},
