@@ -465,54 +465,87 @@ __global__ void coef_kernel(const __grid_constant__ CoefArgs<R> a) {
 }
 
 // ---------------------------------------------------------------------------
-// banded operators along j, one thread per (band, G) column
+// banded operators along j
+// S X: one thread per (band, row j, G) (the 2K-1 rows it reads are shared
+// through L1 with the neighbouring rows' threads)
 template <typename R>
 __global__ void banded_S_kernel(const R *Sband, int order, int nb, int ng, int ldg, int nbands,
                                 const typename V2<R>::T *X, typename V2<R>::T *Y) {
     typedef typename V2<R>::T R2;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = blockIdx.y;
+    const int j = blockIdx.y, b = blockIdx.z;
     if (g >= ldg) return;
     const int K = order, W = 2 * K - 1;
-    const R2 *x = X + (size_t)b * nb * ldg;
-    R2 *y = Y + (size_t)b * nb * ldg;
-    for (int j = 0; j < nb; ++j) {
-        R2 s = czero<R2>();
-        if (g < ng)
-            for (int dd = 0; dd < W; ++dd) {
-                int jj = j + dd - (K - 1);
-                if (jj >= 0 && jj < nb) rfma(s, Sband[(size_t)j * W + dd], x[(size_t)jj * ldg + g]);
-            }
-        y[(size_t)j * ldg + g] = s;
+    const R2 *x = X + (size_t)b * nb * ldg + g;
+    R2 s = czero<R2>();
+    if (g < ng) {
+        const int dlo = max(0, K - 1 - j), dhi = min(W, nb + K - 1 - j);
+        for (int dd = dlo; dd < dhi; ++dd) rfma(s, __ldg(&Sband[(size_t)j * W + dd]), x[(size_t)(j + dd - (K - 1)) * ldg]);
     }
+    Y[(size_t)b * nb * ldg + (size_t)j * ldg + g] = s;
 }
 
-// L L^T y = x with L[j][j-d] = Lb[(j*K + d)] (per-G factors when gstride > 0)
+// L L^T y = x with L[j][j-d] = Lb[(j*K + d)], one thread per (band, G)
+// column; the recurrence keeps the last K-1 results in registers and runs
+// over tiles of PD rows whose right-hand sides are all loaded first.
 template <typename R>
-__global__ void banded_solve_kernel(const R *Lb, size_t gstride, int order, int nb, int ng, int ldg,
-                                    int nbands, const typename V2<R>::T *X, typename V2<R>::T *Y) {
+__global__ void __launch_bounds__(64) banded_solve_kernel(const R *Lb, int order, int nb, int ng, int ldg,
+                                                          int nbands, const typename V2<R>::T *X,
+                                                          typename V2<R>::T *Y) {
     typedef typename V2<R>::T R2;
+    constexpr int KM = 8, PD = 8;            // largest order; rows per tile
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (g >= ldg) return;
     const int K = order;
-    const R *L = Lb + gstride * g;
-    const R2 *x = X + (size_t)b * nb * ldg;
-    R2 *y = Y + (size_t)b * nb * ldg;
+    const R2 *x = X + (size_t)b * nb * ldg + g;
+    R2 *y = Y + (size_t)b * nb * ldg + g;
     if (g >= ng) {
-        for (int j = 0; j < nb; ++j) y[(size_t)j * ldg + g] = czero<R2>();
+        for (int j = 0; j < nb; ++j) y[(size_t)j * ldg] = czero<R2>();
         return;
     }
-    for (int j = 0; j < nb; ++j) {
-        R2 s = x[(size_t)j * ldg + g];
-        for (int dd = 1; dd < K && dd <= j; ++dd) rfma(s, -L[(size_t)j * K + dd], y[(size_t)(j - dd) * ldg + g]);
-        y[(size_t)j * ldg + g] = rscale(R(1) / L[(size_t)j * K], s);
+    R2 win[KM];                              // win[d-1] = y[j - d]
+#pragma unroll
+    for (int i = 0; i < KM; ++i) win[i] = czero<R2>();
+    for (int j0 = 0; j0 < nb; j0 += PD) {
+        R2 xs[PD];
+#pragma unroll
+        for (int u = 0; u < PD; ++u) xs[u] = j0 + u < nb ? x[(size_t)(j0 + u) * ldg] : czero<R2>();
+#pragma unroll
+        for (int u = 0; u < PD; ++u) {
+            const int j = j0 + u;
+            if (j >= nb) break;
+            R2 s = xs[u];
+#pragma unroll
+            for (int dd = 1; dd < KM; ++dd)
+                if (dd < K && dd <= j) rfma(s, -__ldg(&Lb[(size_t)j * K + dd]), win[dd - 1]);
+            const R2 yj = rscale(R(1) / __ldg(&Lb[(size_t)j * K]), s);
+            y[(size_t)j * ldg] = yj;
+#pragma unroll
+            for (int i = KM - 1; i > 0; --i) win[i] = win[i - 1];
+            win[0] = yj;
+        }
     }
-    for (int j = nb - 1; j >= 0; --j) {
-        R2 s = y[(size_t)j * ldg + g];
-        for (int dd = 1; dd < K && j + dd < nb; ++dd)
-            rfma(s, -L[(size_t)(j + dd) * K + dd], y[(size_t)(j + dd) * ldg + g]);
-        y[(size_t)j * ldg + g] = rscale(R(1) / L[(size_t)j * K], s);
+#pragma unroll
+    for (int i = 0; i < KM; ++i) win[i] = czero<R2>();
+    for (int j1 = nb - 1; j1 >= 0; j1 -= PD) {
+        R2 xs[PD];
+#pragma unroll
+        for (int u = 0; u < PD; ++u) xs[u] = j1 - u >= 0 ? y[(size_t)(j1 - u) * ldg] : czero<R2>();
+#pragma unroll
+        for (int u = 0; u < PD; ++u) {
+            const int j = j1 - u;
+            if (j < 0) break;
+            R2 s = xs[u];
+#pragma unroll
+            for (int dd = 1; dd < KM; ++dd)
+                if (dd < K && j + dd < nb) rfma(s, -__ldg(&Lb[(size_t)(j + dd) * K + dd]), win[dd - 1]);
+            const R2 zj = rscale(R(1) / __ldg(&Lb[(size_t)j * K]), s);
+            y[(size_t)j * ldg] = zj;
+#pragma unroll
+            for (int i = KM - 1; i > 0; --i) win[i] = win[i - 1];
+            win[0] = zj;
+        }
     }
 }
 
@@ -1103,24 +1136,24 @@ int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nb
     if (which != BAND_S && X == Y) return MB_EINVAL;
     MB_CUDA(cudaSetDevice(h->device));
     const KPoint &kp = h->kp[ik];
-    dim3 grid((kp.ldg + 127) / 128, nbands);
+    const dim3 gS((kp.ldg + 127) / 128, h->nb, nbands), gL((kp.ldg + 63) / 64, nbands);
     if (which != BAND_S && which != BAND_SINV) return MB_EINVAL;
     if (prec == MB_FP64) {
         const DevTables &t = h->t64;
         auto x = reinterpret_cast<const double2 *>(X);
         auto y = reinterpret_cast<double2 *>(Y);
         if (which == BAND_S)
-            MB_LAUNCH(h, s, KN_BANDED, banded_S_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
+            MB_LAUNCH(h, s, KN_BANDED, banded_S_kernel<double><<<gS, 128, 0, s>>>((const double *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
         else
-            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<double><<<grid, 128, 0, s>>>((const double *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
+            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<double><<<gL, 64, 0, s>>>((const double *)t.Lband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
     } else {
         const DevTables &t = h->t32;
         auto x = reinterpret_cast<const float2 *>(X);
         auto y = reinterpret_cast<float2 *>(Y);
         if (which == BAND_S)
-            MB_LAUNCH(h, s, KN_BANDED, banded_S_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
+            MB_LAUNCH(h, s, KN_BANDED, banded_S_kernel<float><<<gS, 128, 0, s>>>((const float *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
         else
-            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<float><<<grid, 128, 0, s>>>((const float *)t.Lband, 0, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
+            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<float><<<gL, 64, 0, s>>>((const float *)t.Lband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
     }
     MB_CUDA(cudaGetLastError());
     return MB_OK;
