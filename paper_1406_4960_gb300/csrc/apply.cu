@@ -984,7 +984,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         // plane kernel and are joined before the epilogue
         MB_CUDA(cudaEventRecord(h->ev_fork, s));
         MB_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
-        cudaStream_t s = h->aux;
+        cudaStream_t sa = h->aux;
         NlArgs<R> na;
         na.zf = reinterpret_cast<const R *>(t.zf);
         na.E = reinterpret_cast<const R *>(t.E);
@@ -1007,7 +1007,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
 #define MB_ZX(NZ)                                                                                  \
     do {                                                                                           \
         MB_CUDA(smem_limit_once((const void *)nl_zx_kernel<R, NZ>, h->device, h->smem_optin));   \
-        MB_LAUNCH(h, s, KN_PROJ, (nl_zx_kernel<R, NZ><<<gz, bz, zsm, s>>>(na)));                 \
+        MB_LAUNCH(h, sa, KN_PROJ, (nl_zx_kernel<R, NZ><<<gz, bz, zsm, sa>>>(na)));                 \
     } while (0)
         if (h->nzf <= 2) MB_ZX(2);
         else if (h->nzf <= 4) MB_ZX(4);
@@ -1015,12 +1015,12 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         else if (h->nzf <= 12) MB_ZX(12);
         else MB_ZX(16);
 #undef MB_ZX
-        MB_LAUNCH(h, s, KN_COEF, nl_coef_kernel<R><<<dim3(nbands, nsel, (h->nkb + 7) / 8), 256, 0, s>>>(na));
+        MB_LAUNCH(h, sa, KN_COEF, nl_coef_kernel<R><<<dim3(nbands, nsel, (h->nkb + 7) / 8), 256, 0, sa>>>(na));
         const size_t bsm = (size_t)h->nterm * (sizeof(R2) + sizeof(int));
         MB_CUDA(smem_limit_once((const void *)nl_back_kernel<R>, h->device, h->smem_optin));
-        MB_LAUNCH(h, s, KN_COEF, nl_back_kernel<R><<<dim3((maxldg + 127) / 128, h->nzf, nbands * nsel), 128, bsm, s>>>(
+        MB_LAUNCH(h, sa, KN_COEF, nl_back_kernel<R><<<dim3((maxldg + 127) / 128, h->nzf, nbands * nsel), 128, bsm, sa>>>(
                                      na, d_zstart, d_zlist, d_tproj));
-        MB_CUDA(cudaEventRecord(h->ev_join, s));
+        MB_CUDA(cudaEventRecord(h->ev_join, sa));
         forked = true;
     }
     // local potential through the planes
