@@ -942,10 +942,12 @@ void host_jacobi_sym(int n, std::vector<double> &A, std::vector<double> &w, std:
 
 // Lowest M free-electron states (|k+G|^2/2 + z-mode n): pure plane wave times
 // an S-normalized eigenvector of (D/2) c = e S c.  S-orthonormal by construction.
-void free_electron_start(const mb_handle *h, int ik, int M, std::vector<double2> &X) {
+// The z modes of the free-electron start: eigenvectors c of (D/2) c = w S c,
+// S-normalized (c = L^{-T} y with S = L L^T), ascending in w.  They do not
+// depend on k, so they are computed once per handle.
+static void zmodes(mb_handle *h) {
+    if (!h->zmode_w.empty()) return;
     const int nb = h->nb, K = h->order, W = 2 * K - 1;
-    const KPoint &kp = h->kp[ik];
-    // dense L^{-1} (D/2) L^{-T} with S = L L^T
     std::vector<double> L((size_t)nb * nb, 0.0), D((size_t)nb * nb, 0.0);
     for (int j = 0; j < nb; ++j)
         for (int d = 0; d < K && j - d >= 0; ++d) L[(size_t)j * nb + (j - d)] = h->Lb[(size_t)j * K + d];
@@ -980,20 +982,34 @@ void free_electron_start(const mb_handle *h, int ik, int M, std::vector<double2>
     std::vector<int> ord(nb);
     for (int i = 0; i < nb; ++i) ord[i] = i;
     std::sort(ord.begin(), ord.end(), [&](int a, int b) { return w[a] < w[b]; });
-    // candidate (energy, g, mode)
-    std::vector<std::tuple<double, int, int>> cand;
-    int nmode = std::min(nb, M);
-    for (int g = 0; g < kp.ng; ++g)
-        for (int n = 0; n < nmode; ++n) cand.emplace_back(0.5 * kp.q2[g] + w[ord[n]], g, n);
-    std::sort(cand.begin(), cand.end());
-    X.assign((size_t)M * nb * kp.ldg, make_double2(0.0, 0.0));
-    for (int c = 0; c < M; ++c) {
-        int g = std::get<1>(cand[c]), n = ord[std::get<2>(cand[c])];
+    h->zmode_w.resize(nb);
+    h->zmode_c.assign((size_t)nb * nb, 0.0);   // [mode][j]
+    for (int n = 0; n < nb; ++n) {
+        h->zmode_w[n] = w[ord[n]];
         for (int j = 0; j < nb; ++j) {   // c_z = L^{-T} y
             double s = 0;
-            for (int q = j; q < nb; ++q) s += Li[(size_t)q * nb + j] * V[(size_t)q * nb + n];
-            X[((size_t)c * nb + j) * kp.ldg + g] = make_double2(s, 0.0);
+            for (int q = j; q < nb; ++q) s += Li[(size_t)q * nb + j] * V[(size_t)q * nb + ord[n]];
+            h->zmode_c[(size_t)n * nb + j] = s;
         }
+    }
+}
+
+// Lowest M free-electron states at k-point ik: plane wave G times z mode n,
+// energy |k+G|^2/2 + w_n.
+void free_electron_start(mb_handle *h, int ik, int M, std::vector<double2> &X) {
+    zmodes(h);
+    const int nb = h->nb;
+    const KPoint &kp = h->kp[ik];
+    std::vector<std::tuple<double, int, int>> cand;
+    const int nmode = std::min(nb, M);
+    cand.reserve((size_t)kp.ng * nmode);
+    for (int g = 0; g < kp.ng; ++g)
+        for (int n = 0; n < nmode; ++n) cand.emplace_back(0.5 * kp.q2[g] + h->zmode_w[n], g, n);
+    std::partial_sort(cand.begin(), cand.begin() + std::min<size_t>(M, cand.size()), cand.end());
+    X.assign((size_t)M * nb * kp.ldg, make_double2(0.0, 0.0));
+    for (int c = 0; c < M; ++c) {
+        const int g = std::get<1>(cand[c]), n = std::get<2>(cand[c]);
+        for (int j = 0; j < nb; ++j) X[((size_t)c * nb + j) * kp.ldg + g] = make_double2(h->zmode_c[(size_t)n * nb + j], 0.0);
     }
 }
 

@@ -95,6 +95,8 @@ struct mb_handle {
     std::vector<unsigned long long> rowmask;
     mb::DevTables t64, t32;
     bool pfac_ready = false;
+    // z modes of the eigensolver's free-electron start (k-independent, cached)
+    std::vector<double> zmode_w, zmode_c;
     mb::Scratch scratch;
     void *d_desc = nullptr;          // descriptor arrays for batched launches
     // second stream of the apply: the projector overlaps run there beside the
