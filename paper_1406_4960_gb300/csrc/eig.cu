@@ -44,17 +44,19 @@ struct EigK {
     int ldg, ng;
 };
 
-// vector index sets: i < c1 -> s1 + ch*cs1 + i;  else s2 + ch*cs2 + (i - c1)
+// vector index sets: i < c1 -> s1 + ch*cs1 + i*st1;  else s2 + ch*cs2 + (i - c1)*st2
+// (st = 1: a contiguous run; st = nc: one slot of every chain, the layout of
+// the FP32 Krylov chains, whose slot i of all chains is contiguous)
 struct VSet {
-    int s1, c1, cs1, s2, c2, cs2;
+    int s1, c1, cs1, s2, c2, cs2, st1, st2;
     __host__ __device__ int count() const { return c1 + c2; }
     __host__ __device__ int at(int i, int ch) const {
-        return i < c1 ? s1 + ch * cs1 + i : s2 + ch * cs2 + (i - c1);
+        return i < c1 ? s1 + ch * cs1 + i * st1 : s2 + ch * cs2 + (i - c1) * st2;
     }
 };
-static VSet vs(int s1, int c1, int cs1 = 0, int s2 = 0, int c2 = 0, int cs2 = 0) {
+static VSet vs(int s1, int c1, int cs1 = 0, int s2 = 0, int c2 = 0, int cs2 = 0, int st1 = 1, int st2 = 1) {
     VSet v;
-    v.s1 = s1; v.c1 = c1; v.cs1 = cs1; v.s2 = s2; v.c2 = c2; v.cs2 = cs2;
+    v.s1 = s1; v.c1 = c1; v.cs1 = cs1; v.s2 = s2; v.c2 = c2; v.cs2 = cs2; v.st1 = st1; v.st2 = st2;
     return v;
 }
 
@@ -82,7 +84,7 @@ __global__ void gram_reduce_kernel(const double2 *part, int nsplit, int ma, int 
 __global__ void copy_kernel(const EigK *ks, int nch, VSet S, VSet D, int mode) {
     // grid: (blocks along the vector, vector of the set, problem)
     // mode 0: base -> base; 1: base -> stage (to float); 2: stage -> base (to double);
-    // 3: base -> v32 (to float); 4: v32 -> base (to double); 5: stage -> v32
+    // 3: base -> v32 (to float); 4: v32 -> base (to double); 5: stage -> v32; 6: v32 -> v32
     const int prob = blockIdx.z, i = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
@@ -96,7 +98,8 @@ __global__ void copy_kernel(const EigK *ks, int nch, VSet S, VSet D, int mode) {
         else if (mode == 2) d.base[di] = make_double2((double)d.stage[si].x, (double)d.stage[si].y);
         else if (mode == 3) d.v32[di] = make_float2((float)d.base[si].x, (float)d.base[si].y);
         else if (mode == 4) d.base[di] = make_double2((double)d.v32[si].x, (double)d.v32[si].y);
-        else d.v32[di] = d.stage[si];
+        else if (mode == 5) d.v32[di] = d.stage[si];
+        else d.v32[di] = d.v32[si];
     }
 }
 
@@ -120,6 +123,42 @@ __global__ void krylov_residual_kernel(const EigK *ks, int nch, const int *srcH,
     }
 }
 
+// Bulk cycles of the mixed solver, on the FP32 copies (v32):
+// W_ch = HX_seed - theta SX_seed (slot 0) or HK_{slot-1} - theta SK_{slot-1}
+// of chain ch, the chains' slot s of chain ch at base + s*nc + ch
+__global__ void krylov_residual32_kernel(const EigK *ks, int nch, int slot, const int *seed, const double *theta,
+                                         int oHX, int oSX, int oHK, int oSK, int nc, int dst) {
+    const int prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const float th = (float)theta[prob];
+    const int ih = slot == 0 ? oHX + seed[prob] : oHK + (slot - 1) * nc + ch;
+    const int is = slot == 0 ? oSX + seed[prob] : oSK + (slot - 1) * nc + ch;
+    const float2 *h = d.v32 + (long long)ih * d.nvec;
+    const float2 *s = d.v32 + (long long)is * d.nvec;
+    float2 *w = d.v32 + (long long)(dst + ch) * d.nvec;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.nvec;
+         t += (long long)gridDim.x * blockDim.x) {
+        const float2 hv = h[t], sv = s[t];
+        w[t] = make_float2(fmaf(-th, sv.x, hv.x), fmaf(-th, sv.y, hv.y));
+    }
+}
+
+// R_i = HX_i - eps_i SX_i on the FP32 copies
+__global__ void residual32_kernel(const EigK *ks, int M, int oHX, int oSX, int dst, const double *eps) {
+    const int k = blockIdx.y;
+    const EigK d = ks[k];
+    const long long total = (long long)M * d.nvec;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / d.nvec);
+        const long long t = e - (long long)i * d.nvec;
+        const float ev = (float)eps[k * M + i];
+        const float2 hv = d.v32[(long long)(oHX + i) * d.nvec + t], sv = d.v32[(long long)(oSX + i) * d.nvec + t];
+        d.v32[(long long)(dst + i) * d.nvec + t] = make_float2(fmaf(-ev, sv.x, hv.x), fmaf(-ev, sv.y, hv.y));
+    }
+}
+
 // R_i = HX_i - eps_i SX_i into dst
 __global__ void residual_kernel(const EigK *ks, int M, int oX, int oHX, int oSX, int dst, const double *eps) {
     const int k = blockIdx.y;
@@ -137,14 +176,20 @@ __global__ void residual_kernel(const EigK *ks, int M, int oX, int oHX, int oSX,
 }
 
 // out[prob*m + i] = Re <A_i, B_i>   (block reduction with warp shuffles)
+// F32: on the FP32 copies, per-thread sums in FP32 and the rest in FP64
+template <bool F32>
 __global__ void coldot_kernel(const EigK *ks, int nch, VSet A, VSet B, double *out) {
+    typedef typename std::conditional<F32, float2, double2>::type T2;
+    typedef typename std::conditional<F32, float, double>::type T;
     const int i = blockIdx.x, prob = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
-    const double2 *a = d.base + (long long)A.at(i, ch) * d.nvec;
-    const double2 *b = d.base + (long long)B.at(i, ch) * d.nvec;
-    double s = 0.0;
-    for (long long t = threadIdx.x; t < d.nvec; t += blockDim.x) s = fma(a[t].x, b[t].x, fma(a[t].y, b[t].y, s));
+    const T2 *vb = F32 ? reinterpret_cast<const T2 *>(d.v32) : reinterpret_cast<const T2 *>(d.base);
+    const T2 *a = vb + (long long)A.at(i, ch) * d.nvec;
+    const T2 *b = vb + (long long)B.at(i, ch) * d.nvec;
+    T st = T(0);
+    for (long long t = threadIdx.x; t < d.nvec; t += blockDim.x) st = fma(a[t].x, b[t].x, fma(a[t].y, b[t].y, st));
+    double s = (double)st;
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     __shared__ double ws[32];
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
@@ -159,7 +204,7 @@ __global__ void coldot_kernel(const EigK *ks, int nch, VSet A, VSet B, double *o
 // new Krylov vector: K = W / ||W||_S, SK = SW / ||W||_S, HK slot cleared;
 // a norm below the breakdown threshold marks the slot dead (zero vector).
 __global__ void normalize_kernel(const EigK *ks, int nch, int oW, int oSW, int kV, int kS, int cs,
-                                 int slot, const double *nrm2, int *alive, int kd, int k32, int sk32) {
+                                 int slot, const double *nrm2, int *alive, int kd, int k32, int sk32, int nc) {
     const int prob = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
@@ -172,8 +217,8 @@ __global__ void normalize_kernel(const EigK *ks, int nch, int oW, int oSW, int k
     double2 *kv = d.base + (long long)(kV + ch * cs + slot) * d.nvec;
     double2 *ksv = d.base + (long long)(kS + ch * cs + slot) * d.nvec;
     // FP32 copies for later Gram-Schmidt steps (k32 < 0: none)
-    float2 *kv32 = k32 >= 0 ? d.v32 + (long long)(k32 + ch * kd + slot) * d.nvec : nullptr;
-    float2 *ks32 = k32 >= 0 ? d.v32 + (long long)(sk32 + ch * kd + slot) * d.nvec : nullptr;
+    float2 *kv32 = k32 >= 0 ? d.v32 + (long long)(k32 + slot * nc + ch) * d.nvec : nullptr;
+    float2 *ks32 = k32 >= 0 ? d.v32 + (long long)(sk32 + slot * nc + ch) * d.nvec : nullptr;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.nvec;
          t += (long long)gridDim.x * blockDim.x) {
         const double2 a = rscale(inv, w[t]), b = rscale(inv, sw[t]);
@@ -183,6 +228,28 @@ __global__ void normalize_kernel(const EigK *ks, int nch, int oW, int oSW, int k
             kv32[t] = make_float2((float)a.x, (float)a.y);
             ks32[t] = make_float2((float)b.x, (float)b.y);
         }
+    }
+}
+
+// FP32 chain slot (bulk cycles): K[slot] = W / ||W||_S and SK[slot] (which
+// holds S W) scaled in place; slot s of chain ch at base + s*nc + ch
+__global__ void normalize32_kernel(const EigK *ks, int nch, int oW, int oK, int oSK, int nc, int slot,
+                                   const double *nrm2, int *alive, int kd) {
+    const int prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const double n2 = nrm2[prob];
+    const bool ok = n2 > 1e-24;
+    const float inv = ok ? (float)(1.0 / sqrt(n2)) : 0.f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) alive[prob * kd + slot] = ok ? 1 : 0;
+    const float2 *w = d.v32 + (long long)(oW + ch) * d.nvec;
+    float2 *kv = d.v32 + (long long)(oK + slot * nc + ch) * d.nvec;
+    float2 *sk = d.v32 + (long long)(oSK + slot * nc + ch) * d.nvec;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.nvec;
+         t += (long long)gridDim.x * blockDim.x) {
+        const float2 a = w[t], b = sk[t];
+        kv[t] = make_float2(inv * a.x, inv * a.y);
+        sk[t] = make_float2(inv * b.x, inv * b.y);
     }
 }
 
@@ -512,16 +579,21 @@ __global__ void take_evals_kernel(const double *evals, int M, int nk, double *ep
 
 // banded S and banded solves on vector ranges of every k-point (FP64)
 // S apply: one thread per (vector, j, G).
-template <int K>
-__global__ void eig_banded_S_kernel(const EigK *ks, const double *Sband, int nb, int src, int dst, int nv) {
+// F32: on the FP32 copies with the FP32 band (the bulk cycles).
+template <int K, bool F32>
+__global__ void eig_banded_S_kernel(const EigK *ks, const void *Sbv, int nb, int src, int dst, int nv) {
+    typedef typename std::conditional<F32, float2, double2>::type T2;
+    typedef typename std::conditional<F32, float, double>::type T;
     const int k = blockIdx.z / nv, v = blockIdx.z % nv, j = blockIdx.y;
     const EigK d = ks[k];
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= d.ldg) return;
     constexpr int W = 2 * K - 1;
-    const double2 *x = d.base + (long long)(src + v) * d.nvec;
-    double2 *y = d.base + (long long)(dst + v) * d.nvec;
-    double2 s = make_double2(0.0, 0.0);
+    const T *Sband = reinterpret_cast<const T *>(Sbv);
+    T2 *vb = F32 ? reinterpret_cast<T2 *>(d.v32) : reinterpret_cast<T2 *>(d.base);
+    const T2 *x = vb + (long long)(src + v) * d.nvec;
+    T2 *y = vb + (long long)(dst + v) * d.nvec;
+    T2 s = czero<T2>();
     if (g < d.ng) {
 #pragma unroll
         for (int dd = 0; dd < W; ++dd) {
@@ -1025,7 +1097,10 @@ struct Solver {
     // of their basis (a pencil), so that their result does not depend on how
     // orthogonal the Krylov vectors came out
     bool gs32 = false;
-    int o32X = 0, o32SX = 0, o32HX = 0, o32W = 0, o32K = 0, o32SK = 0, o32HK = 0, o32T = 0, n32 = 0;
+    // bulk cycles (lowp()): X, HX and SX live only in the FP32 copies, and
+    // the chains' slot s of chain ch is at o32K + s*nc + ch (likewise SK, HK),
+    // so that one slot of every chain is a contiguous block for the applies
+    int o32X = 0, o32SX = 0, o32HX = 0, o32W = 0, o32K = 0, o32SK = 0, o32HK = 0, o32T = 0, o32T2 = 0, n32 = 0;
     double2 *d_Sg = nullptr, *d_Ub = nullptr, *d_Tb = nullptr;
     int *d_statb = nullptr;
     int oV, oHV, oSV, oVB, oHVB, oSVB, oQ, oHQ, oW, oSW, oT;
@@ -1138,14 +1213,40 @@ struct Solver {
         const unsigned bx = (unsigned)std::min<long long>(64, (nmax + 255) / 256);
         MB_LAUNCH_E(KN_VEC, copy_kernel<<<dim3(bx, S.count(), nk * nch), 256, 0, s>>>(d_k, nch, S, D, mode));
     }
-    void bandS(int src, int dst, int nv) {
+    void bandS(int src, int dst, int nv, bool f32 = false) {
         const dim3 grid((maxldg + 127) / 128, h->nb, nk * nv);
-        const double *Sb = (const double *)h->t64.Sband;
+        const void *Sb = f32 ? h->t32.Sband : h->t64.Sband;
         switch (h->order) {
-#define MB_BS(KK) case KK: MB_LAUNCH_E(KN_BANDED, eig_banded_S_kernel<KK><<<grid, 128, 0, s>>>(d_k, Sb, h->nb, src, dst, nv)); break;
+#define MB_BS(KK)                                                                                                 \
+    case KK:                                                                                                      \
+        if (f32)                                                                                                  \
+            MB_LAUNCH_E(KN_BANDED, (eig_banded_S_kernel<KK, true><<<grid, 128, 0, s>>>(d_k, Sb, h->nb, src, dst, nv))); \
+        else                                                                                                      \
+            MB_LAUNCH_E(KN_BANDED, (eig_banded_S_kernel<KK, false><<<grid, 128, 0, s>>>(d_k, Sb, h->nb, src, dst, nv))); \
+        break;
             MB_BS(3) MB_BS(4) MB_BS(5) MB_BS(6) MB_BS(7) MB_BS(8)
 #undef MB_BS
         }
+    }
+    void coldot(int nch, VSet A, VSet B, double *out, bool f32 = false) {
+        const dim3 grid(A.count(), nk * nch);
+        if (f32) MB_LAUNCH_E(KN_SMALL, coldot_kernel<true><<<grid, 256, 0, s>>>(d_k, nch, A, B, out));
+        else MB_LAUNCH_E(KN_SMALL, coldot_kernel<false><<<grid, 256, 0, s>>>(d_k, nch, A, B, out));
+    }
+    // Y = H X on the FP32 copies (bulk cycles): nv vectors from src32 to dst32
+    void apply32(int src32, int dst32, int nv) {
+        if (rc) return;
+        std::vector<int> iks(nk);
+        std::vector<const void *> xs(nk);
+        std::vector<void *> ys(nk);
+        for (int k = 0; k < nk; ++k) {
+            iks[k] = k;
+            xs[k] = kd_host[k].v32 + (long long)src32 * kd_host[k].nvec;
+            ys[k] = kd_host[k].v32 + (long long)dst32 * kd_host[k].nvec;
+        }
+        int r = apply_H_batch(h, nk, iks.data(), xs.data(), ys.data(), nv, prec, s);
+        if (r && rc == MB_OK) rc = r;
+        applies += nv * nk;
     }
     void bandSolve(int per_g, int src, int dst, int nv, bool f32 = false) {
         const dim3 grid((maxldg + 63) / 64, 1, nk * nv);
@@ -1186,9 +1287,15 @@ struct Solver {
         applies += nv * nk;
     }
     void residuals_and_seeds(int nch) {
-        MB_LAUNCH_E(KN_VEC, residual_kernel<<<dim3(256, nk), 256, 0, s>>>(d_k, M, oV, oHV, oSV, oT, d_eps));
-        bandSolve(0, oT, oT + M, M);
-        MB_LAUNCH_E(KN_SMALL, coldot_kernel<<<dim3(M, nk), 256, 0, s>>>(d_k, 1, vs(oT, M), vs(oT + M, M), d_dots));
+        if (lowp()) {
+            MB_LAUNCH_E(KN_VEC, residual32_kernel<<<dim3(256, nk), 256, 0, s>>>(d_k, M, o32HX, o32SX, o32T, d_eps));
+            bandSolve(0, o32T, o32T2, M, true);
+            coldot(1, vs(o32T, M), vs(o32T2, M), d_dots, true);
+        } else {
+            MB_LAUNCH_E(KN_VEC, residual_kernel<<<dim3(256, nk), 256, 0, s>>>(d_k, M, oV, oHV, oSV, oT, d_eps));
+            bandSolve(0, oT, oT + M, M);
+            coldot(1, vs(oT, M), vs(oT + M, M), d_dots);
+        }
         int np = nk * nch;
         MB_LAUNCH_E(KN_SMALL, seed_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_dots, M, Mconv, nk, nch, b, d_res, d_eps, d_seed,
                                                                         d_theta, d_srcH, d_srcS, oHV, oSV));
@@ -1216,39 +1323,59 @@ struct Solver {
         int r = apply_H_batch(h, nk, iks.data(), xs.data(), ys.data(), nch, prec, s);
         if (r && rc == MB_OK) rc = r;
         copy(nch, vs(nc_stage(), 1, 1), vs(kH + slot, 1, cs), 2);
-        if (lowp()) copy(nch, vs(nc_stage(), 1, 1), vs(o32HK + slot, 1, kd), 5);
         applies += nch * nk;
+    }
+    // classical Gram-Schmidt, twice, in the S inner product, of the chain
+    // inputs W (one per chain) on the FP32 copies: all coefficients of a pass
+    // come from the same (pre-update) vector.  The roots X are common to
+    // every chain of a k-point, so their part is one product with a column
+    // per chain.
+    void gs32_passes(int nch, int i) {
+        for (int pass = 0; pass < 2; ++pass) {
+            gram(1, vs(o32SX, M), vs(o32W, nch), d_G2, true);                              // SX^H [W_0 .. W_nch-1]
+            if (i > 0) gram(nch, vs(o32SK, i, 1, 0, 0, 0, nc), vs(o32W, 1, 1), d_G, true);  // SK_ch^H W_ch
+            combine(1, vs(o32X, M), vs(o32W, nch), d_G2, -1.0, 1.0, true);
+            if (i > 0) combine(nch, vs(o32K, i, 1, 0, 0, 0, nc), vs(o32W, 1, 1), d_G, -1.0, 1.0, true);
+        }
     }
     void krylov(int nch, int kV, int kS, int kH, int cs) {
         int np = nk * nch;
         MB_LAUNCH_E(KN_SMALL, fill_int_kernel<<<(np * kd + 127) / 128, 128, 0, s>>>(d_alive, np * kd, 1));
+        const unsigned rbx = (unsigned)std::min<long long>(1024, (nmax + 255) / 256);
+        if (lowp()) {
+            // bulk cycles: every step on the FP32 copies; the applies read
+            // and write the chain slots in place
+            for (int i = 0; i < kd && !rc; ++i) {
+                if (i > 0) apply32(o32K + (i - 1) * nc, o32HK + (i - 1) * nc, nch);
+                MB_LAUNCH_E(KN_VEC, krylov_residual32_kernel<<<dim3(rbx, np), 256, 0, s>>>(
+                                        d_k, nch, i, d_seed, d_theta, o32HX, o32SX, o32HK, o32SK, nc, o32W));
+                bandSolve(1, o32W, o32W, nch, true);
+                gs32_passes(nch, i);
+                bandS(o32W, o32SK + i * nc, nch, true);
+                coldot(nch, vs(o32W, 1, 1), vs(o32SK + i * nc, 1, 1), d_dots, true);
+                MB_LAUNCH_E(KN_VEC, normalize32_kernel<<<dim3(128, np), 256, 0, s>>>(d_k, nch, o32W, o32K, o32SK, nc, i,
+                                                                                     d_dots, d_alive, kd));
+            }
+            apply32(o32K + (kd - 1) * nc, o32HK + (kd - 1) * nc, nch);
+            return;
+        }
         if (gs32) {
             copy(1, vs(oV, M), vs(o32X, M), 3);
             copy(1, vs(oSV, M), vs(o32SX, M), 3);
-            if (lowp()) copy(1, vs(oHV, M), vs(o32HX, M), 3);
         }
         for (int i = 0; i < kd && !rc; ++i) {
             if (i > 0) {
                 applyH_chain(nch, i - 1, kV, kH, cs);
                 MB_LAUNCH_E(KN_SMALL, set_src_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_srcH, d_srcS, np, nch, kH, kS, cs, i - 1));
             }
-            MB_LAUNCH_E(KN_VEC, krylov_residual_kernel<<<dim3((unsigned)std::min<long long>(1024, (nmax + 255) / 256), np), 256, 0, s>>>(
+            MB_LAUNCH_E(KN_VEC, krylov_residual_kernel<<<dim3(rbx, np), 256, 0, s>>>(
                                     d_k, nch, d_srcH, d_srcS, d_theta, gs32 ? o32W : oW, gs32 ? 1 : 0));
-            if (!gs32) bandSolve(1, oW, oW, nch);
-            // classical Gram-Schmidt, twice, in the S inner product: all
-            // coefficients of a pass come from the same (pre-update) vector.
-            // The roots X are common to every chain of a k-point, so their
-            // part is one product with a column per chain.
             if (gs32) {
                 bandSolve(1, o32W, o32W, nch, true);
-                for (int pass = 0; pass < 2; ++pass) {
-                    gram(1, vs(o32SX, M), vs(o32W, nch), d_G2, true);
-                    if (i > 0) gram(nch, vs(o32SK, i, kd), vs(o32W, 1, 1), d_G, true);
-                    combine(1, vs(o32X, M), vs(o32W, nch), d_G2, -1.0, 1.0, true);
-                    if (i > 0) combine(nch, vs(o32K, i, kd), vs(o32W, 1, 1), d_G, -1.0, 1.0, true);
-                }
+                gs32_passes(nch, i);
                 copy(nch, vs(o32W, 1, 1), vs(oW, 1, 1), 4);
             } else {
+                bandSolve(1, oW, oW, nch);
                 for (int pass = 0; pass < 2; ++pass) {
                     gram(1, vs(oSV, M), vs(oW, nch), d_G2);                    // SX^H [W_0 .. W_nch-1]
                     if (i > 0) gram(nch, vs(kS, i, cs), vs(oW, 1, 1), d_G);     // SK_ch^H W_ch
@@ -1257,11 +1384,11 @@ struct Solver {
                 }
             }
             bandS(oW, oSW, nch);
-            MB_LAUNCH_E(KN_SMALL, coldot_kernel<<<dim3(1, np), 256, 0, s>>>(d_k, nch, vs(oW, 1, 1), vs(oSW, 1, 1), d_dots));
-            const bool need32 = gs32 && (i + 1 < kd || lowp());
+            coldot(nch, vs(oW, 1, 1), vs(oSW, 1, 1), d_dots);
+            const bool need32 = gs32 && i + 1 < kd;
             MB_LAUNCH_E(KN_VEC, normalize_kernel<<<dim3(128, np), 256, 0, s>>>(d_k, nch, oW, oSW, kV, kS, cs, i,
                                                                                d_dots, d_alive, kd,
-                                                                               need32 ? o32K : -1, o32SK));
+                                                                               need32 ? o32K : -1, o32SK, nc));
         }
         applyH_chain(nch, kd - 1, kV, kH, cs);
     }
@@ -1315,23 +1442,21 @@ struct Solver {
         return d_Tb;
     }
     // X, HX <- [V|..](m) Y[:, :M] and SX = S X (S is banded: recomputing it is
-    // cheaper than rotating it)
-    // fresh_hx: HX from a new apply in the solve's precision instead of the
-    // rotation of [HX|HK] (cheaper than the FP64 rotation when the applies are
-    // FP32, and no less accurate than HK from FP32 applies)
-    // V32: in the bulk cycles, the FP32 copies of the rotated vectors (the
-    // rotation then runs in FP32 and X keeps FP32 accuracy until the finish)
-    void rotate_set(const double2 *Y, int m, bool fresh_hx = false, const VSet *V32 = nullptr) {
-        if (V32) {
+    // cheaper than rotating it).  Bulk cycles (lowp): the rotation of the
+    // FP32 copies V32 in FP32, and HX from a fresh FP32 apply instead of a
+    // rotation (cheaper, and no less accurate than HK from FP32 applies).
+    void rotate_set(const double2 *Y, int m, const VSet *V32 = nullptr) {
+        if (lowp()) {
             combine(1, *V32, vs(o32T, M), Y, 1.0, 0.0, true);
-            copy(1, vs(o32T, M), vs(oV, M), 4);
-        } else {
-            combine(1, vs(oV, m), vs(oT, M), Y, 1.0, 0.0);
+            copy(1, vs(o32T, M), vs(o32X, M), 6);
+            apply32(o32X, o32HX, M);
+            bandS(o32X, o32SX, M, true);
+            return;
         }
-        if (!fresh_hx) combine(1, vs(oHV, m), vs(oT + M, M), Y, 1.0, 0.0);
-        if (!V32) copy(1, vs(oT, M), vs(oV, M), 0);
-        if (fresh_hx) applyH(oV, oHV, M, prec);
-        else copy(1, vs(oT + M, M), vs(oHV, M), 0);
+        combine(1, vs(oV, m), vs(oT, M), Y, 1.0, 0.0);
+        combine(1, vs(oHV, m), vs(oT + M, M), Y, 1.0, 0.0);
+        copy(1, vs(oT, M), vs(oV, M), 0);
+        copy(1, vs(oT + M, M), vs(oHV, M), 0);
         bandS(oV, oSV, M);
     }
     // Rayleigh-Ritz on [X | K_A] (withK) or on X.  With K_A, X holds the Ritz
@@ -1341,8 +1466,8 @@ struct Solver {
         int m = withK ? mA : M;
         if (withK && lowp()) {
             // bulk cycles: the Krylov rows from the FP32 copies
-            gram(1, vs(o32K, kd), vs(o32HX, M, 0, o32HK, kd, 0), d_G2, true);
-            gram(1, vs(o32K, kd), vs(o32SX, M, 0, o32SK, kd, 0), d_T, true);
+            gram(1, vs(o32K, kd, 0, 0, 0, 0, nc), vs(o32HX, M, 0, o32HK, kd, 0, 1, nc), d_G2, true);
+            gram(1, vs(o32K, kd, 0, 0, 0, 0, nc), vs(o32SX, M, 0, o32SK, kd, 0, 1, nc), d_T, true);
         } else if (withK) {
             gram(1, vs(oV + M, kd), vs(oHV, m), d_G2);
             if (gs32) gram(1, vs(oV + M, kd), vs(oSV, m), d_T);
@@ -1351,8 +1476,8 @@ struct Solver {
             MB_LAUNCH_E(KN_SMALL, assemble_rr_kernel<<<dim3((m * m + 127) / 128, nk), 128, 0, s>>>(
                                       d_G2, gs32 ? d_T : nullptr, d_eps, M, m, d_G, gs32 ? d_Sg : nullptr));
             if (gs32) {
-                const VSet v32 = vs(o32X, M, 0, o32K, kd, 0);
-                rotate_set(pencil_solve(1, m, M), m, lowp(), lowp() ? &v32 : nullptr);
+                const VSet v32 = vs(o32X, M, 0, o32K, kd, 0, 1, nc);
+                rotate_set(pencil_solve(1, m, M), m, &v32);
             } else {
                 jacobi(1, m, true, M);
                 rotate_set(d_Y, m);
@@ -1369,9 +1494,6 @@ struct Solver {
     void orth_rr() {
         const bool f32 = lowp();
         if (f32) {
-            copy(1, vs(oV, M), vs(o32X, M), 3);
-            copy(1, vs(oSV, M), vs(o32SX, M), 3);
-            copy(1, vs(oHV, M), vs(o32HX, M), 3);
             gram(1, vs(o32X, M), vs(o32SX, M), d_G, true, true);
         } else {
             gram(1, vs(oV, M), vs(oSV, M), d_G, false, true);
@@ -1386,19 +1508,23 @@ struct Solver {
         jacobi(1, M, false, M, lowp());
         small_gemm(d_U, d_Y, d_T, M, 0);      // U Y
         const VSet x32 = vs(o32X, M);
-        rotate_set(d_T, M, lowp(), f32 ? &x32 : nullptr);
+        rotate_set(d_T, M, &x32);
         MB_LAUNCH_E(KN_SMALL, take_evals_kernel<<<(M * nk + 127) / 128, 128, 0, s>>>(d_evals, M, nk, d_eps));
     }
     void cycle_B() {
         residuals_and_seeds(nblk);
-        copy(nblk, vs(oV, b, b), vs(oVB, b, mB), 0);
-        copy(nblk, vs(oHV, b, b), vs(oHVB, b, mB), 0);
-        if (gs32) copy(nblk, vs(oSV, b, b), vs(oSVB, b, mB), 0);
+        if (!lowp()) {
+            copy(nblk, vs(oV, b, b), vs(oVB, b, mB), 0);
+            copy(nblk, vs(oHV, b, b), vs(oHVB, b, mB), 0);
+            if (gs32) copy(nblk, vs(oSV, b, b), vs(oSVB, b, mB), 0);
+        }
         krylov(nblk, oVB + b, oSVB + b, oHVB + b, mB);
         const double2 *Yc = d_Y;
+        // block ch: [X_b | K_ch] (in the bulk cycles from the FP32 copies)
+        const VSet x32 = vs(o32X, b, b, o32K, kd, 1, 1, nc);
+        const VSet hx32 = vs(o32HX, b, b, o32HK, kd, 1, 1, nc);
         if (lowp()) {
-            Yc = rr_pencil(nblk, vs(o32X, b, b, o32K, kd, kd), vs(o32HX, b, b, o32HK, kd, kd),
-                           vs(o32SX, b, b, o32SK, kd, kd), mB, b, true);
+            Yc = rr_pencil(nblk, x32, hx32, vs(o32SX, b, b, o32SK, kd, 1, 1, nc), mB, b, true);
         } else if (gs32) {
             Yc = rr_pencil(nblk, vs(oVB, mB, mB), vs(oHVB, mB, mB), vs(oSVB, mB, mB), mB, b);
         } else {
@@ -1407,9 +1533,19 @@ struct Solver {
         }
         int np = nk * nblk;
         MB_LAUNCH_E(KN_SMALL, select_kernel<<<(np + 31) / 32, 32, 0, s>>>(d_evals, Yc, mB, b, M, nblk, np, d_eps, d_Ysel));
-        combine(nblk, vs(oVB, mB, mB), vs(oV, b, b), d_Ysel, 1.0, 0.0);
-        combine(nblk, vs(oHVB, mB, mB), vs(oHV, b, b), d_Ysel, 1.0, 0.0);
-        bandS(oV, oSV, M);
+        if (lowp()) {
+            // the new X and HX of every block land in scratch (nblk*b vectors
+            // each) first: the rotation reads the old X
+            combine(nblk, x32, vs(o32T, b, b), d_Ysel, 1.0, 0.0, true);
+            combine(nblk, hx32, vs(o32T2, b, b), d_Ysel, 1.0, 0.0, true);
+            copy(1, vs(o32T, M), vs(o32X, M), 6);
+            copy(1, vs(o32T2, M), vs(o32HX, M), 6);
+            bandS(o32X, o32SX, M, true);
+        } else {
+            combine(nblk, vs(oVB, mB, mB), vs(oV, b, b), d_Ysel, 1.0, 0.0);
+            combine(nblk, vs(oHVB, mB, mB), vs(oHV, b, b), d_Ysel, 1.0, 0.0);
+            bandS(oV, oSV, M);
+        }
     }
 };
 
@@ -1498,7 +1634,8 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     S.o32SK = S.o32K + S.nc * S.kd;
     S.o32HK = S.o32SK + S.nc * S.kd;
     S.o32T = S.o32HK + S.nc * S.kd;
-    S.n32 = S.o32T + S.M;
+    S.o32T2 = S.o32T + std::max(S.M, S.nblk * S.b);
+    S.n32 = S.o32T2 + std::max(S.M, S.nblk * S.b);
     // per-k memory
     S.kd_host.resize(S.nk);
     size_t pofs = 0;
@@ -1571,9 +1708,18 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
             if (r2) return r2;
         }
     }
-    S.applyH(S.oV, S.oHV, S.M, S.prec);
-    S.bandS(S.oV, S.oSV, S.M);
-    S.rr_full(false);
+    if (S.lowp()) {
+        // mixed precision: the bulk cycles start from FP32 copies of the
+        // (S-orthonormal) free-electron roots
+        S.copy(1, vs(S.oV, S.M), vs(S.o32X, S.M), 3);
+        S.apply32(S.o32X, S.o32HX, S.M);
+        S.bandS(S.o32X, S.o32SX, S.M, true);
+        S.orth_rr();
+    } else {
+        S.applyH(S.oV, S.oHV, S.M, S.prec);
+        S.bandS(S.oV, S.oSV, S.M);
+        S.rr_full(false);
+    }
     S.residuals_and_seeds(1);
     std::vector<double> res((size_t)S.nk * S.M);
     double last = 1e300, prev = 1e300, maxres = 1e300, bulk_best = 1e300;
@@ -1659,6 +1805,7 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
             if (maxres < 30.0 * tol || stalled) {
                 // finish phase: the roots get FP64 HX from here on
                 S.fp64_roots = true;
+                S.copy(1, vs(S.o32X, S.M), vs(S.oV, S.M), 4);
                 S.applyH(S.oV, S.oHV, S.M, MB_FP64);
                 S.bandS(S.oV, S.oSV, S.M);
                 S.orth_rr();
@@ -1678,6 +1825,7 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     for (auto &g : gexec)
         if (g) cudaGraphExecDestroy(g);
     if (S.rc) return S.rc;
+    if (S.lowp()) S.copy(1, vs(S.o32X, S.M), vs(S.oV, S.M), 4);   // stopped in the bulk phase
     std::vector<double> eps((size_t)S.nk * S.M);
     S.cuda(cudaMemcpyAsync(eps.data(), S.d_eps, sizeof(double) * eps.size(), cudaMemcpyDeviceToHost, s));
     if (evecs) {
