@@ -348,13 +348,16 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
     __syncthreads();
     const int mp = (m + 1) & ~1;      // players, padded to even
     const int npair = mp / 2;
+    const int nblk2 = npair * (npair + 1) / 2;   // 2x2 blocks (I >= J) of the pair partition
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int r = 0; r < mp - 1; ++r) {
+            // rotation of every pair of the round (q >= m: an index left
+            // alone this round, identity)
             for (int pi = threadIdx.x; pi < npair; pi += blockDim.x) {
                 int a = pi == 0 ? 0 : ((r + pi - 1) % (mp - 1)) + 1;
                 int b = ((r + mp - 1 - pi - 1) % (mp - 1)) + 1;
                 if (pi == 0) b = ((r + mp - 2) % (mp - 1)) + 1;
-                int p = min(a, b), q = max(a, b);
+                const int p = min(a, b), q = max(a, b);
                 T c = 1, s = 0, tm = 0;
                 T2 ep = mk(T(1), T(0));
                 if (q < m) {
@@ -372,8 +375,6 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
                         s = t * c;
                         tm = t * mag;
                     }
-                } else {
-                    p = q = -1;
                 }
                 pp[2 * pi] = p;
                 pp[2 * pi + 1] = q;
@@ -383,39 +384,72 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
                 re[pi] = ep;
             }
             __syncthreads();
-            // columns: A <- A J, V <- V J;  J = diag(1, e^-i phi) [[c, s], [-s, c]]
-            for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
-                int pi = e / m, row = e % m;
-                int p = pp[2 * pi], q = pp[2 * pi + 1];
-                if (p < 0 || rc[5 * pi + 1] == T(0)) continue;
-                T c = rc[5 * pi], s = rc[5 * pi + 1];
-                T2 ec = mk(re[pi].x, -re[pi].y);
-                T2 xp = A[row * m + p], xq = cmul(ec, A[row * m + q]);
-                A[row * m + p] = rscale(c, xp) - rscale(s, xq);
-                A[row * m + q] = rscale(s, xp) + rscale(c, xq);
-                T2 vp = vget(row, p), vq = cmul(ec, vget(row, q));
-                vset(row, p, rscale(c, vp) - rscale(s, vq));
-                vset(row, q, rscale(s, vp) + rscale(c, vq));
-            }
-            __syncthreads();
-            // rows: A <- J^H A
-            for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
-                int pi = e / m, col = e % m;
-                int p = pp[2 * pi], q = pp[2 * pi + 1];
-                if (p < 0 || rc[5 * pi + 1] == T(0)) continue;
-                T c = rc[5 * pi], s = rc[5 * pi + 1];
-                T2 yp = A[p * m + col], yq = cmul(re[pi], A[q * m + col]);
-                A[p * m + col] = rscale(c, yp) - rscale(s, yq);
-                A[q * m + col] = rscale(s, yp) + rscale(c, yq);
-            }
-            __syncthreads();
-            for (int pi = threadIdx.x; pi < npair; pi += blockDim.x) {
-                int p = pp[2 * pi], q = pp[2 * pi + 1];
-                if (p < 0 || rc[5 * pi + 1] == T(0)) continue;
-                A[p * m + q] = czero<T2>();
-                A[q * m + p] = czero<T2>();
-                A[p * m + p] = mk(rc[5 * pi + 3] - rc[5 * pi + 2], T(0));
-                A[q * m + q] = mk(rc[5 * pi + 4] + rc[5 * pi + 2], T(0));
+            // A <- J^H A J by 2x2 blocks (rows of pair I, columns of pair J,
+            // I >= J; the block above the diagonal is written as the
+            // conjugate transpose), then V <- V J by (pair, row).
+            // J = diag(1, e^-i phi) [[c, s], [-s, c]] on each pair's columns.
+            for (int e = threadIdx.x; e < nblk2 + npair * m; e += blockDim.x) {
+                if (e < nblk2) {
+                    int I = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                    while (I * (I + 1) / 2 > e) --I;
+                    while ((I + 1) * (I + 2) / 2 <= e) ++I;
+                    const int J = e - I * (I + 1) / 2;
+                    const int pI = pp[2 * I], qI = pp[2 * I + 1], pJ = pp[2 * J], qJ = pp[2 * J + 1];
+                    const bool vI = qI < m, vJ = qJ < m;
+                    const T sI = rc[5 * I + 1], sJ = rc[5 * J + 1];
+                    const bool actI = vI && sI != T(0), actJ = vJ && sJ != T(0);
+                    T2 a00 = A[pI * m + pJ];
+                    T2 a01 = vJ ? A[pI * m + qJ] : czero<T2>();
+                    T2 a10 = vI ? A[qI * m + pJ] : czero<T2>();
+                    T2 a11 = (vI && vJ) ? A[qI * m + qJ] : czero<T2>();
+                    if (I == J && actI) {
+                        a00 = mk(rc[5 * I + 3] - rc[5 * I + 2], T(0));
+                        a11 = mk(rc[5 * I + 4] + rc[5 * I + 2], T(0));
+                        a01 = a10 = czero<T2>();
+                    } else {
+                        if (actJ) {   // columns pJ, qJ
+                            const T cJ = rc[5 * J];
+                            const T2 ec = mk(re[J].x, -re[J].y);
+                            T2 x = a00, y = cmul(ec, a01);
+                            a00 = rscale(cJ, x) - rscale(sJ, y);
+                            a01 = rscale(sJ, x) + rscale(cJ, y);
+                            x = a10;
+                            y = cmul(ec, a11);
+                            a10 = rscale(cJ, x) - rscale(sJ, y);
+                            a11 = rscale(sJ, x) + rscale(cJ, y);
+                        }
+                        if (actI) {   // rows pI, qI
+                            const T cI = rc[5 * I];
+                            T2 x = a00, y = cmul(re[I], a10);
+                            a00 = rscale(cI, x) - rscale(sI, y);
+                            a10 = rscale(sI, x) + rscale(cI, y);
+                            x = a01;
+                            y = cmul(re[I], a11);
+                            a01 = rscale(cI, x) - rscale(sI, y);
+                            a11 = rscale(sI, x) + rscale(cI, y);
+                        }
+                    }
+                    A[pI * m + pJ] = a00;
+                    if (vJ) A[pI * m + qJ] = a01;
+                    if (vI) A[qI * m + pJ] = a10;
+                    if (vI && vJ) A[qI * m + qJ] = a11;
+                    if (I != J) {
+                        A[pJ * m + pI] = mk(a00.x, -a00.y);
+                        if (vJ) A[qJ * m + pI] = mk(a01.x, -a01.y);
+                        if (vI) A[pJ * m + qI] = mk(a10.x, -a10.y);
+                        if (vI && vJ) A[qJ * m + qI] = mk(a11.x, -a11.y);
+                    }
+                } else {
+                    const int e2 = e - nblk2;
+                    const int pi = e2 / m, row = e2 % m;
+                    const int p = pp[2 * pi], q = pp[2 * pi + 1];
+                    if (q >= m || rc[5 * pi + 1] == T(0)) continue;
+                    const T c = rc[5 * pi], s = rc[5 * pi + 1];
+                    const T2 ec = mk(re[pi].x, -re[pi].y);
+                    T2 vp = vget(row, p), vq = cmul(ec, vget(row, q));
+                    vset(row, p, rscale(c, vp) - rscale(s, vq));
+                    vset(row, q, rscale(s, vp) + rscale(c, vq));
+                }
             }
             __syncthreads();
         }
