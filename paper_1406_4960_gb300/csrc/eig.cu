@@ -278,74 +278,29 @@ __global__ void seed_kernel(const double *dots, int M, int mconv, int nk, int nc
 // ---------------------------------------------------------------------------
 // Jacobi diagonalization of one Hermitian m x m matrix per CTA (m <= JMAX),
 // parallel (round-robin) ordering: m'/2 disjoint rotations per round.
-// VS: the eigenvector matrix lives in shared memory beside A (m <= 84);
-// otherwise it overwrites the input matrix G in global memory (m <= JMAX).
-// T = float runs the rotations in FP32 (the mixed solver's bulk cycles;
-// eigenvectors good to ~1e-6, refined by the FP64 finish cycles).
-template <bool VS, typename T>
-__global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const int *dead, int dead_stride,
-                                                     int dead_ofs, double *evals, double2 *evecs,
-                                                     int max_sweeps, double rel_tol) {
+
+// Per-round scratch of the sweeps (shared memory, sized for T = double).
+struct JacobiScratch {
+    unsigned char *rc;   // per pair: c, s, t*|apq|, app, aqq   (5 * JPAIRS T)
+    unsigned char *re;   // per pair: phase e                     (JPAIRS T2)
+    int *pp;             // per pair: p, q
+    double *red;         // 32 partial sums
+    int *stop;
+};
+constexpr size_t kJacobiScratchBytes = 5 * JPAIRS * sizeof(double) + JPAIRS * sizeof(double2) + 2 * JPAIRS * sizeof(int);
+
+// Sweeps until the off-diagonal Frobenius norm is <= rel_tol * sqrt(fro2).
+// A (m x m, row-major) in shared memory; V is updated as V <- V J through
+// vget/vset (shared or global memory).
+template <typename T, typename VGet, typename VSet_>
+__device__ void jacobi_sweeps(typename std::conditional<std::is_same<T, float>::value, float2, double2>::type *A,
+                              int m, VGet vget, VSet_ vset, int max_sweeps, double rel_tol, double fro2,
+                              JacobiScratch js) {
     typedef typename std::conditional<std::is_same<T, float>::value, float2, double2>::type T2;
     const T skip_rel = std::is_same<T, float>::value ? T(1e-7) : T(1e-15);
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int prob = blockIdx.x;
-    T2 *A = reinterpret_cast<T2 *>(sm);
-    T2 *Vs = A + m * m;                                                  // eigenvectors in shared memory (VS)
-    double2 *Vg = G + (size_t)prob * LD * LD;                            // or in place of G
-    const int ldv = VS ? m : LD;
-    T *rc = reinterpret_cast<T *>(A + (VS ? 2 : 1) * m * m);             // per pair: c, s, t*|apq|, app, aqq
-    T2 *re = reinterpret_cast<T2 *>(rc + 5 * JPAIRS);                   // per pair: phase e
-    int *pp = reinterpret_cast<int *>(re + JPAIRS);                      // per pair: p, q
-    auto vget = [&](int r, int c) -> T2 {
-        if (VS) return Vs[r * ldv + c];
-        const double2 v = Vg[r * ldv + c];
-        return mk((T)v.x, (T)v.y);
-    };
-    auto vset = [&](int r, int c, T2 v) {
-        if (VS) Vs[r * ldv + c] = v;
-        else Vg[r * ldv + c] = make_double2((double)v.x, (double)v.y);
-    };
-    __shared__ double red[32];
-    __shared__ int stop;
-    const double2 *g = G + (size_t)prob * LD * LD;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int i = e / m, j = e % m;
-        // Hermitian completion from the lower triangle: with the subspace
-        // ordered [roots | Krylov vectors], the coupling block comes from
-        // K^H (H X), which uses the roots' HX rather than the Krylov vectors'
-        // HK (HK may come from a reduced-precision apply)
-        double2 v = i >= j ? g[i * LD + j] : g[j * LD + i];
-        if (i < j) v.y = -v.y;
-        if (i == j) v.y = 0.0;
-        bool di = dead && dead[prob * dead_stride + i] == 0 && i >= dead_ofs;
-        bool dj = dead && dead[prob * dead_stride + j] == 0 && j >= dead_ofs;
-        if (di || dj) v = make_double2((i == j) ? 1e30 : 0.0, 0.0);
-        A[e] = mk((T)v.x, (T)v.y);
-    }
-    __syncthreads();   // G is read completely before V (possibly G itself) is initialised
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int i = e / m, j = e % m;
-        vset(i, j, mk(T(i == j ? 1 : 0), T(0)));
-    }
-    __syncthreads();
-    // Frobenius norm of the live part for the stopping rule
-    double f = 0.0;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        T2 a = A[e];
-        if (fabs((double)a.x) < 1e29) f += (double)a.x * a.x + (double)a.y * a.y;
-    }
-    for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        red[0] = s;
-    }
-    __syncthreads();
-    const double fro2 = red[0];
-    __syncthreads();
+    T *rc = reinterpret_cast<T *>(js.rc);
+    T2 *re = reinterpret_cast<T2 *>(js.re);
+    int *pp = js.pp;
     const int mp = (m + 1) & ~1;      // players, padded to even
     const int npair = mp / 2;
     const int nblk2 = npair * (npair + 1) / 2;   // 2x2 blocks (I >= J) of the pair partition
@@ -460,18 +415,57 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
             if (i != j) o += (double)A[e].x * A[e].x + (double)A[e].y * A[e].y;
         }
         for (int off = 16; off > 0; off >>= 1) o += __shfl_down_sync(0xffffffffu, o, off);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = o;
+        if ((threadIdx.x & 31) == 0) js.red[threadIdx.x >> 5] = o;
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-            stop = s <= rel_tol * rel_tol * fro2;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += js.red[w];
+            *js.stop = s <= rel_tol * rel_tol * fro2;
         }
         __syncthreads();
-        if (stop) break;
+        if (*js.stop) break;
     }
-    // sort ascending (selection sort by one thread on the diagonal)
-    __shared__ int perm[LD];
+}
+
+// A (m x m) from the lower triangle of the problem's G (Hermitian
+// completion: with the subspace ordered [roots | Krylov vectors], the
+// coupling block comes from K^H (H X), which uses the roots' HX rather than
+// the Krylov vectors' HK, which may come from a reduced-precision apply);
+// dead slots become decoupled with a huge diagonal.  Returns the squared
+// Frobenius norm of the live part (all threads).
+template <typename T2>
+__device__ double jacobi_load(const double2 *g, int m, const int *dead, int dead_stride, int dead_ofs, T2 *A,
+                              double *red) {
+    const int prob = blockIdx.x;
+    double f = 0.0;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int i = e / m, j = e % m;
+        double2 v = i >= j ? g[i * LD + j] : g[j * LD + i];
+        if (i < j) v.y = -v.y;
+        if (i == j) v.y = 0.0;
+        bool di = dead && dead[prob * dead_stride + i] == 0 && i >= dead_ofs;
+        bool dj = dead && dead[prob * dead_stride + j] == 0 && j >= dead_ofs;
+        if (di || dj) v = make_double2((i == j) ? 1e30 : 0.0, 0.0);
+        else f += v.x * v.x + v.y * v.y;
+        A[e] = mk((decltype(A[0].x))v.x, (decltype(A[0].x))v.y);
+    }
+    for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        red[0] = s;
+    }
+    __syncthreads();
+    const double fro2 = red[0];
+    __syncthreads();
+    return fro2;
+}
+
+// ascending order of the diagonal (selection sort by one thread)
+template <typename T2>
+__device__ void jacobi_sort(const T2 *A, int m, int *perm) {
     if (threadIdx.x == 0) {
         for (int i = 0; i < m; ++i) perm[i] = i;
         for (int i = 0; i < m; ++i) {
@@ -482,6 +476,46 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
         }
     }
     __syncthreads();
+}
+
+// VS: the eigenvector matrix lives in shared memory beside A (m <= 84);
+// otherwise it overwrites the input matrix G in global memory (m <= JMAX).
+// T = float runs the rotations in FP32 (the mixed solver's bulk cycles).
+template <bool VS, typename T>
+__global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const int *dead, int dead_stride,
+                                                     int dead_ofs, double *evals, double2 *evecs,
+                                                     int max_sweeps, double rel_tol) {
+    typedef typename std::conditional<std::is_same<T, float>::value, float2, double2>::type T2;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int prob = blockIdx.x;
+    T2 *A = reinterpret_cast<T2 *>(sm);
+    T2 *Vs = A + m * m;                                                  // eigenvectors in shared memory (VS)
+    double2 *Vg = G + (size_t)prob * LD * LD;                            // or in place of G
+    const int ldv = VS ? m : LD;
+    unsigned char *scr = reinterpret_cast<unsigned char *>(A + (VS ? 2 : 1) * m * m);
+    __shared__ double red[32];
+    __shared__ int stop;
+    __shared__ int perm[LD];
+    JacobiScratch js{scr, scr + 5 * JPAIRS * sizeof(double), reinterpret_cast<int *>(scr + 5 * JPAIRS * sizeof(double) + JPAIRS * sizeof(double2)),
+                     red, &stop};
+    auto vget = [&](int r, int c) -> T2 {
+        if (VS) return Vs[r * ldv + c];
+        const double2 v = Vg[r * ldv + c];
+        return mk((T)v.x, (T)v.y);
+    };
+    auto vset = [&](int r, int c, T2 v) {
+        if (VS) Vs[r * ldv + c] = v;
+        else Vg[r * ldv + c] = make_double2((double)v.x, (double)v.y);
+    };
+    const double fro2 = jacobi_load(G + (size_t)prob * LD * LD, m, dead, dead_stride, dead_ofs, A, red);
+    // G is read completely (jacobi_load ends on a barrier) before V, possibly G itself, is initialised
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int i = e / m, j = e % m;
+        vset(i, j, mk(T(i == j ? 1 : 0), T(0)));
+    }
+    __syncthreads();
+    jacobi_sweeps<T>(A, m, vget, vset, max_sweeps, rel_tol, fro2, js);
+    jacobi_sort(A, m, perm);
     for (int c = threadIdx.x; c < m; c += blockDim.x) evals[(size_t)prob * LD + c] = A[perm[c] * m + perm[c]].x;
     double2 *out = evecs + (size_t)prob * LD * LD;
     if (!VS && out == Vg) {
@@ -499,6 +533,89 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
             const T2 v = vget(r, perm[c]);
             out[r * LD + c] = make_double2(v.x, v.y);
         }
+    }
+}
+
+// FP64 result from FP32 sweeps (m <= JMIX_MAX): Jacobi in FP32 gives V0;
+// B = V0^H A V0 is formed in FP64 (off-diagonal at the FP32 level), FP64
+// sweeps on B converge in one or two (quadratic convergence), and the
+// eigenvectors are V0 V1.  Same result as FP64 sweeps from the start, with
+// most rotations at the FP32 rate.
+constexpr int JMIX_MAX = 64;
+__global__ void __launch_bounds__(256) jacobi_mixed_kernel(const double2 *G, int m, const int *dead, int dead_stride,
+                                                           int dead_ofs, double *evals, double2 *evecs,
+                                                           int max_sweeps, double rel_tol) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int prob = blockIdx.x;
+    double2 *A64 = reinterpret_cast<double2 *>(sm);
+    double2 *W64 = A64 + m * m;
+    float2 *A32 = reinterpret_cast<float2 *>(W64 + m * m);
+    float2 *V32 = A32 + m * m;
+    unsigned char *scr = reinterpret_cast<unsigned char *>(V32 + m * m);
+    __shared__ double red[32];
+    __shared__ int stop;
+    __shared__ int perm[LD];
+    JacobiScratch js{scr, scr + 5 * JPAIRS * sizeof(double), reinterpret_cast<int *>(scr + 5 * JPAIRS * sizeof(double) + JPAIRS * sizeof(double2)),
+                     red, &stop};
+    const double fro2 = jacobi_load(G + (size_t)prob * LD * LD, m, dead, dead_stride, dead_ofs, A64, red);
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        A32[e] = make_float2((float)A64[e].x, (float)A64[e].y);
+        V32[e] = make_float2(i == j ? 1.f : 0.f, 0.f);
+    }
+    __syncthreads();
+    auto v32get = [&](int r, int c) -> float2 { return V32[r * m + c]; };
+    auto v32set = [&](int r, int c, float2 v) { V32[r * m + c] = v; };
+    jacobi_sweeps<float>(A32, m, v32get, v32set, max_sweeps, 1e-6, fro2, js);
+    // W = A V0, then A <- V0^H W  (FP64)
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        double2 s = make_double2(0.0, 0.0);
+        for (int q = 0; q < m; ++q) {
+            const float2 v = V32[q * m + j];
+            cfma(s, A64[i * m + q], make_double2(v.x, v.y));
+        }
+        W64[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        double2 s = make_double2(0.0, 0.0);
+        for (int q = 0; q < m; ++q) {
+            const float2 v = V32[q * m + i];
+            cfma(s, make_double2(v.x, -v.y), W64[q * m + j]);
+        }
+        A64[e] = s;
+    }
+    __syncthreads();
+    // exact Hermitian symmetry and real diagonal before the FP64 sweeps
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        if (i > j) {
+            const double2 lo = A64[e], up = A64[j * m + i];
+            const double2 h = make_double2(0.5 * (lo.x + up.x), 0.5 * (lo.y - up.y));
+            A64[e] = h;
+            A64[j * m + i] = make_double2(h.x, -h.y);
+        } else if (i == j) {
+            A64[e].y = 0.0;
+        }
+        W64[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    auto v64get = [&](int r, int c) -> double2 { return W64[r * m + c]; };
+    auto v64set = [&](int r, int c, double2 v) { W64[r * m + c] = v; };
+    jacobi_sweeps<double>(A64, m, v64get, v64set, max_sweeps, rel_tol, fro2, js);
+    jacobi_sort(A64, m, perm);
+    for (int c = threadIdx.x; c < m; c += blockDim.x) evals[(size_t)prob * LD + c] = A64[perm[c] * m + perm[c]].x;
+    double2 *out = evecs + (size_t)prob * LD * LD;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int r = e / m, c = e % m, pc = perm[c];
+        double2 s = make_double2(0.0, 0.0);
+        for (int q = 0; q < m; ++q) {
+            const float2 v = V32[r * m + q];
+            cfma(s, make_double2(v.x, v.y), W64[q * m + pc]);
+        }
+        out[r * LD + c] = s;
     }
 }
 
@@ -1432,15 +1549,20 @@ struct Solver {
     }
     template <typename T> void jacobi_t(int nch, int m, bool masked, int ofs, double tol) {
         const size_t c2 = 2 * sizeof(T);
-        const size_t extra = 5 * JPAIRS * sizeof(T) + JPAIRS * c2 + 2 * JPAIRS * sizeof(int);
         const size_t stat = 32 * sizeof(double) + sizeof(int) + LD * sizeof(int) + 256;
-        size_t smem2 = (size_t)2 * m * m * c2 + extra;
-        size_t smem1 = (size_t)m * m * c2 + extra;
+        size_t smem2 = (size_t)2 * m * m * c2 + kJacobiScratchBytes;
+        size_t smem1 = (size_t)m * m * c2 + kJacobiScratchBytes;
+        size_t smemx = (size_t)m * m * (2 * sizeof(double2) + 2 * sizeof(float2)) + kJacobiScratchBytes;
         const bool vs = smem2 + stat <= (size_t)h->smem_optin;
+        const bool mixed = std::is_same<T, double>::value && m <= JMIX_MAX && smemx + stat <= (size_t)h->smem_optin;
         int np = nk * nch;
         if (masked)
             MB_LAUNCH_E(KN_SMALL, alive_mask_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_alive, kd, ofs, M, b, nch, m, np, d_mask));
-        if (vs) {
+        if (mixed) {
+            cuda(smem_limit_once((const void *)jacobi_mixed_kernel, h->device, h->smem_optin));
+            MB_LAUNCH_E(KN_JACOBI, (jacobi_mixed_kernel<<<np, 256, smemx, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
+                                                                               d_evals, d_Y, 30, tol)));
+        } else if (vs) {
             cuda(smem_limit_once((const void *)jacobi_kernel<true, T>, h->device, h->smem_optin));
             MB_LAUNCH_E(KN_JACOBI, (jacobi_kernel<true, T><<<np, 256, smem2, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
                                                                                   d_evals, d_Y, 30, tol)));
