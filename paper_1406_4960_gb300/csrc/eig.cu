@@ -131,7 +131,10 @@ __global__ void krylov_residual32_kernel(const EigK *ks, int nch, int slot, cons
     const int prob = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
-    const float th = (float)theta[prob];
+    __shared__ float th_s;
+    if (threadIdx.x == 0) th_s = (float)theta[prob];
+    __syncthreads();
+    const float th = th_s;
     const int ih = slot == 0 ? oHX + seed[prob] : oHK + (slot - 1) * nc + ch;
     const int is = slot == 0 ? oSX + seed[prob] : oSK + (slot - 1) * nc + ch;
     const float2 *h = d.v32 + (long long)ih * d.nvec;
@@ -208,10 +211,15 @@ __global__ void normalize_kernel(const EigK *ks, int nch, int oW, int oSW, int k
     const int prob = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
-    const double n2 = nrm2[prob];
-    const bool ok = n2 > 1e-24;
-    const double inv = ok ? 1.0 / sqrt(n2) : 0.0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) alive[prob * kd + slot] = ok ? 1 : 0;
+    __shared__ double inv_s;
+    if (threadIdx.x == 0) {
+        const double n2 = nrm2[prob];
+        const bool ok = n2 > 1e-24;
+        inv_s = ok ? 1.0 / sqrt(n2) : 0.0;
+        if (blockIdx.x == 0) alive[prob * kd + slot] = ok ? 1 : 0;
+    }
+    __syncthreads();
+    const double inv = inv_s;
     const double2 *w = d.base + (long long)(oW + ch) * d.nvec;
     const double2 *sw = d.base + (long long)(oSW + ch) * d.nvec;
     double2 *kv = d.base + (long long)(kV + ch * cs + slot) * d.nvec;
@@ -238,10 +246,16 @@ __global__ void normalize32_kernel(const EigK *ks, int nch, int oW, int oK, int 
     const int prob = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
-    const double n2 = nrm2[prob];
-    const bool ok = n2 > 1e-24;
-    const float inv = ok ? (float)(1.0 / sqrt(n2)) : 0.f;
-    if (blockIdx.x == 0 && threadIdx.x == 0) alive[prob * kd + slot] = ok ? 1 : 0;
+    // the scale once per block (FP64 square roots and divisions are slow)
+    __shared__ float inv_s;
+    if (threadIdx.x == 0) {
+        const double n2 = nrm2[prob];
+        const bool ok = n2 > 1e-24;
+        inv_s = ok ? (float)(1.0 / sqrt(n2)) : 0.f;
+        if (blockIdx.x == 0) alive[prob * kd + slot] = ok ? 1 : 0;
+    }
+    __syncthreads();
+    const float inv = inv_s;
     const float2 *w = d.v32 + (long long)(oW + ch) * d.nvec;
     float2 *kv = d.v32 + (long long)(oK + slot * nc + ch) * d.nvec;
     float2 *sk = d.v32 + (long long)(oSK + slot * nc + ch) * d.nvec;
@@ -969,6 +983,82 @@ __global__ void __launch_bounds__(256) gram_tile32_kernel(const EigK *ks, int nc
         }
 }
 
+// Both Grams of a small pencil, V^H HV and V^H SV (lower triangles, m = M
+// <= 8), on the FP32 copies: every thread reads the 3M vectors once per
+// element and keeps all M(M+1) partial sums in registers; the CTA reduces
+// them (FP64 across warps) into per-chunk partials for gram_reduce_kernel.
+template <int M>
+__global__ void __launch_bounds__(128) pencil_gram32_kernel(const EigK *ks, int nch, VSet V, VSet HV, VSet SV,
+                                                           int nsplit, double2 *partH, double2 *partS) {
+    constexpr int NL = M * (M + 1) / 2;
+    constexpr int NW = 128 / 32;
+    __shared__ float2 red[NW][2 * NL];
+    const int split = blockIdx.x, prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const long long n = d.nvec;
+    const long long chunk = (n + nsplit - 1) / nsplit;
+    const long long t0 = (long long)split * chunk, t1 = min(n, t0 + chunk);
+    const float2 *vp[M], *hp[M], *sp[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        vp[i] = d.v32 + (long long)V.at(i, ch) * n;
+        hp[i] = d.v32 + (long long)HV.at(i, ch) * n;
+        sp[i] = d.v32 + (long long)SV.at(i, ch) * n;
+    }
+    float2 aH[NL], aS[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) aH[l] = aS[l] = make_float2(0.f, 0.f);
+    for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        float2 v[M], hv[M], sv[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            v[i] = vp[i][t];
+            hv[i] = hp[i][t];
+            sv[i] = sp[i][t];
+        }
+        int l = 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j, ++l) {      // G[i][j] = conj(v_i) x_j
+                aH[l].x = fmaf(v[i].x, hv[j].x, fmaf(v[i].y, hv[j].y, aH[l].x));
+                aH[l].y = fmaf(v[i].x, hv[j].y, fmaf(-v[i].y, hv[j].x, aH[l].y));
+                aS[l].x = fmaf(v[i].x, sv[j].x, fmaf(v[i].y, sv[j].y, aS[l].x));
+                aS[l].y = fmaf(v[i].x, sv[j].y, fmaf(-v[i].y, sv[j].x, aS[l].y));
+            }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        float hx = aH[l].x, hy = aH[l].y, sx = aS[l].x, sy = aS[l].y;
+        for (int off = 16; off > 0; off >>= 1) {
+            hx += __shfl_down_sync(0xffffffffu, hx, off);
+            hy += __shfl_down_sync(0xffffffffu, hy, off);
+            sx += __shfl_down_sync(0xffffffffu, sx, off);
+            sy += __shfl_down_sync(0xffffffffu, sy, off);
+        }
+        if (lane == 0) {
+            red[warp][l] = make_float2(hx, hy);
+            red[warp][NL + l] = make_float2(sx, sy);
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * NL; e += blockDim.x) {
+        double x = 0.0, y = 0.0;
+        for (int w = 0; w < NW; ++w) {
+            x += (double)red[w][e].x;
+            y += (double)red[w][e].y;
+        }
+        const int l = e % NL;
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= l) ++i;
+        const int j = l - i * (i + 1) / 2;
+        double2 *part = e < NL ? partH : partS;
+        part[((size_t)prob * nsplit + split) * M * M + (size_t)i * M + j] = make_double2(x, y);
+    }
+}
+
 // C_j = beta C_j + alpha sum_i A_i Y[i][j]: one element t per thread, JC
 // output columns at a time with their coefficients staged in shared memory.
 template <int JC, bool F32>
@@ -1579,9 +1669,29 @@ struct Solver {
     // identity), Ritz pairs of U^H (V^H H V) U; returns the Ritz vectors'
     // coordinates in the V basis (U Y) and leaves the values in d_evals.
     const double2 *rr_pencil(int nch, VSet V, VSet HV, VSet SV, int m, int ofs, bool f32 = false) {
-        gram(nch, V, HV, d_G, f32, true);
-        gram(nch, V, SV, d_Sg, f32, true);
+        if (f32 && m >= 2 && m <= 8) {
+            pencil_grams32(nch, V, HV, SV, m);
+        } else {
+            gram(nch, V, HV, d_G, f32, true);
+            gram(nch, V, SV, d_Sg, f32, true);
+        }
         return pencil_solve(nch, m, ofs);
+    }
+    // V^H HV into d_G and V^H SV into d_Sg (lower triangles completed), FP32 copies
+    void pencil_grams32(int nch, VSet V, VSet HV, VSet SV, int m) {
+        const int nprob = nk * nch;
+        int nsplit = std::max(1, std::min(32, (4 * h->num_sms + nprob - 1) / nprob));
+        while ((size_t)2 * nprob * nsplit * m * m > part_cap && nsplit > 1) --nsplit;
+        double2 *pH = d_part, *pS = d_part + (size_t)nprob * nsplit * m * m;
+        const dim3 grid(nsplit, nprob);
+        switch (m) {
+#define MB_PG(MM) case MM: MB_LAUNCH_E(KN_GRAM32, (pencil_gram32_kernel<MM><<<grid, 128, 0, s>>>(d_k, nch, V, HV, SV, nsplit, pH, pS))); break;
+            MB_PG(2) MB_PG(3) MB_PG(4) MB_PG(5) MB_PG(6) MB_PG(7) MB_PG(8)
+#undef MB_PG
+        }
+        const dim3 gr((m * m + 127) / 128, nprob);
+        MB_LAUNCH_E(KN_GRAM32, gram_reduce_kernel<<<gr, 128, 0, s>>>(pH, nsplit, m, m, d_G, 1));
+        MB_LAUNCH_E(KN_GRAM32, gram_reduce_kernel<<<gr, 128, 0, s>>>(pS, nsplit, m, m, d_Sg, 1));
     }
     // the pencil (d_G, d_Sg) of nch problems per k-point
     const double2 *pencil_solve(int nch, int m, int ofs) {
