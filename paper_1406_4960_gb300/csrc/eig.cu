@@ -635,52 +635,62 @@ __global__ void __launch_bounds__(256) jacobi_mixed_kernel(const double2 *G, int
 
 // U = L^{-H} with G = L L^H (G Hermitian positive definite, m <= JMAX).
 // L lives in shared memory; U is written row by row to global memory.
+// T = float: the arithmetic in FP32 (the bulk cycles' S-Grams, which are the
+// identity up to the FP32 Gram-Schmidt error).
+template <typename T>
 __global__ void __launch_bounds__(128) cholinv_kernel(const double2 *G, int m, double2 *U, int *status) {
+    typedef typename std::conditional<std::is_same<T, float>::value, float2, double2>::type T2;
     extern __shared__ __align__(16) unsigned char sm[];
-    double2 *L = reinterpret_cast<double2 *>(sm);     // m x m, lower
+    T2 *L = reinterpret_cast<T2 *>(sm);     // m x m, lower
+    T *rdiag = reinterpret_cast<T *>(L + m * m);
     const int prob = blockIdx.x;
     const double2 *g = G + (size_t)prob * LD * LD;
     double2 *u = U + (size_t)prob * LD * LD;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         int i = e / m, j = e % m;
-        L[e] = i >= j ? g[i * LD + j] : make_double2(0.0, 0.0);
+        const double2 v = i >= j ? g[i * LD + j] : make_double2(0.0, 0.0);
+        L[e] = mk((T)v.x, (T)v.y);
     }
     __syncthreads();
-    __shared__ double piv;
+    __shared__ T rpiv;
     for (int j = 0; j < m; ++j) {
         if (threadIdx.x == 0) {
-            double d = L[j * m + j].x;
-            if (!(d > 0.0)) {
+            T d = L[j * m + j].x;
+            if (!(d > T(0))) {
                 status[prob] = 1;
-                d = 1e-300;
+                d = std::is_same<T, float>::value ? T(1e-30) : T(1e-300);
             }
-            piv = sqrt(d);
-            L[j * m + j] = make_double2(piv, 0.0);
+            const T piv = sqrt(d);
+            rpiv = T(1) / piv;
+            L[j * m + j] = mk(piv, T(0));
         }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) L[i * m + j] = rscale(1.0 / piv, L[i * m + j]);
+        const T r = rpiv;
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) L[i * m + j] = rscale(r, L[i * m + j]);
         __syncthreads();
         // trailing update: L[i][c] -= L[i][j] conj(L[c][j]) for j < c <= i
         for (int e = threadIdx.x; e < (m - j - 1) * (m - j - 1); e += blockDim.x) {
             int i = j + 1 + e / (m - j - 1), c = j + 1 + e % (m - j - 1);
             if (c > i) continue;
-            double2 lij = L[i * m + j], lcj = L[c * m + j];
+            T2 lij = L[i * m + j], lcj = L[c * m + j];
             L[i * m + c] = L[i * m + c] - cmul_c(lij, lcj);
         }
         __syncthreads();
     }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) rdiag[i] = T(1) / L[i * m + i].x;
+    __syncthreads();
     // column c of Z = L^{-1} by forward substitution (one thread per column);
     // U[c][i] = conj(Z[i][c]), and Z[q][c] is read back as conj(U[c][q])
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
         for (int i = 0; i < c; ++i) u[c * LD + i] = make_double2(0.0, 0.0);
         for (int i = c; i < m; ++i) {
-            double2 acc = make_double2(i == c ? 1.0 : 0.0, 0.0);
+            T2 acc = mk(T(i == c ? 1 : 0), T(0));
             for (int q = c; q < i; ++q) {
-                double2 uq = u[c * LD + q];
-                acc = acc - cmul(L[i * m + q], make_double2(uq.x, -uq.y));
+                const double2 uq = u[c * LD + q];
+                acc = acc - cmul(L[i * m + q], mk((T)uq.x, (T)-uq.y));
             }
-            double2 z = rscale(1.0 / L[i * m + i].x, acc);
-            u[c * LD + i] = make_double2(z.x, -z.y);
+            const T2 z = rscale(rdiag[i], acc);
+            u[c * LD + i] = make_double2((double)z.x, (double)-z.y);
         }
     }
 }
@@ -1446,6 +1456,18 @@ struct Solver {
         else
             MB_LAUNCH_E(F32 ? KN_COMBINE32 : KN_COMBINE, (combine2_kernel<16, F32><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
     }
+    // U = L^{-H} of np problems (FP32 arithmetic in the bulk cycles)
+    void cholinv(int np, int m, const double2 *G, double2 *U, int *status, bool f32) {
+        if (f32) {
+            const size_t smem = (size_t)m * m * sizeof(float2) + m * sizeof(float);
+            cuda(smem_limit_once((const void *)cholinv_kernel<float>, h->device, h->smem_optin));
+            MB_LAUNCH_E(KN_SMALL, cholinv_kernel<float><<<np, 128, smem, s>>>(G, m, U, status));
+        } else {
+            const size_t smem = (size_t)m * m * sizeof(double2) + m * sizeof(double);
+            cuda(smem_limit_once((const void *)cholinv_kernel<double>, h->device, h->smem_optin));
+            MB_LAUNCH_E(KN_SMALL, cholinv_kernel<double><<<np, 128, smem, s>>>(G, m, U, status));
+        }
+    }
     void small_gemm(const double2 *A, const double2 *B, double2 *C, int m, int conjA, int np = 0) {
         MB_LAUNCH_E(KN_SMALL, small_zgemm_kernel<<<dim3((m * m + 127) / 128, np > 0 ? np : nk), 128, 0, s>>>(
                                   A, B, C, m, conjA));
@@ -1699,8 +1721,7 @@ struct Solver {
         const dim3 gs((m * m + 127) / 128, np);
         MB_LAUNCH_E(KN_SMALL, alive_mask_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_alive, kd, ofs, M, b, nch, m, np, d_mask));
         MB_LAUNCH_E(KN_SMALL, mask_sgram_kernel<<<gs, 128, 0, s>>>(d_Sg, d_mask, m));
-        cuda(smem_limit_once((const void *)cholinv_kernel, h->device, h->smem_optin));
-        MB_LAUNCH_E(KN_SMALL, cholinv_kernel<<<np, 128, (size_t)m * m * sizeof(double2), s>>>(d_Sg, m, d_Ub, d_statb));
+        cholinv(np, m, d_Sg, d_Ub, d_statb, lowp());
         small_gemm(d_G, d_Ub, d_Tb, m, 0, np);    // (V^H H V) U
         small_gemm(d_Ub, d_Tb, d_G, m, 1, np);    // U^H (V^H H V) U
         jacobi(nch, m, true, ofs, lowp());
@@ -1764,9 +1785,7 @@ struct Solver {
         } else {
             gram(1, vs(oV, M), vs(oSV, M), d_G, false, true);
         }
-        size_t smem = (size_t)M * M * sizeof(double2);
-        cuda(smem_limit_once((const void *)cholinv_kernel, h->device, h->smem_optin));
-        MB_LAUNCH_E(KN_SMALL, cholinv_kernel<<<nk, 128, smem, s>>>(d_G, M, d_U, d_status));
+        cholinv(nk, M, d_G, d_U, d_status, f32);
         if (f32) gram(1, vs(o32X, M), vs(o32HX, M), d_G2, true, true);
         else gram(1, vs(oV, M), vs(oHV, M), d_G2, false, true);
         small_gemm(d_G2, d_U, d_T, M, 0);     // (X^H H X) U
