@@ -13,6 +13,17 @@ extern "C" {
  * 4-byte status word; returns MB_ETIMEOUT if a bounded device wait expired. */
 int mb_debug_gemm_bf16(const void *A, const void *Bt, float *D, int M, int N, int K, void *stream);
 
+/* G = A^H B on the tensor cores (tcgen05, TF32 operands split as hi + lo for
+ * FP32 accuracy, FP32 accumulation in tensor memory, chunks reduced in
+ * FP64): the eigensolver's Gram building block.  V: device FP32 complex
+ * (interleaved), ma + mb vectors of n elements stored one after another, the
+ * ma vectors of A first; nsplit chunks of the vector length (1..4096).  G:
+ * host, ma x mb complex (interleaved doubles), row i = A_i.  Requires
+ * 1 <= ma <= 64 and 1 <= mb <= 64.  Allocates and frees its own device
+ * buffers; returns MB_EINVAL for bad sizes, MB_ETIMEOUT if a bounded device
+ * wait expired. */
+int mb_debug_gram_tc32(const void *V, long long n, int ma, int mb, int nsplit, double *G, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

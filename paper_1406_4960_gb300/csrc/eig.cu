@@ -26,6 +26,7 @@
 
 #include "cplx.cuh"
 #include "mb_internal.h"
+#include "tc_gemm.cuh"
 
 namespace mb {
 
@@ -1069,6 +1070,185 @@ __global__ void __launch_bounds__(128) pencil_gram32_kernel(const EigK *ks, int 
     }
 }
 
+// A^H B on the tensor cores (tcgen05, TF32 inputs, FP32 accumulation in
+// tensor memory) for the FP32 copies, to FP32 accuracy by splitting every
+// value into x = hi + lo (hi = x rounded to TF32) and summing hi*hi + hi*lo +
+// lo*hi.  Complex products become one real product over interleaved (re, im)
+// rows: with the MMA's M side holding B_j and B'_j = (im, -re) of B_j, and its
+// N side holding A_i,
+//   D[j][i]      = sum (ar br + ai bi) = Re (A_i^H B_j)
+//   D[mb + j][i] = sum (ar bi - ai br) = Im (A_i^H B_j).
+// One CTA (128 threads, TMEM lane = row) takes one chunk of the vector length
+// of one problem, in steps of GTC_KC complex elements staged in shared
+// memory (canonical K-major layout without swizzle: 8-row x 16-byte core
+// matrices, element (r, k) at (r/8)*SBO + (k/4)*LBO + (r%8)*16 + (k%4)*4).
+// Requires 2 mb <= 128 and ma <= GTC_NMAX.  Partials go to `part` like the
+// CUDA-core Gram kernels' (reduced by gram_reduce_kernel); a wait on the MMA
+// barrier that runs out sets *err and skips the rest.
+constexpr int GTC_KC = 32;                    // complex elements per step (64 TF32 values per row)
+constexpr int GTC_NMAX = 64;
+constexpr int GTC_LBO = 128, GTC_SBO = (2 * GTC_KC / 4) * 128;
+__host__ __device__ constexpr size_t gtc_smem_bytes(int ntile) {
+    return (size_t)2 * 128 * 2 * GTC_KC * 4 + (size_t)2 * ntile * 2 * GTC_KC * 4;
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ uint32_t gtc_off(int r, int k) {
+    return (uint32_t)((r >> 3) * GTC_SBO + (k >> 2) * GTC_LBO + (r & 7) * 16 + (k & 3) * 4);
+}
+__global__ void __launch_bounds__(128) gram_tc32_kernel(const EigK *ks, int nch, VSet A, VSet B, int nsplit, int ntile,
+                                                        double2 *part, int *err) {
+    extern __shared__ __align__(1024) unsigned char gsm[];
+    unsigned char *Mhi = gsm, *Mlo = gsm + 128 * 2 * GTC_KC * 4;
+    unsigned char *Nhi = Mlo + 128 * 2 * GTC_KC * 4, *Nlo = Nhi + ntile * 2 * GTC_KC * 4;
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int failed;
+    const int split = blockIdx.x, prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const int ma = A.count(), mb = B.count();
+    const long long n = d.nvec;
+    const long long chunk = (n + nsplit - 1) / nsplit;
+    const long long t0 = (long long)split * chunk, t1 = min(n, t0 + chunk);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int ncols = 32;
+    while (ncols < ntile) ncols <<= 1;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_base)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        tc::mbar_init(&mbar, 1);
+        failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // rows that no step writes (M side beyond 2 mb, N side beyond ma) stay zero
+    for (int e = tid; e < (128 - 2 * mb) * 2 * GTC_KC; e += blockDim.x) {
+        const int r = 2 * mb + e / (2 * GTC_KC), kk = e % (2 * GTC_KC);
+        *reinterpret_cast<float *>(Mhi + gtc_off(r, kk)) = 0.f;
+        *reinterpret_cast<float *>(Mlo + gtc_off(r, kk)) = 0.f;
+    }
+    for (int e = tid; e < (ntile - ma) * 2 * GTC_KC; e += blockDim.x) {
+        const int r = ma + e / (2 * GTC_KC), kk = e % (2 * GTC_KC);
+        *reinterpret_cast<float *>(Nhi + gtc_off(r, kk)) = 0.f;
+        *reinterpret_cast<float *>(Nlo + gtc_off(r, kk)) = 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    // kind::tf32 instruction descriptor: D F32, A and B TF32, both K-major, M = 128, N = ntile
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(ntile >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    uint32_t phase = 0;
+    bool any = false;
+    // staging: element e = tid + 128 u of a side maps to row (e/8/KC)*8 + e%8
+    // and element (e/8) % KC (a warp reads 8 rows x 4 consecutive elements);
+    // each thread holds its elements of one step in registers, loaded while
+    // the previous step's products run
+    constexpr int UMAX = GTC_NMAX * GTC_KC / 128;     // 16
+    const int nem = ((mb + 7) / 8) * 8 * GTC_KC, nea = ((ma + 7) / 8) * 8 * GTC_KC;
+    float2 bv[UMAX], av[UMAX];
+    auto fetch = [&](long long tb) {
+#pragma unroll
+        for (int u = 0; u < UMAX; ++u) {
+            const int e = tid + 128 * u;
+            const int rl = e & 7, c = (e >> 3) % GTC_KC, r = ((e >> 3) / GTC_KC) * 8 + rl;
+            const long long t = tb + c;
+            bv[u] = (e < nem && r < mb && t < t1) ? d.v32[(long long)B.at(r, ch) * n + t] : make_float2(0.f, 0.f);
+            av[u] = (e < nea && r < ma && t < t1) ? d.v32[(long long)A.at(r, ch) * n + t] : make_float2(0.f, 0.f);
+        }
+    };
+    if (t0 < t1) fetch(t0);
+    for (long long tb = t0; tb < t1; tb += GTC_KC) {
+#pragma unroll
+        for (int u = 0; u < UMAX; ++u) {
+            const int e = tid + 128 * u;
+            const int rl = e & 7, c = (e >> 3) % GTC_KC, r = ((e >> 3) / GTC_KC) * 8 + rl;
+            if (e < nem && r < mb) {
+                const float2 v = bv[u];
+                const float hx = tf32_rna(v.x), hy = tf32_rna(v.y);
+                const float lx = v.x - hx, ly = v.y - hy;
+                *reinterpret_cast<float2 *>(Mhi + gtc_off(r, 2 * c)) = make_float2(hx, hy);
+                *reinterpret_cast<float2 *>(Mlo + gtc_off(r, 2 * c)) = make_float2(lx, ly);
+                *reinterpret_cast<float2 *>(Mhi + gtc_off(mb + r, 2 * c)) = make_float2(hy, -hx);
+                *reinterpret_cast<float2 *>(Mlo + gtc_off(mb + r, 2 * c)) = make_float2(ly, -lx);
+            }
+            if (e < nea && r < ma) {
+                const float2 v = av[u];
+                const float hx = tf32_rna(v.x), hy = tf32_rna(v.y);
+                *reinterpret_cast<float2 *>(Nhi + gtc_off(r, 2 * c)) = make_float2(hx, hy);
+                *reinterpret_cast<float2 *>(Nlo + gtc_off(r, 2 * c)) = make_float2(v.x - hx, v.y - hy);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+            const uint32_t mh = tc::smem_u32(Mhi), ml = tc::smem_u32(Mlo), nh = tc::smem_u32(Nhi), nl = tc::smem_u32(Nlo);
+            for (int kk = 0; kk < 2 * GTC_KC / 8; ++kk) {
+                const uint32_t o = kk * 2 * GTC_LBO;
+                const uint64_t dmh = tc::smem_desc(mh + o, GTC_LBO, GTC_SBO), dml = tc::smem_desc(ml + o, GTC_LBO, GTC_SBO);
+                const uint64_t dnh = tc::smem_desc(nh + o, GTC_LBO, GTC_SBO), dnl = tc::smem_desc(nl + o, GTC_LBO, GTC_SBO);
+                const uint64_t da[3] = {dmh, dmh, dml}, db[3] = {dnh, dnl, dnh};
+                for (int q = 0; q < 3; ++q) {
+                    const uint32_t acc = (any || kk > 0 || q > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                        "l"(da[q]), "l"(db[q]), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tc::smem_u32(&mbar)));
+        }
+        any = true;
+        if (tb + GTC_KC < t1) fetch(tb + GTC_KC);        // next step's loads overlap the products
+        if (!tc::mbar_wait(&mbar, phase, 1ll << 24)) {
+            if (tid == 0) {
+                failed = 1;
+                atomicExch(err, 1);
+            }
+        }
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (failed) break;
+    }
+    if (!failed) {
+        // warp w holds rows (TMEM lanes) 32w .. 32w+31; 8 columns (A vectors) per load
+        double *pd = reinterpret_cast<double *>(part + ((size_t)prob * nsplit + split) * ma * mb);
+        const int r = 32 * warp + lane;
+        for (int c0 = 0; c0 < ntile; c0 += 8) {
+            uint32_t v[8];
+            if (any) {
+                const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                               "=r"(v[7])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+            } else {
+                for (int j = 0; j < 8; ++j) v[j] = 0u;
+            }
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + j;
+                if (c >= ma) break;
+                if (r < mb) pd[2 * ((size_t)c * mb + r)] = (double)__uint_as_float(v[j]);
+                else if (r < 2 * mb) pd[2 * ((size_t)c * mb + (r - mb)) + 1] = (double)__uint_as_float(v[j]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
 // C_j = beta C_j + alpha sum_i A_i Y[i][j]: one element t per thread, JC
 // output columns at a time with their coefficients staged in shared memory.
 template <int JC, bool F32>
@@ -1364,6 +1544,8 @@ struct Solver {
     double *d_evals = nullptr, *d_eps = nullptr, *d_res = nullptr, *d_dots = nullptr, *d_theta = nullptr;
     int *d_seed = nullptr, *d_srcH = nullptr, *d_srcS = nullptr, *d_alive = nullptr, *d_status = nullptr;
     int *d_mask = nullptr;
+    int *d_tcerr = nullptr;   // set by a tensor-core kernel whose bounded wait ran out
+    bool use_tc = true;       // FP32 Grams on the tensor cores
     size_t part_cap = 0;
     long long nmax = 0;
     int maxldg = 0;
@@ -1408,6 +1590,21 @@ struct Solver {
     template <int GJ> void gram_t(int nch, VSet A, VSet B, double2 *G, bool f32, bool lower) {
         const int nprob = nk * nch;
         const int ma = A.count(), mbc = B.count();
+        if (f32 && mbc >= 4 && 2 * mbc <= 128 && ma <= GTC_NMAX && ma * mbc >= 64 && use_tc) {
+            // tensor cores: two resident CTAs per SM over the whole grid
+            const int ntile = std::max(16, (ma + 15) / 16 * 16);
+            int nsplit = std::max(1, std::min(1024, (2 * h->num_sms + nprob - 1) / nprob));
+            nsplit = std::min<long long>(nsplit, std::max<long long>(1, nmax / (2 * GTC_KC)));
+            while ((size_t)nprob * nsplit * ma * mbc > part_cap && nsplit > 1) --nsplit;
+            const size_t smem = gtc_smem_bytes(ntile);
+            cuda(smem_limit_once((const void *)gram_tc32_kernel, h->device, h->smem_optin));
+            MB_LAUNCH_E(KN_GRAM32, gram_tc32_kernel<<<dim3(nsplit, nprob), 128, smem, s>>>(d_k, nch, A, B, nsplit, ntile,
+                                                                                        d_part, d_tcerr));
+            MB_LAUNCH_E(KN_GRAM32,
+                        gram_reduce_kernel<<<dim3((ma * mbc + 127) / 128, nprob), 128, 0, s>>>(d_part, nsplit, ma, mbc, G,
+                                                                                           lower ? 1 : 0));
+            return;
+        }
         if (f32 && ma * mbc >= 64 && mbc >= 4) {
             // tile kernel: about two resident CTAs per SM over the whole grid
             const int tiles = ((ma + GT_MAX - 1) / GT_MAX) * ((mbc + GT_MAX - 1) / GT_MAX);
@@ -1961,6 +2158,7 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     S.d_alive = S.alloc<int>((size_t)nprob * S.kd);
     S.d_mask = S.alloc<int>((size_t)nprob * LD);
     S.d_status = S.alloc<int>(S.nk);
+    S.d_tcerr = S.alloc<int>(1);
     if (S.gs32) {
         S.d_Sg = S.alloc<double2>((size_t)nprob * LD * LD);
         S.d_Ub = S.alloc<double2>((size_t)nprob * LD * LD);
@@ -1971,6 +2169,7 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     S.cuda(cudaMemcpyAsync(S.d_k, S.kd_host.data(), sizeof(EigK) * S.nk, cudaMemcpyHostToDevice, s));
     S.cuda(cudaMemsetAsync(S.d_Ysel, 0, sizeof(double2) * (size_t)nprob * LD * LD, s));
     S.cuda(cudaMemsetAsync(S.d_status, 0, sizeof(int) * S.nk, s));
+    S.cuda(cudaMemsetAsync(S.d_tcerr, 0, sizeof(int), s));
     // initial trial vectors
     for (int k = 0; k < S.nk && !S.rc; ++k) {
         std::vector<double2> X0;
@@ -2068,8 +2267,14 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
             S.applies += applies_per_cycle[gi];
         }
         S.cuda(cudaMemcpyAsync(res.data(), S.d_res, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, s));
+        int tcerr = 0;
+        S.cuda(cudaMemcpyAsync(&tcerr, S.d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
         S.cuda(cudaStreamSynchronize(s));
         if (S.rc) break;
+        if (tcerr) {           // a tensor-core kernel's bounded wait ran out: its products are not valid
+            S.rc = MB_ETIMEOUT;
+            break;
+        }
         maxres = conv_max();
         if (S.prec != MB_FP64 && !S.fp64_roots) {
             // stalled: two bulk cycles in a row without a 30 % gain on the best
@@ -2136,3 +2341,51 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
 }
 
 }  // namespace mb
+
+// Self-test hook for the tensor-core Gram kernel: G = A^H B (FP64 host
+// output, row-major ma x mb interleaved complex) for ma + mb FP32 complex
+// vectors of length n stored contiguously on the device (A first), split
+// into nsplit chunks.
+extern "C" int mb_debug_gram_tc32(const void *V, long long n, int ma, int mb, int nsplit, double *G, void *stream) {
+    using namespace mb;
+    if (!V || !G || n < 1 || ma < 1 || mb < 1 || 2 * mb > 128 || ma > GTC_NMAX || nsplit < 1 || nsplit > 4096)
+        return MB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    EigK hk{};
+    hk.v32 = reinterpret_cast<float2 *>(const_cast<void *>(V));
+    hk.nvec = n;
+    const int ntile = std::max(16, (ma + 15) / 16 * 16);
+    EigK *dk = nullptr;
+    double2 *part = nullptr, *Gd = nullptr;
+    int *err = nullptr;
+    cudaError_t e = cudaMalloc(&dk, sizeof(EigK));
+    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double2) * (size_t)nsplit * ma * mb);
+    if (e == cudaSuccess) e = cudaMalloc(&Gd, sizeof(double2) * LD * LD);
+    if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dk, &hk, sizeof(EigK), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    const size_t smem = gtc_smem_bytes(ntile);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gram_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        gram_tc32_kernel<<<dim3(nsplit, 1), 128, smem, s>>>(dk, 1, vs(0, ma), vs(ma, mb), nsplit, ntile, part, err);
+        gram_reduce_kernel<<<dim3((ma * mb + 127) / 128, 1), 128, 0, s>>>(part, nsplit, ma, mb, Gd, 0);
+        e = cudaGetLastError();
+    }
+    std::vector<double2> hG((size_t)LD * LD);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hG.data(), Gd, sizeof(double2) * LD * LD, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dk);
+    cudaFree(part);
+    cudaFree(Gd);
+    cudaFree(err);
+    if (e != cudaSuccess) return MB_ECUDA;
+    for (int i = 0; i < ma; ++i)
+        for (int j = 0; j < mb; ++j) {
+            G[2 * ((size_t)i * mb + j)] = hG[(size_t)i * LD + j].x;
+            G[2 * ((size_t)i * mb + j) + 1] = hG[(size_t)i * LD + j].y;
+        }
+    return herr ? MB_ETIMEOUT : MB_OK;
+}

@@ -30,9 +30,17 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// bounded wait for the given phase; false when the limit was reached
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the given phase: at most `limit` polls and one second;
+// false when either limit was reached
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase, long long limit) {
     const uint32_t a = smem_u32(bar);
+    const uint64_t start = global_ns();
     for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
@@ -40,6 +48,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase, long lo
             : "=r"(done)
             : "r"(a), "r"(phase));
         if (done) return true;
+        if (global_ns() - start > 1000000000ull) return false;
     }
     return false;
 }
