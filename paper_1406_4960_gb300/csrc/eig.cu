@@ -1545,7 +1545,6 @@ struct Solver {
     int *d_seed = nullptr, *d_srcH = nullptr, *d_srcS = nullptr, *d_alive = nullptr, *d_status = nullptr;
     int *d_mask = nullptr;
     int *d_tcerr = nullptr;   // set by a tensor-core kernel whose bounded wait ran out
-    bool use_tc = true;       // FP32 Grams on the tensor cores
     size_t part_cap = 0;
     long long nmax = 0;
     int maxldg = 0;
@@ -1590,7 +1589,7 @@ struct Solver {
     template <int GJ> void gram_t(int nch, VSet A, VSet B, double2 *G, bool f32, bool lower) {
         const int nprob = nk * nch;
         const int ma = A.count(), mbc = B.count();
-        if (f32 && mbc >= 4 && 2 * mbc <= 128 && ma <= GTC_NMAX && ma * mbc >= 64 && use_tc) {
+        if (f32 && mbc >= 4 && 2 * mbc <= 128 && ma <= GTC_NMAX && ma * mbc >= 64) {
             // tensor cores: two resident CTAs per SM over the whole grid
             const int ntile = std::max(16, (ma + 15) / 16 * 16);
             int nsplit = std::max(1, std::min(1024, (2 * h->num_sms + nprob - 1) / nprob));
