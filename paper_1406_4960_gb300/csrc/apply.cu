@@ -854,8 +854,8 @@ static size_t per_k_scratch(const mb_handle *h, int ldg, int nbands, int nchunks
 // kMaxK that apply_H_batch forms, each planned as it will be launched).
 size_t apply_scratch_bytes(const mb_handle *h, int nk, int nbands, int prec) {
     const size_t c2 = prec == MB_FP64 ? 16 : 8;
-    const bool reg = prec == MB_FP64 ? plane_reg_supported<double>(h->n1, h->n2)
-                                     : plane_reg_supported<float>(h->n1, h->n2);
+    const bool reg = prec == MB_FP64 ? plane_reg_supported<double>(h->n1, h->n2, h->order)
+                                     : plane_reg_supported<float>(h->n1, h->n2, h->order);
     nk = std::min(nk, (int)h->kp.size());
     size_t need = 0;
     for (int i0 = 0; i0 < nk; i0 += kMaxK) {
@@ -882,7 +882,7 @@ static size_t apply_H_need(const mb_handle *h, int nsel, const int *iks, int nba
     const size_t c2 = sizeof(typename V2<R>::T);
     int maxldg = 0;
     for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
-    const PlanePlan plan = plan_plane(h, nsel, nbands, c2, maxldg, plane_reg_supported<R>(h->n1, h->n2));
+    const PlanePlan plan = plan_plane(h, nsel, nbands, c2, maxldg, plane_reg_supported<R>(h->n1, h->n2, h->order));
     return (size_t)nsel * per_k_scratch(h, maxldg, nbands, plan.nchunks, c2, tensor);
 }
 
@@ -920,7 +920,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     size_t off = 0;
     int maxldg = 0;
     for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
-    const PlanePlan plan = plan_plane(h, nsel, nbands, c2, maxldg, plane_reg_supported<R>(h->n1, h->n2));
+    const PlanePlan plan = plan_plane(h, nsel, nbands, c2, maxldg, plane_reg_supported<R>(h->n1, h->n2, h->order));
     const int chunk = plan.chunk, nchunks = plan.nchunks;
     (void)chunk;
     if (plan.np < 1) return MB_EUNSUPPORTED;

@@ -46,7 +46,7 @@ template <typename R> struct PlaneArgs {
 
 
 // register-FFT plane kernel (plane_reg.cu): available grids and launch
-template <typename R> bool plane_reg_supported(int n1, int n2);
+template <typename R> bool plane_reg_supported(int n1, int n2, int order);
 template <typename R>
 cudaError_t plane_reg_launch(const PlaneArgs<R> &a, unsigned grid, size_t smem, cudaStream_t s);
 void upload_fft_twiddles();

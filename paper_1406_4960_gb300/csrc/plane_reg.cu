@@ -99,7 +99,9 @@ template <typename R, int N1, int N2> struct PlaneShape {
                               : (N1 <= 32 && N2 <= 32 && sizeof(R) == 4) ? 2 : 1;
 };
 
-template <typename R, int N1, int N2>
+// KK: the B-spline order when it is known at compile time (6, every cell
+// here), else 0 (read from the arguments, at most 8)
+template <typename R, int N1, int N2, int KK>
 __global__ void __launch_bounds__(PlaneShape<R, N1, N2>::threads, PlaneShape<R, N1, N2>::ctas)
     plane_reg_kernel(const __grid_constant__ PlaneArgs<R> a) {
     typedef typename V2<R>::T C;
@@ -109,7 +111,8 @@ __global__ void __launch_bounds__(PlaneShape<R, N1, N2>::threads, PlaneShape<R, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *planes = reinterpret_cast<C *>(smem_raw);
     C *acc = planes + (size_t)a.np * PS;
-    const int K = a.order, P = a.nquad, nb = a.nb;
+    constexpr int KM = KK ? KK : 8;       // register extent of the kappa-wide windows
+    const int K = KK ? KK : a.order, P = a.nquad, nb = a.nb;
 
     const int nbt = (a.nbands + a.bt - 1) / a.bt;
     const int item = blockIdx.x;
@@ -181,22 +184,22 @@ __global__ void __launch_bounds__(PlaneShape<R, N1, N2>::threads, PlaneShape<R, 
                 const int o = goff[g];
                 const int op = o + o / N2;           // padded offset
                 int cur_b = -1;
-                C x[8];
+                C x[KM];
                 for (int pl = 0; pl < npl; ++pl) {
                     const int bb = pl_b[pl];
                     if (bb != cur_b) {
                         cur_b = bb;
                         const C *X = reinterpret_cast<const C *>(d.X) + (size_t)(b0 + bb) * band_stride;
 #pragma unroll
-                        for (int m = 0; m < 8; ++m) {
+                        for (int m = 0; m < KM; ++m) {
                             int j = t + m - 1;
-                            x[m] = (m < K && j >= 0 && j < nb) ? X[(size_t)j * ldg + g] : czero<C>();
+                            x[m] = ((KK || m < K) && j >= 0 && j < nb) ? X[(size_t)j * ldg + g] : czero<C>();
                         }
                     }
                     C psi = czero<C>();
 #pragma unroll
-                    for (int m = 0; m < 8; ++m)
-                        if (m < K) rfma(psi, bqs[pl * 8 + m], x[m]);
+                    for (int m = 0; m < KM; ++m)
+                        if (KK || m < K) rfma(psi, bqs[pl * 8 + m], x[m]);
                     planes[(size_t)pl * PS + op] = psi;
                 }
             }
@@ -247,15 +250,15 @@ __global__ void __launch_bounds__(PlaneShape<R, N1, N2>::threads, PlaneShape<R, 
             for (int g = threadIdx.x; g < ng; g += blockDim.x) {
                 const int o = goff[g];
                 const int op = o + o / N2;
-                C sum[8];
+                C sum[KM];
 #pragma unroll
-                for (int m = 0; m < 8; ++m) sum[m] = czero<C>();
+                for (int m = 0; m < KM; ++m) sum[m] = czero<C>();
                 int cur = pl_b[0];
                 auto flush = [&](int bb) {
 #pragma unroll
-                    for (int m = 0; m < 8; ++m) {
+                    for (int m = 0; m < KM; ++m) {
                         const int j = t + m - 1;
-                        if (m < K && j >= 0 && j < nb) {
+                        if ((KK || m < K) && j >= 0 && j < nb) {
                             int sl = slot0 + m;
                             if (sl >= K) sl -= K;
                             acc[((size_t)bb * K + sl) * ldg + g] += sum[m];
@@ -271,8 +274,8 @@ __global__ void __launch_bounds__(PlaneShape<R, N1, N2>::threads, PlaneShape<R, 
                     }
                     const C v = planes[(size_t)pl * PS + op];
 #pragma unroll
-                    for (int m = 0; m < 8; ++m)
-                        if (m < K) rfma(sum[m], bqs[pl * 8 + m], v);
+                    for (int m = 0; m < KM; ++m)
+                        if (KK || m < K) rfma(sum[m], bqs[pl * 8 + m], v);
                 }
                 flush(cur);
             }
@@ -287,22 +290,30 @@ __global__ void __launch_bounds__(PlaneShape<R, N1, N2>::threads, PlaneShape<R, 
     }
 }
 
-template <typename R> bool plane_reg_supported(int n1, int n2) {
+// grids of 16, 32 or 64 points per side (FP64: up to 32) and B-splines of
+// order 6; everything else takes the radix-2 kernel
+template <typename R> bool plane_reg_supported(int n1, int n2, int order) {
     const int lim = sizeof(R) == 4 ? 64 : 32;
     auto ok = [&](int n) { return n == 16 || n == 32 || n == 64; };
-    return ok(n1) && ok(n2) && n1 <= lim && n2 <= lim;
+    return ok(n1) && ok(n2) && n1 <= lim && n2 <= lim && order == 6;
+}
+
+template <typename R, int N1, int N2, int KK>
+static cudaError_t launch_k(const PlaneArgs<R> &a, unsigned grid, size_t smem, cudaStream_t s) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaError_t e = smem_limit_once((const void *)plane_reg_kernel<R, N1, N2, KK>, dev, optin);
+    if (e != cudaSuccess) return e;
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
+    plane_reg_kernel<R, N1, N2, KK><<<grid, PlaneShape<R, N1, N2>::threads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <typename R, int N1, int N2>
 static cudaError_t launch_one(const PlaneArgs<R> &a, unsigned grid, size_t smem, cudaStream_t s) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaError_t e = smem_limit_once((const void *)plane_reg_kernel<R, N1, N2>, dev, optin);
-    if (e != cudaSuccess) return e;
-    if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    plane_reg_kernel<R, N1, N2><<<grid, PlaneShape<R, N1, N2>::threads, smem, s>>>(a);
-    return cudaGetLastError();
+    if (a.order != 6) return cudaErrorInvalidValue;
+    return launch_k<R, N1, N2, 6>(a, grid, smem, s);
 }
 
 template <typename R>
@@ -327,8 +338,8 @@ cudaError_t plane_reg_launch<double>(const PlaneArgs<double> &a, unsigned grid, 
     return cudaErrorInvalidValue;
 }
 
-template bool plane_reg_supported<float>(int, int);
-template bool plane_reg_supported<double>(int, int);
+template bool plane_reg_supported<float>(int, int, int);
+template bool plane_reg_supported<double>(int, int, int);
 template cudaError_t plane_reg_launch<float>(const PlaneArgs<float> &, unsigned, size_t, cudaStream_t);
 
 }  // namespace mb
