@@ -62,23 +62,31 @@ static VSet vs(int s1, int c1, int cs1 = 0, int s2 = 0, int c2 = 0, int cs2 = 0,
 }
 
 // ---------------------------------------------------------------------------
-// Fixed-order reduction of per-chunk partial Gram products (deterministic).
-// lower: only entries j <= i were computed (a Hermitian product); the upper
-// triangle is written as the conjugate of the lower one.
+// Fixed-order reduction of per-chunk partial Gram products (deterministic):
+// one warp per output, lane l sums chunks l, l+32, ... and a fixed shuffle
+// tree combines the lanes.  lower: only entries j <= i were computed (a
+// Hermitian product); the upper triangle is written as the conjugate of the
+// lower one.  Grid: (outputs / 8, problems), 256 threads.
 __global__ void gram_reduce_kernel(const double2 *part, int nsplit, int ma, int mb, double2 *G, int lower) {
     const int prob = blockIdx.y;
     const int nout = ma * mb;
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= nout) return;
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (o >= nout) return;                        // whole warp leaves together
     int i = o / mb, j = o % mb;
     const bool up = lower && j > i;
     const int src = up ? j * mb + i : o;
     const double2 *p = part + (size_t)prob * nsplit * nout + src;
     double2 s = make_double2(0.0, 0.0);
-#pragma unroll 8
-    for (int sp = 0; sp < nsplit; ++sp) s = s + p[(size_t)sp * nout];
-    if (up) s.y = -s.y;
-    G[(size_t)prob * LD * LD + i * LD + j] = s;
+    for (int sp = lane; sp < nsplit; sp += 32) s = s + p[(size_t)sp * nout];
+    for (int off = 16; off > 0; off >>= 1) {
+        s.x += __shfl_down_sync(0xffffffffu, s.x, off);
+        s.y += __shfl_down_sync(0xffffffffu, s.y, off);
+    }
+    if (lane == 0) {
+        if (up) s.y = -s.y;
+        G[(size_t)prob * LD * LD + i * LD + j] = s;
+    }
 }
 
 // dst_i = src_i for index sets (FP64 -> FP64), or into / out of the FP32 stage
@@ -1600,7 +1608,7 @@ struct Solver {
             MB_LAUNCH_E(KN_GRAM32, gram_tc32_kernel<<<dim3(nsplit, nprob), 128, smem, s>>>(d_k, nch, A, B, nsplit, ntile,
                                                                                         d_part, d_tcerr));
             MB_LAUNCH_E(KN_GRAM32,
-                        gram_reduce_kernel<<<dim3((ma * mbc + 127) / 128, nprob), 128, 0, s>>>(d_part, nsplit, ma, mbc, G,
+                        gram_reduce_kernel<<<dim3((ma * mbc + 7) / 8, nprob), 256, 0, s>>>(d_part, nsplit, ma, mbc, G,
                                                                                            lower ? 1 : 0));
             return;
         }
@@ -1613,7 +1621,7 @@ struct Solver {
             MB_LAUNCH_E(KN_GRAM32, gram_tile32_kernel<<<dim3(nsplit, nprob, tiles), 256, 0, s>>>(d_k, nch, A, B, nsplit,
                                                                                                d_part));
             MB_LAUNCH_E(KN_GRAM32,
-                        gram_reduce_kernel<<<dim3((ma * mbc + 127) / 128, nprob), 128, 0, s>>>(d_part, nsplit, ma, mbc, G,
+                        gram_reduce_kernel<<<dim3((ma * mbc + 7) / 8, nprob), 256, 0, s>>>(d_part, nsplit, ma, mbc, G,
                                                                                            lower ? 1 : 0));
             return;
         }
@@ -1629,7 +1637,7 @@ struct Solver {
             MB_LAUNCH_E(KN_GRAM, (gram_rows_kernel<false, GJ><<<dim3(nsplit, nprob, rowgroups * colgroups), 256, 0, s>>>(
                                      d_k, nch, A, B, nsplit, colgroups, d_part, lower ? 1 : 0)));
         MB_LAUNCH_E(f32 ? KN_GRAM32 : KN_GRAM,
-                    gram_reduce_kernel<<<dim3((ma * mbc + 127) / 128, nprob), 128, 0, s>>>(d_part, nsplit, ma, mbc, G,
+                    gram_reduce_kernel<<<dim3((ma * mbc + 7) / 8, nprob), 256, 0, s>>>(d_part, nsplit, ma, mbc, G,
                                                                                            lower ? 1 : 0));
     }
     void combine(int nch, VSet A, VSet C, const double2 *Y, double alpha, double beta, bool f32 = false) {
@@ -1907,9 +1915,9 @@ struct Solver {
             MB_PG(2) MB_PG(3) MB_PG(4) MB_PG(5) MB_PG(6) MB_PG(7) MB_PG(8)
 #undef MB_PG
         }
-        const dim3 gr((m * m + 127) / 128, nprob);
-        MB_LAUNCH_E(KN_GRAM32, gram_reduce_kernel<<<gr, 128, 0, s>>>(pH, nsplit, m, m, d_G, 1));
-        MB_LAUNCH_E(KN_GRAM32, gram_reduce_kernel<<<gr, 128, 0, s>>>(pS, nsplit, m, m, d_Sg, 1));
+        const dim3 gr((m * m + 7) / 8, nprob);
+        MB_LAUNCH_E(KN_GRAM32, gram_reduce_kernel<<<gr, 256, 0, s>>>(pH, nsplit, m, m, d_G, 1));
+        MB_LAUNCH_E(KN_GRAM32, gram_reduce_kernel<<<gr, 256, 0, s>>>(pS, nsplit, m, m, d_Sg, 1));
     }
     // the pencil (d_G, d_Sg) of nch problems per k-point
     const double2 *pencil_solve(int nch, int m, int ofs) {
@@ -2368,7 +2376,7 @@ extern "C" int mb_debug_gram_tc32(const void *V, long long n, int ma, int mb, in
         e = cudaFuncSetAttribute(gram_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         gram_tc32_kernel<<<dim3(nsplit, 1), 128, smem, s>>>(dk, 1, vs(0, ma), vs(ma, mb), nsplit, ntile, part, err);
-        gram_reduce_kernel<<<dim3((ma * mb + 127) / 128, 1), 128, 0, s>>>(part, nsplit, ma, mb, Gd, 0);
+        gram_reduce_kernel<<<dim3((ma * mb + 7) / 8, 1), 256, 0, s>>>(part, nsplit, ma, mb, Gd, 0);
         e = cudaGetLastError();
     }
     std::vector<double2> hG((size_t)LD * LD);
