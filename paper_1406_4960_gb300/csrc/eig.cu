@@ -310,6 +310,7 @@ struct JacobiScratch {
     double *red;         // 32 partial sums
     int *stop;
 };
+constexpr int kJacobiThreads = 512;    // one CTA per problem
 constexpr size_t kJacobiScratchBytes = 5 * JPAIRS * sizeof(double) + JPAIRS * sizeof(double2) + 2 * JPAIRS * sizeof(int);
 
 // Sweeps until the off-diagonal Frobenius norm is <= rel_tol * sqrt(fro2).
@@ -505,7 +506,7 @@ __device__ void jacobi_sort(const T2 *A, int m, int *perm) {
 // otherwise it overwrites the input matrix G in global memory (m <= JMAX).
 // T = float runs the rotations in FP32 (the mixed solver's bulk cycles).
 template <bool VS, typename T>
-__global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const int *dead, int dead_stride,
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double2 *G, int m, const int *dead, int dead_stride,
                                                      int dead_ofs, double *evals, double2 *evecs,
                                                      int max_sweeps, double rel_tol) {
     typedef typename std::conditional<std::is_same<T, float>::value, float2, double2>::type T2;
@@ -565,7 +566,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2 *G, int m, const in
 // eigenvectors are V0 V1.  Same result as FP64 sweeps from the start, with
 // most rotations at the FP32 rate.
 constexpr int JMIX_MAX = 64;
-__global__ void __launch_bounds__(256) jacobi_mixed_kernel(const double2 *G, int m, const int *dead, int dead_stride,
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_mixed_kernel(const double2 *G, int m, const int *dead, int dead_stride,
                                                            int dead_ofs, double *evals, double2 *evecs,
                                                            int max_sweeps, double rel_tol) {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -1876,15 +1877,15 @@ struct Solver {
             MB_LAUNCH_E(KN_SMALL, alive_mask_kernel<<<(np + 63) / 64, 64, 0, s>>>(d_alive, kd, ofs, M, b, nch, m, np, d_mask));
         if (mixed) {
             cuda(smem_limit_once((const void *)jacobi_mixed_kernel, h->device, h->smem_optin));
-            MB_LAUNCH_E(KN_JACOBI, (jacobi_mixed_kernel<<<np, 256, smemx, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
+            MB_LAUNCH_E(KN_JACOBI, (jacobi_mixed_kernel<<<np, kJacobiThreads, smemx, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
                                                                                d_evals, d_Y, 30, tol)));
         } else if (vs) {
             cuda(smem_limit_once((const void *)jacobi_kernel<true, T>, h->device, h->smem_optin));
-            MB_LAUNCH_E(KN_JACOBI, (jacobi_kernel<true, T><<<np, 256, smem2, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
+            MB_LAUNCH_E(KN_JACOBI, (jacobi_kernel<true, T><<<np, kJacobiThreads, smem2, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
                                                                                   d_evals, d_Y, 30, tol)));
         } else {
             cuda(smem_limit_once((const void *)jacobi_kernel<false, T>, h->device, h->smem_optin));
-            MB_LAUNCH_E(KN_JACOBI, (jacobi_kernel<false, T><<<np, 256, smem1, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
+            MB_LAUNCH_E(KN_JACOBI, (jacobi_kernel<false, T><<<np, kJacobiThreads, smem1, s>>>(d_G, m, masked ? d_mask : nullptr, LD, 0,
                                                                                    d_evals, d_Y, 30, tol)));
         }
     }
