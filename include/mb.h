@@ -190,15 +190,19 @@ typedef struct {
 } mb_solve_opts;
 
 /* Lowest `nbands` roots of H c = eps S c at every k-point (§II.C).
- *   prec   MB_FP64: all applies in double ("plain").  MB_FP32 / MB_BF16:
- *          applies in that precision, Gram-Schmidt and Rayleigh-Ritz in
- *          double, then FP64 polish cycles until the FP64 residual < tol.
+ *   prec   MB_FP64: every step in double ("plain").  MB_FP32 / MB_BF16:
+ *          bulk cycles with every vector step in FP32 (applies in that
+ *          precision, Gram products on the tensor cores, small dense
+ *          problems in FP32 or FP64), then finish cycles with FP64 roots
+ *          until the FP64 residual < tol.
  *   tol    residual tolerance ||H x - eps S x||_{S^-1} (Ha)
  *   evals  host, nk*nbands doubles, ascending per k
  *   evecs  optional device pointer (NULL: not returned): nk blocks of
  *          nbands double2 vectors, block ik at offset sum_{i<ik} nbands*nb*ldg(i)
  *   sopts  optional (NULL: defaults); info optional.
- * Returns MB_ENOTCONV (evals still written) if max_cycles is reached. */
+ * Returns MB_ENOTCONV (evals still written) if max_cycles is reached,
+ * MB_ETIMEOUT if a tensor-core kernel's bounded device wait expired (its
+ * products are then not valid and the solve stops). */
 int mb_eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals,
                 void *evecs, const mb_solve_opts *sopts, mb_solve_info *info,
                 void *stream);

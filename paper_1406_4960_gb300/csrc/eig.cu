@@ -2275,11 +2275,13 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
             S.applies += applies_per_cycle[gi];
         }
         S.cuda(cudaMemcpyAsync(res.data(), S.d_res, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, s));
-        int tcerr = 0;
+        int tcerr = 0, tcerr_apply = 0;
         S.cuda(cudaMemcpyAsync(&tcerr, S.d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (h->d_tcerr)        // the projector contractions of MB_BF16 applies
+            S.cuda(cudaMemcpyAsync(&tcerr_apply, h->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
         S.cuda(cudaStreamSynchronize(s));
         if (S.rc) break;
-        if (tcerr) {           // a tensor-core kernel's bounded wait ran out: its products are not valid
+        if (tcerr || tcerr_apply) {   // a tensor-core kernel's bounded wait ran out: its products are not valid
             S.rc = MB_ETIMEOUT;
             break;
         }
