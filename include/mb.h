@@ -40,7 +40,7 @@ enum {
     MB_ENOTCONV = 3,    /* eigensolver did not reach tol within max_cycles */
     MB_ETIMEOUT = 4,    /* a bounded device-side wait expired */
     MB_ECUDA = 5,       /* a CUDA runtime call failed (see mb_last_cuda_error) */
-    MB_EUNSUPPORTED = 6 /* valid request this build does not implement */
+    MB_EUNSUPPORTED = 6 /* valid request that the library does not implement */
 };
 
 /* Arithmetic of an apply.  MB_FP64: every step in double.  MB_FP32: B-spline
