@@ -58,8 +58,16 @@ def _small_slab_2s():
     return dataclasses.replace(w, atoms=atoms, name="slab2s-small")
 
 
+def _order(w, k):
+    # B-splines of order k with k Gauss points per interval: every order other
+    # than 6 takes the radix-2 plane kernel and the order-k banded kernels
+    return dataclasses.replace(w, order=k, nquad=k, name="%s-k%d" % (w.name, k))
+
+
 CASES = {
     "tiny": lambda: W.tiny(),
+    "tiny-k8": lambda: _order(W.tiny(), 8),
+    "slab-small-k4": lambda: _order(_small_slab(), 4),
     "slab-small": _small_slab,
     "graphene-small": _small_graphene,
     "kbatch-small": _small_kbatch,

@@ -54,6 +54,30 @@ def test_eigsolve_tiny_matches_dense(mbmod, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_eigsolve_order_4_matches_dense(mbmod, prec):
+    """Order-4 B-splines (radix-2 plane kernel, order-4 banded kernels)."""
+    w = dataclasses.replace(W.tiny(), order=4, nquad=4, name="tiny-k4")
+    h = mbmod.Handle.from_workload(w)
+    ev, info = h.eigsolve(w.nbands, 1e-7, prec)
+    m, ref = _dense_ref(w, 0, w.nbands)
+    assert np.abs(ev[0] - ref).max() < EV_TOL, (ev[0], ref)
+    h.close()
+
+
+def test_eigsolve_bf16_matches_dense(mbmod):
+    """MB_BF16 solves (BF16 projector contractions in the bulk applies) reach
+    the same FP64-accurate roots: the finish cycles use FP64 applies."""
+    w = _small_slab()
+    h = mbmod.Handle.from_workload(w)
+    ev, info = h.eigsolve(w.nbands, 1e-7, "bf16")
+    for ik in range(w.nk):
+        m, ref = _dense_ref(w, ik, w.nbands)
+        assert np.abs(ev[ik] - ref).max() < EV_TOL, (ik, ev[ik] - ref)
+    assert info.finish_cycles >= 1
+    h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_eigsolve_slab_small_all_k(mbmod, prec):
     w = _small_slab()
     h = mbmod.Handle.from_workload(w)
