@@ -24,6 +24,14 @@ int mb_debug_gemm_bf16(const void *A, const void *Bt, float *D, int M, int N, in
  * wait expired. */
 int mb_debug_gram_tc32(const void *V, long long n, int ma, int mb, int nsplit, double *G, void *stream);
 
+/* C = A Y with the eigensolver's float-float rotation kernel (FP64 vectors,
+ * products and sums in pairs of FP32 numbers).  A: device FP64 complex
+ * (interleaved), ma vectors of n elements one after another; Y: host ma x mc
+ * complex (interleaved doubles), row i = the coefficients of A_i; C: device,
+ * mc vectors of n elements, overwritten.  1 <= ma <= 112, 1 <= mc <= 128.
+ * Allocates and frees its own device buffers; MB_EINVAL for bad sizes. */
+int mb_debug_combine_ff(const void *A, const double *Y, long long n, int ma, int mc, void *C, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

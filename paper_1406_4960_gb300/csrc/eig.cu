@@ -1258,6 +1258,87 @@ __global__ void __launch_bounds__(128) gram_tc32_kernel(const EigK *ks, int nch,
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
+// Float-float arithmetic (a value is hi + lo, two FP32 numbers with
+// |lo| <= ulp(hi)/2): Knuth's two-sum and the FMA two-product give the
+// rounding error of a sum or product exactly, so sums of products carry
+// about 48 significant bits on the FP32 pipe.
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ FF ff_from(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+// (the _rn intrinsics are never contracted into FMAs, which would break the
+// exact error terms)
+__device__ __forceinline__ void ff_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// acc += u v (u, v float-float; the lo*lo term is below the result's precision)
+__device__ __forceinline__ void ff_mac(FF &acc, FF u, FF v) {
+    const float ph = __fmul_rn(u.h, v.h);
+    const float pl = fmaf(u.h, v.h, -ph) + fmaf(u.h, v.l, u.l * v.h);
+    float s, e;
+    ff_two_sum(acc.h, ph, s, e);
+    acc.h = s;
+    acc.l += e + pl;
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.h, -a.l}; }
+
+// C_j = beta C_j + alpha sum_i A_i Y[i][j] on FP64 vectors with the products
+// and sums in float-float arithmetic (the mixed solver's FP64 root rotations:
+// FP64-level results at the FP32 rate).  Same layout and launch as
+// combine2_kernel.
+template <int JC>
+__global__ void __launch_bounds__(256) combine_ff_kernel(const EigK *ks, int nch, VSet A, VSet C,
+                                                         const double2 *Y, double alpha, double beta) {
+    __shared__ float4 Ys[JMAX][JC];     // (re.h, re.l, im.h, im.l)
+    const int prob = blockIdx.y;
+    const int k = prob / nch, ch = prob % nch;
+    const EigK d = ks[k];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = t < d.nvec;
+    const int ma = A.count(), mc = C.count();
+    const double2 *y = Y + (size_t)prob * LD * LD;
+    for (int j0 = 0; j0 < mc; j0 += JC) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < ma * JC; e += blockDim.x) {
+            const int i = e / JC, jj = e % JC;
+            const double2 yv = j0 + jj < mc ? y[i * LD + j0 + jj] : make_double2(0.0, 0.0);
+            const FF re = ff_from(yv.x), im = ff_from(yv.y);
+            Ys[i][jj] = make_float4(re.h, re.l, im.h, im.l);
+        }
+        __syncthreads();
+        if (!live) continue;
+        FF ar[JC], ai[JC];
+#pragma unroll
+        for (int jj = 0; jj < JC; ++jj) ar[jj] = ai[jj] = FF{0.f, 0.f};
+        for (int i = 0; i < ma; ++i) {
+            const double2 av = d.base[(long long)A.at(i, ch) * d.nvec + t];
+            const FF xr = ff_from(av.x), xi = ff_from(av.y);
+#pragma unroll
+            for (int jj = 0; jj < JC; ++jj) {
+                const float4 w = Ys[i][jj];
+                const FF yr{w.x, w.y}, yi{w.z, w.w};
+                ff_mac(ar[jj], xr, yr);          // re += xr yr - xi yi
+                ff_mac(ar[jj], ff_neg(xi), yi);
+                ff_mac(ai[jj], xr, yi);          // im += xr yi + xi yr
+                ff_mac(ai[jj], xi, yr);
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < JC; ++jj) {
+            if (j0 + jj >= mc) break;
+            double2 *c = d.base + (long long)C.at(j0 + jj, ch) * d.nvec + t;
+            const double2 v = make_double2(alpha * ((double)ar[jj].h + (double)ar[jj].l),
+                                           alpha * ((double)ai[jj].h + (double)ai[jj].l));
+            *c = beta == 0.0 ? v : make_double2(beta * c->x + v.x, beta * c->y + v.y);
+        }
+    }
+}
+
 // C_j = beta C_j + alpha sum_i A_i Y[i][j]: one element t per thread, JC
 // output columns at a time with their coefficients staged in shared memory.
 template <int JC, bool F32>
@@ -1642,8 +1723,15 @@ struct Solver {
                                                                                            lower ? 1 : 0));
     }
     void combine(int nch, VSet A, VSet C, const double2 *Y, double alpha, double beta, bool f32 = false) {
-        if (f32) combine_t<true>(nch, A, C, Y, alpha, beta);
-        else combine_t<false>(nch, A, C, Y, alpha, beta);
+        if (f32) {
+            combine_t<true>(nch, A, C, Y, alpha, beta);
+        } else if (gs32 && C.count() > 8) {
+            // mixed solver, FP64 vectors: the root rotations in float-float
+            const dim3 grid((unsigned)((nmax + 255) / 256), nk * nch);
+            MB_LAUNCH_E(KN_COMBINE, (combine_ff_kernel<12><<<grid, 256, 0, s>>>(d_k, nch, A, C, Y, alpha, beta)));
+        } else {
+            combine_t<false>(nch, A, C, Y, alpha, beta);
+        }
     }
     template <bool F32> void combine_t(int nch, VSet A, VSet C, const double2 *Y, double alpha, double beta) {
         const dim3 grid((unsigned)((nmax + 255) / 256), nk * nch);
@@ -2398,4 +2486,43 @@ extern "C" int mb_debug_gram_tc32(const void *V, long long n, int ma, int mb, in
             G[2 * ((size_t)i * mb + j) + 1] = hG[(size_t)i * LD + j].y;
         }
     return herr ? MB_ETIMEOUT : MB_OK;
+}
+
+// Self-test hook for the float-float rotation kernel: C = A Y for ma FP64
+// complex device vectors A of length n (stored one after another) and a host
+// ma x mc complex matrix Y (interleaved doubles, row i = coefficients of
+// A_i); C: mc device vectors of length n, overwritten.
+extern "C" int mb_debug_combine_ff(const void *A, const double *Y, long long n, int ma, int mc, void *C,
+                                   void *stream) {
+    using namespace mb;
+    if (!A || !Y || !C || n < 1 || ma < 1 || mc < 1 || ma > JMAX || mc > LD) return MB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    // one work array holding A then C, addressed through index sets
+    double2 *base = nullptr, *Yd = nullptr;
+    EigK *dk = nullptr;
+    cudaError_t e = cudaMalloc(&base, sizeof(double2) * (size_t)(ma + mc) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&Yd, sizeof(double2) * LD * LD);
+    if (e == cudaSuccess) e = cudaMalloc(&dk, sizeof(EigK));
+    std::vector<double2> hY((size_t)LD * LD, make_double2(0.0, 0.0));
+    for (int i = 0; i < ma; ++i)
+        for (int j = 0; j < mc; ++j)
+            hY[(size_t)i * LD + j] = make_double2(Y[2 * ((size_t)i * mc + j)], Y[2 * ((size_t)i * mc + j) + 1]);
+    EigK hk{};
+    hk.base = base;
+    hk.nvec = n;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base, A, sizeof(double2) * (size_t)ma * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Yd, hY.data(), sizeof(double2) * LD * LD, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dk, &hk, sizeof(EigK), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const dim3 grid((unsigned)((n + 255) / 256), 1);
+        combine_ff_kernel<12><<<grid, 256, 0, s>>>(dk, 1, vs(0, ma), vs(ma, mc), Yd, 1.0, 0.0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(C, base + (size_t)ma * n, sizeof(double2) * (size_t)mc * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(base);
+    cudaFree(Yd);
+    cudaFree(dk);
+    return e == cudaSuccess ? MB_OK : MB_ECUDA;
 }

@@ -26,6 +26,8 @@ def lib():
     l.mb_debug_gemm_bf16.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int] * 3 + [ctypes.c_void_p]
     l.mb_debug_gram_tc32.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    l.mb_debug_combine_ff.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_longlong, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     return l
 
 
@@ -72,3 +74,28 @@ def test_tc_gram_rejects_bad_sizes(lib):
     assert lib.mb_debug_gram_tc32(x.data_ptr(), 4, 1, 65, 1, p, None) == 1      # 2 mb > 128
     assert lib.mb_debug_gram_tc32(x.data_ptr(), 4, 65, 1, 1, p, None) == 1      # ma > 64
     assert lib.mb_debug_gram_tc32(x.data_ptr(), 0, 1, 1, 1, p, None) == 1       # empty vectors
+
+
+# (ma, mc, n): the finish phase's root rotations (41 -> 36, 36 -> 36), a
+# partial column group, a ragged element count
+@pytest.mark.parametrize("ma,mc,n", [(41, 36, 23040), (36, 36, 5000), (7, 13, 999), (1, 9, 33)])
+def test_float_float_rotation_matches_fp64(lib, ma, mc, n):
+    """The mixed solver's FP64 root rotations run in float-float arithmetic;
+    they must agree with an FP64 product to float-float accuracy: products
+    keep 48 bits and each output sums 4 ma of them, so the error stays below
+    ~4 ma 2^-48 of sum |a||y| (2e-12 here; the FP32 level would be 6e-8)."""
+    rng = np.random.default_rng(ma * 100 + mc)
+    A = rng.standard_normal((ma, n)) + 1j * rng.standard_normal((ma, n))
+    A[:, ::5] *= 1e-6                                  # a spread of magnitudes
+    Y = rng.standard_normal((ma, mc)) + 1j * rng.standard_normal((ma, mc))
+    Y[0, :] *= 1e3
+    Ad = torch.from_numpy(A).cuda()
+    Cd = torch.full((mc, n), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
+    Yh = np.ascontiguousarray(Y).view(np.float64)
+    rc = lib.mb_debug_combine_ff(Ad.data_ptr(), Yh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n, ma, mc,
+                                 Cd.data_ptr(), None)
+    assert rc == 0
+    C = Cd.cpu().numpy()
+    ref = Y.T @ A
+    bound = 2e-12 * (np.abs(Y).T @ np.abs(A))
+    assert np.all(np.abs(C - ref) <= bound)
