@@ -1382,21 +1382,6 @@ __global__ void __launch_bounds__(256) combine2_kernel(const EigK *ks, int nch, 
     }
 }
 
-// G <- the Hermitian matrix of its lower triangle (keeps the couplings
-// K^H (H X), which use the roots' HX, over X^H (H K))
-__global__ void herm_lower_kernel(double2 *G, int m) {
-    double2 *g = G + (size_t)blockIdx.y * LD * LD;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m * m) return;
-    const int i = e / m, j = e % m;
-    if (i < j) {
-        const double2 v = g[j * LD + i];
-        g[i * LD + j] = make_double2(v.x, -v.y);
-    } else if (i == j) {
-        g[i * LD + i].y = 0.0;
-    }
-}
-
 // [X|K]^H H [X|K] (and the S counterpart) when X holds Ritz vectors of the
 // last Rayleigh-Ritz (X^H H X = diag(eps), X^H S X = I): rows i >= M come
 // from the products KH = K^H H [X|K], KS = K^H S [X|K] (row i - M), the
