@@ -262,7 +262,9 @@ void mb_server_destroy(mb_server *srv);
 
 /* ---- instrumentation ------------------------------------------------
  * Every kernel the library launches is counted per handle.  With profiling
- * on, each launch is also bracketed by CUDA events on its own stream; the
+ * on (mb_set_profiling: 0 off, 1 every kernel, 2 the plane kernel only, whose
+ * two events per apply leave the rest of the step undisturbed), each
+ * profiled launch is also bracketed by CUDA events on its own stream; the
  * per-kernel totals accumulate until mb_profile_reset.  Kernel ids:
  * 0 plane, 1 epilogue, 2 proj, 3 coef, 4 backproj, 5 banded, 6 gram,
  * 7 combine, 8 jacobi, 9 small, 10 vec, 11 gram32, 12 combine32 (the FP32

@@ -110,7 +110,7 @@ struct mb_handle {
     std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
     // launch accounting (always on) and optional per-kernel event timing
     long long launches = 0;
-    bool profiling = false;
+    int profiling = 0;               // 0 off, 1 every kernel, 2 the plane kernel only
     struct ProfEvent { int kernel; cudaEvent_t a, b; };
     std::vector<ProfEvent> prof_pending;
     std::vector<cudaEvent_t> prof_pool;

@@ -28,10 +28,15 @@ const char *const kKernelNames[KN_COUNT] = {
     "plane", "epilogue", "proj", "coef", "backproj", "banded", "gram", "combine",
     "jacobi", "small", "vec", "gram32", "combine32"};
 
+// whether a launch of `kernel` is bracketed by events in the current mode
+static bool prof_on(const mb_handle *h, int kernel) {
+    return h->profiling == 1 || (h->profiling == 2 && kernel == KN_PLANE);
+}
+
 void prof_begin(mb_handle *h, cudaStream_t s, int kernel, cudaEvent_t *a) {
     h->launches++;
     *a = nullptr;
-    if (!h->profiling) return;
+    if (!prof_on(h, kernel)) return;
     if (h->prof_pool.empty()) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -40,11 +45,10 @@ void prof_begin(mb_handle *h, cudaStream_t s, int kernel, cudaEvent_t *a) {
     *a = h->prof_pool.back();
     h->prof_pool.pop_back();
     cudaEventRecord(*a, s);
-    (void)kernel;
 }
 
 void prof_end(mb_handle *h, cudaStream_t s, int kernel, cudaEvent_t a) {
-    if (!h->profiling || !a) return;
+    if (!prof_on(h, kernel) || !a) return;
     cudaEvent_t b;
     if (h->prof_pool.empty()) {
         if (cudaEventCreate(&b) != cudaSuccess) return;
@@ -80,7 +84,8 @@ extern "C" {
 int mb_set_profiling(mb_handle *h, int on) {
     if (!h) return MB_EINVAL;
     int rc = prof_collect(h);
-    h->profiling = on != 0;
+    if (on < 0 || on > 2) return rc ? rc : MB_EINVAL;
+    h->profiling = on;
     return rc;
 }
 
