@@ -7,15 +7,21 @@
 //   B  roots split into blocks of b; each block does Rayleigh-Ritz on
 //      [X_b | K_b] and keeps the b Ritz pairs of maximum overlap with its
 //      inputs (plus any new lower root).
-// after which X is S-orthonormalized (Cholesky-QR, twice) and rotated to
-// Ritz vectors.  Krylov vectors come from A = P (H - theta S), P the banded
-// per-G solve (T(G) + c S)^-1, S-orthogonalized by classical Gram-Schmidt
-// applied twice.  Every step runs for all k-points in one launch.
+// after which X is S-orthonormalized and rotated to Ritz vectors in one
+// Cholesky-QR + Rayleigh-Ritz step.  Krylov vectors come from
+// A = P (H - theta S), P the banded per-G solve (T(G) + c S)^-1,
+// S-orthogonalized by classical Gram-Schmidt applied twice.  Every step runs
+// for all k-points in one launch; from the second cycle of each phase a
+// grand cycle is one CUDA graph launch.
 //
-// Precision: the H applies run in the requested precision; Gram products,
-// Jacobi, Cholesky-QR, residuals and the banded S / P solves are FP64.  In
-// the mixed mode the last cycles switch the applies to FP64 (the FP64
-// residual is the convergence test).
+// Precision.  MB_FP64: everything in FP64.  Mixed (MB_FP32 / MB_BF16): bulk
+// cycles on FP32 vectors only (FP32 applies in place on the chain slots,
+// Gram products on the tensor cores with a TF32 hi + lo split, FP32 S
+// products, preconditioner solves, rotations, residuals, Cholesky and
+// Jacobi); then finish cycles with FP64 roots: FP64 applies of the roots,
+// FP64 Grams, Cholesky and Jacobi (FP32 sweeps first), and the root
+// rotations in float-float arithmetic, while the chains stay FP32.  The FP64
+// residual is the convergence test.
 #include <algorithm>
 #include <chrono>
 #include <tuple>
