@@ -1605,9 +1605,10 @@ struct Solver {
     int prec;           // precision of the H applies that build Krylov vectors
     bool fp64_roots = false;   // finish phase: HX of the roots recomputed in FP64 every cycle
     // mixed precision: the Krylov Gram-Schmidt runs on FP32 copies (v32), and
-    // the small Rayleigh-Ritz problems of cycles A and B use the FP64 S-Gram
-    // of their basis (a pencil), so that their result does not depend on how
-    // orthogonal the Krylov vectors came out
+    // the small Rayleigh-Ritz problems of cycles A and B use the S-Gram of
+    // their basis (a pencil; FP32 in the bulk cycles, FP64 in the finish
+    // phase), so that their result does not depend on how orthogonal the
+    // Krylov vectors came out
     bool gs32 = false;
     // bulk cycles (lowp()): X, HX and SX live only in the FP32 copies, and
     // the chains' slot s of chain ch is at o32K + s*nc + ch (likewise SK, HK),
