@@ -68,7 +68,10 @@ size_t footprint_of(const mb_handle &h, int nbands, int prec) {
     const size_t nvecs = 3 * (size_t)std::max(mA, nblk * b) + 2 * (size_t)nblk * mB + 4 * nc + 3 * (size_t)mA +
                          (size_t)nblk * mB;
     size_t work = nvecs * vec_bytes + 2 * (size_t)std::max(M, nc) * vec_bytes / 2;
-    if (prec != MB_FP64) work += (size_t)(2 * M + nc * (1 + 2 * kd)) * vec_bytes / 2;   // FP32 Gram-Schmidt copies
+    // FP32 vectors of the mixed solver: X, SX, HX, the chain inputs, K, SK and
+    // HK of every chain, two scratch sets
+    if (prec != MB_FP64)
+        work += (size_t)(3 * M + nc * (1 + 3 * kd) + 2 * std::max(M, nblk * b)) * vec_bytes / 2;
     const size_t LD = 128;
     work += (size_t)h.kp.size() * nc * LD * LD * 16 * (prec != MB_FP64 ? 6 : 3) + (size_t)h.kp.size() * LD * LD * 16 * 3;
     work += (size_t)std::max<size_t>(304, h.kp.size() * nc) * 112 * 112 * 16;
