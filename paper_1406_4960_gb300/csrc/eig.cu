@@ -99,7 +99,7 @@ __global__ void gram_reduce_kernel(const double2 *part, int nsplit, int ma, int 
 __global__ void copy_kernel(const EigK *ks, int nch, VSet S, VSet D, int mode) {
     // grid: (blocks along the vector, vector of the set, problem)
     // mode 0: base -> base; 1: base -> stage (to float); 2: stage -> base (to double);
-    // 3: base -> v32 (to float); 4: v32 -> base (to double); 5: stage -> v32; 6: v32 -> v32
+    // 3: base -> v32 (to float); 4: v32 -> base (to double); 5: v32 -> v32
     const int prob = blockIdx.z, i = blockIdx.y;
     const int k = prob / nch, ch = prob % nch;
     const EigK d = ks[k];
@@ -113,7 +113,6 @@ __global__ void copy_kernel(const EigK *ks, int nch, VSet S, VSet D, int mode) {
         else if (mode == 2) d.base[di] = make_double2((double)d.stage[si].x, (double)d.stage[si].y);
         else if (mode == 3) d.v32[di] = make_float2((float)d.base[si].x, (float)d.base[si].y);
         else if (mode == 4) d.base[di] = make_double2((double)d.v32[si].x, (double)d.v32[si].y);
-        else if (mode == 5) d.v32[di] = d.stage[si];
         else d.v32[di] = d.v32[si];
     }
 }
@@ -2020,7 +2019,7 @@ struct Solver {
     void rotate_set(const double2 *Y, int m, const VSet *V32 = nullptr) {
         if (lowp()) {
             combine(1, *V32, vs(o32T, M), Y, 1.0, 0.0, true);
-            copy(1, vs(o32T, M), vs(o32X, M), 6);
+            copy(1, vs(o32T, M), vs(o32X, M), 5);
             apply32(o32X, o32HX, M);
             bandS(o32X, o32SX, M, true);
             return;
@@ -2108,8 +2107,8 @@ struct Solver {
             // each) first: the rotation reads the old X
             combine(nblk, x32, vs(o32T, b, b), d_Ysel, 1.0, 0.0, true);
             combine(nblk, hx32, vs(o32T2, b, b), d_Ysel, 1.0, 0.0, true);
-            copy(1, vs(o32T, M), vs(o32X, M), 6);
-            copy(1, vs(o32T2, M), vs(o32HX, M), 6);
+            copy(1, vs(o32T, M), vs(o32X, M), 5);
+            copy(1, vs(o32T2, M), vs(o32HX, M), 5);
             bandS(o32X, o32SX, M, true);
         } else {
             combine(nblk, vs(oVB, mB, mB), vs(oV, b, b), d_Ysel, 1.0, 0.0);
