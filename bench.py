@@ -37,11 +37,39 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Hψ GB/s & eigensolves/s at 1e-6 Ha vs plain FP64 GPU; p50/p99 solve latency"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3   # SMs x FP32 lanes x 2 flop x max SM clock (GHz)
-# dram bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one FP32
-# plane-kernel launch of this workload, from an ncu capture of the current
-# kernel (None whenever the kernel changes until it is captured again)
-PLANE_TRAFFIC_BYTES = 25.20e6
+# The plane kernel's sources: its DRAM traffic (from an ncu capture, recorded
+# in the profile summary below) is reported only while these are unchanged.
+PLANE_SOURCES = ("plane_reg.cu", "apply_common.cuh", "cplx.cuh", "apply.cu")
+PLANE_PROFILES = {
+    "slab": "profiles/plane_reg_kernel_slab_fp32.md",
+    "graphene": "profiles/plane_reg_kernel_graphene_fp32.md",
+}
+
+
+def plane_sources_hash():
+    """sha256 (first 16 hex digits) of the plane kernel's source files."""
+    import hashlib
+    d = hashlib.sha256()
+    for f in PLANE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1406_4960_gb300", "csrc", f), "rb") as fh:
+            d.update(fh.read())
+    return d.hexdigest()[:16]
+
+
+def plane_traffic(workload):
+    """(bytes per launch, note): dram__bytes_read.sum + dram__bytes_write.sum of
+    one plane-kernel launch from the committed ncu summary, or None when the
+    summary is missing or was taken on other kernel sources."""
+    import re
+    path = os.path.join(ROOT, PLANE_PROFILES.get(workload, ""))
+    if not os.path.isfile(path):
+        return None, "no ncu summary for this workload"
+    m = re.search(r"traffic per launch: (\d+) bytes; kernel sources sha256 = ([0-9a-f]{16})", open(path).read())
+    if not m:
+        return None, "ncu summary has no traffic line"
+    if m.group(2) != plane_sources_hash():
+        return None, "kernel sources changed since the ncu capture"
+    return float(m.group(1)), "ncu capture of the current kernel (%s)" % PLANE_PROFILES[workload]
 
 
 def _peaks():
@@ -198,43 +226,93 @@ def eig_bench(h, w, args):
     return out
 
 
-def kbatch_bench(mb, W, local, args):
-    """Batched k-points: the 2x2 graphene cell with 64 wedge k-points x 24 bands.
-    The plane-kernel launch shape is autotuned for the batch, then one FP32 H
-    apply of all 64 k-points (one launch sequence) is timed; with
-    --kbatch-solve, one mixed-precision eigensolve of all 64 k-points (grand
-    cycles replayed as CUDA graphs) is timed too."""
-    import torch
+def golden(name):
+    """Oracle eigenvalues written by a tests/golden/make_*.py script (which
+    calls only oracle/): {k index: values}, or None if the file is absent."""
+    path = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(path):
+        return None
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    if name == "graphene_eigs.txt":
+        return {0: np.array(rows[0], dtype=float)}
+    return {int(r[0]): np.array(r[1:], dtype=float) for r in rows}
+
+
+def solve_record(h, nbands, prec, ref, reps=1):
+    """Wall time, cycles, residual and error vs oracle eigenvalues of `reps`
+    eigensolves of every k-point of a handle."""
+    times, ev, info = [], None, None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ev, info = h.eigsolve(nbands, 1e-6, prec)
+        times.append(time.perf_counter() - t0)
+    err = None
+    if ref:
+        err = float(max(np.abs(ev[k] - v).max() for k, v in ref.items()))
+    return {"seconds": float(np.median(times)), "solves_per_s": 1.0 / float(np.median(times)),
+            "cycles": info.cycles, "finish_cycles": info.finish_cycles, "max_residual": info.max_residual,
+            "max_abs_err_vs_oracle_ha": err,
+            "oracle_kpoints": None if not ref else sorted(ref)}, ev
+
+
+def graphene_bench(mb, W, local, args, timed, peak32):
+    """Config 2: the 4x4 graphene cell (1417 G, 80 splines, 64x64 grid, 128
+    projectors, 80 bands).  FP32, FP64 and BF16-projector applies of the
+    80-band block (the plane kernel's roofline from the FP32 steps), then a
+    mixed-precision and a plain-FP64 eigensolve of 80 roots against the
+    oracle's eigenvalues (tests/golden/graphene_eigs.txt)."""
+    w = W.graphene()
+    h = mb.Handle.from_workload(w, device=local)
+    steps = 10
+    ms32, launches, prof_plane = timed(h, w, "fp32", steps, 3, profile=2, sync_ranks=False)
+    ms64, _, _ = timed(h, w, "fp64", 3, 2, sync_ranks=False)
+    msbf, _, _ = timed(h, w, "bf16", 5, 2, sync_ranks=False)
+    _, _, prof = timed(h, w, "fp32", 5, 1, profile=1, sync_ranks=False)
+    b32, f32 = workload_sizes(h, w, "fp32")
+    b64, _ = workload_sizes(h, w, "fp64")
+    out = {"workload": "graphene: 4x4 cell, 32 atoms, Ecut 30 Ha, 64x64 grid, 80 B-splines, Gamma, 80 bands",
+           "fp32": {"value": b32 / (ms32 * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms32,
+                    "kernels_ms_per_step": {k: v[0] / 5 for k, v in prof.items()},
+                    "gpu_launches_per_step": int(launches) // steps},
+           "fp64": {"value": b64 / (ms64 * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms64},
+           "bf16": {"value": b32 / (msbf * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": msbf},
+           "roofline": plane_roofline(prof_plane, f32, steps, ms32, "plane_reg_kernel<float, 64, 64, 6>",
+                                      "graphene", peak32)}
+    if not args.no_eig:
+        ref = golden("graphene_eigs.txt")
+        mixed, e32 = solve_record(h, w.nbands, "fp32", ref)
+        plain, e64 = solve_record(h, w.nbands, "fp64", ref)
+        out["eigsolve"] = {"tol_ha": 1e-6, "roots": w.nbands, "mixed": mixed, "fp64": plain,
+                           "mixed_speedup_vs_fp64": plain["seconds"] / mixed["seconds"],
+                           "mixed_vs_fp64_max_diff_ha": float(np.abs(e32 - e64).max())}
+    h.close()
+    return out
+
+
+def kbatch_bench(mb, W, local, args, timed, peak32):
+    """Config 3: the 2x2 graphene cell with 64 wedge k-points x 24 bands.  The
+    plane-kernel launch shape is autotuned for the batch, then one FP32 H
+    apply of all 64 k-points (one launch sequence) is timed; then one
+    mixed-precision and one plain-FP64 eigensolve of all 64 k-points (grand
+    cycles replayed as CUDA graphs), checked against the oracle's eigenvalues
+    at four of the k-points (tests/golden/kbatch_eigs.txt)."""
     w = W.kbatch()
     h = mb.Handle.from_workload(w, device=local)
     tune = h.autotune(w.nbands, "fp32")
-    iks = list(range(w.nk))
-    Xs, Ys = [], []
-    for ik in iks:
-        ng, nb, ldg = h.sizes(ik)
-        Xs.append(torch.from_numpy(W.random_block(w.nbands, nb, ng, seed=700 + ik, ld=ldg)).to(torch.complex64).cuda())
-        Ys.append(torch.zeros_like(Xs[-1]))
-    stream = torch.cuda.current_stream()
-    for _ in range(3):
-        h.apply_H_batch(iks, Xs, Ys, "fp32", stream)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    reps = 10
-    for _ in range(reps):
-        h.apply_H_batch(iks, Xs, Ys, "fp32", stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+    steps = 10
+    ms, launches, prof_plane = timed(h, w, "fp32", steps, 3, profile=2, sync_ranks=False)
     byts, flops = workload_sizes(h, w, "fp32")
     out = {"workload": "kbatch: 2x2 graphene, Ecut 30 Ha, 32x32 grid, 100 B-splines, 64 k x 24 bands",
            "autotune": tune, "apply_ms": ms, "apply_gbs": byts / (ms * 1e-3) / 1e9,
-           "plane_flops_per_apply_ms_tflops": flops / (ms * 1e-3) / 1e12}
-    if args.kbatch_solve:
-        t0 = time.perf_counter()
-        ev, info = h.eigsolve(w.nbands, 1e-6, "fp32")
-        out["eigsolve"] = {"seconds": time.perf_counter() - t0, "cycles": info.cycles,
-                           "max_residual": info.max_residual}
+           "gpu_launches_per_apply": int(launches) // steps,
+           "roofline": plane_roofline(prof_plane, flops, steps, ms, "plane_reg_kernel<float, 32, 32, 6>",
+                                      "kbatch", peak32)}
+    if not args.no_kbatch_solve:
+        ref = golden("kbatch_eigs.txt")
+        mixed, _ = solve_record(h, w.nbands, "fp32", ref)
+        plain, _ = solve_record(h, w.nbands, "fp64", ref)
+        out["eigsolve"] = {"tol_ha": 1e-6, "roots": w.nbands, "kpoints": w.nk, "mixed": mixed, "fp64": plain,
+                           "mixed_speedup_vs_fp64": plain["seconds"] / mixed["seconds"]}
     h.close()
     return out
 
@@ -307,8 +385,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(1),
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d single-k-point H applies of the 32-band block per step "
-                                   "(a bounded sample of the 4-k batched apply)" % 1},
+                         "sample": "per step: 1 single-k-point H apply of the 32-band block in FP64 "
+                                   "(the oracle; a bounded sample of the 4-k batched apply)"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": wall,
     }
@@ -318,7 +396,7 @@ def run_reference(args):
 def config_of(world):
     """The benchmark configuration (both arms report the same one)."""
     return {"workload": "slab: C(001)-like, 12 atoms, Ecut 25 Ha, 32x16 grid, 120 B-splines, 4 k, 32 bands",
-            "step": "one batched H apply, 4 k x 32 bands, FP32",
+            "step": "one batched H apply, 4 k x 32 bands (precision: the line's dtype)",
             "l2": "256 MB buffer written between timed steps (outside the events)",
             "parallelism": "replica per GPU" if world > 1 else "1 GPU"}
 
@@ -351,7 +429,38 @@ def job_gbs(bytes_per_rank, ms_max, world):
     return world * bytes_per_rank / (ms_max * 1e-3) / 1e9
 
 
+def probe_fp32_peak(lib, device):
+    """Measured FP32 FMA throughput of this GPU (TFLOP/s), or None."""
+    import ctypes
+    fn = lib.mb_probe_fp32_fma
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    if fn(int(device), 5, ctypes.byref(t), ctypes.byref(ms)) != 0:
+        return None
+    return t.value
+
+
+def plane_roofline(prof_plane, flops_per_step, steps, step_ms, kernel, workload, peak):
+    """Roofline object of the plane kernel from its CUDA-event totals inside
+    the timed steps (profiling mode 2)."""
+    if "plane" not in prof_plane:
+        return None
+    t, c = prof_plane["plane"]
+    per_launch_ms = t / c
+    launches_per_step = max(1, c // steps)
+    ach = flops_per_step / launches_per_step / (per_launch_ms * 1e-3) / 1e12
+    traffic, note = plane_traffic(workload)
+    derived = 152 * 128 * 2 * 2.070e-3
+    p = peak if peak else derived
+    return {"bound": "alu", "achieved": ach, "peak": p, "unit": "TFLOP/s", "frac": ach / p,
+            "traffic": traffic, "traffic_source": note, "kernel": kernel,
+            "peak_source": ("measured: FP32 FFMA loop on this GPU (mb_probe_fp32_fma), of measured"
+                            if peak else "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz (probe failed)"),
+            "kernel_ms": per_launch_ms, "share_of_step": t / steps / step_ms}
+
+
 def run_ours(args):
+    import ctypes
     import torch
     import torch.distributed as dist
     from paper_1406_4960_gb300 import mb, workloads as W
@@ -369,56 +478,59 @@ def run_ours(args):
         return max_over_ranks(x, world, "cuda")
 
     w = W.slab()
-    mb.load(build_if_missing=True)
-    lib = mb.load()
+    lib = mb.load(build_if_missing=True)
     h = mb.Handle.from_workload(w, device=local)
-    iks = list(range(w.nk))
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def blocks(prec, seed):
+    def blocks(hd, wd, prec, seed):
         dt = torch.complex128 if prec == "fp64" else torch.complex64
         Xs, Ys = [], []
-        for ik in iks:
-            ng, nb, ldg = h.sizes(ik)
-            x = W.random_block(w.nbands, nb, ng, seed=seed + ik, ld=ldg)
+        for ik in range(wd.nk):
+            ng, nb, ldg = hd.sizes(ik)
+            x = W.random_block(wd.nbands, nb, ng, seed=seed + ik, ld=ldg)
             Xs.append(torch.from_numpy(x).to(dt).cuda())
             Ys.append(torch.zeros_like(Xs[-1]))
         return Xs, Ys
 
-    def timed(prec, steps, warmup, profile=0):
+    def read_profile(hd):
+        prof = {}
+        lib.mb_set_profiling(hd._h, 0)
+        for kid in range(13):
+            t, c = ctypes.c_double(), ctypes.c_longlong()
+            lib.mb_profile_read(hd._h, kid, ctypes.byref(t), ctypes.byref(c))
+            if c.value:
+                prof[lib.mb_kernel_name(kid).decode()] = (t.value, c.value)
+        return prof
+
+    def timed(hd, wd, prec, steps, warmup, profile=0, sync_ranks=True):
         # profile: 0 none, 1 events around every kernel (a breakdown run),
         # 2 events around the plane kernel only (inside the timed steps)
-        Xs, Ys = blocks(prec, replica_seed(1000, rank))
+        iks = list(range(wd.nk))
+        Xs, Ys = blocks(hd, wd, prec, replica_seed(1000, rank))
         for _ in range(warmup):
-            h.apply_H_batch(iks, Xs, Ys, prec, stream)
+            hd.apply_H_batch(iks, Xs, Ys, prec, stream)
         torch.cuda.synchronize()
         if profile:
-            lib.mb_profile_reset(h._h)
-            lib.mb_set_profiling(h._h, profile)
-        n0 = lib.mb_launch_count(h._h)
+            lib.mb_profile_reset(hd._h)
+            lib.mb_set_profiling(hd._h, profile)
+        n0 = lib.mb_launch_count(hd._h)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        barrier()
+        if sync_ranks:
+            barrier()
         torch.cuda.synchronize()
         for i in range(steps):
             flush.zero_()                      # L2 flush outside the timed events
             ev[i][0].record(stream)
-            h.apply_H_batch(iks, Xs, Ys, prec, stream)
+            hd.apply_H_batch(iks, Xs, Ys, prec, stream)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
-        barrier()
-        launches = lib.mb_launch_count(h._h) - n0
+        if sync_ranks:
+            barrier()
+        launches = lib.mb_launch_count(hd._h) - n0
         ms = sum(a.elapsed_time(b) for a, b in ev) / steps
-        prof = {}
-        if profile:
-            import ctypes
-            lib.mb_set_profiling(h._h, 0)
-            for kid in range(13):
-                t, c = ctypes.c_double(), ctypes.c_longlong()
-                lib.mb_profile_read(h._h, kid, ctypes.byref(t), ctypes.byref(c))
-                if c.value:
-                    prof[lib.mb_kernel_name(kid).decode()] = (t.value, c.value)
-        return allmax(ms), launches, prof
+        prof = read_profile(hd) if profile else {}
+        return (allmax(ms) if sync_ranks else ms), launches, prof
 
     if args.eig_only:
         # one mixed and/or one plain-FP64 solve (for launch lists under ncu)
@@ -432,25 +544,37 @@ def run_ours(args):
             print(json.dumps({"eig_only": prec, "seconds": time.perf_counter() - t0, "cycles": info.cycles}))
         h.close()
         return
+    if args.apply_only:
+        # the FP32 batched apply of one workload only (for ncu captures)
+        if args.apply_workload != "slab":
+            h.close()
+            w = W.BY_NAME[args.apply_workload]()
+            h = mb.Handle.from_workload(w, device=local)
+        ms, _, _ = timed(h, w, args.apply_prec, args.steps, args.warmup)
+        print(json.dumps({"apply_only": args.apply_workload, "prec": args.apply_prec, "ms": ms}))
+        h.close()
+        return
 
-    # the timed steps run without the per-kernel events of the library's
-    # profiling mode; the per-kernel breakdown comes from separate runs
-    clocks = Clocks(local)
-    clocks.start()
+    # the denominator of the plane kernel's roofline, measured just before
+    # the timed region at the clocks the GPU is running
+    peak32 = probe_fp32_peak(lib, local)
     # the timed FP32 steps bracket only the plane kernel with events (its
     # duration for the roofline, measured over the timed region)
-    ms32, launches, prof_plane = timed("fp32", args.steps, args.warmup, profile=2)
+    clocks = Clocks(local)
+    clocks.start()
+    ms32, launches, prof_plane = timed(h, w, "fp32", args.steps, args.warmup, profile=2)
     clk = clocks.stop()
     n32p, n64p, nbfp = min(args.steps, 20), 3, 3           # steps of the breakdown runs
-    _, _, prof = timed("fp32", n32p, 3, profile=1)
-    ms64, _, _ = timed("fp64", max(3, args.steps // 5), 3)
-    _, _, prof64 = timed("fp64", n64p, 1, profile=1)
-    msbf, _, _ = timed("bf16", max(3, args.steps // 5), 3)
-    _, _, profbf = timed("bf16", nbfp, 1, profile=1)
+    _, _, prof = timed(h, w, "fp32", n32p, 3, profile=1)
+    ms64, _, _ = timed(h, w, "fp64", max(3, args.steps // 5), 3)
+    _, _, prof64 = timed(h, w, "fp64", n64p, 1, profile=1)
+    msbf, _, _ = timed(h, w, "bf16", max(3, args.steps // 5), 3)
+    _, _, profbf = timed(h, w, "bf16", nbfp, 1, profile=1)
 
     # S and S^-1 (row a7) on the same blocks, all k-points, FP32 and FP64
     def timed_banded(which, prec, reps=10):
-        Xs, Ys = blocks(prec, replica_seed(3000, rank))
+        Xs, Ys = blocks(h, w, prec, replica_seed(3000, rank))
+        iks = list(range(w.nk))
         fn = h.apply_S if which == "S" else h.apply_Sinv
         for _ in range(3):
             for ik in iks:
@@ -465,7 +589,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         byts = sum(2 * x.numel() * x.element_size() for x in Xs)     # read X, write Y
-        return {"ms": ms, "GB/s": byts / (ms * 1e-3) / 1e9, "of_hbm_peak": byts / (ms * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6797.2)}
+        return {"ms": ms, "GB/s": byts / (ms * 1e-3) / 1e9,
+                "of_hbm_peak": byts / (ms * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6797.2)}
 
     banded = {"%s_%s" % (w_, p_): timed_banded(w_, p_) for w_ in ("S", "Sinv") for p_ in ("fp32", "fp64")}
 
@@ -477,7 +602,8 @@ def run_ours(args):
     # copies Y back.  Steps are pipelined over two device buffer sets and three
     # streams (host->device copy, apply, device->host copy), so the copy
     # engines overlap the previous/next step's apply.
-    sets = [blocks("fp32", replica_seed(2000 + 10 * i, rank)) for i in range(2)]
+    iks = list(range(w.nk))
+    sets = [blocks(h, w, "fp32", replica_seed(2000 + 10 * i, rank)) for i in range(2)]
     hX = [x.cpu().pin_memory() for x in sets[0][0]]
     hY = [[torch.empty_like(y, device="cpu").pin_memory() for y in sets[i][1]] for i in range(2)]
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
@@ -526,17 +652,7 @@ def run_ours(args):
     h2d = sum(x.numel() * x.element_size() for x in hX)
     d2h = sum(y.numel() * y.element_size() for y in hY[0])
 
-    roof = None
-    if "plane" in prof_plane:
-        t, c = prof_plane["plane"]
-        per_launch_ms = t / c
-        plane_flops = flops32 / max(1, c // args.steps)
-        ach = plane_flops / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": PLANE_TRAFFIC_BYTES,
-                "kernel": "plane_reg_kernel<float, 32, 16, 6>", "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
-                "kernel_ms": per_launch_ms,
-                "share_of_step": t / args.steps / ms32}
+    roof = plane_roofline(prof_plane, flops32, args.steps, ms32, "plane_reg_kernel<float, 32, 16, 6>", "slab", peak32)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
@@ -556,12 +672,16 @@ def run_ours(args):
                 "pipeline": "2 buffer sets; H2D, apply and D2H on separate streams",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "roofline": roof,
+        "fp32_peak_tflops_measured": peak32,
         "clocks": clk,
     }
     if not args.no_eig:
         line["eigsolve"] = eig_bench(h, w, args)
+    h.close()
+    if not args.no_graphene:
+        line["graphene"] = graphene_bench(mb, W, local, args, timed, peak32)
     if not args.no_kbatch:
-        line["kbatch"] = kbatch_bench(mb, W, local, args)
+        line["kbatch"] = kbatch_bench(mb, W, local, args, timed, peak32)
     if not args.no_serve:
         line["serve"] = serve_bench(mb, W, local, args)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -570,7 +690,6 @@ def run_ours(args):
                                 "sample": sample, "seconds": secs}
     if rank == 0:
         print(json.dumps(line))
-    h.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -586,7 +705,11 @@ def main():
     ap.add_argument("--no-eig", action="store_true")
     ap.add_argument("--eig-only", action="store_true")
     ap.add_argument("--no-kbatch", action="store_true")
-    ap.add_argument("--kbatch-solve", action="store_true")
+    ap.add_argument("--no-kbatch-solve", action="store_true")
+    ap.add_argument("--no-graphene", action="store_true")
+    ap.add_argument("--apply-only", action="store_true", help="time one FP32 batched apply only")
+    ap.add_argument("--apply-workload", default="slab", help="workload of --apply-only")
+    ap.add_argument("--apply-prec", default="fp32", help="precision of --apply-only")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-n", type=int, default=12)
     ap.add_argument("--serve-slots", type=int, default=8)

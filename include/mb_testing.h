@@ -32,6 +32,15 @@ int mb_debug_gram_tc32(const void *V, long long n, int ma, int mb, int nsplit, d
  * Allocates and frees its own device buffers; MB_EINVAL for bad sizes. */
 int mb_debug_combine_ff(const void *A, const double *Y, long long n, int ma, int mc, void *C, void *stream);
 
+/* FP32 fused multiply-add throughput of `device` in TFLOP/s (2 flops per
+ * FFMA): eight independent FFMA chains per thread, 2048 threads on every SM,
+ * timed with CUDA events; the best of `reps` (1..100) launches after one
+ * warm-up launch.  The denominator of the roofline of an FP32-ALU-bound
+ * kernel.  Runs at whatever clocks the device is at (it changes no setting).
+ * Allocates a small sink buffer; MB_EINVAL for bad arguments, MB_ECUDA if a
+ * CUDA call fails.  Outputs may be NULL. */
+int mb_probe_fp32_fma(int device, int reps, double *tflops, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

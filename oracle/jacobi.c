@@ -89,6 +89,10 @@ int oracle_jacobi_herm(int n, double *a_in, double *evals, double *evecs_out,
     /* selection sort ascending, permuting eigenvector columns */
     int *perm = (int *)malloc(sizeof(int) * (size_t)n);
     double *ev = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!perm || !ev) {
+        free(perm); free(ev); free(v);
+        return -2;
+    }
     for (int i = 0; i < n; i++) { perm[i] = i; ev[i] = creal(a[i * n + i]); }
     for (int i = 0; i < n; i++) {
         int m = i;

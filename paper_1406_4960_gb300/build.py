@@ -33,7 +33,8 @@ def _stale(objs):
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(SRC, f) for f in os.listdir(SRC)]
-    deps.append(os.path.join(HERE, "..", "include", "mb.h"))
+    inc = os.path.join(HERE, "..", "include")
+    deps.extend(os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)
 
