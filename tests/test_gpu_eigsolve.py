@@ -147,13 +147,31 @@ def test_eigsolve_second_s_channel(mbmod, prec):
     h.close()
 
 
-def test_eigsolve_ragged_blocks_and_depth(mbmod):
-    """Band count not a multiple of the block size, deeper Krylov spaces."""
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_eigsolve_ragged_blocks_and_depth(mbmod, prec):
+    """Band count not a multiple of the block size (7 roots + 2 guards in
+    blocks of 3: the last block is ragged), deeper Krylov spaces; the mixed
+    solver masks the last block's missing columns in its FP32 bulk cycles."""
     w = W.tiny()
     h = mbmod.Handle.from_workload(w)
-    ev, info = h.eigsolve(7, 1e-7, "fp64", block=3, krylov_depth=6)
+    ev, info = h.eigsolve(7, 1e-7, prec, block=3, krylov_depth=6)
     m, ref = _dense_ref(w, 0, 7)
-    assert np.abs(ev[0] - ref).max() < EV_TOL
+    assert np.abs(ev[0] - ref).max() < EV_TOL, np.abs(ev[0] - ref).max()
+    if prec == "fp32":
+        assert info.finish_cycles < info.cycles
+    h.close()
+
+
+@pytest.mark.parametrize("block", [2, 4])
+def test_eigsolve_mixed_ragged_blocks_slab(mbmod, block):
+    """Blocks of several roots with a ragged last block on a projector-heavy
+    slab at four k-points, mixed precision, against the dense oracle."""
+    w = _small_slab(nb=7)
+    h = mbmod.Handle.from_workload(w)
+    ev, info = h.eigsolve(w.nbands, 1e-7, "fp32", block=block)
+    for ik in range(w.nk):
+        m, ref = _dense_ref(w, ik, w.nbands)
+        assert np.abs(ev[ik] - ref).max() < EV_TOL, (ik, np.abs(ev[ik] - ref).max())
     h.close()
 
 
@@ -215,4 +233,28 @@ def test_eigsolve_full_graphene_mixed_matches_fp64(mbmod):
     assert i32.max_residual < 1e-6 and i64.max_residual < 1e-6
     assert np.abs(e32 - e64).max() < EV_TOL, np.abs(e32 - e64).max()
     assert i32.finish_cycles < i32.cycles          # the bulk cycles did run in FP32
+    h.close()
+
+
+def _golden_kbatch():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "kbatch_eigs.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return {int(r[0]): np.array(r[1:], dtype=float) for r in rows}
+
+
+def test_eigsolve_full_kbatch_matches_oracle_golden(mbmod):
+    """All 64 wedge k-points of the 2x2 graphene cell (352-361 G x 100
+    splines, 24 roots each) in one mixed-precision solve -- the batched
+    launch sequence the benchmark times -- against the oracle's own
+    Lanczos-Krylov eigenvalues at four of them (golden/make_kbatch_eigs.py)."""
+    w = W.kbatch()
+    gold = _golden_kbatch()
+    assert len(gold) == 4
+    h = mbmod.Handle.from_workload(w)
+    h.autotune(w.nbands, "fp32")
+    ev, info = h.eigsolve(w.nbands, 1e-6, "fp32")
+    assert info.max_residual < 1e-6
+    for ik, ref in gold.items():
+        assert np.abs(ev[ik] - ref).max() < EV_TOL, (ik, np.abs(ev[ik] - ref).max())
     h.close()
