@@ -263,6 +263,7 @@ def graphene_bench(mb, W, local, args, timed, peak32):
     oracle's eigenvalues (tests/golden/graphene_eigs.txt)."""
     w = W.graphene()
     h = mb.Handle.from_workload(w, device=local)
+    tune = h.autotune(w.nbands, "fp32")
     steps = 10
     ms32, launches, prof_plane = timed(h, w, "fp32", steps, 3, profile=2, sync_ranks=False)
     ms64, _, _ = timed(h, w, "fp64", 3, 2, sync_ranks=False)
@@ -276,7 +277,8 @@ def graphene_bench(mb, W, local, args, timed, peak32):
                     "gpu_launches_per_step": int(launches) // steps},
            "fp64": {"value": b64 / (ms64 * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms64},
            "bf16": {"value": b32 / (msbf * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": msbf},
-           "roofline": plane_roofline(prof_plane, f32, steps, ms32, "plane_reg_kernel<float, 64, 64, 6>",
+           "autotune": tune,
+           "roofline": plane_roofline(prof_plane, f32, steps, ms32, h.plane_kernel_name(w.nk, w.nbands, "fp32"),
                                       "graphene", peak32)}
     if not args.no_eig:
         ref = golden("graphene_eigs.txt")
@@ -305,7 +307,7 @@ def kbatch_bench(mb, W, local, args, timed, peak32):
     out = {"workload": "kbatch: 2x2 graphene, Ecut 30 Ha, 32x32 grid, 100 B-splines, 64 k x 24 bands",
            "autotune": tune, "apply_ms": ms, "apply_gbs": byts / (ms * 1e-3) / 1e9,
            "gpu_launches_per_apply": int(launches) // steps,
-           "roofline": plane_roofline(prof_plane, flops, steps, ms, "plane_reg_kernel<float, 32, 32, 6>",
+           "roofline": plane_roofline(prof_plane, flops, steps, ms, h.plane_kernel_name(w.nk, w.nbands, "fp32"),
                                       "kbatch", peak32)}
     if not args.no_kbatch_solve:
         ref = golden("kbatch_eigs.txt")
@@ -550,11 +552,19 @@ def run_ours(args):
             h.close()
             w = W.BY_NAME[args.apply_workload]()
             h = mb.Handle.from_workload(w, device=local)
+        tune = h.autotune(w.nbands, args.apply_prec) if args.apply_tune else None
         ms, _, _ = timed(h, w, args.apply_prec, args.steps, args.warmup)
-        print(json.dumps({"apply_only": args.apply_workload, "prec": args.apply_prec, "ms": ms}))
+        _, _, prof = timed(h, w, args.apply_prec, args.steps, 2, profile=2)
+        if tune:
+            print(h.autotune_report())
+        print(json.dumps({"apply_only": args.apply_workload, "prec": args.apply_prec, "ms": ms, "autotune": tune,
+                          "kernel": h.plane_kernel_name(w.nk, w.nbands, args.apply_prec),
+                          "plane_ms": prof["plane"][0] / prof["plane"][1] if "plane" in prof else None}))
         h.close()
         return
 
+    # launch shapes of the timed apply picked by the library's autotuner
+    tune = h.autotune(w.nbands, "fp32")
     # the denominator of the plane kernel's roofline, measured just before
     # the timed region at the clocks the GPU is running
     peak32 = probe_fp32_peak(lib, local)
@@ -652,7 +662,8 @@ def run_ours(args):
     h2d = sum(x.numel() * x.element_size() for x in hX)
     d2h = sum(y.numel() * y.element_size() for y in hY[0])
 
-    roof = plane_roofline(prof_plane, flops32, args.steps, ms32, "plane_reg_kernel<float, 32, 16, 6>", "slab", peak32)
+    roof = plane_roofline(prof_plane, flops32, args.steps, ms32, h.plane_kernel_name(w.nk, w.nbands, "fp32"), "slab",
+                          peak32)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
@@ -672,6 +683,7 @@ def run_ours(args):
                 "pipeline": "2 buffer sets; H2D, apply and D2H on separate streams",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "roofline": roof,
+        "autotune": tune,
         "fp32_peak_tflops_measured": peak32,
         "clocks": clk,
     }
@@ -710,6 +722,7 @@ def main():
     ap.add_argument("--apply-only", action="store_true", help="time one FP32 batched apply only")
     ap.add_argument("--apply-workload", default="slab", help="workload of --apply-only")
     ap.add_argument("--apply-prec", default="fp32", help="precision of --apply-only")
+    ap.add_argument("--apply-tune", action="store_true", help="autotune the launch shape of --apply-only")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-n", type=int, default=12)
     ap.add_argument("--serve-slots", type=int, default=8)

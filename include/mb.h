@@ -208,16 +208,44 @@ int mb_eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals,
                 void *stream);
 
 /* ---- launch-shape autotuner -------------------------------------------
- * Times the plane kernel's candidate launch shapes (bands per CTA, resident
- * waves of CTAs, and with them the length of the knot-interval runs) for an
- * apply of `nbands` bands at all k-points of the handle, on scratch blocks
- * it allocates, and keeps the fastest for later applies and eigensolves of
- * that shape.  Set-up time call (allocates; not during stream capture).
+ * Times the plane kernel's candidate launch shapes for an apply of `nbands`
+ * bands at all k-points of the handle, on scratch blocks it allocates, and
+ * keeps the fastest for later applies and eigensolves of that shape.  The
+ * candidates: in FP32, every compiled instance of the compact-plane kernel
+ * that can run the batch (they differ in threads and bands per CTA, CTAs per
+ * SM and where the window of X rows lives); the register-FFT / radix-2
+ * kernels with 1-4 bands per CTA; each with the built-in run count and with
+ * explicit wave targets.  Set-up time call (allocates; not during stream
+ * capture).  best_bt: bands per CTA of a register-FFT / radix-2 choice, or
+ * -1 - id for compact-plane instance `id` (mb_plane_kernel_name names it).
  * best_waves = 0 means the built-in wave model chose the run length (CTA
  * count rounded to whole waves of resident CTAs); > 0, a target of that many
  * CTAs per resident slot.  Outputs may be NULL. */
 int mb_autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves,
                 double *best_ms);
+
+/* Name of the plane-kernel instance that an apply of `nbands` bands at
+ * k-points 0 .. nk-1 (at most 64) in precision `prec` launches with the
+ * handle's current tuning, written to buf (host, len bytes, truncated and
+ * NUL-terminated). */
+int mb_plane_kernel_name(const mb_handle *h, int nk, int nbands, int prec, char *buf, int len);
+
+/* The candidates the last mb_autotune of this handle timed, one line each
+ * (kernel instance, bands per CTA, wave target, ms per apply), written to buf
+ * (host, len bytes, truncated and NUL-terminated). */
+int mb_autotune_report(const mb_handle *h, char *buf, int len);
+
+/* The compact-plane kernel instances (FP32 and BF16 applies) that can run an
+ * apply of k-points 0 .. nk-1: their ids are written to ids (host, at most
+ * `max`); returns how many there are (0 for MB_FP64), or -MB_EINVAL. */
+int mb_plane_kernel_candidates(const mb_handle *h, int nk, int nbands, int prec, int *ids, int max);
+
+/* Fix the plane-kernel choice for applies of that shape instead of timing
+ * it: id >= 0 a compact-plane instance from mb_plane_kernel_candidates,
+ * -1 the default choice, -2 the register-FFT / radix-2 kernels; waves as
+ * mb_autotune reports it (0: the built-in run count).  MB_EINVAL for an id
+ * that cannot run the batch. */
+int mb_plane_kernel_select(mb_handle *h, int nk, int nbands, int prec, int id, int waves);
 
 /* ---- continuous-batching solve server ---------------------------------
  * Serves mb_eigsolve requests of mixed sizes on one device.  Submitted

@@ -17,6 +17,7 @@
 //  banded_*       S (Eqs. (7)-(8)), S^-1 and the eigensolver's
 //                 preconditioner through banded Cholesky factors.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 
 #include "apply_common.cuh"
@@ -642,6 +643,14 @@ int upload_potential(mb_handle *h) {
     if ((rc = upload<float>(h, &h->t32.V, vp))) return rc;
     if ((rc = upload<double>(h, &h->t64.Vn, vn))) return rc;
     if ((rc = upload<float>(h, &h->t32.Vn, vn))) return rc;
+    // per-column copy for the FP32 compact-plane kernel: [q][i2][i1]
+    const int N1 = h->n1, N2 = h->n2;
+    std::vector<double> vt(vn.size());
+    for (int q = 0; q < h->nq; ++q)
+        for (int i1 = 0; i1 < N1; ++i1)
+            for (int i2 = 0; i2 < N2; ++i2)
+                vt[((size_t)q * N2 + i2) * N1 + i1] = vn[((size_t)q * N1 + i1) * N2 + i2];
+    if ((rc = upload<float>(h, &h->t32.Vt, vt))) return rc;
     return MB_OK;
 }
 
@@ -674,6 +683,42 @@ int upload_tables(mb_handle *h) {
     }
     MB_CUDA(cudaMalloc(&h->d_rows, rows.size() * sizeof(int)));
     MB_CUDA(cudaMemcpy(h->d_rows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+    // compact planes: the disc's rows n1min .. n1max become rows 0 .. nocc-1
+    // (row stride N2 + 1); the positions of those rows outside the disc
+    {
+        const int N2 = h->n2, LDP = N2 + 1;
+        const size_t nk = h->kp.size();
+        std::vector<int> cpos((size_t)h->total_ldg, 0), zpos;
+        h->nocc.assign(nk, 1);
+        h->zofs.assign(nk, 0);
+        h->nzero.assign(nk, 0);
+        for (size_t ik = 0; ik < nk; ++ik) {
+            const KPoint &kp = h->kp[ik];
+            int lo = 0, hi = 0;
+            for (int g = 0; g < kp.ng; ++g) {
+                lo = g ? std::min(lo, kp.n1[g]) : kp.n1[g];
+                hi = g ? std::max(hi, kp.n1[g]) : kp.n1[g];
+            }
+            const int nocc = kp.ng ? hi - lo + 1 : 1;
+            std::vector<char> used((size_t)nocc * N2, 0);
+            for (int g = 0; g < kp.ng; ++g) {
+                const int r = kp.n1[g] - lo, i2 = ((kp.n2[g] % N2) + N2) % N2;
+                used[(size_t)r * N2 + i2] = 1;
+                cpos[h->kofs[ik] + g] = r * LDP + i2;
+            }
+            h->nocc[ik] = nocc;
+            h->zofs[ik] = (int)zpos.size();
+            for (int r = 0; r < nocc; ++r)
+                for (int i2 = 0; i2 < N2; ++i2)
+                    if (!used[(size_t)r * N2 + i2]) zpos.push_back(r * LDP + i2);
+            h->nzero[ik] = (int)zpos.size() - h->zofs[ik];
+        }
+        if (zpos.empty()) zpos.push_back(0);
+        MB_CUDA(cudaMalloc(&h->d_cpos, cpos.size() * sizeof(int)));
+        MB_CUDA(cudaMemcpy(h->d_cpos, cpos.data(), cpos.size() * sizeof(int), cudaMemcpyHostToDevice));
+        MB_CUDA(cudaMalloc(&h->d_zpos, zpos.size() * sizeof(int)));
+        MB_CUDA(cudaMemcpy(h->d_zpos, zpos.data(), zpos.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
     if (h->nterm > 0) {
         std::vector<int> zi(h->pgroup);
         zi.insert(zi.end(), h->zstart.begin(), h->zstart.end());
@@ -709,7 +754,7 @@ int ensure_precond(mb_handle *h) {
 }
 
 static void free_set(DevTables &t) {
-    void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.Lrecip, &t.q2, &t.qproj, &t.zproj, &t.zf, &t.E, &t.Pfac};
+    void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.Lrecip, &t.q2, &t.qproj, &t.zproj, &t.zf, &t.E, &t.Pfac, &t.Vt};
     for (void **p : ps) {
         if (*p) cudaFree(*p);
         *p = nullptr;
@@ -724,6 +769,10 @@ void free_tables(mb_handle *h) {
     h->d_goff = nullptr;
     if (h->d_rows) cudaFree(h->d_rows);
     h->d_rows = nullptr;
+    if (h->d_cpos) cudaFree(h->d_cpos);
+    h->d_cpos = nullptr;
+    if (h->d_zpos) cudaFree(h->d_zpos);
+    h->d_zpos = nullptr;
     if (h->d_projB) cudaFree(h->d_projB);
     h->d_projB = nullptr;
     if (h->d_zidx) cudaFree(h->d_zidx);
@@ -754,24 +803,81 @@ int ensure_scratch(mb_handle *h, size_t bytes) {
 // Launch plan of the plane kernel for one batched apply.
 struct PlanePlan {
     bool reg = false;      // register-FFT kernel (else radix-2 shared-memory kernel)
+    bool p32 = false;      // FP32 compact-plane kernel
+    Plane32Shape sh;       // its instance
     int bt = 1;            // bands per CTA
     int np = 1;            // planes in flight
     int chunk = 1, nchunks = 1;
     size_t smem = 0;
 };
 
-static PlanePlan plan_plane(const mb_handle *h, int nsel, int nbands, size_t c2, int maxldg, bool reg_ok) {
+// Run count of the wave model: a CTA's time ~ its run length + about one
+// interval of run overhead (boundary rows); the launch takes
+// ceil(items / slots) rounds of the longest run.
+static int wave_model_chunks(const mb_handle *h, int pairs, int slots, int nmax_chunks, int waves) {
+    if (waves > 0) {
+        // explicit target: about `waves` CTAs per resident slot
+        const int target = std::max(1, (waves * slots + pairs - 1) / pairs);
+        return std::min(nmax_chunks, target);
+    }
+    double best = 1e300;
+    int nch = 1;
+    for (int n = 1; n <= nmax_chunks; ++n) {
+        const long long items = (long long)pairs * n;
+        const long long rounds = (items + slots - 1) / slots;
+        const double cost = (double)rounds * ((h->nint + n - 1) / n + 1.0);
+        if (cost < best - 1e-9) { best = cost; nch = n; }
+    }
+    return nch;
+}
+
+static PlanePlan plan_plane(const mb_handle *h, int nsel, const int *iks, int nbands, size_t c2, bool reg_ok) {
     PlanePlan p;
     const int K = h->order, P = h->nquad;
     const size_t NN = (size_t)h->n1 * h->n2;
+    int maxldg = 0, nocc_max = 0;
+    for (int i = 0; i < nsel; ++i) {
+        maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
+        nocc_max = std::max(nocc_max, h->nocc[iks[i]]);
+    }
     int ctas_per_sm = 1;
     // defaults, or the shape mb_autotune measured fastest for this batch
     const bool small = h->n1 <= 32 && h->n2 <= 32;
-    int bt_max = small ? 2 : 1, waves = 0;
+    int bt_max = small ? 2 : 1, waves = 0, p32_id = -1;
     auto it = h->tuned.find(std::make_tuple(nsel, nbands, c2 == 16 ? 1 : 0));
     if (it != h->tuned.end()) {
-        bt_max = it->second.first;
-        waves = it->second.second;
+        bt_max = it->second.bt;
+        waves = it->second.waves;
+        p32_id = it->second.p32;
+    }
+    const int nmax_chunks = std::max(1, std::min(kMaxChunks, h->nint / K));   // runs of >= K intervals
+    if (c2 == 8 && p32_id != -2) {
+        // FP32 compact-plane kernel: planes + output-row ring (+ X window
+        // slots) + the run's B values.  The tuned instance if there is one,
+        // else the first whose shared memory fits.
+        Plane32Shape shapes[kMaxPlane32Shapes];
+        const int ns = plane32_shapes(h->n1, h->n2, K, P, nocc_max, maxldg, shapes, kMaxPlane32Shapes);
+        for (int pass = 0; pass < 2; ++pass)
+            for (int v = 0; v < ns; ++v) {
+                const Plane32Shape &sh = shapes[v];
+                if (pass == 0 && sh.id != p32_id) continue;
+                const int pairs = nsel * ((nbands + sh.bt - 1) / sh.bt);
+                const int slots = h->num_sms * sh.ctas_per_sm;
+                const size_t budget = std::min((size_t)h->smem_optin, (size_t)228 * 1024 / sh.ctas_per_sm - 1024);
+                const size_t base = sh.smem_fixed + (size_t)sh.bt * K * maxldg * sizeof(float2);
+                int nch = wave_model_chunks(h, pairs, slots, nmax_chunks, waves);
+                auto smem_of = [&](int n) { return base + (size_t)((h->nint + n - 1) / n) * K * P * sizeof(float); };
+                while (nch < nmax_chunks && smem_of(nch) > budget) ++nch;
+                if (smem_of(nch) > budget) continue;
+                p.p32 = true;
+                p.sh = sh;
+                p.bt = sh.bt;
+                p.np = sh.bt * P;
+                p.nchunks = nch;
+                p.chunk = (h->nint + nch - 1) / nch;
+                p.smem = smem_of(nch);
+                return p;
+            }
     }
     if (reg_ok) {
         const size_t plane_bytes = (size_t)h->n1 * (h->n2 + 1) * c2;
@@ -801,23 +907,7 @@ static PlanePlan plan_plane(const mb_handle *h, int nsel, int nbands, size_t c2,
     }
     const int pairs = nsel * ((nbands + p.bt - 1) / p.bt);
     const int slots = h->num_sms * ctas_per_sm;
-    const int nmax_chunks = std::max(1, std::min(kMaxChunks, h->nint / K));   // runs of >= K intervals
-    if (waves > 0) {
-        // explicit target: about `waves` CTAs per resident slot
-        const int target = std::max(1, (waves * slots + pairs - 1) / pairs);
-        p.nchunks = std::min(nmax_chunks, target);
-    } else {
-        // wave model: a CTA's time ~ its run length + about one interval of
-        // run overhead (boundary rows); the launch takes ceil(items / slots)
-        // rounds of the longest run
-        double best = 1e300;
-        for (int n = 1; n <= nmax_chunks; ++n) {
-            const long long items = (long long)pairs * n;
-            const long long rounds = (items + slots - 1) / slots;
-            const double cost = (double)rounds * ((h->nint + n - 1) / n + 1.0);
-            if (cost < best - 1e-9) { best = cost; p.nchunks = n; }
-        }
-    }
+    p.nchunks = wave_model_chunks(h, pairs, slots, nmax_chunks, waves);
     p.chunk = (h->nint + p.nchunks - 1) / p.nchunks;   // longest run
     return p;
 }
@@ -861,8 +951,12 @@ size_t apply_scratch_bytes(const mb_handle *h, int nk, int nbands, int prec) {
     for (int i0 = 0; i0 < nk; i0 += kMaxK) {
         const int nsel = std::min(kMaxK, nk - i0);
         int maxldg = 0;
-        for (int i = i0; i < i0 + nsel; ++i) maxldg = std::max(maxldg, h->kp[i].ldg);
-        const PlanePlan p = plan_plane(h, nsel, nbands, c2, maxldg, reg);
+        std::vector<int> ik(nsel);
+        for (int i = i0; i < i0 + nsel; ++i) {
+            maxldg = std::max(maxldg, h->kp[i].ldg);
+            ik[i - i0] = i;
+        }
+        const PlanePlan p = plan_plane(h, nsel, ik.data(), nbands, c2, reg);
         need = std::max(need, (size_t)nsel * per_k_scratch(h, maxldg, nbands, p.nchunks, c2, prec == MB_BF16));
     }
     return need;
@@ -882,7 +976,7 @@ static size_t apply_H_need(const mb_handle *h, int nsel, const int *iks, int nba
     const size_t c2 = sizeof(typename V2<R>::T);
     int maxldg = 0;
     for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
-    const PlanePlan plan = plan_plane(h, nsel, nbands, c2, maxldg, plane_reg_supported<R>(h->n1, h->n2, h->order));
+    const PlanePlan plan = plan_plane(h, nsel, iks, nbands, c2, plane_reg_supported<R>(h->n1, h->n2, h->order));
     return (size_t)nsel * per_k_scratch(h, maxldg, nbands, plan.nchunks, c2, tensor);
 }
 
@@ -920,7 +1014,7 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     size_t off = 0;
     int maxldg = 0;
     for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
-    const PlanePlan plan = plan_plane(h, nsel, nbands, c2, maxldg, plane_reg_supported<R>(h->n1, h->n2, h->order));
+    const PlanePlan plan = plan_plane(h, nsel, iks, nbands, c2, plane_reg_supported<R>(h->n1, h->n2, h->order));
     const int chunk = plan.chunk, nchunks = plan.nchunks;
     (void)chunk;
     if (plan.np < 1) return MB_EUNSUPPORTED;
@@ -938,6 +1032,9 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         d.nrows = h->nrows[iks[i]];
         d.rowmask = h->rowmask[iks[i]];
         d.rows_magic = (unsigned)((1ull << 32) / (unsigned)std::max(1, d.nrows) + 1);
+        d.nocc = h->nocc[iks[i]];
+        d.zofs = h->zofs[iks[i]];
+        d.nz = h->nzero[iks[i]];
         // every k-point's regions are laid out for the batch's widest row (maxldg)
         const KScratch ks = per_k_layout(h, maxldg, nbands, nchunks, c2, tensor);
         d.part = base + off;
@@ -1031,6 +1128,9 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     pa.rows = h->d_rows;
     pa.tw = reinterpret_cast<const R2 *>(t.tw);
     pa.goff = h->d_goff;
+    pa.Vt = reinterpret_cast<const R *>(t.Vt);
+    pa.cpos = h->d_cpos;
+    pa.zpos = h->d_zpos;
     pa.n1 = h->n1;
     pa.n2 = h->n2;
     pa.l1 = h->l1;
@@ -1048,7 +1148,14 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     pa.bt = plan.bt;
     pa.np = plan.np;
     std::copy(desc, desc + nsel, pa.d);
-    if (plan.reg) {
+    if (plan.p32) {
+        if constexpr (sizeof(R) == 4) {
+            const unsigned grid = (unsigned)(nsel * ((nbands + plan.bt - 1) / plan.bt) * nchunks);
+            cudaError_t e = cudaSuccess;
+            MB_LAUNCH(h, s, KN_PLANE, e = plane32_launch(pa, plan.sh, grid, plan.smem, s));
+            MB_CUDA(e);
+        }
+    } else if (plan.reg) {
         const unsigned grid = (unsigned)(nsel * ((nbands + plan.bt - 1) / plan.bt) * nchunks);
         cudaError_t e = cudaSuccess;
         MB_LAUNCH(h, s, KN_PLANE, e = plane_reg_launch<R>(pa, grid, plan.smem, s));
@@ -1165,6 +1272,8 @@ int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nb
 // mb_autotune: time the candidate plane-kernel launch shapes for a batch of
 // `nbands` bands at every k-point of the handle and keep the fastest.
 namespace mb {
+int plane_kernel_name(const mb_handle *h, int nk, int nbands, int prec, char *buf, int len);
+
 int autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves, double *best_ms) {
     if (nbands < 1 || nbands > h->max_bands) return MB_EINVAL;
     if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return MB_EINVAL;
@@ -1187,29 +1296,66 @@ int autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves, 
         rc = MB_ECUDA;
     const bool small = h->n1 <= 32 && h->n2 <= 32;
     const auto key = std::make_tuple(std::min(nk, kMaxK), nbands, c2 == 16 ? 1 : 0);
-    double best = 1e300;
-    std::pair<int, int> bestp(small ? 2 : 1, 0);
-    for (int bt = small ? 4 : 2; bt >= 1 && rc == MB_OK; --bt)
-        for (int waves : {0, 1, 2, 4, 8}) {
-            h->tuned[key] = std::make_pair(bt, waves);
-            for (int w = 0; w < 2 && rc == MB_OK; ++w)
-                rc = apply_H_batch(h, nk, iks.data(), (const void *const *)X.data(), Y.data(), nbands, prec, s);
-            if (rc) break;
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < 5 && rc == MB_OK; ++r)
-                rc = apply_H_batch(h, nk, iks.data(), (const void *const *)X.data(), Y.data(), nbands, prec, s);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) rc = MB_ECUDA;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rc == MB_OK && ms / 5 < best) {
-                best = ms / 5;
-                bestp = std::make_pair(bt, waves);
-            }
+    // candidates: every compact-plane instance that can run the batch (FP32),
+    // and the register-FFT / radix-2 kernels with 1..4 bands per CTA; each
+    // with the wave model's run count and with explicit wave targets
+    std::vector<mb_handle::Tuned> cand;
+    if (c2 == 8) {
+        int nocc_max = 0, maxldg = 0;
+        for (int i = 0; i < std::min(nk, kMaxK); ++i) {
+            nocc_max = std::max(nocc_max, h->nocc[i]);
+            maxldg = std::max(maxldg, h->kp[i].ldg);
         }
+        Plane32Shape shapes[kMaxPlane32Shapes];
+        const int ns = plane32_shapes(h->n1, h->n2, h->order, h->nquad, nocc_max, maxldg, shapes, kMaxPlane32Shapes);
+        for (int v = 0; v < ns; ++v)
+            for (int waves : {0, 1, 2, 4, 8}) {
+                mb_handle::Tuned t;
+                t.p32 = shapes[v].id;
+                t.waves = waves;
+                cand.push_back(t);
+            }
+    }
+    for (int bt = small ? 4 : 2; bt >= 1; --bt)
+        for (int waves : {0, 1, 2, 4, 8}) {
+            mb_handle::Tuned t;
+            t.bt = bt;
+            t.waves = waves;
+            t.p32 = -2;            // not the compact-plane kernel
+            cand.push_back(t);
+        }
+    double best = 1e300;
+    mb_handle::Tuned bestp = cand.empty() ? mb_handle::Tuned() : cand[0];
+    h->tune_report.clear();
+    for (const auto &c : cand) {
+        if (rc != MB_OK) break;
+        h->tuned[key] = c;
+        char name[160];
+        plane_kernel_name(h, nk, nbands, prec, name, sizeof(name));
+        for (int w = 0; w < 2 && rc == MB_OK; ++w)
+            rc = apply_H_batch(h, nk, iks.data(), (const void *const *)X.data(), Y.data(), nbands, prec, s);
+        if (rc) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 5 && rc == MB_OK; ++r)
+            rc = apply_H_batch(h, nk, iks.data(), (const void *const *)X.data(), Y.data(), nbands, prec, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = MB_ECUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == MB_OK) {
+            char line[256];
+            std::snprintf(line, sizeof(line), "%s bands/CTA %d waves %d: %.4f ms\n", name,
+                          c.p32 >= 0 ? 0 : c.bt, c.waves, ms / 5);
+            h->tune_report += line;
+        }
+        if (rc == MB_OK && ms / 5 < best) {
+            best = ms / 5;
+            bestp = c;
+        }
+    }
     h->tuned[key] = bestp;
-    if (best_bt) *best_bt = bestp.first;
-    if (best_waves) *best_waves = bestp.second;
+    if (best_bt) *best_bt = bestp.p32 >= 0 ? -1 - bestp.p32 : bestp.bt;
+    if (best_waves) *best_waves = bestp.waves;
     if (best_ms) *best_ms = best;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -1220,9 +1366,79 @@ int autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves, 
     }
     return rc;
 }
+
+// Name of the plane-kernel instance an apply of `nbands` bands at k-points
+// 0 .. min(nk, kMaxK)-1 launches now (after any mb_autotune of that shape).
+int plane_kernel_name(const mb_handle *h, int nk, int nbands, int prec, char *buf, int len) {
+    if (!buf || len < 1 || nk < 1 || nbands < 1) return MB_EINVAL;
+    nk = std::min(std::min(nk, (int)h->kp.size()), kMaxK);
+    std::vector<int> iks(nk);
+    for (int i = 0; i < nk; ++i) iks[i] = i;
+    const size_t c2 = prec == MB_FP64 ? 16 : 8;
+    const bool reg = prec == MB_FP64 ? plane_reg_supported<double>(h->n1, h->n2, h->order)
+                                     : plane_reg_supported<float>(h->n1, h->n2, h->order);
+    const PlanePlan p = plan_plane(h, nk, iks.data(), nbands, c2, reg);
+    char tmp[128];
+    if (p.p32) std::snprintf(tmp, sizeof(tmp), "%s", p.sh.name);
+    else if (p.reg) std::snprintf(tmp, sizeof(tmp), "plane_reg_kernel<%s, %d, %d, %d>", c2 == 8 ? "float" : "double", h->n1, h->n2, h->order);
+    else std::snprintf(tmp, sizeof(tmp), "plane_kernel<%s>", c2 == 8 ? "float" : "double");
+    std::snprintf(buf, (size_t)len, "%s", tmp);
+    return MB_OK;
+}
 }  // namespace mb
 
 extern "C" int mb_autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves, double *best_ms) {
     if (!h) return MB_EINVAL;
     return mb::autotune(h, nbands, prec, best_bt, best_waves, best_ms);
+}
+
+extern "C" int mb_plane_kernel_name(const mb_handle *h, int nk, int nbands, int prec, char *buf, int len) {
+    if (!h) return MB_EINVAL;
+    return mb::plane_kernel_name(h, nk, nbands, prec, buf, len);
+}
+
+namespace mb {
+static int plane_candidates(const mb_handle *h, int nk, int prec, int *ids, int max) {
+    if (prec == MB_FP64) return 0;
+    nk = std::min(std::min(nk, (int)h->kp.size()), kMaxK);
+    int nocc_max = 0, maxldg = 0;
+    for (int i = 0; i < nk; ++i) {
+        nocc_max = std::max(nocc_max, h->nocc[i]);
+        maxldg = std::max(maxldg, h->kp[i].ldg);
+    }
+    Plane32Shape shapes[kMaxPlane32Shapes];
+    const int ns = plane32_shapes(h->n1, h->n2, h->order, h->nquad, nocc_max, maxldg, shapes, kMaxPlane32Shapes);
+    for (int v = 0; v < ns && v < max; ++v) ids[v] = shapes[v].id;
+    return ns;
+}
+}  // namespace mb
+
+extern "C" int mb_plane_kernel_candidates(const mb_handle *h, int nk, int nbands, int prec, int *ids, int max) {
+    if (!h || !ids || nk < 1 || nbands < 1 || max < 0) return -MB_EINVAL;
+    if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return -MB_EINVAL;
+    return mb::plane_candidates(h, nk, prec, ids, max);
+}
+
+extern "C" int mb_plane_kernel_select(mb_handle *h, int nk, int nbands, int prec, int id, int waves) {
+    if (!h || nk < 1 || nbands < 1 || waves < 0 || id < -2) return MB_EINVAL;
+    if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return MB_EINVAL;
+    if (id >= 0) {
+        int ids[mb::kMaxPlane32Shapes];
+        const int n = mb::plane_candidates(h, nk, prec, ids, mb::kMaxPlane32Shapes);
+        bool ok = false;
+        for (int i = 0; i < n; ++i) ok = ok || ids[i] == id;
+        if (!ok) return MB_EINVAL;
+    }
+    mb_handle::Tuned t;
+    t.p32 = id;
+    t.waves = waves;
+    t.bt = h->n1 <= 32 && h->n2 <= 32 ? 2 : 1;
+    h->tuned[std::make_tuple(std::min(std::min(nk, (int)h->kp.size()), mb::kMaxK), nbands, prec == MB_FP64 ? 1 : 0)] = t;
+    return MB_OK;
+}
+
+extern "C" int mb_autotune_report(const mb_handle *h, char *buf, int len) {
+    if (!h || !buf || len < 1) return MB_EINVAL;
+    std::snprintf(buf, (size_t)len, "%s", h->tune_report.c_str());
+    return MB_OK;
 }

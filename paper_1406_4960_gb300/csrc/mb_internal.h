@@ -42,6 +42,7 @@ struct DevTables {
     void *zf = nullptr;      // nzf x nb: the distinct rows of zproj
     void *E = nullptr;       // nkb diagonal strengths, then nkb partner couplings
     void *Pfac = nullptr;    // preconditioner factors: all k, ldg x nb x order each
+    void *Vt = nullptr;      // nq x N2 x N1, w_q V / (N1 N2), i1 fastest (FP32 compact-plane kernel)
 };
 
 struct Scratch {
@@ -92,6 +93,11 @@ struct mb_handle {
     void *d_tcerr = nullptr;         // status word of the tensor-core kernels' bounded waits
     std::vector<int> pb0_ofs, pb1_ofs, pb0_ld, pb1_ld;
     std::vector<int> rows_ofs, nrows;
+    // compact planes of the FP32 plane kernel, per k-point: occupied grid
+    // rows n1min .. n1min + nocc - 1, and the disc-free positions of those rows
+    int *d_cpos = nullptr;           // all k (int), offset kofs: (n1 - n1min)(N2 + 1) + (n2 mod N2)
+    int *d_zpos = nullptr;           // all k, offset zofs[k], nzero[k] entries
+    std::vector<int> nocc, zofs, nzero;
     std::vector<unsigned long long> rowmask;
     mb::DevTables t64, t32;
     bool pfac_ready = false;
@@ -106,8 +112,11 @@ struct mb_handle {
     size_t desc_bytes = 0;
     std::string last_cuda_error;
     // plane-kernel launch shapes picked by mb_autotune: (k-points per batch,
-    // bands, FP64?) -> (largest bands per CTA, resident-CTA waves)
-    std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
+    // bands, FP64?) -> (largest bands per CTA of the radix-2 / register-FFT
+    // kernels, resident-CTA waves, compact-plane kernel instance id or -1)
+    struct Tuned { int bt = 1; int waves = 0; int p32 = -1; };
+    std::map<std::tuple<int, int, int>, Tuned> tuned;
+    std::string tune_report;         // the last mb_autotune's candidates and times
     // launch accounting (always on) and optional per-kernel event timing
     long long launches = 0;
     int profiling = 0;               // 0 off, 1 every kernel, 2 the plane kernel only

@@ -18,6 +18,8 @@
 //  * a CTA serves `bt` bands of one k-point over a run of knot intervals and
 //    keeps their kappa output rows in a shared-memory ring, exactly like the
 //    radix-2 kernel (same boundary-row protocol and scratch layout).
+#include <cstdio>
+
 #include "apply_common.cuh"
 #include "mb_internal.h"
 
@@ -335,6 +337,365 @@ cudaError_t plane_reg_launch<double>(const PlaneArgs<double> &a, unsigned grid, 
     if (a.n1 == 16 && a.n2 == 32) return launch_one<double, 16, 32>(a, grid, smem, s);
     if (a.n1 == 32 && a.n2 == 16) return launch_one<double, 32, 16>(a, grid, smem, s);
     if (a.n1 == 32 && a.n2 == 32) return launch_one<double, 32, 32>(a, grid, smem, s);
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 compact-plane kernel.  The same computation as plane_reg_kernel for
+// B-splines of order 6 with 6 Gauss points per knot interval, reorganised
+// around three facts of the method:
+//  * The disc's grid rows form one run of n1 values, n1min .. n1min + nocc - 1.
+//    Storing row n1 at compact row n1 - n1min is a cyclic shift of the
+//    frequency index along the first grid axis.  The column pass (inverse
+//    transform, product with the real potential, forward transform) is a
+//    circular convolution with V^ along that axis, so it commutes with the
+//    shift: the column transforms run on the compact rows (the rest are zero
+//    on input and not needed on output), and no plane ever holds an empty row.
+//    A whole interval of planes (6 Gauss points x bands) then fits in shared
+//    memory even on 64 x 64 grids.
+//  * Every thread owns fixed columns g (= G of the disc) for the whole run of
+//    intervals: it keeps the kappa-row window of X for its columns in
+//    registers (one new row per interval, loaded one interval ahead), and it
+//    alone touches its columns of the output-row ring, so finished rows are
+//    written as soon as the adjoint sum completes them, with no extra pass.
+//  * The potential is stored per column (i1 fastest), so a column task reads
+//    its N1 values with 128-bit loads issued before its inverse transform.
+// Phases per interval: B-spline evaluation -> inverse row transforms of the
+// occupied rows -> fused column pass -> forward row transforms -> adjoint sum
+// (and zeroing of the occupied rows' disc-free positions), four barriers.
+// XM: where the kappa-row window of X lives -- 0: read from global memory
+// each interval; 1: registers; 2: per-thread slots in shared memory (row j in
+// slot j mod kappa), the new row loaded one interval ahead.
+template <int N1, int N2, int NOCC, int BT, int T, int GPT, int CTAS, int XM, bool VPRE>
+__global__ void __launch_bounds__(T, CTAS) plane32_kernel(const __grid_constant__ PlaneArgs<float> a) {
+    constexpr int K = 6, P = 6, KP = K * P;
+    constexpr int LDP = N2 + 1, PS = NOCC * LDP, NPL = BT * P;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *planes = reinterpret_cast<float2 *>(smem_raw);
+    const int lda = a.ldg_max;                 // row stride of the output-row ring
+    float2 *acc = planes + NPL * PS;           // [BT][K][lda]
+    float2 *xs = acc + (size_t)BT * K * lda;   // XM = 2: [K][BT][GPT][T] window slots
+    float *bqs = reinterpret_cast<float *>(xs + (XM == 2 ? K * BT * GPT * T : 0));   // B values of the run
+    constexpr bool XREG = XM == 1;
+
+    const int nbt = (a.nbands + BT - 1) / BT;
+    const int c = blockIdx.x % a.nchunks;
+    const int kb = blockIdx.x / a.nchunks;
+    const int btile = kb % nbt, ks = kb / nbt;
+    const KDesc &d = a.d[ks];
+    const int ldg = d.ldg, ng = d.ng, nb = a.nb, nint = a.nint, nocc = d.nocc;
+    const int b0 = btile * BT, nbb = min(BT, a.nbands - b0), npl = nbb * P;
+    const int ps = nocc * LDP;                 // plane stride: row nocc of a plane is row 0 of the next
+    const int t0 = chunk_begin(c, nint, a.nchunks), t1 = chunk_begin(c + 1, nint, a.nchunks);
+    const size_t band_stride = (size_t)nb * ldg;
+    const size_t part_stride = (size_t)(a.nchunks - 1) * 2 * (K - 1) * ldg;
+    const float2 *X = reinterpret_cast<const float2 *>(d.X) + (size_t)b0 * band_stride;
+    float2 *Y = reinterpret_cast<float2 *>(d.Y) + (size_t)b0 * band_stride;
+    float2 *part = reinterpret_cast<float2 *>(d.part) + (size_t)b0 * part_stride;
+    const int tid = threadIdx.x;
+
+    int cp[GPT];                               // compact-plane offset of each owned column (-1: padding)
+#pragma unroll
+    for (int i = 0; i < GPT; ++i) {
+        const int g = tid + i * T;
+        cp[i] = g < ng ? __ldg(a.cpos + d.kofs + g) : -1;
+    }
+    {
+        for (int e = tid; e < NPL * PS; e += T) planes[e] = make_float2(0.f, 0.f);
+        for (int e = tid; e < (t1 - t0) * KP; e += T) bqs[e] = __ldg(a.Bq + (size_t)t0 * KP + e);
+    }
+#pragma unroll
+    for (int i = 0; i < GPT; ++i) {
+        const int g = tid + i * T;
+        if (g < ldg)
+#pragma unroll
+            for (int r = 0; r < BT * K; ++r) acc[(size_t)r * lda + g] = make_float2(0.f, 0.f);
+    }
+    auto xval = [&](int b, int j, int i) -> float2 {
+        const int g = tid + i * T;
+        return (b < nbb && j >= 0 && j < nb && g < ng) ? __ldg(X + (size_t)b * band_stride + (size_t)j * ldg + g)
+                                                       : make_float2(0.f, 0.f);
+    };
+    // destination of output row j (band 0; band b at + b * stride): Y for rows
+    // that only this run touches, else the boundary scratch, whose two sides
+    // the epilogue adds in a fixed order
+    auto row_dst = [&](int j, size_t &stride) -> float2 * {
+        const int lo = max(0, j - K + 2), hi = min(nint - 1, j + 1);
+        if (lo >= t0 && hi <= t1 - 1) {
+            stride = band_stride;
+            return Y + (size_t)j * ldg;
+        }
+        stride = part_stride;
+        if (lo < t0) return part + ((size_t)((c - 1) * 2 + 1) * (K - 1) + (j - (t0 - 1))) * ldg;
+        return part + ((size_t)(c * 2 + 0) * (K - 1) + (j - (t1 - 1))) * ldg;
+    };
+
+    float2 xw[XREG ? BT : 1][XREG ? GPT : 1][K];   // xw[b][i][m] = X[t + m - 1] at column i
+    auto xslot = [&](int j, int b, int i) -> float2 & { return xs[((((j + K) % K) * BT + b) * GPT + i) * T + tid]; };
+    if constexpr (XM != 0) {
+#pragma unroll
+        for (int b = 0; b < BT; ++b)
+#pragma unroll
+            for (int i = 0; i < GPT; ++i)
+#pragma unroll
+                for (int m = 0; m < K; ++m) {
+                    if constexpr (XREG) xw[b][i][m] = xval(b, t0 + m - 1, i);
+                    else xslot(t0 + m - 1, b, i) = xval(b, t0 + m - 1, i);
+                }
+    }
+    __syncthreads();
+
+    for (int t = t0; t < t1; ++t) {
+        const float2 *bq2 = reinterpret_cast<const float2 *>(bqs + (t - t0) * KP);   // this interval's B values
+        float2 xn[XM ? BT : 1][XM ? GPT : 1];
+        // (a) psi_q(G) = sum_m B_{t+m}(z_q) X[t+m-1][G] for the interval's planes
+        {
+            float2 x[BT][GPT][K];
+#pragma unroll
+            for (int b = 0; b < BT; ++b)
+#pragma unroll
+                for (int i = 0; i < GPT; ++i)
+#pragma unroll
+                    for (int m = 0; m < K; ++m) {
+                        if constexpr (XREG) x[b][i][m] = xw[b][i][m];
+                        else if constexpr (XM == 2) x[b][i][m] = xslot(t + m - 1, b, i);
+                        else x[b][i][m] = xval(b, t + m - 1, i);
+                    }
+            if constexpr (XM != 0) {
+                // the next interval's new row, in flight during this interval's transforms
+#pragma unroll
+                for (int b = 0; b < BT; ++b)
+#pragma unroll
+                    for (int i = 0; i < GPT; ++i) xn[b][i] = xval(b, t + K - 1, i);
+            }
+#pragma unroll
+            for (int s = 0; s < P; ++s) {
+                float bq[K];                       // B_{t+m}(z_q) of Gauss point s
+#pragma unroll
+                for (int m = 0; m < K; m += 2) {
+                    const float2 v = bq2[(s * K + m) / 2];
+                    bq[m] = v.x;
+                    bq[m + 1] = v.y;
+                }
+#pragma unroll
+                for (int i = 0; i < GPT; ++i) {
+                    if (cp[i] < 0) continue;
+#pragma unroll
+                    for (int b = 0; b < BT; ++b) {
+                        if (b >= nbb) break;
+                        float2 psi = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int m = 0; m < K; ++m) rfma(psi, bq[m], x[b][i][m]);
+                        planes[(b * P + s) * ps + cp[i]] = psi;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // (b1) inverse transforms of the occupied rows
+        for (int e = tid; e < npl * nocc; e += T) {
+            float2 *line = planes + e * LDP;      // plane e / nocc, row e % nocc
+            float2 v[N2];
+#pragma unroll
+            for (int i = 0; i < N2; ++i) v[i] = line[i];
+            fft_reg<N2, true>(v);
+#pragma unroll
+            for (int i = 0; i < N2; ++i) line[i] = v[i];
+        }
+        __syncthreads();
+        // (b2, c, d1) columns on the compact rows: inverse transform, w_q V / (N1 N2), forward transform
+        for (int e = tid; e < npl * N2; e += T) {
+            const int pl = e / N2, col = e % N2;
+            const int s = pl % P;
+            float2 *line = planes + pl * ps + col;
+            const float4 *Vc = reinterpret_cast<const float4 *>(a.Vt + ((size_t)(t * P + s) * N2 + col) * N1);
+            float vv[N1];
+            if constexpr (VPRE) {
+#pragma unroll
+                for (int q = 0; q < N1 / 4; ++q) {
+                    const float4 w = __ldg(Vc + q);
+                    vv[4 * q] = w.x;
+                    vv[4 * q + 1] = w.y;
+                    vv[4 * q + 2] = w.z;
+                    vv[4 * q + 3] = w.w;
+                }
+            }
+            float2 v[N1];
+#pragma unroll
+            for (int i = 0; i < N1; ++i) v[i] = (i < NOCC && i < nocc) ? line[i * LDP] : make_float2(0.f, 0.f);
+            fft_reg<N1, true>(v);
+            if constexpr (VPRE) {
+#pragma unroll
+                for (int i = 0; i < N1; ++i) v[i] = rscale(vv[i], v[i]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < N1 / 4; ++q) {
+                    const float4 w = __ldg(Vc + q);
+                    v[4 * q] = rscale(w.x, v[4 * q]);
+                    v[4 * q + 1] = rscale(w.y, v[4 * q + 1]);
+                    v[4 * q + 2] = rscale(w.z, v[4 * q + 2]);
+                    v[4 * q + 3] = rscale(w.w, v[4 * q + 3]);
+                }
+            }
+            fft_reg<N1, false>(v);
+#pragma unroll
+            for (int i = 0; i < NOCC; ++i)
+                if (i < nocc) line[i * LDP] = v[i];
+        }
+        __syncthreads();
+        // (d2) forward transforms of the occupied rows
+        for (int e = tid; e < npl * nocc; e += T) {
+            float2 *line = planes + e * LDP;      // plane e / nocc, row e % nocc
+            float2 v[N2];
+#pragma unroll
+            for (int i = 0; i < N2; ++i) v[i] = line[i];
+            fft_reg<N2, false>(v);
+#pragma unroll
+            for (int i = 0; i < N2; ++i) line[i] = v[i];
+        }
+        __syncthreads();
+        // (e) adjoint sum of the owned columns into the ring; row t-1 is then
+        // complete and leaves the ring
+        {
+            const int slot0 = (t - 1 + K) % K;      // ring slot of row t-1
+            size_t dstride = 0;
+            float2 *dst = t >= 1 ? row_dst(t - 1, dstride) : nullptr;
+#pragma unroll
+            for (int i = 0; i < GPT; ++i) {
+                const int g = tid + i * T;
+                if (g >= ldg) continue;
+#pragma unroll
+                for (int b = 0; b < BT; ++b) {
+                    if (b >= nbb) break;
+                    float2 cm[K];
+#pragma unroll
+                    for (int m = 0; m < K; ++m) cm[m] = make_float2(0.f, 0.f);
+                    if (cp[i] >= 0) {
+#pragma unroll
+                        for (int s = 0; s < P; ++s) {
+                            const float2 phi = planes[(b * P + s) * ps + cp[i]];
+#pragma unroll
+                            for (int m = 0; m < K; m += 2) {
+                                const float2 v = bq2[(s * K + m) / 2];
+                                rfma(cm[m], v.x, phi);
+                                rfma(cm[m + 1], v.y, phi);
+                            }
+                        }
+                    }
+                    float2 *ab = acc + (size_t)b * K * lda + g;
+                    {
+                        float2 *sl = ab + (size_t)slot0 * lda;
+                        if (dst) dst[(size_t)b * dstride + g] = *sl + cm[0];
+                        *sl = make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int m = 1; m < K; ++m) {
+                        if (t + m - 1 < nb) {
+                            int sl = slot0 + m;
+                            if (sl >= K) sl -= K;
+                            ab[(size_t)sl * lda] += cm[m];
+                        }
+                    }
+                }
+            }
+            // the occupied rows' disc-free positions start the next interval at zero
+            for (int e = tid; e < d.nz; e += T) {
+                const int pos = __ldg(a.zpos + d.zofs + e);
+                for (int pl = 0; pl < npl; ++pl) planes[pl * ps + pos] = make_float2(0.f, 0.f);
+            }
+            if constexpr (XREG) {
+#pragma unroll
+                for (int b = 0; b < BT; ++b)
+#pragma unroll
+                    for (int i = 0; i < GPT; ++i) {
+#pragma unroll
+                        for (int m = 0; m + 1 < K; ++m) xw[b][i][m] = xw[b][i][m + 1];
+                        xw[b][i][K - 1] = xn[b][i];
+                    }
+            } else if constexpr (XM == 2) {
+                // row t+K-1 takes the slot of row t-1, which no later interval reads
+#pragma unroll
+                for (int b = 0; b < BT; ++b)
+#pragma unroll
+                    for (int i = 0; i < GPT; ++i) xslot(t + K - 1, b, i) = xn[b][i];
+            }
+        }
+    }
+    // rows t1-1 .. t1+K-3 are complete once the run ends
+    for (int m = 0; m + 1 < K; ++m) {
+        const int j = t1 - 1 + m;
+        if (j < 0 || j >= nb) continue;
+        size_t dstride = 0;
+        float2 *dst = row_dst(j, dstride);
+        const int sl = j % K;
+#pragma unroll
+        for (int i = 0; i < GPT; ++i) {
+            const int g = tid + i * T;
+            if (g >= ldg) continue;
+#pragma unroll
+            for (int b = 0; b < BT; ++b)
+                if (b < nbb) dst[(size_t)b * dstride + g] = acc[((size_t)b * K + sl) * lda + g];
+        }
+    }
+}
+
+// Instances: id, grid, bound on the occupied rows, bands per CTA, threads,
+// columns per thread, CTAs per SM, X window (XM), potential loaded ahead of
+// the inverse column transform.  The first feasible instance of a grid is the
+// default; mb_autotune times all of them.
+#define MB_P32_LIST(X)                                   \
+    X(0, 16, 16, 10, 2, 96, 1, 4, 1, true)               \
+    X(1, 32, 16, 24, 2, 192, 1, 2, 1, true)              \
+    X(2, 32, 16, 24, 2, 256, 1, 2, 2, false)             \
+    X(3, 32, 16, 24, 2, 192, 1, 2, 2, true)              \
+    X(4, 32, 16, 24, 1, 96, 2, 4, 1, true)               \
+    X(5, 32, 32, 24, 1, 192, 2, 2, 1, true)              \
+    X(6, 32, 32, 24, 2, 384, 1, 1, 1, true)              \
+    X(7, 32, 32, 23, 1, 192, 2, 3, 2, false)             \
+    X(8, 64, 64, 48, 1, 384, 4, 1, 0, false)             \
+    X(9, 64, 64, 48, 1, 256, 6, 1, 0, false)             \
+    X(10, 32, 16, 22, 2, 192, 1, 3, 2, false)
+
+int plane32_shapes(int n1, int n2, int order, int nquad, int nocc, int ldg, Plane32Shape *out, int max) {
+    int n = 0;
+    if (order != 6 || nquad != 6) return 0;
+#define MB_P32_SHAPE(ID, A, B, NO, BT, T, GPT, CT, XR, VP)                                          \
+    if (n1 == A && n2 == B && nocc <= NO && ldg <= T * GPT && n < max) {                            \
+        Plane32Shape &sh = out[n++];                                                                 \
+        sh.ok = true;                                                                                \
+        sh.id = ID;                                                                                  \
+        sh.nocc_max = NO;                                                                            \
+        sh.ldg_max = T * GPT;                                                                        \
+        sh.bt = BT;                                                                                  \
+        sh.threads = T;                                                                              \
+        sh.ctas_per_sm = CT;                                                                         \
+        sh.smem_fixed = ((size_t)BT * 6 * NO * (B + 1) + (XR == 2 ? 6 * BT * GPT * T : 0)) * sizeof(float2); \
+        std::snprintf(sh.name, sizeof(sh.name), "plane32_kernel<%d, %d, %d, %d, %d, %d, %d, %d, %d>", A, B, NO, \
+                      BT, T, GPT, CT, XR, VP ? 1 : 0);                                              \
+    }
+    MB_P32_LIST(MB_P32_SHAPE)
+#undef MB_P32_SHAPE
+    return n;
+}
+
+cudaError_t plane32_launch(const PlaneArgs<float> &a, const Plane32Shape &sh, unsigned grid, size_t smem,
+                           cudaStream_t s) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
+#define MB_P32_LAUNCH(ID, A, B, NO, BT, T, GPT, CT, XR, VP)                                          \
+    if (sh.id == ID) {                                                                               \
+        if (a.n1 != A || a.n2 != B) return cudaErrorInvalidValue;                                    \
+        const void *fn = (const void *)plane32_kernel<A, B, NO, BT, T, GPT, CT, XR, VP>;              \
+        cudaError_t e = smem_limit_once(fn, dev, optin);                                             \
+        if (e != cudaSuccess) return e;                                                              \
+        plane32_kernel<A, B, NO, BT, T, GPT, CT, XR, VP><<<grid, T, smem, s>>>(a);                   \
+        return cudaGetLastError();                                                                   \
+    }
+    MB_P32_LIST(MB_P32_LAUNCH)
+#undef MB_P32_LAUNCH
     return cudaErrorInvalidValue;
 }
 

@@ -217,7 +217,12 @@ int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int
                 }
             }
         if (gl.empty()) return MB_EINVAL;
-        std::sort(gl.begin(), gl.end());
+        // disc order: by n2, then n1 -- column by column of the grid, so that
+        // consecutive G of a warp sit one compact-plane row apart (a stride
+        // of N2 + 1 elements, free of shared-memory bank conflicts)
+        std::sort(gl.begin(), gl.end(), [](const std::tuple<int, int, int> &x, const std::tuple<int, int, int> &y) {
+            return std::make_pair(std::get<2>(x), std::get<1>(x)) < std::make_pair(std::get<2>(y), std::get<1>(y));
+        });
         kp.ng = (int)gl.size();
         kp.ldg = (kp.ng + 31) / 32 * 32;
         for (auto &e : gl) {

@@ -23,7 +23,9 @@ EXPORTS = ("mb_setup", "mb_destroy", "mb_sizes", "mb_gvectors", "mb_zplanes",
            "mb_apply_Sinv", "mb_eigsolve", "mb_strerror", "mb_last_cuda_error",
            "mb_set_profiling", "mb_profile_read", "mb_profile_reset", "mb_launch_count",
            "mb_kernel_name", "mb_apply_H_noalloc", "mb_server_create", "mb_server_submit",
-           "mb_server_wait", "mb_server_stats", "mb_server_destroy", "mb_autotune")
+           "mb_server_wait", "mb_server_stats", "mb_server_destroy", "mb_autotune",
+           "mb_plane_kernel_name", "mb_autotune_report", "mb_plane_kernel_candidates",
+           "mb_plane_kernel_select")
 
 
 class MBError(RuntimeError):
@@ -119,6 +121,10 @@ def load(build_if_missing: bool = False):
     lib.mb_server_destroy.argtypes = [vp]
     lib.mb_server_destroy.restype = None
     lib.mb_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, ip, ip, dp]
+    lib.mb_plane_kernel_name.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
+    lib.mb_autotune_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_int]
+    lib.mb_plane_kernel_candidates.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int]
+    lib.mb_plane_kernel_select.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.mb_kernel_name.argtypes = [ctypes.c_int]
     lib.mb_kernel_name.restype = ctypes.c_char_p
     _lib = lib
@@ -335,7 +341,30 @@ class Handle:
         bt, waves, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         self._check(self._lib.mb_autotune(self._h, int(nbands), self._prec(prec), ctypes.byref(bt),
                                           ctypes.byref(waves), ctypes.byref(ms)), "mb_autotune")
-        return {"bands_per_cta": bt.value, "waves": waves.value, "ms": ms.value}
+        return {"bands_per_cta": bt.value if bt.value > 0 else None, "waves": waves.value, "ms": ms.value,
+                "kernel": self.plane_kernel_name(self.nk, nbands, prec)}
+
+    def plane_kernel_candidates(self, nk, nbands, prec="fp32"):
+        ids = (ctypes.c_int * 16)()
+        n = self._lib.mb_plane_kernel_candidates(self._h, int(nk), int(nbands), self._prec(prec), ids, 16)
+        if n < 0:
+            raise MBError(-n, "mb_plane_kernel_candidates")
+        return list(ids[:n])
+
+    def plane_kernel_select(self, nk, nbands, prec, kernel_id, waves=0):
+        self._check(self._lib.mb_plane_kernel_select(self._h, int(nk), int(nbands), self._prec(prec), int(kernel_id),
+                                                     int(waves)), "mb_plane_kernel_select")
+
+    def autotune_report(self):
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(self._lib.mb_autotune_report(self._h, buf, 1 << 16), "mb_autotune_report")
+        return buf.value.decode()
+
+    def plane_kernel_name(self, nk, nbands, prec="fp32"):
+        buf = ctypes.create_string_buffer(128)
+        self._check(self._lib.mb_plane_kernel_name(self._h, int(nk), int(nbands), self._prec(prec), buf, 128),
+                    "mb_plane_kernel_name")
+        return buf.value.decode()
 
     def eigsolve(self, nbands, tol, prec="fp64", evecs=None, krylov_depth=0, block=0,
                  max_cycles=0, polish=0, stream=None, allow_notconv=False, guard=0):

@@ -311,3 +311,37 @@ def test_apply_bf16_matches_oracle(mbmod, case):
         err = np.abs(Y - ref).max()
         assert err <= bound, (ik, err, bound)
     h.close()
+
+
+@pytest.mark.parametrize("case", ["tiny", "slab-small", "graphene-small", "kbatch-small"])
+def test_every_plane_kernel_instance_matches_oracle(mbmod, case):
+    """Every compiled compact-plane instance that can run the batch (the
+    autotuner may pick any of them), and the register-FFT kernel beside
+    them, with two run counts each, against the oracle in FP32."""
+    w = CASES[case]()
+    h = mbmod.Handle.from_workload(w)
+    ids = h.plane_kernel_candidates(w.nk, w.nbands, "fp32")
+    assert ids, "no compact-plane instance for %s" % case
+    Xs, perms, models, Xo = [], [], [], []
+    for ik in range(w.nk):
+        ng, nb, ldg = h.sizes(ik)
+        m = Hm.model_from_workload(w, ik)
+        perm = gmap(h, m, ik)
+        X = W.random_block(w.nbands, nb, ng, seed=900 + ik)
+        Xo.append(X)
+        perms.append(perm)
+        models.append(m)
+        Xs.append(torch.from_numpy(lib_block(X, perm, ldg, np.complex64)).cuda())
+    refs = [models[ik].apply_H(Xo[ik]) for ik in range(w.nk)]
+    for kid in ids + [-2]:
+        for waves in (0, 8):
+            h.plane_kernel_select(w.nk, w.nbands, "fp32", kid, waves)
+            Ys = [torch.full_like(x, complex(np.nan, np.nan)) for x in Xs]
+            h.apply_H_batch(list(range(w.nk)), Xs, Ys, "fp32")
+            torch.cuda.synchronize()
+            for ik in range(w.nk):
+                Yh = Ys[ik].cpu().numpy()
+                assert np.all(Yh[:, :, len(perms[ik]):] == 0)
+                err = rel_err(oracle_block(Yh, perms[ik]), refs[ik])
+                assert err < TOL["fp32"], (case, h.plane_kernel_name(w.nk, w.nbands, "fp32"), waves, ik, err)
+    h.close()
