@@ -198,8 +198,8 @@ template <typename R, int NZB>
 __global__ void __launch_bounds__(512) nl_zx_kernel(const __grid_constant__ NlArgs<R> a) {
     typedef typename V2<R>::T R2;
     extern __shared__ __align__(16) unsigned char nsm[];
-    R2 *red = reinterpret_cast<R2 *>(nsm);                  // nseg x 64
-    R *zs = reinterpret_cast<R *>(red + a.nseg * 64);      // nz x nb
+    R2 *red = reinterpret_cast<R2 *>(nsm);                  // nseg x NZB x 64 partial sums
+    R *zs = reinterpret_cast<R *>(red + a.nseg * NZB * 64); // nz x nb
     const int tx = threadIdx.x, seg = threadIdx.y;
     const int tid = seg * 64 + tx, nthr = 64 * a.nseg;
     const int g = blockIdx.x * 64 + tx, b = blockIdx.y;
@@ -210,7 +210,6 @@ __global__ void __launch_bounds__(512) nl_zx_kernel(const __grid_constant__ NlAr
     const int j0 = (seg * nb) / a.nseg, j1 = ((seg + 1) * nb) / a.nseg, nr = j1 - j0;
     const bool live = g < d.ng;
     const R2 *X = reinterpret_cast<const R2 *>(d.X) + ((size_t)b * nb + j0) * ldg + g;
-    R2 *Z = reinterpret_cast<R2 *>(d.W) + (size_t)b * a.nz * ldg + g;
     for (int f0 = 0; f0 < a.nz; f0 += NZB) {
         R2 acc[NZB];
 #pragma unroll
@@ -234,18 +233,21 @@ __global__ void __launch_bounds__(512) nl_zx_kernel(const __grid_constant__ NlAr
                     if (f0 + f < a.nz) rfma(acc[f], zs[(f0 + f) * nb + j0 + j], x);
             }
         }
+        // every factor's partial sums at once, then each output summed over
+        // the segments in segment order (one barrier per factor chunk)
 #pragma unroll
-        for (int f = 0; f < NZB; ++f) {
-            if (f0 + f >= a.nz) break;
-            red[seg * 64 + tx] = acc[f];
-            __syncthreads();
-            if (seg == 0 && live) {
-                R2 t = red[tx];
-                for (int sg = 1; sg < a.nseg; ++sg) t = t + red[sg * 64 + tx];
-                Z[(size_t)(f0 + f) * ldg] = t;
-            }
-            __syncthreads();
+        for (int f = 0; f < NZB; ++f) red[(seg * NZB + f) * 64 + tx] = acc[f];
+        __syncthreads();
+        const int nzc = min(NZB, a.nz - f0);
+        R2 *Zb = reinterpret_cast<R2 *>(d.W) + (size_t)b * a.nz * ldg + blockIdx.x * 64;
+        for (int o = tid; o < nzc * 64; o += nthr) {
+            const int f = o / 64, x = o % 64;
+            if (blockIdx.x * 64 + x >= d.ng) continue;
+            R2 t = red[f * 64 + x];
+            for (int sg = 1; sg < a.nseg; ++sg) t = t + red[(sg * NZB + f) * 64 + x];
+            Zb[(size_t)(f0 + f) * ldg + x] = t;
         }
+        __syncthreads();
     }
 }
 
@@ -326,101 +328,125 @@ __global__ void __launch_bounds__(128) nl_back_kernel(const __grid_constant__ Nl
 // inside one plane-kernel run) or from the two boundary partials (rows shared
 // by neighbouring runs), added in a fixed order.  `base` = 0 runs only the KB
 // term for the distinct z factors [f0, f1) (when there are more than NZB).
+constexpr int kMaxEpiRows = 1024;   // B-splines the epilogue's row table covers
 template <typename R> struct EpiArgs {
     const R *Sband, *Dband, *q2;
     const R *zf;                    // nz x nb
     int order, nb, nbands, nchunks, nint, nz, f0, f1, base, njseg;
     KDesc d[kMaxK];
+    short src[kMaxEpiRows];         // row j: its first boundary partial row, or -1 (its own Y row)
 };
 
-// HW = largest half-width of the band (order - 1) the instance handles: X
-// rows j-HW .. j+HW stay in registers and one new row is loaded per output
-// row (the next one is in flight while the current row is computed).
-template <typename R, int NZB, int HW>
+// N values (N a multiple of 4) from 16-byte aligned shared memory in 128-bit
+// loads (FP32) or 128-bit pairs (FP64)
+template <typename R, int N> __device__ __forceinline__ void load_row(const R *p, R (&out)[N]);
+template <typename R, int N> __device__ __forceinline__ void load_row(const R *p, R (&out)[N]) {
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q) {
+            const float4 v = reinterpret_cast<const float4 *>(p)[q];
+            out[4 * q] = v.x;
+            out[4 * q + 1] = v.y;
+            out[4 * q + 2] = v.z;
+            out[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N / 2; ++q) {
+            const double2 v = reinterpret_cast<const double2 *>(p)[q];
+            out[2 * q] = v.x;
+            out[2 * q + 1] = v.y;
+        }
+    }
+}
+
+// HW = largest half-width of the band (order - 1) the instance handles.  A
+// thread takes at most RM consecutive rows j and issues every load before it
+// computes: the X rows j0-HW .. j0+RM-1+HW (clamped to the basis: the band
+// coefficients are zero outside it) and the local part of each row, so it
+// waits on memory once.  Per row, the band coefficients (padded to a multiple
+// of 4) and the z factors come from shared memory in 128-bit loads at
+// compile-time offsets, and where the row's local part lives (its Y row or
+// the two boundary partials) is decided once per CTA.
+template <typename R, int NZB, int HW, int RM>
 __global__ void __launch_bounds__(64) epilogue_kernel(const __grid_constant__ EpiArgs<R> a) {
     typedef typename V2<R>::T R2;
-    constexpr int WW = 2 * HW + 1;
+    constexpr int WW = 2 * HW + 1, WP = (WW + 3) / 4 * 4;
     extern __shared__ __align__(16) unsigned char esm[];
+    R *cS = reinterpret_cast<R *>(esm);                 // [RM][WP]: S[j][j+o], o = i - HW
+    R *cD = cS + RM * WP;                               // [RM][WP]: D[j][j+o] / 2
+    R *zs = cD + RM * WP;                               // [RM][NZB]: z_f(j), zero for f >= nf
     const int b = blockIdx.y / a.njseg, js = blockIdx.y % a.njseg;
     const KDesc &d = a.d[blockIdx.z];
     const int K = a.order, W = 2 * K - 1, ldg = d.ldg, nb = a.nb;
     const int j0 = (js * nb) / a.njseg, j1 = ((js + 1) * nb) / a.njseg, nr = j1 - j0;
     const int nf = a.f1 - a.f0;
-    // band rows of S and D/2 (zero-padded to WW entries) and the z factors
-    R *cS = reinterpret_cast<R *>(esm);
-    R *cD = cS + nr * WW;
-    R *zs = cD + nr * WW;
-    for (int e = threadIdx.x; e < nr * WW; e += blockDim.x) {
-        const int rr = e / WW, o = e % WW - HW;            // offset o = jj - j
-        const int dd = o + K - 1;
-        const bool in = dd >= 0 && dd < W;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = g < d.ng;
+    // every global load of the thread first, then the shared coefficient
+    // tables: the thread waits on memory once
+    R2 r[NZB];                  // KB: R[b][f][G] = sum_{t: f(t) = f} c_{p(t)}(b) q_t(G) (nl_back)
+    R2 xw[RM + 2 * HW];         // xw[i] = X[j0 - HW + i]
+    R2 loc[RM];
+    R hq = R(0);
+    R2 *Y = reinterpret_cast<R2 *>(d.Y) + ((size_t)b * nb + j0) * ldg + g;
+    if (live) {
+        const R2 *Rg = reinterpret_cast<const R2 *>(d.W) + ((size_t)b * a.nz + a.f0) * ldg + g;
+#pragma unroll
+        for (int f = 0; f < NZB; ++f) r[f] = f < nf ? Rg[(size_t)f * ldg] : czero<R2>();
+        hq = R(0.5) * a.q2[d.kofs + g];
+        if (a.base) {
+            const R2 *X = reinterpret_cast<const R2 *>(d.X) + (size_t)b * nb * ldg + g;
+#pragma unroll
+            for (int i = 0; i < RM + 2 * HW; ++i) {
+                const int row = min(max(j0 - HW + i, 0), nb - 1);
+                xw[i] = X[(size_t)row * ldg];
+            }
+            const R2 *part = reinterpret_cast<const R2 *>(d.part) + (size_t)b * (a.nchunks - 1) * 2 * (K - 1) * ldg + g;
+#pragma unroll
+            for (int rr = 0; rr < RM; ++rr) {
+                if (rr >= nr) break;
+                const int s = a.src[j0 + rr];
+                loc[rr] = s < 0 ? Y[(size_t)rr * ldg] : part[(size_t)s * ldg] + part[(size_t)(s + K - 1) * ldg];
+            }
+        } else {
+#pragma unroll
+            for (int rr = 0; rr < RM; ++rr) loc[rr] = rr < nr ? Y[(size_t)rr * ldg] : czero<R2>();
+        }
+    }
+    for (int e = threadIdx.x; e < RM * WP; e += blockDim.x) {
+        const int rr = e / WP, i = e % WP, dd = i - HW + K - 1;
+        const bool in = a.base && rr < nr && i < WW && dd >= 0 && dd < W;
         cS[e] = in ? a.Sband[(size_t)(j0 + rr) * W + dd] : R(0);
         cD[e] = in ? R(0.5) * a.Dband[(size_t)(j0 + rr) * W + dd] : R(0);
     }
-    for (int e = threadIdx.x; e < nf * nr; e += blockDim.x) zs[e] = a.zf[(size_t)(a.f0 + e / nr) * nb + j0 + e % nr];
+    for (int e = threadIdx.x; e < RM * NZB; e += blockDim.x) {
+        const int rr = e / NZB, f = e % NZB;
+        zs[e] = (rr < nr && f < nf) ? a.zf[(size_t)(a.f0 + f) * nb + j0 + rr] : R(0);
+    }
     __syncthreads();
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ldg) return;
-    R2 *Y = reinterpret_cast<R2 *>(d.Y) + (size_t)b * nb * ldg + g;
-    if (g >= d.ng) {
+    if (!live) {
         if (a.base)
-            for (int j = j0; j < j1; ++j) Y[(size_t)j * ldg] = czero<R2>();
+            for (int rr = 0; rr < nr; ++rr) Y[(size_t)rr * ldg] = czero<R2>();
         return;
     }
-    // KB: r_f = R[b][f][G] = sum_{t: f(t) = f} c_{p(t)}(b) q_t(G) (nl_back)
-    R2 r[NZB];
-    const R2 *Rg = reinterpret_cast<const R2 *>(d.W) + ((size_t)b * a.nz + a.f0) * ldg + g;
 #pragma unroll
-    for (int f = 0; f < NZB; ++f) r[f] = f < nf ? Rg[(size_t)f * ldg] : czero<R2>();
-    const R2 *X = reinterpret_cast<const R2 *>(d.X) + (size_t)b * nb * ldg + g;
-    const R2 *part = reinterpret_cast<const R2 *>(d.part) + (size_t)b * (a.nchunks - 1) * 2 * (K - 1) * ldg + g;
-    const R hq = R(0.5) * a.q2[d.kofs + g];
-    R2 xw[WW];                                           // xw[HW + o] = X[j + o]
-    if (a.base) {
-#pragma unroll
-        for (int i = 0; i < WW; ++i) {
-            const int row = j0 + i - HW;
-            xw[i] = (row >= 0 && row < nb) ? X[(size_t)row * ldg] : czero<R2>();
-        }
-    }
-    // run boundary bc (between runs bc and bc+1) starts at interval t1 and
-    // owns rows [t1 - 1, t1 + K - 3]
-    int bc = 0, t1 = a.nchunks > 1 ? a.nint / a.nchunks : 0;
-    // local part of row j: Y (rows inside one plane-kernel run) or the two
-    // boundary partials; loaded one row ahead of its use
-    auto local_row = [&](int j) -> R2 {
-        while (bc < a.nchunks - 1 && t1 + K - 3 < j) {
-            ++bc;
-            t1 = ((bc + 1) * a.nint) / a.nchunks;
-        }
-        if (bc < a.nchunks - 1 && j >= t1 - 1) {
-            const int br = j - (t1 - 1);
-            return part[((size_t)(bc * 2 + 0) * (K - 1) + br) * ldg] + part[((size_t)(bc * 2 + 1) * (K - 1) + br) * ldg];
-        }
-        return Y[(size_t)j * ldg];
-    };
-    R2 vnext = (a.base && j0 < j1) ? local_row(j0) : czero<R2>();
-    for (int j = j0; j < j1; ++j) {
-        R2 v;
+    for (int rr = 0; rr < RM; ++rr) {
+        if (rr >= nr) break;
+        R2 v = loc[rr];
         if (a.base) {
-            const int rn = j + HW + 1;
-            const R2 nxt = rn < nb ? X[(size_t)rn * ldg] : czero<R2>();
-            v = vnext;
-            if (j + 1 < j1) vnext = local_row(j + 1);
-            const R *Sr = cS + (j - j0) * WW;
-            const R *Dr = cD + (j - j0) * WW;
+            R sr[WP], dr[WP];
+            load_row<R, WP>(cS + rr * WP, sr);
+            load_row<R, WP>(cD + rr * WP, dr);
 #pragma unroll
-            for (int i = 0; i < WW; ++i) rfma(v, fma(hq, Sr[i], Dr[i]), xw[i]);
-#pragma unroll
-            for (int i = 0; i + 1 < WW; ++i) xw[i] = xw[i + 1];
-            xw[WW - 1] = nxt;
-        } else {
-            v = Y[(size_t)j * ldg];
+            for (int i = 0; i < WW; ++i) rfma(v, fma(hq, sr[i], dr[i]), xw[rr + i]);
         }
+        R zr[NZB];
+        load_row<R, NZB>(zs + rr * NZB, zr);
 #pragma unroll
-        for (int f = 0; f < NZB; ++f)
-            if (f < nf) rfma(v, zs[f * nr + (j - j0)], r[f]);
-        Y[(size_t)j * ldg] = v;
+        for (int f = 0; f < NZB; ++f) rfma(v, zr[f], r[f]);
+        Y[(size_t)rr * ldg] = v;
     }
 }
 
@@ -1100,9 +1126,9 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
         const int zseg = std::max(1, std::min(8, h->nb / 8));
         na.nseg = zseg;
         const dim3 gz((maxldg + 63) / 64, nbands, nsel), bz(64, zseg);
-        const size_t zsm = (size_t)zseg * 64 * sizeof(R2) + (size_t)h->nzf * h->nb * sizeof(R);
 #define MB_ZX(NZ)                                                                                  \
     do {                                                                                           \
+        const size_t zsm = (size_t)zseg * NZ * 64 * sizeof(R2) + (size_t)h->nzf * h->nb * sizeof(R); \
         MB_CUDA(smem_limit_once((const void *)nl_zx_kernel<R, NZ>, h->device, h->smem_optin));   \
         MB_LAUNCH(h, sa, KN_PROJ, (nl_zx_kernel<R, NZ><<<gz, bz, zsm, sa>>>(na)));                 \
     } while (0)
@@ -1177,32 +1203,48 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     ea.nchunks = nchunks;
     ea.nint = h->nint;
     ea.nz = h->nzf;
-    ea.njseg = nseg;
+    // rows per epilogue thread: at most 8 (FP32) / 4 (FP64), all loaded at once
+    constexpr int ERM = sizeof(R) == 4 ? 8 : 4;
+    const int ejseg = (h->nb + ERM - 1) / ERM;
+    ea.njseg = ejseg;
+    // where each row's local part lives: run boundary bc (between runs bc and
+    // bc+1) starts at interval t1 and owns rows [t1 - 1, t1 + K - 3]
+    if (h->nb > kMaxEpiRows) return MB_EUNSUPPORTED;
+    for (int j = 0; j < h->nb; ++j) {
+        int sv = -1;
+        for (int bc = 0; bc + 1 < nchunks && sv < 0; ++bc) {
+            const int t1 = chunk_begin(bc + 1, h->nint, nchunks);
+            if (j >= t1 - 1 && j <= t1 + h->order - 3) sv = (bc * 2 + 0) * (h->order - 1) + (j - (t1 - 1));
+        }
+        ea.src[j] = (short)sv;
+    }
     std::copy(desc, desc + nsel, ea.d);
     // kinetic term, boundary sums and the KB term of the first 16 z factors;
     // further passes add the KB term of the rest
     const int nzf = (h->nterm > 0 && !tensor) ? h->nzf : 0;
-    const dim3 ge((maxldg + 63) / 64, nbands * nseg, nsel);
+    const dim3 ge((maxldg + 63) / 64, nbands * ejseg, nsel);
     for (int f0 = 0, pass = 0; pass == 0 || f0 < nzf; f0 += 16, ++pass) {
         ea.f0 = f0;
         ea.f1 = std::min(nzf, f0 + 16);
         ea.base = pass == 0;
-        const int nrmax = (h->nb + nseg - 1) / nseg;
         const int HWn = h->order <= 6 ? 5 : 7;
-        const size_t esm = ((size_t)2 * nrmax * (2 * HWn + 1) + (size_t)(ea.f1 - ea.f0) * nrmax) * sizeof(R);
         const int nfp = ea.f1 - ea.f0;
-#define MB_EPI(NZ, HWV)                                                                                   \
-    do {                                                                                                  \
-        MB_CUDA(smem_limit_once((const void *)epilogue_kernel<R, NZ, HWV>, h->device, h->smem_optin));  \
-        MB_LAUNCH(h, s, KN_EPILOGUE, (epilogue_kernel<R, NZ, HWV><<<ge, 64, esm, s>>>(ea)));            \
+        const int nzb = nfp <= 4 ? 4 : nfp <= 8 ? 8 : nfp <= 12 ? 12 : 16;
+        const size_t esm = ((size_t)2 * ERM * ((2 * HWn + 1 + 3) / 4 * 4) + (size_t)ERM * nzb) * sizeof(R);
+#define MB_EPI(NZ, HWV)                                                                                        \
+    do {                                                                                                       \
+        MB_CUDA(smem_limit_once((const void *)epilogue_kernel<R, NZ, HWV, ERM>, h->device, h->smem_optin));  \
+        MB_LAUNCH(h, s, KN_EPILOGUE, (epilogue_kernel<R, NZ, HWV, ERM><<<ge, 64, esm, s>>>(ea)));            \
     } while (0)
         if (HWn == 5) {
-            if (nfp <= 4) MB_EPI(4, 5);
-            else if (nfp <= 8) MB_EPI(8, 5);
+            if (nzb == 4) MB_EPI(4, 5);
+            else if (nzb == 8) MB_EPI(8, 5);
+            else if (nzb == 12) MB_EPI(12, 5);
             else MB_EPI(16, 5);
         } else {
-            if (nfp <= 4) MB_EPI(4, 7);
-            else if (nfp <= 8) MB_EPI(8, 7);
+            if (nzb == 4) MB_EPI(4, 7);
+            else if (nzb == 8) MB_EPI(8, 7);
+            else if (nzb == 12) MB_EPI(12, 7);
             else MB_EPI(16, 7);
         }
 #undef MB_EPI
