@@ -102,12 +102,38 @@ int mb_apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *
 
 int mb_apply_S(mb_handle *h, int ik, const void *X, void *Y, int nbands, int prec, void *stream) {
     if (!h) return MB_EINVAL;
-    return apply_banded(h, BAND_S, ik, X, Y, nbands, prec, (cudaStream_t)stream);
+    const void *xs[1] = {X};
+    void *ys[1] = {Y};
+    return apply_banded_batch(h, BAND_S, 1, &ik, xs, ys, nbands, prec, (cudaStream_t)stream);
 }
 
 int mb_apply_Sinv(mb_handle *h, int ik, const void *X, void *Y, int nbands, int prec, void *stream) {
     if (!h) return MB_EINVAL;
-    return apply_banded(h, BAND_SINV, ik, X, Y, nbands, prec, (cudaStream_t)stream);
+    const void *xs[1] = {X};
+    void *ys[1] = {Y};
+    return apply_banded_batch(h, BAND_SINV, 1, &ik, xs, ys, nbands, prec, (cudaStream_t)stream);
+}
+
+int mb_apply_S_batch(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y, int nbands,
+                     int prec, void *stream) {
+    if (!h) return MB_EINVAL;
+    return apply_banded_batch(h, BAND_S, nsel, iks, X, Y, nbands, prec, (cudaStream_t)stream);
+}
+
+int mb_apply_Sinv_batch(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y, int nbands,
+                        int prec, void *stream) {
+    if (!h) return MB_EINVAL;
+    return apply_banded_batch(h, BAND_SINV, nsel, iks, X, Y, nbands, prec, (cudaStream_t)stream);
+}
+
+int mb_status(mb_handle *h) {
+    if (!h) return MB_EINVAL;
+    if (!h->d_tcerr) return MB_OK;
+    if (cudaSetDevice(h->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return MB_ECUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, h->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MB_ECUDA;
+    if (v && cudaMemset(h->d_tcerr, 0, sizeof(int)) != cudaSuccess) return MB_ECUDA;
+    return v ? MB_ETIMEOUT : MB_OK;
 }
 
 int mb_eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void *evecs,

@@ -757,6 +757,11 @@ int upload_tables(mb_handle *h) {
         MB_CUDA(cudaMemcpy(h->d_zidx, zi.data(), zi.size() * sizeof(int), cudaMemcpyHostToDevice));
     }
     upload_fft_twiddles();
+    if (!h->d_tcerr) {
+        // status word of the kernels' bounded device waits (mb_status)
+        MB_CUDA(cudaMalloc(&h->d_tcerr, sizeof(int)));
+        MB_CUDA(cudaMemset(h->d_tcerr, 0, sizeof(int)));
+    }
     MB_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
     MB_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     MB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
@@ -1273,6 +1278,29 @@ int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X, 
         int rc = prec == MB_FP64 ? apply_H_group<double>(h, n, iks + i0, X + i0, Y + i0, nbands, s, h->t64)
                                  : apply_H_group<float>(h, n, iks + i0, X + i0, Y + i0, nbands, s, h->t32,
                                                         prec == MB_BF16);
+        if (rc) return rc;
+    }
+    return MB_OK;
+}
+
+int banded_block_apply(mb_handle *h, bool inv, int nsel, const int *iks, const void *const *X, void *const *Y,
+                       int nbands, int prec, cudaStream_t s);
+bool banded_block_supported(const mb_handle *h, int prec, bool inv);
+
+int apply_banded_batch(mb_handle *h, int which, int nsel, const int *iks, const void *const *X, void *const *Y,
+                       int nbands, int prec, cudaStream_t s) {
+    if (nsel <= 0 || !iks || !X || !Y || nbands <= 0) return MB_EINVAL;
+    if (which != BAND_S && which != BAND_SINV) return MB_EINVAL;
+    if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return MB_EINVAL;
+    for (int i = 0; i < nsel; ++i) {
+        if (iks[i] < 0 || iks[i] >= (int)h->kp.size() || !X[i] || !Y[i]) return MB_EINVAL;
+        if (X[i] == Y[i]) return MB_EINVAL;
+    }
+    MB_CUDA(cudaSetDevice(h->device));
+    if (banded_block_supported(h, prec, which == BAND_SINV))
+        return banded_block_apply(h, which == BAND_SINV, nsel, iks, X, Y, nbands, prec, s);
+    for (int i = 0; i < nsel; ++i) {
+        const int rc = apply_banded(h, which, iks[i], X[i], Y[i], nbands, prec, s);
         if (rc) return rc;
     }
     return MB_OK;

@@ -147,6 +147,8 @@ int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X,
                   void *const *Y, int nbands, int prec, cudaStream_t s);
 int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nbands,
                  int prec, cudaStream_t s);
+int apply_banded_batch(mb_handle *h, int which, int nsel, const int *iks, const void *const *X,
+                       void *const *Y, int nbands, int prec, cudaStream_t s);
 size_t apply_scratch_bytes(const mb_handle *h, int nk, int nbands, int prec);
 size_t apply_H_scratch_need(const mb_handle *h, int ik, int nbands, int prec);
 int apply_H_on_scratch(mb_handle *h, int ik, const void *X, void *Y, int nbands, int prec, cudaStream_t s,

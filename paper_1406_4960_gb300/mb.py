@@ -25,7 +25,7 @@ EXPORTS = ("mb_setup", "mb_destroy", "mb_sizes", "mb_gvectors", "mb_zplanes",
            "mb_kernel_name", "mb_apply_H_noalloc", "mb_server_create", "mb_server_submit",
            "mb_server_wait", "mb_server_stats", "mb_server_destroy", "mb_autotune",
            "mb_plane_kernel_name", "mb_autotune_report", "mb_plane_kernel_candidates",
-           "mb_plane_kernel_select")
+           "mb_plane_kernel_select", "mb_apply_S_batch", "mb_apply_Sinv_batch", "mb_status")
 
 
 class MBError(RuntimeError):
@@ -102,6 +102,9 @@ def load(build_if_missing: bool = False):
                                      ctypes.c_int, ctypes.c_int, vp]
     lib.mb_apply_S.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     lib.mb_apply_Sinv.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    for fn in (lib.mb_apply_S_batch, lib.mb_apply_Sinv_batch):
+        fn.argtypes = [vp, ctypes.c_int, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp]
+    lib.mb_status.argtypes = [vp]
     lib.mb_eigsolve.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, vp,
                                 ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.mb_strerror.argtypes = [ctypes.c_int]
@@ -336,6 +339,28 @@ class Handle:
         self._check(self._lib.mb_apply_Sinv(self._h, ik, ctypes.c_void_p(X.data_ptr()),
                                             ctypes.c_void_p(Y.data_ptr()), X.shape[0],
                                             self._prec(prec), _stream_ptr(stream)), "mb_apply_Sinv")
+
+    def _banded_batch(self, fn, name, iks, Xs, Ys, prec, stream):
+        n = len(iks)
+        if len(Xs) != n or len(Ys) != n:
+            raise MBError(1, "one X and one Y per k-point")
+        for ik, X, Y in zip(iks, Xs, Ys):
+            if self._check_block(ik, X, prec) != Xs[0].shape[0] or self._check_block(ik, Y, prec) != Xs[0].shape[0]:
+                raise MBError(1, "all blocks need the same band count")
+        ik_arr = (ctypes.c_int * n)(*iks)
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Xs])
+        yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in Ys])
+        self._check(fn(self._h, n, ik_arr, xp, yp, Xs[0].shape[0], self._prec(prec), _stream_ptr(stream)), name)
+
+    def apply_S_batch(self, iks, Xs, Ys, prec="fp64", stream=None):
+        self._banded_batch(self._lib.mb_apply_S_batch, "mb_apply_S_batch", iks, Xs, Ys, prec, stream)
+
+    def apply_Sinv_batch(self, iks, Xs, Ys, prec="fp64", stream=None):
+        self._banded_batch(self._lib.mb_apply_Sinv_batch, "mb_apply_Sinv_batch", iks, Xs, Ys, prec, stream)
+
+    def status(self):
+        """MB_OK, or raises MBError(MB_ETIMEOUT) when a bounded device wait ran out."""
+        self._check(self._lib.mb_status(self._h), "mb_status")
 
     def autotune(self, nbands, prec="fp32"):
         bt, waves, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
