@@ -319,13 +319,10 @@ def kbatch_bench(mb, W, local, args, timed, peak32):
     return out
 
 
-def serve_bench(mb, W, local, args):
-    """The serving stream: Poisson arrivals (50/s) of slab solves drawn from
-    the tiny/slab/graphene workloads (Nz 40-160, 8-80 bands, 1-8 k-points),
-    mixed precision, replayed in real time into the continuous-batching
-    server; a bounded sample of the first --serve-n requests."""
+def serve_run(mb, W, local, args, reqs, prec):
+    """Replay `reqs` in real time (Poisson arrival times) into a fresh
+    continuous-batching server; returns its record."""
     import torch
-    reqs = W.serve_stream()[:args.serve_n]
     free, total = torch.cuda.mem_get_info(local)
     budget = 0.7 * free
     srv = mb.Server(device=local, slots=args.serve_slots, hbm_budget_bytes=budget)
@@ -335,21 +332,44 @@ def serve_bench(mb, W, local, args):
         dt = r.arrival_s - (time.perf_counter() - t0)
         if dt > 0:
             time.sleep(dt)
-        tickets.append(srv.submit(W.request_workload(r), r.nbands, 1e-6, "fp32"))
-    lats, bad = [], 0
+        tickets.append(srv.submit(W.request_workload(r), r.nbands, 1e-6, prec))
+    lats, phases, bad, cycles = [], [], 0, []
     for t in tickets:
-        rc, ev, info, lat = srv.wait(t)
+        rc, ev, info, lat, ph = srv.wait(t, phases=True)
         bad += rc != 0
         lats.append(lat)
+        phases.append(ph)
+        cycles.append(info.cycles)
     elapsed = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
     la = np.array(lats) * 1e3
-    return {"sample": "first %d requests of the 256-request stream" % len(reqs),
-            "slots": args.serve_slots, "hbm_budget_gb": budget / 1e9,
-            "solves_per_s": len(reqs) / elapsed, "p50_ms": float(np.percentile(la, 50)),
-            "p99_ms": float(np.percentile(la, 99)), "failed": int(bad),
-            "peak_running": st["peak_running"], "peak_gb": st["peak_bytes"] / 1e9}
+    ph = np.array(phases)
+    return {"requests": len(reqs), "slots": args.serve_slots, "hbm_budget_gb": budget / 1e9,
+            "seconds": elapsed, "solves_per_s": len(reqs) / elapsed,
+            "p50_ms": float(np.percentile(la, 50)), "p99_ms": float(np.percentile(la, 99)),
+            "mean_queue_ms": 1e3 * float(ph[:, 0].mean()), "mean_setup_ms": 1e3 * float(ph[:, 1].mean()),
+            "mean_solve_ms": 1e3 * float(ph[:, 2].mean()),
+            "setup_share_of_busy": float(ph[:, 1].sum() / max(1e-12, ph[:, 1:].sum())),
+            "failed": int(bad), "peak_running": st["peak_running"], "peak_gb": st["peak_bytes"] / 1e9}
+
+
+def serve_bench(mb, W, local, args):
+    """Config 4, the serving stream: 256 Poisson arrivals (50/s) of slab
+    solves drawn from the tiny/slab/graphene workloads (Nz 40-160, 8-80
+    bands, 1-8 k-points), replayed in real time into the continuous-batching
+    server.  The whole stream in mixed precision, and -- the comparison the
+    stream's FP64 cost allows -- its first --serve-cmp-n requests through a
+    mixed and a plain-FP64 server each."""
+    reqs = W.serve_stream()
+    out = {"mixed": serve_run(mb, W, local, args, reqs[:args.serve_n], "fp32")}
+    if args.serve_cmp_n > 0:
+        pre = reqs[:args.serve_cmp_n]
+        cmp_m = serve_run(mb, W, local, args, pre, "fp32")
+        cmp_p = serve_run(mb, W, local, args, pre, "fp64")
+        out["prefix"] = {"requests": len(pre), "mixed": cmp_m, "fp64": cmp_p,
+                         "mixed_speedup_vs_fp64": cmp_m["solves_per_s"] / cmp_p["solves_per_s"]}
+    return out
 
 
 def _blas_threads():
@@ -543,6 +563,10 @@ def run_ours(args):
         prof = read_profile(hd) if profile else {}
         return (allmax(ms) if sync_ranks else ms), launches, prof
 
+    if args.serve_only:
+        h.close()
+        print(json.dumps({"serve": serve_bench(mb, W, local, args)}))
+        return
     if args.eig_only:
         # one mixed and/or one plain-FP64 solve (for launch lists under ncu)
         if args.eig_workload != "slab":
@@ -735,7 +759,9 @@ def main():
     ap.add_argument("--apply-prec", default="fp32", help="precision of --apply-only")
     ap.add_argument("--apply-tune", action="store_true", help="autotune the launch shape of --apply-only")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-n", type=int, default=12)
+    ap.add_argument("--serve-n", type=int, default=256)
+    ap.add_argument("--serve-cmp-n", type=int, default=12, help="requests of the mixed vs plain-FP64 server comparison")
+    ap.add_argument("--serve-only", action="store_true", help="run the serving section only")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--eig-reps", type=int, default=6)
     ap.add_argument("--eig-prec", default="fp32,fp64", help="precisions of --eig-only (comma-separated)")

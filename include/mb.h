@@ -102,7 +102,13 @@ int mb_setup(const mb_cell *cell, const double *kpts, int nk, double ecut,
              const mb_atom *atoms, int natoms, const mb_opts *opts,
              mb_handle **out);
 
-/* Release everything the handle owns.  NULL is ignored. */
+/* Release everything the handle owns.  NULL is ignored.  The work queued on
+ * the handle's calls must have completed (synchronize the streams passed to
+ * it first; mb_eigsolve returns with its own work done).  Device memory of the
+ * handle -- tables and apply scratch -- is allocated and freed stream-ordered
+ * from the library's memory pool on the handle's own streams, so neither
+ * mb_setup nor mb_destroy waits for other work on the device; the pool keeps
+ * up to 16 GiB of freed memory reserved for the next handle. */
 void mb_destroy(mb_handle *h);
 
 /* Sizes at k-point ik: disc size ng, retained B-splines nb, padded stride
@@ -120,7 +126,8 @@ int mb_zplanes(const mb_handle *h, int *nq, double *zq, double *wq);
 /* Replace the local potential by a caller-given real table
  * V[q][i1][i2] = V(r_par = i1/n1 a1 + i2/n2 a2, z_q) in Ha on the quadrature
  * planes (host, nq*n1*n2 doubles) -- the general local potential of
- * §II.B.1, Eqs. (19)-(20).  Projectors are unchanged. */
+ * §II.B.1, Eqs. (19)-(20).  Projectors are unchanged.  Waits for all work on
+ * the device first (queued applies may still read the old table). */
 int mb_set_local_potential(mb_handle *h, const double *V);
 
 /* Y = H X at k-point ik (§II.B.1: kinetic Eq. (9), local potential through
@@ -296,10 +303,12 @@ int mb_server_create(int device, int slots, double hbm_budget_bytes, mb_server *
 int mb_server_submit(mb_server *srv, const mb_request *req, long long *ticket);
 /* Blocks until the request completes (timeout_s <= 0: no limit; otherwise
  * MB_ETIMEOUT after that many seconds, the request still pending).  evals:
- * host nk*nbands doubles; latency_s: submission to completion.  Returns the
- * request's own status (that of mb_setup / mb_eigsolve). */
+ * host nk*nbands doubles; latency_s: submission to completion; phases: host
+ * array of 3 (queue wait, set-up of the request's handle, solve and
+ * teardown), seconds, summing to latency_s.  Outputs may be NULL.  Returns
+ * the request's own status (that of mb_setup / mb_eigsolve). */
 int mb_server_wait(mb_server *srv, long long ticket, double *evals, mb_solve_info *info,
-                   double *latency_s, double timeout_s);
+                   double *latency_s, double *phases, double timeout_s);
 int mb_server_stats(mb_server *srv, int *queued, int *running, int *peak_running,
                     double *bytes_in_use, double *peak_bytes);
 /* Finishes every queued and running request, then frees the server. */

@@ -11,6 +11,18 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
              const mb_solve_opts *sopts, mb_solve_info *info, cudaStream_t s);
 }
 
+namespace mb {
+int setup_device(mb_handle *h) {
+    if (cudaSetDevice(h->device) != cudaSuccess) return MB_ECUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) {
+        h->smem_optin = (int)prop.sharedMemPerBlockOptin;
+        h->num_sms = prop.multiProcessorCount;
+    }
+    return upload_tables(h);
+}
+}  // namespace mb
+
 extern "C" {
 
 int mb_setup(const mb_cell *cell, const double *kpts, int nk, double ecut, const double *breaks,
@@ -28,14 +40,7 @@ int mb_setup(const mb_cell *cell, const double *kpts, int nk, double ecut, const
         return MB_ECUDA;
     }
     int rc = build_host_tables(h, cell, kpts, nk, ecut, breaks, nbreaks, order, atoms, natoms, opts);
-    if (rc == MB_OK) {
-        cudaDeviceProp prop;
-        if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) {
-            h->smem_optin = (int)prop.sharedMemPerBlockOptin;
-            h->num_sms = prop.multiProcessorCount;
-        }
-        rc = upload_tables(h);
-    }
+    if (rc == MB_OK) rc = setup_device(h);
     if (rc != MB_OK) {
         free_tables(h);
         delete h;
@@ -83,7 +88,8 @@ int mb_set_local_potential(mb_handle *h, const double *V) {
     for (size_t i = 0; i < n; ++i)
         if (!(V[i] == V[i]) || V[i] > 1e300 || V[i] < -1e300) return MB_EINVAL;   // NaN / inf
     h->Vnat.assign(V, V + n);
-    if (cudaSetDevice(h->device) != cudaSuccess) return MB_ECUDA;
+    // the old tables may still be read by queued work on any stream
+    if (cudaSetDevice(h->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return MB_ECUDA;
     return upload_potential(h);
 }
 

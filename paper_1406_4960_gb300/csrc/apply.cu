@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "apply_common.cuh"
 #include "cplx.cuh"
@@ -599,15 +601,43 @@ int cuda_fail(mb_handle *h, cudaError_t e) {
         if (e_ != cudaSuccess) return cuda_fail(h, e_); \
     } while (0)
 
+cudaMemPool_t mb_pool(int device) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(device);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = 16ull << 30;     // up to 16 GiB of freed memory stays reserved for the next handle
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[device] = pool;
+    return pool;
+}
+
+void dev_free(mb_handle *h, void **p) {
+    if (*p) cudaFreeAsync(*p, h->hs);
+    *p = nullptr;
+}
+
+int dev_upload(mb_handle *h, void **dst, const void *src, size_t bytes) {
+    dev_free(h, dst);
+    if (!bytes) return MB_OK;
+    cudaMemPool_t pool = mb_pool(h->device);
+    if (!pool) return MB_ECUDA;
+    MB_CUDA(cudaMallocFromPoolAsync(dst, bytes, pool, h->hs));
+    if (src) MB_CUDA(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, h->hs));
+    return MB_OK;
+}
+
 template <typename R>
 static int upload(mb_handle *h, void **dst, const std::vector<double> &src) {
     std::vector<R> tmp(src.begin(), src.end());
-    if (*dst) cudaFree(*dst);
-    *dst = nullptr;
-    if (tmp.empty()) return MB_OK;
-    MB_CUDA(cudaMalloc(dst, tmp.size() * sizeof(R)));
-    MB_CUDA(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(R), cudaMemcpyHostToDevice));
-    return MB_OK;
+    return dev_upload(h, dst, tmp.data(), tmp.size() * sizeof(R));
 }
 
 template <typename R>
@@ -617,12 +647,7 @@ static int upload_complex(mb_handle *h, void **dst, const std::vector<cdouble> &
         tmp[2 * i] = (R)src[i].real();
         tmp[2 * i + 1] = (R)src[i].imag();
     }
-    if (*dst) cudaFree(*dst);
-    *dst = nullptr;
-    if (tmp.empty()) return MB_OK;
-    MB_CUDA(cudaMalloc(dst, tmp.size() * sizeof(R)));
-    MB_CUDA(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(R), cudaMemcpyHostToDevice));
-    return MB_OK;
+    return dev_upload(h, dst, tmp.data(), tmp.size() * sizeof(R));
 }
 
 template <typename R>
@@ -677,11 +702,13 @@ int upload_potential(mb_handle *h) {
             for (int i2 = 0; i2 < N2; ++i2)
                 vt[((size_t)q * N2 + i2) * N1 + i1] = vn[((size_t)q * N1 + i1) * N2 + i2];
     if ((rc = upload<float>(h, &h->t32.Vt, vt))) return rc;
+    MB_CUDA(cudaStreamSynchronize(h->hs));
     return MB_OK;
 }
 
 int upload_tables(mb_handle *h) {
     MB_CUDA(cudaSetDevice(h->device));
+    if (!h->hs) MB_CUDA(cudaStreamCreateWithFlags(&h->hs, cudaStreamNonBlocking));
     int rc;
     if ((rc = upload_set<double>(h, h->t64))) return rc;
     if ((rc = upload_set<float>(h, h->t32))) return rc;
@@ -689,8 +716,7 @@ int upload_tables(mb_handle *h) {
     std::vector<int> goff((size_t)h->total_ldg, 0);
     for (size_t ik = 0; ik < h->kp.size(); ++ik)
         for (int g = 0; g < h->kp[ik].ng; ++g) goff[h->kofs[ik] + g] = h->kp[ik].goff[g];
-    MB_CUDA(cudaMalloc(&h->d_goff, goff.size() * sizeof(int)));
-    MB_CUDA(cudaMemcpy(h->d_goff, goff.data(), goff.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if ((rc = dev_upload(h, (void **)&h->d_goff, goff.data(), goff.size() * sizeof(int)))) return rc;
     // grid rows that hold disc points, per k-point
     std::vector<int> rows;
     h->rows_ofs.assign(h->kp.size(), 0);
@@ -707,8 +733,7 @@ int upload_tables(mb_handle *h) {
             }
         h->nrows[ik] = (int)rows.size() - h->rows_ofs[ik];
     }
-    MB_CUDA(cudaMalloc(&h->d_rows, rows.size() * sizeof(int)));
-    MB_CUDA(cudaMemcpy(h->d_rows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if ((rc = dev_upload(h, (void **)&h->d_rows, rows.data(), rows.size() * sizeof(int)))) return rc;
     // compact planes: the disc's rows n1min .. n1max become rows 0 .. nocc-1
     // (row stride N2 + 1); the positions of those rows outside the disc
     {
@@ -740,10 +765,8 @@ int upload_tables(mb_handle *h) {
             h->nzero[ik] = (int)zpos.size() - h->zofs[ik];
         }
         if (zpos.empty()) zpos.push_back(0);
-        MB_CUDA(cudaMalloc(&h->d_cpos, cpos.size() * sizeof(int)));
-        MB_CUDA(cudaMemcpy(h->d_cpos, cpos.data(), cpos.size() * sizeof(int), cudaMemcpyHostToDevice));
-        MB_CUDA(cudaMalloc(&h->d_zpos, zpos.size() * sizeof(int)));
-        MB_CUDA(cudaMemcpy(h->d_zpos, zpos.data(), zpos.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if ((rc = dev_upload(h, (void **)&h->d_cpos, cpos.data(), cpos.size() * sizeof(int)))) return rc;
+        if ((rc = dev_upload(h, (void **)&h->d_zpos, zpos.data(), zpos.size() * sizeof(int)))) return rc;
     }
     if (h->nterm > 0) {
         std::vector<int> zi(h->pgroup);
@@ -753,20 +776,22 @@ int upload_tables(mb_handle *h) {
         zi.insert(zi.end(), h->partner.begin(), h->partner.end());
         zi.insert(zi.end(), h->pstart.begin(), h->pstart.end());
         zi.insert(zi.end(), h->plist.begin(), h->plist.end());
-        MB_CUDA(cudaMalloc(&h->d_zidx, zi.size() * sizeof(int)));
-        MB_CUDA(cudaMemcpy(h->d_zidx, zi.data(), zi.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if ((rc = dev_upload(h, (void **)&h->d_zidx, zi.data(), zi.size() * sizeof(int)))) return rc;
     }
     upload_fft_twiddles();
     if (!h->d_tcerr) {
         // status word of the kernels' bounded device waits (mb_status)
-        MB_CUDA(cudaMalloc(&h->d_tcerr, sizeof(int)));
-        MB_CUDA(cudaMemset(h->d_tcerr, 0, sizeof(int)));
+        const int zero = 0;
+        if ((rc = dev_upload(h, &h->d_tcerr, &zero, sizeof(int)))) return rc;
     }
     MB_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
     MB_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     MB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    MB_CUDA(cudaEventCreateWithFlags(&h->scratch_ev, cudaEventDisableTiming));
+    if ((rc = upload_proj_tables(h))) return rc;
+    MB_CUDA(cudaStreamSynchronize(h->hs));      // tables in place before any other stream uses them
     MB_CUDA(cudaGetLastError());
-    return upload_proj_tables(h);
+    return MB_OK;
 }
 
 int ensure_precond(mb_handle *h) {
@@ -780,53 +805,59 @@ int ensure_precond(mb_handle *h) {
     int rc;
     if ((rc = upload<double>(h, &h->t64.Pfac, all))) return rc;
     if ((rc = upload<float>(h, &h->t32.Pfac, all))) return rc;
+    MB_CUDA(cudaStreamSynchronize(h->hs));
     h->pfac_ready = true;
     return MB_OK;
 }
 
-static void free_set(DevTables &t) {
+static void free_set(mb_handle *h, DevTables &t) {
     void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.Lrecip, &t.q2, &t.qproj, &t.zproj, &t.zf, &t.E, &t.Pfac, &t.Vt};
-    for (void **p : ps) {
-        if (*p) cudaFree(*p);
-        *p = nullptr;
-    }
+    for (void **p : ps) dev_free(h, p);
 }
 
+// The caller has finished its work on the handle (mb_destroy's contract):
+// everything is freed stream-ordered on the handle's stream.
 void free_tables(mb_handle *h) {
     cudaSetDevice(h->device);
-    free_set(h->t64);
-    free_set(h->t32);
-    if (h->d_goff) cudaFree(h->d_goff);
-    h->d_goff = nullptr;
-    if (h->d_rows) cudaFree(h->d_rows);
-    h->d_rows = nullptr;
-    if (h->d_cpos) cudaFree(h->d_cpos);
-    h->d_cpos = nullptr;
-    if (h->d_zpos) cudaFree(h->d_zpos);
-    h->d_zpos = nullptr;
-    if (h->d_projB) cudaFree(h->d_projB);
-    h->d_projB = nullptr;
-    if (h->d_zidx) cudaFree(h->d_zidx);
-    h->d_zidx = nullptr;
+    if (!h->hs) cudaStreamCreateWithFlags(&h->hs, cudaStreamNonBlocking);
+    if (h->aux) cudaStreamSynchronize(h->aux);
+    if (h->scratch_ev) cudaEventSynchronize(h->scratch_ev);
+    free_set(h, h->t64);
+    free_set(h, h->t32);
+    dev_free(h, (void **)&h->d_goff);
+    dev_free(h, (void **)&h->d_rows);
+    dev_free(h, (void **)&h->d_cpos);
+    dev_free(h, (void **)&h->d_zpos);
+    dev_free(h, &h->d_projB);
+    dev_free(h, (void **)&h->d_zidx);
+    dev_free(h, &h->d_tcerr);
+    dev_free(h, &h->scratch.ptr);
+    h->scratch = Scratch();
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->scratch_ev) cudaEventDestroy(h->scratch_ev);
     h->aux = nullptr;
-    h->ev_fork = h->ev_join = nullptr;
-    if (h->d_tcerr) cudaFree(h->d_tcerr);
-    h->d_tcerr = nullptr;
-    if (h->scratch.ptr) cudaFree(h->scratch.ptr);
-    h->scratch = Scratch();
+    h->ev_fork = h->ev_join = h->scratch_ev = nullptr;
+    if (h->hs) {
+        cudaStreamSynchronize(h->hs);
+        cudaStreamDestroy(h->hs);
+    }
+    h->hs = nullptr;
 }
 
-int ensure_scratch(mb_handle *h, size_t bytes) {
+// Grows the apply scratch, stream-ordered on the caller's stream s: the old
+// buffer is released once the last apply that used it has finished (its
+// event), the new one is in place when this returns (a host wait on s only).
+int ensure_scratch(mb_handle *h, size_t bytes, cudaStream_t s) {
     if (bytes <= h->scratch.bytes) return MB_OK;
-    if (h->scratch.ptr) {
-        MB_CUDA(cudaDeviceSynchronize());
-        cudaFree(h->scratch.ptr);
-    }
+    if (h->scratch.ptr && h->scratch_ev) MB_CUDA(cudaEventSynchronize(h->scratch_ev));
+    cudaMemPool_t pool = mb_pool(h->device);
+    if (!pool) return MB_ECUDA;
+    if (h->scratch.ptr) MB_CUDA(cudaFreeAsync(h->scratch.ptr, s));
     h->scratch = Scratch();
-    MB_CUDA(cudaMalloc(&h->scratch.ptr, bytes));
+    MB_CUDA(cudaMallocFromPoolAsync(&h->scratch.ptr, bytes, pool, s));
+    MB_CUDA(cudaStreamSynchronize(s));
     h->scratch.bytes = bytes;
     return MB_OK;
 }
@@ -1014,9 +1045,16 @@ static size_t apply_H_need(const mb_handle *h, int nsel, const int *iks, int nba
 template <typename R>
 static int apply_H_group(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y,
                          int nbands, cudaStream_t s, const DevTables &t, bool tensor = false) {
-    int rc = ensure_scratch(h, apply_H_need<R>(h, nsel, iks, nbands, tensor));
+    int rc = ensure_scratch(h, apply_H_need<R>(h, nsel, iks, nbands, tensor), s);
     if (rc) return rc;
-    return apply_H_launch<R>(h, nsel, iks, X, Y, nbands, s, t, reinterpret_cast<char *>(h->scratch.ptr), tensor);
+    rc = apply_H_launch<R>(h, nsel, iks, X, Y, nbands, s, t, reinterpret_cast<char *>(h->scratch.ptr), tensor);
+    if (rc) return rc;
+    // the scratch is in use until this point of s (not recorded during a
+    // capture: scratch never grows then)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MB_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone) MB_CUDA(cudaEventRecord(h->scratch_ev, s));
+    return MB_OK;
 }
 
 // Scratch need of a single-k-point apply, and the apply itself on a scratch

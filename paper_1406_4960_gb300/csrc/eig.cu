@@ -1643,7 +1643,7 @@ struct Solver {
     template <typename T> T *alloc(size_t n) {
         void *p = nullptr;
         if (rc) return nullptr;
-        if (cuda(cudaMallocAsync(&p, std::max<size_t>(n, 1) * sizeof(T), s))) return nullptr;
+        if (cuda(cudaMallocFromPoolAsync(&p, std::max<size_t>(n, 1) * sizeof(T), mb_pool(h->device), s))) return nullptr;
         allocs.push_back(p);
         return reinterpret_cast<T *>(p);
     }
@@ -2275,7 +2275,7 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
                 need = std::max(need, apply_scratch_bytes(h, S.nk, sizes[bi], pi == 0 ? MB_FP64 : MB_FP32));
         S.cuda(cudaStreamSynchronize(s));
         if (S.rc == MB_OK) {
-            int r2 = ensure_scratch(h, need);
+            int r2 = ensure_scratch(h, need, s);
             if (r2) return r2;
         }
     }

@@ -109,6 +109,11 @@ struct mb_handle {
     // plane kernel (fork and join by events, capturable into graphs)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the handle's own stream: its tables are allocated, uploaded and freed
+    // there (stream-ordered, from the library's pool), so setting up or
+    // destroying a handle never waits for other work on the device
+    cudaStream_t hs = nullptr;
+    cudaEvent_t scratch_ev = nullptr;      // recorded after the last apply that used the scratch
     size_t desc_bytes = 0;
     std::string last_cuda_error;
     // plane-kernel launch shapes picked by mb_autotune: (k-points per batch,
@@ -142,7 +147,15 @@ int upload_tables(mb_handle *h);
 int upload_potential(mb_handle *h);
 int ensure_precond(mb_handle *h);
 void free_tables(mb_handle *h);
-int ensure_scratch(mb_handle *h, size_t bytes);
+int ensure_scratch(mb_handle *h, size_t bytes, cudaStream_t s);
+// the library's stream-ordered memory pool on a device (freed memory is kept
+// for reuse up to a threshold instead of being returned at every sync)
+cudaMemPool_t mb_pool(int device);
+// device tables of a handle: allocate + upload on the handle's stream, free there
+int dev_upload(mb_handle *h, void **dst, const void *src, size_t bytes);
+void dev_free(mb_handle *h, void **p);
+// the device half of mb_setup, for host tables already built
+int setup_device(mb_handle *h);
 int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X,
                   void *const *Y, int nbands, int prec, cudaStream_t s);
 int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nbands,

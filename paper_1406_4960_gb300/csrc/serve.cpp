@@ -39,7 +39,8 @@ struct Job {
     int nbands = 0, prec = 0;
     double tol = 0;
     size_t footprint = 0;
-    clk::time_point submitted, started, finished;
+    std::unique_ptr<mb_handle> host;   // host tables, built once at submission
+    clk::time_point submitted, started, setup_done, finished;
     // results
     bool done = false;
     int rc = MB_OK;
@@ -51,7 +52,7 @@ struct Job {
 // apply scratch, and the eigensolver workspace (vectors + small matrices).
 size_t footprint_of(const mb_handle &h, int nbands, int prec) {
     const size_t NN = (size_t)h.n1 * h.n2;
-    size_t tables = (size_t)h.nq * NN * (8 + 4) * 2;                       // V: permuted + natural, FP64 + FP32
+    size_t tables = (size_t)h.nq * NN * ((8 + 4) * 2 + 4);                 // V: permuted + natural (FP64 + FP32), per column (FP32)
     tables += (size_t)h.nq * h.order * 12 + (size_t)h.nb * (2 * h.order - 1) * 12 * 2 + (size_t)h.nb * h.order * 12;
     size_t vec_bytes = 0, pf = 0;
     int maxldg = 0;
@@ -138,13 +139,18 @@ struct mb_server {
         }
     }
 
+    // The device half of the request's set-up (its host tables were built at
+    // submission), the solve, and the teardown; allocations and frees are
+    // stream-ordered on the request's own streams, so none of this waits for
+    // the other requests' work on the device.
     void run(Job &j) {
-        mb_handle *h = nullptr;
-        j.rc = mb_setup(&j.cell, j.kpts.data(), j.nk, j.ecut, j.breaks.data(), (int)j.breaks.size(), j.order,
-                        j.atoms.empty() ? nullptr : j.atoms.data(), (int)j.atoms.size(), &j.opts, &h);
-        if (j.rc != MB_OK) return;
-        j.evals.assign((size_t)j.nk * j.nbands, 0.0);
-        j.rc = mb_eigsolve(h, j.nbands, j.tol, j.prec, j.evals.data(), nullptr, nullptr, &j.info, nullptr);
+        mb_handle *h = j.host.release();
+        j.rc = setup_device(h);
+        j.setup_done = clk::now();
+        if (j.rc == MB_OK) {
+            j.evals.assign((size_t)j.nk * j.nbands, 0.0);
+            j.rc = mb_eigsolve(h, j.nbands, j.tol, j.prec, j.evals.data(), nullptr, nullptr, &j.info, nullptr);
+        }
         mb_destroy(h);
     }
 };
@@ -181,14 +187,17 @@ int mb_server_submit(mb_server *s, const mb_request *r, long long *ticket) {
     job->nbands = r->nbands;
     job->prec = r->prec;
     job->tol = r->tol;
-    // exact sizes from a host-only set-up of the basis
+    // the request's host tables (kept for its set-up) give its exact sizes
     {
-        mb_handle tmp;
-        int rc = build_host_tables(&tmp, &job->cell, job->kpts.data(), job->nk, job->ecut, job->breaks.data(),
-                                   (int)job->breaks.size(), job->order, job->atoms.empty() ? nullptr : job->atoms.data(),
-                                   (int)job->atoms.size(), &job->opts);
+        job->host.reset(new (std::nothrow) mb_handle());
+        if (!job->host) return MB_ENOMEM;
+        job->host->device = s->device;
+        int rc = build_host_tables(job->host.get(), &job->cell, job->kpts.data(), job->nk, job->ecut,
+                                   job->breaks.data(), (int)job->breaks.size(), job->order,
+                                   job->atoms.empty() ? nullptr : job->atoms.data(), (int)job->atoms.size(),
+                                   &job->opts);
         if (rc != MB_OK) return rc;
-        job->footprint = footprint_of(tmp, job->nbands, job->prec);
+        job->footprint = footprint_of(*job->host, job->nbands, job->prec);
     }
     if (job->footprint > s->budget) return MB_ENOMEM;     // could never be admitted
     {
@@ -205,7 +214,7 @@ int mb_server_submit(mb_server *s, const mb_request *r, long long *ticket) {
 }
 
 int mb_server_wait(mb_server *s, long long ticket, double *evals, mb_solve_info *info, double *latency_s,
-                   double timeout_s) {
+                   double *phases, double timeout_s) {
     if (!s) return MB_EINVAL;
     std::shared_ptr<Job> job;
     {
@@ -224,6 +233,11 @@ int mb_server_wait(mb_server *s, long long ticket, double *evals, mb_solve_info 
     if (evals && !job->evals.empty()) std::memcpy(evals, job->evals.data(), sizeof(double) * job->evals.size());
     if (info) *info = job->info;
     if (latency_s) *latency_s = std::chrono::duration<double>(job->finished - job->submitted).count();
+    if (phases) {
+        phases[0] = std::chrono::duration<double>(job->started - job->submitted).count();
+        phases[1] = std::chrono::duration<double>(job->setup_done - job->started).count();
+        phases[2] = std::chrono::duration<double>(job->finished - job->setup_done).count();
+    }
     return job->rc;
 }
 

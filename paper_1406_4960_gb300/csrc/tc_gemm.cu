@@ -141,18 +141,8 @@ int upload_proj_tables(mb_handle *h) {
             }
         all.insert(all.end(), b1.begin(), b1.end());
     }
-    if (h->d_projB) cudaFree(h->d_projB);
-    h->d_projB = nullptr;
-    cudaError_t e = cudaMalloc(&h->d_projB, all.size() * sizeof(__nv_bfloat16));
-    if (e != cudaSuccess) return cuda_fail(h, e);
-    e = cudaMemcpy(h->d_projB, all.data(), all.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(h, e);
-    if (!h->d_tcerr) {
-        e = cudaMalloc(&h->d_tcerr, sizeof(int));
-        if (e != cudaSuccess) return cuda_fail(h, e);
-        cudaMemset(h->d_tcerr, 0, sizeof(int));
-    }
-    return MB_OK;
+    // uploaded on the handle's stream (upload_tables waits for it before returning)
+    return dev_upload(h, &h->d_projB, all.data(), all.size() * sizeof(__nv_bfloat16));
 }
 
 // one projector contraction for a group of k-points (mode 0 or 1)

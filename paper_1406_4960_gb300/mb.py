@@ -119,7 +119,7 @@ def load(build_if_missing: bool = False):
     lib.mb_apply_H_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     lib.mb_server_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(vp)]
     lib.mb_server_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_longlong)]
-    lib.mb_server_wait.argtypes = [vp, ctypes.c_longlong, dp, ctypes.POINTER(SolveInfo), dp, ctypes.c_double]
+    lib.mb_server_wait.argtypes = [vp, ctypes.c_longlong, dp, ctypes.POINTER(SolveInfo), dp, dp, ctypes.c_double]
     lib.mb_server_stats.argtypes = [vp, ip, ip, ip, dp, dp]
     lib.mb_server_destroy.argtypes = [vp]
     lib.mb_server_destroy.restype = None
@@ -186,13 +186,17 @@ class Server:
         self._meta[t.value] = (kp.shape[0], int(nbands))
         return t.value
 
-    def wait(self, ticket, timeout_s=0.0):
+    def wait(self, ticket, timeout_s=0.0, phases=False):
+        """(rc, eigenvalues (nk, nbands), SolveInfo, latency s[, (queue, setup, solve) s])."""
         nk, nb = self._meta.pop(ticket)
         ev = np.zeros(nk * nb)
         info = SolveInfo()
         lat = ctypes.c_double()
+        ph = np.zeros(3)
         rc = self._lib.mb_server_wait(self._s, ticket, _dptr(ev), ctypes.byref(info), ctypes.byref(lat),
-                                      float(timeout_s))
+                                      _dptr(ph), float(timeout_s))
+        if phases:
+            return rc, ev.reshape(nk, nb), info, lat.value, tuple(ph)
         return rc, ev.reshape(nk, nb), info, lat.value
 
     def stats(self):
