@@ -35,6 +35,11 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The serving section runs up to 8 requests at once, each with a solve
+# stream, a projector stream and a set-up stream: give the process enough
+# hardware work queues that a request's set-up copies do not wait behind
+# another request's kernels (read when the CUDA context is created).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "Hψ GB/s & eigensolves/s at 1e-6 Ha vs plain FP64 GPU; p50/p99 solve latency"
 # The plane kernel's sources: its DRAM traffic (from an ncu capture, recorded

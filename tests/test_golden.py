@@ -49,3 +49,12 @@ def test_kbatch_golden_shape():
         ev = np.array(r[1:], dtype=float)
         assert ev.shape == (w.nbands,)
         assert np.all(np.diff(ev) >= 0)
+
+
+def test_graphene_golden_shape():
+    w = W.graphene()
+    rows = _rows("graphene_eigs.txt")
+    assert len(rows) == 1
+    ev = np.array(rows[0], dtype=float)
+    assert ev.shape == (w.nbands,)
+    assert np.all(np.diff(ev) >= 0)

@@ -219,18 +219,22 @@ def test_eigsolve_full_slab_matches_oracle_golden(mbmod, prec):
     h.close()
 
 
-def test_eigsolve_full_graphene_mixed_matches_fp64(mbmod):
-    """The 4x4 graphene cell (1417 G x 77 splines, 80 roots, 128 projectors,
+def test_eigsolve_full_graphene_matches_oracle_golden(mbmod):
+    """The 4x4 graphene cell (1417 G x 80 splines, 80 roots, 128 projectors,
     64x64 grid): the mixed-precision solve (FP32 bulk cycles, FP64 finish)
-    against the plain FP64 solve, both at the benchmark tolerance.  The
-    oracle's dense or matrix-free solve of this cell is out of reach in test
-    time, so this case checks the two GPU paths against each other; the slab
-    cases above check both against the oracle."""
+    and the plain FP64 solve at the benchmark tolerance, against the
+    oracle's own Lanczos-Krylov eigenvalues (golden/make_graphene_eigs.py,
+    residual < 1e-9) and against each other."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "graphene_eigs.txt")
+    ref = np.array([l.split() for l in open(path) if l.strip() and not l.startswith("#")][0], dtype=float)
     w = W.graphene()
     h = mbmod.Handle.from_workload(w)
     e32, i32 = h.eigsolve(w.nbands, 1e-6, "fp32")
     e64, i64 = h.eigsolve(w.nbands, 1e-6, "fp64")
     assert i32.max_residual < 1e-6 and i64.max_residual < 1e-6
+    assert np.abs(e32[0] - ref).max() < EV_TOL, np.abs(e32[0] - ref).max()
+    assert np.abs(e64[0] - ref).max() < EV_TOL, np.abs(e64[0] - ref).max()
     assert np.abs(e32 - e64).max() < EV_TOL, np.abs(e32 - e64).max()
     assert i32.finish_cycles < i32.cycles          # the bulk cycles did run in FP32
     h.close()
