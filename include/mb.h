@@ -157,8 +157,11 @@ int mb_apply_H_batch(mb_handle *h, int nsel, const int *iks,
  *
  *   - The array is a file-scope __device__ object: every GPU on which the
  *     library's device code is loaded holds it until the process exits.
- *   - The first call on a device looks the array's address up on that device
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Each call made outside stream capture looks the array's address up on
+ *     the handle's device (cudaGetSymbolAddress); a call inside a capture
+ *     uses the address of the last uncaptured call on that device, so make
+ *     the first call on a device before any stream capture (a first call
+ *     inside a capture returns MB_EINVAL).
  *   - Every call, from every handle, shares the one array and leaves its
  *     contents behind.  Nothing in it has to start at zero (each element is
  *     written before it is read), but calls whose work overlaps on the GPU --
@@ -237,7 +240,8 @@ int mb_eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals,
  * keeps the fastest for later applies and eigensolves of that shape.  The
  * candidates: in FP32, every compiled instance of the compact-plane kernel
  * that can run the batch (they differ in threads and bands per CTA, CTAs per
- * SM and where the window of X rows lives); the register-FFT / radix-2
+ * SM and where the window of X rows lives), each as a static grid and as a
+ * persistent launch fed by a device work queue; the register-FFT / radix-2
  * kernels with 1-4 bands per CTA; each with the built-in run count and with
  * explicit wave targets.  Set-up time call (allocates; not during stream
  * capture).  best_bt: bands per CTA of a register-FFT / radix-2 choice, or
@@ -267,9 +271,12 @@ int mb_plane_kernel_candidates(const mb_handle *h, int nk, int nbands, int prec,
 /* Fix the plane-kernel choice for applies of that shape instead of timing
  * it: id >= 0 a compact-plane instance from mb_plane_kernel_candidates,
  * -1 the default choice, -2 the register-FFT / radix-2 kernels; waves as
- * mb_autotune reports it (0: the built-in run count).  MB_EINVAL for an id
- * that cannot run the batch. */
-int mb_plane_kernel_select(mb_handle *h, int nk, int nbands, int prec, int id, int waves);
+ * mb_autotune reports it (0: the built-in run count); persistent != 0: the
+ * compact-plane kernel's persistent launch, one CTA per resident slot taking
+ * (k-point, band tile, interval run) items from a device work queue.
+ * MB_EINVAL for an id that cannot run the batch. */
+int mb_plane_kernel_select(mb_handle *h, int nk, int nbands, int prec, int id, int waves,
+                           int persistent);
 
 /* ---- continuous-batching solve server ---------------------------------
  * Serves mb_eigsolve requests of mixed sizes on one device.  Submitted

@@ -784,6 +784,10 @@ int upload_tables(mb_handle *h) {
         const int zero = 0;
         if ((rc = dev_upload(h, &h->d_tcerr, &zero, sizeof(int)))) return rc;
     }
+    {
+        const int zeros[2] = {0, 0};
+        if ((rc = dev_upload(h, (void **)&h->d_queue, zeros, sizeof(zeros)))) return rc;
+    }
     MB_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
     MB_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     MB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
@@ -831,6 +835,7 @@ void free_tables(mb_handle *h) {
     dev_free(h, &h->d_projB);
     dev_free(h, (void **)&h->d_zidx);
     dev_free(h, &h->d_tcerr);
+    dev_free(h, (void **)&h->d_queue);
     dev_free(h, &h->scratch.ptr);
     h->scratch = Scratch();
     if (h->aux) cudaStreamDestroy(h->aux);
@@ -866,6 +871,7 @@ int ensure_scratch(mb_handle *h, size_t bytes, cudaStream_t s) {
 struct PlanePlan {
     bool reg = false;      // register-FFT kernel (else radix-2 shared-memory kernel)
     bool p32 = false;      // FP32 compact-plane kernel
+    bool persist = false;  // its persistent, work-queue launch
     Plane32Shape sh;       // its instance
     int bt = 1;            // bands per CTA
     int np = 1;            // planes in flight
@@ -905,12 +911,13 @@ static PlanePlan plan_plane(const mb_handle *h, int nsel, const int *iks, int nb
     int ctas_per_sm = 1;
     // defaults, or the shape mb_autotune measured fastest for this batch
     const bool small = h->n1 <= 32 && h->n2 <= 32;
-    int bt_max = small ? 2 : 1, waves = 0, p32_id = -1;
+    int bt_max = small ? 2 : 1, waves = 0, p32_id = -1, persist = 0;
     auto it = h->tuned.find(std::make_tuple(nsel, nbands, c2 == 16 ? 1 : 0));
     if (it != h->tuned.end()) {
         bt_max = it->second.bt;
         waves = it->second.waves;
         p32_id = it->second.p32;
+        persist = it->second.persist;
     }
     const int nmax_chunks = std::max(1, std::min(kMaxChunks, h->nint / K));   // runs of >= K intervals
     if (c2 == 8 && p32_id != -2) {
@@ -932,6 +939,7 @@ static PlanePlan plan_plane(const mb_handle *h, int nsel, const int *iks, int nb
                 while (nch < nmax_chunks && smem_of(nch) > budget) ++nch;
                 if (smem_of(nch) > budget) continue;
                 p.p32 = true;
+                p.persist = persist != 0;
                 p.sh = sh;
                 p.bt = sh.bt;
                 p.np = sh.bt * P;
@@ -1216,10 +1224,13 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     pa.nsel = nsel;
     pa.bt = plan.bt;
     pa.np = plan.np;
+    pa.queue = plan.persist ? h->d_queue : nullptr;
     std::copy(desc, desc + nsel, pa.d);
     if (plan.p32) {
         if constexpr (sizeof(R) == 4) {
-            const unsigned grid = (unsigned)(nsel * ((nbands + plan.bt - 1) / plan.bt) * nchunks);
+            const unsigned items = (unsigned)(nsel * ((nbands + plan.bt - 1) / plan.bt) * nchunks);
+            const unsigned grid =
+                plan.persist ? std::min(items, (unsigned)(h->num_sms * plan.sh.ctas_per_sm)) : items;
             cudaError_t e = cudaSuccess;
             MB_LAUNCH(h, s, KN_PLANE, e = plane32_launch(pa, plan.sh, grid, plan.smem, s));
             MB_CUDA(e);
@@ -1417,12 +1428,14 @@ int autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves, 
         Plane32Shape shapes[kMaxPlane32Shapes];
         const int ns = plane32_shapes(h->n1, h->n2, h->order, h->nquad, nocc_max, maxldg, shapes, kMaxPlane32Shapes);
         for (int v = 0; v < ns; ++v)
-            for (int waves : {0, 1, 2, 4, 8}) {
-                mb_handle::Tuned t;
-                t.p32 = shapes[v].id;
-                t.waves = waves;
-                cand.push_back(t);
-            }
+            for (int persist : {0, 1})
+                for (int waves : {0, 1, 2, 4, 8}) {
+                    mb_handle::Tuned t;
+                    t.p32 = shapes[v].id;
+                    t.waves = waves;
+                    t.persist = persist;
+                    cand.push_back(t);
+                }
     }
     for (int bt = small ? 4 : 2; bt >= 1; --bt)
         for (int waves : {0, 1, 2, 4, 8}) {
@@ -1453,7 +1466,7 @@ int autotune(mb_handle *h, int nbands, int prec, int *best_bt, int *best_waves, 
         if (rc == MB_OK) {
             char line[256];
             std::snprintf(line, sizeof(line), "%s bands/CTA %d waves %d: %.4f ms\n", name,
-                          c.p32 >= 0 ? 0 : c.bt, c.waves, ms / 5);
+                          c.p32 >= 0 ? 0 : c.bt, c.waves, ms / 5);   // the name says "persistent" for the queue launch
             h->tune_report += line;
         }
         if (rc == MB_OK && ms / 5 < best) {
@@ -1487,7 +1500,7 @@ int plane_kernel_name(const mb_handle *h, int nk, int nbands, int prec, char *bu
                                      : plane_reg_supported<float>(h->n1, h->n2, h->order);
     const PlanePlan p = plan_plane(h, nk, iks.data(), nbands, c2, reg);
     char tmp[128];
-    if (p.p32) std::snprintf(tmp, sizeof(tmp), "%s", p.sh.name);
+    if (p.p32) std::snprintf(tmp, sizeof(tmp), "%s%s", p.sh.name, p.persist ? " persistent" : "");
     else if (p.reg) std::snprintf(tmp, sizeof(tmp), "plane_reg_kernel<%s, %d, %d, %d>", c2 == 8 ? "float" : "double", h->n1, h->n2, h->order);
     else std::snprintf(tmp, sizeof(tmp), "plane_kernel<%s>", c2 == 8 ? "float" : "double");
     std::snprintf(buf, (size_t)len, "%s", tmp);
@@ -1527,7 +1540,8 @@ extern "C" int mb_plane_kernel_candidates(const mb_handle *h, int nk, int nbands
     return mb::plane_candidates(h, nk, prec, ids, max);
 }
 
-extern "C" int mb_plane_kernel_select(mb_handle *h, int nk, int nbands, int prec, int id, int waves) {
+extern "C" int mb_plane_kernel_select(mb_handle *h, int nk, int nbands, int prec, int id, int waves,
+                                      int persistent) {
     if (!h || nk < 1 || nbands < 1 || waves < 0 || id < -2) return MB_EINVAL;
     if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return MB_EINVAL;
     if (id >= 0) {
@@ -1540,6 +1554,7 @@ extern "C" int mb_plane_kernel_select(mb_handle *h, int nk, int nbands, int prec
     mb_handle::Tuned t;
     t.p32 = id;
     t.waves = waves;
+    t.persist = persistent ? 1 : 0;
     t.bt = h->n1 <= 32 && h->n2 <= 32 ? 2 : 1;
     h->tuned[std::make_tuple(std::min(std::min(nk, (int)h->kp.size()), mb::kMaxK), nbands, prec == MB_FP64 ? 1 : 0)] = t;
     return MB_OK;

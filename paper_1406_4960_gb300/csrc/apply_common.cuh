@@ -48,6 +48,7 @@ template <typename R> struct PlaneArgs {
     int nbands, nchunks, chunk, np, ldg_max;
     int nsel;
     int bt;           // bands per CTA (register-FFT kernel)
+    int *queue;       // compact-plane kernel, persistent mode: {next item, finished CTAs}, zero between launches
     KDesc d[kMaxK];
 };
 

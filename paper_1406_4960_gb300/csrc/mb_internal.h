@@ -114,12 +114,13 @@ struct mb_handle {
     // destroying a handle never waits for other work on the device
     cudaStream_t hs = nullptr;
     cudaEvent_t scratch_ev = nullptr;      // recorded after the last apply that used the scratch
+    int *d_queue = nullptr;                // work-queue counters of the persistent plane kernel (2 ints)
     size_t desc_bytes = 0;
     std::string last_cuda_error;
     // plane-kernel launch shapes picked by mb_autotune: (k-points per batch,
     // bands, FP64?) -> (largest bands per CTA of the radix-2 / register-FFT
     // kernels, resident-CTA waves, compact-plane kernel instance id or -1)
-    struct Tuned { int bt = 1; int waves = 0; int p32 = -1; };
+    struct Tuned { int bt = 1; int waves = 0; int p32 = -1; int persist = 0; };
     std::map<std::tuple<int, int, int>, Tuned> tuned;
     std::string tune_report;         // the last mb_autotune's candidates and times
     // launch accounting (always on) and optional per-kernel event timing

@@ -23,18 +23,26 @@ std::mutex g_scratch_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
 }  // namespace
 
-// Device address of g_noalloc_scratch on the handle's device, looked up once
-// per device with that device current.
-static int noalloc_scratch(mb_handle *h, void **out) {
+// Device address of g_noalloc_scratch on the handle's device, with that device
+// current.  Outside stream capture it is looked up on every call (so a
+// re-created context never leaves a stale address behind); inside a capture
+// the address of the last uncaptured call on that device is used, and a
+// first call inside a capture is refused (MB_EINVAL).
+static int noalloc_scratch(mb_handle *h, cudaStream_t s, void **out) {
     if (h->device < 0 || h->device >= kMaxDevices) return MB_EINVAL;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return cuda_fail(h, e);
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[h->device]) {
-        cudaError_t e = cudaSetDevice(h->device);
-        if (e != cudaSuccess) return cuda_fail(h, e);
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(h, e);
         g_scratch_ptr[h->device] = p;
+    } else if (!g_scratch_ptr[h->device]) {
+        return MB_EINVAL;
     }
     *out = g_scratch_ptr[h->device];
     return MB_OK;
@@ -51,9 +59,7 @@ extern "C" int mb_apply_H_noalloc(mb_handle *h, int ik, const void *X, void *Y, 
     if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return MB_EINVAL;
     if (apply_H_scratch_need(h, ik, nbands, prec) > (size_t)MB_NOALLOC_SCRATCH_BYTES) return MB_EINVAL;
     void *scratch = nullptr;
-    int rc = noalloc_scratch(h, &scratch);
+    int rc = noalloc_scratch(h, (cudaStream_t)stream, &scratch);
     if (rc) return rc;
-    cudaError_t e = cudaSetDevice(h->device);
-    if (e != cudaSuccess) return cuda_fail(h, e);
     return apply_H_on_scratch(h, ik, X, Y, nbands, prec, (cudaStream_t)stream, scratch);
 }

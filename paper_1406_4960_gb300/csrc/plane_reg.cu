@@ -367,7 +367,7 @@ cudaError_t plane_reg_launch<double>(const PlaneArgs<double> &a, unsigned grid, 
 // each interval; 1: registers; 2: per-thread slots in shared memory (row j in
 // slot j mod kappa), the new row loaded one interval ahead.
 template <int N1, int N2, int NOCC, int BT, int T, int GPT, int CTAS, int XM, bool VPRE>
-__global__ void __launch_bounds__(T, CTAS) plane32_kernel(const __grid_constant__ PlaneArgs<float> a) {
+__device__ __forceinline__ void plane32_item(const PlaneArgs<float> &a, const int item) {
     constexpr int K = 6, P = 6, KP = K * P;
     constexpr int LDP = N2 + 1, PS = NOCC * LDP, NPL = BT * P;
 
@@ -380,8 +380,8 @@ __global__ void __launch_bounds__(T, CTAS) plane32_kernel(const __grid_constant_
     constexpr bool XREG = XM == 1;
 
     const int nbt = (a.nbands + BT - 1) / BT;
-    const int c = blockIdx.x % a.nchunks;
-    const int kb = blockIdx.x / a.nchunks;
+    const int c = item % a.nchunks;
+    const int kb = item / a.nchunks;
     const int btile = kb % nbt, ks = kb / nbt;
     const KDesc &d = a.d[ks];
     const int ldg = d.ldg, ng = d.ng, nb = a.nb, nint = a.nint, nocc = d.nocc;
@@ -636,6 +636,35 @@ __global__ void __launch_bounds__(T, CTAS) plane32_kernel(const __grid_constant_
 #pragma unroll
             for (int b = 0; b < BT; ++b)
                 if (b < nbb) dst[(size_t)b * dstride + g] = acc[((size_t)b * K + sl) * lda + g];
+        }
+    }
+}
+
+// One launch covers every (k-point, band tile, run of intervals) item of the
+// batch.  Static mode: CTA i takes item i.  Persistent mode (a.queue set):
+// the grid is one CTA per resident slot, and each CTA takes the next item
+// from a device counter until none is left, so items of uneven cost (the
+// k-points' discs differ in size) balance over the SMs; the last CTA to
+// finish resets the counter pair, which leaves it ready for the next launch
+// (and for replays of a captured graph) without a separate memset.
+template <int N1, int N2, int NOCC, int BT, int T, int GPT, int CTAS, int XM, bool VPRE>
+__global__ void __launch_bounds__(T, CTAS) plane32_kernel(const __grid_constant__ PlaneArgs<float> a) {
+    __shared__ int s_item;
+    const int nitems = a.nsel * ((a.nbands + BT - 1) / BT) * a.nchunks;
+    for (int pass = 0;; ++pass) {
+        if (threadIdx.x == 0) s_item = a.queue ? atomicAdd(a.queue, 1) : (pass == 0 ? (int)blockIdx.x : nitems);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= nitems) break;
+        plane32_item<N1, N2, NOCC, BT, T, GPT, CTAS, XM, VPRE>(a, item);
+        __syncthreads();
+    }
+    if (a.queue && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.queue + 1, 1) == (int)gridDim.x - 1) {
+            atomicExch(a.queue, 0);
+            atomicExch(a.queue + 1, 0);
         }
     }
 }

@@ -127,7 +127,8 @@ def load(build_if_missing: bool = False):
     lib.mb_plane_kernel_name.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
     lib.mb_autotune_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_int]
     lib.mb_plane_kernel_candidates.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int]
-    lib.mb_plane_kernel_select.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.mb_plane_kernel_select.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int]
     lib.mb_kernel_name.argtypes = [ctypes.c_int]
     lib.mb_kernel_name.restype = ctypes.c_char_p
     _lib = lib
@@ -380,9 +381,9 @@ class Handle:
             raise MBError(-n, "mb_plane_kernel_candidates")
         return list(ids[:n])
 
-    def plane_kernel_select(self, nk, nbands, prec, kernel_id, waves=0):
+    def plane_kernel_select(self, nk, nbands, prec, kernel_id, waves=0, persistent=False):
         self._check(self._lib.mb_plane_kernel_select(self._h, int(nk), int(nbands), self._prec(prec), int(kernel_id),
-                                                     int(waves)), "mb_plane_kernel_select")
+                                                     int(waves), 1 if persistent else 0), "mb_plane_kernel_select")
 
     def autotune_report(self):
         buf = ctypes.create_string_buffer(1 << 16)

@@ -316,8 +316,10 @@ def test_apply_bf16_matches_oracle(mbmod, case):
 @pytest.mark.parametrize("case", ["tiny", "slab-small", "graphene-small", "kbatch-small"])
 def test_every_plane_kernel_instance_matches_oracle(mbmod, case):
     """Every compiled compact-plane instance that can run the batch (the
-    autotuner may pick any of them), and the register-FFT kernel beside
-    them, with two run counts each, against the oracle in FP32."""
+    autotuner may pick any of them), as a static grid and as a persistent
+    work-queue launch, and the register-FFT kernel beside them, with two run
+    counts each, against the oracle in FP32.  The persistent launches run
+    back to back, so each starts from the counters the previous one reset."""
     w = CASES[case]()
     h = mbmod.Handle.from_workload(w)
     ids = h.plane_kernel_candidates(w.nk, w.nbands, "fp32")
@@ -334,8 +336,10 @@ def test_every_plane_kernel_instance_matches_oracle(mbmod, case):
         Xs.append(torch.from_numpy(lib_block(X, perm, ldg, np.complex64)).cuda())
     refs = [models[ik].apply_H(Xo[ik]) for ik in range(w.nk)]
     for kid in ids + [-2]:
-        for waves in (0, 8):
-            h.plane_kernel_select(w.nk, w.nbands, "fp32", kid, waves)
+        for waves, persistent in ((0, False), (8, False), (0, True), (8, True)):
+            if kid == -2 and persistent:
+                continue
+            h.plane_kernel_select(w.nk, w.nbands, "fp32", kid, waves, persistent)
             Ys = [torch.full_like(x, complex(np.nan, np.nan)) for x in Xs]
             h.apply_H_batch(list(range(w.nk)), Xs, Ys, "fp32")
             torch.cuda.synchronize()
