@@ -43,11 +43,13 @@ os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "Hψ GB/s & eigensolves/s at 1e-6 Ha vs plain FP64 GPU; p50/p99 solve latency"
 # The plane kernel's sources: its DRAM traffic (from an ncu capture, recorded
-# in the profile summary below) is reported only while these are unchanged.
-PLANE_SOURCES = ("plane_reg.cu", "apply_common.cuh", "cplx.cuh", "apply.cu")
+# in the profile summary below with the kernel instance) is reported only
+# while these are unchanged and the same instance runs.
+PLANE_SOURCES = ("plane_reg.cu", "apply_common.cuh", "cplx.cuh")
 PLANE_PROFILES = {
-    "slab": "profiles/plane_reg_kernel_slab_fp32.md",
-    "graphene": "profiles/plane_reg_kernel_graphene_fp32.md",
+    "slab": "profiles/plane32_kernel_slab_fp32.md",
+    "graphene": "profiles/plane32_kernel_graphene_fp32.md",
+    "kbatch": "profiles/plane32_kernel_kbatch_fp32.md",
 }
 
 
@@ -61,20 +63,26 @@ def plane_sources_hash():
     return d.hexdigest()[:16]
 
 
-def plane_traffic(workload):
+def plane_traffic(workload, kernel):
     """(bytes per launch, note): dram__bytes_read.sum + dram__bytes_write.sum of
     one plane-kernel launch from the committed ncu summary, or None when the
-    summary is missing or was taken on other kernel sources."""
+    summary is missing, was taken on other kernel sources or of another
+    kernel instance."""
     import re
     path = os.path.join(ROOT, PLANE_PROFILES.get(workload, ""))
     if not os.path.isfile(path):
         return None, "no ncu summary for this workload"
-    m = re.search(r"traffic per launch: (\d+) bytes; kernel sources sha256 = ([0-9a-f]{16})", open(path).read())
-    if not m:
+    lines = re.findall(r"traffic per launch: (\d+) bytes; kernel = (.+?); kernel sources sha256 = ([0-9a-f]{16})",
+                       open(path).read())
+    if not lines:
         return None, "ncu summary has no traffic line"
-    if m.group(2) != plane_sources_hash():
-        return None, "kernel sources changed since the ncu capture"
-    return float(m.group(1)), "ncu capture of the current kernel (%s)" % PLANE_PROFILES[workload]
+    want = kernel.replace(" persistent", "").strip()
+    for nbytes, name, sha in lines:
+        if name.strip() == want:
+            if sha != plane_sources_hash():
+                return None, "kernel sources changed since the ncu capture"
+            return float(nbytes), "ncu capture of this instance (%s)" % PLANE_PROFILES[workload]
+    return None, "no ncu capture of this instance"
 
 
 def _peaks():
@@ -476,7 +484,7 @@ def plane_roofline(prof_plane, flops_per_step, steps, step_ms, kernel, workload,
     per_launch_ms = t / c
     launches_per_step = max(1, c // steps)
     ach = flops_per_step / launches_per_step / (per_launch_ms * 1e-3) / 1e12
-    traffic, note = plane_traffic(workload)
+    traffic, note = plane_traffic(workload, kernel)
     derived = 152 * 128 * 2 * 2.070e-3
     p = peak if peak else derived
     return {"bound": "alu", "achieved": ach, "peak": p, "unit": "TFLOP/s", "frac": ach / p,
@@ -591,6 +599,8 @@ def run_ours(args):
             w = W.BY_NAME[args.apply_workload]()
             h = mb.Handle.from_workload(w, device=local)
         tune = h.autotune(w.nbands, args.apply_prec) if args.apply_tune else None
+        if args.apply_kernel is not None:
+            h.plane_kernel_select(w.nk, w.nbands, args.apply_prec, args.apply_kernel, 0, args.apply_persistent)
         ms, _, _ = timed(h, w, args.apply_prec, args.steps, args.warmup)
         _, _, prof = timed(h, w, args.apply_prec, args.steps, 2, profile=2)
         if tune:
@@ -763,6 +773,8 @@ def main():
     ap.add_argument("--apply-workload", default="slab", help="workload of --apply-only")
     ap.add_argument("--apply-prec", default="fp32", help="precision of --apply-only")
     ap.add_argument("--apply-tune", action="store_true", help="autotune the launch shape of --apply-only")
+    ap.add_argument("--apply-kernel", type=int, default=None, help="compact-plane instance id for --apply-only")
+    ap.add_argument("--apply-persistent", action="store_true", help="persistent launch for --apply-kernel")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-n", type=int, default=256)
     ap.add_argument("--serve-cmp-n", type=int, default=12, help="requests of the mixed vs plain-FP64 server comparison")
