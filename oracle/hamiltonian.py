@@ -12,6 +12,12 @@ Elements, in Hartree (the paper's Rydberg -nabla^2 becomes -nabla^2/2):
       V = sum_atoms I(i; a, R_z; i') exp(-i dG.R_par) (A/A_c)(pi/a) exp(-|dG|^2/4a)
   with I by the z quadrature and dG wrapped onto the in-plane FFT grid (the
   grid on which the potential is tabulated; see ``wrap``);
+* the core term -Z erf(r/R_c)/r of Eq. (10): the Coulomb potential of the
+  Gaussian core charge rho_c, taken through the 2D transform of 1/r as in the
+  Coulomb integral of §II.B.1; its in-plane components depend on z and g
+  together (``core_term``), so its elements are
+      <i|V_core|i'>(dG) = sum_q w_q B_i(z_q) B_i'(z_q) V_core(z_q, dG)
+  (the general local-potential form, Eqs. (19)-(20));
 * a general local potential given by its in-plane Fourier components per z,
   Eqs. (19)-(20): <i|V|i'>(dG) = int B_i B_i' V(z, dG) dz;
 * Kleinman-Bylander projectors, Eqs. (14)-(17) and the Z.Q factorization that
@@ -32,13 +38,24 @@ Readings:
 * one Gaussian radius per atom: alpha_0 = alpha_1 = 1 / (2 r_c^2);
 * dG is wrapped to the grid frequency range [-N/2, N/2) per axis, which is what
   a product on an N1 x N2 grid computes; the unwrapped element differs by terms
-  of size exp(-g_Nyquist^2 / 4a).
+  of size exp(-g_Nyquist^2 / 4a);
+* the core term's sign is the one Eq. (10) prints (attractive for Z > 0); the
+  Coulomb integral's rho carries the electron's sign convention;
+* the core term at g = 0: (2 pi/g) times the cell's net core charge diverges
+  as g -> 0 and does not depend on z; it is dropped (in a neutral cell it
+  cancels against the electrons' Hartree term, and a constant only shifts
+  every eigenvalue by itself).  The z-dependent remainder,
+  +(2 pi/A_c) int dz' rho_c(z') |z - z'|, is kept;
+* the core term is tabulated on the grid as a real potential, so a coefficient
+  enters as (c(m) + conj(c(-m))) / 2, with -m wrapped; this is c(m) itself for
+  every m but those on the Nyquist row or column, where -m wraps onto m.
 """
 from __future__ import annotations
 
 import math
 
 import numpy as np
+from scipy.special import erf, erfc, erfcx
 
 from .bspline import ZBasis
 
@@ -52,6 +69,42 @@ def reciprocal(a1, a2):
 def wrap(n, N):
     """Integer frequency n mapped into [-N/2, N/2)."""
     return ((np.asarray(n) + N // 2) % N) - N // 2
+
+
+def core_term(g, dz, Z, Rc, Ac):
+    """In-plane Fourier component of the core term -Z erf(r/R_c)/r of Eq. (10)
+    at in-plane wavevector magnitude g and height dz above the atom, per unit
+    cell area (the convention of Eq. (13)).
+
+    The core term is the potential of the Gaussian core charge
+    rho_c(r) = Z exp(-r^2/R_c^2) / (pi^(3/2) R_c^3); with the 2D transform of
+    1/r (the Coulomb integral of §II.B.1) its component at g is
+        -(2 pi / g) int dz' rho_c(z', g) exp(-g |dz - z'|),
+        rho_c(z', g) = (Z / A_c) exp(-g^2 R_c^2 / 4) exp(-z'^2 / R_c^2) / (sqrt(pi) R_c),
+    which integrates in closed form to
+        -(Z / A_c) (pi / g) [T(dz) + T(-dz)],  T(z) = exp(g z) erfc(g R_c / 2 + z / R_c).
+    Where the erfc argument x is >= 0, T is written exp(-g^2 R_c^2/4 - z^2/R_c^2) erfcx(x)
+    (g z - x^2 = -g^2 R_c^2 / 4 - z^2 / R_c^2), which cannot overflow.
+    g = 0: the divergent constant is dropped (module docstring) and
+        +(2 pi Z / A_c) [dz erf(dz / R_c) + (R_c / sqrt(pi)) exp(-dz^2 / R_c^2)]
+    is kept."""
+    g, dz = np.broadcast_arrays(np.asarray(g, dtype=np.float64), np.asarray(dz, dtype=np.float64))
+    out = np.empty(g.shape)
+    zero = g == 0.0
+    z0 = dz[zero]
+    out[zero] = (2.0 * math.pi * Z / Ac) * (z0 * erf(z0 / Rc) + Rc / math.sqrt(math.pi) * np.exp(-(z0 / Rc) ** 2))
+    gp, zp = g[~zero], dz[~zero]
+
+    def T(z):
+        x = 0.5 * gp * Rc + z / Rc
+        t = np.empty(x.shape)
+        pos = x >= 0.0
+        t[pos] = np.exp(-0.25 * (gp[pos] * Rc) ** 2 - (z[pos] / Rc) ** 2) * erfcx(x[pos])
+        t[~pos] = np.exp(gp[~pos] * z[~pos]) * erfc(x[~pos])
+        return t
+
+    out[~zero] = -(Z / Ac) * (math.pi / gp) * (T(zp) + T(-zp))
+    return out
 
 
 class Model:
@@ -136,6 +189,57 @@ class Model:
                 terms.append((I, F))
         return terms
 
+    def core_table(self):
+        """Core-term components V_core(z_q, m) for every grid frequency m, shape
+        (nq, N1, N2), index u standing for m = wrap(u): the atoms' sum of
+        ``core_term`` times exp(-i g_m . R_par), as coefficients of a real
+        table on the grid.  None when no atom has a core term."""
+        ions = [at for at in self.atoms if getattr(at, "Z", 0.0) != 0.0]
+        if not ions:
+            return None
+        N1, N2 = self.grid
+        m1 = wrap(np.arange(N1), N1)
+        m2 = wrap(np.arange(N2), N2)
+        g = m1[:, None, None] * self.b1[None, None, :] + m2[None, :, None] * self.b2[None, None, :]
+        gn = np.sqrt(np.sum(g * g, axis=-1))
+        tab = np.zeros((len(self.zb.zq), N1, N2), dtype=np.complex128)
+        for at in ions:
+            if not at.Rcore > 0.0:
+                raise ValueError("a core term needs Rcore > 0")
+            phase = np.exp(-1j * (g[..., 0] * at.pos[0] + g[..., 1] * at.pos[1]))
+            prof = core_term(gn[None, :, :], (self.zb.zq - at.pos[2])[:, None, None], at.Z, at.Rcore, self.Ac)
+            tab += prof * phase[None, :, :]
+        neg = tab[:, (-np.arange(N1)) % N1][:, :, (-np.arange(N2)) % N2]
+        return 0.5 * (tab + np.conj(neg))
+
+    def local_table(self):
+        """The local potential V(r_par, z_q), shape (nq, N1, N2), on the grid
+        r_par = (i1/N1) a1 + (i2/N2) a2: the sum over grid frequencies m of
+        the Gaussian components (Eq. (13)) and the core components, each
+        times exp(i g_m . r_par), by numpy's inverse FFT."""
+        N1, N2 = self.grid
+        m1 = wrap(np.arange(N1), N1)
+        m2 = wrap(np.arange(N2), N2)
+        g = m1[:, None, None] * self.b1[None, None, :] + m2[None, :, None] * self.b2[None, None, :]
+        g2 = np.sum(g * g, axis=-1)
+        c = np.zeros((len(self.zb.zq), N1, N2), dtype=np.complex128)
+        for at in self.atoms:
+            if at.A == 0.0:
+                continue
+            a = 1.0 / (2.0 * at.w * at.w)
+            phase = np.exp(-1j * (g[..., 0] * at.pos[0] + g[..., 1] * at.pos[1]))
+            F = (at.A / self.Ac) * (math.pi / a) * np.exp(-g2 / (4.0 * a)) * phase
+            c += np.exp(-a * (self.zb.zq - at.pos[2]) ** 2)[:, None, None] * F[None, :, :]
+        Vc = self.core_table()
+        if Vc is not None:
+            c += Vc
+        return (N1 * N2) * np.fft.ifft2(c, axes=(1, 2)).real
+
+    def _core_index(self):
+        """Flat grid index (u * N2 + v) of the wrapped G - G' of every pair."""
+        d1, d2, _ = self._dG_wrapped()
+        return (d1 % self.grid[0]) * self.grid[1] + (d2 % self.grid[1])
+
     # ---- Kleinman-Bylander projectors (Eqs. (14)-(17), Z.Q factors) ----
     def kb_projectors(self):
         """(E (nproj, nproj), U (nproj, nb, ng)) with V_NL = sum_pq E_pq u_p u_q^H.
@@ -197,6 +301,14 @@ class Model:
             H[np.ix_(ix, ix)] += T
         for I, F in self.local_terms():
             H += np.kron(I, F)
+        Vc = self.core_table()
+        if Vc is not None:
+            # one z matrix per distinct wrapped dG: I_m = sum_q w_q B B V_core(z_q, m)
+            ms, inv = np.unique(self._core_index(), return_inverse=True)
+            Vq = Vc.reshape(Vc.shape[0], -1)[:, ms]
+            Im = np.einsum("q,qi,qm,qj->mij", self.zb.wq, self.zb.B, Vq, self.zb.B)
+            blk = Im[inv.reshape(self.ng, self.ng)]                  # [g, g', i, i']
+            H += blk.transpose(2, 0, 3, 1).reshape(n, n)
         E, U = self.kb_projectors()
         if len(E):
             Uf = U.reshape(len(E), -1).T
@@ -214,6 +326,17 @@ class Model:
         Y += 0.5 * self.q2[None, None, :] * np.einsum("ij,bjg->big", self.S, X)
         for I, F in self.local_terms():
             Y += np.einsum("ij,bjh,gh->big", I, X, F, optimize=True)
+        Vc = self.core_table()
+        if Vc is not None:
+            # per plane: psi_q(G') = sum_i' B_i'(z_q) X(i', G'), then the
+            # in-plane sum over G' with V_core(z_q, G - G'), then sum_q w_q B_i(z_q)
+            idx = self._core_index()
+            psi = np.einsum("qj,bjg->qbg", self.zb.B, X)
+            Vf = Vc.reshape(Vc.shape[0], -1)
+            out = np.empty_like(psi)
+            for q in range(psi.shape[0]):
+                out[q] = psi[q] @ Vf[q][idx].T
+            Y += np.einsum("q,qi,qbg->big", self.zb.wq, self.zb.B, out)
         E, U = self.kb_projectors()
         if len(E):
             Fp = np.einsum("pjg,bjg->pb", np.conj(U), X)      # u_q^H X
@@ -226,12 +349,19 @@ class Model:
         terms = self.local_terms()
         E, U = self.kb_projectors()
         Fp = np.einsum("pjg,bjg->pb", np.conj(U), X) if len(E) else None
+        Vc = self.core_table()
+        if Vc is not None:
+            idx = self._core_index()
+            psi = np.einsum("qj,bjg->qbg", self.zb.B, X)
+            Vf = Vc.reshape(Vc.shape[0], -1)
         out = np.zeros(len(entries), dtype=np.complex128)
         for n, (b, i, g) in enumerate(entries):
             T = 0.5 * self.D[i] + 0.5 * self.q2[g] * self.S[i]
             v = T @ X[b, :, g]
             for I, F in terms:
                 v += I[i] @ X[b] @ F[g]
+            if Vc is not None:
+                v += np.sum(self.zb.wq * self.zb.B[:, i] * np.sum(Vf[:, idx[g]] * psi[:, b, :], axis=1))
             if Fp is not None:
                 v += U[:, i, g] @ (E @ Fp[:, b])
             out[n] = v

@@ -51,6 +51,8 @@ class Atom:
     rc: float = 1.0                      # KB Gaussian radius, bohr
     e2s: float = 0.0                     # E of the second s channel (nproj == 5), Ha
     e12: float = 0.0                     # 1s-2s coupling E_{12} = E_{21} (nproj == 5), Ha
+    Z: float = 0.0                       # core term -Z erf(r/Rcore)/r (0: none)
+    Rcore: float = 0.0                   # its radius, bohr
 
 
 @dataclasses.dataclass
@@ -223,6 +225,12 @@ def scaled(w: Workload, *, ecut: Optional[float] = None, n_int: Optional[int] = 
         kpts=w.kpts if kpts is None else np.asarray(kpts, dtype=np.float64),
         grid=w.grid if grid is None else grid,
         atoms=list(w.atoms))
+
+
+def with_core(w: Workload, Z: float, Rcore: float, name: Optional[str] = None) -> Workload:
+    """A copy of `w` whose atoms also carry the core term -Z erf(r/Rcore)/r."""
+    return dataclasses.replace(w, name=name or (w.name + "-core"),
+                               atoms=[dataclasses.replace(a, Z=float(Z), Rcore=float(Rcore)) for a in w.atoms])
 
 
 def random_block(nbands: int, nb: int, ng: int, seed: int, ld: Optional[int] = None) -> np.ndarray:
