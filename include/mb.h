@@ -54,8 +54,15 @@ typedef enum { MB_FP64 = 0, MB_FP32 = 1, MB_BF16 = 2 } mb_prec;
 typedef struct { double a1[2]; double a2[2]; } mb_cell;
 
 /* One atom of the surface unit cell.
- * Local pseudopotential (§II.B.1, Eq. (10), Gaussian part):
- *     A * exp(-|r - pos|^2 / (2 w^2))            (A in Ha, w in bohr)
+ * Local pseudopotential (§II.B.1, Eq. (10)):
+ *     -Z erf(|r - pos| / Rcore) / |r - pos|  +  A * exp(-|r - pos|^2 / (2 w^2))
+ * (Z in units of e, Rcore and w in bohr, A in Ha; Z = 0 or A = 0 drops the
+ * term).  The core term is the Coulomb potential of a Gaussian core charge;
+ * its in-plane g = 0 component diverges like 2 pi Z / (A_c g) and that
+ * z-independent constant is dropped, keeping
+ *     +(2 pi Z / A_c) [dz erf(dz / Rcore) + (Rcore / sqrt(pi)) exp(-dz^2 / Rcore^2)],
+ * dz = z - pos[2] (a constant shifts every eigenvalue by itself; in a neutral
+ * cell the electrons' Hartree term cancels it).
  * Kleinman-Bylander projectors (Eq. (14)), GTH Gaussian radial parts with
  * alpha = 1 / (2 rc^2) for every channel: nproj = 0 (none), 4 (1s, p_x, p_y,
  * p_z) or 5 (the same and the second s channel, beta ~ r^2 exp(-alpha r^2),
@@ -72,6 +79,8 @@ typedef struct {
     double rc;
     double E2s;
     double E12;
+    double Z;
+    double Rcore;
 } mb_atom;
 
 typedef struct {
@@ -129,6 +138,15 @@ int mb_zplanes(const mb_handle *h, int *nq, double *zq, double *wq);
  * §II.B.1, Eqs. (19)-(20).  Projectors are unchanged.  Waits for all work on
  * the device first (queued applies may still read the old table). */
 int mb_set_local_potential(mb_handle *h, const double *V);
+
+/* The local potential the applies use, in mb_set_local_potential's layout
+ * (host buffer of nq*n1*n2 doubles).  mb_setup builds it on the device from
+ * the atoms' terms: V(r_par, z_q) = Re sum_m c(m, z_q) exp(i g_m . r_par)
+ * over the grid frequencies m in [-n/2, n/2) per axis, c the sum over atoms
+ * of each term's in-plane component times exp(-i g_m . pos_par) -- Eq. (13)
+ * for the Gaussian, the Coulomb integral of §II.B.1 of the Gaussian core
+ * charge for the core term (see mb_atom).  Blocks until the copy is done. */
+int mb_local_potential(mb_handle *h, double *V);
 
 /* Y = H X at k-point ik (§II.B.1: kinetic Eq. (9), local potential through
  * in-plane FFTs on the quadrature planes, Kleinman-Bylander Eq. (17)).

@@ -83,14 +83,23 @@ int mb_zplanes(const mb_handle *h, int *nq, double *zq, double *wq) {
 }
 
 int mb_set_local_potential(mb_handle *h, const double *V) {
-    if (!h || !V) return MB_EINVAL;
+    if (!h || !V || !h->d_vloc) return MB_EINVAL;
     size_t n = (size_t)h->nq * h->n1 * h->n2;
     for (size_t i = 0; i < n; ++i)
         if (!(V[i] == V[i]) || V[i] > 1e300 || V[i] < -1e300) return MB_EINVAL;   // NaN / inf
-    h->Vnat.assign(V, V + n);
     // the old tables may still be read by queued work on any stream
     if (cudaSetDevice(h->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return MB_ECUDA;
-    return upload_potential(h);
+    MB_CUDA(cudaMemcpyAsync(h->d_vloc, V, n * sizeof(double), cudaMemcpyHostToDevice, h->hs));
+    return vloc_derive_tables(h);
+}
+
+int mb_local_potential(mb_handle *h, double *V) {
+    if (!h || !V || !h->d_vloc) return MB_EINVAL;
+    MB_CUDA(cudaSetDevice(h->device));
+    MB_CUDA(cudaMemcpyAsync(V, h->d_vloc, (size_t)h->nq * h->n1 * h->n2 * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->hs));
+    MB_CUDA(cudaStreamSynchronize(h->hs));
+    return MB_OK;
 }
 
 int mb_apply_H(mb_handle *h, int ik, const void *X, void *Y, int nbands, int prec, void *stream) {

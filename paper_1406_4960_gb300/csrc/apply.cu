@@ -595,11 +595,6 @@ int cuda_fail(mb_handle *h, cudaError_t e) {
         prof_end(h, s, kid, ev_);                       \
     } while (0)
 
-#define MB_CUDA(call)                                  \
-    do {                                               \
-        cudaError_t e_ = (call);                       \
-        if (e_ != cudaSuccess) return cuda_fail(h, e_); \
-    } while (0)
 
 cudaMemPool_t mb_pool(int device) {
     static std::mutex mu;
@@ -685,26 +680,9 @@ static int upload_set(mb_handle *h, DevTables &t) {
     return MB_OK;
 }
 
-int upload_potential(mb_handle *h) {
-    std::vector<double> vp, vn;
-    vtable_permuted(h, vp);
-    vtable_natural(h, vn);
-    int rc;
-    if ((rc = upload<double>(h, &h->t64.V, vp))) return rc;
-    if ((rc = upload<float>(h, &h->t32.V, vp))) return rc;
-    if ((rc = upload<double>(h, &h->t64.Vn, vn))) return rc;
-    if ((rc = upload<float>(h, &h->t32.Vn, vn))) return rc;
-    // per-column copy for the FP32 compact-plane kernel: [q][i2][i1]
-    const int N1 = h->n1, N2 = h->n2;
-    std::vector<double> vt(vn.size());
-    for (int q = 0; q < h->nq; ++q)
-        for (int i1 = 0; i1 < N1; ++i1)
-            for (int i2 = 0; i2 < N2; ++i2)
-                vt[((size_t)q * N2 + i2) * N1 + i1] = vn[((size_t)q * N1 + i1) * N2 + i2];
-    if ((rc = upload<float>(h, &h->t32.Vt, vt))) return rc;
-    MB_CUDA(cudaStreamSynchronize(h->hs));
-    return MB_OK;
-}
+// The local potential's tables: built on the device from the atoms' analytic
+// terms (vloc.cu).
+int upload_potential(mb_handle *h) { return vloc_build(h); }
 
 int upload_tables(mb_handle *h) {
     MB_CUDA(cudaSetDevice(h->device));
@@ -836,6 +814,7 @@ void free_tables(mb_handle *h) {
     dev_free(h, (void **)&h->d_zidx);
     dev_free(h, &h->d_tcerr);
     dev_free(h, (void **)&h->d_queue);
+    dev_free(h, (void **)&h->d_vloc);
     dev_free(h, &h->scratch.ptr);
     h->scratch = Scratch();
     if (h->aux) cudaStreamDestroy(h->aux);

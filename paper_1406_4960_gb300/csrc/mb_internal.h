@@ -67,7 +67,13 @@ struct mb_handle {
     std::vector<double> zq, wq;
     std::vector<double> Bq;          // nq x order
     std::vector<double> Sb, Db, Lb;  // band storage as in DevTables
-    std::vector<double> Vnat;        // nq x N1 x N2 natural order, V(r, z_q) (Ha)
+    // local pseudopotential terms (Eq. (10)) grouped by profile: lgrp[3 g ..] =
+    // kind (0 Gaussian, 1 core term), width (a, or R_c), height R_z; the
+    // atoms of group g are lion[3 i ..] = (weight A or Z, x, y) for i in
+    // lstart[g] .. lstart[g+1]
+    std::vector<double> lgrp, lion;
+    std::vector<int> lstart;
+    double *d_vloc = nullptr;        // nq x N1 x N2 natural order, V(r, z_q) (Ha), on the device
     // Kleinman-Bylander projectors as sums of separable terms: projector p
     // (nkb of them) is u_p = sum_{t in terms(p)} zproj[t](j) qproj[t](G); a
     // 1s or p projector has one term, a 2s projector two.  Strengths: the
@@ -139,13 +145,15 @@ namespace mb {
 int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int nk,
                       double ecut, const double *breaks, int nbreaks, int order,
                       const mb_atom *atoms, int natoms, const mb_opts *opts);
-void vtable_permuted(const mb_handle *h, std::vector<double> &out);
-void vtable_natural(const mb_handle *h, std::vector<double> &out);
 void precond_factors(const mb_handle *h, int ik, double shift, std::vector<double> &out);
 
 // apply.cu
 int upload_tables(mb_handle *h);
 int upload_potential(mb_handle *h);
+// vloc.cu
+int vloc_build(mb_handle *h);             // d_vloc from the atoms' analytic terms, then the derived tables
+int vloc_derive_tables(mb_handle *h);     // d_vloc -> t64.V/Vn, t32.V/Vn/Vt
+size_t vloc_build_scratch_bytes(const mb_handle *h);
 int ensure_precond(mb_handle *h);
 void free_tables(mb_handle *h);
 int ensure_scratch(mb_handle *h, size_t bytes, cudaStream_t s);
@@ -185,6 +193,12 @@ void prof_end(mb_handle *h, cudaStream_t s, int kernel, cudaEvent_t a);
 int prof_collect(mb_handle *h);
 
 int cuda_fail(mb_handle *h, cudaError_t e);
+// returns cuda_fail(h, e) from the enclosing function when a CUDA call fails
+#define MB_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_); \
+    } while (0)
 int upload_proj_tables(mb_handle *h);
 cudaError_t smem_limit_once(const void *func, int device, int bytes);
 

@@ -1,8 +1,11 @@
 // Host-side FP64 set-up of the mixed basis: knots, B-spline tables on the
 // Gauss planes, banded S and D with the Cholesky factor of S, cutoff discs,
-// the local potential on the quadrature planes and the Kleinman-Bylander
-// factors.  Runs once per handle; nothing here is on the apply path.
+// the local pseudopotential's terms grouped by profile (the table on the
+// quadrature planes is built from them on the device) and the
+// Kleinman-Bylander factors.  Runs once per handle; nothing here is on the
+// apply path.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <map>
 #include <tuple>
@@ -240,58 +243,31 @@ int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int
     }
     h->total_ldg = h->kofs[nk];
 
-    // ---- local potential on the planes: V(r, z_q) = sum_groups f(z_q) P(r),
-    // P(r) = Re sum_m c(m) exp(i g_m . r) over the grid frequencies
-    // m in [-N/2, N/2), c(m) = sum_atoms (A/A_c)(pi/a) exp(-|g_m|^2/4a) exp(-i g_m.R)
-    const int N1 = h->n1, N2 = h->n2, NN = N1 * N2;
-    h->Vnat.assign((size_t)nq * NN, 0.0);
-    std::map<std::pair<double, double>, std::vector<int>> groups;   // (a, Rz) -> atoms
-    for (int i = 0; i < natoms; ++i) {
-        if (atoms[i].A == 0.0) continue;
-        if (!(atoms[i].w > 0.0)) return MB_EINVAL;
-        double a = 1.0 / (2.0 * atoms[i].w * atoms[i].w);
-        groups[{a, atoms[i].pos[2]}].push_back(i);
-    }
-    std::vector<cdouble> e1((size_t)N1 * N1), e2((size_t)N2 * N2);
-    for (int m = 0; m < N1; ++m)
-        for (int i = 0; i < N1; ++i) e1[(size_t)m * N1 + i] = std::polar(1.0, 2 * kPi * (double)m * i / N1);
-    for (int m = 0; m < N2; ++m)
-        for (int i = 0; i < N2; ++i) e2[(size_t)m * N2 + i] = std::polar(1.0, 2 * kPi * (double)m * i / N2);
-    for (auto &gr : groups) {
-        double a = gr.first.first, Rz = gr.first.second;
-        std::vector<cdouble> c((size_t)NN, 0.0);   // index (m1 mod N1, m2 mod N2)
-        for (int u = 0; u < N1; ++u) {
-            int m1 = u < N1 / 2 ? u : u - N1;
-            for (int v = 0; v < N2; ++v) {
-                int m2 = v < N2 / 2 ? v : v - N2;
-                double gx = m1 * h->b1[0] + m2 * h->b2[0], gy = m1 * h->b1[1] + m2 * h->b2[1];
-                double g2 = gx * gx + gy * gy;
-                cdouble s = 0.0;
-                for (int ia : gr.second)
-                    s += (atoms[ia].A / h->Ac) * (kPi / a) * std::exp(-g2 / (4 * a)) *
-                         std::polar(1.0, -(gx * atoms[ia].pos[0] + gy * atoms[ia].pos[1]));
-                c[(size_t)u * N2 + v] = s;
+    // ---- local pseudopotential (Eq. (10)): the terms, grouped by profile
+    // (kind, width, height); the table V(r, z_q) is built from them on the
+    // device when the handle's tables are uploaded
+    {
+        std::map<std::tuple<int, double, double>, std::vector<std::array<double, 3>>> groups;
+        for (int i = 0; i < natoms; ++i) {
+            const mb_atom &at = atoms[i];
+            if (at.A != 0.0) {
+                if (!(at.w > 0.0)) return MB_EINVAL;
+                groups[{0, 1.0 / (2.0 * at.w * at.w), at.pos[2]}].push_back({at.A, at.pos[0], at.pos[1]});
+            }
+            if (at.Z != 0.0) {
+                if (!(at.Rcore > 0.0) || !std::isfinite(at.Z)) return MB_EINVAL;
+                groups[{1, at.Rcore, at.pos[2]}].push_back({at.Z, at.pos[0], at.pos[1]});
             }
         }
-        // separable inverse DFT: first over m2, then over m1 (phase index m*i mod N)
-        std::vector<cdouble> tmp((size_t)NN, 0.0), Pr((size_t)NN, 0.0);
-        for (int u = 0; u < N1; ++u)
-            for (int i2 = 0; i2 < N2; ++i2) {
-                cdouble s = 0.0;
-                for (int v = 0; v < N2; ++v) s += c[(size_t)u * N2 + v] * e2[(size_t)v * N2 + i2];
-                tmp[(size_t)u * N2 + i2] = s;
-            }
-        for (int i1 = 0; i1 < N1; ++i1)
-            for (int i2 = 0; i2 < N2; ++i2) {
-                cdouble s = 0.0;
-                for (int u = 0; u < N1; ++u) s += tmp[(size_t)u * N2 + i2] * e1[(size_t)u * N1 + i1];
-                Pr[(size_t)i1 * N2 + i2] = s;
-            }
-        for (int q = 0; q < nq; ++q) {
-            double f = std::exp(-a * (h->zq[q] - Rz) * (h->zq[q] - Rz));
-            double *row = &h->Vnat[(size_t)q * NN];
-            for (int e = 0; e < NN; ++e) row[e] += f * Pr[e].real();
+        h->lgrp.clear();
+        h->lion.clear();
+        h->lstart.assign(1, 0);
+        for (auto &gr : groups) {
+            h->lgrp.insert(h->lgrp.end(), {(double)std::get<0>(gr.first), std::get<1>(gr.first), std::get<2>(gr.first)});
+            for (auto &ion : gr.second) h->lion.insert(h->lion.end(), ion.begin(), ion.end());
+            h->lstart.push_back((int)(h->lion.size() / 3));
         }
+        if (groups.empty()) h->lstart.clear();
     }
 
     // ---- Kleinman-Bylander projectors (Eqs. (14)-(17)) as separable terms
@@ -398,34 +374,6 @@ int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int
         h->zstart.push_back((int)h->zlist.size());
     }
     return MB_OK;
-}
-
-// V table in the layout the plane kernel multiplies in: weight and 1/(N1 N2)
-// folded in, both axes bit-reversed (the inverse transform is decimation in
-// frequency, the forward one decimation in time, so no reordering pass runs).
-void vtable_permuted(const mb_handle *h, std::vector<double> &out) {
-    const int N1 = h->n1, N2 = h->n2, NN = N1 * N2;
-    auto rev = [](int x, int bits) {
-        int r = 0;
-        for (int b = 0; b < bits; ++b) r |= ((x >> b) & 1) << (bits - 1 - b);
-        return r;
-    };
-    out.assign((size_t)h->nq * NN, 0.0);
-    double scale = 1.0 / NN;
-    for (int q = 0; q < h->nq; ++q)
-        for (int p1 = 0; p1 < N1; ++p1)
-            for (int p2 = 0; p2 < N2; ++p2)
-                out[(size_t)q * NN + p1 * N2 + p2] =
-                    h->wq[q] * scale * h->Vnat[(size_t)q * NN + rev(p1, h->l1) * N2 + rev(p2, h->l2)];
-}
-
-// The same table in natural layout (register-FFT kernel).
-void vtable_natural(const mb_handle *h, std::vector<double> &out) {
-    const int NN = h->n1 * h->n2;
-    out.assign((size_t)h->nq * NN, 0.0);
-    double scale = 1.0 / NN;
-    for (int q = 0; q < h->nq; ++q)
-        for (int e = 0; e < NN; ++e) out[(size_t)q * NN + e] = h->wq[q] * scale * h->Vnat[(size_t)q * NN + e];
 }
 
 // Banded Cholesky factors of T(G) + c S = D/2 + (|k+G|^2/2 + c) S for every

@@ -25,7 +25,8 @@ EXPORTS = ("mb_setup", "mb_destroy", "mb_sizes", "mb_gvectors", "mb_zplanes",
            "mb_kernel_name", "mb_apply_H_noalloc", "mb_server_create", "mb_server_submit",
            "mb_server_wait", "mb_server_stats", "mb_server_destroy", "mb_autotune",
            "mb_plane_kernel_name", "mb_autotune_report", "mb_plane_kernel_candidates",
-           "mb_plane_kernel_select", "mb_apply_S_batch", "mb_apply_Sinv_batch", "mb_status")
+           "mb_plane_kernel_select", "mb_apply_S_batch", "mb_apply_Sinv_batch", "mb_status",
+           "mb_local_potential")
 
 
 class MBError(RuntimeError):
@@ -41,7 +42,8 @@ class _Cell(ctypes.Structure):
 class _Atom(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_double * 3), ("A", ctypes.c_double), ("w", ctypes.c_double),
                 ("nproj", ctypes.c_int), ("E", ctypes.c_double * 4), ("rc", ctypes.c_double),
-                ("E2s", ctypes.c_double), ("E12", ctypes.c_double)]
+                ("E2s", ctypes.c_double), ("E12", ctypes.c_double), ("Z", ctypes.c_double),
+                ("Rcore", ctypes.c_double)]
 
 
 class _Opts(ctypes.Structure):
@@ -97,6 +99,7 @@ def load(build_if_missing: bool = False):
     lib.mb_gvectors.argtypes = [vp, ctypes.c_int, ip]
     lib.mb_zplanes.argtypes = [vp, ip, dp, dp]
     lib.mb_set_local_potential.argtypes = [vp, dp]
+    lib.mb_local_potential.argtypes = [vp, dp]
     lib.mb_apply_H.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     lib.mb_apply_H_batch.argtypes = [vp, ctypes.c_int, ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.c_int, ctypes.c_int, vp]
@@ -156,6 +159,8 @@ def _atoms_array(atoms):
         arr[i].rc = at.rc
         arr[i].E2s = getattr(at, "e2s", 0.0)
         arr[i].E12 = getattr(at, "e12", 0.0)
+        arr[i].Z = getattr(at, "Z", 0.0)
+        arr[i].Rcore = getattr(at, "Rcore", 0.0)
     return arr
 
 
@@ -290,6 +295,13 @@ class Handle:
         if V.size != len(zq) * self.grid[0] * self.grid[1]:
             raise MBError(1, "local potential must hold nq * n1 * n2 values")
         self._check(self._lib.mb_set_local_potential(self._h, _dptr(V)), "mb_set_local_potential")
+
+    def local_potential(self):
+        """The local potential table V[q][i1][i2] (Ha) the applies use."""
+        zq, _ = self.zplanes()
+        V = np.zeros((len(zq), self.grid[0], self.grid[1]))
+        self._check(self._lib.mb_local_potential(self._h, _dptr(V)), "mb_local_potential")
+        return V
 
     # ---- applies on torch device tensors --------------------------------
     @staticmethod

@@ -22,7 +22,8 @@ class Cell(ctypes.Structure):
 class Atom(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_double * 3), ("A", ctypes.c_double), ("w", ctypes.c_double),
                 ("nproj", ctypes.c_int), ("E", ctypes.c_double * 4), ("rc", ctypes.c_double),
-                ("E2s", ctypes.c_double), ("E12", ctypes.c_double)]
+                ("E2s", ctypes.c_double), ("E12", ctypes.c_double), ("Z", ctypes.c_double),
+                ("Rcore", ctypes.c_double)]
 
 
 class Opts(ctypes.Structure):
