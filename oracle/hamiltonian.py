@@ -111,7 +111,7 @@ class Model:
     """One k-point of the slab problem with all matrix-element ingredients."""
 
     def __init__(self, a1, a2, k, ecut, breaks, order, atoms, grid, nquad=None,
-                 local_components=None):
+                 local_components=None, table=None):
         self.a1 = np.asarray(a1, dtype=np.float64)
         self.a2 = np.asarray(a2, dtype=np.float64)
         self.k = np.asarray(k, dtype=np.float64)
@@ -123,6 +123,10 @@ class Model:
         self.Ac = abs(self.a1[0] * self.a2[1] - self.a1[1] * self.a2[0])
         self.atoms = list(atoms)
         self.local_components = list(local_components or [])
+        # an extra local potential tabulated on the grid, V(r_par, z_q) of shape
+        # (nq, N1, N2) (the general local potential of Eqs. (19)-(20); the SCF
+        # loop puts V_H + V_xc here)
+        self.table = None if table is None else np.asarray(table, dtype=np.float64)
         self._sphere()
         self.S = self.zb.overlap()
         self.D = self.zb.stiffness()
@@ -216,7 +220,8 @@ class Model:
         """The local potential V(r_par, z_q), shape (nq, N1, N2), on the grid
         r_par = (i1/N1) a1 + (i2/N2) a2: the sum over grid frequencies m of
         the Gaussian components (Eq. (13)) and the core components, each
-        times exp(i g_m . r_par), by numpy's inverse FFT."""
+        times exp(i g_m . r_par), by numpy's inverse FFT, plus the extra
+        table when there is one."""
         N1, N2 = self.grid
         m1 = wrap(np.arange(N1), N1)
         m2 = wrap(np.arange(N2), N2)
@@ -233,7 +238,20 @@ class Model:
         Vc = self.core_table()
         if Vc is not None:
             c += Vc
-        return (N1 * N2) * np.fft.ifft2(c, axes=(1, 2)).real
+        V = (N1 * N2) * np.fft.ifft2(c, axes=(1, 2)).real
+        return V if self.table is None else V + self.table
+
+    def nonsep_table(self):
+        """Components on every grid frequency of the local terms that depend
+        on z and g together: the core term and the extra table (its
+        coefficients (1/(N1 N2)) sum_r V(r) exp(-i g_m . r) by numpy's FFT).
+        None when there are neither."""
+        Vc = self.core_table()
+        if self.table is not None:
+            N1, N2 = self.grid
+            T = np.fft.fft2(self.table, axes=(1, 2)) / (N1 * N2)
+            Vc = T if Vc is None else Vc + T
+        return Vc
 
     def _core_index(self):
         """Flat grid index (u * N2 + v) of the wrapped G - G' of every pair."""
@@ -301,7 +319,7 @@ class Model:
             H[np.ix_(ix, ix)] += T
         for I, F in self.local_terms():
             H += np.kron(I, F)
-        Vc = self.core_table()
+        Vc = self.nonsep_table()
         if Vc is not None:
             # one z matrix per distinct wrapped dG: I_m = sum_q w_q B B V_core(z_q, m)
             ms, inv = np.unique(self._core_index(), return_inverse=True)
@@ -326,7 +344,7 @@ class Model:
         Y += 0.5 * self.q2[None, None, :] * np.einsum("ij,bjg->big", self.S, X)
         for I, F in self.local_terms():
             Y += np.einsum("ij,bjh,gh->big", I, X, F, optimize=True)
-        Vc = self.core_table()
+        Vc = self.nonsep_table()
         if Vc is not None:
             # per plane: psi_q(G') = sum_i' B_i'(z_q) X(i', G'), then the
             # in-plane sum over G' with V_core(z_q, G - G'), then sum_q w_q B_i(z_q)
@@ -349,7 +367,7 @@ class Model:
         terms = self.local_terms()
         E, U = self.kb_projectors()
         Fp = np.einsum("pjg,bjg->pb", np.conj(U), X) if len(E) else None
-        Vc = self.core_table()
+        Vc = self.nonsep_table()
         if Vc is not None:
             idx = self._core_index()
             psi = np.einsum("qj,bjg->qbg", self.zb.B, X)
@@ -368,8 +386,8 @@ class Model:
         return out
 
 
-def model_from_workload(w, ik=0, local_components=None, with_atoms=True):
+def model_from_workload(w, ik=0, local_components=None, with_atoms=True, table=None):
     """Oracle model for k-point `ik` of a workload description."""
     return Model(w.a1, w.a2, w.kpts[ik], w.ecut, w.breaks, w.order,
                  w.atoms if with_atoms else [], w.grid, w.nquad,
-                 local_components=local_components)
+                 local_components=local_components, table=table)

@@ -1,0 +1,237 @@
+"""The self-consistent loop of §II.B.1 and §III.A, plain FP64.
+
+Test infrastructure only: tests, the package's smoke check and the
+benchmark's CPU baseline use it; the library never does.
+
+* Electron density on the quadrature planes (Eq. (6) basis):
+      rho(r_par, z_q) = sum_{k,n} f_nk |phi_nk(r_par, z_q)|^2,
+      phi = A_c^(-1/2) sum_{G,j} c_{Gj} exp(i (k+G).r_par) B_j(z);
+  the k phase drops out of |phi|^2, so on the N1 x N2 grid each band is an
+  inverse FFT of sum_j B_j(z_q) c_{Gj} placed at (n1 mod N1, n2 mod N2).
+* Coulomb potential of the electrons by the 2D transform of 1/r (the
+  Coulomb integral of §II.B.1), on the planes' in-plane components
+  rho(z, g) = (1/(N1 N2)) sum_r rho(r, z) exp(-i g.r):
+      V_H(z, g) = int dz' rho(z', g) (2 pi / g) exp(-g |z - z'|)      (g != 0)
+      V_H(z, 0) = -2 pi int dz' rho(z', 0) |z - z'|
+  (at g = 0 the term (2 pi / g) x net charge is dropped, the same reading as
+  for the core term: with the core terms' it cancels in a neutral cell).
+  The z integral is the Gauss rule of the planes.
+* Exchange-correlation: LDA, spin-unpolarized, exchange of the uniform gas
+  and the Ceperley-Alder correlation as parametrized by Perdew and Zunger
+  (Phys. Rev. B 23, 5048 (1981)), the form the paper cites.
+* Mixing (§III.A): the paper's Kerker form
+      rho_new(z, g) = rho_in(z, g) + W g^2 / (g^2 + g_max^2) (rho_out - rho_in)(z, g)
+  on g != 0; the g = 0 profile, which that factor would never update, is
+  mixed linearly with weight W.  Pulay / RMM-DIIS over the last 4 steps: the
+  input densities and residuals R = rho_out - rho_in are combined with
+  coefficients summing to 1 that minimize |sum a_i R_i|, and the Kerker step
+  is taken from that combination.  Inner product of two (z, g) fields:
+  sum_q w_q sum_g Re(conj(a) b).
+* Occupations: Fermi-Dirac of width sigma, two electrons per state, k-point
+  weights w_k; the chemical potential by bisection on the electron count.
+* Convergence (§III.A): the change of V_scf = V_H + V_xc between successive
+  iterations, max over the planes' grid points, below tol.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import eigen as E
+from . import hamiltonian as Hm
+
+# Perdew-Zunger (1981) parametrization of the Ceperley-Alder correlation
+# energy per electron of the unpolarized gas, in Hartree
+PZ_GAMMA, PZ_BETA1, PZ_BETA2 = -0.1423, 1.0529, 0.3334
+PZ_A, PZ_B, PZ_C, PZ_D = 0.0311, -0.048, 0.0020, -0.0116
+RHO_FLOOR = 1e-30   # below this density (or negative) the xc potential is zero
+
+
+def grid_freqs(model):
+    """Cartesian g_m and |g_m| for the grid index (u, v), m = wrap(u, v)."""
+    N1, N2 = model.grid
+    m1 = Hm.wrap(np.arange(N1), N1)
+    m2 = Hm.wrap(np.arange(N2), N2)
+    g = m1[:, None, None] * model.b1[None, None, :] + m2[None, :, None] * model.b2[None, None, :]
+    return g, np.sqrt(np.sum(g * g, axis=-1))
+
+
+def density(models, coefs, occ):
+    """rho(r_par, z_q), shape (nq, N1, N2).
+
+    models: one Model per k-point; coefs[k]: (nbands, nb, ng) coefficients
+    c[n, j, G]; occ[k][n]: occupation f_nk (spin and k weight included)."""
+    m0 = models[0]
+    N1, N2 = m0.grid
+    nq = len(m0.zb.zq)
+    rho = np.zeros((nq, N1, N2))
+    for m, C, f in zip(models, coefs, occ):
+        u = m.gidx[:, 0] % N1
+        v = m.gidx[:, 1] % N2
+        for n in range(C.shape[0]):
+            if f[n] == 0.0:
+                continue
+            psi_q = m.zb.B @ C[n]                       # (nq, ng): sum_j B_j(z_q) c_{Gj}
+            grid = np.zeros((nq, N1, N2), dtype=np.complex128)
+            grid[:, u, v] = psi_q
+            phi = (N1 * N2) * np.fft.ifft2(grid, axes=(1, 2))
+            rho += f[n] * np.abs(phi) ** 2 / m.Ac
+    return rho
+
+
+def to_g(field):
+    """In-plane components (1/(N1 N2)) sum_r f(r) exp(-i g.r) per plane."""
+    return np.fft.fft2(field, axes=(1, 2)) / (field.shape[1] * field.shape[2])
+
+
+def to_r(comp):
+    """The real field with in-plane components `comp` (inverse of to_g)."""
+    return (comp.shape[1] * comp.shape[2]) * np.fft.ifft2(comp, axes=(1, 2)).real
+
+
+def hartree_g(model, rho_g):
+    """V_H(z_q, g) from rho(z_q, g) by the Coulomb integral, z integral by the
+    planes' Gauss rule (module docstring)."""
+    zq, wq = model.zb.zq, model.zb.wq
+    _, gn = grid_freqs(model)
+    dz = np.abs(zq[:, None] - zq[None, :])               # |z_q - z_q'|
+    out = np.zeros_like(rho_g)
+    N1, N2 = model.grid
+    for u in range(N1):
+        for v in range(N2):
+            g = gn[u, v]
+            K = -2.0 * math.pi * dz if g == 0.0 else (2.0 * math.pi / g) * np.exp(-g * dz)
+            out[:, u, v] = K @ (wq * rho_g[:, u, v])
+    return out
+
+
+def xc_pz(rho):
+    """(v_xc, eps_xc) per point of a density array (Hartree): LDA exchange
+    and the Perdew-Zunger correlation; zero where rho <= RHO_FLOOR."""
+    rho = np.asarray(rho, dtype=np.float64)
+    v = np.zeros_like(rho)
+    e = np.zeros_like(rho)
+    ok = rho > RHO_FLOOR
+    n = rho[ok]
+    rs = (3.0 / (4.0 * math.pi * n)) ** (1.0 / 3.0)
+    ex = -0.75 * (3.0 * n / math.pi) ** (1.0 / 3.0)
+    vx = (4.0 / 3.0) * ex
+    ec = np.empty_like(n)
+    vc = np.empty_like(n)
+    hi = rs >= 1.0
+    sr = np.sqrt(rs[hi])
+    den = 1.0 + PZ_BETA1 * sr + PZ_BETA2 * rs[hi]
+    ec[hi] = PZ_GAMMA / den
+    vc[hi] = ec[hi] * (1.0 + (7.0 / 6.0) * PZ_BETA1 * sr + (4.0 / 3.0) * PZ_BETA2 * rs[hi]) / den
+    lo = ~hi
+    r = rs[lo]
+    lr = np.log(r)
+    ec[lo] = PZ_A * lr + PZ_B + PZ_C * r * lr + PZ_D * r
+    vc[lo] = PZ_A * lr + (PZ_B - PZ_A / 3.0) + (2.0 / 3.0) * PZ_C * r * lr + (2.0 * PZ_D - PZ_C) * r / 3.0
+    v[ok] = vx + vc
+    e[ok] = ex + ec
+    return v, e
+
+
+def occupations(evals, kweights, nelec, sigma):
+    """Fermi-Dirac occupations f_nk = 2 w_k / (1 + exp((eps - mu)/sigma)) with
+    sum f = nelec; mu by bisection.  Returns (f, mu)."""
+    ev = np.asarray(evals, dtype=np.float64)
+    wk = np.asarray(kweights, dtype=np.float64)[:, None]
+
+    def count(mu):
+        x = np.clip((ev - mu) / sigma, -700.0, 700.0)
+        return float(np.sum(2.0 * wk / (1.0 + np.exp(x))))
+
+    lo, hi = ev.min() - 40.0 * sigma, ev.max() + 40.0 * sigma
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if count(mid) < nelec:
+            lo = mid
+        else:
+            hi = mid
+    mu = 0.5 * (lo + hi)
+    x = np.clip((ev - mu) / sigma, -700.0, 700.0)
+    return 2.0 * wk / (1.0 + np.exp(x)), mu
+
+
+def core_density(model):
+    """The atoms' Gaussian core charges rho_c on the grid (the start density):
+    components (Z/A_c) exp(-g^2 R_c^2/4) exp(-dz^2/R_c^2) / (sqrt(pi) R_c) exp(-i g.R_par)."""
+    g, gn = grid_freqs(model)
+    c = np.zeros((len(model.zb.zq),) + gn.shape, dtype=np.complex128)
+    for at in model.atoms:
+        if getattr(at, "Z", 0.0) == 0.0:
+            continue
+        Rc = at.Rcore
+        dz = model.zb.zq - at.pos[2]
+        prof = np.exp(-(dz / Rc) ** 2) / (math.sqrt(math.pi) * Rc)
+        phase = np.exp(-1j * (g[..., 0] * at.pos[0] + g[..., 1] * at.pos[1]))
+        c += (at.Z / model.Ac) * prof[:, None, None] * (np.exp(-0.25 * (gn * Rc) ** 2) * phase)[None]
+    return to_r(c)
+
+
+class Mixer:
+    """Kerker + Pulay (RMM-DIIS) over the last `depth` steps (§III.A)."""
+
+    def __init__(self, model, W, gmax, depth=4):
+        self.w = model.zb.wq
+        _, gn = grid_freqs(model)
+        g2 = gn * gn
+        self.K = np.where(g2 > 0.0, W * g2 / (g2 + gmax * gmax), W)
+        self.depth = depth
+        self.hist = []            # (rho_in_g, R_g)
+
+    def dot(self, a, b):
+        return float(np.sum(self.w[:, None, None] * np.real(np.conj(a) * b)))
+
+    def step(self, rho_in, rho_out):
+        """New input density (real space) from this step's input and output."""
+        ri, ro = to_g(rho_in), to_g(rho_out)
+        self.hist.append((ri, ro - ri))
+        self.hist = self.hist[-self.depth:]
+        m = len(self.hist)
+        A = np.zeros((m + 1, m + 1))
+        for i in range(m):
+            for j in range(m):
+                A[i, j] = self.dot(self.hist[i][1], self.hist[j][1])
+        A[:m, m] = A[m, :m] = 1.0
+        rhs = np.zeros(m + 1)
+        rhs[m] = 1.0
+        a = np.linalg.lstsq(A, rhs, rcond=None)[0][:m]
+        rho_opt = sum(a[i] * self.hist[i][0] for i in range(m))
+        R_opt = sum(a[i] * self.hist[i][1] for i in range(m))
+        return to_r(rho_opt + self.K[None, :, :] * R_opt)
+
+
+def scf(w, nbands, nelec, sigma=0.01, W=0.5, gmax=1.0, tol=1e-7, max_iter=60, kweights=None):
+    """Plain SCF on a workload: dense generalized eigensolves per k-point.
+    Returns dict(evals (nk, nbands), rho, vscf, iterations, dv)."""
+    nk = w.nk
+    kw = np.full(nk, 1.0 / nk) if kweights is None else np.asarray(kweights, dtype=np.float64)
+    base = [Hm.model_from_workload(w, ik) for ik in range(nk)]
+    rho_in = core_density(base[0])
+    mixer = Mixer(base[0], W, gmax)
+    vprev = None
+    dv = math.inf
+    it = 0
+    for it in range(1, max_iter + 1):
+        vh = to_r(hartree_g(base[0], to_g(rho_in)))
+        vxc, _ = xc_pz(rho_in)
+        vscf = vh + vxc
+        dv = math.inf if vprev is None else float(np.abs(vscf - vprev).max())
+        vprev = vscf
+        models = [Hm.model_from_workload(w, ik, table=vscf) for ik in range(nk)]
+        evals, coefs = [], []
+        for m in models:
+            ev, C = E.generalized_lowest(m.dense_H(), m.dense_S(), nbands, vectors=True)
+            evals.append(ev)
+            coefs.append(C.T.reshape(nbands, m.nb, m.ng))
+        evals = np.array(evals)
+        if dv < tol:
+            break
+        f, _ = occupations(evals, kw, nelec, sigma)
+        rho_out = density(models, coefs, f)
+        rho_in = mixer.step(rho_in, rho_out)
+    return {"evals": evals, "rho": rho_in, "vscf": vscf, "iterations": it, "dv": dv}
