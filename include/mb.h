@@ -252,6 +252,72 @@ int mb_eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals,
                 void *evecs, const mb_solve_opts *sopts, mb_solve_info *info,
                 void *stream);
 
+/* ---- the self-consistent loop (§II.B.1 and §III.A) ---------------------
+ * Fields on the quadrature planes are device arrays of nq*n1*n2 doubles in
+ * mb_set_local_potential's layout, f[q][i1][i2] at r_par = i1/n1 a1 + i2/n2 a2.
+ *
+ * Electron density rho = sum_{k,n} f_nk |phi_nk|^2 of the coefficient blocks
+ * evecs (device, the layout of mb_eigsolve's evecs: nk blocks of nbands
+ * vectors [band][j][ldg]) with occupations occ (host, nk*nbands, spin and
+ * k-point weight included); phi is the basis expansion of Eq. (6) with
+ * A = A_c.  FP64; deterministic (partials summed in a fixed order).  The
+ * caller's stream is synchronized before return (occ is read from the host). */
+int mb_density(mb_handle *h, const void *evecs, int nbands, const double *occ, double *rho, void *stream);
+
+/* Coulomb potential of an electron density, V_H(r) = int rho(r')/|r - r'|,
+ * through the 2D transform of 1/r (the Coulomb integral of §II.B.1): per
+ * in-plane component g, V(z, g) = int dz' rho(z', g) (2 pi/g) exp(-g|z - z'|),
+ * the z integral by the planes' Gauss rule; at g = 0 the z-independent
+ * divergence (2 pi/g) x net charge is dropped, keeping
+ * -2 pi int dz' rho(z', 0) |z - z'| (with the atoms' core terms, which drop
+ * theirs, a neutral cell loses nothing).  rho and vh: device fields.  The
+ * stream is synchronized before return. */
+int mb_hartree(mb_handle *h, const double *rho, double *vh, void *stream);
+
+/* LDA exchange-correlation potential v_xc and energy per electron exc
+ * (optional, may be NULL) of a density: exchange of the uniform gas and the
+ * Ceperley-Alder correlation as parametrized by Perdew and Zunger (Phys. Rev.
+ * B 23, 5048 (1981)), spin-unpolarized; zero where rho <= 1e-30.  Device
+ * fields; asynchronous on the stream. */
+int mb_xc_lda(mb_handle *h, const double *rho, double *vxc, double *exc, void *stream);
+
+typedef struct {
+    int nbands;           /* roots per k-point (room above nelec/2 for the smearing) */
+    double nelec;         /* electrons per cell (<= 0: the atoms' sum of Z, a neutral cell) */
+    double sigma;         /* Fermi-Dirac width (Ha), > 0 */
+    double mix_weight;    /* W of the Kerker mixing (0: 0.5) */
+    double g_max;         /* Kerker cutoff wave vector (1/bohr) (0: 1) */
+    int pulay_depth;      /* steps Pulay combines, at most 8 (0: 4; 1: Kerker alone) */
+    double tol;           /* stop when max |change of V_H + V_xc| < tol (Ha) */
+    int max_iter;         /* eigensolves at most (0: 60) */
+    double eig_tol;       /* residual tolerance of each eigensolve (0: tol / 10) */
+    int prec;             /* MB_FP64 or MB_FP32 (mixed-precision eigensolves) */
+    const double *kweights; /* host, nk weights summing to 1 (NULL: uniform) */
+} mb_scf_opts;
+
+typedef struct {
+    int iterations;       /* eigensolves run */
+    double dv;            /* last max |change of V_H + V_xc| (Ha) */
+    double mu;            /* Fermi level of the last occupations (Ha) */
+    double nelec;         /* electrons in the final input density */
+    int eig_cycles;       /* grand cycles over all eigensolves */
+    double seconds, seconds_eig, seconds_density, seconds_potential;
+} mb_scf_info;
+
+/* Self-consistent field (§II.B.1, §III.A).  Starting from the atoms' Gaussian
+ * core charges as the electron density, each iteration adds V_scf = V_H + V_xc
+ * of the input density to the atoms' local potential, solves for the lowest
+ * nbands roots (mb_eigsolve), fills them with Fermi-Dirac occupations and
+ * mixes the output density into the next input: the paper's Kerker form
+ * W g^2/(g^2 + g_max^2) on g != 0 (the g = 0 profile, which that factor
+ * would freeze, mixed linearly by W) from the Pulay combination of the last
+ * pulay_depth steps that minimizes the residual.  Stops when V_scf changes by
+ * less than tol (§III.A's criterion).  evals: host nk*nbands, the roots of
+ * the final potential; rho_out: optional device field, the final input
+ * density.  The handle's local potential holds the final total potential on
+ * return.  MB_ENOTCONV when max_iter is reached (evals still written). */
+int mb_scf(mb_handle *h, const mb_scf_opts *opts, double *evals, double *rho_out, mb_scf_info *info);
+
 /* ---- launch-shape autotuner -------------------------------------------
  * Times the plane kernel's candidate launch shapes for an apply of `nbands`
  * bands at all k-points of the handle, on scratch blocks it allocates, and

@@ -154,6 +154,7 @@ int upload_potential(mb_handle *h);
 int vloc_build(mb_handle *h);             // d_vloc from the atoms' analytic terms, then the derived tables
 int vloc_derive_tables(mb_handle *h);     // d_vloc -> t64.V/Vn, t32.V/Vn/Vt
 size_t vloc_build_scratch_bytes(const mb_handle *h);
+int vloc_tabulate(mb_handle *h, int mode, double *out, cudaStream_t s);   // 0: V(r, z_q); 1: core charge density
 int ensure_precond(mb_handle *h);
 void free_tables(mb_handle *h);
 int ensure_scratch(mb_handle *h, size_t bytes, cudaStream_t s);

@@ -49,8 +49,16 @@ __device__ __forceinline__ void grid_g(const VlocGeom &G, int u, int v, double &
 }
 
 // z profile of one group at |g| and height dz above the group's atoms, per
-// unit weight (A of a Gaussian, Z of a core term) and per unit cell area
-__device__ double profile(int kind, double p, double g, double dz, double Ac) {
+// unit weight (A of a Gaussian, Z of a core term) and per unit cell area.
+// mode 0: the potential; mode 1: the core charge density
+// rho_c = Z exp(-r^2/R_c^2) / (pi^(3/2) R_c^3), whose components are
+// exp(-g^2 R_c^2/4) exp(-dz^2/R_c^2) / (sqrt(pi) R_c A_c) (Gaussians: none).
+__device__ double profile(int mode, int kind, double p, double g, double dz, double Ac) {
+    if (mode == 1) {
+        if (kind != 1) return 0.0;
+        const double u = dz / p;
+        return kInvSqrtPi / (p * Ac) * exp(-0.25 * (g * p) * (g * p) - u * u);
+    }
     if (kind == 0) {   // Gaussian, p = a
         return (kPiD / p) / Ac * exp(-g * g / (4.0 * p)) * exp(-p * dz * dz);
     }
@@ -88,7 +96,7 @@ __global__ void vloc_sfac_kernel(VlocGeom G, const double *ion, const int *start
 
 // One (row u, plane q): c(m, z_q) for the N2 frequencies of the row, then
 // tmp[q][u][i2] = sum_v c(u, v) exp(2 pi i v i2 / N2).  blockDim.x = N2.
-__global__ void vloc_rows_kernel(VlocGeom G, const double *grp, const double2 *S, const double *zq, int q0,
+__global__ void vloc_rows_kernel(VlocGeom G, int mode, const double *grp, const double2 *S, const double *zq, int q0,
                                  double2 *tmp) {
     extern __shared__ double2 rs[];
     double2 *c = rs, *tw = rs + G.N2;
@@ -103,7 +111,7 @@ __global__ void vloc_rows_kernel(VlocGeom G, const double *grp, const double2 *S
     const double g = sqrt(gx * gx + gy * gy), z = zq[q];
     double re = 0.0, im = 0.0;
     for (int k = 0; k < G.ngrp; ++k) {
-        const double f = profile((int)grp[3 * k], grp[3 * k + 1], g, z - grp[3 * k + 2], G.Ac);
+        const double f = profile(mode, (int)grp[3 * k], grp[3 * k + 1], g, z - grp[3 * k + 2], G.Ac);
         const double2 s = S[(size_t)k * NN + u * G.N2 + v];
         re += f * s.x;
         im += f * s.y;
@@ -202,48 +210,59 @@ int vloc_derive_tables(mb_handle *h) {
     return MB_OK;
 }
 
-// V(r, z_q) from the atoms' analytic terms into d_vloc, then the derived tables.
-int vloc_build(mb_handle *h) {
+// The real table of the atoms' analytic terms on the planes into out (nq x
+// N1 x N2, device), on stream s: mode 0 the local potential V(r, z_q),
+// mode 1 the Gaussian core charge density.
+int vloc_tabulate(mb_handle *h, int mode, double *out, cudaStream_t s) {
     const int N1 = h->n1, N2 = h->n2, NN = N1 * N2, nq = h->nq;
     const int ngrp = h->lstart.empty() ? 0 : (int)h->lstart.size() - 1;
-    int rc;
-    if ((rc = pool_alloc(h, (void **)&h->d_vloc, (size_t)nq * NN * sizeof(double)))) return rc;
     if (ngrp == 0) {
-        MB_CUDA(cudaMemsetAsync(h->d_vloc, 0, (size_t)nq * NN * sizeof(double), h->hs));
-        return vloc_derive_tables(h);
+        MB_CUDA(cudaMemsetAsync(out, 0, (size_t)nq * NN * sizeof(double), s));
+        return MB_OK;
     }
     VlocGeom G{N1, N2, nq, ngrp, h->b1[0], h->b1[1], h->b2[0], h->b2[1], h->Ac};
-    double *ion = nullptr, *grp = nullptr, *zq = nullptr;
-    int *start = nullptr;
-    double2 *S = nullptr, *tmp = nullptr;
     const size_t per_plane = (size_t)NN * sizeof(double2);
     const int qc = (int)std::max<size_t>(1, std::min<size_t>(nq, kVlocChunkBytes / per_plane));
-    auto release = [&] {
-        dev_free(h, (void **)&ion);
-        dev_free(h, (void **)&grp);
-        dev_free(h, (void **)&zq);
-        dev_free(h, (void **)&start);
-        dev_free(h, (void **)&S);
-        dev_free(h, (void **)&tmp);
-    };
-    if ((rc = dev_upload(h, (void **)&ion, h->lion.data(), h->lion.size() * sizeof(double))) ||
-        (rc = dev_upload(h, (void **)&grp, h->lgrp.data(), h->lgrp.size() * sizeof(double))) ||
-        (rc = dev_upload(h, (void **)&zq, h->zq.data(), h->zq.size() * sizeof(double))) ||
-        (rc = dev_upload(h, (void **)&start, h->lstart.data(), h->lstart.size() * sizeof(int))) ||
-        (rc = dev_upload(h, (void **)&S, nullptr, (size_t)ngrp * per_plane)) ||
-        (rc = dev_upload(h, (void **)&tmp, nullptr, (size_t)qc * per_plane))) {
-        release();
-        return rc;
+    cudaMemPool_t pool = mb_pool(h->device);
+    if (!pool) return MB_ECUDA;
+    // one pool block: ions | groups | planes | group starts (int) | S | tmp
+    const size_t nion = h->lion.size(), ngv = h->lgrp.size();
+    const size_t off_grp = nion * sizeof(double), off_zq = off_grp + ngv * sizeof(double);
+    const size_t off_start = off_zq + (size_t)nq * sizeof(double);
+    const size_t off_S = (off_start + h->lstart.size() * sizeof(int) + 255) / 256 * 256;
+    const size_t off_tmp = off_S + (size_t)ngrp * per_plane, bytes = off_tmp + (size_t)qc * per_plane;
+    unsigned char *blk = nullptr;
+    MB_CUDA(cudaMallocFromPoolAsync((void **)&blk, bytes, pool, s));
+    double *ion = reinterpret_cast<double *>(blk), *grp = reinterpret_cast<double *>(blk + off_grp);
+    double *zq = reinterpret_cast<double *>(blk + off_zq);
+    int *start = reinterpret_cast<int *>(blk + off_start);
+    double2 *S = reinterpret_cast<double2 *>(blk + off_S), *tmp = reinterpret_cast<double2 *>(blk + off_tmp);
+    cudaError_t e = cudaMemcpyAsync(ion, h->lion.data(), nion * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grp, h->lgrp.data(), ngv * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(zq, h->zq.data(), nq * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(start, h->lstart.data(), h->lstart.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        vloc_sfac_kernel<<<dim3((NN + 255) / 256, ngrp), 256, 0, s>>>(G, ion, start, S);
+        for (int q0 = 0; q0 < nq; q0 += qc) {
+            const int n = std::min(qc, nq - q0);
+            vloc_rows_kernel<<<dim3(N1, n), N2, 2 * N2 * sizeof(double2), s>>>(G, mode, grp, S, zq, q0, tmp);
+            vloc_cols_kernel<<<dim3(N2, n), N1, 2 * N1 * sizeof(double2), s>>>(G, tmp, q0, out);
+        }
+        e = cudaGetLastError();
     }
-    vloc_sfac_kernel<<<dim3((NN + 255) / 256, ngrp), 256, 0, h->hs>>>(G, ion, start, S);
-    for (int q0 = 0; q0 < nq; q0 += qc) {
-        const int n = std::min(qc, nq - q0);
-        vloc_rows_kernel<<<dim3(N1, n), N2, 2 * N2 * sizeof(double2), h->hs>>>(G, grp, S, zq, q0, tmp);
-        vloc_cols_kernel<<<dim3(N2, n), N1, 2 * N1 * sizeof(double2), h->hs>>>(G, tmp, q0, h->d_vloc);
-    }
-    cudaError_t e = cudaGetLastError();
-    release();
+    cudaFreeAsync(blk, s);
     if (e != cudaSuccess) return cuda_fail(h, e);
+    // the host vectors copied above must stay untouched until the copies ran
+    MB_CUDA(cudaStreamSynchronize(s));
+    return MB_OK;
+}
+
+// V(r, z_q) from the atoms' analytic terms into d_vloc, then the derived tables.
+int vloc_build(mb_handle *h) {
+    int rc;
+    if ((rc = pool_alloc(h, (void **)&h->d_vloc, (size_t)h->nq * h->n1 * h->n2 * sizeof(double)))) return rc;
+    if ((rc = vloc_tabulate(h, 0, h->d_vloc, h->hs))) return rc;
     return vloc_derive_tables(h);
 }
 

@@ -26,7 +26,7 @@ EXPORTS = ("mb_setup", "mb_destroy", "mb_sizes", "mb_gvectors", "mb_zplanes",
            "mb_server_wait", "mb_server_stats", "mb_server_destroy", "mb_autotune",
            "mb_plane_kernel_name", "mb_autotune_report", "mb_plane_kernel_candidates",
            "mb_plane_kernel_select", "mb_apply_S_batch", "mb_apply_Sinv_batch", "mb_status",
-           "mb_local_potential")
+           "mb_local_potential", "mb_density", "mb_hartree", "mb_xc_lda", "mb_scf")
 
 
 class MBError(RuntimeError):
@@ -66,6 +66,20 @@ class _Request(ctypes.Structure):
                 ("tol", ctypes.c_double), ("prec", ctypes.c_int)]
 
 
+class ScfOpts(ctypes.Structure):
+    _fields_ = [("nbands", ctypes.c_int), ("nelec", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("mix_weight", ctypes.c_double), ("g_max", ctypes.c_double), ("pulay_depth", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("eig_tol", ctypes.c_double),
+                ("prec", ctypes.c_int), ("kweights", ctypes.POINTER(ctypes.c_double))]
+
+
+class ScfInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("dv", ctypes.c_double), ("mu", ctypes.c_double),
+                ("nelec", ctypes.c_double), ("eig_cycles", ctypes.c_int), ("seconds", ctypes.c_double),
+                ("seconds_eig", ctypes.c_double), ("seconds_density", ctypes.c_double),
+                ("seconds_potential", ctypes.c_double)]
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("krylov_depth", ctypes.c_int), ("block", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("polish", ctypes.c_int), ("guard", ctypes.c_int)]
@@ -100,6 +114,10 @@ def load(build_if_missing: bool = False):
     lib.mb_zplanes.argtypes = [vp, ip, dp, dp]
     lib.mb_set_local_potential.argtypes = [vp, dp]
     lib.mb_local_potential.argtypes = [vp, dp]
+    lib.mb_density.argtypes = [vp, vp, ctypes.c_int, dp, vp, vp]
+    lib.mb_hartree.argtypes = [vp, vp, vp, vp]
+    lib.mb_xc_lda.argtypes = [vp, vp, vp, vp, vp]
+    lib.mb_scf.argtypes = [vp, ctypes.POINTER(ScfOpts), dp, vp, ctypes.POINTER(ScfInfo)]
     lib.mb_apply_H.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     lib.mb_apply_H_batch.argtypes = [vp, ctypes.c_int, ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.c_int, ctypes.c_int, vp]
@@ -295,6 +313,58 @@ class Handle:
         if V.size != len(zq) * self.grid[0] * self.grid[1]:
             raise MBError(1, "local potential must hold nq * n1 * n2 values")
         self._check(self._lib.mb_set_local_potential(self._h, _dptr(V)), "mb_set_local_potential")
+
+    # ---- the self-consistent loop (fields: CUDA float64 tensors nq x n1 x n2)
+    def _field_ok(self, t, name):
+        zq, _ = self.zplanes()
+        n = len(zq) * self.grid[0] * self.grid[1]
+        if t.dtype.itemsize != 8 or t.is_complex() or t.numel() != n or not t.is_cuda or not t.is_contiguous():
+            raise MBError(1, "%s must be a contiguous CUDA float64 tensor of %d elements" % (name, n))
+
+    def density(self, evecs, nbands, occ, rho, stream=None):
+        """rho <- sum_{k,n} f_nk |phi_nk|^2 of the eigenvector blocks evecs."""
+        need = sum(nbands * self.sizes(ik)[1] * self.sizes(ik)[2] for ik in range(self.nk))
+        if evecs.dtype.itemsize != 16 or evecs.numel() < need or not evecs.is_cuda or not evecs.is_contiguous():
+            raise MBError(1, "evecs must be a contiguous CUDA complex128 buffer of %d elements" % need)
+        self._field_ok(rho, "rho")
+        occ = np.ascontiguousarray(np.asarray(occ, dtype=np.float64).reshape(self.nk * nbands))
+        self._check(self._lib.mb_density(self._h, ctypes.c_void_p(evecs.data_ptr()), nbands, _dptr(occ),
+                                         ctypes.c_void_p(rho.data_ptr()), _stream_ptr(stream)), "mb_density")
+
+    def hartree(self, rho, vh, stream=None):
+        self._field_ok(rho, "rho")
+        self._field_ok(vh, "vh")
+        self._check(self._lib.mb_hartree(self._h, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(vh.data_ptr()),
+                                         _stream_ptr(stream)), "mb_hartree")
+
+    def xc_lda(self, rho, vxc, exc=None, stream=None):
+        self._field_ok(rho, "rho")
+        self._field_ok(vxc, "vxc")
+        if exc is not None:
+            self._field_ok(exc, "exc")
+        self._check(self._lib.mb_xc_lda(self._h, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(vxc.data_ptr()),
+                                        ctypes.c_void_p(exc.data_ptr()) if exc is not None else None,
+                                        _stream_ptr(stream)), "mb_xc_lda")
+
+    def scf(self, nbands, tol, sigma, nelec=0.0, mix_weight=0.0, g_max=0.0, pulay_depth=0, max_iter=0,
+            eig_tol=0.0, prec="fp64", kweights=None, rho_out=None, allow_notconv=False):
+        """Self-consistent loop; returns (evals (nk, nbands), ScfInfo)."""
+        kw = None
+        if kweights is not None:
+            kw = np.ascontiguousarray(np.asarray(kweights, dtype=np.float64).reshape(self.nk))
+        o = ScfOpts(int(nbands), float(nelec), float(sigma), float(mix_weight), float(g_max), int(pulay_depth),
+                    float(tol), int(max_iter), float(eig_tol), self._prec(prec),
+                    kw.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if kw is not None else None)
+        if rho_out is not None:
+            self._field_ok(rho_out, "rho_out")
+        ev = np.zeros(self.nk * nbands)
+        info = ScfInfo()
+        rc = self._lib.mb_scf(self._h, ctypes.byref(o), _dptr(ev),
+                              ctypes.c_void_p(rho_out.data_ptr()) if rho_out is not None else None,
+                              ctypes.byref(info))
+        if rc and not (rc == 3 and allow_notconv):
+            self._check(rc, "mb_scf")
+        return ev.reshape(self.nk, nbands), info
 
     def local_potential(self):
         """The local potential table V[q][i1][i2] (Ha) the applies use."""
