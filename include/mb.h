@@ -277,8 +277,10 @@ int mb_hartree(mb_handle *h, const double *rho, double *vh, void *stream);
 /* LDA exchange-correlation potential v_xc and energy per electron exc
  * (optional, may be NULL) of a density: exchange of the uniform gas and the
  * Ceperley-Alder correlation as parametrized by Perdew and Zunger (Phys. Rev.
- * B 23, 5048 (1981)), spin-unpolarized; zero where rho <= 1e-30.  Device
- * fields; asynchronous on the stream. */
+ * B 23, 5048 (1981)), spin-unpolarized, evaluated at max(rho, 1e-10 bohr^-3)
+ * (in the vacuum the density falls below what FP64 sums and converged
+ * eigenvectors resolve; there the potential is the small constant of the
+ * floor).  Device fields; asynchronous on the stream. */
 int mb_xc_lda(mb_handle *h, const double *rho, double *vxc, double *exc, void *stream);
 
 typedef struct {
@@ -310,8 +312,9 @@ typedef struct {
  * nbands roots (mb_eigsolve), fills them with Fermi-Dirac occupations and
  * mixes the output density into the next input: the paper's Kerker form
  * W g^2/(g^2 + g_max^2) on g != 0 (the g = 0 profile, which that factor
- * would freeze, mixed linearly by W) from the Pulay combination of the last
- * pulay_depth steps that minimizes the residual.  Stops when V_scf changes by
+ * would freeze, scaled by the factor of the grid's first nonzero shell: the
+ * mixing stays local in z and keeps the electron count) from the Pulay
+ * combination of the last pulay_depth steps that minimizes the residual.  Stops when V_scf changes by
  * less than tol (§III.A's criterion).  evals: host nk*nbands, the roots of
  * the final potential; rho_out: optional device field, the final input
  * density.  The handle's local potential holds the final total potential on

@@ -41,6 +41,10 @@ int mb_debug_combine_ff(const void *A, const double *Y, long long n, int ma, int
  * CUDA call fails.  Outputs may be NULL. */
 int mb_probe_fp32_fma(int device, int reps, double *tflops, double *ms);
 
+/* The same probe with FP64 FMA chains (fewer iterations: GB300's FP64 rate
+ * is a small fraction of its FP32 rate). */
+int mb_probe_fp64_fma(int device, int reps, double *tflops, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,11 +18,20 @@ benchmark's CPU baseline use it; the library never does.
   The z integral is the Gauss rule of the planes.
 * Exchange-correlation: LDA, spin-unpolarized, exchange of the uniform gas
   and the Ceperley-Alder correlation as parametrized by Perdew and Zunger
-  (Phys. Rev. B 23, 5048 (1981)), the form the paper cites.
+  (Phys. Rev. B 23, 5048 (1981)), the form the paper cites, evaluated at
+  max(rho, RHO_FLOOR): in the vacuum the density falls to values (1e-16 and
+  below) that neither FP64 sums nor converged eigenvectors resolve, and the
+  cube root of that noise would dominate any change of V_xc; below the floor
+  the potential is the small constant v_xc(RHO_FLOOR) (continuous in rho).
 * Mixing (§III.A): the paper's Kerker form
       rho_new(z, g) = rho_in(z, g) + W g^2 / (g^2 + g_max^2) (rho_out - rho_in)(z, g)
-  on g != 0; the g = 0 profile, which that factor would never update, is
-  mixed linearly with weight W.  Pulay / RMM-DIIS over the last 4 steps: the
+  on g != 0.  The printed factor is 0 at g = 0, which would freeze the
+  planar-average profile rho(z, 0); that profile is mixed with the factor's
+  value on the grid's first nonzero shell, W g_1^2 / (g_1^2 + g_max^2), g_1
+  the shortest nonzero grid vector.  The mixing stays local in z (each
+  component's profile is scaled), so the electron count is kept exactly and
+  nothing is smeared into the vacuum, where the LDA potential is most
+  sensitive to small densities.  Pulay / RMM-DIIS over the last 4 steps: the
   input densities and residuals R = rho_out - rho_in are combined with
   coefficients summing to 1 that minimize |sum a_i R_i|, and the Kerker step
   is taken from that combination.  Inner product of two (z, g) fields:
@@ -45,7 +54,7 @@ from . import hamiltonian as Hm
 # energy per electron of the unpolarized gas, in Hartree
 PZ_GAMMA, PZ_BETA1, PZ_BETA2 = -0.1423, 1.0529, 0.3334
 PZ_A, PZ_B, PZ_C, PZ_D = 0.0311, -0.048, 0.0020, -0.0116
-RHO_FLOOR = 1e-30   # below this density (or negative) the xc potential is zero
+RHO_FLOOR = 1e-10   # bohr^-3: the LDA is evaluated at max(rho, RHO_FLOOR)
 
 
 def grid_freqs(model):
@@ -108,12 +117,8 @@ def hartree_g(model, rho_g):
 
 def xc_pz(rho):
     """(v_xc, eps_xc) per point of a density array (Hartree): LDA exchange
-    and the Perdew-Zunger correlation; zero where rho <= RHO_FLOOR."""
-    rho = np.asarray(rho, dtype=np.float64)
-    v = np.zeros_like(rho)
-    e = np.zeros_like(rho)
-    ok = rho > RHO_FLOOR
-    n = rho[ok]
+    and the Perdew-Zunger correlation of max(rho, RHO_FLOOR)."""
+    n = np.maximum(np.asarray(rho, dtype=np.float64), RHO_FLOOR)
     rs = (3.0 / (4.0 * math.pi * n)) ** (1.0 / 3.0)
     ex = -0.75 * (3.0 * n / math.pi) ** (1.0 / 3.0)
     vx = (4.0 / 3.0) * ex
@@ -129,8 +134,8 @@ def xc_pz(rho):
     lr = np.log(r)
     ec[lo] = PZ_A * lr + PZ_B + PZ_C * r * lr + PZ_D * r
     vc[lo] = PZ_A * lr + (PZ_B - PZ_A / 3.0) + (2.0 / 3.0) * PZ_C * r * lr + (2.0 * PZ_D - PZ_C) * r / 3.0
-    v[ok] = vx + vc
-    e[ok] = ex + ec
+    v = vx + vc
+    e = ex + ec
     return v, e
 
 
@@ -179,9 +184,14 @@ class Mixer:
         self.w = model.zb.wq
         _, gn = grid_freqs(model)
         g2 = gn * gn
-        self.K = np.where(g2 > 0.0, W * g2 / (g2 + gmax * gmax), W)
+        g1 = np.min(g2[g2 > 0.0])
+        self.K = np.where(g2 > 0.0, W * g2 / (g2 + gmax * gmax), W * g1 / (g1 + gmax * gmax))
         self.depth = depth
         self.hist = []            # (rho_in_g, R_g)
+
+    def kerker(self, R):
+        """The Kerker step's factor on every component (module docstring)."""
+        return self.K[None, :, :] * R
 
     def dot(self, a, b):
         return float(np.sum(self.w[:, None, None] * np.real(np.conj(a) * b)))
@@ -202,7 +212,7 @@ class Mixer:
         a = np.linalg.lstsq(A, rhs, rcond=None)[0][:m]
         rho_opt = sum(a[i] * self.hist[i][0] for i in range(m))
         R_opt = sum(a[i] * self.hist[i][1] for i in range(m))
-        return to_r(rho_opt + self.K[None, :, :] * R_opt)
+        return to_r(rho_opt + self.kerker(R_opt))
 
 
 def scf(w, nbands, nelec, sigma=0.01, W=0.5, gmax=1.0, tol=1e-7, max_iter=60, kweights=None):

@@ -18,8 +18,11 @@
 //                      dropped, as for the core term).
 //  xc_lda_kernel       LDA exchange and the Perdew-Zunger (1981)
 //                      parametrization of the Ceperley-Alder correlation.
-//  mixing kernels      the paper's Kerker form on g != 0 (the g = 0 profile
-//                      mixed linearly), Pulay over the last steps (§III.A).
+//  mixing kernels      the paper's Kerker form on g != 0; the g = 0 profile
+//                      (which the printed factor would freeze) scaled by the
+//                      factor of the grid's first nonzero shell, so the
+//                      mixing stays local in z and keeps the electron count;
+//                      Pulay over the last steps (§III.A).
 // mb_scf drives the loop: V_scf = V_H + V_xc of the input density is added
 // to the atoms' table, the eigensolver runs on the handle, Fermi-Dirac
 // occupations give the output density, and the mixer the next input, until
@@ -46,7 +49,11 @@ constexpr double kTwoPi = 6.283185307179586476925;
 // energy per electron of the unpolarized electron gas (Hartree)
 constexpr double kPzGamma = -0.1423, kPzBeta1 = 1.0529, kPzBeta2 = 0.3334;
 constexpr double kPzA = 0.0311, kPzB = -0.048, kPzC = 0.0020, kPzD = -0.0116;
-constexpr double kRhoFloor = 1e-30;   // at or below: no exchange-correlation potential
+// The LDA is evaluated at max(rho, kRhoFloor) (bohr^-3): the vacuum's densities
+// of 1e-16 and below are noise of the FP64 sums and of the eigenvectors, and
+// their cube root would dominate every change of V_xc; below the floor the
+// potential is the small constant v_xc(kRhoFloor), continuous in rho.
+constexpr double kRhoFloor = 1e-10;
 
 struct DensK {
     const double2 *X;   // nbands x nb x ldg coefficients of this k-point
@@ -231,24 +238,20 @@ __global__ void hartree_sweep_kernel(const double2 *rg, double2 *vg, const doubl
 
 __global__ void xc_lda_kernel(const double *rho, double *vxc, double *exc, size_t n) {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const double d = rho[e];
-        double v = 0.0, en = 0.0;
-        if (d > kRhoFloor) {
-            const double rs = cbrt(3.0 / (4.0 * 3.14159265358979323846 * d));
-            const double ex = -0.75 * cbrt(3.0 * d / 3.14159265358979323846);
-            double ec, vc;
-            if (rs >= 1.0) {
-                const double sr = sqrt(rs), den = 1.0 + kPzBeta1 * sr + kPzBeta2 * rs;
-                ec = kPzGamma / den;
-                vc = ec * (1.0 + (7.0 / 6.0) * kPzBeta1 * sr + (4.0 / 3.0) * kPzBeta2 * rs) / den;
-            } else {
-                const double lr = log(rs);
-                ec = kPzA * lr + kPzB + kPzC * rs * lr + kPzD * rs;
-                vc = kPzA * lr + (kPzB - kPzA / 3.0) + (2.0 / 3.0) * kPzC * rs * lr + (2.0 * kPzD - kPzC) * rs / 3.0;
-            }
-            v = (4.0 / 3.0) * ex + vc;
-            en = ex + ec;
+        const double d = fmax(rho[e], kRhoFloor);
+        const double rs = cbrt(3.0 / (4.0 * 3.14159265358979323846 * d));
+        const double ex = -0.75 * cbrt(3.0 * d / 3.14159265358979323846);
+        double ec, vc;
+        if (rs >= 1.0) {
+            const double sr = sqrt(rs), den = 1.0 + kPzBeta1 * sr + kPzBeta2 * rs;
+            ec = kPzGamma / den;
+            vc = ec * (1.0 + (7.0 / 6.0) * kPzBeta1 * sr + (4.0 / 3.0) * kPzBeta2 * rs) / den;
+        } else {
+            const double lr = log(rs);
+            ec = kPzA * lr + kPzB + kPzC * rs * lr + kPzD * rs;
+            vc = kPzA * lr + (kPzB - kPzA / 3.0) + (2.0 / 3.0) * kPzC * rs * lr + (2.0 * kPzD - kPzC) * rs / 3.0;
         }
+        const double v = (4.0 / 3.0) * ex + vc, en = ex + ec;
         vxc[e] = v;
         if (exc) exc[e] = en;
     }
@@ -299,16 +302,17 @@ struct MixArgs {
     const double2 *rin[kMaxPulay], *res[kMaxPulay];
     double a[kMaxPulay];
     int m, N1, N2, NN;
-    double b1x, b1y, b2x, b2y, W, gmax2;
+    double b1x, b1y, b2x, b2y, W, gmax2, K0;
 };
 
-// out(z, g) = sum_i a_i rho_in_i + K(g) sum_i a_i R_i, K = W g^2/(g^2 + g_max^2) (g != 0), W (g = 0)
+// out(z, g) = sum_i a_i rho_in_i + K(g) sum_i a_i R_i, K = W g^2/(g^2 + g_max^2)
+// (g != 0), K0 = the same factor on the grid's first nonzero shell (g = 0)
 __global__ void mix_combine_kernel(const __grid_constant__ MixArgs a, double2 *out, size_t n) {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(e % a.NN), u = r / a.N2, v = r % a.N2;
         const int m1 = u < a.N1 / 2 ? u : u - a.N1, m2 = v < a.N2 / 2 ? v : v - a.N2;
         const double gx = m1 * a.b1x + m2 * a.b2x, gy = m1 * a.b1y + m2 * a.b2y, g2 = gx * gx + gy * gy;
-        const double K = g2 > 0.0 ? a.W * g2 / (g2 + a.gmax2) : a.W;
+        const double K = g2 > 0.0 ? a.W * g2 / (g2 + a.gmax2) : a.K0;
         double2 x = czero<double2>(), y = czero<double2>();
         for (int i = 0; i < a.m; ++i) {
             const double2 p = a.rin[i][e], q = a.res[i][e];
@@ -615,6 +619,15 @@ int mb_scf(mb_handle *h, const mb_scf_opts *o, double *evals, double *rho_out, m
                 for (int i = h->lstart[g]; i < h->lstart[g + 1]; ++i) nelec += h->lion[3 * i];
     }
     if (!(nelec > 0.0) || nelec > 2.0 * nbands) return MB_EINVAL;
+    // |g|^2 of the grid's first nonzero shell (the g = 0 profile's mixing factor)
+    double g1sq = INFINITY;
+    for (int u = 0; u < h->n1; ++u)
+        for (int v = 0; v < h->n2; ++v) {
+            const int m1 = u < h->n1 / 2 ? u : u - h->n1, m2 = v < h->n2 / 2 ? v : v - h->n2;
+            const double gx = m1 * h->b1[0] + m2 * h->b2[0], gy = m1 * h->b1[1] + m2 * h->b2[1];
+            const double g2 = gx * gx + gy * gy;
+            if (g2 > 0.0) g1sq = std::min(g1sq, g2);
+        }
     std::vector<double> wk(nk, 1.0 / nk);
     if (o->kweights) {
         double sw = 0.0;
@@ -754,6 +767,7 @@ int mb_scf(mb_handle *h, const mb_scf_opts *o, double *evals, double *rho_out, m
             ma.b2y = h->b2[1];
             ma.W = W;
             ma.gmax2 = gmax * gmax;
+            ma.K0 = W * g1sq / (g1sq + gmax * gmax);
             mix_combine_kernel<<<grid_blocks(h, n), 256, 0, s>>>(ma, cur_in, n);
             MB_CUDA(cudaGetLastError());
             ++h->launches;

@@ -121,14 +121,15 @@ def test_xc_matches_oracle(mbmod):
     rng = np.random.default_rng(6)
     rs = np.exp(rng.uniform(np.log(0.02), np.log(200.0), shape))
     rho_h = 3.0 / (4.0 * math.pi * rs ** 3)
-    rho_h.reshape(-1)[:5] = [0.0, -1e-6, 1e-31, 1e-29, 3.0 / (4.0 * math.pi)]
+    rho_h.reshape(-1)[:5] = [0.0, -1e-6, 1e-31, 1e-9, 3.0 / (4.0 * math.pi)]
     rho = torch.from_numpy(rho_h).cuda()
     v, e = _field(h), _field(h)
     h.xc_lda(rho, v, e)
     torch.cuda.synchronize()
     vr, er = F.xc_pz(rho_h)
     assert _rel(v.cpu().numpy(), vr) < 1e-13 and _rel(e.cpu().numpy(), er) < 1e-13
-    assert not np.any(v.cpu().numpy().reshape(-1)[:3])
+    vf = v.cpu().numpy().reshape(-1)
+    assert vf[0] == vf[1] == vf[2] and vf[3] < vf[0] < 0
     h.close()
 
 

@@ -107,7 +107,7 @@ def test_hartree_error_falls_with_the_knot_spacing():
 
 def test_xc_potential_is_the_derivative_of_the_energy_density():
     """v_xc = d(rho eps_xc)/d rho on both sides of r_s = 1 (central differences)."""
-    rs = np.array([0.05, 0.3, 0.9, 1.2, 3.0, 10.0, 60.0])
+    rs = np.array([0.05, 0.3, 0.9, 1.2, 3.0, 10.0, 60.0, 400.0])
     n = 3.0 / (4.0 * math.pi * rs ** 3)
     v, _ = F.xc_pz(n)
     h = 1e-5 * n
@@ -131,9 +131,11 @@ def test_xc_limits_and_continuity():
     hi = F.xc_pz(np.array([n1 * (1 - 1e-12)]))
     assert abs(lo[0][0] - hi[0][0]) < 1e-4 and abs(lo[1][0] - hi[1][0]) < 1e-4
     assert np.all(ec < 0) and np.all(np.diff(ec[np.argsort(rs)]) > 0)
-    # no density, no potential
-    v0, e0 = F.xc_pz(np.array([0.0, -1e-9, 1e-40]))
-    assert not np.any(v0) and not np.any(e0)
+    # below the floor (and for negative densities) the value at the floor:
+    # continuous in rho, small, constant
+    v0, e0 = F.xc_pz(np.array([0.0, -1e-9, 1e-40, F.RHO_FLOOR, 2 * F.RHO_FLOOR]))
+    assert np.all(v0[:4] == v0[3]) and np.all(e0[:4] == e0[3])
+    assert -1e-3 < v0[3] < 0 and v0[4] < v0[3]
 
 
 def test_occupations_count_and_limits():
@@ -162,7 +164,7 @@ def test_pulay_coefficients_minimise_the_residual():
     rins = [rng.standard_normal((nq, 8, 8)) for _ in range(3)]
     routs = [r + 0.1 * rng.standard_normal((nq, 8, 8)) for r in rins]
     new1 = mx.step(rins[0], routs[0])
-    kerker = F.to_r(F.to_g(rins[0]) + mx.K[None] * (F.to_g(routs[0]) - F.to_g(rins[0])))
+    kerker = F.to_r(F.to_g(rins[0]) + mx.kerker(F.to_g(routs[0]) - F.to_g(rins[0])))
     assert np.abs(new1 - kerker).max() < 1e-12
     mx.step(rins[1], routs[1])
     mx.step(rins[2], routs[2])
@@ -179,6 +181,22 @@ def test_pulay_coefficients_minimise_the_residual():
     a = np.linalg.solve(M, np.r_[0, 0, 0, 1.0])[:3]
     assert abs(obj(a[:2]) - obj(best)) < 1e-10 * obj(best)
     assert np.abs(a - a_best).max() < 1e-5
+
+
+def test_kerker_factor_keeps_the_charge():
+    """The paper's factor on g != 0; at g = 0 the factor of the first shell, a
+    profile scaling, so a residual with no net charge moves none."""
+    m = Hm.model_from_workload(_cell(grid=(8, 8)))
+    mx = F.Mixer(m, 0.7, 0.8)
+    _, gn = F.grid_freqs(m)
+    g2 = gn * gn
+    assert abs(mx.K[3, 1] - 0.7 * g2[3, 1] / (g2[3, 1] + 0.64)) < 1e-15
+    g1 = np.min(g2[g2 > 0])
+    assert abs(mx.K[0, 0] - 0.7 * g1 / (g1 + 0.64)) < 1e-15
+    rng = np.random.default_rng(1)
+    R = F.to_g(rng.standard_normal((len(m.zb.zq), 8, 8)))
+    R[:, 0, 0] -= np.sum(m.zb.wq * R[:, 0, 0]) / np.sum(m.zb.wq)      # no net charge
+    assert abs(np.sum(m.zb.wq * mx.kerker(R)[:, 0, 0])) < 1e-14
 
 
 def test_scf_reaches_a_self_consistent_density():
