@@ -232,6 +232,10 @@ typedef struct {
     int polish;           /* reserved (0) */
     int guard;            /* extra roots carried above the requested ones
                              (0: max(2, ceil(nbands/8)); negative: none) */
+    int warm_start;       /* nonzero: evecs holds start vectors for the nbands
+                             roots (any basis of a nearby subspace, e.g. the
+                             roots of a previous potential); they replace the
+                             lowest free-electron states of the cold start */
 } mb_solve_opts;
 
 /* Lowest `nbands` roots of H c = eps S c at every k-point (§II.C).

@@ -2123,6 +2123,10 @@ struct Solver {
 namespace {
 // The solve runs on a private non-blocking stream (capturable, unlike the
 // legacy default stream) that first waits for the caller's stream.
+// a mixed-precision warm start whose FP64 residuals are all below this (Ha)
+// goes straight to the finish phase
+constexpr double kWarmFinishResidual = 1e-4;
+
 struct SolveStream {
     cudaStream_t s = nullptr;
     cudaError_t err = cudaSuccess;
@@ -2257,11 +2261,19 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
     S.cuda(cudaMemsetAsync(S.d_Ysel, 0, sizeof(double2) * (size_t)nprob * LD * LD, s));
     S.cuda(cudaMemsetAsync(S.d_status, 0, sizeof(int) * S.nk, s));
     S.cuda(cudaMemsetAsync(S.d_tcerr, 0, sizeof(int), s));
-    // initial trial vectors
+    // initial trial vectors: the lowest free-electron states, or (warm
+    // start) the caller's vectors in place of the first nbands of them
+    const bool warm = so && so->warm_start && evecs;
+    size_t woff = 0;
     for (int k = 0; k < S.nk && !S.rc; ++k) {
         std::vector<double2> X0;
         free_electron_start(h, k, S.M, X0);
         S.cuda(cudaMemcpyAsync(S.kd_host[k].base, X0.data(), sizeof(double2) * X0.size(), cudaMemcpyHostToDevice, s));
+        const size_t nwarm = (size_t)nbands * h->nb * h->kp[k].ldg;
+        if (warm)
+            S.cuda(cudaMemcpyAsync(S.kd_host[k].base, reinterpret_cast<const double2 *>(evecs) + woff,
+                                   sizeof(double2) * nwarm, cudaMemcpyDeviceToDevice, s));
+        woff += nwarm;
         S.cuda(cudaStreamSynchronize(s));
     }
     S.prec = prec;
@@ -2279,19 +2291,44 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
             if (r2) return r2;
         }
     }
-    if (S.lowp()) {
-        // mixed precision: the bulk cycles start from FP32 copies of the
-        // (S-orthonormal) free-electron roots
-        S.copy(1, vs(S.oV, S.M), vs(S.o32X, S.M), 3);
-        S.apply32(S.o32X, S.o32HX, S.M);
-        S.bandS(S.o32X, S.o32SX, S.M, true);
-        S.orth_rr();
-    } else {
-        S.applyH(S.oV, S.oHV, S.M, S.prec);
+    bool started = false;
+    if (S.lowp() && warm) {
+        // a warm start already near convergence skips the FP32 bulk cycles
+        // (whose rounding would first undo its accuracy): the start vectors'
+        // FP64 residuals decide
+        S.fp64_roots = true;
+        S.applyH(S.oV, S.oHV, S.M, MB_FP64);
         S.bandS(S.oV, S.oSV, S.M);
-        S.rr_full(false);
+        S.orth_rr();
+        S.residuals_and_seeds(1);
+        std::vector<double> r0((size_t)S.nk * S.M);
+        S.cuda(cudaMemcpyAsync(r0.data(), S.d_res, sizeof(double) * r0.size(), cudaMemcpyDeviceToHost, s));
+        S.cuda(cudaStreamSynchronize(s));
+        double mx = 0.0;
+        for (int k = 0; k < S.nk; ++k)
+            for (int i = 0; i < S.Mconv; ++i) {
+                const double r = r0[(size_t)k * S.M + i];
+                mx = std::max(mx, r == r ? r : 1e300);
+            }
+        if (mx < kWarmFinishResidual) started = true;
+        else S.fp64_roots = false;
     }
-    S.residuals_and_seeds(1);
+    if (!started) {
+        if (S.lowp()) {
+            // mixed precision: the bulk cycles start from FP32 copies of the
+            // (S-orthonormal) start vectors
+            S.copy(1, vs(S.oV, S.M), vs(S.o32X, S.M), 3);
+            S.apply32(S.o32X, S.o32HX, S.M);
+            S.bandS(S.o32X, S.o32SX, S.M, true);
+            S.orth_rr();
+        } else {
+            S.applyH(S.oV, S.oHV, S.M, S.prec);
+            S.bandS(S.oV, S.oSV, S.M);
+            if (warm) S.orth_rr();        // the caller's vectors next to free-electron guards: S-orthonormalize
+            else S.rr_full(false);
+        }
+        S.residuals_and_seeds(1);
+    }
     std::vector<double> res((size_t)S.nk * S.M);
     double last = 1e300, prev = 1e300, maxres = 1e300, bulk_best = 1e300;
     int bulk_idle = 0;

@@ -697,7 +697,9 @@ int mb_scf(mb_handle *h, const mb_scf_opts *o, double *evals, double *rho_out, m
             auto t1 = clk::now();
             t_pot += std::chrono::duration<double>(t1 - t0).count();
             mb_solve_info si{};
-            rc = mb_eigsolve(h, nbands, eig_tol, o->prec, ev.data(), evecs, nullptr, &si, s);
+            mb_solve_opts so{};
+            so.warm_start = it > 1;          // from the roots of the previous potential
+            rc = mb_eigsolve(h, nbands, eig_tol, o->prec, ev.data(), evecs, &so, &si, s);
             cycles += si.cycles;
             auto t2 = clk::now();
             t_eig += std::chrono::duration<double>(t2 - t1).count();

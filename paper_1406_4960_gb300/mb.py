@@ -82,7 +82,8 @@ class ScfInfo(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("krylov_depth", ctypes.c_int), ("block", ctypes.c_int),
-                ("max_cycles", ctypes.c_int), ("polish", ctypes.c_int), ("guard", ctypes.c_int)]
+                ("max_cycles", ctypes.c_int), ("polish", ctypes.c_int), ("guard", ctypes.c_int),
+                ("warm_start", ctypes.c_int)]
 
 
 _lib = None
@@ -479,10 +480,12 @@ class Handle:
         return buf.value.decode()
 
     def eigsolve(self, nbands, tol, prec="fp64", evecs=None, krylov_depth=0, block=0,
-                 max_cycles=0, polish=0, stream=None, allow_notconv=False, guard=0):
+                 max_cycles=0, polish=0, stream=None, allow_notconv=False, guard=0, warm_start=False):
         ev = np.zeros(self.nk * nbands)
         info = SolveInfo()
-        so = SolveOpts(krylov_depth, block, max_cycles, polish, guard)
+        if warm_start and evecs is None:
+            raise MBError(1, "warm_start needs the start vectors in evecs")
+        so = SolveOpts(krylov_depth, block, max_cycles, polish, guard, int(bool(warm_start)))
         if evecs is not None:
             need = sum(nbands * self.sizes(ik)[1] * self.sizes(ik)[2] for ik in range(self.nk))
             if evecs.dtype.itemsize != 16 or evecs.numel() < need or not evecs.is_cuda or not evecs.is_contiguous():

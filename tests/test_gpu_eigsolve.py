@@ -262,3 +262,25 @@ def test_eigsolve_full_kbatch_matches_oracle_golden(mbmod):
     for ik, ref in gold.items():
         assert np.abs(ev[ik] - ref).max() < EV_TOL, (ik, np.abs(ev[ik] - ref).max())
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_warm_start(mbmod, prec):
+    """Starting from converged roots the solve ends at once with the same
+    eigenvalues; after a constant shift of the potential (the roots are
+    unchanged, the eigenvalues shift by it) it needs fewer cycles than a cold
+    start and matches the dense oracle."""
+    w = W.tiny()
+    h = mbmod.Handle.from_workload(w)
+    need = sum(w.nbands * h.sizes(ik)[1] * h.sizes(ik)[2] for ik in range(w.nk))
+    evecs = torch.zeros(need, dtype=torch.complex128, device="cuda")
+    ev0, cold = h.eigsolve(w.nbands, 1e-8, prec, evecs=evecs)
+    ev1, warm = h.eigsolve(w.nbands, 1e-8, prec, evecs=evecs, warm_start=True)
+    m, ref = _dense_ref(w, 0, w.nbands)
+    assert warm.cycles <= 2 and np.abs(ev1[0] - ref).max() < EV_TOL
+    V = h.local_potential()
+    h.set_local_potential(V + 0.37)
+    ev2, shifted = h.eigsolve(w.nbands, 1e-8, prec, evecs=evecs, warm_start=True)
+    assert shifted.cycles < cold.cycles
+    assert np.abs(ev2[0] - (ref + 0.37)).max() < EV_TOL
+    h.close()
