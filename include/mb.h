@@ -63,6 +63,15 @@ typedef struct { double a1[2]; double a2[2]; } mb_cell;
  *     +(2 pi Z / A_c) [dz erf(dz / Rcore) + (Rcore / sqrt(pi)) exp(-dz^2 / Rcore^2)],
  * dz = z - pos[2] (a constant shifts every eigenvalue by itself; in a neutral
  * cell the electrons' Hartree term cancels it).
+ * Ultrasoft augmentation (§II.B.2; used when any q is nonzero): the overlap
+ * becomes S = S_0 + sum q_pq |beta_p><beta_q| over the atom's projectors,
+ * q[0..3] for 1s, p_x, p_y, p_z, q2s for 2s and q12 for the 1s-2s pair (the
+ * pairs whose augmentation charge Q_{nl,n'l'}(r) Y_LM with L = min|l - l'|
+ * integrates to nonzero in the real p basis), with the synthetic charge
+ * shape Q_pq(r) = q_pq exp(-r^2/rQ^2) / (pi^(3/2) rQ^3) (rQ > 0 in bohr).
+ * mb_scf makes the strengths self-consistent, D_pq = E_pq + int V_eff Q_pq,
+ * and augments the density; mb_apply_S includes the term; mb_apply_Sinv
+ * returns MB_EUNSUPPORTED for such a handle.
  * Kleinman-Bylander projectors (Eq. (14)), GTH Gaussian radial parts with
  * alpha = 1 / (2 rc^2) for every channel: nproj = 0 (none), 4 (1s, p_x, p_y,
  * p_z) or 5 (the same and the second s channel, beta ~ r^2 exp(-alpha r^2),
@@ -81,6 +90,10 @@ typedef struct {
     double E12;
     double Z;
     double Rcore;
+    double q[4];
+    double q2s;
+    double q12;
+    double rQ;
 } mb_atom;
 
 typedef struct {

@@ -26,6 +26,15 @@ Elements, in Hartree (the paper's Rydberg -nabla^2 becomes -nabla^2/2):
   Z_{1,00} Q_{2,00} + Z_{2,00} Q_{1,00} (r^2 split into its in-plane and z
   parts).  The strengths form a Hermitian matrix per atom: E_{nl} on the
   diagonal and an optional 1s-2s coupling (the general E_{nl,n'l'} of GTH).
+* ultrasoft pseudopotentials (§II.B.2): the overlap becomes
+      S = S_0 + sum_pq q_pq u_p u_q^H,  q_pq = int Q_pq(r) d^3r,
+  and the strengths E_pq are the self-consistent ones of the loop (``scf``).
+  With the paper's restriction Q_pq(r) = Q_{nl,n'l'}(r) Y_LM, L = min |l - l'|,
+  only pairs whose L = 0 part survives integrate to nonzero q: in the real
+  p_x, p_y, p_z basis those are (s, s), (2s, 2s), (1s, 2s) and (p_i, p_i),
+  the pattern of the KB strengths.  The radial parts are synthetic (no
+  Vanderbilt files are at hand): Q_pq(r) = q_pq g(r), g the normalized
+  Gaussian exp(-r^2/r_Q^2) / (pi^(3/2) r_Q^3) of the atom;
 
 Readings:
 * Gaussian local term A exp(-|r-R|^2/(2 w^2)), i.e. a = 1/(2 w^2);
@@ -111,7 +120,7 @@ class Model:
     """One k-point of the slab problem with all matrix-element ingredients."""
 
     def __init__(self, a1, a2, k, ecut, breaks, order, atoms, grid, nquad=None,
-                 local_components=None, table=None):
+                 local_components=None, table=None, strengths=None):
         self.a1 = np.asarray(a1, dtype=np.float64)
         self.a2 = np.asarray(a2, dtype=np.float64)
         self.k = np.asarray(k, dtype=np.float64)
@@ -127,6 +136,9 @@ class Model:
         # (nq, N1, N2) (the general local potential of Eqs. (19)-(20); the SCF
         # loop puts V_H + V_xc here)
         self.table = None if table is None else np.asarray(table, dtype=np.float64)
+        # strengths E_pq replacing the atoms' (the self-consistent D of the
+        # ultrasoft loop), same layout as kb_projectors' E
+        self.strengths = None if strengths is None else np.asarray(strengths, dtype=np.float64)
         self._sphere()
         self.S = self.zb.overlap()
         self.D = self.zb.stiffness()
@@ -291,23 +303,32 @@ class Model:
                 raise ValueError("nproj must be 0, 4 or 5")
             for p in range(at.nproj):
                 Us.append(phase[None, :] * np.conj(fs[p]) / math.sqrt(self.Ac))
-            Eb = np.diag(np.array(list(at.E) + ([at.e2s] if at.nproj == 5 else []), dtype=float))
-            if at.nproj == 5:
-                Eb[0, 4] = Eb[4, 0] = at.e12
-            blocks.append(Eb)
+            blocks.append(_atom_block(at, list(at.E), at.e2s, at.e12))
         if not Us:
             return np.zeros((0, 0)), np.zeros((0, self.nb, self.ng), dtype=np.complex128)
-        n = sum(b.shape[0] for b in blocks)
-        E = np.zeros((n, n))
-        o = 0
-        for b in blocks:
-            E[o:o + b.shape[0], o:o + b.shape[0]] = b
-            o += b.shape[0]
+        E = _block_diag(blocks)
+        if self.strengths is not None:
+            E = self.strengths
         return E, np.array(Us)
+
+    def uspp_q(self):
+        """q_pq of the ultrasoft overlap (§II.B.2), kb_projectors' layout."""
+        return _block_diag([_atom_block(at, list(getattr(at, "q", (0.0,) * 4)), getattr(at, "q2s", 0.0),
+                                        getattr(at, "q12", 0.0)) for at in self.atoms if at.nproj])
+
+    @property
+    def uspp(self):
+        Q = self.uspp_q()
+        return Q.size > 0 and bool(np.any(Q != 0.0))
 
     # ---- dense matrices -------------------------------------------------
     def dense_S(self):
-        return np.kron(self.S, np.eye(self.ng)).astype(np.complex128)
+        S = np.kron(self.S, np.eye(self.ng)).astype(np.complex128)
+        if self.uspp:
+            _, U = self.kb_projectors()
+            Uf = U.reshape(U.shape[0], -1).T
+            S += Uf @ self.uspp_q() @ Uf.conj().T
+        return S
 
     def dense_H(self):
         n = self.nbasis
@@ -336,7 +357,12 @@ class Model:
     # ---- matrix-free apply (the same elements, contracted directly) ----
     def apply_S(self, X):
         X = np.asarray(X, dtype=np.complex128)
-        return np.einsum("ij,bjg->big", self.S, X)
+        Y = np.einsum("ij,bjg->big", self.S, X)
+        if self.uspp:
+            _, U = self.kb_projectors()
+            Fp = np.einsum("pjg,bjg->pb", np.conj(U), X)
+            Y += np.einsum("pjg,pb->bjg", U, self.uspp_q() @ Fp)
+        return Y
 
     def apply_H(self, X):
         X = np.asarray(X, dtype=np.complex128)
@@ -386,8 +412,27 @@ class Model:
         return out
 
 
-def model_from_workload(w, ik=0, local_components=None, with_atoms=True, table=None):
+def _atom_block(at, diag, d2s, d12):
+    """One atom's block: diag over 1s, p_x, p_y, p_z (and 2s), the 1s-2s
+    coupling off the diagonal."""
+    b = np.diag(np.array(list(diag) + ([d2s] if at.nproj == 5 else []), dtype=float))
+    if at.nproj == 5:
+        b[0, 4] = b[4, 0] = d12
+    return b
+
+
+def _block_diag(blocks):
+    n = sum(b.shape[0] for b in blocks)
+    M = np.zeros((n, n))
+    o = 0
+    for b in blocks:
+        M[o:o + b.shape[0], o:o + b.shape[0]] = b
+        o += b.shape[0]
+    return M
+
+
+def model_from_workload(w, ik=0, local_components=None, with_atoms=True, table=None, strengths=None):
     """Oracle model for k-point `ik` of a workload description."""
     return Model(w.a1, w.a2, w.kpts[ik], w.ecut, w.breaks, w.order,
                  w.atoms if with_atoms else [], w.grid, w.nquad,
-                 local_components=local_components, table=table)
+                 local_components=local_components, table=table, strengths=strengths)

@@ -40,6 +40,14 @@ benchmark's CPU baseline use it; the library never does.
   weights w_k; the chemical potential by bisection on the electron count.
 * Convergence (§III.A): the change of V_scf = V_H + V_xc between successive
   iterations, max over the planes' grid points, below tol.
+* Ultrasoft atoms (§II.B.2, Eq. for E_nlm,n'l'm'): the strengths of every
+  iteration are D_pq = E0_pq + int V_eff Q_pq d^3r with V_eff = V_H + V_xc +
+  V_LOC (the tabulated total local potential), i.e. with Q_pq = q_pq g
+  (hamiltonian.py), D_pq = E0_pq + q_pq int V_eff g, the integral the grid
+  sum sum_q w_q sum_r V g A_c / (N1 N2); the eigenproblem is H c = eps S c
+  with the ultrasoft S; and the density is augmented inside the cores,
+      rho += sum_atoms g(r) sum_n f_n sum_pq q_pq <phi_n|beta_p><beta_q|phi_n>,
+  which keeps the electron count: int rho = sum_n f_n <phi_n|S|phi_n>.
 """
 from __future__ import annotations
 
@@ -177,6 +185,64 @@ def core_density(model):
     return to_r(c)
 
 
+def atom_gaussian(model, at, R=None):
+    """The normalized Gaussian exp(-|r - R|^2/R^2) / (pi^(3/2) R^3) of an atom
+    on the grid (radius R, default the atom's augmentation radius rQ)."""
+    R = at.rQ if R is None else R
+    g, gn = grid_freqs(model)
+    dz = model.zb.zq - at.pos[2]
+    prof = np.exp(-(dz / R) ** 2) / (math.sqrt(math.pi) * R)
+    phase = np.exp(-1j * (g[..., 0] * at.pos[0] + g[..., 1] * at.pos[1]))
+    return to_r((1.0 / model.Ac) * prof[:, None, None] * (np.exp(-0.25 * (gn * R) ** 2) * phase)[None])
+
+
+def grid_integral(model, f):
+    """int f d^3r on the planes' grid: sum_q w_q sum_r f A_c / (N1 N2)."""
+    N1, N2 = model.grid
+    return float(np.sum(model.zb.wq[:, None, None] * f) * model.Ac / (N1 * N2))
+
+
+def _proj_atoms(model):
+    """(atom, first projector index, count) of every atom with projectors."""
+    out, o = [], 0
+    for at in model.atoms:
+        if at.nproj:
+            out.append((at, o, at.nproj))
+            o += at.nproj
+    return out
+
+
+def uspp_strengths(model, veff):
+    """D = E0 + q (int V_eff g) per atom block (§II.B.2)."""
+    E0 = Hm._block_diag([Hm._atom_block(at, list(at.E), at.e2s, at.e12) for at in model.atoms if at.nproj])
+    Q = model.uspp_q()
+    D = E0.copy()
+    for at, o, n in _proj_atoms(model):
+        if np.any(Q[o:o + n, o:o + n] != 0.0):
+            D[o:o + n, o:o + n] += Q[o:o + n, o:o + n] * grid_integral(model, veff * atom_gaussian(model, at))
+    return D
+
+
+def augmentation(models, coefs, occ):
+    """sum_atoms g(r) w_atom, w_atom = sum_{k,n} f sum_pq q_pq conj(F_p) F_q,
+    F_p = <beta_p|phi> = u_p^H c."""
+    m0 = models[0]
+    Q = m0.uspp_q()
+    atoms = _proj_atoms(m0)
+    w = np.zeros(len(atoms))
+    for m, C, f in zip(models, coefs, occ):
+        _, U = m.kb_projectors()
+        F = np.einsum("pjg,njg->np", np.conj(U), C)            # F[n, p]
+        for i, (at, o, n) in enumerate(atoms):
+            Fa = F[:, o:o + n]
+            w[i] += float(np.real(np.einsum("n,np,pq,nq->", f, np.conj(Fa), Q[o:o + n, o:o + n], Fa)))
+    rho = np.zeros((len(m0.zb.zq),) + m0.grid)
+    for i, (at, o, n) in enumerate(atoms):
+        if w[i] != 0.0:
+            rho += w[i] * atom_gaussian(m0, at)
+    return rho
+
+
 class Mixer:
     """Kerker + Pulay (RMM-DIIS) over the last `depth` steps (§III.A)."""
 
@@ -226,13 +292,17 @@ def scf(w, nbands, nelec, sigma=0.01, W=0.5, gmax=1.0, tol=1e-7, max_iter=60, kw
     vprev = None
     dv = math.inf
     it = 0
+    uspp = base[0].uspp
     for it in range(1, max_iter + 1):
         vh = to_r(hartree_g(base[0], to_g(rho_in)))
         vxc, _ = xc_pz(rho_in)
         vscf = vh + vxc
         dv = math.inf if vprev is None else float(np.abs(vscf - vprev).max())
         vprev = vscf
-        models = [Hm.model_from_workload(w, ik, table=vscf) for ik in range(nk)]
+        D = None
+        if uspp:
+            D = uspp_strengths(base[0], Hm.model_from_workload(w, 0, table=vscf).local_table())
+        models = [Hm.model_from_workload(w, ik, table=vscf, strengths=D) for ik in range(nk)]
         evals, coefs = [], []
         for m in models:
             ev, C = E.generalized_lowest(m.dense_H(), m.dense_S(), nbands, vectors=True)
@@ -243,5 +313,7 @@ def scf(w, nbands, nelec, sigma=0.01, W=0.5, gmax=1.0, tol=1e-7, max_iter=60, kw
             break
         f, _ = occupations(evals, kw, nelec, sigma)
         rho_out = density(models, coefs, f)
+        if uspp:
+            rho_out = rho_out + augmentation(models, coefs, f)
         rho_in = mixer.step(rho_in, rho_out)
-    return {"evals": evals, "rho": rho_in, "vscf": vscf, "iterations": it, "dv": dv}
+    return {"evals": evals, "rho": rho_in, "vscf": vscf, "iterations": it, "dv": dv, "strengths": D}

@@ -631,6 +631,14 @@ static int upload_set(mb_handle *h, DevTables &t) {
         std::vector<double> e(h->Ekb);
         e.insert(e.end(), h->Ecoup.begin(), h->Ecoup.end());
         if ((rc = upload<R>(h, &t.E, e))) return rc;
+        if (h->uspp) {
+            std::vector<double> q(h->Qkb);
+            q.insert(q.end(), h->Qcoup.begin(), h->Qcoup.end());
+            if ((rc = upload<R>(h, &t.Q, q))) return rc;
+            std::vector<double> id(2 * (size_t)h->nkb, 0.0);
+            std::fill(id.begin(), id.begin() + h->nkb, 1.0);
+            if ((rc = upload<R>(h, &t.Eid, id))) return rc;
+        }
     }
     const int nmax = std::max(h->n1, h->n2);
     std::vector<cdouble> tw(nmax / 2);
@@ -645,7 +653,13 @@ int upload_potential(mb_handle *h) { return vloc_build(h); }
 
 int upload_tables(mb_handle *h) {
     MB_CUDA(cudaSetDevice(h->device));
-    if (!h->hs) MB_CUDA(cudaStreamCreateWithFlags(&h->hs, cudaStreamNonBlocking));
+    if (!h->hs) {
+        // set-up work at the highest priority: a new handle's uploads and
+        // table kernels are scheduled ahead of the kernels of running solves
+        int lo = 0, hi = 0;
+        MB_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        MB_CUDA(cudaStreamCreateWithPriority(&h->hs, cudaStreamNonBlocking, hi));
+    }
     int rc;
     if ((rc = upload_set<double>(h, h->t64))) return rc;
     if ((rc = upload_set<float>(h, h->t32))) return rc;
@@ -752,7 +766,7 @@ int ensure_precond(mb_handle *h) {
 }
 
 static void free_set(mb_handle *h, DevTables &t) {
-    void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.Lrecip, &t.q2, &t.qproj, &t.zproj, &t.zf, &t.E, &t.Pfac, &t.Vt};
+    void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.Lrecip, &t.q2, &t.qproj, &t.zproj, &t.zf, &t.E, &t.Pfac, &t.Vt, &t.Q, &t.Eid};
     for (void **p : ps) dev_free(h, p);
 }
 
@@ -1250,6 +1264,194 @@ static int apply_H_launch(mb_handle *h, int nsel, const int *iks, const void *co
     return MB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Ultrasoft overlap term (§II.B.2): Y += sum_pq q_pq beta_p (beta_q^H X), by
+// the KB kernels with the strengths q in place of E (same sparsity: diagonal
+// and the 1s-2s partner), the back-projection added to Y by the epilogue's
+// KB-only pass.  Scratch: the projector regions of the apply's layout.
+size_t uspp_scratch_group(const mb_handle *h, int nsel, const int *iks, int nbands, int prec) {
+    const size_t c2 = prec == MB_FP64 ? 16 : 8;
+    int maxldg = 0;
+    for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
+    return (size_t)nsel * per_k_scratch(h, maxldg, nbands, 1, c2, false);
+}
+
+size_t uspp_scratch_bytes(const mb_handle *h, int nk, int nbands, int prec) {
+    nk = std::min(nk, (int)h->kp.size());
+    size_t need = 0;
+    for (int i0 = 0; i0 < nk; i0 += kMaxK) {
+        std::vector<int> ik;
+        for (int i = i0; i < std::min(nk, i0 + kMaxK); ++i) ik.push_back(i);
+        need = std::max(need, uspp_scratch_group(h, (int)ik.size(), ik.data(), nbands, prec));
+    }
+    return need;
+}
+
+// The KB contraction of X with strengths Es (device, the layout of E) into
+// the scratch's c[b][p] (coef_only) or, further, back-projected and added
+// to Y.
+template <typename R>
+static int projector_pass(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y, int nbands,
+                          cudaStream_t s, const DevTables &t, const void *Es, bool coef_only, KDesc *desc_out) {
+    typedef typename V2<R>::T R2;
+    if (h->nterm <= 0) return MB_OK;
+    const size_t c2 = sizeof(R2);
+    int maxldg = 0;
+    for (int i = 0; i < nsel; ++i) maxldg = std::max(maxldg, h->kp[iks[i]].ldg);
+    if (h->scratch.bytes < uspp_scratch_group(h, nsel, iks, nbands, sizeof(R) == 8 ? MB_FP64 : MB_FP32))
+        return MB_EUNSUPPORTED;
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    char *base = reinterpret_cast<char *>(h->scratch.ptr);
+    KDesc desc[kMaxK];
+    size_t off = 0;
+    for (int i = 0; i < nsel; ++i) {
+        const KPoint &kp = h->kp[iks[i]];
+        KDesc &d = desc[i];
+        d = KDesc();
+        d.X = X[i];
+        d.Y = Y ? Y[i] : nullptr;
+        d.ng = kp.ng;
+        d.ldg = kp.ldg;
+        d.kofs = h->kofs[iks[i]];
+        d.qofs = h->qofs[iks[i]];
+        const KScratch ks = per_k_layout(h, maxldg, nbands, 1, c2, false);
+        d.part = base + off;
+        off += al(ks.part);
+        d.W = base + off;
+        off += al(ks.w);
+        d.C = base + off;
+        off += al(ks.c);
+    }
+    if (desc_out) std::copy(desc, desc + nsel, desc_out);
+    const int *d_pgroup = h->d_zidx;
+    const int *d_zstart = d_pgroup + h->nterm;
+    const int *d_zlist = d_zstart + h->nzf + 1;
+    const int *d_tproj = d_zlist + h->nterm;
+    const int *d_partner = d_tproj + h->nterm;
+    const int *d_pstart = d_partner + h->nkb;
+    const int *d_plist = d_pstart + h->nkb + 1;
+    NlArgs<R> na;
+    na.zf = reinterpret_cast<const R *>(t.zf);
+    na.E = reinterpret_cast<const R *>(Es);
+    na.pgroup = d_pgroup;
+    na.partner = d_partner;
+    na.pstart = d_pstart;
+    na.plist = d_plist;
+    na.Q = reinterpret_cast<const R2 *>(t.qproj);
+    na.nb = h->nb;
+    na.nbands = nbands;
+    na.nterm = h->nterm;
+    na.nkb = h->nkb;
+    na.nz = h->nzf;
+    std::copy(desc, desc + nsel, na.d);
+    const int zseg = std::max(1, std::min(8, h->nb / 8));
+    na.nseg = zseg;
+    const dim3 gz((maxldg + 63) / 64, nbands, nsel), bz(64, zseg);
+#define MB_ZX(NZ)                                                                                  \
+    do {                                                                                           \
+        const size_t zsm = (size_t)zseg * NZ * 64 * sizeof(R2) + (size_t)h->nzf * h->nb * sizeof(R); \
+        MB_CUDA(smem_limit_once((const void *)nl_zx_kernel<R, NZ>, h->device, h->smem_optin));   \
+        MB_LAUNCH(h, s, KN_PROJ, (nl_zx_kernel<R, NZ><<<gz, bz, zsm, s>>>(na)));                   \
+    } while (0)
+    if (h->nzf <= 2) MB_ZX(2);
+    else if (h->nzf <= 4) MB_ZX(4);
+    else if (h->nzf <= 8) MB_ZX(8);
+    else if (h->nzf <= 12) MB_ZX(12);
+    else MB_ZX(16);
+#undef MB_ZX
+    MB_LAUNCH(h, s, KN_COEF, nl_coef_kernel<R><<<dim3(nbands, nsel, (h->nkb + 7) / 8), 256, 0, s>>>(na));
+    if (coef_only) {
+        MB_CUDA(cudaGetLastError());
+        return MB_OK;
+    }
+    const size_t bsm = (size_t)h->nterm * (sizeof(R2) + sizeof(int));
+    MB_CUDA(smem_limit_once((const void *)nl_back_kernel<R>, h->device, h->smem_optin));
+    MB_LAUNCH(h, s, KN_COEF, nl_back_kernel<R><<<dim3((maxldg + 127) / 128, h->nzf, nbands * nsel), 128, bsm, s>>>(
+                                 na, d_zstart, d_zlist, d_tproj));
+    // Y += sum_f z_f(j) R_f(G): the epilogue's KB-only passes
+    EpiArgs<R> ea;
+    ea.Sband = reinterpret_cast<const R *>(t.Sband);
+    ea.Dband = reinterpret_cast<const R *>(t.Dband);
+    ea.q2 = reinterpret_cast<const R *>(t.q2);
+    ea.zf = reinterpret_cast<const R *>(t.zf);
+    ea.order = h->order;
+    ea.nb = h->nb;
+    ea.nbands = nbands;
+    ea.nchunks = 1;
+    ea.nint = h->nint;
+    ea.nz = h->nzf;
+    constexpr int ERM = sizeof(R) == 4 ? 8 : 4;
+    const int ejseg = (h->nb + ERM - 1) / ERM;
+    ea.njseg = ejseg;
+    if (h->nb > kMaxEpiRows) return MB_EUNSUPPORTED;
+    for (int j = 0; j < h->nb; ++j) ea.src[j] = -1;
+    std::copy(desc, desc + nsel, ea.d);
+    const dim3 ge((maxldg + 63) / 64, nbands * ejseg, nsel);
+    for (int f0 = 0; f0 < h->nzf; f0 += 16) {
+        ea.f0 = f0;
+        ea.f1 = std::min(h->nzf, f0 + 16);
+        ea.base = 0;
+        const int nfp = ea.f1 - ea.f0;
+        const int nzb = nfp <= 4 ? 4 : nfp <= 8 ? 8 : nfp <= 12 ? 12 : 16;
+        constexpr int HWn = 5;   // unused by the KB-only pass (no band rows)
+        const size_t esm = ((size_t)2 * ERM * ((2 * HWn + 1 + 3) / 4 * 4) + (size_t)ERM * nzb) * sizeof(R);
+#define MB_EPI(NZ)                                                                                            \
+    do {                                                                                                      \
+        MB_CUDA(smem_limit_once((const void *)epilogue_kernel<R, NZ, HWn, ERM>, h->device, h->smem_optin));  \
+        MB_LAUNCH(h, s, KN_EPILOGUE, (epilogue_kernel<R, NZ, HWn, ERM><<<ge, 64, esm, s>>>(ea)));            \
+    } while (0)
+        if (nzb == 4) MB_EPI(4);
+        else if (nzb == 8) MB_EPI(8);
+        else if (nzb == 12) MB_EPI(12);
+        else MB_EPI(16);
+#undef MB_EPI
+    }
+    MB_CUDA(cudaGetLastError());
+    return MB_OK;
+}
+
+int uspp_S_add(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y, int nbands, int prec,
+               cudaStream_t s) {
+    if (!h->uspp) return MB_OK;
+    for (int i0 = 0; i0 < nsel; i0 += kMaxK) {
+        const int n = std::min(kMaxK, nsel - i0);
+        const int rc = prec == MB_FP64
+                           ? projector_pass<double>(h, n, iks + i0, X + i0, Y + i0, nbands, s, h->t64, h->t64.Q,
+                                                    false, nullptr)
+                           : projector_pass<float>(h, n, iks + i0, X + i0, Y + i0, nbands, s, h->t32, h->t32.Q,
+                                                   false, nullptr);
+        if (rc) return rc;
+    }
+    return MB_OK;
+}
+
+int uspp_overlaps(mb_handle *h, const void *evecs, int nbands, double *F, cudaStream_t s) {
+    if (!h->uspp || h->nkb == 0) return MB_EINVAL;
+    const int nk = (int)h->kp.size();
+    std::vector<int> iks(nk);
+    std::vector<const void *> xs(nk);
+    size_t off = 0;
+    for (int k = 0; k < nk; ++k) {
+        iks[k] = k;
+        xs[k] = reinterpret_cast<const double2 *>(evecs) + off;
+        off += (size_t)nbands * h->nb * h->kp[k].ldg;
+    }
+    int rc = ensure_scratch(h, uspp_scratch_bytes(h, nk, nbands, MB_FP64), s);
+    if (rc) return rc;
+    for (int k0 = 0; k0 < nk; k0 += kMaxK) {
+        const int n = std::min(kMaxK, nk - k0);
+        KDesc desc[kMaxK];
+        if ((rc = projector_pass<double>(h, n, iks.data() + k0, xs.data() + k0, nullptr, nbands, s, h->t64,
+                                         h->t64.Eid, true, desc)))
+            return rc;
+        for (int i = 0; i < n; ++i)
+            MB_CUDA(cudaMemcpyAsync(F + 2 * (size_t)(k0 + i) * nbands * h->nkb, desc[i].C,
+                                    sizeof(double2) * (size_t)nbands * h->nkb, cudaMemcpyDeviceToHost, s));
+        MB_CUDA(cudaStreamSynchronize(s));   // the next group reuses the scratch
+    }
+    return MB_OK;
+}
+
 int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y,
                   int nbands, int prec, cudaStream_t s) {
     if (nsel <= 0 || !iks || !X || !Y) return MB_EINVAL;
@@ -1284,13 +1486,24 @@ int apply_banded_batch(mb_handle *h, int which, int nsel, const int *iks, const 
         if (X[i] == Y[i]) return MB_EINVAL;
     }
     MB_CUDA(cudaSetDevice(h->device));
-    if (banded_block_supported(h, prec, which == BAND_SINV))
-        return banded_block_apply(h, which == BAND_SINV, nsel, iks, X, Y, nbands, prec, s);
-    for (int i = 0; i < nsel; ++i) {
-        const int rc = apply_banded(h, which, iks[i], X[i], Y[i], nbands, prec, s);
-        if (rc) return rc;
+    if (h->uspp && which == BAND_SINV) return MB_EUNSUPPORTED;   // the inverse of the augmented S is not banded
+    int rc = MB_OK;
+    if (banded_block_supported(h, prec, which == BAND_SINV)) {
+        rc = banded_block_apply(h, which == BAND_SINV, nsel, iks, X, Y, nbands, prec, s);
+    } else {
+        for (int i = 0; i < nsel && rc == MB_OK; ++i) rc = apply_banded(h, which, iks[i], X[i], Y[i], nbands, prec, s);
     }
-    return MB_OK;
+    if (rc == MB_OK && h->uspp) {
+        // the ultrasoft term on top of S_0 X (grows the scratch: not during stream capture)
+        size_t need = 0;
+        for (int i0 = 0; i0 < nsel; i0 += kMaxK) {
+            std::vector<int> ik(iks + i0, iks + std::min(nsel, i0 + kMaxK));
+            need = std::max(need, uspp_scratch_group(h, (int)ik.size(), ik.data(), nbands, prec));
+        }
+        if ((rc = ensure_scratch(h, need, s))) return rc;
+        rc = uspp_S_add(h, nsel, iks, X, Y, nbands, prec, s);
+    }
+    return rc;
 }
 
 int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nbands, int prec,

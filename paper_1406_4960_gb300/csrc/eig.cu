@@ -1760,6 +1760,8 @@ struct Solver {
         const unsigned bx = (unsigned)std::min<long long>(64, (nmax + 255) / 256);
         MB_LAUNCH_E(KN_VEC, copy_kernel<<<dim3(bx, S.count(), nk * nch), 256, 0, s>>>(d_k, nch, S, D, mode));
     }
+    // S X: the banded S_0 of Eqs. (7)-(8) and, for ultrasoft atoms, the
+    // augmentation term sum q |beta><beta| X (§II.B.2)
     void bandS(int src, int dst, int nv, bool f32 = false) {
         const dim3 grid((maxldg + 127) / 128, h->nb, nk * nv);
         const void *Sb = f32 ? h->t32.Sband : h->t64.Sband;
@@ -1773,6 +1775,23 @@ struct Solver {
         break;
             MB_BS(3) MB_BS(4) MB_BS(5) MB_BS(6) MB_BS(7) MB_BS(8)
 #undef MB_BS
+        }
+        if (h->uspp && !rc) {
+            std::vector<int> iks(nk);
+            std::vector<const void *> xs(nk);
+            std::vector<void *> ys(nk);
+            for (int k = 0; k < nk; ++k) {
+                iks[k] = k;
+                if (f32) {
+                    xs[k] = kd_host[k].v32 + (long long)src * kd_host[k].nvec;
+                    ys[k] = kd_host[k].v32 + (long long)dst * kd_host[k].nvec;
+                } else {
+                    xs[k] = kd_host[k].base + (long long)src * kd_host[k].nvec;
+                    ys[k] = kd_host[k].base + (long long)dst * kd_host[k].nvec;
+                }
+            }
+            const int r = uspp_S_add(h, nk, iks.data(), xs.data(), ys.data(), nv, f32 ? MB_FP32 : MB_FP64, s);
+            if (r && rc == MB_OK) rc = r;
         }
     }
     void coldot(int nch, VSet A, VSet B, double *out, bool f32 = false) {
@@ -2283,8 +2302,10 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
         size_t need = 0;
         const int sizes[3] = {1, S.nc, S.nc_stage()};
         for (int pi = 0; pi < 2; ++pi)
-            for (int bi = 0; bi < 3; ++bi)
+            for (int bi = 0; bi < 3; ++bi) {
                 need = std::max(need, apply_scratch_bytes(h, S.nk, sizes[bi], pi == 0 ? MB_FP64 : MB_FP32));
+                if (h->uspp) need = std::max(need, uspp_scratch_bytes(h, S.nk, sizes[bi], pi == 0 ? MB_FP64 : MB_FP32));
+            }
         S.cuda(cudaStreamSynchronize(s));
         if (S.rc == MB_OK) {
             int r2 = ensure_scratch(h, need, s);
@@ -2324,7 +2345,9 @@ int eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals, void
         } else {
             S.applyH(S.oV, S.oHV, S.M, S.prec);
             S.bandS(S.oV, S.oSV, S.M);
-            if (warm) S.orth_rr();        // the caller's vectors next to free-electron guards: S-orthonormalize
+            // the caller's vectors next to free-electron guards, or free-electron
+            // states that the ultrasoft S does not keep orthonormal: S-orthonormalize
+            if (warm || h->uspp) S.orth_rr();
             else S.rr_full(false);
         }
         S.residuals_and_seeds(1);

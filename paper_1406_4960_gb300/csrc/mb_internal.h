@@ -43,6 +43,8 @@ struct DevTables {
     void *E = nullptr;       // nkb diagonal strengths, then nkb partner couplings
     void *Pfac = nullptr;    // preconditioner factors: all k, ldg x nb x order each
     void *Vt = nullptr;      // nq x N2 x N1, w_q V / (N1 N2), i1 fastest (FP32 compact-plane kernel)
+    void *Q = nullptr;       // ultrasoft q: nkb diagonal, then nkb partner couplings (the layout of E)
+    void *Eid = nullptr;     // strengths 1 (diagonal) and 0 (couplings): the overlaps <beta_p|x> themselves
 };
 
 struct Scratch {
@@ -81,6 +83,13 @@ struct mb_handle {
     // (the 1s-2s pair of an atom; -1 for none).
     int nkb = 0;
     std::vector<double> zproj, Ekb, Ecoup;
+    // ultrasoft augmentation (§II.B.2): q of every projector and of its
+    // partner coupling (the layout of Ekb / Ecoup); the atoms whose
+    // augmentation charges are nonzero: first projector, count, position, r_Q
+    bool uspp = false;
+    std::vector<double> Qkb, Qcoup;
+    struct AugAtom { int p0, np; double x, y, z, rQ; };
+    std::vector<AugAtom> aug;
     std::vector<int> tproj, partner, pstart, plist;   // term -> projector; terms of projector p
     // distinct z factors of the terms: zfun (nzf x nb), pgroup[t] = f, and
     // the terms of factor f in zlist[zstart[f] .. zstart[f+1])
@@ -154,7 +163,16 @@ int upload_potential(mb_handle *h);
 int vloc_build(mb_handle *h);             // d_vloc from the atoms' analytic terms, then the derived tables
 int vloc_derive_tables(mb_handle *h);     // d_vloc -> t64.V/Vn, t32.V/Vn/Vt
 size_t vloc_build_scratch_bytes(const mb_handle *h);
-int vloc_tabulate(mb_handle *h, int mode, double *out, cudaStream_t s);   // 0: V(r, z_q); 1: core charge density
+int vloc_tabulate(mb_handle *h, int mode, double *out, cudaStream_t s, const std::vector<double> *lgrp = nullptr,
+                  const std::vector<double> *lion = nullptr, const std::vector<int> *lstart = nullptr);
+// 0: V(r, z_q); 1: core charge density (of the given groups instead of the atoms', when passed)
+// apply.cu: the ultrasoft overlap term Y += sum q_pq beta_p (beta_q^H X) (§II.B.2)
+int uspp_S_add(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y, int nbands, int prec,
+               cudaStream_t s);
+size_t uspp_scratch_bytes(const mb_handle *h, int nk, int nbands, int prec);
+// apply.cu: <beta_p|x_b> of FP64 blocks (the layout of mb_eigsolve's evecs) into F (host,
+// nk x nbands x nkb complex as interleaved doubles)
+int uspp_overlaps(mb_handle *h, const void *evecs, int nbands, double *F, cudaStream_t s);
 int ensure_precond(mb_handle *h);
 void free_tables(mb_handle *h);
 int ensure_scratch(mb_handle *h, size_t bytes, cudaStream_t s);

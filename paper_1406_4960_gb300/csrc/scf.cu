@@ -23,10 +23,15 @@
 //                      factor of the grid's first nonzero shell, so the
 //                      mixing stays local in z and keeps the electron count;
 //                      Pulay over the last steps (§III.A).
+//  aug_integral_kernel int V_eff g_a d^3r for the ultrasoft atoms' normalized
+//                      augmentation Gaussians g_a, in the planes' components.
 // mb_scf drives the loop: V_scf = V_H + V_xc of the input density is added
 // to the atoms' table, the eigensolver runs on the handle, Fermi-Dirac
 // occupations give the output density, and the mixer the next input, until
-// V_scf changes by less than the tolerance.
+// V_scf changes by less than the tolerance.  With ultrasoft atoms (§II.B.2)
+// every iteration also sets the strengths D_pq = E_pq + q_pq int V_eff g_a
+// (Q_pq = q_pq g_a) and augments the output density by
+// g_a sum_n f_n sum_pq q_pq <phi_n|beta_p><beta_q|phi_n>.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -257,6 +262,37 @@ __global__ void xc_lda_kernel(const double *rho, double *vxc, double *exc, size_
     }
 }
 
+// One (plane q, ultrasoft atom a): Ac w_q sum_m Re(conj(V(z_q, m)) g_a(z_q, m)),
+// g_a's components (1/(sqrt(pi) r_Q A_c)) e^{-g^2 r_Q^2/4 - dz^2/r_Q^2} e^{-i g.R}.
+// The host adds the planes in order: int V g_a = sum_q out[a][q].
+__global__ void __launch_bounds__(256) aug_integral_kernel(const double2 *Vg, const double *atoms, const double *zq,
+                                                           const double *wq, int nq, int N1, int N2, double b1x,
+                                                           double b1y, double b2x, double b2y, double Ac,
+                                                           double *out) {
+    __shared__ double red[256];
+    const int q = blockIdx.x, at = blockIdx.y, NN = N1 * N2;
+    const double x = atoms[4 * at], y = atoms[4 * at + 1], dz = zq[q] - atoms[4 * at + 2], rq = atoms[4 * at + 3];
+    const double pre = 0.56418958354775628695 / (rq * Ac) * exp(-(dz / rq) * (dz / rq));
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < NN; e += 256) {
+        const int u = e / N2, v = e % N2;
+        const int m1 = u < N1 / 2 ? u : u - N1, m2 = v < N2 / 2 ? v : v - N2;
+        const double gx = m1 * b1x + m2 * b2x, gy = m1 * b1y + m2 * b2y;
+        double sn, cs;
+        sincos(-(gx * x + gy * y), &sn, &cs);
+        const double a = pre * exp(-0.25 * (gx * gx + gy * gy) * rq * rq);
+        const double2 V = Vg[(size_t)q * NN + e];
+        acc += V.x * a * cs + V.y * a * sn;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[(size_t)at * nq + q] = Ac * wq[q] * red[0];
+}
+
 // out = a + b (+ c)
 __global__ void add_kernel(const double *a, const double *b, const double *c, double *out, size_t n) {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
@@ -471,9 +507,11 @@ static int upload_planes(mb_handle *h, Buf &B, ScfPlanes &pl, cudaStream_t s) {
 }
 
 // V_H (real field) of the density rho (real field)
-static int hartree(mb_handle *h, const double *rho, double *vh, Buf &B, const ScfPlanes &pl, cudaStream_t s) {
+static int hartree(mb_handle *h, const double *rho, double *vh, Buf &B, const ScfPlanes &pl, cudaStream_t s,
+                   double2 *rg = nullptr, double2 *vg = nullptr) {
     const size_t n = (size_t)h->nq * h->n1 * h->n2;
-    double2 *rg = B.get<double2>(n), *vg = B.get<double2>(n);
+    if (!rg) rg = B.get<double2>(n);
+    if (!vg) vg = B.get<double2>(n);
     if (B.rc) return B.rc;
     int rc;
     if ((rc = plane_fft2(h, false, rho, nullptr, nullptr, rg, 1.0 / (h->n1 * h->n2), s))) return rc;
@@ -552,6 +590,82 @@ static double occupations(const std::vector<double> &ev, const std::vector<doubl
     for (int k = 0; k < nk; ++k)
         for (int n = 0; n < nbands; ++n) f[(size_t)k * nbands + n] = 2.0 * wk[k] * fd(ev[(size_t)k * nbands + n], mu);
     return mu;
+}
+
+// Ultrasoft strengths D = E + q int V g_a from the handle's current table
+// (V_eff = V_H + V_xc + V_LOC), uploaded to both precisions' tables.
+static int uspp_strengths(mb_handle *h, const ScfPlanes &pl, double2 *vg, double *atoms, double *out,
+                          std::vector<double> &Ehost, cudaStream_t s) {
+    const int na = (int)h->aug.size(), NN = h->n1 * h->n2;
+    std::vector<double> ah(4 * (size_t)na), oh((size_t)na * h->nq);
+    for (int a = 0; a < na; ++a) {
+        ah[4 * a] = h->aug[a].x;
+        ah[4 * a + 1] = h->aug[a].y;
+        ah[4 * a + 2] = h->aug[a].z;
+        ah[4 * a + 3] = h->aug[a].rQ;
+    }
+    MB_CUDA(cudaMemcpyAsync(atoms, ah.data(), sizeof(double) * ah.size(), cudaMemcpyHostToDevice, s));
+    int rc = plane_fft2(h, false, h->d_vloc, nullptr, nullptr, vg, 1.0 / NN, s);
+    if (rc) return rc;
+    aug_integral_kernel<<<dim3(h->nq, na), 256, 0, s>>>(vg, atoms, pl.zq, pl.wq, h->nq, h->n1, h->n2, h->b1[0],
+                                                         h->b1[1], h->b2[0], h->b2[1], h->Ac, out);
+    MB_CUDA(cudaGetLastError());
+    ++h->launches;
+    MB_CUDA(cudaMemcpyAsync(oh.data(), out, sizeof(double) * oh.size(), cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    Ehost.assign(h->Ekb.begin(), h->Ekb.end());
+    Ehost.insert(Ehost.end(), h->Ecoup.begin(), h->Ecoup.end());
+    for (int a = 0; a < na; ++a) {
+        double I = 0.0;
+        for (int q = 0; q < h->nq; ++q) I += oh[(size_t)a * h->nq + q];
+        for (int p = h->aug[a].p0; p < h->aug[a].p0 + h->aug[a].np; ++p) {
+            Ehost[p] += h->Qkb[p] * I;
+            Ehost[h->nkb + p] += h->Qcoup[p] * I;
+        }
+    }
+    std::vector<float> e32(Ehost.begin(), Ehost.end());
+    MB_CUDA(cudaMemcpyAsync(h->t64.E, Ehost.data(), sizeof(double) * Ehost.size(), cudaMemcpyHostToDevice, s));
+    MB_CUDA(cudaMemcpyAsync(h->t32.E, e32.data(), sizeof(float) * e32.size(), cudaMemcpyHostToDevice, s));
+    MB_CUDA(cudaStreamSynchronize(s));   // e32 and Ehost are host buffers
+    return MB_OK;
+}
+
+// Augmentation of the output density: rho += sum_a w_a g_a with
+// w_a = sum_{k,n} f sum_pq q_pq conj(F_p) F_q, F_p = <beta_p|phi_n>.
+static int uspp_augment(mb_handle *h, const void *evecs, int nbands, const std::vector<double> &f, double *rho,
+                        double *aug, cudaStream_t s) {
+    const int nk = (int)h->kp.size(), nkb = h->nkb, na = (int)h->aug.size();
+    const size_t n = (size_t)h->nq * h->n1 * h->n2;
+    std::vector<double> F((size_t)nk * nbands * nkb * 2);
+    int rc = uspp_overlaps(h, evecs, nbands, F.data(), s);
+    if (rc) return rc;
+    std::vector<double> grp, ion;
+    std::vector<int> start(1, 0);
+    for (int a = 0; a < na; ++a) {
+        double w = 0.0;
+        for (int k = 0; k < nk; ++k)
+            for (int b = 0; b < nbands; ++b) {
+                const double fb = f[(size_t)k * nbands + b];
+                if (fb == 0.0) continue;
+                const double *Fk = F.data() + 2 * ((size_t)k * nbands + b) * nkb;
+                for (int p = h->aug[a].p0; p < h->aug[a].p0 + h->aug[a].np; ++p) {
+                    const double re = Fk[2 * p], im = Fk[2 * p + 1];
+                    double t = h->Qkb[p] * (re * re + im * im);
+                    const int q = h->partner[p];
+                    if (q >= 0) t += h->Qcoup[p] * (re * Fk[2 * q] + im * Fk[2 * q + 1]);
+                    w += fb * t;
+                }
+            }
+        // one group per atom: the core-density profile of radius r_Q, weight w_a
+        grp.insert(grp.end(), {1.0, h->aug[a].rQ, h->aug[a].z});
+        ion.insert(ion.end(), {w, h->aug[a].x, h->aug[a].y});
+        start.push_back(a + 1);
+    }
+    if ((rc = vloc_tabulate(h, 1, aug, s, &grp, &ion, &start))) return rc;
+    add_kernel<<<grid_blocks(h, n), 256, 0, s>>>(rho, aug, nullptr, rho, n);
+    MB_CUDA(cudaGetLastError());
+    ++h->launches;
+    return MB_OK;
 }
 
 }  // namespace mb
@@ -662,20 +776,27 @@ int mb_scf(mb_handle *h, const mb_scf_opts *o, double *evals, double *rho_out, m
             hin[i] = B.get<double2>(n);
             hres[i] = B.get<double2>(n);
         }
+        // work fields, allocated once: two spectra (the Coulomb step and the
+        // ultrasoft integrals), the augmentation density, the ultrasoft atoms
+        double2 *wk1 = B.get<double2>(n), *wk2 = B.get<double2>(n);
+        double *aug = h->uspp ? B.get<double>(n) : nullptr;
+        const size_t na = h->aug.size();
+        double *aug_atoms = h->uspp ? B.get<double>(4 * na) : nullptr;
+        double *aug_out = h->uspp ? B.get<double>(na * h->nq) : nullptr;
         ScfPlanes pl;
         if (B.rc) return B.rc;
         if ((rc = upload_planes(h, B, pl, s))) return rc;
         // the atoms' table, and the start density: their Gaussian core charges
         MB_CUDA(cudaMemcpyAsync(vext, h->d_vloc, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         if ((rc = vloc_tabulate(h, 1, rho_in, s))) return rc;
-        std::vector<double> ev((size_t)nk * nbands), f, red_h(h->nq), Ahist((size_t)depth * depth, 0.0);
+        std::vector<double> ev((size_t)nk * nbands), f, red_h(h->nq), Ahist((size_t)depth * depth, 0.0), Ehost;
         int nh = 0, head = 0;   // history entries and the slot the next one goes to
         double dv = INFINITY, mu = 0.0, t_eig = 0.0, t_dens = 0.0, t_pot = 0.0;
         int it = 0, cycles = 0;
         for (it = 1; it <= max_iter; ++it) {
             auto t0 = clk::now();
             // V_scf of the input density, its change, and the apply tables
-            if ((rc = hartree(h, rho_in, vh, B, pl, s)) || (rc = xc(h, rho_in, vx, nullptr, s))) {
+            if ((rc = hartree(h, rho_in, vh, B, pl, s, wk1, wk2)) || (rc = xc(h, rho_in, vx, nullptr, s))) {
                 result = rc;
                 break;
             }
@@ -691,6 +812,10 @@ int mb_scf(mb_handle *h, const mb_scf_opts *o, double *evals, double *rho_out, m
             MB_CUDA(cudaStreamSynchronize(s));
             if (it > 1) dv = *std::max_element(red_h.begin(), red_h.end());
             if ((rc = vloc_derive_tables(h))) {
+                result = rc;
+                break;
+            }
+            if (h->uspp && (rc = uspp_strengths(h, pl, wk1, aug_atoms, aug_out, Ehost, s))) {
                 result = rc;
                 break;
             }
@@ -712,6 +837,10 @@ int mb_scf(mb_handle *h, const mb_scf_opts *o, double *evals, double *rho_out, m
             mu = occupations(ev, wk, nbands, nelec, o->sigma, f);
             MB_CUDA(cudaMemcpyAsync(occ, f.data(), sizeof(double) * f.size(), cudaMemcpyHostToDevice, s));
             if ((rc = scf_density(h, evecs, nbands, occ, rho_o, s))) {
+                result = rc;
+                break;
+            }
+            if (h->uspp && (rc = uspp_augment(h, evecs, nbands, f, rho_o, aug, s))) {
                 result = rc;
                 break;
             }

@@ -285,6 +285,9 @@ int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int
     h->zproj.assign((size_t)NP * nb, 0.0);
     h->Ekb.assign(h->nkb, 0.0);
     h->Ecoup.assign(h->nkb, 0.0);
+    h->Qkb.assign(h->nkb, 0.0);
+    h->Qcoup.assign(h->nkb, 0.0);
+    h->aug.clear();
     h->partner.assign(h->nkb, -1);
     h->tproj.assign(NP, 0);
     h->pstart.assign(h->nkb + 1, 0);
@@ -319,12 +322,21 @@ int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int
             }
         }
         for (int c = 0; c < 4; ++c) h->Ekb[pp + c] = at.E[c];
+        for (int c = 0; c < 4; ++c) h->Qkb[pp + c] = at.q[c];
         for (int c = 0; c < nt; ++c) h->tproj[tt + c] = pp + (c < 4 ? c : 4);
         if (two_s) {
             h->Ekb[pp + 4] = at.E2s;
             h->partner[pp] = pp + 4;
             h->partner[pp + 4] = pp;
             h->Ecoup[pp] = h->Ecoup[pp + 4] = at.E12;
+            h->Qkb[pp + 4] = at.q2s;
+            h->Qcoup[pp] = h->Qcoup[pp + 4] = at.q12;
+        }
+        bool aug = false;
+        for (int c = 0; c < at.nproj; ++c) aug = aug || h->Qkb[pp + c] != 0.0 || h->Qcoup[pp + c] != 0.0;
+        if (aug) {
+            if (!(at.rQ > 0.0)) return MB_EINVAL;
+            h->aug.push_back({pp, at.nproj, at.pos[0], at.pos[1], at.pos[2], at.rQ});
         }
         for (int ik = 0; ik < nk; ++ik) {
             KPoint &kp = h->kp[ik];
@@ -347,6 +359,7 @@ int build_host_tables(mb_handle *h, const mb_cell *cell, const double *kpts, int
         tt += nt;
         pp += at.nproj;
     }
+    h->uspp = !h->aug.empty();
     for (int p = 0; p < h->nkb; ++p) {
         for (int t = 0; t < NP; ++t)
             if (h->tproj[t] == p) h->plist.push_back(t);

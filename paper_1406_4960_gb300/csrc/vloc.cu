@@ -94,52 +94,59 @@ __global__ void vloc_sfac_kernel(VlocGeom G, const double *ion, const int *start
     S[(size_t)grp * NN + e] = make_double2(re, im);
 }
 
-// One (row u, plane q): c(m, z_q) for the N2 frequencies of the row, then
-// tmp[q][u][i2] = sum_v c(u, v) exp(2 pi i v i2 / N2).  blockDim.x = N2.
+// One (row u, plane q) per threadIdx.y slice: c(m, z_q) for the N2
+// frequencies of the row, then tmp[q][u][i2] = sum_v c(u, v) exp(2 pi i v i2 / N2).
+// blockDim = (N2, planes per block).
 __global__ void vloc_rows_kernel(VlocGeom G, int mode, const double *grp, const double2 *S, const double *zq, int q0,
-                                 double2 *tmp) {
+                                 int nqc, double2 *tmp) {
     extern __shared__ double2 rs[];
-    double2 *c = rs, *tw = rs + G.N2;
-    const int u = blockIdx.x, q = q0 + blockIdx.y, v = threadIdx.x, NN = G.N1 * G.N2;
-    {
+    double2 *tw = rs, *c = rs + G.N2 + threadIdx.y * G.N2;
+    const int u = blockIdx.x, qq = blockIdx.y * blockDim.y + threadIdx.y, v = threadIdx.x, NN = G.N1 * G.N2;
+    if (threadIdx.y == 0) {
         double sn, cs;
         sincospi(2.0 * v / G.N2, &sn, &cs);
         tw[v] = make_double2(cs, sn);
     }
-    double gx, gy;
-    grid_g(G, u, v, gx, gy);
-    const double g = sqrt(gx * gx + gy * gy), z = zq[q];
-    double re = 0.0, im = 0.0;
-    for (int k = 0; k < G.ngrp; ++k) {
-        const double f = profile(mode, (int)grp[3 * k], grp[3 * k + 1], g, z - grp[3 * k + 2], G.Ac);
-        const double2 s = S[(size_t)k * NN + u * G.N2 + v];
-        re += f * s.x;
-        im += f * s.y;
+    const bool live = qq < nqc;
+    if (live) {
+        double gx, gy;
+        grid_g(G, u, v, gx, gy);
+        const double g = sqrt(gx * gx + gy * gy), z = zq[q0 + qq];
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < G.ngrp; ++k) {
+            const double f = profile(mode, (int)grp[3 * k], grp[3 * k + 1], g, z - grp[3 * k + 2], G.Ac);
+            const double2 s = S[(size_t)k * NN + u * G.N2 + v];
+            re += f * s.x;
+            im += f * s.y;
+        }
+        c[v] = make_double2(re, im);
     }
-    c[v] = make_double2(re, im);
     __syncthreads();
+    if (!live) return;
     double sr = 0.0, si = 0.0;
     for (int w = 0; w < G.N2; ++w) {
         const double2 a = c[w], t = tw[(w * v) & (G.N2 - 1)];
         sr += a.x * t.x - a.y * t.y;
         si += a.x * t.y + a.y * t.x;
     }
-    tmp[((size_t)blockIdx.y * G.N1 + u) * G.N2 + v] = make_double2(sr, si);
+    tmp[((size_t)qq * G.N1 + u) * G.N2 + v] = make_double2(sr, si);
 }
 
-// One (column i2, plane q): V[q][i1][i2] = Re sum_u tmp[q][u][i2] exp(2 pi i u i1 / N1).
-// blockDim.x = N1.
-__global__ void vloc_cols_kernel(VlocGeom G, const double2 *tmp, int q0, double *V) {
+// One (column i2, plane q) per threadIdx.y slice:
+// V[q][i1][i2] = Re sum_u tmp[q][u][i2] exp(2 pi i u i1 / N1).  blockDim = (N1, planes per block).
+__global__ void vloc_cols_kernel(VlocGeom G, const double2 *tmp, int q0, int nqc, double *V) {
     extern __shared__ double2 cs_[];
-    double2 *col = cs_, *tw = cs_ + G.N1;
-    const int i2 = blockIdx.x, qq = blockIdx.y, i1 = threadIdx.x;
-    col[i1] = tmp[((size_t)qq * G.N1 + i1) * G.N2 + i2];
-    {
+    double2 *tw = cs_, *col = cs_ + G.N1 + threadIdx.y * G.N1;
+    const int i2 = blockIdx.x, qq = blockIdx.y * blockDim.y + threadIdx.y, i1 = threadIdx.x;
+    const bool live = qq < nqc;
+    if (live) col[i1] = tmp[((size_t)qq * G.N1 + i1) * G.N2 + i2];
+    if (threadIdx.y == 0) {
         double sn, cs;
         sincospi(2.0 * i1 / G.N1, &sn, &cs);
         tw[i1] = make_double2(cs, sn);
     }
     __syncthreads();
+    if (!live) return;
     double s = 0.0;
     for (int u = 0; u < G.N1; ++u) {
         const double2 a = col[u], t = tw[(u * i1) & (G.N1 - 1)];
@@ -213,9 +220,12 @@ int vloc_derive_tables(mb_handle *h) {
 // The real table of the atoms' analytic terms on the planes into out (nq x
 // N1 x N2, device), on stream s: mode 0 the local potential V(r, z_q),
 // mode 1 the Gaussian core charge density.
-int vloc_tabulate(mb_handle *h, int mode, double *out, cudaStream_t s) {
+int vloc_tabulate(mb_handle *h, int mode, double *out, cudaStream_t s, const std::vector<double> *lgrp_in,
+                  const std::vector<double> *lion_in, const std::vector<int> *lstart_in) {
+    const std::vector<double> &lgrp = lgrp_in ? *lgrp_in : h->lgrp, &lion = lion_in ? *lion_in : h->lion;
+    const std::vector<int> &lstart = lstart_in ? *lstart_in : h->lstart;
     const int N1 = h->n1, N2 = h->n2, NN = N1 * N2, nq = h->nq;
-    const int ngrp = h->lstart.empty() ? 0 : (int)h->lstart.size() - 1;
+    const int ngrp = lstart.empty() ? 0 : (int)lstart.size() - 1;
     if (ngrp == 0) {
         MB_CUDA(cudaMemsetAsync(out, 0, (size_t)nq * NN * sizeof(double), s));
         return MB_OK;
@@ -226,10 +236,10 @@ int vloc_tabulate(mb_handle *h, int mode, double *out, cudaStream_t s) {
     cudaMemPool_t pool = mb_pool(h->device);
     if (!pool) return MB_ECUDA;
     // one pool block: ions | groups | planes | group starts (int) | S | tmp
-    const size_t nion = h->lion.size(), ngv = h->lgrp.size();
+    const size_t nion = lion.size(), ngv = lgrp.size();
     const size_t off_grp = nion * sizeof(double), off_zq = off_grp + ngv * sizeof(double);
     const size_t off_start = off_zq + (size_t)nq * sizeof(double);
-    const size_t off_S = (off_start + h->lstart.size() * sizeof(int) + 255) / 256 * 256;
+    const size_t off_S = (off_start + lstart.size() * sizeof(int) + 255) / 256 * 256;
     const size_t off_tmp = off_S + (size_t)ngrp * per_plane, bytes = off_tmp + (size_t)qc * per_plane;
     unsigned char *blk = nullptr;
     MB_CUDA(cudaMallocFromPoolAsync((void **)&blk, bytes, pool, s));
@@ -237,17 +247,21 @@ int vloc_tabulate(mb_handle *h, int mode, double *out, cudaStream_t s) {
     double *zq = reinterpret_cast<double *>(blk + off_zq);
     int *start = reinterpret_cast<int *>(blk + off_start);
     double2 *S = reinterpret_cast<double2 *>(blk + off_S), *tmp = reinterpret_cast<double2 *>(blk + off_tmp);
-    cudaError_t e = cudaMemcpyAsync(ion, h->lion.data(), nion * sizeof(double), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(grp, h->lgrp.data(), ngv * sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(ion, lion.data(), nion * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grp, lgrp.data(), ngv * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(zq, h->zq.data(), nq * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(start, h->lstart.data(), h->lstart.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(start, lstart.data(), lstart.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         vloc_sfac_kernel<<<dim3((NN + 255) / 256, ngrp), 256, 0, s>>>(G, ion, start, S);
+        // planes per block: blocks of about 256 threads
+        const int pr = std::max(1, 256 / N2), pc = std::max(1, 256 / N1);
         for (int q0 = 0; q0 < nq; q0 += qc) {
             const int n = std::min(qc, nq - q0);
-            vloc_rows_kernel<<<dim3(N1, n), N2, 2 * N2 * sizeof(double2), s>>>(G, mode, grp, S, zq, q0, tmp);
-            vloc_cols_kernel<<<dim3(N2, n), N1, 2 * N1 * sizeof(double2), s>>>(G, tmp, q0, out);
+            vloc_rows_kernel<<<dim3(N1, (n + pr - 1) / pr), dim3(N2, pr), (size_t)(1 + pr) * N2 * sizeof(double2), s>>>(
+                G, mode, grp, S, zq, q0, n, tmp);
+            vloc_cols_kernel<<<dim3(N2, (n + pc - 1) / pc), dim3(N1, pc), (size_t)(1 + pc) * N1 * sizeof(double2), s>>>(
+                G, tmp, q0, n, out);
         }
         e = cudaGetLastError();
     }

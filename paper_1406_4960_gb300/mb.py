@@ -43,7 +43,8 @@ class _Atom(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_double * 3), ("A", ctypes.c_double), ("w", ctypes.c_double),
                 ("nproj", ctypes.c_int), ("E", ctypes.c_double * 4), ("rc", ctypes.c_double),
                 ("E2s", ctypes.c_double), ("E12", ctypes.c_double), ("Z", ctypes.c_double),
-                ("Rcore", ctypes.c_double)]
+                ("Rcore", ctypes.c_double), ("q", ctypes.c_double * 4), ("q2s", ctypes.c_double),
+                ("q12", ctypes.c_double), ("rQ", ctypes.c_double)]
 
 
 class _Opts(ctypes.Structure):
@@ -180,6 +181,10 @@ def _atoms_array(atoms):
         arr[i].E12 = getattr(at, "e12", 0.0)
         arr[i].Z = getattr(at, "Z", 0.0)
         arr[i].Rcore = getattr(at, "Rcore", 0.0)
+        arr[i].q = (ctypes.c_double * 4)(*getattr(at, "q", (0.0, 0.0, 0.0, 0.0)))
+        arr[i].q2s = getattr(at, "q2s", 0.0)
+        arr[i].q12 = getattr(at, "q12", 0.0)
+        arr[i].rQ = getattr(at, "rQ", 0.0)
     return arr
 
 

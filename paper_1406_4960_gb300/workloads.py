@@ -53,6 +53,10 @@ class Atom:
     e12: float = 0.0                     # 1s-2s coupling E_{12} = E_{21} (nproj == 5), Ha
     Z: float = 0.0                       # core term -Z erf(r/Rcore)/r (0: none)
     Rcore: float = 0.0                   # its radius, bohr
+    q: Tuple[float, float, float, float] = (0.0, 0.0, 0.0, 0.0)   # ultrasoft q of 1s, p_x, p_y, p_z
+    q2s: float = 0.0                     # q of the 2s channel (nproj == 5)
+    q12: float = 0.0                     # 1s-2s q (nproj == 5)
+    rQ: float = 0.0                      # radius of the augmentation Gaussian, bohr
 
 
 @dataclasses.dataclass
@@ -231,6 +235,15 @@ def with_core(w: Workload, Z: float, Rcore: float, name: Optional[str] = None) -
     """A copy of `w` whose atoms also carry the core term -Z erf(r/Rcore)/r."""
     return dataclasses.replace(w, name=name or (w.name + "-core"),
                                atoms=[dataclasses.replace(a, Z=float(Z), Rcore=float(Rcore)) for a in w.atoms])
+
+
+def with_uspp(w: Workload, q: Tuple[float, float, float, float], rQ: float, q2s: float = 0.0, q12: float = 0.0,
+              name: Optional[str] = None) -> Workload:
+    """A copy of `w` whose projectors carry ultrasoft augmentation q (the
+    overlap S = S_0 + sum q |beta><beta|) with Gaussian charges of radius rQ."""
+    return dataclasses.replace(w, name=name or (w.name + "-uspp"),
+                               atoms=[dataclasses.replace(a, q=tuple(float(x) for x in q), q2s=float(q2s),
+                                                          q12=float(q12), rQ=float(rQ)) for a in w.atoms])
 
 
 def random_block(nbands: int, nb: int, ng: int, seed: int, ld: Optional[int] = None) -> np.ndarray:

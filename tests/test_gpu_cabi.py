@@ -23,7 +23,8 @@ class Atom(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_double * 3), ("A", ctypes.c_double), ("w", ctypes.c_double),
                 ("nproj", ctypes.c_int), ("E", ctypes.c_double * 4), ("rc", ctypes.c_double),
                 ("E2s", ctypes.c_double), ("E12", ctypes.c_double), ("Z", ctypes.c_double),
-                ("Rcore", ctypes.c_double)]
+                ("Rcore", ctypes.c_double), ("q", ctypes.c_double * 4), ("q2s", ctypes.c_double),
+                ("q12", ctypes.c_double), ("rQ", ctypes.c_double)]
 
 
 class Opts(ctypes.Structure):
