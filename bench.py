@@ -344,6 +344,7 @@ def probe_fp64_peak(lib, device):
 SCF_Z, SCF_RCORE = 4.0, 0.6          # carbon-like core charges on the slab's 12 atoms: 48 electrons
 SCF_SIGMA, SCF_W, SCF_GMAX = 0.01, 0.5, 1.0
 SCF_TOL = 0.5e-6                     # the paper's criterion: V_scf changes by less than 1e-6 Ry
+SCF_USPP_Q, SCF_USPP_RQ = (0.5, 0.2, 0.2, 0.2), 0.8   # synthetic ultrasoft q (1s, p) and charge radius
 
 
 def scf_workload(W):
@@ -424,6 +425,16 @@ def scf_bench(mb, W, local, args):
         h.close()
     out["mixed_speedup_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
     out["mixed_vs_fp64_max_eig_diff_ha"] = float(np.abs(evs["fp32"] - evs["fp64"]).max())
+    # the same slab with ultrasoft augmentation on every projector (section (f)4)
+    wu = W.with_uspp(w, SCF_USPP_Q, SCF_USPP_RQ)
+    h = mb.Handle.from_workload(wu, device=local)
+    ev, info = h.scf(wu.nbands, SCF_TOL, SCF_SIGMA, mix_weight=SCF_W, g_max=SCF_GMAX, prec="fp32",
+                     eig_tol=SCF_TOL / 5, max_iter=80, allow_notconv=True)
+    out["uspp_mixed"] = {"q": list(SCF_USPP_Q), "rQ": SCF_USPP_RQ, "converged": bool(info.dv < SCF_TOL),
+                         "iterations": info.iterations, "seconds": info.seconds, "seconds_eig": info.seconds_eig,
+                         "eig_cycles": info.eig_cycles, "dv_ha": info.dv, "fermi_ha": info.mu,
+                         "nelec": info.nelec, "lowest_ha": float(ev.min())}
+    h.close()
     return out
 
 
