@@ -363,6 +363,48 @@ def density_flops(h, w, nbands):
     return tot
 
 
+def scf_steps(mb, h, w, local):
+    """The self-consistent loop's device steps alone on a handle's current
+    potential: the density of its lowest w.nbands roots (the first 24 per
+    k-point filled), its Coulomb and LDA potentials, each timed with CUDA
+    events on its stream; the density kernel's roofline against the measured
+    FP64 FMA rate."""
+    import torch
+    need = sum(w.nbands * h.sizes(ik)[1] * h.sizes(ik)[2] for ik in range(w.nk))
+    evecs = torch.zeros(need, dtype=torch.complex128, device="cuda:%d" % local)
+    h.eigsolve(w.nbands, SCF_TOL, "fp32", evecs=evecs)
+    zq, _ = h.zplanes()
+    shape = (len(zq), w.grid[0], w.grid[1])
+    rho = torch.zeros(shape, dtype=torch.float64, device="cuda:%d" % local)
+    vh, vx = torch.zeros_like(rho), torch.zeros_like(rho)
+    occ = np.zeros((w.nk, w.nbands))
+    occ[:, :24] = 2.0 / w.nk
+    st = torch.cuda.Stream(device=local)
+    ms = {}
+    for name, fn in (("density", lambda: h.density(evecs, w.nbands, occ, rho, stream=st)),
+                     ("hartree", lambda: h.hartree(rho, vh, stream=st)),
+                     ("xc", lambda: h.xc_lda(rho, vx, stream=st))):
+        for _ in range(2):
+            fn()
+        reps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(local)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize(local)
+        ms[name] = e0.elapsed_time(e1) / reps
+    fl = density_flops(h, w, w.nbands)
+    peak64 = probe_fp64_peak(mb.load(), local)
+    ach = fl / (ms["density"] * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
+            "frac": ach / peak64 if peak64 else None, "gflop": fl / 1e9,
+            "peak_source": "measured: FP64 DFMA loop on this GPU (mb_probe_fp64_fma)",
+            "note": "mb_density as called: occupation upload, partial planes, fixed-order reduction included"}
+    return ms, roof
+
+
 def scf_bench(mb, W, local, args):
     """Section (f)3: the self-consistent loop on the slab with carbon-like core
     charges (48 electrons in 32 bands per k-point), to the paper's criterion,
@@ -388,40 +430,7 @@ def scf_bench(mb, W, local, args):
             "fermi_ha": info.mu, "nelec": info.nelec}
         if prec == "fp32":
             # the device steps alone, on the converged potential
-            need = sum(w.nbands * h.sizes(ik)[1] * h.sizes(ik)[2] for ik in range(w.nk))
-            evecs = torch.zeros(need, dtype=torch.complex128, device="cuda:%d" % local)
-            h.eigsolve(w.nbands, SCF_TOL, "fp32", evecs=evecs)
-            zq, _ = h.zplanes()
-            shape = (len(zq), w.grid[0], w.grid[1])
-            rho = torch.zeros(shape, dtype=torch.float64, device="cuda:%d" % local)
-            vh, vx = torch.zeros_like(rho), torch.zeros_like(rho)
-            occ = np.zeros((w.nk, w.nbands))
-            occ[:, :24] = 2.0 / w.nk
-            st = torch.cuda.Stream(device=local)
-            ms = {}
-            for name, fn in (("density", lambda: h.density(evecs, w.nbands, occ, rho, stream=st)),
-                             ("hartree", lambda: h.hartree(rho, vh, stream=st)),
-                             ("xc", lambda: h.xc_lda(rho, vx, stream=st))):
-                for _ in range(2):
-                    fn()
-                reps = 5
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize(local)
-                e0.record(st)
-                for _ in range(reps):
-                    fn()
-                e1.record(st)
-                torch.cuda.synchronize(local)
-                ms[name] = e0.elapsed_time(e1) / reps
-            fl = density_flops(h, w, w.nbands)
-            peak64 = probe_fp64_peak(mb.load(), local)
-            ach = fl / (ms["density"] * 1e-3) / 1e12
-            out["steps_ms"] = ms
-            out["density_roofline"] = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
-                                       "frac": ach / peak64 if peak64 else None, "gflop": fl / 1e9,
-                                       "peak_source": "measured: FP64 DFMA loop on this GPU (mb_probe_fp64_fma)",
-                                       "note": "mb_density as called: occupation upload, partial planes, "
-                                               "fixed-order reduction included"}
+            out["steps_ms"], out["density_roofline"] = scf_steps(mb, h, w, local)
         h.close()
     out["mixed_speedup_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
     out["mixed_vs_fp64_max_eig_diff_ha"] = float(np.abs(evs["fp32"] - evs["fp64"]).max())
@@ -686,6 +695,14 @@ def run_ours(args):
         h.close()
         print(json.dumps({"scf": scf_bench(mb, W, local, args)}))
         return
+    if args.scf_steps_only:
+        h.close()
+        ws = scf_workload(W)
+        hs = mb.Handle.from_workload(ws, device=local)
+        ms, roof = scf_steps(mb, hs, ws, local)
+        hs.close()
+        print(json.dumps({"scf_steps_ms": ms, "density_roofline": roof}))
+        return
     if args.serve_only:
         h.close()
         print(json.dumps({"serve": serve_bench(mb, W, local, args)}))
@@ -890,6 +907,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-scf", action="store_true")
     ap.add_argument("--scf-only", action="store_true", help="run the self-consistent loop section only")
+    ap.add_argument("--scf-steps-only", action="store_true",
+                    help="time the density, Coulomb and LDA steps of the loop's slab once (no loop)")
     ap.add_argument("--serve-n", type=int, default=256)
     ap.add_argument("--serve-cmp-n", type=int, default=12, help="requests of the mixed vs plain-FP64 server comparison")
     ap.add_argument("--serve-only", action="store_true", help="run the serving section only")

@@ -189,55 +189,120 @@ __global__ void __launch_bounds__(256) plane_fft2_kernel(const double *in_r, con
     }
 }
 
-// Coulomb integral per in-plane component (thread per g), planes in z order.
-__global__ void hartree_sweep_kernel(const double2 *rg, double2 *vg, const double *zq, const double *wq, int nq,
-                                     int N1, int N2, double b1x, double b1y, double b2x, double b2y) {
+__device__ __forceinline__ double2 shfl_up2(double2 v, int d) {
+    return make_double2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ double2 shfl_down2(double2 v, int d) {
+    return make_double2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ double2 axpy2(double a, double2 x, double2 y) {
+    return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
+}
+
+// Coulomb integral per in-plane component, one warp per component g, the
+// planes (in z order) split into 32 consecutive chunks, one per lane.
+// g != 0: the forward sums L_q = f_q L_{q-1} + a_q (a = w rho, f_q =
+// e^{-g (z_q - z_{q-1})} <= 1) and the backward sums R_{q-1} = f_q (R_q + a_q)
+// are affine maps per chunk (L_out = A L_in + B, A = e^{-g (z_last - z_{first-1})}),
+// combined across the lanes by shuffle scans and then re-run with the carry:
+// V_q = (2 pi/g)(L_q + R_q).  g = 0: -2 pi sum_q' a_q' |z_q - z_q'| from the
+// prefix sums of a and a z, scanned the same way.
+__global__ void __launch_bounds__(128) hartree_sweep_kernel(const double2 *rg, double2 *vg, const double *zq,
+                                                            const double *wq, int nq, int N1, int N2, double b1x,
+                                                            double b1y, double b2x, double b2y) {
     const int NN = N1 * N2;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= NN) return;
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (e >= NN) return;                         // whole warps
     const int u = e / N2, v = e % N2;
     const int m1 = u < N1 / 2 ? u : u - N1, m2 = v < N2 / 2 ? v : v - N2;
     const double gx = m1 * b1x + m2 * b2x, gy = m1 * b1y + m2 * b2y;
     const double g = sqrt(gx * gx + gy * gy);
+    const int C = (nq + 31) / 32, q0 = min(nq, lane * C), q1 = min(nq, q0 + C);
+    auto a_at = [&](int q) {
+        const double2 r = rg[(size_t)q * NN + e];
+        return make_double2(wq[q] * r.x, wq[q] * r.y);
+    };
     if (g == 0.0) {
-        // -2 pi sum_q' w rho |z_q - z_q'| = -2 pi [z_q P_q - Pz_q + (Pz_tot - Pz_q) - z_q (P_tot - P_q)]
-        double2 PT = czero<double2>(), PzT = czero<double2>();
-        for (int q = 0; q < nq; ++q) {
-            const double2 r = rg[(size_t)q * NN + e];
-            const double wz = wq[q] * zq[q];
-            PT = make_double2(PT.x + wq[q] * r.x, PT.y + wq[q] * r.y);
-            PzT = make_double2(PzT.x + wz * r.x, PzT.y + wz * r.y);
-        }
         double2 P = czero<double2>(), Pz = czero<double2>();
-        for (int q = 0; q < nq; ++q) {
-            const double2 r = rg[(size_t)q * NN + e];
-            const double z = zq[q], wz = wq[q] * z;
-            P = make_double2(P.x + wq[q] * r.x, P.y + wq[q] * r.y);
-            Pz = make_double2(Pz.x + wz * r.x, Pz.y + wz * r.y);
+        for (int q = q0; q < q1; ++q) {
+            const double2 a = a_at(q);
+            P = P + a;
+            Pz = axpy2(zq[q], a, Pz);
+        }
+        // inclusive sums over the lanes, totals from the last lane
+        for (int d = 1; d < 32; d <<= 1) {
+            const double2 p = shfl_up2(P, d), pz = shfl_up2(Pz, d);
+            if (lane >= d) {
+                P = P + p;
+                Pz = Pz + pz;
+            }
+        }
+        const double2 PT = make_double2(__shfl_sync(0xffffffffu, P.x, 31), __shfl_sync(0xffffffffu, P.y, 31));
+        const double2 PzT = make_double2(__shfl_sync(0xffffffffu, Pz.x, 31), __shfl_sync(0xffffffffu, Pz.y, 31));
+        P = shfl_up2(P, 1);
+        Pz = shfl_up2(Pz, 1);
+        if (lane == 0) P = Pz = czero<double2>();
+        for (int q = q0; q < q1; ++q) {
+            const double2 a = a_at(q);
+            const double z = zq[q];
+            P = P + a;
+            Pz = axpy2(z, a, Pz);
             const double re = z * P.x - Pz.x + (PzT.x - Pz.x) - z * (PT.x - P.x);
             const double im = z * P.y - Pz.y + (PzT.y - Pz.y) - z * (PT.y - P.y);
             vg[(size_t)q * NN + e] = make_double2(-kTwoPi * re, -kTwoPi * im);
         }
         return;
     }
-    // L_q = sum_{q' <= q} w rho e^{-g (z_q - z_q')}, R_q = sum_{q' > q} w rho e^{-g (z_q' - z_q)}
-    double2 L = czero<double2>();
-    for (int q = 0; q < nq; ++q) {
-        const double2 r = rg[(size_t)q * NN + e];
-        const double f = q > 0 ? exp(-g * (zq[q] - zq[q - 1])) : 0.0;
-        L = make_double2(f * L.x + wq[q] * r.x, f * L.y + wq[q] * r.y);
+    auto f_at = [&](int q) { return q > 0 ? exp(-g * (zq[q] - zq[q - 1])) : 0.0; };
+    // this chunk's maps: forward L and backward R (same multiplier A)
+    double A = 1.0;
+    double2 BL = czero<double2>(), BR = czero<double2>();
+    if (q1 > q0) {
+        A = q0 > 0 ? exp(-g * (zq[q1 - 1] - zq[q0 - 1])) : 0.0;
+        for (int q = q0; q < q1; ++q) BL = axpy2(f_at(q), BL, a_at(q));
+        for (int q = q1 - 1; q >= q0; --q) {
+            const double2 a = a_at(q);
+            const double f = f_at(q);
+            BR = make_double2(f * (BR.x + a.x), f * (BR.y + a.y));
+        }
+    }
+    // forward: inclusive scan from lane 0 (earlier chunks applied first)
+    double IA = A;
+    double2 IB = BL;
+    for (int d = 1; d < 32; d <<= 1) {
+        const double pa = __shfl_up_sync(0xffffffffu, IA, d);
+        const double2 pb = shfl_up2(IB, d);
+        if (lane >= d) {
+            IB = axpy2(IA, pb, IB);
+            IA *= pa;
+        }
+    }
+    double2 L = shfl_up2(IB, 1);
+    if (lane == 0) L = czero<double2>();
+    for (int q = q0; q < q1; ++q) {
+        L = axpy2(f_at(q), L, a_at(q));
         vg[(size_t)q * NN + e] = L;
     }
+    // backward: inclusive scan from lane 31 (later chunks applied first)
+    double JA = A;
+    double2 JB = BR;
+    for (int d = 1; d < 32; d <<= 1) {
+        const double pa = __shfl_down_sync(0xffffffffu, JA, d);
+        const double2 pb = shfl_down2(JB, d);
+        if (lane + d < 32) {
+            JB = axpy2(JA, pb, JB);
+            JA *= pa;
+        }
+    }
+    double2 R = shfl_down2(JB, 1);
+    if (lane == 31) R = czero<double2>();
     const double c = kTwoPi / g;
-    double2 R = czero<double2>();
-    for (int q = nq - 1; q >= 0; --q) {
+    for (int q = q1 - 1; q >= q0; --q) {
         const double2 l = vg[(size_t)q * NN + e];
         vg[(size_t)q * NN + e] = make_double2(c * (l.x + R.x), c * (l.y + R.y));
-        if (q > 0) {
-            const double2 r = rg[(size_t)q * NN + e];
-            const double f = exp(-g * (zq[q] - zq[q - 1]));
-            R = make_double2(f * (R.x + wq[q] * r.x), f * (R.y + wq[q] * r.y));
-        }
+        const double2 a = a_at(q);
+        const double f = f_at(q);
+        R = make_double2(f * (R.x + a.x), f * (R.y + a.y));
     }
 }
 
@@ -490,8 +555,8 @@ struct ScfPlanes {
 
 static int hartree_g(mb_handle *h, const double2 *rg, double2 *vg, const ScfPlanes &pl, cudaStream_t s) {
     const int NN = h->n1 * h->n2;
-    hartree_sweep_kernel<<<(NN + 127) / 128, 128, 0, s>>>(rg, vg, pl.zq, pl.wq, h->nq, h->n1, h->n2, h->b1[0],
-                                                           h->b1[1], h->b2[0], h->b2[1]);
+    hartree_sweep_kernel<<<(NN + 3) / 4, 128, 0, s>>>(rg, vg, pl.zq, pl.wq, h->nq, h->n1, h->n2, h->b1[0],
+                                                       h->b1[1], h->b2[0], h->b2[1]);
     MB_CUDA(cudaGetLastError());
     ++h->launches;
     return MB_OK;
