@@ -384,3 +384,22 @@ def test_apply_S_and_Sinv_batched_match_oracle(mbmod, case, prec):
             tol = TOL[prec] if op == "S" else (1e-11 if prec == "fp64" else 1e-4)
             assert rel_err(Y, ref) < tol, (op, ik, rel_err(Y, ref))
     h.close()
+
+
+def test_largest_grid_radix2_fallback_and_fp64_refusal(mbmod):
+    """A 128 x 128 grid: beyond the register-FFT and compact-plane kernels,
+    the FP32 apply takes the radix-2 plane kernel (one 128 KB plane in shared
+    memory) and matches the oracle; an FP64 plane (256 KB) does not fit in
+    shared memory, and the FP64 apply is refused with MB_EUNSUPPORTED instead
+    of launching."""
+    w = dataclasses.replace(W.tiny(), grid=(128, 128), nbands=3, name="tiny-128")
+    h = mbmod.Handle.from_workload(w)
+    ng, nb, ldg = h.sizes(0)
+    X = W.random_block(w.nbands, nb, ng, seed=21)
+    m, Y = _run_apply(mbmod, h, w, 0, X, "fp32")
+    assert rel_err(Y, m.apply_H(X)) < TOL["fp32"]
+    Xd = torch.zeros((w.nbands, nb, ldg), dtype=torch.complex128, device="cuda")
+    with pytest.raises(mbmod.MBError) as e:
+        h.apply_H(0, Xd, torch.zeros_like(Xd), "fp64")
+    assert e.value.code == 6
+    h.close()
