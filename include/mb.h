@@ -309,7 +309,9 @@ typedef struct {
     int pulay_depth;      /* steps Pulay combines, at most 8 (0: 4; 1: Kerker alone) */
     double tol;           /* stop when max |change of V_H + V_xc| < tol (Ha) */
     int max_iter;         /* eigensolves at most (0: 60) */
-    double eig_tol;       /* residual tolerance of each eigensolve (0: tol / 10) */
+    double eig_tol;       /* residual tolerance of the eigensolves (0: tol / 10); while the
+                             potential still changes by dv, an iteration solves to
+                             max(eig_tol, min(dv / 10, 1e-3)) */
     int prec;             /* MB_FP64 or MB_FP32 (mixed-precision eigensolves) */
     const double *kweights; /* host, nk weights summing to 1 (NULL: uniform) */
 } mb_scf_opts;

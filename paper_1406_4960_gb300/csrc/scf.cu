@@ -889,7 +889,11 @@ int mb_scf(mb_handle *h, const mb_scf_opts *o, double *evals, double *rho_out, m
             mb_solve_info si{};
             mb_solve_opts so{};
             so.warm_start = it > 1;          // from the roots of the previous potential
-            rc = mb_eigsolve(h, nbands, eig_tol, o->prec, ev.data(), evecs, &so, &si, s);
+            // while the potential still moves by dv, roots more accurate than
+            // about dv / 10 buy nothing: the tolerance follows dv down to
+            // eig_tol (reached once dv < tol, so the final roots are exact to it)
+            const double tol_it = std::min(std::max(eig_tol, 1e-3), std::max(eig_tol, 0.1 * dv));
+            rc = mb_eigsolve(h, nbands, tol_it, o->prec, ev.data(), evecs, &so, &si, s);
             cycles += si.cycles;
             auto t2 = clk::now();
             t_eig += std::chrono::duration<double>(t2 - t1).count();
