@@ -149,3 +149,32 @@ def test_scf_matches_oracle(mbmod, prec):
     assert np.abs(vscf - ref["vscf"]).max() < 1e-6 * max(1.0, np.abs(ref["vscf"]).max())
     assert abs(info.nelec - 2.0) < 1e-8
     h.close()
+
+
+def test_scf_with_kpoint_weights_matches_oracle(mbmod):
+    """Non-uniform k-point weights (3/4 and 1/4) enter the occupations."""
+    w = _cell(nk=2)
+    kw = np.array([0.75, 0.25])
+    ref = F.scf(w, nbands=4, nelec=2.0, sigma=0.02, W=0.5, gmax=1.0, tol=1e-8, max_iter=80, kweights=kw)
+    h = mbmod.Handle.from_workload(w)
+    ev, info = h.scf(4, 1e-8, 0.02, nelec=2.0, mix_weight=0.5, g_max=1.0, max_iter=80, eig_tol=1e-9, prec="fp64",
+                     kweights=kw)
+    assert info.dv < 1e-8
+    assert np.abs(ev - ref["evals"]).max() < 1e-6
+    h.close()
+
+
+def test_scf_rejects_bad_options(mbmod):
+    """Invalid requests return MB_EINVAL before any work: no width, no
+    tolerance, more electrons than the bands hold, weights not summing to 1,
+    an unknown precision."""
+    w = _cell(nk=2)
+    h = mbmod.Handle.from_workload(w)
+    bad = [dict(sigma=0.0), dict(tol=0.0), dict(nelec=9.0), dict(kweights=[0.5, 0.4]), dict(prec="bf16")]
+    for b in bad:
+        kw = dict(nbands=4, tol=1e-6, sigma=0.02, nelec=2.0)
+        kw.update(b)
+        with pytest.raises(mbmod.MBError) as e:
+            h.scf(kw.pop("nbands"), kw.pop("tol"), kw.pop("sigma"), max_iter=3, **kw)
+        assert e.value.code == 1, b
+    h.close()
