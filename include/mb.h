@@ -337,7 +337,9 @@ typedef struct {
  * less than tol (§III.A's criterion).  evals: host nk*nbands, the roots of
  * the final potential; rho_out: optional device field, the final input
  * density.  The handle's local potential holds the final total potential on
- * return.  MB_ENOTCONV when max_iter is reached (evals still written). */
+ * return (and, with ultrasoft atoms, its projector strengths the final D);
+ * its later applies and eigensolves use them.  MB_ENOTCONV when max_iter is
+ * reached (evals still written). */
 int mb_scf(mb_handle *h, const mb_scf_opts *opts, double *evals, double *rho_out, mb_scf_info *info);
 
 /* ---- launch-shape autotuner -------------------------------------------
