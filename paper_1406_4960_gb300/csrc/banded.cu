@@ -159,13 +159,13 @@ static size_t band_smem(const mb_handle *h, size_t c2, int cw, bool inv) {
 bool banded_block_supported(const mb_handle *h, int prec, bool inv) {
     if (h->order != 6) return false;
     const size_t c2 = prec == MB_FP64 ? 16 : 8;
-    return band_smem(h, c2, prec == MB_FP64 ? 32 : 64, inv) > 0 && h->nb >= 4;
+    return band_smem(h, c2, 32, inv) > 0 && h->nb >= 4;
 }
 
 template <typename R, bool INV>
 static int launch_band(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y, int nbands,
                        cudaStream_t s) {
-    constexpr int CW = sizeof(R) == 4 ? 64 : 32;
+    constexpr int CW = 32;   // columns per tile (FP32 and FP64)
     const DevTables &t = sizeof(R) == 4 ? h->t32 : h->t64;
     BandArgs<R> a;
     a.coef = reinterpret_cast<const R *>(INV ? t.Lrecip : t.Sband);
