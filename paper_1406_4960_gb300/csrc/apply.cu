@@ -851,6 +851,22 @@ static int wave_model_chunks(const mb_handle *h, int pairs, int slots, int nmax_
     return nch;
 }
 
+// Shared memory of a compact-plane instance at its CTAs per SM: planes,
+// output-row ring (and X window slots), and the B values of a run of
+// intervals; runs as short as the plan allows (K intervals) must fit.
+static size_t p32_budget(const mb_handle *h, const Plane32Shape &sh) {
+    return std::min((size_t)h->smem_optin, (size_t)228 * 1024 / sh.ctas_per_sm - 1024);
+}
+static size_t p32_smem(const mb_handle *h, const Plane32Shape &sh, int maxldg, int nch) {
+    const int K = h->order, P = h->nquad;
+    return sh.smem_fixed + (size_t)sh.bt * K * maxldg * sizeof(float2) +
+           (size_t)((h->nint + nch - 1) / nch) * K * P * sizeof(float);
+}
+static bool p32_fits(const mb_handle *h, const Plane32Shape &sh, int maxldg) {
+    const int nmax_chunks = std::max(1, std::min(kMaxChunks, h->nint / h->order));
+    return p32_smem(h, sh, maxldg, nmax_chunks) <= p32_budget(h, sh);
+}
+
 static PlanePlan plan_plane(const mb_handle *h, int nsel, const int *iks, int nbands, size_t c2, bool reg_ok) {
     PlanePlan p;
     const int K = h->order, P = h->nquad;
@@ -884,10 +900,9 @@ static PlanePlan plan_plane(const mb_handle *h, int nsel, const int *iks, int nb
                 if (pass == 0 && sh.id != p32_id) continue;
                 const int pairs = nsel * ((nbands + sh.bt - 1) / sh.bt);
                 const int slots = h->num_sms * sh.ctas_per_sm;
-                const size_t budget = std::min((size_t)h->smem_optin, (size_t)228 * 1024 / sh.ctas_per_sm - 1024);
-                const size_t base = sh.smem_fixed + (size_t)sh.bt * K * maxldg * sizeof(float2);
+                const size_t budget = p32_budget(h, sh);
                 int nch = wave_model_chunks(h, pairs, slots, nmax_chunks, waves);
-                auto smem_of = [&](int n) { return base + (size_t)((h->nint + n - 1) / n) * K * P * sizeof(float); };
+                auto smem_of = [&](int n) { return p32_smem(h, sh, maxldg, n); };
                 while (nch < nmax_chunks && smem_of(nch) > budget) ++nch;
                 if (smem_of(nch) > budget) continue;
                 p.p32 = true;
@@ -1680,8 +1695,13 @@ static int plane_candidates(const mb_handle *h, int nk, int prec, int *ids, int 
     }
     Plane32Shape shapes[kMaxPlane32Shapes];
     const int ns = plane32_shapes(h->n1, h->n2, h->order, h->nquad, nocc_max, maxldg, shapes, kMaxPlane32Shapes);
-    for (int v = 0; v < ns && v < max; ++v) ids[v] = shapes[v].id;
-    return ns;
+    int n = 0;   // the instances whose shared memory fits this batch
+    for (int v = 0; v < ns; ++v)
+        if (p32_fits(h, shapes[v], maxldg)) {
+            if (n < max) ids[n] = shapes[v].id;
+            ++n;
+        }
+    return n;
 }
 }  // namespace mb
 
