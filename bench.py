@@ -461,6 +461,18 @@ def scf_bench(mb, W, local, args):
                          "eig_cycles": info.eig_cycles, "dv_ha": info.dv, "fermi_ha": info.mu,
                          "nelec": info.nelec, "lowest_ha": float(ev.min())}
     h.close()
+    # the 4x4 graphene cell with the same core charges (128 electrons in 80 bands)
+    wg = W.with_core(W.graphene(), SCF_Z, SCF_RCORE, name="graphene-scf")
+    h = mb.Handle.from_workload(wg, device=local)
+    evg, infog = h.scf(wg.nbands, SCF_TOL, SCF_SIGMA, mix_weight=SCF_W, g_max=SCF_GMAX, prec="fp32",
+                       eig_tol=SCF_TOL / 5, max_iter=80, allow_notconv=True)
+    out["graphene_mixed"] = {"workload": "graphene 4x4 (1417 G, 64x64 grid, 80 B-splines) with Z = %g core "
+                                         "charges on its 32 atoms: 128 electrons in 80 bands" % SCF_Z,
+                             "converged": bool(infog.dv < SCF_TOL), "iterations": infog.iterations,
+                             "seconds": infog.seconds, "seconds_eig": infog.seconds_eig,
+                             "seconds_density": infog.seconds_density, "eig_cycles": infog.eig_cycles,
+                             "dv_ha": infog.dv, "fermi_ha": infog.mu, "nelec": infog.nelec}
+    h.close()
     return out
 
 
