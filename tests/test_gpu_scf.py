@@ -178,3 +178,31 @@ def test_scf_rejects_bad_options(mbmod):
             h.scf(kw.pop("nbands"), kw.pop("tol"), kw.pop("sigma"), max_iter=3, **kw)
         assert e.value.code == 1, b
     h.close()
+
+
+def test_density_of_more_kpoints_than_one_launch_holds(mbmod):
+    """40 k-points (the density launches take 32 at a time) with random
+    coefficient blocks: the chunked launches and the fixed-order partial sum
+    against the oracle."""
+    rng = np.random.default_rng(12)
+    w = _cell(nk=1)
+    kpts = rng.uniform(-0.4, 0.4, (40, 2))
+    import dataclasses
+    w = dataclasses.replace(w, kpts=kpts)
+    h = mbmod.Handle.from_workload(w)
+    nbands = 2
+    models, coefs, blocks = [], [], []
+    occ = rng.random((w.nk, nbands))
+    for ik in range(w.nk):
+        m = Hm.model_from_workload(w, ik)
+        C = W.random_block(nbands, m.nb, m.ng, seed=600 + ik)
+        models.append(m)
+        coefs.append(C)
+        ng, nb, ldg = h.sizes(ik)
+        blocks.append(lib_block(C, gmap(h, m, ik), ldg, np.complex128).ravel())
+    evecs = torch.from_numpy(np.concatenate(blocks)).cuda()
+    rho = _field(h)
+    h.density(evecs, nbands, occ, rho)
+    ref = F.density(models, coefs, occ)
+    assert _rel(rho.cpu().numpy(), ref) < FIELD_TOL
+    h.close()
