@@ -158,7 +158,8 @@ int mb_set_local_potential(mb_handle *h, const double *V);
  * over the grid frequencies m in [-n/2, n/2) per axis, c the sum over atoms
  * of each term's in-plane component times exp(-i g_m . pos_par) -- Eq. (13)
  * for the Gaussian, the Coulomb integral of §II.B.1 of the Gaussian core
- * charge for the core term (see mb_atom).  Blocks until the copy is done. */
+ * charge for the core term (see mb_atom).  Blocks until the copy is done.
+ * Errors: MB_EINVAL (NULL arguments), MB_ECUDA. */
 int mb_local_potential(mb_handle *h, double *V);
 
 /* Y = H X at k-point ik (§II.B.1: kinetic Eq. (9), local potential through
@@ -278,7 +279,9 @@ int mb_eigsolve(mb_handle *h, int nbands, double tol, int prec, double *evals,
  * vectors [band][j][ldg]) with occupations occ (host, nk*nbands, spin and
  * k-point weight included); phi is the basis expansion of Eq. (6) with
  * A = A_c.  FP64; deterministic (partials summed in a fixed order).  The
- * caller's stream is synchronized before return (occ is read from the host). */
+ * caller's stream is synchronized before return (occ is read from the host).
+ * Errors: MB_EINVAL (NULL pointers, nbands < 1), MB_EUNSUPPORTED (a grid
+ * whose FP64 plane does not fit in shared memory), MB_ECUDA. */
 int mb_density(mb_handle *h, const void *evecs, int nbands, const double *occ, double *rho, void *stream);
 
 /* Coulomb potential of an electron density, V_H(r) = int rho(r')/|r - r'|,
@@ -288,7 +291,7 @@ int mb_density(mb_handle *h, const void *evecs, int nbands, const double *occ, d
  * divergence (2 pi/g) x net charge is dropped, keeping
  * -2 pi int dz' rho(z', 0) |z - z'| (with the atoms' core terms, which drop
  * theirs, a neutral cell loses nothing).  rho and vh: device fields.  The
- * stream is synchronized before return. */
+ * stream is synchronized before return.  Errors as mb_density's. */
 int mb_hartree(mb_handle *h, const double *rho, double *vh, void *stream);
 
 /* LDA exchange-correlation potential v_xc and energy per electron exc
@@ -297,7 +300,8 @@ int mb_hartree(mb_handle *h, const double *rho, double *vh, void *stream);
  * B 23, 5048 (1981)), spin-unpolarized, evaluated at max(rho, 1e-10 bohr^-3)
  * (in the vacuum the density falls below what FP64 sums and converged
  * eigenvectors resolve; there the potential is the small constant of the
- * floor).  Device fields; asynchronous on the stream. */
+ * floor).  Device fields; asynchronous on the stream.  Errors: MB_EINVAL
+ * (NULL rho or vxc), MB_ECUDA. */
 int mb_xc_lda(mb_handle *h, const double *rho, double *vxc, double *exc, void *stream);
 
 typedef struct {
@@ -338,8 +342,11 @@ typedef struct {
  * the final potential; rho_out: optional device field, the final input
  * density.  The handle's local potential holds the final total potential on
  * return (and, with ultrasoft atoms, its projector strengths the final D);
- * its later applies and eigensolves use them.  MB_ENOTCONV when max_iter is
- * reached (evals still written). */
+ * its later applies and eigensolves use them.  Errors: MB_EINVAL (nbands < 1,
+ * sigma or tol not positive, a precision other than MB_FP64 / MB_FP32, no
+ * electrons or more than 2 nbands of them, weights not summing to 1),
+ * MB_ENOTCONV when max_iter is reached (evals still written), the errors of
+ * mb_eigsolve and mb_density. */
 int mb_scf(mb_handle *h, const mb_scf_opts *opts, double *evals, double *rho_out, mb_scf_info *info);
 
 /* ---- launch-shape autotuner -------------------------------------------
