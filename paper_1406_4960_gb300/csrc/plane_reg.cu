@@ -6,8 +6,9 @@
 // for throughput:
 //  * every 1D transform of N <= 64 points runs inside one thread's registers
 //    (radix-2, bit reversal by register renaming, trivial twiddles folded at
-//    compile time), so a plane crosses shared memory three times per
-//    direction instead of once per butterfly stage;
+//    compile time, six fused multiply-adds per butterfly with a nontrivial
+//    twiddle), so a plane crosses shared memory three times per direction
+//    instead of once per butterfly stage;
 //  * planes are stored with rows padded to N2 + 1 so that row-wise and
 //    column-wise line loads are both free of bank conflicts;
 //  * the inverse column transform, the potential product and the forward
@@ -25,24 +26,38 @@
 
 namespace mb {
 
-__constant__ float2 c_twf[64];    // exp(+2 pi i k / 64)
-__constant__ double2 c_twd[64];
+// Twiddles of the in-register transforms, in the scaled form of the radix-2
+// butterfly with fused multiply-adds (Linzer & Feig, 1993): the twiddle
+// w = cos a + i sin a of angle a = 2 pi k / 64 is stored as w = c (1 + i r)
+// with (c, r) = (cos a, tan a) where |cos a| >= |sin a|, else as
+// w = c (r + i) with (c, r) = (sin a, cot a).  Then a +- w b costs two fused
+// multiply-adds for t = b (1 + i r) (or b (r + i)) and four for a +- c t:
+// six per butterfly instead of eight for a complex product and two complex
+// additions, with |r| <= 1 so that no term is amplified.
+__constant__ float2 c_tsf[64];
+__constant__ double2 c_tsd[64];
+
+constexpr bool tw_tan_form(int k) { return (k % 32) <= 8 || (k % 32) >= 24; }
 
 void upload_fft_twiddles() {
     float2 tf[64];
     double2 td[64];
     for (int k = 0; k < 64; ++k) {
-        double a = 2.0 * 3.14159265358979323846 * k / 64.0;
-        td[k] = make_double2(std::cos(a), std::sin(a));
+        const double a = 2.0 * 3.14159265358979323846 * k / 64.0;
+        const double c = std::cos(a), s = std::sin(a);
+        td[k] = tw_tan_form(k) ? make_double2(c, s / c) : make_double2(s, c / s);
         tf[k] = make_float2((float)td[k].x, (float)td[k].y);
     }
-    cudaMemcpyToSymbol(c_twf, tf, sizeof(tf));
-    cudaMemcpyToSymbol(c_twd, td, sizeof(td));
+    cudaMemcpyToSymbol(c_tsf, tf, sizeof(tf));
+    cudaMemcpyToSymbol(c_tsd, td, sizeof(td));
 }
 
-template <typename C> __device__ __forceinline__ C ctw(int k);
-template <> __device__ __forceinline__ float2 ctw<float2>(int k) { return c_twf[k]; }
-template <> __device__ __forceinline__ double2 ctw<double2>(int k) { return c_twd[k]; }
+template <typename C> __device__ __forceinline__ C ctws(int k);
+template <> __device__ __forceinline__ float2 ctws<float2>(int k) { return c_tsf[k]; }
+template <> __device__ __forceinline__ double2 ctws<double2>(int k) { return c_tsd[k]; }
+
+__device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmar(double a, double b, double c) { return fma(a, b, c); }
 
 constexpr int brev_c(int x, int bits) {
     int r = 0;
@@ -51,18 +66,80 @@ constexpr int brev_c(int x, int bits) {
 }
 constexpr int ilog2_c(int n) { return n <= 1 ? 0 : 1 + ilog2_c(n / 2); }
 
-// b * exp(sign 2 pi i tk / N), sign = + for the inverse transform
+// (a, b) <- (a + w b, a - w b), w = exp(sign 2 pi i tk / N), sign = + for the
+// inverse transform (the forward twiddle is the conjugate: r and, in the
+// cot form, c change sign)
 template <int N, bool INV, typename C>
-__device__ __forceinline__ C twmul(C b, int tk) {
-    if (tk == 0) return b;
-    if (4 * tk == N) return INV ? mk(-b.y, b.x) : mk(b.y, -b.x);
-    C w = ctw<C>(tk * (64 / N));
-    if (!INV) w.y = -w.y;
-    return cmul(b, w);
+__device__ __forceinline__ void bfly(C &a, C &b, int tk) {
+    const C u = a;
+    if (tk == 0) {
+        a = u + b;
+        b = u - b;
+        return;
+    }
+    if (4 * tk == N) {
+        const C wb = INV ? mk(-b.y, b.x) : mk(b.y, -b.x);
+        a = u + wb;
+        b = u - wb;
+        return;
+    }
+    const int k = tk * (64 / N);
+    const C q = ctws<C>(k);
+    auto c = q.x, r = q.y;
+    const bool tan_form = tw_tan_form(k);
+    if (!INV) {
+        r = -r;
+        if (!tan_form) c = -c;
+    }
+    C t;
+    if (tan_form) {
+        t.x = fmar(-r, b.y, b.x);
+        t.y = fmar(r, b.x, b.y);
+    } else {
+        t.x = fmar(r, b.x, -b.y);
+        t.y = fmar(r, b.y, b.x);
+    }
+    a.x = fmar(c, t.x, u.x);
+    a.y = fmar(c, t.y, u.y);
+    b.x = fmar(-c, t.x, u.x);
+    b.y = fmar(-c, t.y, u.y);
 }
 
-// in-register radix-2 FFT of N points (natural order in and out)
-template <int N, bool INV, typename C>
+// true when every input index that reaches positions [p, p + len) of the
+// bit-reversed array is >= nin (those positions hold zeros until the stage
+// that merges them with a lower block)
+constexpr bool zero_block(int p, int len, int bits, int nin) {
+    for (int i = p; i < p + len; ++i)
+        if (brev_c(i, bits) < nin) return false;
+    return true;
+}
+// bit q: the lower half of butterfly group q of the stage of half-width
+// `half` is all zeros
+constexpr unsigned long long stage_zero_mask(int n, int half, int bits, int nin) {
+    unsigned long long m = 0;
+    for (int g = 0; g < n; g += 2 * half)
+        if (nin < n && zero_block(g + half, half, bits, nin)) m |= 1ull << (g / (2 * half));
+    return m;
+}
+
+template <int N, bool INV, int NIN, int HALF, typename C>
+__device__ __forceinline__ void fft_stages(C (&x)[N]) {
+    constexpr unsigned long long zm = stage_zero_mask(N, HALF, ilog2_c(N), NIN);
+#pragma unroll
+    for (int g = 0; g < N; g += 2 * HALF) {
+#pragma unroll
+        for (int j = 0; j < HALF; ++j) {
+            if ((zm >> (g / (2 * HALF))) & 1) x[g + j + HALF] = x[g + j];
+            else bfly<N, INV>(x[g + j], x[g + j + HALF], j * (N / (2 * HALF)));
+        }
+    }
+    if constexpr (2 * HALF < N) fft_stages<N, INV, NIN, 2 * HALF>(x);
+}
+
+// in-register radix-2 FFT of N points (natural order in and out); inputs
+// NIN .. N-1 are known to be zero, and the butterflies whose lower operand
+// is still all zeros become copies (a + w 0 = a - w 0 = a)
+template <int N, bool INV, int NIN = N, typename C>
 __device__ __forceinline__ void fft_reg(C (&x)[N]) {
     constexpr int L = ilog2_c(N);
 #pragma unroll
@@ -74,19 +151,7 @@ __device__ __forceinline__ void fft_reg(C (&x)[N]) {
             x[j] = t;
         }
     }
-#pragma unroll
-    for (int half = 1; half < N; half *= 2) {
-#pragma unroll
-        for (int g = 0; g < N; g += 2 * half) {
-#pragma unroll
-            for (int j = 0; j < half; ++j) {
-                C b = twmul<N, INV>(x[g + j + half], j * (N / (2 * half)));
-                C a = x[g + j];
-                x[g + j] = a + b;
-                x[g + j + half] = a - b;
-            }
-        }
-    }
+    fft_stages<N, INV, NIN, 1>(x);
 }
 
 // CTA shape: FP32 planes of 16 columns, and 32 x 32 FP32 planes, use 192
@@ -524,7 +589,7 @@ __device__ __forceinline__ void plane32_item(const PlaneArgs<float> &a, const in
             float2 v[N1];
 #pragma unroll
             for (int i = 0; i < N1; ++i) v[i] = (i < NOCC && i < nocc) ? line[i * LDP] : make_float2(0.f, 0.f);
-            fft_reg<N1, true>(v);
+            fft_reg<N1, true, (NOCC < N1 ? NOCC : N1)>(v);
             if constexpr (VPRE) {
 #pragma unroll
                 for (int i = 0; i < N1; ++i) v[i] = rscale(vv[i], v[i]);
