@@ -214,11 +214,11 @@ int mb_apply_Sinv(mb_handle *h, int ik, const void *X, void *Y, int nbands,
                   int prec, void *stream);
 
 /* S X and S^-1 X for several k-points in one launch: X[i], Y[i] are the
- * blocks of k-point iks[i] (host arrays of nsel distinct device pointers).
- * For B-splines of order 6 each (k-point, band, 64-column) tile of X is
- * brought into shared memory by TMA bulk copies; if their bounded wait
- * expires the tile's output is not written and mb_status reports
- * MB_ETIMEOUT. */
+ * blocks of k-point iks[i] (host arrays of nsel distinct device pointers;
+ * X[i] and Y[i] must not overlap).  Each (k-point, band, 32-column) tile of
+ * X -- for S, a run of 32 rows of it and its halo -- is brought into shared
+ * memory by TMA bulk copies; if their bounded wait expires the tile's output
+ * is not written and mb_status reports MB_ETIMEOUT. */
 int mb_apply_S_batch(mb_handle *h, int nsel, const int *iks, const void *const *X,
                      void *const *Y, int nbands, int prec, void *stream);
 int mb_apply_Sinv_batch(mb_handle *h, int nsel, const int *iks, const void *const *X,

@@ -609,6 +609,13 @@ static int upload_set(mb_handle *h, DevTables &t) {
     int rc;
     if ((rc = upload<R>(h, &t.Bq, h->Bq))) return rc;
     if ((rc = upload<R>(h, &t.Sband, h->Sb))) return rc;
+    {
+        const int W = 2 * h->order - 1, WP = band_pad(h->order);
+        std::vector<double> sp((size_t)h->nb * WP, 0.0);
+        for (int j = 0; j < h->nb; ++j)
+            for (int d = 0; d < W; ++d) sp[(size_t)j * WP + d] = h->Sb[(size_t)j * W + d];
+        if ((rc = upload<R>(h, &t.SbandP, sp))) return rc;
+    }
     if ((rc = upload<R>(h, &t.Dband, h->Db))) return rc;
     if ((rc = upload<R>(h, &t.Lband, h->Lb))) return rc;
     {
@@ -766,7 +773,7 @@ int ensure_precond(mb_handle *h) {
 }
 
 static void free_set(mb_handle *h, DevTables &t) {
-    void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.Dband, &t.Lband, &t.Lrecip, &t.q2, &t.qproj, &t.zproj, &t.zf, &t.E, &t.Pfac, &t.Vt, &t.Q, &t.Eid};
+    void **ps[] = {&t.Bq, &t.V, &t.Vn, &t.tw, &t.Sband, &t.SbandP, &t.Dband, &t.Lband, &t.Lrecip, &t.q2, &t.qproj, &t.zproj, &t.zf, &t.E, &t.Pfac, &t.Vt, &t.Q, &t.Eid};
     for (void **p : ps) dev_free(h, p);
 }
 
@@ -1486,10 +1493,6 @@ int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X, 
     }
     return MB_OK;
 }
-
-int banded_block_apply(mb_handle *h, bool inv, int nsel, const int *iks, const void *const *X, void *const *Y,
-                       int nbands, int prec, cudaStream_t s);
-bool banded_block_supported(const mb_handle *h, int prec, bool inv);
 
 int apply_banded_batch(mb_handle *h, int which, int nsel, const int *iks, const void *const *X, void *const *Y,
                        int nbands, int prec, cudaStream_t s) {

@@ -767,33 +767,7 @@ __global__ void take_evals_kernel(const double *evals, int M, int nk, double *ep
     if (e < M * nk) eps[e] = evals[(size_t)(e / M) * LD + (e % M)];
 }
 
-// banded S and banded solves on vector ranges of every k-point (FP64)
-// S apply: one thread per (vector, j, G).
-// F32: on the FP32 copies with the FP32 band (the bulk cycles).
-template <int K, bool F32>
-__global__ void eig_banded_S_kernel(const EigK *ks, const void *Sbv, int nb, int src, int dst, int nv) {
-    typedef typename std::conditional<F32, float2, double2>::type T2;
-    typedef typename std::conditional<F32, float, double>::type T;
-    const int k = blockIdx.z / nv, v = blockIdx.z % nv, j = blockIdx.y;
-    const EigK d = ks[k];
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= d.ldg) return;
-    constexpr int W = 2 * K - 1;
-    const T *Sband = reinterpret_cast<const T *>(Sbv);
-    T2 *vb = F32 ? reinterpret_cast<T2 *>(d.v32) : reinterpret_cast<T2 *>(d.base);
-    const T2 *x = vb + (long long)(src + v) * d.nvec;
-    T2 *y = vb + (long long)(dst + v) * d.nvec;
-    T2 s = czero<T2>();
-    if (g < d.ng) {
-#pragma unroll
-        for (int dd = 0; dd < W; ++dd) {
-            const int jj = j + dd - (K - 1);
-            if (jj >= 0 && jj < nb) rfma(s, __ldg(&Sband[(size_t)j * W + dd]), x[(size_t)jj * d.ldg + g]);
-        }
-    }
-    y[(size_t)j * d.ldg + g] = s;
-}
-
+// banded solves on vector ranges of every k-point (FP64)
 // L L^T y = x, one thread per (vector, G) column; the last K-1 solution values
 // ride in registers.  per_g: the k-point's factors L_G[j][d] stored as
 // pfac[(j*K + d)*ldg + G] (coalesced over G); else the G-independent L_z.
@@ -1763,36 +1737,24 @@ struct Solver {
     // S X: the banded S_0 of Eqs. (7)-(8) and, for ultrasoft atoms, the
     // augmentation term sum q |beta><beta| X (§II.B.2)
     void bandS(int src, int dst, int nv, bool f32 = false) {
-        const dim3 grid((maxldg + 127) / 128, h->nb, nk * nv);
-        const void *Sb = f32 ? h->t32.Sband : h->t64.Sband;
-        switch (h->order) {
-#define MB_BS(KK)                                                                                                 \
-    case KK:                                                                                                      \
-        if (f32)                                                                                                  \
-            MB_LAUNCH_E(KN_BANDED, (eig_banded_S_kernel<KK, true><<<grid, 128, 0, s>>>(d_k, Sb, h->nb, src, dst, nv))); \
-        else                                                                                                      \
-            MB_LAUNCH_E(KN_BANDED, (eig_banded_S_kernel<KK, false><<<grid, 128, 0, s>>>(d_k, Sb, h->nb, src, dst, nv))); \
-        break;
-            MB_BS(3) MB_BS(4) MB_BS(5) MB_BS(6) MB_BS(7) MB_BS(8)
-#undef MB_BS
-        }
-        if (h->uspp && !rc) {
-            std::vector<int> iks(nk);
-            std::vector<const void *> xs(nk);
-            std::vector<void *> ys(nk);
-            for (int k = 0; k < nk; ++k) {
-                iks[k] = k;
-                if (f32) {
-                    xs[k] = kd_host[k].v32 + (long long)src * kd_host[k].nvec;
-                    ys[k] = kd_host[k].v32 + (long long)dst * kd_host[k].nvec;
-                } else {
-                    xs[k] = kd_host[k].base + (long long)src * kd_host[k].nvec;
-                    ys[k] = kd_host[k].base + (long long)dst * kd_host[k].nvec;
-                }
+        if (rc) return;
+        std::vector<int> iks(nk);
+        std::vector<const void *> xs(nk);
+        std::vector<void *> ys(nk);
+        for (int k = 0; k < nk; ++k) {
+            iks[k] = k;
+            if (f32) {
+                xs[k] = kd_host[k].v32 + (long long)src * kd_host[k].nvec;
+                ys[k] = kd_host[k].v32 + (long long)dst * kd_host[k].nvec;
+            } else {
+                xs[k] = kd_host[k].base + (long long)src * kd_host[k].nvec;
+                ys[k] = kd_host[k].base + (long long)dst * kd_host[k].nvec;
             }
-            const int r = uspp_S_add(h, nk, iks.data(), xs.data(), ys.data(), nv, f32 ? MB_FP32 : MB_FP64, s);
-            if (r && rc == MB_OK) rc = r;
         }
+        const int prec = f32 ? MB_FP32 : MB_FP64;
+        int r = banded_block_apply(h, false, nk, iks.data(), xs.data(), ys.data(), nv, prec, s);
+        if (r == MB_OK && h->uspp) r = uspp_S_add(h, nk, iks.data(), xs.data(), ys.data(), nv, prec, s);
+        if (r && rc == MB_OK) rc = r;
     }
     void coldot(int nch, VSet A, VSet B, double *out, bool f32 = false) {
         const dim3 grid(A.count(), nk * nch);

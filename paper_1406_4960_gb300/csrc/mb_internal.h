@@ -26,6 +26,10 @@ struct KPoint {
     std::vector<cdouble> qproj;     // nterm x ldg in-plane projector factors
 };
 
+// entries of a padded row of the S band: 2 order - 1 rounded up to a multiple
+// of 4, so that a row is a whole number of 16-byte loads in both precisions
+constexpr int band_pad(int order) { return (2 * order - 1 + 3) / 4 * 4; }
+
 // Device copies of one precision (R = double or float).
 struct DevTables {
     void *Bq = nullptr;      // nq x order, B_{t+m}(z_q) of the full basis
@@ -33,6 +37,7 @@ struct DevTables {
     void *Vn = nullptr;      // the same in natural layout
     void *tw = nullptr;      // Nmax/2 complex, exp(+2 pi i k / Nmax)
     void *Sband = nullptr;   // nb x (2 order - 1): S[j][j+d], d = -(order-1)..order-1
+    void *SbandP = nullptr;  // the same with rows padded to band_pad(order) entries (zeros)
     void *Dband = nullptr;   // same layout for D = <B'|B'>
     void *Lband = nullptr;   // nb x order: Cholesky L[j][j-d], d = 0..order-1
     void *Lrecip = nullptr;  // the same with 1 / L[j][j] at d = 0 (eigensolver's solves)
@@ -167,6 +172,12 @@ int vloc_tabulate(mb_handle *h, int mode, double *out, cudaStream_t s, const std
                   const std::vector<double> *lion = nullptr, const std::vector<int> *lstart = nullptr);
 // 0: V(r, z_q); 1: core charge density (of the given groups instead of the atoms', when passed)
 // apply.cu: the ultrasoft overlap term Y += sum q_pq beta_p (beta_q^H X) (§II.B.2)
+// S_0 X (inv = false) or S_0^-1 X (inv = true) for the blocks X[i] -> Y[i] of
+// k-points iks[i] (nbands vectors at stride nb * ldg, X[i] != Y[i]); one launch
+// per kMaxK k-points
+int banded_block_apply(mb_handle *h, bool inv, int nsel, const int *iks, const void *const *X, void *const *Y,
+                       int nbands, int prec, cudaStream_t s);
+bool banded_block_supported(const mb_handle *h, int prec, bool inv);
 int uspp_S_add(mb_handle *h, int nsel, const int *iks, const void *const *X, void *const *Y, int nbands, int prec,
                cudaStream_t s);
 size_t uspp_scratch_bytes(const mb_handle *h, int nk, int nbands, int prec);

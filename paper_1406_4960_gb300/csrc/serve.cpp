@@ -55,7 +55,8 @@ size_t footprint_of(const mb_handle &h, int nbands, int prec) {
     // V: the natural FP64 table, permuted + natural (FP64 + FP32), per column
     // (FP32); the transient buffers of its build
     size_t tables = (size_t)h.nq * NN * (8 + (8 + 4) * 2 + 4) + vloc_build_scratch_bytes(&h);
-    tables += (size_t)h.nq * h.order * 12 + (size_t)h.nb * (2 * h.order - 1) * 12 * 2 + (size_t)h.nb * h.order * 12;
+    tables += (size_t)h.nq * h.order * 12 + (size_t)h.nb * (2 * h.order - 1) * 12 * 2 + (size_t)h.nb * h.order * 12 +
+              (size_t)h.nb * band_pad(h.order) * 12;   // the padded S band
     size_t vec_bytes = 0, pf = 0;
     int maxldg = 0;
     for (auto &k : h.kp) {
