@@ -60,7 +60,8 @@ def _small_slab_2s():
 
 def _order(w, k):
     # B-splines of order k with k Gauss points per interval: every order other
-    # than 6 takes the radix-2 plane kernel and the order-k banded kernels
+    # than 6 takes the radix-2 plane kernel, the order-k epilogue and S kernel
+    # and the per-k-point S^-1 kernel
     return dataclasses.replace(w, order=k, nquad=k, name="%s-k%d" % (w.name, k))
 
 
@@ -351,12 +352,13 @@ def test_every_plane_kernel_instance_matches_oracle(mbmod, case):
     h.close()
 
 
-@pytest.mark.parametrize("case", ["slab", "slab-small", "slab-small-k4", "graphene-small"])
+@pytest.mark.parametrize("case", ["slab", "slab-small", "slab-small-k4", "graphene-small", "tiny-k8"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_apply_S_and_Sinv_batched_match_oracle(mbmod, case, prec):
-    """S X and S^-1 X for every k-point in one batched call (order 6: the
-    TMA-staged tile kernel; order 4: the per-k-point kernels) against the
-    oracle's S and a dense inverse of it, every element."""
+    """S X and S^-1 X for every k-point in one batched call (S: the TMA-staged
+    tile kernel at every order; S^-1: the tile kernel at order 6, the
+    per-k-point kernel at orders 4 and 8) against the oracle's S and a dense
+    inverse of it, every element."""
     w = W.slab() if case == "slab" else CASES[case]()
     h = mbmod.Handle.from_workload(w)
     cdt = np.complex128 if prec == "fp64" else np.complex64
