@@ -453,26 +453,7 @@ __global__ void coef_kernel(const __grid_constant__ CoefArgs<R> a) {
 }
 
 // ---------------------------------------------------------------------------
-// banded operators along j
-// S X: one thread per (band, row j, G) (the 2K-1 rows it reads are shared
-// through L1 with the neighbouring rows' threads)
-template <typename R>
-__global__ void banded_S_kernel(const R *Sband, int order, int nb, int ng, int ldg, int nbands,
-                                const typename V2<R>::T *X, typename V2<R>::T *Y) {
-    typedef typename V2<R>::T R2;
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, b = blockIdx.z;
-    if (g >= ldg) return;
-    const int K = order, W = 2 * K - 1;
-    const R2 *x = X + (size_t)b * nb * ldg + g;
-    R2 s = czero<R2>();
-    if (g < ng) {
-        const int dlo = max(0, K - 1 - j), dhi = min(W, nb + K - 1 - j);
-        for (int dd = dlo; dd < dhi; ++dd) rfma(s, __ldg(&Sband[(size_t)j * W + dd]), x[(size_t)(j + dd - (K - 1)) * ldg]);
-    }
-    Y[(size_t)b * nb * ldg + (size_t)j * ldg + g] = s;
-}
-
+// banded solve along j (the S^-1 of orders without the tile kernel)
 // L L^T y = x with L[j][j-d] = Lb[(j*K + d)], one thread per (band, G)
 // column; the recurrence keeps the last K-1 results in registers and runs
 // over tiles of PD rows whose right-hand sides are all loaded first.
@@ -1494,6 +1475,8 @@ int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X, 
     return MB_OK;
 }
 
+static int apply_sinv_per_k(mb_handle *h, int ik, const void *X, void *Y, int nbands, int prec, cudaStream_t s);
+
 int apply_banded_batch(mb_handle *h, int which, int nsel, const int *iks, const void *const *X, void *const *Y,
                        int nbands, int prec, cudaStream_t s) {
     if (nsel <= 0 || !iks || !X || !Y || nbands <= 0) return MB_EINVAL;
@@ -1509,7 +1492,8 @@ int apply_banded_batch(mb_handle *h, int which, int nsel, const int *iks, const 
     if (banded_block_supported(h, prec, which == BAND_SINV)) {
         rc = banded_block_apply(h, which == BAND_SINV, nsel, iks, X, Y, nbands, prec, s);
     } else {
-        for (int i = 0; i < nsel && rc == MB_OK; ++i) rc = apply_banded(h, which, iks[i], X[i], Y[i], nbands, prec, s);
+        // S has the tile kernel at every order 3-8; this is S^-1 at orders other than 6
+        for (int i = 0; i < nsel && rc == MB_OK; ++i) rc = apply_sinv_per_k(h, iks[i], X[i], Y[i], nbands, prec, s);
     }
     if (rc == MB_OK && h->uspp) {
         // the ultrasoft term on top of S_0 X (grows the scratch: not during stream capture)
@@ -1524,31 +1508,22 @@ int apply_banded_batch(mb_handle *h, int which, int nsel, const int *iks, const 
     return rc;
 }
 
-int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nbands, int prec,
-                 cudaStream_t s) {
-    if (ik < 0 || ik >= (int)h->kp.size() || !X || !Y || nbands <= 0) return MB_EINVAL;
+// S^-1 X for one k-point with the per-column solve kernel (orders whose
+// S^-1 has no tile kernel)
+static int apply_sinv_per_k(mb_handle *h, int ik, const void *X, void *Y, int nbands, int prec, cudaStream_t s) {
+    if (ik < 0 || ik >= (int)h->kp.size() || !X || !Y || X == Y || nbands <= 0) return MB_EINVAL;
     if (prec != MB_FP64 && prec != MB_FP32 && prec != MB_BF16) return MB_EINVAL;
-    if (which != BAND_S && X == Y) return MB_EINVAL;
     MB_CUDA(cudaSetDevice(h->device));
     const KPoint &kp = h->kp[ik];
-    const dim3 gS((kp.ldg + 127) / 128, h->nb, nbands), gL((kp.ldg + 63) / 64, nbands);
-    if (which != BAND_S && which != BAND_SINV) return MB_EINVAL;
+    const dim3 gL((kp.ldg + 63) / 64, nbands);
     if (prec == MB_FP64) {
-        const DevTables &t = h->t64;
-        auto x = reinterpret_cast<const double2 *>(X);
-        auto y = reinterpret_cast<double2 *>(Y);
-        if (which == BAND_S)
-            MB_LAUNCH(h, s, KN_BANDED, banded_S_kernel<double><<<gS, 128, 0, s>>>((const double *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
-        else
-            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<double><<<gL, 64, 0, s>>>((const double *)t.Lband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
+        MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<double><<<gL, 64, 0, s>>>(
+                                       (const double *)h->t64.Lband, h->order, h->nb, kp.ng, kp.ldg, nbands,
+                                       reinterpret_cast<const double2 *>(X), reinterpret_cast<double2 *>(Y)));
     } else {
-        const DevTables &t = h->t32;
-        auto x = reinterpret_cast<const float2 *>(X);
-        auto y = reinterpret_cast<float2 *>(Y);
-        if (which == BAND_S)
-            MB_LAUNCH(h, s, KN_BANDED, banded_S_kernel<float><<<gS, 128, 0, s>>>((const float *)t.Sband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
-        else
-            MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<float><<<gL, 64, 0, s>>>((const float *)t.Lband, h->order, h->nb, kp.ng, kp.ldg, nbands, x, y));
+        MB_LAUNCH(h, s, KN_BANDED, banded_solve_kernel<float><<<gL, 64, 0, s>>>(
+                                       (const float *)h->t32.Lband, h->order, h->nb, kp.ng, kp.ldg, nbands,
+                                       reinterpret_cast<const float2 *>(X), reinterpret_cast<float2 *>(Y)));
     }
     MB_CUDA(cudaGetLastError());
     return MB_OK;

@@ -197,8 +197,6 @@ void dev_free(mb_handle *h, void **p);
 int setup_device(mb_handle *h);
 int apply_H_batch(mb_handle *h, int nsel, const int *iks, const void *const *X,
                   void *const *Y, int nbands, int prec, cudaStream_t s);
-int apply_banded(mb_handle *h, int which, int ik, const void *X, void *Y, int nbands,
-                 int prec, cudaStream_t s);
 int apply_banded_batch(mb_handle *h, int which, int nsel, const int *iks, const void *const *X,
                        void *const *Y, int nbands, int prec, cudaStream_t s);
 size_t apply_scratch_bytes(const mb_handle *h, int nk, int nbands, int prec);
